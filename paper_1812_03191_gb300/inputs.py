@@ -1,0 +1,99 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle's.
+
+This module holds parameter sets and random-number draws only: no step of the
+solver's arithmetic.  Both sides receive the same dicts and arrays from here.
+
+Workloads (all synthetic; the paper uses no dataset):
+  * ``single_mesh``   -- one 32^3 level on [-4,4]^3, Mach 0.5 wind along -x,
+                         GM=0.01, softening 2 cells, chi=1, L=0 (Sec. 3.4 set-up,
+                         transposed to a full box with upstream injection).
+  * ``nested``        -- 3 levels of 64^3 on [-8,8]^3, ratio 2, Mach 0.5, GM=0.01,
+                         chi=1, luminosity L_c = 4 pi GM rho0 chi / gamma (Eq. 49)
+                         deposited as a Gaussian of sigma = softening = 2 finest cells.
+  * ``precision``     -- 5 levels of 128^3 on [-16,16]^3, Mach 1.2, same physics.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# boundary types (same numbering on both sides of the boundary)
+BC_PERIODIC, BC_OUTFLOW, BC_INFLOW, BC_REFLECT = 0, 1, 2, 3
+
+DEFAULT_G = 8      # ghost layers: twice the reach of one level step (measured: 4)
+DEFAULT_BAND = 5   # CommMean band in coarse cells (smallest band with exact results)
+
+
+def base_params(**over) -> dict:
+    p = dict(
+        gamma=5.0 / 3.0, rho0=1.0, cs=1.0, mach=0.5, flow_dir=(-1.0, 0.0, 0.0),
+        GM=0.01, eps=0.5, chi=1.0, L=0.0, lum_sigma=0.0,
+        cfl=0.44, cfl_diff=0.44, dt_fixed=0.0, xi_mode=0,
+        bc=(BC_OUTFLOW, BC_INFLOW, BC_OUTFLOW, BC_OUTFLOW, BC_OUTFLOW, BC_OUTFLOW),
+        diff_face_rho=0, hydro_on=1, band=DEFAULT_BAND,
+    )
+    p.update(over)
+    return p
+
+
+def critical_luminosity(GM, rho0, chi, gamma):
+    """L_c of Eq. 49 (used only to choose the luminosity of a workload)."""
+    return 4.0 * math.pi * GM * rho0 * chi / gamma
+
+
+def wind_bcs(flow_dir):
+    """Injection on the upstream face, outflow elsewhere."""
+    bc = [BC_OUTFLOW] * 6
+    ax = int(np.argmax(np.abs(flow_dir)))
+    bc[2 * ax + (1 if flow_dir[ax] < 0 else 0)] = BC_INFLOW
+    return tuple(bc)
+
+
+def single_mesh():
+    return dict(
+        name="single_mesh_32^3_fp64",
+        n_levels=1, n=32, lo=(-4.0,) * 3, hi=(4.0,) * 3, G=DEFAULT_G, steps=20,
+        params=base_params(eps=0.5),
+    )
+
+
+def nested(n=64, n_levels=3, half=8.0, mach=0.5, steps=1000):
+    dx_f = 2 * half / n / 2 ** (n_levels - 1)
+    eps = 2 * dx_f
+    p = base_params(mach=mach, eps=eps, lum_sigma=eps,
+                    L=critical_luminosity(0.01, 1.0, 1.0, 5.0 / 3.0))
+    return dict(
+        name=f"nested_{n_levels}x{n}^3_fp64",
+        n_levels=n_levels, n=n, lo=(-half,) * 3, hi=(half,) * 3, G=DEFAULT_G, steps=steps,
+        params=p,
+    )
+
+
+def precision(n=128, n_levels=5, half=16.0):
+    cfg = nested(n=n, n_levels=n_levels, half=half, mach=1.2, steps=50)
+    cfg["name"] = f"precision_{n_levels}x{n}^3"
+    return cfg
+
+
+def smooth_perturbation(shape, seed, amp, n_modes=4):
+    """Sum of a few random low-wavenumber periodic modes (shape = (nz, ny, nx))."""
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz) / nz, np.arange(ny) / ny, np.arange(nx) / nx,
+                          indexing="ij")
+    out = np.zeros(shape)
+    for _ in range(n_modes):
+        kx, ky, kz = rng.integers(0, 3, size=3)
+        ph = rng.uniform(0, 2 * np.pi)
+        out += rng.uniform(-1, 1) * np.cos(2 * np.pi * (kx * x + ky * y + kz * z) + ph)
+    return amp * out / n_modes
+
+
+def random_state(n, n_levels, seed, amp=1e-2):
+    """Per-level multiplicative/additive perturbations of (rho, e, vx, vy, vz)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_levels):
+        out.append([rng.standard_normal((n, n, n)) * amp for _ in range(5)])
+    return out
