@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark of one coarse step of the nested-mesh solver on GB300.
+
+Workload (default): 3 nested levels of 64^3 cells, ratio 2, coarse box [-8,8]^3,
+Mach 0.5 wind, GM=0.01, chi=1, Gaussian luminosity L_c, FP64 state (the nested
+configuration the metric is quoted on).  A step is one coarse step: the Eq. 55
+time-step reduction, the Sec. 3.3 recursion over all levels (7 level steps),
+CommFlux/CommUp/CommMean, and the Eq. 18 force reduction.
+
+Metric: cell-updates/s summed over levels (sub-cycles counted).  `value` is timed
+with inputs resident in HBM; `e2e` through the C ABI with the state uploaded from
+pinned host memory and the force read back every step.  Multi-GPU runs are
+independent replicas (weak scaling, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on
+bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1812_03191_gb300 import inputs as I  # noqa: E402
+
+METRIC = "cell-updates/s"
+UNIT = "cell-updates/s"
+
+
+def workload(name):
+    if name == "nested":
+        return I.nested()
+    if name == "single":
+        return I.single_mesh()
+    if name == "precision":
+        return I.precision()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def cell_updates_per_step(cfg):
+    n = cfg["n"]
+    n3 = n**3 if isinstance(n, int) else n[0] * n[1] * n[2]
+    return sum(n3 * 2**l for l in range(cfg["n_levels"]))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- algorithmic bytes
+# Arrays each stencil kernel reads + writes once per element of its box (the
+# compulsory traffic of the kernel as designed, neighbour reuse assumed cached).
+ARRAYS_PER_ELEM = {
+    "source": 12,        # rho, e, phi, v3 -> v3, pi3
+    "compress_lum": 8,   # e, v3, rho, lumw -> e, e/rho
+    "diffuse": 4,        # rho, e/rho, e -> e
+    "tprep": 9,          # rho, e, pi3 -> e/rho, w3
+    "tflux": 5,          # rho, e/rho, v_d -> F, E
+    "tmom": 8,           # w3, F, v_d -> P3
+    "tupdate": 15,       # F, E, P3, rho, e, pi3 -> rho, e, pi3
+    "vrec_source": 9,    # rho, e, phi, pi3 -> v3
+}
+
+
+def level_step_boxes(cfg):
+    """box elements of every level step of one coarse step (level 0: margin 4;
+    finer levels: first sub-cycle margin 8, second margin 4, capped at the array)."""
+    n, G = cfg["n"], cfg["G"]
+    margins = [4]
+    for l in range(1, cfg["n_levels"]):
+        margins += [8, 4] * 2 ** (l - 1)
+    return [min(n + 2 * m, n + 2 * G) ** 3 for m in margins]
+
+
+def bytes_per_launch(cfg, kind, esz):
+    boxes = level_step_boxes(cfg)
+    n, G = cfg["n"], cfg["G"]
+    if kind in ARRAYS_PER_ELEM:
+        return ARRAYS_PER_ELEM[kind] * esz * sum(boxes) / len(boxes)
+    if kind == "commup":  # write every fine ghost element, read each coarse host once
+        return 5 * esz * (((n + 2 * G) ** 3 - n**3) + (n // 2 + G + 2) ** 3)
+    if kind == "commmean":  # read 8 fine cells / 4 faces, write the covered coarse cell
+        return 5 * esz * (n**3 + (n // 2) ** 3)
+    return None
+
+
+def cpu_oracle_rate(cfg, budget_s, steps_cap=None):
+    """Oracle cell-updates/s on a bounded sample: whole coarse steps until budget."""
+    from oracle import Oracle
+    lo, hi = cfg["lo"], cfg["hi"]
+    orc = Oracle(cfg["n_levels"], cfg["n"], lo, hi, cfg["G"], cfg["params"])
+    cu = cell_updates_per_step(cfg)
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        orc.step(1)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (steps_cap and done >= steps_cap):
+            break
+    orc.close()
+    return cu * done / el, done, el
+
+
+def run_reference(args, cfg):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cu = cell_updates_per_step(cfg)
+    from oracle import Oracle
+    orc = Oracle(cfg["n_levels"], cfg["n"], cfg["lo"], cfg["hi"], cfg["G"], cfg["params"])
+    for _ in range(args.warmup):
+        orc.step(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.step(1)
+        times.append(time.perf_counter() - t0)
+    orc.close()
+    tot = sum(times)
+    value = cu * args.steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "n_levels": cfg["n_levels"], "n": cfg["n"],
+                   "box": [cfg["lo"][0], cfg["hi"][0]], "ghost": cfg["G"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} whole coarse steps of {cfg['name']} "
+                                   f"after {args.warmup} warm-up steps, single-threaded C"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nested", choices=["nested", "single", "precision"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    cfg = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+
+    from paper_1812_03191_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # CPU baseline first (oracle on the host cores, rank 0 only, bounded sample)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, nsteps, el = cpu_oracle_rate(cfg, args.cpu_budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{nsteps} whole coarse steps of {cfg['name']} ({el:.1f} s, "
+                         f"single-threaded C, -O2)"}
+
+    prec = binding.DF_FP64 if args.precision == "fp64" else binding.DF_FP32_STATE
+    stream = torch.cuda.current_stream()
+    sim = binding.Sim(cfg["n_levels"], cfg["n"], cfg["lo"], cfg["hi"], cfg["G"], cfg["params"],
+                      precision=prec, device=local, stream=stream.cuda_stream)
+    cu = cell_updates_per_step(cfg)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K graph-replayed coarse steps, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    l0 = sim.kernel_launches()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = sim.kernel_launches() - l0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = cu * args.steps * world / (ms / 1e3)
+    clocks = clk.summary()
+    F, Fmot = sim.force()
+
+    # ---- per-kernel device time over the same number of steps (events per launch)
+    sim.set_timing(True)
+    for k in range(args.steps):
+        flush.zero_()
+        sim.step(1)
+    kinds = {}
+    for kind in range(binding.KERNEL_KINDS):
+        kms, kn = sim.kernel_time(kind)
+        if kn:
+            kinds[binding.kernel_name(kind)] = (kms, kn)
+    sim.set_timing(False)
+    total_k = sum(v[0] for v in kinds.values())
+    esz = 8 if prec == binding.DF_FP64 else 4
+    # dominant kernel with a defined algorithmic byte count
+    ranked = sorted(kinds, key=lambda k: -kinds[k][0])
+    dom = next(k for k in ranked if bytes_per_launch(cfg, k, esz) is not None)
+    dom_ms, dom_n = kinds[dom]
+    bpl = bytes_per_launch(cfg, dom, esz)
+    avg_s = dom_ms / dom_n / 1e3
+    achieved = bpl / avg_s / 1e9
+    peak, peak_kind = peaks()
+    roofline = {
+        "kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+        "algorithmic_bytes_per_launch": bpl, "launches_timed": dom_n,
+        "avg_launch_ms": dom_ms / dom_n,
+        "share_of_kernel_time": dom_ms / total_k if total_k else None,
+        "top_kernel": ranked[0],
+    }
+
+    # ---- e2e: state from pinned host memory, one step, force back, every step
+    nstate = sim.state_size()
+    host = torch.empty(nstate, dtype=torch.float64, pin_memory=True)
+    st_np, t_now = sim.get_state(host.numpy())
+    e2e_times = []
+    for k in range(max(3, min(args.steps, 20))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.set_state(st_np, t_now)
+        sim.step(1)
+        sim.force()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    e2e = {"value": cu * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nstate * 8,
+           "d2h_bytes_per_step": 3 * 8 + 4}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == binding.DF_FP64 else "f32-state/f64-reductions",
+            "data": "synthetic",
+            "config": {"workload": cfg["name"], "n_levels": cfg["n_levels"], "n": cfg["n"],
+                       "box": [cfg["lo"][0], cfg["hi"][0]], "ghost": cfg["G"],
+                       "cell_updates_per_step": cu, "l2": "flushed between timed steps "
+                       "(256 MB write outside the step events)",
+                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kinds.items(),
+                                                                 key=lambda x: -x[1][0])},
+            "force": {"F": list(F), "F_along_motion": Fmot},
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,163 @@
+/*
+ * dfnest.h -- C ABI of libdfnest.so, the GB300 (sm_103a) nested-mesh solver of
+ * Velasco Romero & Masset (2018), "Numerical study of dynamical friction with
+ * thermal effects -- I", Sec. 3 (nested meshes) and Sec. 3.4 (set-up).
+ *
+ * A context holds one hierarchy of n_levels nested Cartesian meshes, refinement
+ * ratio 2 (Sec. 3), all resident in the memory of one GPU.  Level l covers
+ * [lo*2^-l, hi*2^-l] with n[0] x n[1] x n[2] active cells and G ghost layers.
+ * Fields: 0 rho (density), 1 e (internal energy density), 2..4 v_x, v_y, v_z.
+ * rho and e are cell-centred; v_d sits on the lower d-face of its cell (staggered).
+ * Host arrays are x-fastest, i.e. index ((k*ny)+j)*nx+i.
+ *
+ * Conventions shared by every call:
+ *  - return value: DF_OK (0) or a negative DF_E* code; df_last_error() gives a
+ *    message for the calling thread.  No call aborts the process.
+ *  - the context owns every device allocation it makes; the caller owns every
+ *    host buffer it passes (read or written synchronously before return).
+ *  - work is issued on the stream given at creation (a cudaStream_t, NULL for
+ *    the legacy default stream); calls that return host data synchronise it.
+ *  - a context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef DFNEST_H
+#define DFNEST_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DF_OK 0
+#define DF_EINVAL (-1)     /* bad argument, size or geometry */
+#define DF_ENOMEM (-2)     /* device or host allocation failed */
+#define DF_ECUDA (-3)      /* a CUDA runtime call failed */
+#define DF_EUNHEALTHY (-4) /* NaN, rho <= 0 or e <= 0 found by the time-step reduction */
+#define DF_ETIMEOUT (-5)   /* reserved: a bounded device wait ran out */
+#define DF_EBUSY (-6)      /* reserved: no capacity */
+
+#define DF_MAX_LEVELS 16
+
+/* level-0 boundary types, one per face -x,+x,-y,+y,-z,+z */
+#define DF_BC_PERIODIC 0
+#define DF_BC_OUTFLOW 1 /* zero gradient: copy of the nearest active element */
+#define DF_BC_INFLOW 2  /* background rho0, e0, V in every ghost element (injection) */
+#define DF_BC_REFLECT 3 /* mirror, normal velocity odd (Sec. 3.4 symmetric/antisymmetric) */
+
+/* state precision */
+#define DF_FP64 0       /* FP64 state and arithmetic */
+#define DF_FP32_STATE 1 /* FP32 state and stencils; FP64 force, time step, flux sums */
+
+typedef struct {
+  double gamma;       /* adiabatic index; p = (gamma-1) e (Sec. 2.1) */
+  double rho0;        /* background density (Sec. 3.4) */
+  double cs;          /* background adiabatic sound speed; e0 = cs^2 rho0/(gamma(gamma-1)) */
+  double mach;        /* |V|/cs of the wind */
+  double flow_dir[3]; /* unit vector of the wind V (the perturber moves along -V) */
+  double GM;          /* perturber mass, Plummer potential Phi = -GM/sqrt(r^2+eps^2) (Eq. 16) */
+  double eps;         /* softening length, also in the force sum (Eq. 18) */
+  double chi;         /* thermal diffusivity (Eq. 3, Eqs. 19-22) */
+  double L;           /* luminosity (Sec. 3.4): L dt added per level step */
+  double lum_sigma;   /* 0: split over the 8 cells at the vertex; >0: Gaussian, this sigma */
+  double cfl;         /* Courant number of the advective limit */
+  double cfl_diff;    /* safety factor of the explicit-diffusion limit 1/(2 chi sum dx^-2) */
+  double dt_fixed;    /* >0: coarse step used instead of the reduction */
+  int xi_mode;        /* 0: xi = 2 on every level (Sec. 3.1); 1: Eq. 55-56 search per step */
+  int bc[6];          /* DF_BC_* of level 0 */
+  int diff_face_rho;  /* 0: face density = mean of the two cells (Eq. 3); 1: rho0 (Eqs. 19-21) */
+  int hydro_on;       /* 0 freezes rho and v (pure diffusion) */
+  int band;           /* CommMean band width in coarse cells (Sec. 3.2.2); default 5 */
+} df_params;
+
+typedef struct df_ctx df_ctx;
+
+/* Create a hierarchy (Sec. 3, Sec. 3.4).  n[d] % 4 == 0, n[d] >= 8, n[d] >= G; G even
+ * and >= 2 (G >= 8 makes the active cells independent of the ghost width); every finer level
+ * must sit on parent faces with its ghosts and the 27-point CommUp stencil inside
+ * the parent's active cells (offset >= G/2+1 parent cells on each side).
+ * precision: DF_FP64 or DF_FP32_STATE.  device: CUDA ordinal (made current).
+ * stream: cudaStream_t or NULL.  The state is uninitialised until df_set_params.
+ * Errors: DF_EINVAL (geometry), DF_ENOMEM, DF_ECUDA. */
+int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], const double hi[3],
+              int G, int precision, int device, void* stream);
+
+/* Copy the parameters, precompute the static potential (Eq. 16) and luminosity
+ * weights, and set every level to the uniform background (Sec. 3.4): rho0, e0, V.
+ * Resets t to 0 and clears the force history.  DF_EINVAL on bad values. */
+int df_set_params(df_ctx* ctx, const df_params* p);
+
+/* Advance n coarse steps: per step the time step of Eq. 55 (reductions on the
+ * device), then the recursion of Sec. 3.3 (finer levels first, xi sub-cycles,
+ * CommFlux, CommUp, CommMean), then the force of Eq. 18.  Asynchronous on the
+ * context's stream; DF_EUNHEALTHY is reported by the next synchronising call. */
+int df_step(df_ctx* ctx, int n_coarse_steps);
+
+/* Synchronise, then return time, last coarse step and health (0 healthy). */
+int df_status(df_ctx* ctx, double* t, double* dt_last, int* unhealthy);
+
+/* Force on the perturber after the last coarse step (Eq. 18 with rho - rho0,
+ * covered coarse cells excluded), FP64.  F_along_motion (nullable) = F . (-V/|V|).
+ * Synchronises.  Before any step it is the force of the current state. */
+int df_force(df_ctx* ctx, double F_out[3], double* F_along_motion);
+
+/* Recompute the force of the current state now (does not advance). */
+int df_force_now(df_ctx* ctx, double F_out[3]);
+
+/* Time step the next coarse step would take (Eq. 55) and the per-level limits
+ * (dt_level nullable, n_levels entries).  Synchronises. */
+int df_compute_dt(df_ctx* ctx, double* dt, double* dt_level);
+
+/* Active cells of one field of one level as FP64 (n0*n1*n2, x fastest). Sync. */
+int df_get_field(df_ctx* ctx, int level, int field, double* host_out);
+int df_set_field(df_ctx* ctx, int level, int field, const double* host_in);
+
+/* Whole padded array ((n+2G)^3 elements, x fastest) of one field, FP64. Sync. */
+int df_get_full(df_ctx* ctx, int level, int field, double* host_out);
+int df_set_full(df_ctx* ctx, int level, int field, const double* host_in);
+
+/* Checkpoint: every padded field of every level plus (t, step) as FP64, in the
+ * order level-major, field-minor.  df_state_size gives the element count. */
+size_t df_state_size(const df_ctx* ctx);
+int df_get_state(df_ctx* ctx, double* host_out, double* t_out);
+int df_set_state(df_ctx* ctx, const double* host_in, double t);
+
+/* Inter-level operators on demand (Sec. 3.2): CommUp fills every ghost element
+ * of level coarse_level+1 from coarse_level; CommMean overwrites the band of
+ * coarse_level from coarse_level+1; fill_bc applies the level-0 boundaries. */
+int df_prolong(df_ctx* ctx, int coarse_level);
+int df_restrict(df_ctx* ctx, int coarse_level);
+int df_fill_bc(df_ctx* ctx);
+
+/* Number of kernels launched by this context since creation (counts every
+ * launch, graph replays included). */
+long long df_kernel_launches(const df_ctx* ctx);
+
+/* Timing hook.  With timing on, df_step launches without the CUDA graph and
+ * brackets every kernel with a pooled pair of CUDA events on the context's
+ * stream (no host synchronisation inside a step).  df_kernel_time synchronises,
+ * then returns the summed device time (ms) and launch count of one kernel kind
+ * since df_set_timing; df_kernel_name(kind) names the kinds 0..DF_KERNEL_KINDS-1.
+ * df_set_timing resets the totals. */
+#define DF_KERNEL_KINDS 16
+int df_set_timing(df_ctx* ctx, int on);
+int df_kernel_time(df_ctx* ctx, int kind, double* ms, long long* launches);
+const char* df_kernel_name(int kind);
+
+/* Verification switch: with on != 0 every operator runs over its whole stencil
+ * range in the padded array (the ghost layers evolve exactly as in a plain
+ * sweep of the whole array) instead of the active box plus the reach margin.
+ * Active cells are identical either way when G >= 8. */
+int df_debug_full_boxes(df_ctx* ctx, int on);
+
+int df_destroy(df_ctx* ctx);
+
+/* Eq. 55-56 (Appendix A): brute force over xi in {1,2}^(n-1), maximising dt/C. */
+int df_xi_search(int n, const double* dt_level, const double* cost, int* xi_out, double* ratio);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* df_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,271 @@
+"""ctypes binding of libdfnest.so (C ABI in include/dfnest.h).
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  There is no fallback: if the library is missing or no GPU is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdfnest.so")
+
+DF_OK, DF_EINVAL, DF_ENOMEM, DF_ECUDA, DF_EUNHEALTHY, DF_ETIMEOUT, DF_EBUSY = 0, -1, -2, -3, -4, -5, -6
+DF_FP64, DF_FP32_STATE = 0, 1
+KERNEL_KINDS = 16
+
+# every symbol include/dfnest.h declares
+EXPORTS = (
+    "df_create", "df_set_params", "df_step", "df_status", "df_force", "df_force_now",
+    "df_compute_dt", "df_get_field", "df_set_field", "df_get_full", "df_set_full",
+    "df_state_size", "df_get_state", "df_set_state", "df_prolong", "df_restrict",
+    "df_fill_bc", "df_kernel_launches", "df_set_timing", "df_kernel_time", "df_kernel_name",
+    "df_debug_full_boxes", "df_destroy", "df_xi_search", "df_last_error",
+)
+
+
+class DfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dfnest error {code}: {msg}")
+        self.code = code
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("gamma", C.c_double), ("rho0", C.c_double), ("cs", C.c_double), ("mach", C.c_double),
+        ("flow_dir", C.c_double * 3), ("GM", C.c_double), ("eps", C.c_double),
+        ("chi", C.c_double), ("L", C.c_double), ("lum_sigma", C.c_double),
+        ("cfl", C.c_double), ("cfl_diff", C.c_double), ("dt_fixed", C.c_double),
+        ("xi_mode", C.c_int), ("bc", C.c_int * 6), ("diff_face_rho", C.c_int),
+        ("hydro_on", C.c_int), ("band", C.c_int),
+    ]
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Params":
+        p = cls()
+        for k, v in d.items():
+            if k in ("flow_dir", "bc"):
+                arr = getattr(p, k)
+                for i, x in enumerate(v):
+                    arr[i] = x
+            else:
+                setattr(p, k, v)
+        return p
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run __graft_entry__.build() (nvcc, sm_103a)")
+    lib = C.CDLL(path)
+    P, dp, vp = C.POINTER, C.POINTER(C.c_double), C.c_void_p
+    sig = {
+        "df_create": (C.c_int, [P(vp), C.c_int, P(C.c_int), dp, dp, C.c_int, C.c_int, C.c_int, vp]),
+        "df_set_params": (C.c_int, [vp, P(Params)]),
+        "df_step": (C.c_int, [vp, C.c_int]),
+        "df_status": (C.c_int, [vp, dp, dp, P(C.c_int)]),
+        "df_force": (C.c_int, [vp, dp, dp]),
+        "df_force_now": (C.c_int, [vp, dp]),
+        "df_compute_dt": (C.c_int, [vp, dp, dp]),
+        "df_get_field": (C.c_int, [vp, C.c_int, C.c_int, dp]),
+        "df_set_field": (C.c_int, [vp, C.c_int, C.c_int, dp]),
+        "df_get_full": (C.c_int, [vp, C.c_int, C.c_int, dp]),
+        "df_set_full": (C.c_int, [vp, C.c_int, C.c_int, dp]),
+        "df_state_size": (C.c_size_t, [vp]),
+        "df_get_state": (C.c_int, [vp, dp, dp]),
+        "df_set_state": (C.c_int, [vp, dp, C.c_double]),
+        "df_prolong": (C.c_int, [vp, C.c_int]),
+        "df_restrict": (C.c_int, [vp, C.c_int]),
+        "df_fill_bc": (C.c_int, [vp]),
+        "df_kernel_launches": (C.c_longlong, [vp]),
+        "df_set_timing": (C.c_int, [vp, C.c_int]),
+        "df_kernel_time": (C.c_int, [vp, C.c_int, dp, P(C.c_longlong)]),
+        "df_kernel_name": (C.c_char_p, [C.c_int]),
+        "df_debug_full_boxes": (C.c_int, [vp, C.c_int]),
+        "df_destroy": (C.c_int, [vp]),
+        "df_xi_search": (C.c_int, [C.c_int, dp, dp, P(C.c_int), dp]),
+        "df_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != DF_OK:
+        raise DfError(rc, _lib.df_last_error().decode())
+    return rc
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def kernel_name(kind: int) -> str:
+    return load().df_kernel_name(kind).decode()
+
+
+def xi_search(dt_level, cost):
+    lib = load()
+    n = len(dt_level)
+    a = np.ascontiguousarray(dt_level, dtype=np.float64)
+    b = np.ascontiguousarray(cost, dtype=np.float64)
+    xi = (C.c_int * max(n - 1, 1))()
+    r = C.c_double()
+    _check(lib.df_xi_search(n, _dp(a), _dp(b), xi, C.byref(r)))
+    return r.value, [xi[i] for i in range(n - 1)]
+
+
+class Sim:
+    """One nested hierarchy resident on one GPU (a df_ctx)."""
+
+    def __init__(self, n_levels, n, lo, hi, G, params: dict | None = None,
+                 precision=DF_FP64, device=0, stream=None):
+        lib = load()
+        self.lib = lib
+        if isinstance(n, int):
+            n = (n, n, n)
+        self.n = tuple(int(x) for x in n)
+        self.n_levels = int(n_levels)
+        self.G = int(G)
+        self.precision = precision
+        h = C.c_void_p()
+        na = (C.c_int * 3)(*self.n)
+        lo_ = (C.c_double * 3)(*lo)
+        hi_ = (C.c_double * 3)(*hi)
+        st = C.c_void_p(stream) if stream else None
+        _check(lib.df_create(C.byref(h), self.n_levels, na, lo_, hi_, self.G, precision,
+                             device, st))
+        self.h = h
+        if params is not None:
+            self.set_params(params)
+
+    # lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.df_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # calls
+    def set_params(self, params: dict):
+        self.params = dict(params)
+        _check(self.lib.df_set_params(self.h, C.byref(Params.from_dict(params))))
+
+    def step(self, n=1):
+        _check(self.lib.df_step(self.h, int(n)))
+
+    def status(self):
+        t, dt = C.c_double(), C.c_double()
+        bad = C.c_int()
+        _check(self.lib.df_status(self.h, C.byref(t), C.byref(dt), C.byref(bad)))
+        return t.value, dt.value, bad.value
+
+    @property
+    def t(self):
+        return self.status()[0]
+
+    def force(self):
+        F = np.zeros(3)
+        along = C.c_double()
+        _check(self.lib.df_force(self.h, _dp(F), C.byref(along)))
+        return F, along.value
+
+    def force_now(self):
+        F = np.zeros(3)
+        _check(self.lib.df_force_now(self.h, _dp(F)))
+        return F
+
+    def compute_dt(self):
+        dt = C.c_double()
+        lv = np.zeros(self.n_levels)
+        _check(self.lib.df_compute_dt(self.h, C.byref(dt), _dp(lv)))
+        return dt.value, lv
+
+    def get_field(self, level, field):
+        nx, ny, nz = self.n
+        out = np.empty(nx * ny * nz)
+        _check(self.lib.df_get_field(self.h, level, field, _dp(out)))
+        return out.reshape(nz, ny, nx)
+
+    def set_field(self, level, field, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).ravel()
+        if a.size != self.n[0] * self.n[1] * self.n[2]:
+            raise ValueError("wrong size")
+        _check(self.lib.df_set_field(self.h, level, field, _dp(a)))
+
+    def full_shape(self):
+        return tuple(x + 2 * self.G for x in self.n[::-1])
+
+    def get_full(self, level, field):
+        out = np.empty(int(np.prod(self.full_shape())))
+        _check(self.lib.df_get_full(self.h, level, field, _dp(out)))
+        return out.reshape(self.full_shape())
+
+    def set_full(self, level, field, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).ravel()
+        if a.size != int(np.prod(self.full_shape())):
+            raise ValueError("wrong size")
+        _check(self.lib.df_set_full(self.h, level, field, _dp(a)))
+
+    def state_size(self):
+        return int(self.lib.df_state_size(self.h))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.state_size())
+        t = C.c_double()
+        _check(self.lib.df_get_state(self.h, _dp(out), C.byref(t)))
+        return out, t.value
+
+    def set_state(self, state, t):
+        a = np.ascontiguousarray(state, dtype=np.float64)
+        _check(self.lib.df_set_state(self.h, _dp(a), float(t)))
+
+    def prolong(self, coarse_level):
+        _check(self.lib.df_prolong(self.h, coarse_level))
+
+    def restrict(self, coarse_level):
+        _check(self.lib.df_restrict(self.h, coarse_level))
+
+    def fill_bc(self):
+        _check(self.lib.df_fill_bc(self.h))
+
+    def kernel_launches(self):
+        return int(self.lib.df_kernel_launches(self.h))
+
+    def set_timing(self, on):
+        _check(self.lib.df_set_timing(self.h, 1 if on else 0))
+
+    def kernel_time(self, kind):
+        ms = C.c_double()
+        n = C.c_longlong()
+        _check(self.lib.df_kernel_time(self.h, kind, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def debug_full_boxes(self, on):
+        _check(self.lib.df_debug_full_boxes(self.h, 1 if on else 0))

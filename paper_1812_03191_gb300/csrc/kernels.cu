@@ -1,0 +1,1112 @@
+// kernels.cu -- sm_103a kernels of one level step of the nested-mesh solver
+// (Velasco Romero & Masset 2018, Sec. 3) and of the inter-level operators.
+//
+// Each stencil kernel is one thread per element of a box (flattened, x fastest, so
+// consecutive threads touch consecutive addresses).  A kernel applies its operator
+// to the elements of the box where its stencil fits inside the padded array; the
+// host picks the box (the active cells plus the margin whose values can still reach
+// them before the next ghost fill).  T is the state type (double, or float for the
+// FP32-state form); time steps, the force and the frontier flux sums are FP64.
+#include "internal.h"
+
+#include <math.h>
+
+namespace dfn {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+__device__ __forceinline__ bool decode(const Box& b, long long t, int& i, int& j, int& k) {
+  int bx = b.hi[0] - b.lo[0], by = b.hi[1] - b.lo[1], bz = b.hi[2] - b.lo[2];
+  long long plane = (long long)bx * by;
+  if (t >= plane * bz) return false;
+  int kk = (int)(t / plane);
+  int r = (int)(t - (long long)kk * plane);
+  int jj = r / bx;
+  i = b.lo[0] + (r - jj * bx);
+  j = b.lo[1] + jj;
+  k = b.lo[2] + kk;
+  return true;
+}
+
+__device__ __forceinline__ int cidx(const LevelView& L, int i, int j, int k) {
+  return (k * L.s[1] + j) * L.s[0] + i;
+}
+
+// van Leer (1977) harmonic limited slope (Sec. 3.2.1 cites it for the interpolation)
+template <class T>
+__device__ __forceinline__ T vanleer(T dl, T dr) {
+  T pr = dl * dr;
+  return pr <= T(0) ? T(0) : (T(2) * pr) / (dl + dr);
+}
+
+// time-centred upwind value at the face between elements c-st and c
+template <class T>
+__device__ __forceinline__ T upwind(const T* __restrict__ q, int c, int st, T u, T cour) {
+  if (u > T(0)) {
+    T a = q[c - st];
+    T sl = vanleer(a - q[c - 2 * st], q[c] - a);
+    return a + T(0.5) * (T(1) - cour) * sl;
+  }
+  T a = q[c];
+  T sr = vanleer(a - q[c - st], q[c + st] - a);
+  return a - T(0.5) * (T(1) + cour) * sr;
+}
+
+// products that are later differenced must be rounded on their own: a multiply
+// fused into the subtraction would return the rounding error of the product
+// instead of an exact zero for equal inputs (uniform states stay uniform)
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+// coarse frontier face test: returns side (0/1) and the slot, or -1
+__device__ __forceinline__ int coarse_frontier(const LevelView& L, int d, int f0, int f1, int f2,
+                                               int& slot) {
+  int f[3] = {f0, f1, f2};
+  int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  int a = f[t1] - L.G - L.coff[t1], b = f[t2] - L.G - L.coff[t2];
+  int h1 = L.cn[t1] >> 1, h2 = L.cn[t2] >> 1;
+  if (a < 0 || a >= h1 || b < 0 || b >= h2) return -1;
+  int lo = L.G + L.coff[d];
+  int side = f[d] == lo ? 0 : (f[d] == lo + (L.cn[d] >> 1) ? 1 : -1);
+  slot = b * h1 + a;
+  return side;
+}
+
+// ------------------------------------------------------------------ source S
+// S(h) of Eq. 15: v_d -= h [ (p_c - p_m)/(dx rho_face) + (Phi_c - Phi_m)/dx ]
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_source(LevelView L, Box b, Scratch S,
+                                                   const double* __restrict__ dtp, double hscale,
+                                                   int write_pi, T gm1) {
+  int i, j, k;
+  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  const T* __restrict__ rho = (const T*)L.q[F_RHO];
+  const T* __restrict__ e = (const T*)L.q[F_E];
+  const T* __restrict__ phi = (const T*)L.phi;
+  const T h = (T)(hscale * dtp[0]);
+  const int c = cidx(L, i, j, k);
+  const int c3[3] = {i, j, k};
+  const T rc = rho[c], pc = mul_rn(gm1, e[c]), fc = phi[c];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T* v = (T*)L.q[F_VX + d];
+    if (c3[d] >= 1) {
+      int m = c - L.st[d];
+      T pl = mul_rn(gm1, e[m]);
+      T rf = T(0.5) * (rho[m] + rc);
+      T acc = ((pc - pl) / rf + (fc - phi[m])) * (T)L.inv_dx[d];
+      T vn = v[c] - h * acc;
+      v[c] = vn;
+      if (write_pi) ((T*)S.pi[d])[c] = rf * vn;
+    } else if (write_pi) {
+      ((T*)S.pi[d])[c] = T(0);
+    }
+  }
+}
+
+// ------------------------------------------------- SubStep3 + luminosity + e/rho
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_compress_lum(LevelView L, Box b, Scratch S,
+                                                         const double* __restrict__ dtp, T gm1,
+                                                         T lum, int do_ss3, int do_lum,
+                                                         int do_eps) {
+  int i, j, k;
+  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  const T dt = (T)(dtp[0] * L.dt_scale);
+  const int c = cidx(L, i, j, k);
+  T* e = (T*)L.q[F_E];
+  T ec = e[c];
+  if (do_ss3 && i < L.s[0] - 1 && j < L.s[1] - 1 && k < L.s[2] - 1) {
+    const T* vx = (const T*)L.q[F_VX];
+    const T* vy = (const T*)L.q[F_VX + 1];
+    const T* vz = (const T*)L.q[F_VX + 2];
+    T div = (vx[c + L.st[0]] - vx[c]) * (T)L.inv_dx[0] +
+            (vy[c + L.st[1]] - vy[c]) * (T)L.inv_dx[1] + (vz[c + L.st[2]] - vz[c]) * (T)L.inv_dx[2];
+    T a = T(0.5) * dt * gm1 * div;
+    ec = ec * (T(1) - a) / (T(1) + a);
+  }
+  if (do_lum && i >= L.G && i < L.G + L.n[0] && j >= L.G && j < L.G + L.n[1] && k >= L.G &&
+      k < L.G + L.n[2])
+    ec = ec + lum * dt * ((const T*)L.lumw)[c];
+  e[c] = ec;
+  if (do_eps) ((T*)S.eps)[c] = ec / ((const T*)L.q[F_RHO])[c];
+}
+
+// --------------------------------------------------------------- diffusion
+// energy moved in +d across a face during dt: -chi rho_f d(e/rho)/dx * area * dt
+template <class T>
+__device__ __forceinline__ T diff_flux(const LevelView& L, const T* __restrict__ rho,
+                                       const T* __restrict__ eps, int f, int d, T chi, T dt,
+                                       T rho0, int dfr) {
+  int m = f - L.st[d];
+  T rf = dfr ? rho0 : T(0.5) * (rho[m] + rho[f]);
+  return -chi * rf * (eps[f] - eps[m]) * (T)L.dcoef[d] * dt;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_diffuse(LevelView L, Box b, Scratch S,
+                                                    const double* __restrict__ dtp, T chi,
+                                                    T rho0, int dfr) {
+  int i, j, k;
+  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  if (i < 1 || j < 1 || k < 1 || i >= L.s[0] - 1 || j >= L.s[1] - 1 || k >= L.s[2] - 1) return;
+  const T dt = (T)(dtp[0] * L.dt_scale);
+  const T* __restrict__ rho = (const T*)L.q[F_RHO];
+  const T* __restrict__ eps = (const T*)S.eps;
+  const int c = cidx(L, i, j, k);
+  const int c3[3] = {i, j, k};
+  T div = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int up = c + L.st[d];
+    T qlo = diff_flux(L, rho, eps, c, d, chi, dt, rho0, dfr);
+    T qhi = diff_flux(L, rho, eps, up, d, chi, dt, rho0, dfr);
+    if (L.has_child) {
+      int slot, f3[3] = {c3[0], c3[1], c3[2]};
+      int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+      if (side >= 0) qlo = (T)L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot];
+      f3[d] += 1;
+      side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+      if (side >= 0) qhi = (T)L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot];
+    }
+    div += qhi - qlo;
+  }
+  T* e = (T*)L.q[F_E];
+  e[c] = e[c] - div * (T)L.inv_vol;
+}
+
+// fine frontier faces of one side: the 4 faces of one coarse slot, accumulated in
+// the order (u,v) = (0,0), (1,0), (0,1), (1,1)
+__device__ __forceinline__ void fine_face(const LevelView& L, int side, int a, int b, int u,
+                                          int v, int& f) {
+  int d = side >> 1, hi = side & 1;
+  int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  int c3[3];
+  c3[d] = L.G + (hi ? L.n[d] : 0);
+  c3[t1] = L.G + 2 * a + u;
+  c3[t2] = L.G + 2 * b + v;
+  f = (c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0];
+}
+
+__device__ __forceinline__ bool slot_of(const LevelView& L, long long t, int sides_lo,
+                                        int n_sides, int& side, int& a, int& b) {
+  // slots are laid out side-major; every side of axis d has (n_t1/2)*(n_t2/2) slots
+  int rem = (int)t;
+  for (int s = sides_lo; s < sides_lo + n_sides; ++s) {
+    int d = s >> 1;
+    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    int h1 = L.n[t1] >> 1, h2 = L.n[t2] >> 1;
+    if (rem < h1 * h2) {
+      side = s;
+      a = rem % h1;
+      b = rem / h1;
+      return true;
+    }
+    rem -= h1 * h2;
+  }
+  return false;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_frontier_diff(LevelView L, Scratch S,
+                                                          const double* __restrict__ dtp, T chi,
+                                                          T rho0, int dfr) {
+  int side, a, b;
+  if (!slot_of(L, blockIdx.x * (long long)kBlock + threadIdx.x, 0, 6, side, a, b)) return;
+  const T dt = (T)(dtp[0] * L.dt_scale);
+  const int d = side >> 1;
+  const int t1 = d == 0 ? 1 : 0;
+  const int slot = b * (L.n[t1] >> 1) + a;
+  double* acc = L.acc + (side * 3 + 2) * L.acc_slots + slot;
+  double s = *acc;
+#pragma unroll
+  for (int v = 0; v < 2; ++v)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      int f;
+      fine_face(L, side, a, b, u, v, f);
+      s += (double)diff_flux(L, (const T*)L.q[F_RHO], (const T*)S.eps, f, d, chi, dt, rho0, dfr);
+    }
+  *acc = s;
+}
+
+// --------------------------------------------------------------- transport
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_tprep(LevelView L, Box b, Scratch S) {
+  int i, j, k;
+  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  const T* __restrict__ rho = (const T*)L.q[F_RHO];
+  const int c = cidx(L, i, j, k);
+  const int c3[3] = {i, j, k};
+  const T rc = rho[c];
+  ((T*)S.eps)[c] = ((const T*)L.q[F_E])[c] / rc;  // e/rho
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+    ((T*)S.w[m])[c] =
+        c3[m] >= 1 ? ((const T*)S.pi[m])[c] / (T(0.5) * (rho[c - L.st[m]] + rc)) : T(0);
+}
+
+// mass and energy flux at d-faces 2 <= i_d < s_d - 1
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_tflux(LevelView L, Box b, Scratch S, int d,
+                                                  const double* __restrict__ dtp) {
+  int i, j, k;
+  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  const int c = cidx(L, i, j, k);
+  const int c3[3] = {i, j, k};
+  T Fv = T(0), Ev = T(0);
+  if (c3[d] >= 2 && c3[d] < L.s[d] - 1) {
+    const T dt = (T)(dtp[0] * L.dt_scale);
+    const int st = L.st[d];
+    const T u = ((const T*)L.q[F_VX + d])[c];
+    const T cour = u * (dt * (T)L.inv_dx[d]);
+    T rs = upwind((const T*)L.q[F_RHO], c, st, u, cour);
+    Fv = rs * u * (T)L.area[d] * dt;
+    T es = upwind((const T*)S.eps, c, st, u, cour);
+    Ev = es * Fv;
+  }
+  ((T*)S.F)[c] = Fv;
+  ((T*)S.E)[c] = Ev;
+}
+
+// child frontier capture of the transport fluxes of axis d (sides 2d, 2d+1)
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_tfrontier(LevelView L, Scratch S, int d) {
+  int side, a, b;
+  if (!slot_of(L, blockIdx.x * (long long)kBlock + threadIdx.x, 2 * d, 2, side, a, b)) return;
+  const int t1 = d == 0 ? 1 : 0;
+  const int slot = b * (L.n[t1] >> 1) + a;
+  double* accF = L.acc + (side * 3 + 0) * L.acc_slots + slot;
+  double* accE = L.acc + (side * 3 + 1) * L.acc_slots + slot;
+  double sF = *accF, sE = *accE;
+#pragma unroll
+  for (int v = 0; v < 2; ++v)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      int f;
+      fine_face(L, side, a, b, u, v, f);
+      sF += (double)((const T*)S.F)[f];
+      sE += (double)((const T*)S.E)[f];
+    }
+  *accF = sF;
+  *accE = sE;
+}
+
+// staggered momentum fluxes of sweep d
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_tmom(LevelView L, Box b, Scratch S, int d,
+                                                 const double* __restrict__ dtp) {
+  int i, j, k;
+  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  const int c = cidx(L, i, j, k);
+  const int c3[3] = {i, j, k};
+  const T dt = (T)(dtp[0] * L.dt_scale);
+  const int st = L.st[d];
+  const T* __restrict__ vd = (const T*)L.q[F_VX + d];
+  const T* __restrict__ F = (const T*)S.F;
+  const T dtdx = dt * (T)L.inv_dx[d];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    T P = T(0);
+    if (m == d) {
+      if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
+        T uc = T(0.5) * (vd[c] + vd[c + st]);
+        T Fc = T(0.5) * (F[c] + F[c + st]);
+        T ws = upwind((const T*)S.w[m], c + st, st, uc, uc * dtdx);
+        P = ws * Fc;
+      }
+    } else if (c3[d] >= 2 && c3[d] < L.s[d] - 1 && c3[m] >= 1) {
+      const int sm = L.st[m];
+      T ue = T(0.5) * (vd[c - sm] + vd[c]);
+      T Fe = T(0.5) * (F[c - sm] + F[c]);
+      T ws = upwind((const T*)S.w[m], c, st, ue, ue * dtdx);
+      P = ws * Fe;
+    }
+    ((T*)S.P[m])[c] = P;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_tupdate(LevelView L, Box b, Scratch S, int d) {
+  int i, j, k;
+  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  const int c = cidx(L, i, j, k);
+  const int c3[3] = {i, j, k};
+  const int st = L.st[d];
+  const T iv = (T)L.inv_vol;
+  if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
+    T Flo = ((const T*)S.F)[c], Fhi = ((const T*)S.F)[c + st];
+    T Elo = ((const T*)S.E)[c], Ehi = ((const T*)S.E)[c + st];
+    if (L.has_child) {
+      int slot, f3[3] = {c3[0], c3[1], c3[2]};
+      int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+      if (side >= 0) {
+        Flo = (T)L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot];
+        Elo = (T)L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot];
+      }
+      f3[d] += 1;
+      side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+      if (side >= 0) {
+        Fhi = (T)L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot];
+        Ehi = (T)L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot];
+      }
+    }
+    T* rho = (T*)L.q[F_RHO];
+    T* e = (T*)L.q[F_E];
+    rho[c] = rho[c] - (Fhi - Flo) * iv;
+    e[c] = e[c] - (Ehi - Elo) * iv;
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    T* pi = (T*)S.pi[m];
+    const T* P = (const T*)S.P[m];
+    if (m == d) {
+      if (c3[d] >= 3 && c3[d] < L.s[d] - 2) pi[c] = pi[c] - (P[c] - P[c - st]) * iv;
+    } else if (c3[d] >= 2 && c3[d] < L.s[d] - 2 && c3[m] >= 1) {
+      pi[c] = pi[c] - (P[c + st] - P[c]) * iv;
+    }
+  }
+}
+
+// velocity from the transported momenta, then the second half kick S(dt/2)
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_vrec_source(LevelView L, Box b, Scratch S,
+                                                        const double* __restrict__ dtp,
+                                                        double hscale, T gm1) {
+  int i, j, k;
+  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  const T* __restrict__ rho = (const T*)L.q[F_RHO];
+  const T* __restrict__ e = (const T*)L.q[F_E];
+  const T* __restrict__ phi = (const T*)L.phi;
+  const T h = (T)(hscale * dtp[0]);
+  const int c = cidx(L, i, j, k);
+  const int c3[3] = {i, j, k};
+  const T rc = rho[c], pc = mul_rn(gm1, e[c]), fc = phi[c];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (c3[d] < 1) continue;
+    int m = c - L.st[d];
+    T rf = T(0.5) * (rho[m] + rc);
+    T rinv = T(1) / rf;
+    T v = ((const T*)S.pi[d])[c] * rinv;
+    T pl = mul_rn(gm1, e[m]);
+    T acc = ((pc - pl) * rinv + (fc - phi[m])) * (T)L.inv_dx[d];
+    ((T*)L.q[F_VX + d])[c] = v - h * acc;
+  }
+}
+
+// ------------------------------------------------------ level-0 boundaries
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_bc_axis(LevelView L, int d, int type_lo, int type_hi,
+                                                    T rho0, T e0, T V0, T V1, T V2) {
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  const int G = L.G, n = L.n[d];
+  long long per = (long long)L.s[t1] * L.s[t2];
+  long long total = per * 2 * G * 5;
+  if (t >= total) return;
+  int f = (int)(t / (per * 2 * G));
+  long long r = t - (long long)f * per * 2 * G;
+  int side = (int)(r / (per * G));
+  r -= (long long)side * per * G;
+  int g = 1 + (int)(r / per);
+  r -= (long long)(g - 1) * per;
+  int b = (int)(r / L.s[t1]);
+  int a = (int)(r - (long long)b * L.s[t1]);
+  int type = side ? type_hi : type_lo;
+  int normal = (f == F_VX + d);
+  int dst = side == 0 ? G - g : G + n - 1 + g, src = -1;
+  T sign = T(1), fixed = T(0);
+  bool use_fixed = false;
+  switch (type) {
+    case 0:  // periodic
+      src = side == 0 ? dst + n : dst - n;
+      break;
+    case 1:  // outflow
+      src = side == 0 ? G : G + n - 1;
+      break;
+    case 2: {  // inflow
+      use_fixed = true;
+      const T vv[3] = {V0, V1, V2};
+      fixed = f == F_RHO ? rho0 : (f == F_E ? e0 : vv[f - F_VX]);
+      break;
+    }
+    default:  // reflect
+      if (!normal) {
+        src = side == 0 ? G - 1 + g : G + n - g;
+      } else {
+        sign = T(-1);
+        if (side == 0) {
+          src = G + g;
+        } else {
+          int gp = dst - (G + n);
+          if (gp == 0) {
+            use_fixed = true;
+            fixed = T(0);
+          } else {
+            src = G + n - gp;
+          }
+        }
+      }
+      break;
+  }
+  int c3[3];
+  c3[t1] = a;
+  c3[t2] = b;
+  c3[d] = dst;
+  T* q = (T*)L.q[f];
+  int cd = (c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0];
+  if (use_fixed) {
+    q[cd] = fixed;
+  } else {
+    c3[d] = src;
+    int cs = (c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0];
+    q[cd] = sign * q[cs];
+  }
+  if (type == 3 && side == 0 && normal && g == 1) {
+    c3[d] = G;
+    q[(c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0]] = T(0);
+  }
+}
+
+// ---------------------------------------------------------------- CommUp
+// One thread per (coarse host element, field).  The 2x2x2 fine elements hosted by
+// one coarse element share their van Leer slopes: the z pass gives 9 slopes (one
+// per (y,x) column) for both fine z offsets, the y pass 3 per z offset, the x pass
+// 1 per (z,y) offset -- the same arithmetic per fine element as interpolating each
+// one alone, with the slopes computed once.
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_commup(LevelView C, LevelView F) {
+  const int G = F.G, hg = G >> 1;
+  const int nh0 = (F.n[0] >> 1) + G, nh1 = (F.n[1] >> 1) + G, nh2 = (F.n[2] >> 1) + G;
+  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  long long per = (long long)nh0 * nh1 * nh2;
+  if (t >= 5 * per) return;
+  const int f = (int)(t / per);
+  int r = (int)(t - (long long)f * per);
+  const int h0 = r % nh0 - hg, h1 = (r / nh0) % nh1 - hg, h2 = r / (nh0 * nh1) - hg;
+  // hosted fine elements: rel = 2h + {0,1} on each axis; skip if all are active
+  const int hh[3] = {h0, h1, h2};
+  bool all_active = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) all_active = all_active && hh[a] >= 0 && 2 * hh[a] + 1 < F.n[a];
+  if (all_active) return;
+  const int sa = f >= F_VX ? f - F_VX : -1;
+  T dl[3], dh[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    dl[a] = a == sa ? T(0) : T(-0.25);
+    dh[a] = a == sa ? T(0.5) : T(0.25);
+  }
+  const T* q = (const T*)C.q[f];
+  const int base = ((C.G + F.off[2] + h2) * C.s[1] + C.G + F.off[1] + h1) * C.s[0] + C.G +
+                   F.off[0] + h0;
+  // z pass
+  T vz[2][3][3];
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      int b = base + (dy - 1) * C.st[1] + (dx - 1);
+      T qm = q[b - C.st[2]], q0 = q[b], qp = q[b + C.st[2]];
+      T s = vanleer(q0 - qm, qp - q0);
+      vz[0][dy][dx] = q0 + dl[2] * s;
+      vz[1][dy][dx] = q0 + dh[2] * s;
+    }
+  // y pass
+  T vy[2][2][3];
+#pragma unroll
+  for (int iz = 0; iz < 2; ++iz)
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) {
+      T qm = vz[iz][0][dx], q0 = vz[iz][1][dx], qp = vz[iz][2][dx];
+      T s = vanleer(q0 - qm, qp - q0);
+      vy[iz][0][dx] = q0 + dl[1] * s;
+      vy[iz][1][dx] = q0 + dh[1] * s;
+    }
+  // x pass and stores
+  T* out = (T*)F.q[f];
+#pragma unroll
+  for (int iz = 0; iz < 2; ++iz)
+#pragma unroll
+    for (int iy = 0; iy < 2; ++iy) {
+      T qm = vy[iz][iy][0], q0 = vy[iz][iy][1], qp = vy[iz][iy][2];
+      T s = vanleer(q0 - qm, qp - q0);
+#pragma unroll
+      for (int ix = 0; ix < 2; ++ix) {
+        int fi = G + 2 * h0 + ix, fj = G + 2 * h1 + iy, fk = G + 2 * h2 + iz;
+        bool act = fi >= G && fi < G + F.n[0] && fj >= G && fj < G + F.n[1] && fk >= G &&
+                   fk < G + F.n[2];
+        bool inside = fi >= 0 && fi < F.s[0] && fj >= 0 && fj < F.s[1] && fk >= 0 &&
+                      fk < F.s[2];
+        if (!act && inside) out[(fk * F.s[1] + fj) * F.s[0] + fi] = q0 + (ix ? dh[0] : dl[0]) * s;
+      }
+    }
+}
+
+// -------------------------------------------------------------- CommMean
+__device__ __forceinline__ bool in_band(const LevelView& F, int band, int a0, int a1, int a2) {
+  int a3[3] = {a0, a1, a2};
+  int dist = 1 << 30;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int lo = a3[d] - F.off[d], hi = F.off[d] + (F.n[d] >> 1) - 1 - a3[d];
+    if (lo < 0 || hi < 0) return false;
+    dist = min(dist, min(lo, hi));
+  }
+  return dist < band;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_commmean(LevelView C, LevelView F, int band) {
+  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  int h0 = F.n[0] >> 1, h1 = F.n[1] >> 1, h2 = F.n[2] >> 1;
+  if (t >= (long long)h0 * h1 * h2) return;
+  int a = (int)(t % h0), b = (int)((t / h0) % h1), cc = (int)(t / ((long long)h0 * h1));
+  int r[3] = {a, b, cc};
+  int a3[3] = {a + F.off[0], b + F.off[1], cc + F.off[2]};
+  const int Gf = F.G, Gc = C.G;
+  int dst = ((Gc + a3[2]) * C.s[1] + Gc + a3[1]) * C.s[0] + Gc + a3[0];
+  if (in_band(F, band, a3[0], a3[1], a3[2])) {
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const T* q = (const T*)F.q[f];
+      T sz[2];
+#pragma unroll
+      for (int dz = 0; dz < 2; ++dz) {
+        T sy[2];
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          int c0 = ((Gf + 2 * cc + dz) * F.s[1] + Gf + 2 * b + dy) * F.s[0] + Gf + 2 * a;
+          sy[dy] = q[c0] + q[c0 + 1];
+        }
+        sz[dz] = sy[0] + sy[1];
+      }
+      ((T*)C.q[f])[dst] = T(0.125) * (sz[0] + sz[1]);
+    }
+  }
+#pragma unroll
+  for (int sa = 0; sa < 3; ++sa) {
+    if (r[sa] == 0) continue;
+    int m3[3] = {a3[0], a3[1], a3[2]};
+    m3[sa] -= 1;
+    if (!in_band(F, band, a3[0], a3[1], a3[2]) && !in_band(F, band, m3[0], m3[1], m3[2])) continue;
+    int t1 = sa == 0 ? 1 : 0, t2 = sa == 2 ? 1 : 2;
+    const T* q = (const T*)F.q[F_VX + sa];
+    T sv[2];
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      T pair[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        int fi[3];
+        fi[sa] = Gf + 2 * r[sa];
+        fi[t1] = Gf + 2 * r[t1] + u;
+        fi[t2] = Gf + 2 * r[t2] + v;
+        pair[u] = q[(fi[2] * F.s[1] + fi[1]) * F.s[0] + fi[0]];
+      }
+      sv[v] = pair[0] + pair[1];
+    }
+    ((T*)C.q[F_VX + sa])[dst] = T(0.25) * (sv[0] + sv[1]);
+  }
+}
+
+// ------------------------------------------------------------- time step
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_dt_level(LevelView L, int level, double gg,
+                                                     double cfl, int hydro, DevScalars* ds) {
+  __shared__ double sm[kBlock / 32];
+  __shared__ int bad_s;
+  if (threadIdx.x == 0) bad_s = 0;
+  __syncthreads();
+  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  double best = INFINITY;
+  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  if (t < na) {
+    int i = L.G + (int)(t % L.n[0]);
+    int j = L.G + (int)((t / L.n[0]) % L.n[1]);
+    int k = L.G + (int)(t / ((long long)L.n[0] * L.n[1]));
+    int c = (k * L.s[1] + j) * L.s[0] + i;
+    double rho = (double)((const T*)L.q[F_RHO])[c];
+    double e = (double)((const T*)L.q[F_E])[c];
+    if (!(rho > 0.0) || !(e > 0.0)) bad_s = 1;
+    if (hydro) {
+      double cs = sqrt(gg * e / rho);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T* v = (const T*)L.q[F_VX + d];
+        double v0 = fabs((double)v[c]), v1 = fabs((double)v[c + L.st[d]]);
+        double vm = v0 > v1 ? v0 : v1;
+        double tt = cfl * L.dx[d] / (cs + vm);
+        if (tt < best) best = tt;
+      }
+    }
+  }
+  best = warp_min(best);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kBlock / 32 ? sm[threadIdx.x] : INFINITY;
+    v = warp_min(v);
+    if (threadIdx.x == 0) {
+      // positive doubles order like their bit patterns; +inf is the largest
+      if (v < INFINITY) atomicMin(&ds->dtmin[level], (unsigned long long)__double_as_longlong(v));
+      if (bad_s) atomicOr(&ds->unhealthy, 1);
+    }
+  }
+}
+
+struct DtFinal {
+  double prod[16];
+  double diff_lim[16];
+};
+
+__global__ void k_dt_finalize(DevScalars* ds, int n_levels, DtFinal fin, double dt_fixed) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double dt = INFINITY;
+  for (int l = 0; l < n_levels; ++l) {
+    unsigned long long bits = ds->dtmin[l];
+    double lim = __longlong_as_double((long long)bits);
+    if (fin.diff_lim[l] < lim) lim = fin.diff_lim[l];
+    double t = lim * fin.prod[l];
+    if (t < dt) dt = t;
+    ds->dtmin[l] = (unsigned long long)__double_as_longlong(INFINITY);
+  }
+  if (dt_fixed > 0.0) dt = dt_fixed;
+  ds->dt = dt;
+}
+
+__global__ void k_time_advance(DevScalars* ds) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) ds->t += ds->dt;
+}
+
+// ------------------------------------------------------------------ force
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_force_level(LevelView L, double GM, double eps,
+                                                        double rho0, double* partials) {
+  __shared__ double sx[kBlock], sy[kBlock], sz[kBlock];
+  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  double fx = 0.0, fy = 0.0, fz = 0.0;
+  if (t < na) {
+    int ai = (int)(t % L.n[0]);
+    int aj = (int)((t / L.n[0]) % L.n[1]);
+    int ak = (int)(t / ((long long)L.n[0] * L.n[1]));
+    bool covered = false;
+    if (L.has_child)
+      covered = ai >= L.coff[0] && ai < L.coff[0] + (L.cn[0] >> 1) && aj >= L.coff[1] &&
+                aj < L.coff[1] + (L.cn[1] >> 1) && ak >= L.coff[2] &&
+                ak < L.coff[2] + (L.cn[2] >> 1);
+    if (!covered) {
+      int c = ((L.G + ak) * L.s[1] + L.G + aj) * L.s[0] + L.G + ai;
+      double x = L.lo[0] + (ai + 0.5) * L.dx[0];
+      double y = L.lo[1] + (aj + 0.5) * L.dx[1];
+      double z = L.lo[2] + (ak + 0.5) * L.dx[2];
+      double r2 = x * x + y * y + z * z + eps * eps;
+      double inv3 = 1.0 / (r2 * sqrt(r2));
+      double m = ((double)((const T*)L.q[F_RHO])[c] - rho0) * L.vol;
+      fx = GM * m * x * inv3;
+      fy = GM * m * y * inv3;
+      fz = GM * m * z * inv3;
+    }
+  }
+  sx[threadIdx.x] = fx;
+  sy[threadIdx.x] = fy;
+  sz[threadIdx.x] = fz;
+  __syncthreads();
+  for (int w = kBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sx[threadIdx.x] += sx[threadIdx.x + w];
+      sy[threadIdx.x] += sy[threadIdx.x + w];
+      sz[threadIdx.x] += sz[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[3 * blockIdx.x + 0] = sx[0];
+    partials[3 * blockIdx.x + 1] = sy[0];
+    partials[3 * blockIdx.x + 2] = sz[0];
+  }
+}
+
+// fixed-order compensated (Neumaier) sum of the block partials, one warp per component
+__global__ void k_force_finalize(const double* __restrict__ partials, int n, DevScalars* ds,
+                                 double* ring, int ring_cap, long long* ring_pos) {
+  int comp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (comp >= 3) return;
+  double s = 0.0, cmp = 0.0;
+  for (int p = lane; p < n; p += 32) {
+    double v = partials[3 * p + comp];
+    double tt = s + v;
+    if (fabs(s) >= fabs(v))
+      cmp += (s - tt) + v;
+    else
+      cmp += (v - tt) + s;
+    s = tt;
+  }
+  // fixed butterfly over the lanes, then fold the compensation in
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    double so = __shfl_down_sync(0xffffffffu, s, o);
+    double co = __shfl_down_sync(0xffffffffu, cmp, o);
+    if (lane < o) {
+      double tt = s + so;
+      if (fabs(s) >= fabs(so))
+        cmp += (s - tt) + so;
+      else
+        cmp += (so - tt) + s;
+      s = tt;
+      cmp += co;
+    }
+  }
+  if (lane == 0) {
+    double F = s + cmp;
+    ds->F[comp] = F;
+    if (ring) {
+      long long pos = *ring_pos;
+      ring[3 * (pos % ring_cap) + comp] = F;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && ring) *ring_pos += 1;
+}
+
+// ----------------------------------------------------------- initialisation
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_init_uniform(LevelView L, T rho0, T e0, T V0, T V1,
+                                                         T V2) {
+  long long c = blockIdx.x * (long long)kBlock + threadIdx.x;
+  if (c >= L.nc) return;
+  ((T*)L.q[F_RHO])[c] = rho0;
+  ((T*)L.q[F_E])[c] = e0;
+  ((T*)L.q[F_VX])[c] = V0;
+  ((T*)L.q[F_VX + 1])[c] = V1;
+  ((T*)L.q[F_VX + 2])[c] = V2;
+}
+
+// Plummer potential (Eq. 16, attractive sign) at every cell centre; Gaussian
+// luminosity weights on active cells (their sum goes to wsum)
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_static(LevelView L, double GM, double eps,
+                                                   double sigma, int vertex_ok, int vx0, int vx1,
+                                                   int vx2, double* wsum) {
+  __shared__ double sm[kBlock];
+  long long c = blockIdx.x * (long long)kBlock + threadIdx.x;
+  double wgt = 0.0;
+  if (c < L.nc) {
+    int i = (int)(c % L.s[0]), j = (int)((c / L.s[0]) % L.s[1]),
+        k = (int)(c / ((long long)L.s[0] * L.s[1]));
+    double x = L.lo[0] + (i - L.G + 0.5) * L.dx[0];
+    double y = L.lo[1] + (j - L.G + 0.5) * L.dx[1];
+    double z = L.lo[2] + (k - L.G + 0.5) * L.dx[2];
+    ((T*)L.phi)[c] = (T)(-GM / sqrt(x * x + y * y + z * z + eps * eps));
+    bool act = i >= L.G && i < L.G + L.n[0] && j >= L.G && j < L.G + L.n[1] && k >= L.G &&
+               k < L.G + L.n[2];
+    double lw = 0.0;
+    if (act) {
+      if (sigma > 0.0) {
+        wgt = exp(-(x * x + y * y + z * z) / (2.0 * sigma * sigma));
+        lw = wgt;
+      } else if (vertex_ok) {
+        int ai = i - L.G, aj = j - L.G, ak = k - L.G;
+        if ((ai == vx0 - 1 || ai == vx0) && (aj == vx1 - 1 || aj == vx1) &&
+            (ak == vx2 - 1 || ak == vx2))
+          lw = 1.0 / (8.0 * L.vol);
+      }
+    }
+    ((T*)L.lumw)[c] = (T)lw;
+  }
+  sm[threadIdx.x] = wgt;
+  __syncthreads();
+  for (int w = kBlock / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && sigma > 0.0) atomicAdd(wsum, sm[0]);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_normalise_lum(LevelView L, const double* wsum) {
+  long long c = blockIdx.x * (long long)kBlock + threadIdx.x;
+  if (c >= L.nc) return;
+  T* lw = (T*)L.lumw;
+  lw[c] = (T)((double)lw[c] / (wsum[0] * L.vol));
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_pack(LevelView L, int field, double* out, int full) {
+  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  const T* q = (const T*)L.q[field];
+  if (full) {
+    if (t < L.nc) out[t] = (double)q[t];
+    return;
+  }
+  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  if (t >= na) return;
+  int i = (int)(t % L.n[0]), j = (int)((t / L.n[0]) % L.n[1]),
+      k = (int)(t / ((long long)L.n[0] * L.n[1]));
+  out[t] = (double)q[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G];
+}
+
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_unpack(LevelView L, int field, const double* in,
+                                                   int full) {
+  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  T* q = (T*)L.q[field];
+  if (full) {
+    if (t < L.nc) q[t] = (T)in[t];
+    return;
+  }
+  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  if (t >= na) return;
+  int i = (int)(t % L.n[0]), j = (int)((t / L.n[0]) % L.n[1]),
+      k = (int)(t / ((long long)L.n[0] * L.n[1]));
+  q[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G] = (T)in[t];
+}
+
+}  // namespace
+
+// =================================================================== launchers
+
+template <class T>
+int launch_source(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
+                  double hscale, int write_pi, double gm1, cudaStream_t st) {
+  k_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, hscale, write_pi, (T)gm1);
+  return 1;
+}
+
+template <class T>
+int launch_compress_lum(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
+                        const Phys& P, int do_ss3, int do_lum, int do_eps, cudaStream_t st) {
+  k_compress_lum<T><<<grid_for(b.count()), kBlock, 0, st>>>(
+      L, b, S, dt, (T)(P.gamma - 1.0), (T)P.L, do_ss3, do_lum, do_eps);
+  return 1;
+}
+
+template <class T>
+int launch_diffuse(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
+                   const Phys& P, cudaStream_t st) {
+  k_diffuse<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, (T)P.chi, (T)P.rho0,
+                                                        P.diff_face_rho);
+  return 1;
+}
+
+static long long slots_total(const LevelView& L, int sides_lo, int n_sides) {
+  long long tot = 0;
+  for (int s = sides_lo; s < sides_lo + n_sides; ++s) {
+    int d = s >> 1;
+    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    tot += (long long)(L.n[t1] >> 1) * (L.n[t2] >> 1);
+  }
+  return tot;
+}
+
+template <class T>
+int launch_frontier_diff(const LevelView& L, const Scratch& S, const double* dt, const Phys& P,
+                         cudaStream_t st) {
+  k_frontier_diff<T><<<grid_for(slots_total(L, 0, 6)), kBlock, 0, st>>>(
+      L, S, dt, (T)P.chi, (T)P.rho0, P.diff_face_rho);
+  return 1;
+}
+
+template <class T>
+int launch_tprep(const LevelView& L, const Box& b, const Scratch& S, cudaStream_t st) {
+  k_tprep<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S);
+  return 1;
+}
+
+template <class T>
+int launch_tflux(const LevelView& L, const Box& b, const Scratch& S, int d, const double* dt,
+                 cudaStream_t st) {
+  k_tflux<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d, dt);
+  return 1;
+}
+
+template <class T>
+int launch_tfrontier(const LevelView& L, const Scratch& S, int d, cudaStream_t st) {
+  k_tfrontier<T><<<grid_for(slots_total(L, 2 * d, 2)), kBlock, 0, st>>>(L, S, d);
+  return 1;
+}
+
+template <class T>
+int launch_tmom(const LevelView& L, const Box& b, const Scratch& S, int d, const double* dt,
+                cudaStream_t st) {
+  k_tmom<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d, dt);
+  return 1;
+}
+
+template <class T>
+int launch_tupdate(const LevelView& L, const Box& b, const Scratch& S, int d, cudaStream_t st) {
+  k_tupdate<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d);
+  return 1;
+}
+
+template <class T>
+int launch_vrec_source(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
+                       double hscale, double gm1, cudaStream_t st) {
+  k_vrec_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, hscale, (T)gm1);
+  return 1;
+}
+
+template <class T>
+int launch_bc_fill(const LevelView& L, const Phys& P, cudaStream_t st) {
+  int n = 0;
+  for (int d = 0; d < 3; ++d) {
+    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    long long total = (long long)L.s[t1] * L.s[t2] * 2 * L.G * 5;
+    k_bc_axis<T><<<grid_for(total), kBlock, 0, st>>>(L, d, P.bc[2 * d], P.bc[2 * d + 1],
+                                                      (T)P.rho0, (T)P.e0, (T)P.V[0], (T)P.V[1],
+                                                      (T)P.V[2]);
+    ++n;
+  }
+  return n;
+}
+
+template <class T>
+int launch_commup(const LevelView& C, const LevelView& F, cudaStream_t st) {
+  long long hosts = (long long)((F.n[0] >> 1) + F.G) * ((F.n[1] >> 1) + F.G) * ((F.n[2] >> 1) + F.G);
+  k_commup<T><<<grid_for(5 * hosts), kBlock, 0, st>>>(C, F);
+  return 1;
+}
+
+template <class T>
+int launch_commmean(const LevelView& C, const LevelView& F, int band, cudaStream_t st) {
+  long long n = (long long)(F.n[0] >> 1) * (F.n[1] >> 1) * (F.n[2] >> 1);
+  k_commmean<T><<<grid_for(n), kBlock, 0, st>>>(C, F, band);
+  return 1;
+}
+
+template <class T>
+int launch_dt_level(const LevelView& L, int level, const Phys& P, DevScalars* ds,
+                    cudaStream_t st) {
+  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  k_dt_level<T><<<grid_for(na), kBlock, 0, st>>>(L, level, P.gamma * (P.gamma - 1.0), P.cfl,
+                                                  P.hydro_on, ds);
+  return 1;
+}
+
+int launch_dt_finalize(DevScalars* ds, int n_levels, const double* prod, double dt_fixed,
+                       cudaStream_t st) {
+  // prod[0..n) then diffusion limits [n..2n)
+  DtFinal fin;
+  for (int l = 0; l < 16; ++l) {
+    fin.prod[l] = l < n_levels ? prod[l] : 1.0;
+    fin.diff_lim[l] = l < n_levels ? prod[n_levels + l] : INFINITY;
+  }
+  k_dt_finalize<<<1, 32, 0, st>>>(ds, n_levels, fin, dt_fixed);
+  return 1;
+}
+
+int force_partials_per_level(const LevelView& L) {
+  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  return (int)grid_for(na);
+}
+
+template <class T>
+int launch_force_level(const LevelView& L, const Phys& P, double* partials, int offset,
+                       cudaStream_t st) {
+  k_force_level<T><<<force_partials_per_level(L), kBlock, 0, st>>>(L, P.GM, P.eps, P.rho0,
+                                                                   partials + 3 * offset);
+  return 1;
+}
+
+int launch_force_finalize(const double* partials, int n, DevScalars* ds, double* ring,
+                          int ring_cap, long long* ring_pos, cudaStream_t st) {
+  k_force_finalize<<<1, 96, 0, st>>>(partials, n, ds, ring, ring_cap, ring_pos);
+  return 1;
+}
+
+int launch_time_advance(DevScalars* ds, cudaStream_t st) {
+  k_time_advance<<<1, 32, 0, st>>>(ds);
+  return 1;
+}
+
+template <class T>
+int launch_init_uniform(const LevelView& L, const Phys& P, cudaStream_t st) {
+  k_init_uniform<T><<<grid_for(L.nc), kBlock, 0, st>>>(L, (T)P.rho0, (T)P.e0, (T)P.V[0],
+                                                        (T)P.V[1], (T)P.V[2]);
+  return 1;
+}
+
+template <class T>
+int launch_static_fields(const LevelView& L, const Phys& P, double lum_sigma, double* wsum,
+                         cudaStream_t st) {
+  int v[3], ok = 1;
+  for (int d = 0; d < 3; ++d) {
+    double o = -L.lo[d] / L.dx[d];
+    v[d] = (int)floor(o + 0.5);
+    if (fabs(o - v[d]) > 1e-9 || v[d] < 1 || v[d] > L.n[d] - 1) ok = 0;
+  }
+  k_static<T><<<grid_for(L.nc), kBlock, 0, st>>>(L, P.GM, P.eps, lum_sigma, ok, v[0], v[1],
+                                                  v[2], wsum);
+  return 1;
+}
+
+template <class T>
+int launch_normalise_lum(const LevelView& L, const double* wsum, cudaStream_t st) {
+  k_normalise_lum<T><<<grid_for(L.nc), kBlock, 0, st>>>(L, wsum);
+  return 1;
+}
+
+template <class T>
+int launch_pack_active(const LevelView& L, int field, double* out, int full, cudaStream_t st) {
+  long long n = full ? L.nc : (long long)L.n[0] * L.n[1] * L.n[2];
+  k_pack<T><<<grid_for(n), kBlock, 0, st>>>(L, field, out, full);
+  return 1;
+}
+
+template <class T>
+int launch_unpack_active(const LevelView& L, int field, const double* in, int full,
+                         cudaStream_t st) {
+  long long n = full ? L.nc : (long long)L.n[0] * L.n[1] * L.n[2];
+  k_unpack<T><<<grid_for(n), kBlock, 0, st>>>(L, field, in, full);
+  return 1;
+}
+
+#define DFN_INSTANTIATE(T)                                                                     \
+  template int launch_source<T>(const LevelView&, const Box&, const Scratch&, const double*,   \
+                                double, int, double, cudaStream_t);                            \
+  template int launch_compress_lum<T>(const LevelView&, const Box&, const Scratch&,            \
+                                      const double*, const Phys&, int, int, int, cudaStream_t); \
+  template int launch_diffuse<T>(const LevelView&, const Box&, const Scratch&, const double*,  \
+                                 const Phys&, cudaStream_t);                                   \
+  template int launch_frontier_diff<T>(const LevelView&, const Scratch&, const double*,        \
+                                       const Phys&, cudaStream_t);                             \
+  template int launch_tprep<T>(const LevelView&, const Box&, const Scratch&, cudaStream_t);    \
+  template int launch_tflux<T>(const LevelView&, const Box&, const Scratch&, int, const double*, \
+                               cudaStream_t);                                                  \
+  template int launch_tfrontier<T>(const LevelView&, const Scratch&, int, cudaStream_t);       \
+  template int launch_tmom<T>(const LevelView&, const Box&, const Scratch&, int, const double*, \
+                              cudaStream_t);                                                   \
+  template int launch_tupdate<T>(const LevelView&, const Box&, const Scratch&, int,            \
+                                 cudaStream_t);                                                \
+  template int launch_vrec_source<T>(const LevelView&, const Box&, const Scratch&,             \
+                                     const double*, double, double, cudaStream_t);             \
+  template int launch_bc_fill<T>(const LevelView&, const Phys&, cudaStream_t);                 \
+  template int launch_commup<T>(const LevelView&, const LevelView&, cudaStream_t);             \
+  template int launch_commmean<T>(const LevelView&, const LevelView&, int, cudaStream_t);      \
+  template int launch_dt_level<T>(const LevelView&, int, const Phys&, DevScalars*,             \
+                                  cudaStream_t);                                               \
+  template int launch_force_level<T>(const LevelView&, const Phys&, double*, int,              \
+                                     cudaStream_t);                                            \
+  template int launch_init_uniform<T>(const LevelView&, const Phys&, cudaStream_t);            \
+  template int launch_static_fields<T>(const LevelView&, const Phys&, double, double*,         \
+                                       cudaStream_t);                                          \
+  template int launch_normalise_lum<T>(const LevelView&, const double*, cudaStream_t);         \
+  template int launch_pack_active<T>(const LevelView&, int, double*, int, cudaStream_t);       \
+  template int launch_unpack_active<T>(const LevelView&, int, const double*, int, cudaStream_t);
+
+DFN_INSTANTIATE(double)
+DFN_INSTANTIATE(float)
+
+}  // namespace dfn

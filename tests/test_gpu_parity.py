@@ -1,0 +1,252 @@
+"""GPU (CUDA path through the C ABI) versus the FP64 oracle, element by element.
+
+Tolerance (FP64 path): per field and level, max|gpu - oracle| / s_f <= 1e-10, with
+s_f = 1 for rho and e and s_f = max(V, 1e-3 c_s) for the velocities; the force to
+1e-10 of its magnitude.  The two sides differ only in rounding order (the GPU
+contracts multiply-adds, the oracle does not; the force sum is a tree on the GPU).
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1812_03191_gb300 import binding
+from paper_1812_03191_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1812_03191_gb300 import build as B
+    B.build()
+    binding.load()
+
+
+def pair(nl, n, half, params, G=I.DEFAULT_G, precision=binding.DF_FP64):
+    lo = tuple(-h for h in half) if not np.isscalar(half) else (-half,) * 3
+    hi = tuple(half) if not np.isscalar(half) else (half,) * 3
+    sim = binding.Sim(nl, n, lo, hi, G, params, precision=precision)
+    orc = Oracle(nl, n, lo, hi, G, params)
+    return sim, orc
+
+
+def field_errors(sim, orc, params):
+    out = []
+    vs = max(params["mach"] * params["cs"], 1e-3 * params["cs"])
+    for l in range(sim.n_levels):
+        for f in range(5):
+            a, b = sim.get_field(l, f), orc.get_field(l, f)
+            out.append((l, f, float(np.abs(a - b).max()) / (1.0 if f < 2 else vs)))
+    return out
+
+
+def assert_parity(sim, orc, params, tol=TOL, ftol=TOL):
+    errs = field_errors(sim, orc, params)
+    worst = max(errs, key=lambda x: x[2])
+    assert worst[2] <= tol, f"level {worst[0]} field {worst[1]}: {worst[2]:.3e}"
+    F, _ = sim.force()
+    Fo = orc.force()
+    assert np.abs(F - Fo).max() <= ftol * max(np.abs(Fo).max(), 1e-300), (F, Fo)
+    t, dt, bad = sim.status()
+    assert bad == 0
+    assert abs(t - orc.t) <= 1e-13 * max(orc.t, 1e-300)
+
+
+def perturb_both(sim, orc, seed, amp=1e-2):
+    n = sim.n
+    for l in range(sim.n_levels):
+        for f in range(5):
+            base = orc.get_field(l, f)
+            pert = I.smooth_perturbation(n[::-1], seed + 17 * l + f, amp)
+            val = base * (1 + pert) if f < 2 else base + pert
+            orc.set_field(l, f, val)
+            sim.set_field(l, f, val)
+    for l in range(sim.n_levels - 1):
+        orc.commup(l)
+        sim.prolong(l)
+
+
+def test_uniform_flow_bitwise():
+    p = I.base_params(GM=0.0, L=0.0, chi=1.0, mach=0.7, flow_dir=(-0.6, 0.0, 0.8))
+    sim, orc = pair(3, 24, 6.0, p)
+    init = [[orc.get_field(l, f) for f in range(5)] for l in range(3)]
+    sim.step(10)
+    for l in range(3):
+        for f in range(5):
+            assert np.array_equal(sim.get_field(l, f), init[l][f]), (l, f)
+
+
+def test_single_mesh_100_steps():
+    """32^3 single mesh, Mach 0.5 wind, GM=0.01, softening 2 cells, chi=1: 100 steps."""
+    cfg = I.single_mesh()
+    p = cfg["params"]
+    sim, orc = pair(1, cfg["n"], cfg["hi"][0], p)
+    sim.step(100)
+    orc.step(100)
+    assert_parity(sim, orc, p)
+    assert abs(sim.force()[0][0]) > 0
+
+
+def test_nested_100_coarse_steps():
+    """3 nested levels (ratio 2) of 32^3 with a Gaussian luminosity: 100 coarse steps."""
+    p = I.base_params(GM=0.01, eps=0.125, chi=1.0, L=I.critical_luminosity(0.01, 1, 1, 5 / 3),
+                      lum_sigma=0.125, mach=0.5)
+    sim, orc = pair(3, 32, 8.0, p)
+    sim.step(100)
+    orc.step(100)
+    assert_parity(sim, orc, p)
+
+
+@pytest.mark.parametrize("bc", [
+    (I.BC_PERIODIC,) * 6,
+    (I.BC_REFLECT, I.BC_OUTFLOW, I.BC_REFLECT, I.BC_INFLOW, I.BC_OUTFLOW, I.BC_REFLECT),
+    I.wind_bcs((0.0, 0.6, -0.8)),
+])
+def test_perturbed_nested_boundaries(bc):
+    p = I.base_params(GM=0.02, eps=0.3, chi=0.4, L=0.03, lum_sigma=0.0, mach=0.8,
+                      flow_dir=(0.0, 0.6, -0.8), bc=bc)
+    sim, orc = pair(2, (24, 28, 32), (6.0, 7.0, 8.0), p)
+    perturb_both(sim, orc, seed=3)
+    sim.step(12)
+    orc.step(12)
+    assert_parity(sim, orc, p)
+
+
+def test_margin_boxes_equal_full_boxes():
+    """The active cells do not depend on the ghost margin the kernels sweep."""
+    p = I.base_params(GM=0.01, eps=0.125, chi=1.0, L=0.05, lum_sigma=0.125, mach=0.9)
+    a = binding.Sim(3, 24, (-6.0,) * 3, (6.0,) * 3, I.DEFAULT_G, p)
+    b = binding.Sim(3, 24, (-6.0,) * 3, (6.0,) * 3, I.DEFAULT_G, p)
+    b.debug_full_boxes(True)
+    for s in (a, b):
+        for l in range(3):
+            for f in range(5):
+                base = s.get_field(l, f)
+                s.set_field(l, f, base + I.smooth_perturbation((24,) * 3, 40 + 5 * l + f, 5e-3))
+        for l in range(2):
+            s.prolong(l)
+    a.step(15)
+    b.step(15)
+    for l in range(3):
+        for f in range(5):
+            assert np.array_equal(a.get_field(l, f), b.get_field(l, f)), (l, f)
+    assert np.array_equal(a.force()[0], b.force()[0])
+
+
+def test_inter_level_operators():
+    p = I.base_params()
+    sim, orc = pair(2, 24, 6.0, p)
+    rng = np.random.default_rng(9)
+    shape = sim.full_shape()
+    for l in range(2):
+        for f in range(5):
+            a = 1.0 + 0.1 * rng.standard_normal(shape)
+            sim.set_full(l, f, a)
+            orc.set_full(l, f, a)
+    sim.prolong(0)
+    orc.commup(0)
+    sim.restrict(0)
+    orc.commmean(0)
+    for l in range(2):
+        for f in range(5):
+            a, b = sim.get_full(l, f), orc.get_full(l, f)
+            assert np.abs(a - b).max() <= 1e-15 * np.abs(b).max(), (l, f)
+
+
+def test_bc_fill_matches():
+    p = I.base_params(bc=(I.BC_REFLECT, I.BC_PERIODIC, I.BC_INFLOW, I.BC_OUTFLOW, I.BC_OUTFLOW,
+                          I.BC_REFLECT))
+    p2 = dict(p, bc=(I.BC_PERIODIC,) * 2 + (I.BC_INFLOW, I.BC_OUTFLOW, I.BC_OUTFLOW, I.BC_REFLECT))
+    sim, orc = pair(1, 16, 4.0, p2)
+    rng = np.random.default_rng(2)
+    for f in range(5):
+        a = 1.0 + 0.1 * rng.standard_normal(sim.full_shape())
+        sim.set_full(0, f, a)
+        orc.set_full(0, f, a)
+    sim.fill_bc()
+    orc.fill_bc()
+    for f in range(5):
+        assert np.array_equal(sim.get_full(0, f), orc.get_full(0, f)), f
+
+
+def test_time_step_matches():
+    p = I.base_params(GM=0.05, eps=0.3, chi=0.02, mach=1.5)
+    sim, orc = pair(3, 24, 6.0, p)
+    perturb_both(sim, orc, seed=8, amp=5e-2)
+    dt, lv = sim.compute_dt()
+    dto, lvo = orc.compute_dt()
+    assert abs(dt - dto) <= 1e-15 * dto
+    assert np.allclose(lv, lvo, rtol=1e-15, atol=0)
+
+
+def test_xi_search_mode_parity():
+    """Eq. 55-56 search each coarse step (advective limit dominant: chi small)."""
+    p = I.base_params(GM=0.02, eps=0.3, chi=0.005, mach=1.2, xi_mode=1)
+    sim, orc = pair(3, 24, 6.0, p)
+    perturb_both(sim, orc, seed=12, amp=2e-2)
+    sim.step(6)
+    orc.step(6)
+    assert_parity(sim, orc, p)
+
+
+def test_full_size_nested_config():
+    """The benchmarked configuration (3 levels of 64^3, coarse box [-8,8]^3, Mach 0.5,
+    chi=1, Gaussian luminosity L_c) in the launch configuration the bench times."""
+    cfg = I.nested()
+    p = cfg["params"]
+    sim, orc = pair(cfg["n_levels"], cfg["n"], cfg["hi"][0], p)
+    sim.step(3)
+    orc.step(3)
+    assert_parity(sim, orc, p)
+
+
+def test_unhealthy_state_reported():
+    p = I.base_params(GM=0.0, chi=0.5)
+    sim = binding.Sim(1, 16, (-2.0,) * 3, (2.0,) * 3, I.DEFAULT_G, p)
+    rho = sim.get_field(0, 0)
+    rho[3, 4, 5] = -1.0
+    sim.set_field(0, 0, rho)
+    sim.step(1)
+    with pytest.raises(binding.DfError) as ei:
+        sim.force()
+    assert ei.value.code == binding.DF_EUNHEALTHY
+
+
+def test_checkpoint_resume_bitwise():
+    p = I.base_params(GM=0.01, eps=0.125, chi=1.0, L=0.05, lum_sigma=0.125, mach=0.5)
+    a = binding.Sim(3, 24, (-6.0,) * 3, (6.0,) * 3, I.DEFAULT_G, p)
+    a.step(4)
+    st, t = a.get_state()
+    a.step(5)
+    b = binding.Sim(3, 24, (-6.0,) * 3, (6.0,) * 3, I.DEFAULT_G, p)
+    b.set_state(st, t)
+    b.step(5)
+    s1, t1 = a.get_state()
+    s2, t2 = b.get_state()
+    assert t1 == t2
+    assert np.array_equal(s1, s2)
+
+
+def test_fp32_state_close_to_fp64():
+    """FP32 state with FP64 reductions: after 60 coarse steps the fields stay within
+    1e-4 of the FP64 run (FP32 rounding accumulated over ~400 level steps) and the
+    force within 1e-3 relative (the precision form's target)."""
+    cfg = I.nested(n=32, n_levels=3, half=8.0, mach=1.2)
+    p = cfg["params"]
+    lo, hi = cfg["lo"], cfg["hi"]
+    s64 = binding.Sim(3, 32, lo, hi, I.DEFAULT_G, p, precision=binding.DF_FP64)
+    s32 = binding.Sim(3, 32, lo, hi, I.DEFAULT_G, p, precision=binding.DF_FP32_STATE)
+    s64.step(60)
+    s32.step(60)
+    for l in range(3):
+        for f in range(2):
+            a, b = s32.get_field(l, f), s64.get_field(l, f)
+            assert np.abs(a - b).max() < 1e-4, (l, f)
+    F64 = s64.force()[0]
+    F32 = s32.force()[0]
+    assert np.abs(F32 - F64).max() <= 1e-3 * np.abs(F64).max(), (F32, F64)
