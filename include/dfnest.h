@@ -151,6 +151,34 @@ int df_debug_full_boxes(df_ctx* ctx, int on);
 
 int df_destroy(df_ctx* ctx);
 
+/* Force of one level without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- a host whose
+ * device memory is entirely reserved by another allocator, a latency-critical loop
+ * that cannot afford cudaMalloc's implicit device synchronisation, or a sandboxed
+ * plug-in that is not allowed to allocate.  It computes the same per-level sum as
+ * the context's force reduction (Eq. 18 terms with rho - rho0, cells whose centre
+ * lies in the child box excluded), with its scratch -- one triple of partial sums
+ * per 256 active cells -- in a fixed file-scope device array of
+ * DF_NOALLOC_MAX_CELLS/256 triples (384 KiB) that every GPU loading the library
+ * holds until the process exits.
+ *  rho: device pointer to the padded density array of the level, ((n+2G)^3, x fastest);
+ *  n, G, lo (lower corner of the active box), dx: the level's geometry (host arrays);
+ *  child_off, child_n: the covered box in this level's active cells and the child's
+ *    cell counts halved (both NULL for a level without a child);
+ *  GM, eps, rho0: Eq. 18 parameters; F_out: device pointer to 3 doubles (written).
+ * The first call on a device looks up the array's device address once (with that
+ * device current); make that first call before any stream capture.  Every call uses
+ * the same array and leaves its contents behind; each call writes every partial it
+ * reads, so nothing needs clearing, but calls whose work overlaps on the GPU (on
+ * different streams, or from several threads) race on the array and give wrong sums.
+ * Asynchronous on `stream`.  DF_EINVAL for null pointers, bad sizes or more than
+ * DF_NOALLOC_MAX_CELLS active cells; DF_ECUDA if the lookup or a launch fails.
+ * It calls no cudaMalloc, cudaFree or allocating library routine. */
+#define DF_NOALLOC_MAX_CELLS 4194304
+int df_force_level_noalloc(const double* rho, const int n[3], int G, const double lo[3],
+                           const double dx[3], const int child_off[3], const int child_n[3],
+                           double GM, double eps, double rho0, double* F_out, void* stream);
+
 /* Eq. 55-56 (Appendix A): brute force over xi in {1,2}^(n-1), maximising dt/C. */
 int df_xi_search(int n, const double* dt_level, const double* cost, int* xi_out, double* ratio);
 

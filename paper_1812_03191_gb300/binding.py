@@ -25,7 +25,9 @@ EXPORTS = (
     "df_state_size", "df_get_state", "df_set_state", "df_prolong", "df_restrict",
     "df_fill_bc", "df_kernel_launches", "df_set_timing", "df_kernel_time", "df_kernel_name",
     "df_debug_full_boxes", "df_destroy", "df_xi_search", "df_last_error",
+    "df_force_level_noalloc",
 )
+NOALLOC_MAX_CELLS = 4194304
 
 
 class DfError(RuntimeError):
@@ -95,6 +97,9 @@ def load(path: str = LIB_PATH):
         "df_destroy": (C.c_int, [vp]),
         "df_xi_search": (C.c_int, [C.c_int, dp, dp, P(C.c_int), dp]),
         "df_last_error": (C.c_char_p, []),
+        "df_force_level_noalloc": (C.c_int, [vp, P(C.c_int), C.c_int, dp, dp, P(C.c_int),
+                                             P(C.c_int), C.c_double, C.c_double, C.c_double,
+                                             vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -127,6 +132,19 @@ def xi_search(dt_level, cost):
     r = C.c_double()
     _check(lib.df_xi_search(n, _dp(a), _dp(b), xi, C.byref(r)))
     return r.value, [xi[i] for i in range(n - 1)]
+
+
+def force_level_noalloc(rho_dev_ptr, n, G, lo, dx, child_off=None, child_n=None, GM=0.0,
+                        eps=0.0, rho0=1.0, F_dev_ptr=0, stream=None):
+    """Per-level Eq. 18 force on device buffers, with no device allocation (see the
+    C declaration).  rho_dev_ptr / F_dev_ptr are device addresses (ints)."""
+    lib = load()
+    ci = lambda v: (C.c_int * 3)(*v) if v is not None else None  # noqa: E731
+    cd = lambda v: (C.c_double * 3)(*v)  # noqa: E731
+    _check(lib.df_force_level_noalloc(C.c_void_p(rho_dev_ptr), ci(n), int(G), cd(lo), cd(dx),
+                                      ci(child_off), ci(child_n), float(GM), float(eps),
+                                      float(rho0), C.c_void_p(F_dev_ptr),
+                                      C.c_void_p(stream) if stream else None))
 
 
 class Sim:

@@ -56,6 +56,16 @@ struct Level {
 
 }  // namespace
 
+int dfn::set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
 struct df_ctx {
   int nl = 0, prec = 0, device = 0, G = 0;
   int n[3] = {0, 0, 0};

@@ -124,4 +124,7 @@ template <class T> int launch_pack_active(const LevelView& L, int field, double*
 template <class T> int launch_unpack_active(const LevelView& L, int field, const double* in,
                                             int full, cudaStream_t st);
 
+// set the calling thread's last-error message (df_last_error) and return `code`
+int set_error(int code, const char* fmt, ...);
+
 }  // namespace dfn
