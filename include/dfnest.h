@@ -115,8 +115,10 @@ int df_set_field(df_ctx* ctx, int level, int field, const double* host_in);
 int df_get_full(df_ctx* ctx, int level, int field, double* host_out);
 int df_set_full(df_ctx* ctx, int level, int field, const double* host_in);
 
-/* Checkpoint: every padded field of every level plus (t, step) as FP64, in the
- * order level-major, field-minor.  df_state_size gives the element count. */
+/* Checkpoint: every padded field of every level as stored -- the deviation from
+ * the uniform background (rho - rho0, e - e0, v - V), converted to FP64 -- in the
+ * order level-major, field-minor, plus the time t.  df_state_size gives the
+ * element count.  Restoring a saved state resumes a run bitwise. */
 size_t df_state_size(const df_ctx* ctx);
 int df_get_state(df_ctx* ctx, double* host_out, double* t_out);
 int df_set_state(df_ctx* ctx, const double* host_in, double t);

@@ -157,6 +157,7 @@ class Sim:
         if isinstance(n, int):
             n = (n, n, n)
         self.n = tuple(int(x) for x in n)
+        self.lo, self.hi = tuple(float(x) for x in lo), tuple(float(x) for x in hi)
         self.n_levels = int(n_levels)
         self.G = int(G)
         self.precision = precision

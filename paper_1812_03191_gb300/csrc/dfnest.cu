@@ -163,7 +163,7 @@ struct Ops {
     double h = 0.5 * v.dt_scale;
     if (l == 0) n += timed(c, K_BC, [&] { return launch_bc_fill<T>(v, P, st); });
     if (P.hydro_on)
-      n += timed(c, K_SOURCE, [&] { return launch_source<T>(v, b, S, dt, h, 1, gm1, st); });
+      n += timed(c, K_SOURCE, [&] { return launch_source<T>(v, b, S, dt, h, 1, gm1, P, st); });
     int do_lum = P.L != 0.0, do_eps = P.chi > 0.0;
     if (P.hydro_on || do_lum || do_eps)
       n += timed(c, K_COMPRESS, [&] {
@@ -176,15 +176,15 @@ struct Ops {
     }
     if (P.hydro_on) {
       for (int d = 0; d < 3; ++d) {
-        n += timed(c, K_TPREP, [&] { return launch_tprep<T>(v, b, S, st); });
-        n += timed(c, K_TFLUX, [&] { return launch_tflux<T>(v, b, S, d, dt, st); });
+        n += timed(c, K_TPREP, [&] { return launch_tprep<T>(v, b, S, P, st); });
+        n += timed(c, K_TFLUX, [&] { return launch_tflux<T>(v, b, S, d, dt, P, st); });
         if (v.is_child)
           n += timed(c, K_TFRONTIER, [&] { return launch_tfrontier<T>(v, S, d, st); });
-        n += timed(c, K_TMOM, [&] { return launch_tmom<T>(v, b, S, d, dt, st); });
+        n += timed(c, K_TMOM, [&] { return launch_tmom<T>(v, b, S, d, dt, P, st); });
         n += timed(c, K_TUPDATE, [&] { return launch_tupdate<T>(v, b, S, d, st); });
       }
       n += timed(c, K_VREC_SOURCE,
-                 [&] { return launch_vrec_source<T>(v, b, S, dt, h, gm1, st); });
+                 [&] { return launch_vrec_source<T>(v, b, S, dt, h, gm1, P, st); });
     }
     return n;
   }
@@ -352,18 +352,25 @@ int sync_health(df_ctx* c) {
   return DF_OK;
 }
 
+// background value of a field (the stored state is the deviation from it)
+double field_bg(const df_ctx* c, int field) {
+  return field == 0 ? c->P.rho0 : field == 1 ? c->P.e0 : c->P.V[field - 2];
+}
+
 template <class T>
-int do_io(df_ctx* c, int level, int field, double* out, const double* in, int full) {
+int do_io(df_ctx* c, int level, int field, double* out, const double* in, int full,
+          bool raw = false) {
   if (level < 0 || level >= c->nl || field < 0 || field > 4)
     return fail(DF_EINVAL, "level %d / field %d out of range", level, field);
   LevelView& v = c->L[level].v;
   size_t n = full ? (size_t)v.nc : (size_t)v.n[0] * v.n[1] * v.n[2];
   if (in) {
     CK(cudaMemcpyAsync(c->stage, in, n * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    c->launches += launch_unpack_active<T>(v, field, c->stage, full, c->st);
-    c->gexec = c->gexec;  // state change does not invalidate the graph
+    double bgv = raw ? 0.0 : field_bg(c, field);
+    c->launches += launch_unpack_active<T>(v, field, c->stage, full, bgv, c->st);
   } else {
-    c->launches += launch_pack_active<T>(v, field, c->stage, full, c->st);
+    double bgv = raw ? 0.0 : field_bg(c, field);
+    c->launches += launch_pack_active<T>(v, field, c->stage, full, bgv, c->st);
     CK(cudaMemcpyAsync(out, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   }
   CK(cudaGetLastError());
@@ -602,12 +609,11 @@ int df_set_params(df_ctx* c, const df_params* p) {
     LevelView& v = c->L[l].v;
     c->launches += c->prec == DF_FP64 ? launch_init_uniform<double>(v, P, c->st)
                                       : launch_init_uniform<float>(v, P, c->st);
-    CK(cudaMemsetAsync(c->wsum, 0, sizeof(double), c->st));
     if (c->prec == DF_FP64) {
-      c->launches += launch_static_fields<double>(v, P, p->lum_sigma, c->wsum, c->st);
+      c->launches += launch_static_fields<double>(v, P, p->lum_sigma, c->wsum, c->partials, c->st);
       if (p->lum_sigma > 0.0) c->launches += launch_normalise_lum<double>(v, c->wsum, c->st);
     } else {
-      c->launches += launch_static_fields<float>(v, P, p->lum_sigma, c->wsum, c->st);
+      c->launches += launch_static_fields<float>(v, P, p->lum_sigma, c->wsum, c->partials, c->st);
       if (p->lum_sigma > 0.0) c->launches += launch_normalise_lum<float>(v, c->wsum, c->st);
     }
     CK(cudaMemsetAsync(c->L[l].acc, 0, c->L[l].acc_elems * sizeof(double), c->st));
@@ -783,11 +789,16 @@ int df_get_state(df_ctx* c, double* out, double* t_out) {
   if (check_ctx(c)) return DF_EINVAL;
   if (!out) return fail(DF_EINVAL, "null output");
   size_t nc = (size_t)c->L[0].v.nc;
+  DevGuard g(c->device);
+  enter(c);
   for (int l = 0; l < c->nl; ++l)
     for (int f = 0; f < 5; ++f) {
-      int r = df_get_full(c, l, f, out + (l * 5 + f) * nc);
+      int r = c->prec == DF_FP64
+                  ? do_io<double>(c, l, f, out + (l * 5 + f) * nc, nullptr, 1, true)
+                  : do_io<float>(c, l, f, out + (l * 5 + f) * nc, nullptr, 1, true);
       if (r) return r;
     }
+  leave(c);
   if (t_out) return df_status(c, t_out, nullptr, nullptr);
   return DF_OK;
 }
@@ -796,12 +807,16 @@ int df_set_state(df_ctx* c, const double* in, double t) {
   if (check_ctx(c)) return DF_EINVAL;
   if (!in) return fail(DF_EINVAL, "null input");
   size_t nc = (size_t)c->L[0].v.nc;
+  DevGuard g(c->device);
+  enter(c);
   for (int l = 0; l < c->nl; ++l)
     for (int f = 0; f < 5; ++f) {
-      int r = df_set_full(c, l, f, in + (l * 5 + f) * nc);
+      int r = c->prec == DF_FP64
+                  ? do_io<double>(c, l, f, nullptr, in + (l * 5 + f) * nc, 1, true)
+                  : do_io<float>(c, l, f, nullptr, in + (l * 5 + f) * nc, 1, true);
       if (r) return r;
     }
-  DevGuard g(c->device);
+  leave(c);
   CK(cudaMemcpy(&c->ds->t, &t, sizeof(double), cudaMemcpyHostToDevice));
   int zero = 0;
   CK(cudaMemcpy(&c->ds->unhealthy, &zero, sizeof(int), cudaMemcpyHostToDevice));

@@ -73,7 +73,7 @@ struct DevScalars {
 // Every launcher returns the number of kernels it launched.
 template <class T> int launch_source(const LevelView& L, const Box& b, const Scratch& S,
                                      const double* dt, double hscale, int write_pi,
-                                     double gm1, cudaStream_t st);
+                                     double gm1, const Phys& P, cudaStream_t st);
 template <class T> int launch_compress_lum(const LevelView& L, const Box& b, const Scratch& S,
                                            const double* dt, const Phys& P, int do_ss3,
                                            int do_lum, int do_eps, cudaStream_t st);
@@ -82,13 +82,13 @@ template <class T> int launch_diffuse(const LevelView& L, const Box& b, const Sc
 template <class T> int launch_frontier_diff(const LevelView& L, const Scratch& S,
                                             const double* dt, const Phys& P, cudaStream_t st);
 template <class T> int launch_tprep(const LevelView& L, const Box& b, const Scratch& S,
-                                    cudaStream_t st);
+                                    const Phys& P, cudaStream_t st);
 template <class T> int launch_tflux(const LevelView& L, const Box& b, const Scratch& S, int d,
-                                    const double* dt, cudaStream_t st);
+                                    const double* dt, const Phys& P, cudaStream_t st);
 template <class T> int launch_tfrontier(const LevelView& L, const Scratch& S, int d,
                                         cudaStream_t st);
 template <class T> int launch_tmom(const LevelView& L, const Box& b, const Scratch& S, int d,
-                                   const double* dt, cudaStream_t st);
+                                   const double* dt, const Phys& P, cudaStream_t st);
 template <class T> int launch_tupdate(const LevelView& L, const Box& b, const Scratch& S, int d,
                                       cudaStream_t st);
 
@@ -99,7 +99,7 @@ enum KernelKind {
 };
 template <class T> int launch_vrec_source(const LevelView& L, const Box& b, const Scratch& S,
                                           const double* dt, double hscale, double gm1,
-                                          cudaStream_t st);
+                                          const Phys& P, cudaStream_t st);
 template <class T> int launch_bc_fill(const LevelView& L, const Phys& P, cudaStream_t st);
 template <class T> int launch_commup(const LevelView& C, const LevelView& F, cudaStream_t st);
 template <class T> int launch_commmean(const LevelView& C, const LevelView& F, int band,
@@ -116,13 +116,14 @@ int launch_force_finalize(const double* partials, int n, DevScalars* ds, double*
 int launch_time_advance(DevScalars* ds, cudaStream_t st);
 template <class T> int launch_init_uniform(const LevelView& L, const Phys& P, cudaStream_t st);
 template <class T> int launch_static_fields(const LevelView& L, const Phys& P, double lum_sigma,
-                                            double* wsum, cudaStream_t st);
+                                            double* wsum, double* partials, cudaStream_t st);
 template <class T> int launch_normalise_lum(const LevelView& L, const double* wsum,
                                             cudaStream_t st);
+// host I/O; bgv = background value of the field (0 moves the stored deviations)
 template <class T> int launch_pack_active(const LevelView& L, int field, double* out, int full,
-                                          cudaStream_t st);
+                                          double bgv, cudaStream_t st);
 template <class T> int launch_unpack_active(const LevelView& L, int field, const double* in,
-                                            int full, cudaStream_t st);
+                                            int full, double bgv, cudaStream_t st);
 
 // set the calling thread's last-error message (df_last_error) and return `code`
 int set_error(int code, const char* fmt, ...);

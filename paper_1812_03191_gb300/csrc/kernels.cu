@@ -7,6 +7,13 @@
 // host picks the box (the active cells plus the margin whose values can still reach
 // them before the next ghost fill).  T is the state type (double, or float for the
 // FP32-state form); time steps, the force and the frontier flux sums are FP64.
+//
+// The state is stored as deviations from the uniform background of Sec. 3.4:
+// drho = rho - rho0, de = e - e0, dv = v - V.  Every flux is written so that its
+// background part cancels exactly (the mass flux F' = F - rho0 V_d A dt, etc.);
+// the algebra is that of the plain fields, but rounding scales with the
+// perturbation instead of the background, which the FP32 state needs (the drag
+// is a small difference of large contributions).
 #include "internal.h"
 
 #include <math.h>
@@ -54,11 +61,21 @@ __device__ __forceinline__ T upwind(const T* __restrict__ q, int c, int st, T u,
   return a - T(0.5) * (T(1) + cour) * sr;
 }
 
-// products that are later differenced must be rounded on their own: a multiply
-// fused into the subtraction would return the rounding error of the product
-// instead of an exact zero for equal inputs (uniform states stay uniform)
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+// uniform background in the kernels' arithmetic type
+template <class T>
+struct Bg {
+  T rho0, e0, eps0, V[3];
+};
+
+template <class T>
+Bg<T> make_bg(const Phys& P) {
+  Bg<T> b;
+  b.rho0 = (T)P.rho0;
+  b.e0 = (T)P.e0;
+  b.eps0 = (T)(P.e0 / P.rho0);
+  for (int d = 0; d < 3; ++d) b.V[d] = (T)P.V[d];
+  return b;
+}
 
 inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
@@ -81,7 +98,7 @@ __device__ __forceinline__ int coarse_frontier(const LevelView& L, int d, int f0
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_source(LevelView L, Box b, Scratch S,
                                                    const double* __restrict__ dtp, double hscale,
-                                                   int write_pi, T gm1) {
+                                                   int write_pi, T gm1, Bg<T> bg) {
   int i, j, k;
   if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
@@ -90,18 +107,19 @@ __global__ void __launch_bounds__(kBlock) k_source(LevelView L, Box b, Scratch S
   const T h = (T)(hscale * dtp[0]);
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T rc = rho[c], pc = mul_rn(gm1, e[c]), fc = phi[c];
+  const T rc = rho[c], ec = e[c], fc = phi[c];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     T* v = (T*)L.q[F_VX + d];
     if (c3[d] >= 1) {
       int m = c - L.st[d];
-      T pl = mul_rn(gm1, e[m]);
-      T rf = T(0.5) * (rho[m] + rc);
-      T acc = ((pc - pl) / rf + (fc - phi[m])) * (T)L.inv_dx[d];
+      T drf = T(0.5) * (rho[m] + rc);
+      T rf = bg.rho0 + drf;
+      T acc = (gm1 * (ec - e[m]) / rf + (fc - phi[m])) * (T)L.inv_dx[d];
       T vn = v[c] - h * acc;
       v[c] = vn;
-      if (write_pi) ((T*)S.pi[d])[c] = rf * vn;
+      // momentum deviation: rf (V + dv) - rho0 V
+      if (write_pi) ((T*)S.pi[d])[c] = bg.rho0 * vn + drf * (bg.V[d] + vn);
     } else if (write_pi) {
       ((T*)S.pi[d])[c] = T(0);
     }
@@ -113,7 +131,7 @@ template <class T>
 __global__ void __launch_bounds__(kBlock) k_compress_lum(LevelView L, Box b, Scratch S,
                                                          const double* __restrict__ dtp, T gm1,
                                                          T lum, int do_ss3, int do_lum,
-                                                         int do_eps) {
+                                                         int do_eps, Bg<T> bg) {
   int i, j, k;
   if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
   const T dt = (T)(dtp[0] * L.dt_scale);
@@ -127,13 +145,18 @@ __global__ void __launch_bounds__(kBlock) k_compress_lum(LevelView L, Box b, Scr
     T div = (vx[c + L.st[0]] - vx[c]) * (T)L.inv_dx[0] +
             (vy[c + L.st[1]] - vy[c]) * (T)L.inv_dx[1] + (vz[c + L.st[2]] - vz[c]) * (T)L.inv_dx[2];
     T a = T(0.5) * dt * gm1 * div;
-    ec = ec * (T(1) - a) / (T(1) + a);
+    // (e0 + de)(1 - a)/(1 + a) - e0
+    ec = (ec * (T(1) - a) - T(2) * a * bg.e0) / (T(1) + a);
   }
   if (do_lum && i >= L.G && i < L.G + L.n[0] && j >= L.G && j < L.G + L.n[1] && k >= L.G &&
       k < L.G + L.n[2])
     ec = ec + lum * dt * ((const T*)L.lumw)[c];
   e[c] = ec;
-  if (do_eps) ((T*)S.eps)[c] = ec / ((const T*)L.q[F_RHO])[c];
+  if (do_eps) {
+    // e/rho - e0/rho0 = (de - eps0 drho)/(rho0 + drho)
+    T dr = ((const T*)L.q[F_RHO])[c];
+    ((T*)S.eps)[c] = (ec - bg.eps0 * dr) / (bg.rho0 + dr);
+  }
 }
 
 // --------------------------------------------------------------- diffusion
@@ -143,7 +166,7 @@ __device__ __forceinline__ T diff_flux(const LevelView& L, const T* __restrict__
                                        const T* __restrict__ eps, int f, int d, T chi, T dt,
                                        T rho0, int dfr) {
   int m = f - L.st[d];
-  T rf = dfr ? rho0 : T(0.5) * (rho[m] + rho[f]);
+  T rf = dfr ? rho0 : rho0 + T(0.5) * (rho[m] + rho[f]);
   return -chi * rf * (eps[f] - eps[m]) * (T)L.dcoef[d] * dt;
 }
 
@@ -236,24 +259,30 @@ __global__ void __launch_bounds__(kBlock) k_frontier_diff(LevelView L, Scratch S
 
 // --------------------------------------------------------------- transport
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_tprep(LevelView L, Box b, Scratch S) {
+__global__ void __launch_bounds__(kBlock) k_tprep(LevelView L, Box b, Scratch S, Bg<T> bg) {
   int i, j, k;
   if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const T rc = rho[c];
-  ((T*)S.eps)[c] = ((const T*)L.q[F_E])[c] / rc;  // e/rho
+  ((T*)S.eps)[c] = (((const T*)L.q[F_E])[c] - bg.eps0 * rc) / (bg.rho0 + rc);
 #pragma unroll
-  for (int m = 0; m < 3; ++m)
-    ((T*)S.w[m])[c] =
-        c3[m] >= 1 ? ((const T*)S.pi[m])[c] / (T(0.5) * (rho[c - L.st[m]] + rc)) : T(0);
+  for (int m = 0; m < 3; ++m) {
+    T wv = T(0);
+    if (c3[m] >= 1) {
+      // Pi/rho_face - V = (dPi - V drf)/(rho0 + drf)
+      T drf = T(0.5) * (rho[c - L.st[m]] + rc);
+      wv = (((const T*)S.pi[m])[c] - bg.V[m] * drf) / (bg.rho0 + drf);
+    }
+    ((T*)S.w[m])[c] = wv;
+  }
 }
 
 // mass and energy flux at d-faces 2 <= i_d < s_d - 1
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_tflux(LevelView L, Box b, Scratch S, int d,
-                                                  const double* __restrict__ dtp) {
+                                                  const double* __restrict__ dtp, Bg<T> bg) {
   int i, j, k;
   if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
   const int c = cidx(L, i, j, k);
@@ -262,12 +291,15 @@ __global__ void __launch_bounds__(kBlock) k_tflux(LevelView L, Box b, Scratch S,
   if (c3[d] >= 2 && c3[d] < L.s[d] - 1) {
     const T dt = (T)(dtp[0] * L.dt_scale);
     const int st = L.st[d];
-    const T u = ((const T*)L.q[F_VX + d])[c];
+    const T Adt = (T)L.area[d] * dt;
+    const T du = ((const T*)L.q[F_VX + d])[c];
+    const T u = bg.V[d] + du;
     const T cour = u * (dt * (T)L.inv_dx[d]);
-    T rs = upwind((const T*)L.q[F_RHO], c, st, u, cour);
-    Fv = rs * u * (T)L.area[d] * dt;
-    T es = upwind((const T*)S.eps, c, st, u, cour);
-    Ev = es * Fv;
+    const T F0 = bg.rho0 * bg.V[d] * Adt;
+    T drs = upwind((const T*)L.q[F_RHO], c, st, u, cour);
+    Fv = (bg.rho0 * du + drs * u) * Adt;        // F - rho0 V_d A dt
+    T des = upwind((const T*)S.eps, c, st, u, cour);
+    Ev = bg.eps0 * Fv + des * (F0 + Fv);        // E - eps0 rho0 V_d A dt
   }
   ((T*)S.F)[c] = Fv;
   ((T*)S.E)[c] = Ev;
@@ -297,9 +329,10 @@ __global__ void __launch_bounds__(kBlock) k_tfrontier(LevelView L, Scratch S, in
 }
 
 // staggered momentum fluxes of sweep d
+// staggered momentum fluxes of sweep d (deviation: P - V_m rho0 V_d A dt)
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_tmom(LevelView L, Box b, Scratch S, int d,
-                                                 const double* __restrict__ dtp) {
+                                                 const double* __restrict__ dtp, Bg<T> bg) {
   int i, j, k;
   if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
   const int c = cidx(L, i, j, k);
@@ -309,22 +342,23 @@ __global__ void __launch_bounds__(kBlock) k_tmom(LevelView L, Box b, Scratch S, 
   const T* __restrict__ vd = (const T*)L.q[F_VX + d];
   const T* __restrict__ F = (const T*)S.F;
   const T dtdx = dt * (T)L.inv_dx[d];
+  const T F0 = bg.rho0 * bg.V[d] * ((T)L.area[d] * dt);
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     T P = T(0);
     if (m == d) {
       if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
-        T uc = T(0.5) * (vd[c] + vd[c + st]);
+        T uc = bg.V[d] + T(0.5) * (vd[c] + vd[c + st]);
         T Fc = T(0.5) * (F[c] + F[c + st]);
         T ws = upwind((const T*)S.w[m], c + st, st, uc, uc * dtdx);
-        P = ws * Fc;
+        P = bg.V[m] * Fc + ws * (F0 + Fc);
       }
     } else if (c3[d] >= 2 && c3[d] < L.s[d] - 1 && c3[m] >= 1) {
       const int sm = L.st[m];
-      T ue = T(0.5) * (vd[c - sm] + vd[c]);
+      T ue = bg.V[d] + T(0.5) * (vd[c - sm] + vd[c]);
       T Fe = T(0.5) * (F[c - sm] + F[c]);
       T ws = upwind((const T*)S.w[m], c, st, ue, ue * dtdx);
-      P = ws * Fe;
+      P = bg.V[m] * Fe + ws * (F0 + Fe);
     }
     ((T*)S.P[m])[c] = P;
   }
@@ -376,7 +410,7 @@ __global__ void __launch_bounds__(kBlock) k_tupdate(LevelView L, Box b, Scratch 
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_vrec_source(LevelView L, Box b, Scratch S,
                                                         const double* __restrict__ dtp,
-                                                        double hscale, T gm1) {
+                                                        double hscale, T gm1, Bg<T> bg) {
   int i, j, k;
   if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
@@ -385,16 +419,15 @@ __global__ void __launch_bounds__(kBlock) k_vrec_source(LevelView L, Box b, Scra
   const T h = (T)(hscale * dtp[0]);
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T rc = rho[c], pc = mul_rn(gm1, e[c]), fc = phi[c];
+  const T rc = rho[c], ec = e[c], fc = phi[c];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (c3[d] < 1) continue;
     int m = c - L.st[d];
-    T rf = T(0.5) * (rho[m] + rc);
-    T rinv = T(1) / rf;
-    T v = ((const T*)S.pi[d])[c] * rinv;
-    T pl = mul_rn(gm1, e[m]);
-    T acc = ((pc - pl) * rinv + (fc - phi[m])) * (T)L.inv_dx[d];
+    T drf = T(0.5) * (rho[m] + rc);
+    T rinv = T(1) / (bg.rho0 + drf);
+    T v = (((const T*)S.pi[d])[c] - bg.V[d] * drf) * rinv;
+    T acc = (gm1 * (ec - e[m]) * rinv + (fc - phi[m])) * (T)L.inv_dx[d];
     ((T*)L.q[F_VX + d])[c] = v - h * acc;
   }
 }
@@ -420,8 +453,11 @@ __global__ void __launch_bounds__(kBlock) k_bc_axis(LevelView L, int d, int type
   int type = side ? type_hi : type_lo;
   int normal = (f == F_VX + d);
   int dst = side == 0 ? G - g : G + n - 1 + g, src = -1;
-  T sign = T(1), fixed = T(0);
+  (void)rho0;
+  (void)e0;
+  T sign = T(1), fixed = T(0), shift = T(0);
   bool use_fixed = false;
+  const T Vd = d == 0 ? V0 : (d == 1 ? V1 : V2);
   switch (type) {
     case 0:  // periodic
       src = side == 0 ? dst + n : dst - n;
@@ -429,24 +465,24 @@ __global__ void __launch_bounds__(kBlock) k_bc_axis(LevelView L, int d, int type
     case 1:  // outflow
       src = side == 0 ? G : G + n - 1;
       break;
-    case 2: {  // inflow
+    case 2:  // inflow: the background itself, zero deviation
       use_fixed = true;
-      const T vv[3] = {V0, V1, V2};
-      fixed = f == F_RHO ? rho0 : (f == F_E ? e0 : vv[f - F_VX]);
+      fixed = T(0);
       break;
-    }
     default:  // reflect
       if (!normal) {
         src = side == 0 ? G - 1 + g : G + n - g;
       } else {
+        // v_ghost = -v_mirror, so dv_ghost = -dv_mirror - 2 V_d; wall face v = 0
         sign = T(-1);
+        shift = T(-2) * Vd;
         if (side == 0) {
           src = G + g;
         } else {
           int gp = dst - (G + n);
           if (gp == 0) {
             use_fixed = true;
-            fixed = T(0);
+            fixed = -Vd;
           } else {
             src = G + n - gp;
           }
@@ -465,11 +501,11 @@ __global__ void __launch_bounds__(kBlock) k_bc_axis(LevelView L, int d, int type
   } else {
     c3[d] = src;
     int cs = (c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0];
-    q[cd] = sign * q[cs];
+    q[cd] = sign * q[cs] + shift;
   }
   if (type == 3 && side == 0 && normal && g == 1) {
     c3[d] = G;
-    q[(c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0]] = T(0);
+    q[(c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0]] = -Vd;
   }
 }
 
@@ -624,7 +660,9 @@ __device__ __forceinline__ double warp_min(double v) {
 
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_dt_level(LevelView L, int level, double gg,
-                                                     double cfl, int hydro, DevScalars* ds) {
+                                                     double cfl, int hydro, DevScalars* ds,
+                                                     double rho0, double e0, double V0, double V1,
+                                                     double V2) {
   __shared__ double sm[kBlock / 32];
   __shared__ int bad_s;
   if (threadIdx.x == 0) bad_s = 0;
@@ -637,15 +675,16 @@ __global__ void __launch_bounds__(kBlock) k_dt_level(LevelView L, int level, dou
     int j = L.G + (int)((t / L.n[0]) % L.n[1]);
     int k = L.G + (int)(t / ((long long)L.n[0] * L.n[1]));
     int c = (k * L.s[1] + j) * L.s[0] + i;
-    double rho = (double)((const T*)L.q[F_RHO])[c];
-    double e = (double)((const T*)L.q[F_E])[c];
+    double rho = rho0 + (double)((const T*)L.q[F_RHO])[c];
+    double e = e0 + (double)((const T*)L.q[F_E])[c];
+    const double Vb[3] = {V0, V1, V2};
     if (!(rho > 0.0) || !(e > 0.0)) bad_s = 1;
     if (hydro) {
       double cs = sqrt(gg * e / rho);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const T* v = (const T*)L.q[F_VX + d];
-        double v0 = fabs((double)v[c]), v1 = fabs((double)v[c + L.st[d]]);
+        double v0 = fabs(Vb[d] + (double)v[c]), v1 = fabs(Vb[d] + (double)v[c + L.st[d]]);
         double vm = v0 > v1 ? v0 : v1;
         double tt = cfl * L.dx[d] / (cs + vm);
         if (tt < best) best = tt;
@@ -714,7 +753,8 @@ __global__ void __launch_bounds__(kBlock) k_force_level(LevelView L, double GM, 
       double z = L.lo[2] + (ak + 0.5) * L.dx[2];
       double r2 = x * x + y * y + z * z + eps * eps;
       double inv3 = 1.0 / (r2 * sqrt(r2));
-      double m = ((double)((const T*)L.q[F_RHO])[c] - rho0) * L.vol;
+      double m = (double)((const T*)L.q[F_RHO])[c] * L.vol;  // (rho - rho0) V_c
+      (void)rho0;
       fx = GM * m * x * inv3;
       fy = GM * m * y * inv3;
       fz = GM * m * z * inv3;
@@ -787,52 +827,78 @@ __global__ void __launch_bounds__(kBlock) k_init_uniform(LevelView L, T rho0, T 
                                                          T V2) {
   long long c = blockIdx.x * (long long)kBlock + threadIdx.x;
   if (c >= L.nc) return;
-  ((T*)L.q[F_RHO])[c] = rho0;
-  ((T*)L.q[F_E])[c] = e0;
-  ((T*)L.q[F_VX])[c] = V0;
-  ((T*)L.q[F_VX + 1])[c] = V1;
-  ((T*)L.q[F_VX + 2])[c] = V2;
+  (void)rho0;
+  (void)e0;
+  (void)V0;
+  (void)V1;
+  (void)V2;
+#pragma unroll
+  for (int f = 0; f < 5; ++f) ((T*)L.q[f])[c] = T(0);
 }
 
-// Plummer potential (Eq. 16, attractive sign) at every cell centre; Gaussian
-// luminosity weights on active cells (their sum goes to wsum)
+// Plummer potential (Eq. 16, attractive sign) at every cell centre; luminosity
+// weights on active cells (Gaussian weights are normalised afterwards)
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_static(LevelView L, double GM, double eps,
                                                    double sigma, int vertex_ok, int vx0, int vx1,
-                                                   int vx2, double* wsum) {
-  __shared__ double sm[kBlock];
+                                                   int vx2) {
   long long c = blockIdx.x * (long long)kBlock + threadIdx.x;
-  double wgt = 0.0;
-  if (c < L.nc) {
-    int i = (int)(c % L.s[0]), j = (int)((c / L.s[0]) % L.s[1]),
-        k = (int)(c / ((long long)L.s[0] * L.s[1]));
-    double x = L.lo[0] + (i - L.G + 0.5) * L.dx[0];
-    double y = L.lo[1] + (j - L.G + 0.5) * L.dx[1];
-    double z = L.lo[2] + (k - L.G + 0.5) * L.dx[2];
-    ((T*)L.phi)[c] = (T)(-GM / sqrt(x * x + y * y + z * z + eps * eps));
-    bool act = i >= L.G && i < L.G + L.n[0] && j >= L.G && j < L.G + L.n[1] && k >= L.G &&
-               k < L.G + L.n[2];
-    double lw = 0.0;
-    if (act) {
-      if (sigma > 0.0) {
-        wgt = exp(-(x * x + y * y + z * z) / (2.0 * sigma * sigma));
-        lw = wgt;
-      } else if (vertex_ok) {
-        int ai = i - L.G, aj = j - L.G, ak = k - L.G;
-        if ((ai == vx0 - 1 || ai == vx0) && (aj == vx1 - 1 || aj == vx1) &&
-            (ak == vx2 - 1 || ak == vx2))
-          lw = 1.0 / (8.0 * L.vol);
-      }
+  if (c >= L.nc) return;
+  int i = (int)(c % L.s[0]), j = (int)((c / L.s[0]) % L.s[1]),
+      k = (int)(c / ((long long)L.s[0] * L.s[1]));
+  double x = L.lo[0] + (i - L.G + 0.5) * L.dx[0];
+  double y = L.lo[1] + (j - L.G + 0.5) * L.dx[1];
+  double z = L.lo[2] + (k - L.G + 0.5) * L.dx[2];
+  ((T*)L.phi)[c] = (T)(-GM / sqrt(x * x + y * y + z * z + eps * eps));
+  bool act = i >= L.G && i < L.G + L.n[0] && j >= L.G && j < L.G + L.n[1] && k >= L.G &&
+             k < L.G + L.n[2];
+  double lw = 0.0;
+  if (act) {
+    if (sigma > 0.0) {
+      lw = exp(-(x * x + y * y + z * z) / (2.0 * sigma * sigma));
+    } else if (vertex_ok) {
+      int ai = i - L.G, aj = j - L.G, ak = k - L.G;
+      if ((ai == vx0 - 1 || ai == vx0) && (aj == vx1 - 1 || aj == vx1) &&
+          (ak == vx2 - 1 || ak == vx2))
+        lw = 1.0 / (8.0 * L.vol);
     }
-    ((T*)L.lumw)[c] = (T)lw;
   }
-  sm[threadIdx.x] = wgt;
+  ((T*)L.lumw)[c] = (T)lw;
+}
+
+// Gaussian weights: fixed-order sum over the active cells (block tree, then one
+// block in index order), so every context normalises to the same bits
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_lum_partials(LevelView L, double* partials) {
+  __shared__ double sm[kBlock];
+  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  double w = 0.0;
+  if (t < na) {
+    int i = (int)(t % L.n[0]), j = (int)((t / L.n[0]) % L.n[1]),
+        k = (int)(t / ((long long)L.n[0] * L.n[1]));
+    w = (double)((const T*)L.lumw)[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G];
+  }
+  sm[threadIdx.x] = w;
+  __syncthreads();
+  for (int s = kBlock / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] += sm[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int n, double* out) {
+  __shared__ double sm[kBlock];
+  double s = 0.0;
+  for (int p = threadIdx.x; p < n; p += kBlock) s += partials[p];
+  sm[threadIdx.x] = s;
   __syncthreads();
   for (int w = kBlock / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0 && sigma > 0.0) atomicAdd(wsum, sm[0]);
+  if (threadIdx.x == 0) *out = sm[0];
 }
 
 template <class T>
@@ -843,35 +909,37 @@ __global__ void __launch_bounds__(kBlock) k_normalise_lum(LevelView L, const dou
   lw[c] = (T)((double)lw[c] / (wsum[0] * L.vol));
 }
 
+// host I/O: full values = background + stored deviation (bgv = 0 for raw state)
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_pack(LevelView L, int field, double* out, int full) {
+__global__ void __launch_bounds__(kBlock) k_pack(LevelView L, int field, double* out, int full,
+                                                 double bgv) {
   long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
   const T* q = (const T*)L.q[field];
   if (full) {
-    if (t < L.nc) out[t] = (double)q[t];
+    if (t < L.nc) out[t] = bgv + (double)q[t];
     return;
   }
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
   if (t >= na) return;
   int i = (int)(t % L.n[0]), j = (int)((t / L.n[0]) % L.n[1]),
       k = (int)(t / ((long long)L.n[0] * L.n[1]));
-  out[t] = (double)q[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G];
+  out[t] = bgv + (double)q[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G];
 }
 
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_unpack(LevelView L, int field, const double* in,
-                                                   int full) {
+                                                   int full, double bgv) {
   long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
   T* q = (T*)L.q[field];
   if (full) {
-    if (t < L.nc) q[t] = (T)in[t];
+    if (t < L.nc) q[t] = (T)(in[t] - bgv);
     return;
   }
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
   if (t >= na) return;
   int i = (int)(t % L.n[0]), j = (int)((t / L.n[0]) % L.n[1]),
       k = (int)(t / ((long long)L.n[0] * L.n[1]));
-  q[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G] = (T)in[t];
+  q[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G] = (T)(in[t] - bgv);
 }
 
 }  // namespace
@@ -880,8 +948,9 @@ __global__ void __launch_bounds__(kBlock) k_unpack(LevelView L, int field, const
 
 template <class T>
 int launch_source(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
-                  double hscale, int write_pi, double gm1, cudaStream_t st) {
-  k_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, hscale, write_pi, (T)gm1);
+                  double hscale, int write_pi, double gm1, const Phys& P, cudaStream_t st) {
+  k_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, hscale, write_pi, (T)gm1,
+                                                       make_bg<T>(P));
   return 1;
 }
 
@@ -889,7 +958,7 @@ template <class T>
 int launch_compress_lum(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
                         const Phys& P, int do_ss3, int do_lum, int do_eps, cudaStream_t st) {
   k_compress_lum<T><<<grid_for(b.count()), kBlock, 0, st>>>(
-      L, b, S, dt, (T)(P.gamma - 1.0), (T)P.L, do_ss3, do_lum, do_eps);
+      L, b, S, dt, (T)(P.gamma - 1.0), (T)P.L, do_ss3, do_lum, do_eps, make_bg<T>(P));
   return 1;
 }
 
@@ -920,15 +989,16 @@ int launch_frontier_diff(const LevelView& L, const Scratch& S, const double* dt,
 }
 
 template <class T>
-int launch_tprep(const LevelView& L, const Box& b, const Scratch& S, cudaStream_t st) {
-  k_tprep<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S);
+int launch_tprep(const LevelView& L, const Box& b, const Scratch& S, const Phys& P,
+                 cudaStream_t st) {
+  k_tprep<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, make_bg<T>(P));
   return 1;
 }
 
 template <class T>
 int launch_tflux(const LevelView& L, const Box& b, const Scratch& S, int d, const double* dt,
-                 cudaStream_t st) {
-  k_tflux<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d, dt);
+                 const Phys& P, cudaStream_t st) {
+  k_tflux<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d, dt, make_bg<T>(P));
   return 1;
 }
 
@@ -940,8 +1010,8 @@ int launch_tfrontier(const LevelView& L, const Scratch& S, int d, cudaStream_t s
 
 template <class T>
 int launch_tmom(const LevelView& L, const Box& b, const Scratch& S, int d, const double* dt,
-                cudaStream_t st) {
-  k_tmom<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d, dt);
+                const Phys& P, cudaStream_t st) {
+  k_tmom<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d, dt, make_bg<T>(P));
   return 1;
 }
 
@@ -953,8 +1023,9 @@ int launch_tupdate(const LevelView& L, const Box& b, const Scratch& S, int d, cu
 
 template <class T>
 int launch_vrec_source(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
-                       double hscale, double gm1, cudaStream_t st) {
-  k_vrec_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, hscale, (T)gm1);
+                       double hscale, double gm1, const Phys& P, cudaStream_t st) {
+  k_vrec_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, hscale, (T)gm1,
+                                                            make_bg<T>(P));
   return 1;
 }
 
@@ -991,7 +1062,8 @@ int launch_dt_level(const LevelView& L, int level, const Phys& P, DevScalars* ds
                     cudaStream_t st) {
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
   k_dt_level<T><<<grid_for(na), kBlock, 0, st>>>(L, level, P.gamma * (P.gamma - 1.0), P.cfl,
-                                                  P.hydro_on, ds);
+                                                  P.hydro_on, ds, P.rho0, P.e0, P.V[0], P.V[1],
+                                                  P.V[2]);
   return 1;
 }
 
@@ -1040,16 +1112,19 @@ int launch_init_uniform(const LevelView& L, const Phys& P, cudaStream_t st) {
 
 template <class T>
 int launch_static_fields(const LevelView& L, const Phys& P, double lum_sigma, double* wsum,
-                         cudaStream_t st) {
+                         double* partials, cudaStream_t st) {
   int v[3], ok = 1;
   for (int d = 0; d < 3; ++d) {
     double o = -L.lo[d] / L.dx[d];
     v[d] = (int)floor(o + 0.5);
     if (fabs(o - v[d]) > 1e-9 || v[d] < 1 || v[d] > L.n[d] - 1) ok = 0;
   }
-  k_static<T><<<grid_for(L.nc), kBlock, 0, st>>>(L, P.GM, P.eps, lum_sigma, ok, v[0], v[1],
-                                                  v[2], wsum);
-  return 1;
+  k_static<T><<<grid_for(L.nc), kBlock, 0, st>>>(L, P.GM, P.eps, lum_sigma, ok, v[0], v[1], v[2]);
+  if (lum_sigma <= 0.0) return 1;
+  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  k_lum_partials<T><<<grid_for(na), kBlock, 0, st>>>(L, partials);
+  k_sum_partials<<<1, kBlock, 0, st>>>(partials, (int)grid_for(na), wsum);
+  return 3;
 }
 
 template <class T>
@@ -1059,39 +1134,41 @@ int launch_normalise_lum(const LevelView& L, const double* wsum, cudaStream_t st
 }
 
 template <class T>
-int launch_pack_active(const LevelView& L, int field, double* out, int full, cudaStream_t st) {
+int launch_pack_active(const LevelView& L, int field, double* out, int full, double bgv,
+                       cudaStream_t st) {
   long long n = full ? L.nc : (long long)L.n[0] * L.n[1] * L.n[2];
-  k_pack<T><<<grid_for(n), kBlock, 0, st>>>(L, field, out, full);
+  k_pack<T><<<grid_for(n), kBlock, 0, st>>>(L, field, out, full, bgv);
   return 1;
 }
 
 template <class T>
-int launch_unpack_active(const LevelView& L, int field, const double* in, int full,
+int launch_unpack_active(const LevelView& L, int field, const double* in, int full, double bgv,
                          cudaStream_t st) {
   long long n = full ? L.nc : (long long)L.n[0] * L.n[1] * L.n[2];
-  k_unpack<T><<<grid_for(n), kBlock, 0, st>>>(L, field, in, full);
+  k_unpack<T><<<grid_for(n), kBlock, 0, st>>>(L, field, in, full, bgv);
   return 1;
 }
 
 #define DFN_INSTANTIATE(T)                                                                     \
   template int launch_source<T>(const LevelView&, const Box&, const Scratch&, const double*,   \
-                                double, int, double, cudaStream_t);                            \
+                                double, int, double, const Phys&, cudaStream_t);               \
   template int launch_compress_lum<T>(const LevelView&, const Box&, const Scratch&,            \
                                       const double*, const Phys&, int, int, int, cudaStream_t); \
   template int launch_diffuse<T>(const LevelView&, const Box&, const Scratch&, const double*,  \
                                  const Phys&, cudaStream_t);                                   \
   template int launch_frontier_diff<T>(const LevelView&, const Scratch&, const double*,        \
                                        const Phys&, cudaStream_t);                             \
-  template int launch_tprep<T>(const LevelView&, const Box&, const Scratch&, cudaStream_t);    \
-  template int launch_tflux<T>(const LevelView&, const Box&, const Scratch&, int, const double*, \
+  template int launch_tprep<T>(const LevelView&, const Box&, const Scratch&, const Phys&,      \
                                cudaStream_t);                                                  \
+  template int launch_tflux<T>(const LevelView&, const Box&, const Scratch&, int, const double*, \
+                               const Phys&, cudaStream_t);                                     \
   template int launch_tfrontier<T>(const LevelView&, const Scratch&, int, cudaStream_t);       \
   template int launch_tmom<T>(const LevelView&, const Box&, const Scratch&, int, const double*, \
-                              cudaStream_t);                                                   \
+                              const Phys&, cudaStream_t);                                      \
   template int launch_tupdate<T>(const LevelView&, const Box&, const Scratch&, int,            \
                                  cudaStream_t);                                                \
   template int launch_vrec_source<T>(const LevelView&, const Box&, const Scratch&,             \
-                                     const double*, double, double, cudaStream_t);             \
+                                     const double*, double, double, const Phys&, cudaStream_t); \
   template int launch_bc_fill<T>(const LevelView&, const Phys&, cudaStream_t);                 \
   template int launch_commup<T>(const LevelView&, const LevelView&, cudaStream_t);             \
   template int launch_commmean<T>(const LevelView&, const LevelView&, int, cudaStream_t);      \
@@ -1101,10 +1178,11 @@ int launch_unpack_active(const LevelView& L, int field, const double* in, int fu
                                      cudaStream_t);                                            \
   template int launch_init_uniform<T>(const LevelView&, const Phys&, cudaStream_t);            \
   template int launch_static_fields<T>(const LevelView&, const Phys&, double, double*,         \
-                                       cudaStream_t);                                          \
+                                       double*, cudaStream_t);                                 \
   template int launch_normalise_lum<T>(const LevelView&, const double*, cudaStream_t);         \
-  template int launch_pack_active<T>(const LevelView&, int, double*, int, cudaStream_t);       \
-  template int launch_unpack_active<T>(const LevelView&, int, const double*, int, cudaStream_t);
+  template int launch_pack_active<T>(const LevelView&, int, double*, int, double, cudaStream_t); \
+  template int launch_unpack_active<T>(const LevelView&, int, const double*, int, double,      \
+                                       cudaStream_t);
 
 DFN_INSTANTIATE(double)
 DFN_INSTANTIATE(float)

@@ -45,13 +45,35 @@ def field_errors(sim, orc, params):
     return out
 
 
+def force_term_scale(sim, params):
+    """rho0 * sum over uncovered active cells of |GM V_c r_c / (r^2 + eps^2)^1.5|: the
+    oracle forms rho - rho0 from rounded densities, so its force carries an absolute
+    error of order eps_mach times this sum (the library sums the stored deviations)."""
+    GM, eps, rho0 = params["GM"], params["eps"], params["rho0"]
+    tot = 0.0
+    n = np.array(sim.n)
+    for l in range(sim.n_levels):
+        dx = (np.array(sim.hi) - np.array(sim.lo)) / 2**l / n
+        lo = np.array(sim.lo) / 2**l
+        ax = [lo[d] + (np.arange(n[d]) + 0.5) * dx[d] for d in range(3)]
+        z, y, x = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        r2 = x**2 + y**2 + z**2 + eps**2
+        w = GM * np.prod(dx) * np.sqrt(x**2 + y**2 + z**2) / r2**1.5
+        if l + 1 < sim.n_levels:
+            q = n // 4
+            w[q[2]:q[2] + n[2] // 2, q[1]:q[1] + n[1] // 2, q[0]:q[0] + n[0] // 2] = 0
+        tot += w.sum()
+    return rho0 * tot
+
+
 def assert_parity(sim, orc, params, tol=TOL, ftol=TOL):
     errs = field_errors(sim, orc, params)
     worst = max(errs, key=lambda x: x[2])
     assert worst[2] <= tol, f"level {worst[0]} field {worst[1]}: {worst[2]:.3e}"
     F, _ = sim.force()
     Fo = orc.force()
-    assert np.abs(F - Fo).max() <= ftol * max(np.abs(Fo).max(), 1e-300), (F, Fo)
+    bound = ftol * np.abs(Fo).max() + 64 * np.finfo(float).eps * force_term_scale(sim, params)
+    assert np.abs(F - Fo).max() <= bound, (F, Fo, bound)
     t, dt, bad = sim.status()
     assert bad == 0
     assert abs(t - orc.t) <= 1e-13 * max(orc.t, 1e-300)
@@ -171,7 +193,10 @@ def test_bc_fill_matches():
     sim.fill_bc()
     orc.fill_bc()
     for f in range(5):
-        assert np.array_equal(sim.get_full(0, f), orc.get_full(0, f)), f
+        # the library stores deviations from the background: full values are exact
+        # up to the rounding of background + deviation
+        a, b = sim.get_full(0, f), orc.get_full(0, f)
+        assert np.abs(a - b).max() <= 4e-16 * np.abs(b).max(), f
 
 
 def test_time_step_matches():
