@@ -153,6 +153,12 @@ int df_debug_full_boxes(df_ctx* ctx, int on);
 
 int df_destroy(df_ctx* ctx);
 
+/* Self-check of the FP64 division the stencil kernels use (Newton-Raphson on the
+ * hardware reciprocal estimate, Markstein 1990) against IEEE division on the current
+ * device: n operand pairs from host arrays; *max_ulp receives the largest difference
+ * in units in the last place of the IEEE quotient.  Synchronous. */
+int df_check_division(const double* a, const double* b, int n, double* max_ulp);
+
 /* Force of one level without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- a host whose
  * device memory is entirely reserved by another allocator, a latency-critical loop

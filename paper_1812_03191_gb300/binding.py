@@ -25,7 +25,7 @@ EXPORTS = (
     "df_state_size", "df_get_state", "df_set_state", "df_prolong", "df_restrict",
     "df_fill_bc", "df_kernel_launches", "df_set_timing", "df_kernel_time", "df_kernel_name",
     "df_debug_full_boxes", "df_destroy", "df_xi_search", "df_last_error",
-    "df_force_level_noalloc",
+    "df_force_level_noalloc", "df_check_division",
 )
 NOALLOC_MAX_CELLS = 4194304
 
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
         "df_destroy": (C.c_int, [vp]),
         "df_xi_search": (C.c_int, [C.c_int, dp, dp, P(C.c_int), dp]),
         "df_last_error": (C.c_char_p, []),
+        "df_check_division": (C.c_int, [dp, dp, C.c_int, dp]),
         "df_force_level_noalloc": (C.c_int, [vp, P(C.c_int), C.c_int, dp, dp, P(C.c_int),
                                              P(C.c_int), C.c_double, C.c_double, C.c_double,
                                              vp, vp]),
@@ -132,6 +133,16 @@ def xi_search(dt_level, cost):
     r = C.c_double()
     _check(lib.df_xi_search(n, _dp(a), _dp(b), xi, C.byref(r)))
     return r.value, [xi[i] for i in range(n - 1)]
+
+
+def check_division(a, b):
+    """max ulp difference of the kernels' FP64 division from IEEE division"""
+    lib = load()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    m = C.c_double()
+    _check(lib.df_check_division(_dp(a), _dp(b), a.size, C.byref(m)))
+    return m.value
 
 
 def force_level_noalloc(rho_dev_ptr, n, G, lo, dx, child_off=None, child_n=None, GM=0.0,

@@ -141,6 +141,12 @@ void harvest_timing(df_ctx* c) {
 
 template <class T>
 struct Ops {
+  // device address of level l's step in T
+  static const T* level_dt(df_ctx* c, int l) {
+    if (sizeof(T) == 8) return (const T*)&c->ds->dtl[l];
+    return (const T*)&c->ds->dtf[l];
+  }
+
   static Box box(const df_ctx* c, const LevelView& v, int margin) {
     Box b;
     int M = c->full_boxes ? v.G : margin;
@@ -155,15 +161,14 @@ struct Ops {
     LevelView& v = c->L[l].v;
     const Phys& P = c->P;
     cudaStream_t st = c->st;
-    const double* dt = &c->ds->dt;
+    const T* dt = level_dt(c, l);
     const Scratch& S = c->S;
     long long n = 0;
     Box b = box(c, v, m_out + kReach);
     double gm1 = P.gamma - 1.0;
-    double h = 0.5 * v.dt_scale;
     if (l == 0) n += timed(c, K_BC, [&] { return launch_bc_fill<T>(v, P, st); });
     if (P.hydro_on)
-      n += timed(c, K_SOURCE, [&] { return launch_source<T>(v, b, S, dt, h, 1, gm1, P, st); });
+      n += timed(c, K_SOURCE, [&] { return launch_source<T>(v, b, S, dt, 1, gm1, P, st); });
     int do_lum = P.L != 0.0, do_eps = P.chi > 0.0;
     if (P.hydro_on || do_lum || do_eps)
       n += timed(c, K_COMPRESS, [&] {
@@ -184,7 +189,7 @@ struct Ops {
         n += timed(c, K_TUPDATE, [&] { return launch_tupdate<T>(v, b, S, d, st); });
       }
       n += timed(c, K_VREC_SOURCE,
-                 [&] { return launch_vrec_source<T>(v, b, S, dt, h, gm1, P, st); });
+                 [&] { return launch_vrec_source<T>(v, b, S, dt, gm1, P, st); });
     }
     return n;
   }
@@ -206,7 +211,7 @@ struct Ops {
     return n;
   }
 
-  static void prods(const df_ctx* c, double* out /* 2*nl */) {
+  static void prods(const df_ctx* c, double* out /* 5*nl */) {
     double pr = 1.0;
     for (int l = 0; l < c->nl; ++l) {
       if (l > 0) pr *= c->xi[l - 1];
@@ -219,6 +224,8 @@ struct Ops {
         lim = c->P.cfl_diff / (2.0 * c->P.chi * sinv);
       }
       out[c->nl + l] = lim;
+      for (int d = 0; d < 3; ++d)
+        out[2 * c->nl + 3 * l + d] = c->P.hydro_on ? c->P.cfl * v.dx[d] : 0.0;
     }
   }
 
@@ -247,7 +254,7 @@ struct Ops {
   // one coarse step with the current xi word
   static long long coarse_step(df_ctx* c) {
     long long n = dt_levels(c);
-    double pr[2 * DF_MAX_LEVELS];
+    double pr[5 * DF_MAX_LEVELS];
     prods(c, pr);
     n += timed(c, K_DT, [&] { return launch_dt_finalize(c->ds, c->nl, pr, c->P.dt_fixed, c->st); });
     n += advance(c, 0, 0);
@@ -265,17 +272,20 @@ int run_steps(df_ctx* c, int nsteps) {
     // Eq. 55-56 search each coarse step: per-level limits come back to the host
     for (int s = 0; s < nsteps; ++s) {
       c->launches += Ops<T>::dt_levels(c);
-      unsigned long long bits[DF_MAX_LEVELS];
-      CK(cudaMemcpyAsync(bits, c->ds->dtmin, c->nl * sizeof(unsigned long long),
+      unsigned long long bits[3 * DF_MAX_LEVELS];
+      CK(cudaMemcpyAsync(bits, c->ds->dtmin, 3 * c->nl * sizeof(unsigned long long),
                          cudaMemcpyDeviceToHost, c->st));
       CK(cudaStreamSynchronize(c->st));
-      double pr[2 * DF_MAX_LEVELS], lim[DF_MAX_LEVELS], cost[DF_MAX_LEVELS];
+      double pr[5 * DF_MAX_LEVELS], lim[DF_MAX_LEVELS], cost[DF_MAX_LEVELS];
       for (int l = 0; l < c->nl; ++l) c->xi[l] = 2;
       Ops<T>::prods(c, pr);
       for (int l = 0; l < c->nl; ++l) {
-        double b;
-        memcpy(&b, &bits[l], 8);
-        lim[l] = std::min(b, pr[c->nl + l]);
+        lim[l] = pr[c->nl + l];
+        for (int d = 0; d < 3; ++d) {
+          double mx;
+          memcpy(&mx, &bits[3 * l + d], 8);
+          lim[l] = std::min(lim[l], pr[2 * c->nl + 3 * l + d] / mx);
+        }
         cost[l] = (double)c->n[0] * c->n[1] * c->n[2];
       }
       int xiw[DF_MAX_LEVELS];
@@ -384,6 +394,7 @@ void free_ctx(df_ctx* c) {
   for (auto& l : c->L) {
     cudaFree(l.mem);
     cudaFree(l.acc);
+    cudaFree(l.v.fw);
   }
   cudaFree(c->scratch_mem);
   cudaFree(c->ds);
@@ -533,6 +544,7 @@ int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], co
     v.acc_slots = slots;
     c->L[l].acc_elems = (size_t)18 * slots;
     CKF(cudaMalloc(&c->L[l].acc, c->L[l].acc_elems * sizeof(double)));
+    CKF(cudaMalloc(&v.fw, (size_t)n[0] * n[1] * n[2] * sizeof(double)));
     CKF(cudaMemset(c->L[l].acc, 0, c->L[l].acc_elems * sizeof(double)));
     v.acc = c->L[l].acc;
   }
@@ -562,10 +574,14 @@ int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], co
   }
   CKF(cudaMalloc(&c->ds, sizeof(DevScalars)));
   CKF(cudaMemset(c->ds, 0, sizeof(DevScalars)));
+  // partials: 3 per force block of every level, and one per 256 active cells of a
+  // level for the luminosity normalisation (the two uses never overlap in time)
   int np = 0;
   for (int l = 0; l < n_levels; ++l) np += force_partials_per_level(c->L[l].v);
   c->n_partials = np;
-  CKF(cudaMalloc(&c->partials, 3 * (size_t)np * sizeof(double)));
+  size_t lum_blocks = ((size_t)n[0] * n[1] * n[2] + 255) / 256;
+  size_t pelems = std::max(3 * (size_t)np, lum_blocks);
+  CKF(cudaMalloc(&c->partials, pelems * sizeof(double)));
   CKF(cudaMalloc(&c->ring, 3 * (size_t)c->ring_cap * sizeof(double)));
   CKF(cudaMalloc(&c->ring_pos, sizeof(long long)));
   CKF(cudaMemset(c->ring_pos, 0, sizeof(long long)));
@@ -617,13 +633,11 @@ int df_set_params(df_ctx* c, const df_params* p) {
       if (p->lum_sigma > 0.0) c->launches += launch_normalise_lum<float>(v, c->wsum, c->st);
     }
     CK(cudaMemsetAsync(c->L[l].acc, 0, c->L[l].acc_elems * sizeof(double), c->st));
+    c->launches += launch_force_weights(v, P, c->st);
   }
   DevScalars h;
   memset(&h, 0, sizeof h);
-  for (int l = 0; l < 32; ++l) {
-    double inf = INFINITY;
-    memcpy(&h.dtmin[l], &inf, 8);
-  }
+  // per-axis maxima start at +0.0 (bit pattern 0)
   CK(cudaMemcpyAsync(c->ds, &h, sizeof h, cudaMemcpyHostToDevice, c->st));
   CK(cudaMemsetAsync(c->ring_pos, 0, sizeof(long long), c->st));
   CK(cudaGetLastError());
@@ -705,34 +719,26 @@ int df_compute_dt(df_ctx* c, double* dt, double* dt_level) {
   enter(c);
   long long n =
       c->prec == DF_FP64 ? Ops<double>::dt_levels(c) : Ops<float>::dt_levels(c);
-  unsigned long long bits[DF_MAX_LEVELS];
-  CK(cudaMemcpyAsync(bits, c->ds->dtmin, c->nl * sizeof(unsigned long long),
-                     cudaMemcpyDeviceToHost, c->st));
-  double pr[2 * DF_MAX_LEVELS];
+  double pr[5 * DF_MAX_LEVELS];
   for (int l = 0; l < c->nl; ++l) c->xi[l] = 2;
   if (c->prec == DF_FP64)
     Ops<double>::prods(c, pr);
   else
     Ops<float>::prods(c, pr);
-  // the finalize kernel resets the per-level minima; keep the step in a copy
+  // the finalize kernel overwrites the coarse step; keep the last one taken
   DevScalars before;
   CK(cudaMemcpyAsync(&before, c->ds, sizeof before, cudaMemcpyDeviceToHost, c->st));
   n += launch_dt_finalize(c->ds, c->nl, pr, c->P.dt_fixed, c->st);
   DevScalars after;
   CK(cudaMemcpyAsync(&after, c->ds, sizeof after, cudaMemcpyDeviceToHost, c->st));
   CK(cudaStreamSynchronize(c->st));
-  // restore the previous coarse step (df_status reports the last one taken)
   CK(cudaMemcpyAsync(&c->ds->dt, &before.dt, sizeof(double), cudaMemcpyHostToDevice, c->st));
   CK(cudaStreamSynchronize(c->st));
   leave(c);
   c->launches += n;
   if (dt) *dt = after.dt;
   if (dt_level)
-    for (int l = 0; l < c->nl; ++l) {
-      double b;
-      memcpy(&b, &bits[l], 8);
-      dt_level[l] = std::min(b, pr[c->nl + l]);
-    }
+    for (int l = 0; l < c->nl; ++l) dt_level[l] = after.dtlev[l];
   return DF_OK;
 }
 
@@ -901,6 +907,24 @@ int df_debug_full_boxes(df_ctx* c, int on) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
   }
+  return DF_OK;
+}
+
+int df_check_division(const double* a_host, const double* b_host, int n, double* max_ulp) {
+  if (!a_host || !b_host || !max_ulp || n < 1) return fail(DF_EINVAL, "bad division check input");
+  double *da = nullptr, *db = nullptr, *dm = nullptr;
+  CK(cudaMalloc(&da, n * sizeof(double)));
+  CK(cudaMalloc(&db, n * sizeof(double)));
+  CK(cudaMalloc(&dm, sizeof(double)));
+  CK(cudaMemcpy(da, a_host, n * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(db, b_host, n * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemset(dm, 0, sizeof(double)));
+  launch_hdiv_check(da, db, n, dm, nullptr);
+  CK(cudaGetLastError());
+  CK(cudaMemcpy(max_ulp, dm, sizeof(double), cudaMemcpyDeviceToHost));
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dm);
   return DF_OK;
 }
 

@@ -25,6 +25,7 @@ struct LevelView {
   void* q[5];         // rho, e, vx, vy, vz
   void* phi;          // potential at cell centres (Eq. 16)
   void* lumw;         // luminosity weight / cell volume on active cells
+  double* fw;         // static force weights GM V_c / (r^2 + eps^2)^(3/2), active cells
   double* acc;        // frontier flux sums of this level as a child: [side][quantity][slot]
   int acc_slots;      // slots per (side, quantity) block
   // child geometry (coarse frontier overwrite, covered mask), has_child = 0 if none
@@ -64,31 +65,35 @@ struct DevScalars {
   double t;                   // simulated time
   double F[3];                // force after the last coarse step
   double dt_last;             // coarse step of the last completed coarse step
-  unsigned long long dtmin[32];  // per-level time-step limits (bit patterns of positive doubles)
+  unsigned long long dtmin[48];  // per-level, per-axis max of cs + |v_d| (bit patterns)
+  double dtlev[16];              // per-level limits of the last reduction
+  double dtl[16];                // level step of each level: dt / prod_{m<l} xi_m
+  float dtf[16];                 // the same in FP32
   int unhealthy;
   int pad;
 };
 
 // ---- launchers (kernels.cu); T = double or float, all asynchronous on `st`.
 // Every launcher returns the number of kernels it launched.
+// dt: device pointer to this level's step in T (DevScalars::dtl or ::dtf)
 template <class T> int launch_source(const LevelView& L, const Box& b, const Scratch& S,
-                                     const double* dt, double hscale, int write_pi,
-                                     double gm1, const Phys& P, cudaStream_t st);
+                                     const T* dt, int write_pi, double gm1, const Phys& P,
+                                     cudaStream_t st);
 template <class T> int launch_compress_lum(const LevelView& L, const Box& b, const Scratch& S,
-                                           const double* dt, const Phys& P, int do_ss3,
-                                           int do_lum, int do_eps, cudaStream_t st);
+                                           const T* dt, const Phys& P, int do_ss3, int do_lum,
+                                           int do_eps, cudaStream_t st);
 template <class T> int launch_diffuse(const LevelView& L, const Box& b, const Scratch& S,
-                                      const double* dt, const Phys& P, cudaStream_t st);
-template <class T> int launch_frontier_diff(const LevelView& L, const Scratch& S,
-                                            const double* dt, const Phys& P, cudaStream_t st);
+                                      const T* dt, const Phys& P, cudaStream_t st);
+template <class T> int launch_frontier_diff(const LevelView& L, const Scratch& S, const T* dt,
+                                            const Phys& P, cudaStream_t st);
 template <class T> int launch_tprep(const LevelView& L, const Box& b, const Scratch& S,
                                     const Phys& P, cudaStream_t st);
 template <class T> int launch_tflux(const LevelView& L, const Box& b, const Scratch& S, int d,
-                                    const double* dt, const Phys& P, cudaStream_t st);
+                                    const T* dt, const Phys& P, cudaStream_t st);
 template <class T> int launch_tfrontier(const LevelView& L, const Scratch& S, int d,
                                         cudaStream_t st);
 template <class T> int launch_tmom(const LevelView& L, const Box& b, const Scratch& S, int d,
-                                   const double* dt, const Phys& P, cudaStream_t st);
+                                   const T* dt, const Phys& P, cudaStream_t st);
 template <class T> int launch_tupdate(const LevelView& L, const Box& b, const Scratch& S, int d,
                                       cudaStream_t st);
 
@@ -98,8 +103,8 @@ enum KernelKind {
   K_TMOM, K_TUPDATE, K_VREC_SOURCE, K_COMMUP, K_COMMMEAN, K_DT, K_FORCE, K_OTHER, K_NKINDS
 };
 template <class T> int launch_vrec_source(const LevelView& L, const Box& b, const Scratch& S,
-                                          const double* dt, double hscale, double gm1,
-                                          const Phys& P, cudaStream_t st);
+                                          const T* dt, double gm1, const Phys& P,
+                                          cudaStream_t st);
 template <class T> int launch_bc_fill(const LevelView& L, const Phys& P, cudaStream_t st);
 template <class T> int launch_commup(const LevelView& C, const LevelView& F, cudaStream_t st);
 template <class T> int launch_commmean(const LevelView& C, const LevelView& F, int band,
@@ -111,6 +116,7 @@ int launch_dt_finalize(DevScalars* ds, int n_levels, const double* prod, double 
 template <class T> int launch_force_level(const LevelView& L, const Phys& P, double* partials,
                                           int offset, cudaStream_t st);
 int force_partials_per_level(const LevelView& L);
+int launch_force_weights(const LevelView& L, const Phys& P, cudaStream_t st);
 int launch_force_finalize(const double* partials, int n, DevScalars* ds, double* ring,
                           int ring_cap, long long* ring_pos, cudaStream_t st);
 int launch_time_advance(DevScalars* ds, cudaStream_t st);
@@ -124,6 +130,9 @@ template <class T> int launch_pack_active(const LevelView& L, int field, double*
                                           double bgv, cudaStream_t st);
 template <class T> int launch_unpack_active(const LevelView& L, int field, const double* in,
                                             int full, double bgv, cudaStream_t st);
+
+// hot-path FP64 division versus IEEE division (device arrays; max_ulp zeroed by caller)
+int launch_hdiv_check(const double* a, const double* b, int n, double* max_ulp, cudaStream_t st);
 
 // set the calling thread's last-error message (df_last_error) and return `code`
 int set_error(int code, const char* fmt, ...);

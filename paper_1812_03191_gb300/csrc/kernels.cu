@@ -24,16 +24,17 @@ namespace {
 
 constexpr int kBlock = 256;
 
-__device__ __forceinline__ bool decode(const Box& b, long long t, int& i, int& j, int& k) {
-  int bx = b.hi[0] - b.lo[0], by = b.hi[1] - b.lo[1], bz = b.hi[2] - b.lo[2];
-  long long plane = (long long)bx * by;
+// box element t -> (i, j, k); boxes hold fewer than 2^31 elements
+__device__ __forceinline__ bool decode(const Box& b, unsigned t, int& i, int& j, int& k) {
+  unsigned bx = b.hi[0] - b.lo[0], by = b.hi[1] - b.lo[1], bz = b.hi[2] - b.lo[2];
+  unsigned plane = bx * by;
   if (t >= plane * bz) return false;
-  int kk = (int)(t / plane);
-  int r = (int)(t - (long long)kk * plane);
-  int jj = r / bx;
-  i = b.lo[0] + (r - jj * bx);
-  j = b.lo[1] + jj;
-  k = b.lo[2] + kk;
+  unsigned kk = t / plane;
+  unsigned r = t - kk * plane;
+  unsigned jj = r / bx;
+  i = b.lo[0] + (int)(r - jj * bx);
+  j = b.lo[1] + (int)jj;
+  k = b.lo[2] + (int)kk;
   return true;
 }
 
@@ -41,11 +42,30 @@ __device__ __forceinline__ int cidx(const LevelView& L, int i, int j, int k) {
   return (k * L.s[1] + j) * L.s[0] + i;
 }
 
-// van Leer (1977) harmonic limited slope (Sec. 3.2.1 cites it for the interpolation)
+// Division on the hot path.  FP64: Newton-Raphson refinement of the hardware
+// reciprocal estimate (two steps r <- r + r(1 - b r), then one residual correction
+// q <- q + r(a - b q), after Markstein, IBM J. Res. Dev. 34 (1990)); accurate to
+// about one ulp for the normal, non-zero divisors used here (densities, 1 + a,
+// and the sum of two same-signed slopes).  FP32: the fast reciprocal-based divide.
+__device__ __forceinline__ double hdiv(double a, double b) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+  double e = fma(-b, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-b, r, 1.0);
+  r = fma(r, e, r);
+  double q = a * r;
+  return fma(r, fma(-b, q, a), q);
+}
+__device__ __forceinline__ float hdiv(float a, float b) { return __fdividef(a, b); }
+
+// van Leer (1977) harmonic limited slope (Sec. 3.2.1 cites it for the interpolation).
+// When the product underflows to zero the slope is zero, so the divisor dl + dr is
+// never zero or subnormal.
 template <class T>
 __device__ __forceinline__ T vanleer(T dl, T dr) {
   T pr = dl * dr;
-  return pr <= T(0) ? T(0) : (T(2) * pr) / (dl + dr);
+  return pr <= T(0) ? T(0) : hdiv(T(2) * pr, dl + dr);
 }
 
 // time-centred upwind value at the face between elements c-st and c
@@ -59,6 +79,25 @@ __device__ __forceinline__ T upwind(const T* __restrict__ q, int c, int st, T u,
   T a = q[c];
   T sr = vanleer(a - q[c - st], q[c + st] - a);
   return a - T(0.5) * (T(1) + cour) * sr;
+}
+
+// per-level geometry constants in the kernels' arithmetic type (no FP64 work in
+// FP32 kernels: GB300's FP64 pipe is 1/64 of its FP32 rate)
+template <class T>
+struct Geo {
+  T inv_dx[3], area[3], dcoef[3], inv_vol;
+};
+
+template <class T>
+Geo<T> make_geo(const LevelView& L) {
+  Geo<T> g;
+  for (int d = 0; d < 3; ++d) {
+    g.inv_dx[d] = (T)L.inv_dx[d];
+    g.area[d] = (T)L.area[d];
+    g.dcoef[d] = (T)L.dcoef[d];
+  }
+  g.inv_vol = (T)L.inv_vol;
+  return g;
 }
 
 // uniform background in the kernels' arithmetic type
@@ -97,14 +136,14 @@ __device__ __forceinline__ int coarse_frontier(const LevelView& L, int d, int f0
 // S(h) of Eq. 15: v_d -= h [ (p_c - p_m)/(dx rho_face) + (Phi_c - Phi_m)/dx ]
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_source(LevelView L, Box b, Scratch S,
-                                                   const double* __restrict__ dtp, double hscale,
-                                                   int write_pi, T gm1, Bg<T> bg) {
+                                                   const T* __restrict__ dtp, int write_pi, T gm1,
+                                                   Bg<T> bg, Geo<T> g) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const T* __restrict__ e = (const T*)L.q[F_E];
   const T* __restrict__ phi = (const T*)L.phi;
-  const T h = (T)(hscale * dtp[0]);
+  const T h = T(0.5) * dtp[0];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const T rc = rho[c], ec = e[c], fc = phi[c];
@@ -115,7 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_source(LevelView L, Box b, Scratch S
       int m = c - L.st[d];
       T drf = T(0.5) * (rho[m] + rc);
       T rf = bg.rho0 + drf;
-      T acc = (gm1 * (ec - e[m]) / rf + (fc - phi[m])) * (T)L.inv_dx[d];
+      T acc = (hdiv(gm1 * (ec - e[m]), rf) + (fc - phi[m])) * g.inv_dx[d];
       T vn = v[c] - h * acc;
       v[c] = vn;
       // momentum deviation: rf (V + dv) - rho0 V
@@ -129,12 +168,12 @@ __global__ void __launch_bounds__(kBlock) k_source(LevelView L, Box b, Scratch S
 // ------------------------------------------------- SubStep3 + luminosity + e/rho
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_compress_lum(LevelView L, Box b, Scratch S,
-                                                         const double* __restrict__ dtp, T gm1,
+                                                         const T* __restrict__ dtp, T gm1,
                                                          T lum, int do_ss3, int do_lum,
-                                                         int do_eps, Bg<T> bg) {
+                                                         int do_eps, Bg<T> bg, Geo<T> g) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
-  const T dt = (T)(dtp[0] * L.dt_scale);
+  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
+  const T dt = dtp[0];
   const int c = cidx(L, i, j, k);
   T* e = (T*)L.q[F_E];
   T ec = e[c];
@@ -142,11 +181,11 @@ __global__ void __launch_bounds__(kBlock) k_compress_lum(LevelView L, Box b, Scr
     const T* vx = (const T*)L.q[F_VX];
     const T* vy = (const T*)L.q[F_VX + 1];
     const T* vz = (const T*)L.q[F_VX + 2];
-    T div = (vx[c + L.st[0]] - vx[c]) * (T)L.inv_dx[0] +
-            (vy[c + L.st[1]] - vy[c]) * (T)L.inv_dx[1] + (vz[c + L.st[2]] - vz[c]) * (T)L.inv_dx[2];
+    T div = (vx[c + L.st[0]] - vx[c]) * g.inv_dx[0] + (vy[c + L.st[1]] - vy[c]) * g.inv_dx[1] +
+            (vz[c + L.st[2]] - vz[c]) * g.inv_dx[2];
     T a = T(0.5) * dt * gm1 * div;
     // (e0 + de)(1 - a)/(1 + a) - e0
-    ec = (ec * (T(1) - a) - T(2) * a * bg.e0) / (T(1) + a);
+    ec = hdiv(ec * (T(1) - a) - T(2) * a * bg.e0, T(1) + a);
   }
   if (do_lum && i >= L.G && i < L.G + L.n[0] && j >= L.G && j < L.G + L.n[1] && k >= L.G &&
       k < L.G + L.n[2])
@@ -155,29 +194,29 @@ __global__ void __launch_bounds__(kBlock) k_compress_lum(LevelView L, Box b, Scr
   if (do_eps) {
     // e/rho - e0/rho0 = (de - eps0 drho)/(rho0 + drho)
     T dr = ((const T*)L.q[F_RHO])[c];
-    ((T*)S.eps)[c] = (ec - bg.eps0 * dr) / (bg.rho0 + dr);
+    ((T*)S.eps)[c] = hdiv(ec - bg.eps0 * dr, bg.rho0 + dr);
   }
 }
 
 // --------------------------------------------------------------- diffusion
 // energy moved in +d across a face during dt: -chi rho_f d(e/rho)/dx * area * dt
 template <class T>
-__device__ __forceinline__ T diff_flux(const LevelView& L, const T* __restrict__ rho,
-                                       const T* __restrict__ eps, int f, int d, T chi, T dt,
-                                       T rho0, int dfr) {
+__device__ __forceinline__ T diff_flux(const LevelView& L, const Geo<T>& g,
+                                       const T* __restrict__ rho, const T* __restrict__ eps, int f,
+                                       int d, T chi, T dt, T rho0, int dfr) {
   int m = f - L.st[d];
   T rf = dfr ? rho0 : rho0 + T(0.5) * (rho[m] + rho[f]);
-  return -chi * rf * (eps[f] - eps[m]) * (T)L.dcoef[d] * dt;
+  return -chi * rf * (eps[f] - eps[m]) * g.dcoef[d] * dt;
 }
 
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_diffuse(LevelView L, Box b, Scratch S,
-                                                    const double* __restrict__ dtp, T chi,
-                                                    T rho0, int dfr) {
+                                                    const T* __restrict__ dtp, T chi, T rho0,
+                                                    int dfr, Geo<T> g) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
   if (i < 1 || j < 1 || k < 1 || i >= L.s[0] - 1 || j >= L.s[1] - 1 || k >= L.s[2] - 1) return;
-  const T dt = (T)(dtp[0] * L.dt_scale);
+  const T dt = dtp[0];
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const T* __restrict__ eps = (const T*)S.eps;
   const int c = cidx(L, i, j, k);
@@ -186,8 +225,8 @@ __global__ void __launch_bounds__(kBlock) k_diffuse(LevelView L, Box b, Scratch 
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     int up = c + L.st[d];
-    T qlo = diff_flux(L, rho, eps, c, d, chi, dt, rho0, dfr);
-    T qhi = diff_flux(L, rho, eps, up, d, chi, dt, rho0, dfr);
+    T qlo = diff_flux(L, g, rho, eps, c, d, chi, dt, rho0, dfr);
+    T qhi = diff_flux(L, g, rho, eps, up, d, chi, dt, rho0, dfr);
     if (L.has_child) {
       int slot, f3[3] = {c3[0], c3[1], c3[2]};
       int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
@@ -199,7 +238,7 @@ __global__ void __launch_bounds__(kBlock) k_diffuse(LevelView L, Box b, Scratch 
     div += qhi - qlo;
   }
   T* e = (T*)L.q[F_E];
-  e[c] = e[c] - div * (T)L.inv_vol;
+  e[c] = e[c] - div * g.inv_vol;
 }
 
 // fine frontier faces of one side: the 4 faces of one coarse slot, accumulated in
@@ -236,11 +275,11 @@ __device__ __forceinline__ bool slot_of(const LevelView& L, long long t, int sid
 
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_frontier_diff(LevelView L, Scratch S,
-                                                          const double* __restrict__ dtp, T chi,
-                                                          T rho0, int dfr) {
+                                                          const T* __restrict__ dtp, T chi,
+                                                          T rho0, int dfr, Geo<T> g) {
   int side, a, b;
   if (!slot_of(L, blockIdx.x * (long long)kBlock + threadIdx.x, 0, 6, side, a, b)) return;
-  const T dt = (T)(dtp[0] * L.dt_scale);
+  const T dt = dtp[0];
   const int d = side >> 1;
   const int t1 = d == 0 ? 1 : 0;
   const int slot = b * (L.n[t1] >> 1) + a;
@@ -252,7 +291,8 @@ __global__ void __launch_bounds__(kBlock) k_frontier_diff(LevelView L, Scratch S
     for (int u = 0; u < 2; ++u) {
       int f;
       fine_face(L, side, a, b, u, v, f);
-      s += (double)diff_flux(L, (const T*)L.q[F_RHO], (const T*)S.eps, f, d, chi, dt, rho0, dfr);
+      s += (double)diff_flux(L, g, (const T*)L.q[F_RHO], (const T*)S.eps, f, d, chi, dt, rho0,
+                             dfr);
     }
   *acc = s;
 }
@@ -261,40 +301,42 @@ __global__ void __launch_bounds__(kBlock) k_frontier_diff(LevelView L, Scratch S
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_tprep(LevelView L, Box b, Scratch S, Bg<T> bg) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const T rc = rho[c];
-  ((T*)S.eps)[c] = (((const T*)L.q[F_E])[c] - bg.eps0 * rc) / (bg.rho0 + rc);
+  ((T*)S.eps)[c] = hdiv(((const T*)L.q[F_E])[c] - bg.eps0 * rc, bg.rho0 + rc);
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     T wv = T(0);
     if (c3[m] >= 1) {
       // Pi/rho_face - V = (dPi - V drf)/(rho0 + drf)
       T drf = T(0.5) * (rho[c - L.st[m]] + rc);
-      wv = (((const T*)S.pi[m])[c] - bg.V[m] * drf) / (bg.rho0 + drf);
+      wv = hdiv(((const T*)S.pi[m])[c] - bg.V[m] * drf, bg.rho0 + drf);
     }
     ((T*)S.w[m])[c] = wv;
   }
 }
 
 // mass and energy flux at d-faces 2 <= i_d < s_d - 1
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_tflux(LevelView L, Box b, Scratch S, int d,
-                                                  const double* __restrict__ dtp, Bg<T> bg) {
+// the sweep direction is a template parameter: every per-axis constant is then a
+// fixed kernel-parameter operand instead of a dynamically indexed load
+template <class T, int d>
+__global__ void __launch_bounds__(kBlock) k_tflux(LevelView L, Box b, Scratch S,
+                                                  const T* __restrict__ dtp, Bg<T> bg, Geo<T> g) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   T Fv = T(0), Ev = T(0);
   if (c3[d] >= 2 && c3[d] < L.s[d] - 1) {
-    const T dt = (T)(dtp[0] * L.dt_scale);
+    const T dt = dtp[0];
     const int st = L.st[d];
-    const T Adt = (T)L.area[d] * dt;
+    const T Adt = g.area[d] * dt;
     const T du = ((const T*)L.q[F_VX + d])[c];
     const T u = bg.V[d] + du;
-    const T cour = u * (dt * (T)L.inv_dx[d]);
+    const T cour = u * (dt * g.inv_dx[d]);
     const T F0 = bg.rho0 * bg.V[d] * Adt;
     T drs = upwind((const T*)L.q[F_RHO], c, st, u, cour);
     Fv = (bg.rho0 * du + drs * u) * Adt;        // F - rho0 V_d A dt
@@ -330,19 +372,19 @@ __global__ void __launch_bounds__(kBlock) k_tfrontier(LevelView L, Scratch S, in
 
 // staggered momentum fluxes of sweep d
 // staggered momentum fluxes of sweep d (deviation: P - V_m rho0 V_d A dt)
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_tmom(LevelView L, Box b, Scratch S, int d,
-                                                 const double* __restrict__ dtp, Bg<T> bg) {
+template <class T, int d>
+__global__ void __launch_bounds__(kBlock) k_tmom(LevelView L, Box b, Scratch S,
+                                                 const T* __restrict__ dtp, Bg<T> bg, Geo<T> g) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T dt = (T)(dtp[0] * L.dt_scale);
+  const T dt = dtp[0];
   const int st = L.st[d];
   const T* __restrict__ vd = (const T*)L.q[F_VX + d];
   const T* __restrict__ F = (const T*)S.F;
-  const T dtdx = dt * (T)L.inv_dx[d];
-  const T F0 = bg.rho0 * bg.V[d] * ((T)L.area[d] * dt);
+  const T dtdx = dt * g.inv_dx[d];
+  const T F0 = bg.rho0 * bg.V[d] * (g.area[d] * dt);
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     T P = T(0);
@@ -364,14 +406,14 @@ __global__ void __launch_bounds__(kBlock) k_tmom(LevelView L, Box b, Scratch S, 
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kBlock) k_tupdate(LevelView L, Box b, Scratch S, int d) {
+template <class T, int d>
+__global__ void __launch_bounds__(kBlock) k_tupdate(LevelView L, Box b, Scratch S, Geo<T> g) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const int st = L.st[d];
-  const T iv = (T)L.inv_vol;
+  const T iv = g.inv_vol;
   if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
     T Flo = ((const T*)S.F)[c], Fhi = ((const T*)S.F)[c + st];
     T Elo = ((const T*)S.E)[c], Ehi = ((const T*)S.E)[c + st];
@@ -409,14 +451,14 @@ __global__ void __launch_bounds__(kBlock) k_tupdate(LevelView L, Box b, Scratch 
 // velocity from the transported momenta, then the second half kick S(dt/2)
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_vrec_source(LevelView L, Box b, Scratch S,
-                                                        const double* __restrict__ dtp,
-                                                        double hscale, T gm1, Bg<T> bg) {
+                                                        const T* __restrict__ dtp, T gm1, Bg<T> bg,
+                                                        Geo<T> g) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * (long long)kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const T* __restrict__ e = (const T*)L.q[F_E];
   const T* __restrict__ phi = (const T*)L.phi;
-  const T h = (T)(hscale * dtp[0]);
+  const T h = T(0.5) * dtp[0];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const T rc = rho[c], ec = e[c], fc = phi[c];
@@ -425,9 +467,9 @@ __global__ void __launch_bounds__(kBlock) k_vrec_source(LevelView L, Box b, Scra
     if (c3[d] < 1) continue;
     int m = c - L.st[d];
     T drf = T(0.5) * (rho[m] + rc);
-    T rinv = T(1) / (bg.rho0 + drf);
+    T rinv = hdiv(T(1), bg.rho0 + drf);
     T v = (((const T*)S.pi[d])[c] - bg.V[d] * drf) * rinv;
-    T acc = (gm1 * (ec - e[m]) * rinv + (fc - phi[m])) * (T)L.inv_dx[d];
+    T acc = (gm1 * (ec - e[m]) * rinv + (fc - phi[m])) * g.inv_dx[d];
     ((T*)L.q[F_VX + d])[c] = v - h * acc;
   }
 }
@@ -658,71 +700,98 @@ __device__ __forceinline__ double warp_min(double v) {
   return v;
 }
 
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Per-level Courant limit: min over active cells and axes of cfl dx_d / (cs + |v_d|).
+// Division is correctly rounded and monotone, so that minimum equals
+// cfl dx_d / max(cs + |v_d|): the kernel reduces the per-axis maxima (one division
+// per level instead of three per cell).  Also flags NaN, rho <= 0 or e <= 0.
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_dt_level(LevelView L, int level, double gg,
-                                                     double cfl, int hydro, DevScalars* ds,
-                                                     double rho0, double e0, double V0, double V1,
+                                                     int hydro, DevScalars* ds, double rho0,
+                                                     double e0, double V0, double V1,
                                                      double V2) {
-  __shared__ double sm[kBlock / 32];
+  __shared__ double sm[3][kBlock / 32];
   __shared__ int bad_s;
   if (threadIdx.x == 0) bad_s = 0;
   __syncthreads();
   long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
-  double best = INFINITY;
+  double mx[3] = {0.0, 0.0, 0.0};
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
   if (t < na) {
     int i = L.G + (int)(t % L.n[0]);
     int j = L.G + (int)((t / L.n[0]) % L.n[1]);
     int k = L.G + (int)(t / ((long long)L.n[0] * L.n[1]));
     int c = (k * L.s[1] + j) * L.s[0] + i;
-    double rho = rho0 + (double)((const T*)L.q[F_RHO])[c];
-    double e = e0 + (double)((const T*)L.q[F_E])[c];
-    const double Vb[3] = {V0, V1, V2};
-    if (!(rho > 0.0) || !(e > 0.0)) bad_s = 1;
+    // per-cell arithmetic in the state's type (an FP32 state gives FP32 sound
+    // speeds); the maxima, the minimum over levels and dt itself are FP64
+    T rho = (T)rho0 + ((const T*)L.q[F_RHO])[c];
+    T e = (T)e0 + ((const T*)L.q[F_E])[c];
+    if (!(rho > T(0)) || !(e > T(0))) bad_s = 1;
     if (hydro) {
-      double cs = sqrt(gg * e / rho);
+      T cs = sqrt((T)gg * e / rho);
+      const T Vb[3] = {(T)V0, (T)V1, (T)V2};
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const T* v = (const T*)L.q[F_VX + d];
-        double v0 = fabs(Vb[d] + (double)v[c]), v1 = fabs(Vb[d] + (double)v[c + L.st[d]]);
-        double vm = v0 > v1 ? v0 : v1;
-        double tt = cfl * L.dx[d] / (cs + vm);
-        if (tt < best) best = tt;
+        T v0 = fabs(Vb[d] + v[c]), v1 = fabs(Vb[d] + v[c + L.st[d]]);
+        mx[d] = (double)(cs + (v0 > v1 ? v0 : v1));
       }
     }
   }
-  best = warp_min(best);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double v = warp_max(mx[d]);
+    if ((threadIdx.x & 31) == 0) sm[d][threadIdx.x >> 5] = v;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
-    double v = threadIdx.x < kBlock / 32 ? sm[threadIdx.x] : INFINITY;
-    v = warp_min(v);
-    if (threadIdx.x == 0) {
-      // positive doubles order like their bit patterns; +inf is the largest
-      if (v < INFINITY) atomicMin(&ds->dtmin[level], (unsigned long long)__double_as_longlong(v));
-      if (bad_s) atomicOr(&ds->unhealthy, 1);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double v = threadIdx.x < kBlock / 32 ? sm[d][threadIdx.x] : 0.0;
+      v = warp_max(v);
+      // non-negative doubles order like their bit patterns (NaN is caught above)
+      if (threadIdx.x == 0 && v > 0.0)
+        atomicMax(&ds->dtmin[3 * level + d], (unsigned long long)__double_as_longlong(v));
     }
+    if (threadIdx.x == 0 && bad_s) atomicOr(&ds->unhealthy, 1);
   }
 }
 
 struct DtFinal {
   double prod[16];
   double diff_lim[16];
+  double cfl_dx[16][3];
 };
 
+// Eq. 55: dt = min_l dt_l prod_{m<l} xi_m; resets the per-level maxima
 __global__ void k_dt_finalize(DevScalars* ds, int n_levels, DtFinal fin, double dt_fixed) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double dt = INFINITY;
   for (int l = 0; l < n_levels; ++l) {
-    unsigned long long bits = ds->dtmin[l];
-    double lim = __longlong_as_double((long long)bits);
-    if (fin.diff_lim[l] < lim) lim = fin.diff_lim[l];
+    double lim = fin.diff_lim[l];
+    for (int d = 0; d < 3; ++d) {
+      double mx = __longlong_as_double((long long)ds->dtmin[3 * l + d]);
+      double t = fin.cfl_dx[l][d] / mx;  // +inf when the maximum is 0
+      if (t < lim) lim = t;
+      ds->dtmin[3 * l + d] = 0ull;
+    }
+    ds->dtlev[l] = lim;
     double t = lim * fin.prod[l];
     if (t < dt) dt = t;
-    ds->dtmin[l] = (unsigned long long)__double_as_longlong(INFINITY);
   }
   if (dt_fixed > 0.0) dt = dt_fixed;
   ds->dt = dt;
+  // level steps take dt / prod_{m<l} xi_m (a power of two: exact)
+  for (int l = 0; l < n_levels; ++l) {
+    double dl = dt / fin.prod[l];
+    ds->dtl[l] = dl;
+    ds->dtf[l] = (float)dl;
+  }
 }
 
 __global__ void k_time_advance(DevScalars* ds) {
@@ -730,53 +799,64 @@ __global__ void k_time_advance(DevScalars* ds) {
 }
 
 // ------------------------------------------------------------------ force
+// Eq. 18 on one level: F += (rho - rho0) w_c r_c over uncovered active cells, with
+// the static weight w_c = GM V_c / (r^2 + eps^2)^(3/2) precomputed in FP64.  Each
+// thread accumulates kForceCells cells (strided by the block size), then a fixed
+// warp-shuffle tree and the 8 warp sums give one partial per block.
+constexpr int kForceCells = 4;
+
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_force_level(LevelView L, double GM, double eps,
-                                                        double rho0, double* partials) {
-  __shared__ double sx[kBlock], sy[kBlock], sz[kBlock];
-  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+__global__ void __launch_bounds__(kBlock) k_force_level(LevelView L, const double* __restrict__ fw,
+                                                        double* partials) {
+  __shared__ double sw[3][kBlock / 32];
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
-  double fx = 0.0, fy = 0.0, fz = 0.0;
-  if (t < na) {
+  double f[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int u = 0; u < kForceCells; ++u) {
+    long long t = (long long)blockIdx.x * kBlock * kForceCells + u * kBlock + threadIdx.x;
+    if (t >= na) break;
     int ai = (int)(t % L.n[0]);
     int aj = (int)((t / L.n[0]) % L.n[1]);
     int ak = (int)(t / ((long long)L.n[0] * L.n[1]));
-    bool covered = false;
-    if (L.has_child)
-      covered = ai >= L.coff[0] && ai < L.coff[0] + (L.cn[0] >> 1) && aj >= L.coff[1] &&
-                aj < L.coff[1] + (L.cn[1] >> 1) && ak >= L.coff[2] &&
-                ak < L.coff[2] + (L.cn[2] >> 1);
-    if (!covered) {
-      int c = ((L.G + ak) * L.s[1] + L.G + aj) * L.s[0] + L.G + ai;
-      double x = L.lo[0] + (ai + 0.5) * L.dx[0];
-      double y = L.lo[1] + (aj + 0.5) * L.dx[1];
-      double z = L.lo[2] + (ak + 0.5) * L.dx[2];
-      double r2 = x * x + y * y + z * z + eps * eps;
-      double inv3 = 1.0 / (r2 * sqrt(r2));
-      double m = (double)((const T*)L.q[F_RHO])[c] * L.vol;  // (rho - rho0) V_c
-      (void)rho0;
-      fx = GM * m * x * inv3;
-      fy = GM * m * y * inv3;
-      fz = GM * m * z * inv3;
-    }
+    bool covered = L.has_child && ai >= L.coff[0] && ai < L.coff[0] + (L.cn[0] >> 1) &&
+                   aj >= L.coff[1] && aj < L.coff[1] + (L.cn[1] >> 1) && ak >= L.coff[2] &&
+                   ak < L.coff[2] + (L.cn[2] >> 1);
+    if (covered) continue;
+    int c = ((L.G + ak) * L.s[1] + L.G + aj) * L.s[0] + L.G + ai;
+    double mw = (double)((const T*)L.q[F_RHO])[c] * fw[t];
+    f[0] += mw * (L.lo[0] + (ai + 0.5) * L.dx[0]);
+    f[1] += mw * (L.lo[1] + (aj + 0.5) * L.dx[1]);
+    f[2] += mw * (L.lo[2] + (ak + 0.5) * L.dx[2]);
   }
-  sx[threadIdx.x] = fx;
-  sy[threadIdx.x] = fy;
-  sz[threadIdx.x] = fz;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) f[d] += __shfl_down_sync(0xffffffffu, f[d], o);
+    if ((threadIdx.x & 31) == 0) sw[d][threadIdx.x >> 5] = f[d];
+  }
   __syncthreads();
-  for (int w = kBlock / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      sx[threadIdx.x] += sx[threadIdx.x + w];
-      sy[threadIdx.x] += sy[threadIdx.x + w];
-      sz[threadIdx.x] += sz[threadIdx.x + w];
-    }
-    __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) s += sw[threadIdx.x][w];
+    partials[3 * blockIdx.x + threadIdx.x] = s;
   }
-  if (threadIdx.x == 0) {
-    partials[3 * blockIdx.x + 0] = sx[0];
-    partials[3 * blockIdx.x + 1] = sy[0];
-    partials[3 * blockIdx.x + 2] = sz[0];
-  }
+}
+
+// static force weights of the active cells
+__global__ void __launch_bounds__(kBlock) k_force_weights(LevelView L, double GM, double eps,
+                                                          double* fw) {
+  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  if (t >= na) return;
+  int ai = (int)(t % L.n[0]);
+  int aj = (int)((t / L.n[0]) % L.n[1]);
+  int ak = (int)(t / ((long long)L.n[0] * L.n[1]));
+  double x = L.lo[0] + (ai + 0.5) * L.dx[0];
+  double y = L.lo[1] + (aj + 0.5) * L.dx[1];
+  double z = L.lo[2] + (ak + 0.5) * L.dx[2];
+  double r2 = x * x + y * y + z * z + eps * eps;
+  fw[t] = GM * L.vol / (r2 * sqrt(r2));
 }
 
 // fixed-order compensated (Neumaier) sum of the block partials, one warp per component
@@ -942,31 +1022,54 @@ __global__ void __launch_bounds__(kBlock) k_unpack(LevelView L, int field, const
   q[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G] = (T)(in[t] - bgv);
 }
 
+// hdiv versus IEEE division on the given operands: max |error| in ulps of the IEEE
+// quotient (as a double), over n pairs
+__global__ void k_hdiv_check(const double* a, const double* b, int n, double* max_ulp) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double u = 0.0;
+  if (t < n) {
+    double q = a[t] / b[t];
+    double h = hdiv(a[t], b[t]);
+    double aq = fabs(q);
+    double ulp = __longlong_as_double(__double_as_longlong(aq) + 1) - aq;
+    u = q == h ? 0.0 : fabs(h - q) / ulp;
+  }
+  for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
+  if ((threadIdx.x & 31) == 0 && u > 0.0)
+    atomicMax((unsigned long long*)max_ulp, (unsigned long long)__double_as_longlong(u));
+}
+
 }  // namespace
+
+int launch_hdiv_check(const double* a, const double* b, int n, double* max_ulp, cudaStream_t st) {
+  k_hdiv_check<<<(n + 255) / 256, 256, 0, st>>>(a, b, n, max_ulp);
+  return 1;
+}
 
 // =================================================================== launchers
 
 template <class T>
-int launch_source(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
-                  double hscale, int write_pi, double gm1, const Phys& P, cudaStream_t st) {
-  k_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, hscale, write_pi, (T)gm1,
-                                                       make_bg<T>(P));
+int launch_source(const LevelView& L, const Box& b, const Scratch& S, const T* dt, int write_pi,
+                  double gm1, const Phys& P, cudaStream_t st) {
+  k_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, write_pi, (T)gm1,
+                                                       make_bg<T>(P), make_geo<T>(L));
   return 1;
 }
 
 template <class T>
-int launch_compress_lum(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
+int launch_compress_lum(const LevelView& L, const Box& b, const Scratch& S, const T* dt,
                         const Phys& P, int do_ss3, int do_lum, int do_eps, cudaStream_t st) {
   k_compress_lum<T><<<grid_for(b.count()), kBlock, 0, st>>>(
-      L, b, S, dt, (T)(P.gamma - 1.0), (T)P.L, do_ss3, do_lum, do_eps, make_bg<T>(P));
+      L, b, S, dt, (T)(P.gamma - 1.0), (T)P.L, do_ss3, do_lum, do_eps, make_bg<T>(P),
+      make_geo<T>(L));
   return 1;
 }
 
 template <class T>
-int launch_diffuse(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
+int launch_diffuse(const LevelView& L, const Box& b, const Scratch& S, const T* dt,
                    const Phys& P, cudaStream_t st) {
   k_diffuse<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, (T)P.chi, (T)P.rho0,
-                                                        P.diff_face_rho);
+                                                        P.diff_face_rho, make_geo<T>(L));
   return 1;
 }
 
@@ -981,10 +1084,10 @@ static long long slots_total(const LevelView& L, int sides_lo, int n_sides) {
 }
 
 template <class T>
-int launch_frontier_diff(const LevelView& L, const Scratch& S, const double* dt, const Phys& P,
+int launch_frontier_diff(const LevelView& L, const Scratch& S, const T* dt, const Phys& P,
                          cudaStream_t st) {
   k_frontier_diff<T><<<grid_for(slots_total(L, 0, 6)), kBlock, 0, st>>>(
-      L, S, dt, (T)P.chi, (T)P.rho0, P.diff_face_rho);
+      L, S, dt, (T)P.chi, (T)P.rho0, P.diff_face_rho, make_geo<T>(L));
   return 1;
 }
 
@@ -996,9 +1099,14 @@ int launch_tprep(const LevelView& L, const Box& b, const Scratch& S, const Phys&
 }
 
 template <class T>
-int launch_tflux(const LevelView& L, const Box& b, const Scratch& S, int d, const double* dt,
+int launch_tflux(const LevelView& L, const Box& b, const Scratch& S, int d, const T* dt,
                  const Phys& P, cudaStream_t st) {
-  k_tflux<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d, dt, make_bg<T>(P));
+  unsigned gr = grid_for(b.count());
+  Bg<T> bg = make_bg<T>(P);
+  Geo<T> g = make_geo<T>(L);
+  if (d == 0) k_tflux<T, 0><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
+  if (d == 1) k_tflux<T, 1><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
+  if (d == 2) k_tflux<T, 2><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
   return 1;
 }
 
@@ -1009,23 +1117,32 @@ int launch_tfrontier(const LevelView& L, const Scratch& S, int d, cudaStream_t s
 }
 
 template <class T>
-int launch_tmom(const LevelView& L, const Box& b, const Scratch& S, int d, const double* dt,
+int launch_tmom(const LevelView& L, const Box& b, const Scratch& S, int d, const T* dt,
                 const Phys& P, cudaStream_t st) {
-  k_tmom<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d, dt, make_bg<T>(P));
+  unsigned gr = grid_for(b.count());
+  Bg<T> bg = make_bg<T>(P);
+  Geo<T> g = make_geo<T>(L);
+  if (d == 0) k_tmom<T, 0><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
+  if (d == 1) k_tmom<T, 1><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
+  if (d == 2) k_tmom<T, 2><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
   return 1;
 }
 
 template <class T>
 int launch_tupdate(const LevelView& L, const Box& b, const Scratch& S, int d, cudaStream_t st) {
-  k_tupdate<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, d);
+  unsigned gr = grid_for(b.count());
+  Geo<T> g = make_geo<T>(L);
+  if (d == 0) k_tupdate<T, 0><<<gr, kBlock, 0, st>>>(L, b, S, g);
+  if (d == 1) k_tupdate<T, 1><<<gr, kBlock, 0, st>>>(L, b, S, g);
+  if (d == 2) k_tupdate<T, 2><<<gr, kBlock, 0, st>>>(L, b, S, g);
   return 1;
 }
 
 template <class T>
-int launch_vrec_source(const LevelView& L, const Box& b, const Scratch& S, const double* dt,
-                       double hscale, double gm1, const Phys& P, cudaStream_t st) {
-  k_vrec_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, hscale, (T)gm1,
-                                                            make_bg<T>(P));
+int launch_vrec_source(const LevelView& L, const Box& b, const Scratch& S, const T* dt,
+                       double gm1, const Phys& P, cudaStream_t st) {
+  k_vrec_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, (T)gm1, make_bg<T>(P),
+                                                            make_geo<T>(L));
   return 1;
 }
 
@@ -1061,7 +1178,7 @@ template <class T>
 int launch_dt_level(const LevelView& L, int level, const Phys& P, DevScalars* ds,
                     cudaStream_t st) {
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
-  k_dt_level<T><<<grid_for(na), kBlock, 0, st>>>(L, level, P.gamma * (P.gamma - 1.0), P.cfl,
+  k_dt_level<T><<<grid_for(na), kBlock, 0, st>>>(L, level, P.gamma * (P.gamma - 1.0),
                                                   P.hydro_on, ds, P.rho0, P.e0, P.V[0], P.V[1],
                                                   P.V[2]);
   return 1;
@@ -1069,11 +1186,12 @@ int launch_dt_level(const LevelView& L, int level, const Phys& P, DevScalars* ds
 
 int launch_dt_finalize(DevScalars* ds, int n_levels, const double* prod, double dt_fixed,
                        cudaStream_t st) {
-  // prod[0..n) then diffusion limits [n..2n)
+  // prod[0..n) xi products, [n..2n) diffusion limits, [2n..5n) cfl*dx per axis
   DtFinal fin;
   for (int l = 0; l < 16; ++l) {
     fin.prod[l] = l < n_levels ? prod[l] : 1.0;
     fin.diff_lim[l] = l < n_levels ? prod[n_levels + l] : INFINITY;
+    for (int d = 0; d < 3; ++d) fin.cfl_dx[l][d] = l < n_levels ? prod[2 * n_levels + 3 * l + d] : 0.0;
   }
   k_dt_finalize<<<1, 32, 0, st>>>(ds, n_levels, fin, dt_fixed);
   return 1;
@@ -1081,14 +1199,20 @@ int launch_dt_finalize(DevScalars* ds, int n_levels, const double* prod, double 
 
 int force_partials_per_level(const LevelView& L) {
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
-  return (int)grid_for(na);
+  return (int)((na + kBlock * kForceCells - 1) / (kBlock * kForceCells));
 }
 
 template <class T>
 int launch_force_level(const LevelView& L, const Phys& P, double* partials, int offset,
                        cudaStream_t st) {
-  k_force_level<T><<<force_partials_per_level(L), kBlock, 0, st>>>(L, P.GM, P.eps, P.rho0,
-                                                                   partials + 3 * offset);
+  (void)P;
+  k_force_level<T><<<force_partials_per_level(L), kBlock, 0, st>>>(L, L.fw, partials + 3 * offset);
+  return 1;
+}
+
+int launch_force_weights(const LevelView& L, const Phys& P, cudaStream_t st) {
+  k_force_weights<<<grid_for((long long)L.n[0] * L.n[1] * L.n[2]), kBlock, 0, st>>>(L, P.GM, P.eps,
+                                                                                   L.fw);
   return 1;
 }
 
@@ -1150,25 +1274,25 @@ int launch_unpack_active(const LevelView& L, int field, const double* in, int fu
 }
 
 #define DFN_INSTANTIATE(T)                                                                     \
-  template int launch_source<T>(const LevelView&, const Box&, const Scratch&, const double*,   \
-                                double, int, double, const Phys&, cudaStream_t);               \
-  template int launch_compress_lum<T>(const LevelView&, const Box&, const Scratch&,            \
-                                      const double*, const Phys&, int, int, int, cudaStream_t); \
-  template int launch_diffuse<T>(const LevelView&, const Box&, const Scratch&, const double*,  \
+  template int launch_source<T>(const LevelView&, const Box&, const Scratch&, const T*, int,    \
+                                double, const Phys&, cudaStream_t);                            \
+  template int launch_compress_lum<T>(const LevelView&, const Box&, const Scratch&, const T*,  \
+                                      const Phys&, int, int, int, cudaStream_t);               \
+  template int launch_diffuse<T>(const LevelView&, const Box&, const Scratch&, const T*,       \
                                  const Phys&, cudaStream_t);                                   \
-  template int launch_frontier_diff<T>(const LevelView&, const Scratch&, const double*,        \
+  template int launch_frontier_diff<T>(const LevelView&, const Scratch&, const T*,             \
                                        const Phys&, cudaStream_t);                             \
   template int launch_tprep<T>(const LevelView&, const Box&, const Scratch&, const Phys&,      \
                                cudaStream_t);                                                  \
-  template int launch_tflux<T>(const LevelView&, const Box&, const Scratch&, int, const double*, \
+  template int launch_tflux<T>(const LevelView&, const Box&, const Scratch&, int, const T*,    \
                                const Phys&, cudaStream_t);                                     \
   template int launch_tfrontier<T>(const LevelView&, const Scratch&, int, cudaStream_t);       \
-  template int launch_tmom<T>(const LevelView&, const Box&, const Scratch&, int, const double*, \
+  template int launch_tmom<T>(const LevelView&, const Box&, const Scratch&, int, const T*,     \
                               const Phys&, cudaStream_t);                                      \
   template int launch_tupdate<T>(const LevelView&, const Box&, const Scratch&, int,            \
                                  cudaStream_t);                                                \
-  template int launch_vrec_source<T>(const LevelView&, const Box&, const Scratch&,             \
-                                     const double*, double, double, const Phys&, cudaStream_t); \
+  template int launch_vrec_source<T>(const LevelView&, const Box&, const Scratch&, const T*,   \
+                                     double, const Phys&, cudaStream_t);                       \
   template int launch_bc_fill<T>(const LevelView&, const Phys&, cudaStream_t);                 \
   template int launch_commup<T>(const LevelView&, const LevelView&, cudaStream_t);             \
   template int launch_commmean<T>(const LevelView&, const LevelView&, int, cudaStream_t);      \

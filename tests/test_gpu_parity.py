@@ -275,3 +275,15 @@ def test_fp32_state_close_to_fp64():
     F64 = s64.force()[0]
     F32 = s32.force()[0]
     assert np.abs(F32 - F64).max() <= 1e-3 * np.abs(F64).max(), (F32, F64)
+
+
+def test_hot_path_division_within_one_ulp():
+    """The FP64 division of the stencil kernels (Newton-Raphson on the hardware
+    reciprocal estimate) against IEEE division, over the operand ranges it meets:
+    densities near 1, 1 + a, and sums of same-signed slopes over many decades."""
+    rng = np.random.default_rng(17)
+    n = 1 << 20
+    b = np.concatenate([1.0 + 0.3 * rng.standard_normal(n // 2),
+                        np.exp(rng.uniform(-300, 300, n // 2)) * rng.choice([-1, 1], n // 2)])
+    a = rng.standard_normal(n) * np.exp(rng.uniform(-30, 30, n))
+    assert binding.check_division(a, b) <= 1.0
