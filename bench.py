@@ -208,18 +208,116 @@ def run_reference(args, cfg):
     return 0
 
 
+def run_batched(args):
+    """64 uneven runs in one pool (FP32 state, FP64 reductions), one coarse step of
+    every run per step; tiles picked by the pool's autotuner."""
+    import torch
+
+    from paper_1812_03191_gb300 import binding
+    runs = I.batched()
+    cu = sum(r["n"] ** 3 * (2 ** r["n_levels"] - 1) for r in runs)
+    if args.impl == "reference":
+        return 0
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t_e2e0 = time.perf_counter()
+    pool = binding.Pool(64 << 30, precision=binding.DF_FP32_STATE, stream=stream.cuda_stream)
+    for r in runs:
+        pool.admit(r["n_levels"], r["n"], r["lo"], r["hi"], r["G"], r["params"])
+    t_admit = time.perf_counter() - t_e2e0
+    tiles = pool.autotune()
+    for _ in range(args.warmup):
+        pool.step(1)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    l0 = pool.info()["launches"]
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            pool.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = pool.info()["launches"] - l0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    value = cu * args.steps / (ms / 1e3)
+    # per-kernel times (events around every launch) over the same number of steps
+    pool.set_timing(True)
+    for _ in range(args.steps):
+        pool.step(1)
+    kinds = {}
+    for kind in range(binding.KERNEL_KINDS):
+        kms, kn = pool.kernel_time(kind)
+        if kn:
+            kinds[binding.kernel_name(kind)] = (kms, kn)
+    pool.set_timing(False)
+    total_k = sum(v[0] for v in kinds.values())
+    dom = max((k for k in kinds if k in ARRAYS_PER_ELEM), key=lambda k: kinds[k][0])
+    # algorithmic bytes of all launches of that kind in one step, from the runs' boxes
+    esz = 4
+    per_step_bytes = 0.0
+    for r in runs:
+        boxes = level_step_boxes(dict(n=r["n"], G=r["G"], n_levels=r["n_levels"]))
+        mult = 3 if dom in ("tprep", "tflux", "tmom", "tupdate") else 1
+        per_step_bytes += ARRAYS_PER_ELEM[dom] * esz * sum(boxes) * mult
+    dom_ms, dom_n = kinds[dom]
+    achieved = per_step_bytes * args.steps / (dom_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    # e2e: admission from host parameters, K steps, forces read back every step
+    t0 = time.perf_counter()
+    pool2 = binding.Pool(64 << 30, precision=binding.DF_FP32_STATE, stream=stream.cuda_stream)
+    for r in runs:
+        pool2.admit(r["n_levels"], r["n"], r["lo"], r["hi"], r["G"], r["params"])
+    pool2.set_tiles(tiles)
+    for _ in range(args.steps):
+        pool2.step(1)
+        pool2.query()
+    e2e_s = time.perf_counter() - t0
+    q = pool.query()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-state/f64-reductions",
+        "data": "synthetic",
+        "config": {"workload": "batched_64_runs", "runs": len(runs), "levels": "2..4",
+                   "mesh": "{32,48,64,96}^3", "cell_updates_per_step": cu,
+                   "l2": "flushed between timed steps; working set 5.6 GB",
+                   "tiles_blocks_per_sm": tiles, "admission_s": t_admit},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_kind, "launches_timed": dom_n,
+                     "share_of_kernel_time": dom_ms / total_k},
+        "cpu_baseline": None,
+        "e2e": {"value": cu * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 6 * 8 * len(runs),
+                "note": "admission of the 64 runs from host parameters included"},
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kinds.items(), key=lambda x: -x[1][0])},
+        "unhealthy_runs": int(np.nansum(q[:, 5])),
+    }
+    print(json.dumps(line), flush=True)
+    pool.close()
+    pool2.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nested", choices=["nested", "single", "precision"])
+    ap.add_argument("--workload", default="nested",
+                    choices=["nested", "single", "precision", "batched"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "batched":
+        return run_batched(args)
     cfg = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, cfg)

@@ -187,6 +187,60 @@ int df_force_level_noalloc(const double* rho, const int n[3], int G, const doubl
                            const double dx[3], const int child_off[3], const int child_n[3],
                            double GM, double eps, double rho0, double* F_out, void* stream);
 
+/* ---- Batched runs (pools).  A pool holds many independent hierarchies ("runs",
+ * e.g. a parameter sweep or a stream of simulation requests) on one GPU and
+ * advances all of them together: one coarse step of every run is one sequence of
+ * persistent work-list launches, each carrying the same operator (Sec. 3.3 level
+ * step, CommUp, CommMean, Eq. 55 and Eq. 18 reductions) for every run that has it
+ * next, captured once into a CUDA graph.  Runs may differ in level count, mesh
+ * size and physics; every run sub-cycles with xi = 2 and takes its own time step. */
+typedef struct df_pool df_pool;
+
+/* Device bytes one run of this shape holds (the pool's admission measure). */
+size_t df_run_bytes(int n_levels, const int n[3], int G, int precision);
+
+/* Create an empty pool that admits runs while their bytes stay within
+ * hbm_budget_bytes.  precision as in df_create (one precision per pool). */
+int df_pool_create(df_pool** out, size_t hbm_budget_bytes, int precision, int device,
+                   void* stream);
+
+/* Admit one run (arguments as df_create + df_set_params); returns its slot.
+ * DF_EBUSY when the budget would be exceeded (nothing is allocated then);
+ * DF_EINVAL for bad shapes or parameters (xi_mode must be 0). */
+int df_pool_admit(df_pool* pool, int n_levels, const int n[3], const double lo[3],
+                  const double hi[3], int G, const df_params* p, int* slot_out);
+
+/* Free a run's slot and memory (synchronises the pool's stream first). */
+int df_pool_release(df_pool* pool, int slot);
+
+/* Advance every admitted run by n coarse steps (asynchronous). */
+int df_pool_step(df_pool* pool, int n_coarse_steps);
+
+/* Synchronise, then write 6 doubles per slot (slots 0..max_slots-1): F_x, F_y,
+ * F_z of the last coarse step, t, the last coarse dt, and the health flag (NaN for
+ * empty slots).  Returns the number of slots written. */
+int df_pool_query(df_pool* pool, double* out, int max_slots);
+
+/* Active cells of one field of one level of a slot's run, FP64 (as df_get_field). */
+int df_pool_get_field(df_pool* pool, int slot, int level, int field, double* host_out);
+
+/* Active runs, bytes in use, the budget, kernels launched so far. */
+int df_pool_info(df_pool* pool, int* active, size_t* used, size_t* budget, long long* launches);
+
+/* Tile (grid) shape of the work-list launches: persistent blocks per SM for each
+ * of the DF_POOL_OPS operators.  df_pool_autotune times every operator of one
+ * coarse step of the current runs for 1..32 blocks per SM, keeps the fastest per
+ * operator (written to blocks_per_sm_out, nullable) and restores the runs' state. */
+#define DF_POOL_OPS 19
+int df_pool_set_tiles(df_pool* pool, const int* blocks_per_sm);
+int df_pool_autotune(df_pool* pool, int* blocks_per_sm_out);
+
+/* Timing hook of a pool (as df_set_timing / df_kernel_time). */
+int df_pool_set_timing(df_pool* pool, int on);
+int df_pool_kernel_time(df_pool* pool, int kind, double* ms, long long* launches);
+
+int df_pool_destroy(df_pool* pool);
+
 /* Eq. 55-56 (Appendix A): brute force over xi in {1,2}^(n-1), maximising dt/C. */
 int df_xi_search(int n, const double* dt_level, const double* cost, int* xi_out, double* ratio);
 

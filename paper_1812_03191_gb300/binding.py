@@ -26,7 +26,11 @@ EXPORTS = (
     "df_fill_bc", "df_kernel_launches", "df_set_timing", "df_kernel_time", "df_kernel_name",
     "df_debug_full_boxes", "df_destroy", "df_xi_search", "df_last_error",
     "df_force_level_noalloc", "df_check_division",
+    "df_run_bytes", "df_pool_create", "df_pool_admit", "df_pool_release", "df_pool_step",
+    "df_pool_query", "df_pool_get_field", "df_pool_info", "df_pool_set_tiles",
+    "df_pool_autotune", "df_pool_destroy", "df_pool_set_timing", "df_pool_kernel_time",
 )
+POOL_OPS = 19
 NOALLOC_MAX_CELLS = 4194304
 
 
@@ -98,6 +102,21 @@ def load(path: str = LIB_PATH):
         "df_xi_search": (C.c_int, [C.c_int, dp, dp, P(C.c_int), dp]),
         "df_last_error": (C.c_char_p, []),
         "df_check_division": (C.c_int, [dp, dp, C.c_int, dp]),
+        "df_run_bytes": (C.c_size_t, [C.c_int, P(C.c_int), C.c_int, C.c_int]),
+        "df_pool_create": (C.c_int, [P(vp), C.c_size_t, C.c_int, C.c_int, vp]),
+        "df_pool_admit": (C.c_int, [vp, C.c_int, P(C.c_int), dp, dp, C.c_int, P(Params),
+                                    P(C.c_int)]),
+        "df_pool_release": (C.c_int, [vp, C.c_int]),
+        "df_pool_step": (C.c_int, [vp, C.c_int]),
+        "df_pool_query": (C.c_int, [vp, dp, C.c_int]),
+        "df_pool_get_field": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, dp]),
+        "df_pool_info": (C.c_int, [vp, P(C.c_int), P(C.c_size_t), P(C.c_size_t),
+                                   P(C.c_longlong)]),
+        "df_pool_set_tiles": (C.c_int, [vp, P(C.c_int)]),
+        "df_pool_autotune": (C.c_int, [vp, P(C.c_int)]),
+        "df_pool_destroy": (C.c_int, [vp]),
+        "df_pool_set_timing": (C.c_int, [vp, C.c_int]),
+        "df_pool_kernel_time": (C.c_int, [vp, C.c_int, dp, P(C.c_longlong)]),
         "df_force_level_noalloc": (C.c_int, [vp, P(C.c_int), C.c_int, dp, dp, P(C.c_int),
                                              P(C.c_int), C.c_double, C.c_double, C.c_double,
                                              vp, vp]),
@@ -299,3 +318,94 @@ class Sim:
 
     def debug_full_boxes(self, on):
         _check(self.lib.df_debug_full_boxes(self.h, 1 if on else 0))
+
+
+def run_bytes(n_levels, n, G, precision=DF_FP64):
+    if isinstance(n, int):
+        n = (n, n, n)
+    return int(load().df_run_bytes(n_levels, (C.c_int * 3)(*n), G, precision))
+
+
+class Pool:
+    """Many independent runs stepped together on one GPU (a df_pool)."""
+
+    def __init__(self, budget_bytes, precision=DF_FP64, device=0, stream=None):
+        lib = load()
+        self.lib = lib
+        self.precision = precision
+        h = C.c_void_p()
+        _check(lib.df_pool_create(C.byref(h), int(budget_bytes), precision, device,
+                                  C.c_void_p(stream) if stream else None))
+        self.h = h
+        self.shapes = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.df_pool_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def admit(self, n_levels, n, lo, hi, G, params: dict):
+        """slot index, or None when the HBM budget is full"""
+        if isinstance(n, int):
+            n = (n, n, n)
+        slot = C.c_int()
+        rc = self.lib.df_pool_admit(self.h, int(n_levels), (C.c_int * 3)(*n),
+                                    (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), int(G),
+                                    C.byref(Params.from_dict(params)), C.byref(slot))
+        if rc == DF_EBUSY:
+            return None
+        _check(rc)
+        self.shapes[slot.value] = (int(n_levels), tuple(n))
+        return slot.value
+
+    def release(self, slot):
+        _check(self.lib.df_pool_release(self.h, int(slot)))
+        self.shapes.pop(slot, None)
+
+    def step(self, n=1):
+        _check(self.lib.df_pool_step(self.h, int(n)))
+
+    def query(self, max_slots=4096):
+        """array (slots, 6): F_x, F_y, F_z, t, dt, unhealthy (NaN rows for empty slots)"""
+        out = np.empty(6 * max_slots)
+        ns = self.lib.df_pool_query(self.h, _dp(out), max_slots)
+        if ns < 0:
+            _check(ns)
+        return out[:6 * ns].reshape(ns, 6)
+
+    def get_field(self, slot, level, field):
+        nl, n = self.shapes[slot]
+        out = np.empty(n[0] * n[1] * n[2])
+        _check(self.lib.df_pool_get_field(self.h, int(slot), level, field, _dp(out)))
+        return out.reshape(n[2], n[1], n[0])
+
+    def info(self):
+        a, used, budget, launches = C.c_int(), C.c_size_t(), C.c_size_t(), C.c_longlong()
+        _check(self.lib.df_pool_info(self.h, C.byref(a), C.byref(used), C.byref(budget),
+                                     C.byref(launches)))
+        return dict(active=a.value, used=used.value, budget=budget.value,
+                    launches=launches.value)
+
+    def autotune(self):
+        out = (C.c_int * POOL_OPS)()
+        _check(self.lib.df_pool_autotune(self.h, out))
+        return list(out)
+
+    def set_timing(self, on):
+        _check(self.lib.df_pool_set_timing(self.h, 1 if on else 0))
+
+    def kernel_time(self, kind):
+        ms = C.c_double()
+        n = C.c_longlong()
+        _check(self.lib.df_pool_kernel_time(self.h, kind, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def set_tiles(self, blocks_per_sm):
+        arr = (C.c_int * POOL_OPS)(*blocks_per_sm)
+        _check(self.lib.df_pool_set_tiles(self.h, arr))

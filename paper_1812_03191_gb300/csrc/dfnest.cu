@@ -1,11 +1,17 @@
 // dfnest.cu -- host runtime and C ABI of libdfnest.so (see include/dfnest.h).
 //
-// The hierarchy of Sec. 3 lives on one GPU: one padded allocation per field per
-// level, one scratch set shared by all levels (they are advanced one at a time),
-// device scalars for the time step, time, force and health flag.  One coarse step
-// (Eq. 55 time step, the Sec. 3.3 recursion, the Eq. 18 force) is issued as a
-// fixed launch sequence that is captured once into a CUDA graph and replayed; the
-// time step is read by the kernels from device memory, so nothing syncs the host.
+// A *run* is one hierarchy of Sec. 3 resident on one GPU: one padded allocation of
+// 7 planes per level (5 fields, potential, luminosity weights), a scratch set
+// shared by its levels (they are advanced one at a time), frontier slabs, force
+// weights, and device scalars (time step, time, force, health flag).
+//
+// A *plan* is the launch list of one coarse step of a set of runs: the Eq. 55 time
+// step, the recursion of Sec. 3.3 and the Eq. 18 force of every run, as work items
+// of the persistent work-list kernel (kernels.cu).  The op lists of the runs are
+// merged so that one launch carries the same op for every run that has it next;
+// the plan is uploaded once and captured into a CUDA graph, and the time step is
+// read by the kernels from device memory, so stepping never synchronises the host.
+// A context (df_ctx) is one run and its plan; a pool (df_pool) is many runs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -13,6 +19,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -40,7 +47,8 @@ int fail(int code, const char* fmt, ...) {
   do {                                                                               \
     cudaError_t e_ = (call);                                                         \
     if (e_ != cudaSuccess)                                                           \
-      return fail(DF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+      return fail(e_ == cudaErrorMemoryAllocation ? DF_ENOMEM : DF_ECUDA,            \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                   \
   } while (0)
 
 // reach of one level step in cells along any axis (measured by perturbation
@@ -66,13 +74,15 @@ int dfn::set_error(int code, const char* fmt, ...) {
   return code;
 }
 
-struct df_ctx {
-  int nl = 0, prec = 0, device = 0, G = 0;
+namespace {
+
+// ------------------------------------------------------------------------- runs
+
+struct Run {
+  int nl = 0, prec = 0, G = 0;
   int n[3] = {0, 0, 0};
-  double lo[3], hi[3];
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   size_t esz = 8;
-  cudaStream_t user = nullptr, st = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::vector<Level> L;
   Scratch S{};
   void* scratch_mem = nullptr;
@@ -84,15 +94,626 @@ struct df_ctx {
   int ring_cap = 4096;
   double* wsum = nullptr;
   double* stage = nullptr;  // device staging for field I/O
-  double* hstage = nullptr; // pinned host staging
-  size_t stage_elems = 0;
   Phys P{};
   df_params prm{};
   bool have_params = false;
+  bool stepped = false;
   int xi[DF_MAX_LEVELS];
+  size_t bytes = 0;
+};
+
+size_t plane_bytes(size_t nc, size_t esz) { return ((nc * esz + 255) / 256) * 256; }
+
+// device bytes a run of this shape allocates (admission control uses the same sum)
+size_t run_bytes(int nl, const int n[3], int G, int prec) {
+  size_t esz = prec == DF_FP64 ? 8 : 4;
+  size_t nc = 1, na = 1;
+  for (int d = 0; d < 3; ++d) {
+    nc *= (size_t)(n[d] + 2 * G);
+    na *= (size_t)n[d];
+  }
+  int slots = 0;
+  for (int d = 0; d < 3; ++d) {
+    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    slots = std::max(slots, (n[t1] / 2) * (n[t2] / 2));
+  }
+  size_t per_level = plane_bytes(nc, esz) * 7 + 18 * (size_t)slots * 8 + 3 * na * 8;
+  size_t np = (size_t)nl * ((na + 2047) / 2048);
+  size_t pel = std::max(3 * np, (na + 255) / 256);
+  return per_level * nl + plane_bytes(nc, esz) * 12 + sizeof(DevScalars) + pel * 8 +
+         3 * 4096 * 8 + 8 + 8 + nc * 8;
+}
+
+void run_free(Run* r) {
+  if (!r) return;
+  for (auto& l : r->L) {
+    cudaFree(l.mem);
+    cudaFree(l.acc);
+    cudaFree(l.v.fw);
+  }
+  cudaFree(r->scratch_mem);
+  cudaFree(r->ds);
+  cudaFree(r->partials);
+  cudaFree(r->ring);
+  cudaFree(r->ring_pos);
+  cudaFree(r->wsum);
+  cudaFree(r->stage);
+  delete r;
+}
+
+int check_shape(int n_levels, const int n[3], const double lo[3], const double hi[3], int G,
+                int precision) {
+  if (n_levels < 1 || n_levels > DF_MAX_LEVELS) return fail(DF_EINVAL, "n_levels out of range");
+  if (G < 2 || G % 2) return fail(DF_EINVAL, "G must be even and >= 2");
+  if (precision != DF_FP64 && precision != DF_FP32_STATE)
+    return fail(DF_EINVAL, "unknown precision %d", precision);
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < 8 || n[d] % 4 || n[d] < G)
+      return fail(DF_EINVAL, "n[%d]=%d: need n%%4==0, n>=8, n>=G", d, n[d]);
+    if (!(hi[d] > lo[d])) return fail(DF_EINVAL, "empty box on axis %d", d);
+  }
+  long long s3 = 1;
+  for (int d = 0; d < 3; ++d) s3 *= (n[d] + 2 * G);
+  if (s3 >= (1LL << 31) / 5) return fail(DF_EINVAL, "level too large (%lld elements)", s3);
+  // every finer level on parent faces, ghosts and CommUp stencil inside the parent
+  for (int l = 1; l < n_levels; ++l)
+    for (int d = 0; d < 3; ++d) {
+      double ps = std::ldexp(1.0, -(l - 1)), cs = std::ldexp(1.0, -l);
+      double plo = lo[d] * ps, pdx = (hi[d] - lo[d]) * ps / n[d];
+      double o = (lo[d] * cs - plo) / pdx;
+      int oi = (int)std::floor(o + 0.5);
+      if (std::fabs(o - oi) > 1e-9 || oi < G / 2 + 1 || oi + n[d] / 2 + G / 2 + 1 > n[d])
+        return fail(DF_EINVAL, "level %d: offset %.3f on axis %d must be an integer in [%d, %d]",
+                    l, o, d, G / 2 + 1, n[d] - n[d] / 2 - G / 2 - 1);
+    }
+  return DF_OK;
+}
+
+int run_create(Run** out, int n_levels, const int n[3], const double lo[3], const double hi[3],
+               int G, int precision) {
+  *out = nullptr;
+  int rc0 = check_shape(n_levels, n, lo, hi, G, precision);
+  if (rc0) return rc0;
+  Run* r = new (std::nothrow) Run;
+  if (!r) return fail(DF_ENOMEM, "host allocation");
+  r->nl = n_levels;
+  r->prec = precision;
+  r->G = G;
+  r->esz = precision == DF_FP64 ? 8 : 4;
+  for (int d = 0; d < 3; ++d) {
+    r->n[d] = n[d];
+    r->lo[d] = lo[d];
+    r->hi[d] = hi[d];
+  }
+  for (int l = 0; l < DF_MAX_LEVELS; ++l) r->xi[l] = 2;
+  r->bytes = run_bytes(n_levels, n, G, precision);
+#define CKR(call)                                                            \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      int rc_ = fail(e_ == cudaErrorMemoryAllocation ? DF_ENOMEM : DF_ECUDA, \
+                     "%s failed: %s", #call, cudaGetErrorString(e_));        \
+      run_free(r);                                                           \
+      return rc_;                                                            \
+    }                                                                        \
+  } while (0)
+  r->L.resize(n_levels);
+  size_t nc = 1, na = (size_t)n[0] * n[1] * n[2];
+  for (int d = 0; d < 3; ++d) nc *= (size_t)(n[d] + 2 * G);
+  size_t plane = plane_bytes(nc, r->esz);
+  for (int l = 0; l < n_levels; ++l) {
+    LevelView& v = r->L[l].v;
+    memset(&v, 0, sizeof v);
+    double scale = std::ldexp(1.0, -l);
+    v.G = G;
+    v.nc = (int)nc;
+    for (int d = 0; d < 3; ++d) {
+      v.n[d] = n[d];
+      v.s[d] = n[d] + 2 * G;
+      v.lo[d] = lo[d] * scale;
+      v.dx[d] = (hi[d] - lo[d]) * scale / n[d];
+    }
+    v.st[0] = 1;
+    v.st[1] = v.s[0];
+    v.st[2] = v.s[0] * v.s[1];
+    v.vol = v.dx[0] * v.dx[1] * v.dx[2];
+    v.area[0] = v.dx[1] * v.dx[2];
+    v.area[1] = v.dx[0] * v.dx[2];
+    v.area[2] = v.dx[0] * v.dx[1];
+    v.inv_vol = 1.0 / v.vol;
+    for (int d = 0; d < 3; ++d) {
+      v.inv_dx[d] = 1.0 / v.dx[d];
+      v.dcoef[d] = v.area[d] / v.dx[d];
+    }
+    v.dt_scale = scale;
+    v.is_child = l > 0;
+    if (l > 0) {
+      const LevelView& p = r->L[l - 1].v;
+      for (int d = 0; d < 3; ++d) v.off[d] = (int)std::floor((v.lo[d] - p.lo[d]) / p.dx[d] + 0.5);
+    }
+    CKR(cudaMalloc(&r->L[l].mem, plane * 7));
+    char* base = (char*)r->L[l].mem;
+    for (int f = 0; f < 5; ++f) v.q[f] = base + plane * f;
+    v.phi = base + plane * 5;
+    v.lumw = base + plane * 6;
+    int slots = 0;
+    for (int d = 0; d < 3; ++d) {
+      int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      slots = std::max(slots, (n[t1] / 2) * (n[t2] / 2));
+    }
+    v.acc_slots = slots;
+    r->L[l].acc_elems = (size_t)18 * slots;
+    CKR(cudaMalloc(&r->L[l].acc, r->L[l].acc_elems * sizeof(double)));
+    CKR(cudaMemset(r->L[l].acc, 0, r->L[l].acc_elems * sizeof(double)));
+    v.acc = r->L[l].acc;
+    CKR(cudaMalloc(&v.fw, 3 * na * sizeof(double)));
+  }
+  for (int l = 0; l + 1 < n_levels; ++l) {
+    LevelView& v = r->L[l].v;
+    const LevelView& ch = r->L[l + 1].v;
+    v.has_child = 1;
+    for (int d = 0; d < 3; ++d) {
+      v.coff[d] = ch.off[d];
+      v.cn[d] = ch.n[d];
+    }
+    v.cacc = ch.acc;
+    v.cacc_slots = ch.acc_slots;
+  }
+  CKR(cudaMalloc(&r->scratch_mem, plane * 12));
+  CKR(cudaMemset(r->scratch_mem, 0, plane * 12));
+  {
+    char* b = (char*)r->scratch_mem;
+    for (int m = 0; m < 3; ++m) r->S.pi[m] = b + plane * m;
+    r->S.eps = b + plane * 3;
+    for (int m = 0; m < 3; ++m) r->S.w[m] = b + plane * (4 + m);
+    r->S.F = b + plane * 7;
+    r->S.E = b + plane * 8;
+    for (int m = 0; m < 3; ++m) r->S.P[m] = b + plane * (9 + m);
+  }
+  CKR(cudaMalloc(&r->ds, sizeof(DevScalars)));
+  CKR(cudaMemset(r->ds, 0, sizeof(DevScalars)));
+  // partials: 3 per force block of every level, and one per 256 active cells of a
+  // level for the luminosity normalisation (the two uses never overlap in time)
+  int np = 0;
+  for (int l = 0; l < n_levels; ++l) np += force_partials_per_level(r->L[l].v);
+  r->n_partials = np;
+  size_t pelems = std::max(3 * (size_t)np, (na + 255) / 256);
+  CKR(cudaMalloc(&r->partials, pelems * sizeof(double)));
+  CKR(cudaMalloc(&r->ring, 3 * (size_t)r->ring_cap * sizeof(double)));
+  CKR(cudaMalloc(&r->ring_pos, sizeof(long long)));
+  CKR(cudaMemset(r->ring_pos, 0, sizeof(long long)));
+  CKR(cudaMalloc(&r->wsum, sizeof(double)));
+  CKR(cudaMalloc(&r->stage, nc * sizeof(double)));
+#undef CKR
+  *out = r;
+  return DF_OK;
+}
+
+int check_params(const df_params* p) {
+  if (!p) return fail(DF_EINVAL, "null params");
+  if (!(p->gamma > 1.0) || !(p->rho0 > 0.0) || !(p->cs > 0.0) || p->chi < 0.0 ||
+      !(p->cfl > 0.0) || p->band < 1 || p->mach < 0.0)
+    return fail(DF_EINVAL, "invalid physical parameters");
+  if (p->chi > 0.0 && !(p->cfl_diff > 0.0)) return fail(DF_EINVAL, "cfl_diff must be > 0");
+  for (int k = 0; k < 6; ++k)
+    if (p->bc[k] < 0 || p->bc[k] > 3) return fail(DF_EINVAL, "bad boundary type");
+  return DF_OK;
+}
+
+// parameters, uniform background state, static fields; returns kernels launched
+long long run_set_params(Run* r, const df_params* p, cudaStream_t st, int* rc) {
+  *rc = DF_OK;
+  r->prm = *p;
+  Phys& P = r->P;
+  P.gamma = p->gamma;
+  P.rho0 = p->rho0;
+  P.e0 = p->cs * p->cs * p->rho0 / (p->gamma * (p->gamma - 1.0));  // Sec. 3.4
+  for (int d = 0; d < 3; ++d) P.V[d] = p->mach * p->cs * p->flow_dir[d];
+  P.GM = p->GM;
+  P.eps = p->eps;
+  P.chi = p->chi;
+  P.L = p->L;
+  P.cfl = p->cfl;
+  P.cfl_diff = p->cfl_diff;
+  P.dt_fixed = p->dt_fixed;
+  P.diff_face_rho = p->diff_face_rho;
+  P.hydro_on = p->hydro_on;
+  P.band = p->band;
+  for (int k = 0; k < 6; ++k) P.bc[k] = p->bc[k];
+  long long n = 0;
+  for (int l = 0; l < r->nl; ++l) {
+    LevelView& v = r->L[l].v;
+    if (r->prec == DF_FP64) {
+      n += launch_init_uniform<double>(v, P, st);
+      n += launch_static_fields<double>(v, P, p->lum_sigma, r->wsum, r->partials, st);
+      if (p->lum_sigma > 0.0) n += launch_normalise_lum<double>(v, r->wsum, st);
+    } else {
+      n += launch_init_uniform<float>(v, P, st);
+      n += launch_static_fields<float>(v, P, p->lum_sigma, r->wsum, r->partials, st);
+      if (p->lum_sigma > 0.0) n += launch_normalise_lum<float>(v, r->wsum, st);
+    }
+    if (cudaMemsetAsync(r->L[l].acc, 0, r->L[l].acc_elems * sizeof(double), st) != cudaSuccess)
+      *rc = fail(DF_ECUDA, "memset");
+    n += launch_force_weights(v, P, st);
+  }
+  DevScalars h;
+  memset(&h, 0, sizeof h);  // per-axis maxima start at +0.0 (bit pattern 0)
+  if (cudaMemcpyAsync(r->ds, &h, sizeof h, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(r->ring_pos, 0, sizeof(long long), st) != cudaSuccess)
+    *rc = fail(DF_ECUDA, "scalar reset");
+  r->have_params = true;
+  r->stepped = false;
+  return n;
+}
+
+// ------------------------------------------------------------------------ plans
+
+struct LaunchDesc {
+  int op, d, kind;
+  size_t item0, start0;
+  int nitems;
+  unsigned nchunks;
+};
+
+struct Plan {
+  int prec = 0;
+  size_t item_size = 0;
+  std::vector<LaunchDesc> launches;
+  std::vector<unsigned char> items;  // host copy, item_size bytes each
+  std::vector<unsigned> starts;
+  std::vector<DtFinal> fins;
+  void* d_items = nullptr;
+  unsigned* d_starts = nullptr;
+  DtFinal* d_fins = nullptr;
+  size_t cap_items = 0, cap_starts = 0, cap_fins = 0;
   cudaGraphExec_t gexec = nullptr;
-  long long graph_kernels = 0;
-  long long launches = 0;
+  long long kernels = 0;
+  bool valid = false;
+};
+
+void plan_free(Plan& p) {
+  if (p.gexec) cudaGraphExecDestroy(p.gexec);
+  cudaFree(p.d_items);
+  cudaFree(p.d_starts);
+  cudaFree(p.d_fins);
+  p = Plan();
+}
+
+void plan_invalidate(Plan& p) {
+  if (p.gexec) {
+    cudaGraphExecDestroy(p.gexec);
+    p.gexec = nullptr;
+  }
+  p.valid = false;
+}
+
+int kind_of(int op) {
+  switch (op) {
+    case OP_BC: return K_BC;
+    case OP_SOURCE: return K_SOURCE;
+    case OP_COMPRESS: return K_COMPRESS;
+    case OP_DIFFUSE: return K_DIFFUSE;
+    case OP_FRONTIER_DIFF: return K_FRONTIER_DIFF;
+    case OP_TPREP: return K_TPREP;
+    case OP_TFLUX: return K_TFLUX;
+    case OP_TFRONTIER: return K_TFRONTIER;
+    case OP_TMOM: return K_TMOM;
+    case OP_TUPDATE: return K_TUPDATE;
+    case OP_VREC: return K_VREC_SOURCE;
+    case OP_COMMUP: return K_COMMUP;
+    case OP_COMMMEAN: return K_COMMMEAN;
+    case OP_DT_LEVEL: case OP_DT_FINAL: return K_DT;
+    case OP_FORCE_LEVEL: case OP_FORCE_FINAL: return K_FORCE;
+    default: return K_OTHER;
+  }
+}
+
+void fill_fin(const Run& r, DtFinal& fin) {
+  double pr = 1.0;
+  for (int l = 0; l < 16; ++l) {
+    fin.prod[l] = 1.0;
+    fin.diff_lim[l] = INFINITY;
+    for (int d = 0; d < 3; ++d) fin.cfl_dx[l][d] = 0.0;
+  }
+  for (int l = 0; l < r.nl; ++l) {
+    if (l > 0) pr *= r.xi[l - 1];
+    fin.prod[l] = pr;
+    const LevelView& v = r.L[l].v;
+    if (r.P.chi > 0.0) {
+      double sinv = 0.0;
+      for (int d = 0; d < 3; ++d) sinv += 1.0 / (v.dx[d] * v.dx[d]);
+      fin.diff_lim[l] = r.P.cfl_diff / (2.0 * r.P.chi * sinv);
+    }
+    for (int d = 0; d < 3; ++d) fin.cfl_dx[l][d] = r.P.hydro_on ? r.P.cfl * v.dx[d] : 0.0;
+  }
+}
+
+template <class T>
+struct Builder {
+  struct Entry {
+    int op, d;
+    Item<T> it;
+  };
+  std::vector<std::vector<Entry>> per_run;
+  int full_boxes = 0;
+  const DtFinal* d_fins = nullptr;
+
+  Item<T> base(const Run& r, int l) const {
+    Item<T> it;
+    memset(&it, 0, sizeof it);
+    it.L = r.L[l].v;
+    it.S = r.S;
+    it.bg = make_bg<T>(r.P);
+    it.g = make_geo<T>(it.L);
+    it.dt = sizeof(T) == 8 ? (const void*)&r.ds->dtl[l] : (const void*)&r.ds->dtf[l];
+    it.ds = r.ds;
+    it.gm1 = (T)(r.P.gamma - 1.0);
+    it.lum = (T)r.P.L;
+    it.chi = (T)r.P.chi;
+    it.gg = r.P.gamma * (r.P.gamma - 1.0);
+    it.rho0d = r.P.rho0;
+    it.e0d = r.P.e0;
+    for (int d = 0; d < 3; ++d) it.V[d] = r.P.V[d];
+    it.dt_fixed = r.P.dt_fixed;
+    it.level = l;
+    it.band = r.P.band;
+    int fl = 0;
+    if (r.P.hydro_on) fl |= FL_HYDRO | FL_SS3 | FL_WRITE_PI;
+    if (r.P.L != 0.0) fl |= FL_LUM;
+    if (r.P.chi > 0.0) fl |= FL_EPS;
+    if (r.P.diff_face_rho) fl |= FL_DFR;
+    it.flags = fl;
+    return it;
+  }
+
+  Box box(const LevelView& v, int margin) const {
+    Box b;
+    int M = full_boxes ? v.G : margin;
+    for (int d = 0; d < 3; ++d) {
+      b.lo[d] = std::max(0, v.G - M);
+      b.hi[d] = std::min(v.s[d], v.G + v.n[d] + M);
+    }
+    return b;
+  }
+
+  static void add(std::vector<Entry>& out, int op, int d, Item<T> it) {
+    it.count = op_count(op, d, it.L, it.F, it.b);
+    out.push_back({op, d, it});
+  }
+
+  void level_step(const Run& r, int l, int m_out, std::vector<Entry>& out) const {
+    Item<T> it = base(r, l);
+    it.b = box(it.L, m_out + kReach);
+    const Phys& P = r.P;
+    if (l == 0)
+      for (int d = 0; d < 3; ++d) {
+        Item<T> bc = it;
+        bc.bc_lo = P.bc[2 * d];
+        bc.bc_hi = P.bc[2 * d + 1];
+        add(out, OP_BC, d, bc);
+      }
+    if (P.hydro_on) add(out, OP_SOURCE, 0, it);
+    if (P.hydro_on || P.L != 0.0 || P.chi > 0.0) add(out, OP_COMPRESS, 0, it);
+    if (P.chi > 0.0) {
+      if (it.L.is_child) add(out, OP_FRONTIER_DIFF, 0, it);
+      add(out, OP_DIFFUSE, 0, it);
+    }
+    if (P.hydro_on) {
+      for (int d = 0; d < 3; ++d) {
+        add(out, OP_TPREP, 0, it);
+        add(out, OP_TFLUX, d, it);
+        if (it.L.is_child) add(out, OP_TFRONTIER, d, it);
+        add(out, OP_TMOM, d, it);
+        add(out, OP_TUPDATE, d, it);
+      }
+      add(out, OP_VREC, 0, it);
+    }
+  }
+
+  void advance(const Run& r, int l, int m_out, std::vector<Entry>& out) const {
+    if (l + 1 < r.nl) {
+      add(out, OP_ZERO_ACC, 0, base(r, l + 1));
+      int xi = r.xi[l];
+      for (int s = 0; s < xi; ++s) advance(r, l + 1, (xi - 1 - s) * kReach, out);
+    }
+    level_step(r, l, m_out, out);
+    if (l + 1 < r.nl) {
+      Item<T> it = base(r, l);
+      it.F = r.L[l + 1].v;
+      add(out, OP_COMMUP, 0, it);
+      add(out, OP_COMMMEAN, 0, it);
+    }
+  }
+
+  Item<T> force_level_item(const Run& r, int l) const {
+    Item<T> f = base(r, l);
+    int off = 0;
+    for (int m = 0; m < l; ++m) off += force_partials_per_level(r.L[m].v);
+    f.partials = r.partials + 3 * off;
+    return f;
+  }
+
+  Item<T> force_final_item(const Run& r, bool ring) const {
+    Item<T> ff = base(r, 0);
+    ff.partials = r.partials;
+    ff.npart = r.n_partials;
+    if (ring) {
+      ff.ring = r.ring;
+      ff.ring_pos = r.ring_pos;
+      ff.ring_cap = r.ring_cap;
+    }
+    return ff;
+  }
+
+  void coarse_step(const Run& r, int ri, std::vector<Entry>& out) const {
+    for (int l = 0; l < r.nl; ++l) add(out, OP_DT_LEVEL, 0, base(r, l));
+    Item<T> fin = base(r, 0);
+    fin.level = r.nl;  // the finalisation covers all levels
+    fin.fin = d_fins + ri;
+    add(out, OP_DT_FINAL, 0, fin);
+    advance(r, 0, 0, out);
+    for (int l = 0; l < r.nl; ++l) add(out, OP_FORCE_LEVEL, 0, force_level_item(r, l));
+    add(out, OP_FORCE_FINAL, 0, force_final_item(r, true));
+    add(out, OP_TIME, 0, base(r, 0));
+  }
+
+  // greedy merge: repeatedly launch the op kind that heads the most runs' lists,
+  // taking it from every run whose next op it is (each run keeps its own order)
+  void merge(Plan& plan) const {
+    size_t nr = per_run.size();
+    std::vector<size_t> pos(nr, 0);
+    plan.item_size = sizeof(Item<T>);
+    plan.items.clear();
+    plan.starts.clear();
+    plan.launches.clear();
+    for (;;) {
+      std::map<std::pair<int, int>, int> cnt;
+      for (size_t r = 0; r < nr; ++r)
+        if (pos[r] < per_run[r].size()) cnt[{per_run[r][pos[r]].op, per_run[r][pos[r]].d}]++;
+      if (cnt.empty()) break;
+      std::pair<int, int> best = cnt.begin()->first;
+      int bc = -1;
+      for (auto& kv : cnt)
+        if (kv.second > bc) {
+          bc = kv.second;
+          best = kv.first;
+        }
+      LaunchDesc L;
+      L.op = best.first;
+      L.d = best.second;
+      L.kind = kind_of(L.op);
+      L.item0 = plan.items.size() / plan.item_size;
+      L.start0 = plan.starts.size();
+      L.nitems = 0;
+      unsigned chunks = 0;
+      unsigned ce = (unsigned)op_chunk_elems(L.op);
+      for (size_t r = 0; r < nr; ++r) {
+        if (pos[r] >= per_run[r].size()) continue;
+        const Entry& e = per_run[r][pos[r]];
+        if (e.op != best.first || e.d != best.second) continue;
+        ++pos[r];
+        unsigned nch = (e.it.count + ce - 1) / ce;
+        if (nch == 0) continue;
+        const unsigned char* p = reinterpret_cast<const unsigned char*>(&e.it);
+        plan.items.insert(plan.items.end(), p, p + sizeof(Item<T>));
+        plan.starts.push_back(chunks);
+        chunks += nch;
+        ++L.nitems;
+      }
+      L.nchunks = chunks;
+      if (L.nitems) plan.launches.push_back(L);
+    }
+  }
+};
+
+int grow(void** p, size_t* cap, size_t need) {
+  if (need <= *cap) return DF_OK;
+  cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  size_t c = std::max(need, (size_t)4096);
+  CK(cudaMalloc(p, c));
+  *cap = c;
+  return DF_OK;
+}
+
+int plan_upload(Plan& plan) {
+  int rc = grow(&plan.d_items, &plan.cap_items, plan.items.size());
+  if (rc) return rc;
+  rc = grow((void**)&plan.d_starts, &plan.cap_starts, plan.starts.size() * sizeof(unsigned));
+  if (rc) return rc;
+  if (!plan.items.empty())
+    CK(cudaMemcpy(plan.d_items, plan.items.data(), plan.items.size(), cudaMemcpyHostToDevice));
+  if (!plan.starts.empty())
+    CK(cudaMemcpy(plan.d_starts, plan.starts.data(), plan.starts.size() * sizeof(unsigned),
+                  cudaMemcpyHostToDevice));
+  return DF_OK;
+}
+
+template <class T>
+int plan_build(Plan& plan, const std::vector<Run*>& runs, int full_boxes) {
+  plan_invalidate(plan);
+  plan.prec = sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE;
+  size_t nr = runs.size();
+  plan.fins.resize(std::max<size_t>(nr, 1));
+  for (size_t r = 0; r < nr; ++r) fill_fin(*runs[r], plan.fins[r]);
+  int rc = grow((void**)&plan.d_fins, &plan.cap_fins, plan.fins.size() * sizeof(DtFinal));
+  if (rc) return rc;
+  CK(cudaMemcpy(plan.d_fins, plan.fins.data(), plan.fins.size() * sizeof(DtFinal),
+                cudaMemcpyHostToDevice));
+  Builder<T> B;
+  B.full_boxes = full_boxes;
+  B.d_fins = plan.d_fins;
+  B.per_run.resize(nr);
+  for (size_t r = 0; r < nr; ++r) B.coarse_step(*runs[r], (int)r, B.per_run[r]);
+  B.merge(plan);
+  rc = plan_upload(plan);
+  if (rc) return rc;
+  plan.valid = true;
+  return DF_OK;
+}
+
+// a plan of explicitly listed ops of one run (inter-level operators on demand, the
+// force of the current state, the time-step reduction alone)
+template <class T>
+int plan_build_ops(Plan& plan, Run* r, const std::vector<std::pair<int, int>>& ops) {
+  plan_invalidate(plan);
+  plan.prec = sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE;
+  plan.fins.resize(1);
+  fill_fin(*r, plan.fins[0]);
+  int rc = grow((void**)&plan.d_fins, &plan.cap_fins, sizeof(DtFinal));
+  if (rc) return rc;
+  CK(cudaMemcpy(plan.d_fins, plan.fins.data(), sizeof(DtFinal), cudaMemcpyHostToDevice));
+  Builder<T> B;
+  B.d_fins = plan.d_fins;
+  B.per_run.resize(1);
+  auto& v = B.per_run[0];
+  for (auto& ol : ops) {
+    int op = ol.first, l = ol.second;
+    Item<T> it = B.base(*r, l);
+    it.b = B.box(it.L, it.L.G);
+    switch (op) {
+      case OP_COMMUP:
+      case OP_COMMMEAN:
+        it.F = r->L[l + 1].v;
+        B.add(v, op, 0, it);
+        break;
+      case OP_BC:
+        for (int d = 0; d < 3; ++d) {
+          Item<T> bc = it;
+          bc.bc_lo = r->P.bc[2 * d];
+          bc.bc_hi = r->P.bc[2 * d + 1];
+          B.add(v, OP_BC, d, bc);
+        }
+        break;
+      case OP_FORCE_LEVEL:
+        B.add(v, op, 0, B.force_level_item(*r, l));
+        break;
+      case OP_FORCE_FINAL:
+        B.add(v, op, 0, B.force_final_item(*r, false));
+        break;
+      case OP_DT_FINAL:
+        it.level = r->nl;
+        it.fin = plan.d_fins;
+        B.add(v, op, 0, it);
+        break;
+      default:
+        B.add(v, op, 0, it);
+    }
+  }
+  B.merge(plan);
+  rc = plan_upload(plan);
+  if (rc) return rc;
+  plan.valid = true;
+  return DF_OK;
+}
+
+// ---------------------------------------------------------------- execution
+
+struct Exec {
+  cudaStream_t st = nullptr;
+  int sm_count = 148;
+  int bps[OP_COUNT];  // persistent blocks per SM of each op (autotuned for pools)
   bool timing = false;
   struct EvPair {
     cudaEvent_t a, b;
@@ -102,234 +723,109 @@ struct df_ctx {
   size_t ev_used = 0;
   double k_ms[K_NKINDS] = {};
   long long k_n[K_NKINDS] = {};
-  int full_boxes = 0;  // 1: every operator on its whole stencil range (debug/parity)
-  bool stepped = false;
+  long long launches = 0;
+  bool single_fast = true;  // contexts: one-item launches pass the item by value
+  Exec() {
+    for (int o = 0; o < OP_COUNT; ++o) bps[o] = 8;
+  }
 };
 
-namespace {
+void exec_init(Exec& x, int device) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms)
+    x.sm_count = sms;
+}
 
-// Run one launcher; in timing mode bracket it with a pooled event pair of `kind`.
-template <class Fn>
-long long timed(df_ctx* c, int kind, Fn&& fn) {
-  if (!c->timing) return fn();
-  if (c->ev_used == c->evpool.size()) {
-    df_ctx::EvPair p;
-    cudaEventCreate(&p.a);
-    cudaEventCreate(&p.b);
-    c->evpool.push_back(p);
+void exec_free(Exec& x) {
+  for (auto& p : x.evpool) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
   }
-  df_ctx::EvPair& p = c->evpool[c->ev_used++];
-  p.kind = kind;
-  cudaEventRecord(p.a, c->st);
-  long long n = fn();
-  cudaEventRecord(p.b, c->st);
-  return n;
+  x.evpool.clear();
 }
 
 // Fold the recorded event pairs into the per-kind totals (synchronises).
-void harvest_timing(df_ctx* c) {
-  if (!c->ev_used) return;
-  cudaStreamSynchronize(c->st);
-  for (size_t i = 0; i < c->ev_used; ++i) {
+void harvest_timing(Exec& x) {
+  if (!x.ev_used) return;
+  cudaStreamSynchronize(x.st);
+  for (size_t i = 0; i < x.ev_used; ++i) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->evpool[i].a, c->evpool[i].b);
-    c->k_ms[c->evpool[i].kind] += ms;
-    c->k_n[c->evpool[i].kind] += 1;
+    cudaEventElapsedTime(&ms, x.evpool[i].a, x.evpool[i].b);
+    x.k_ms[x.evpool[i].kind] += ms;
+    x.k_n[x.evpool[i].kind] += 1;
   }
-  c->ev_used = 0;
+  x.ev_used = 0;
 }
 
 template <class T>
-struct Ops {
-  // device address of level l's step in T
-  static const T* level_dt(df_ctx* c, int l) {
-    if (sizeof(T) == 8) return (const T*)&c->ds->dtl[l];
-    return (const T*)&c->ds->dtf[l];
-  }
-
-  static Box box(const df_ctx* c, const LevelView& v, int margin) {
-    Box b;
-    int M = c->full_boxes ? v.G : margin;
-    for (int d = 0; d < 3; ++d) {
-      b.lo[d] = std::max(0, v.G - M);
-      b.hi[d] = std::min(v.s[d], v.G + v.n[d] + M);
-    }
-    return b;
-  }
-
-  static long long level_step(df_ctx* c, int l, int m_out) {
-    LevelView& v = c->L[l].v;
-    const Phys& P = c->P;
-    cudaStream_t st = c->st;
-    const T* dt = level_dt(c, l);
-    const Scratch& S = c->S;
-    long long n = 0;
-    Box b = box(c, v, m_out + kReach);
-    double gm1 = P.gamma - 1.0;
-    if (l == 0) n += timed(c, K_BC, [&] { return launch_bc_fill<T>(v, P, st); });
-    if (P.hydro_on)
-      n += timed(c, K_SOURCE, [&] { return launch_source<T>(v, b, S, dt, 1, gm1, P, st); });
-    int do_lum = P.L != 0.0, do_eps = P.chi > 0.0;
-    if (P.hydro_on || do_lum || do_eps)
-      n += timed(c, K_COMPRESS, [&] {
-        return launch_compress_lum<T>(v, b, S, dt, P, P.hydro_on, do_lum, do_eps, st);
-      });
-    if (P.chi > 0.0) {
-      if (v.is_child)
-        n += timed(c, K_FRONTIER_DIFF, [&] { return launch_frontier_diff<T>(v, S, dt, P, st); });
-      n += timed(c, K_DIFFUSE, [&] { return launch_diffuse<T>(v, b, S, dt, P, st); });
-    }
-    if (P.hydro_on) {
-      for (int d = 0; d < 3; ++d) {
-        n += timed(c, K_TPREP, [&] { return launch_tprep<T>(v, b, S, P, st); });
-        n += timed(c, K_TFLUX, [&] { return launch_tflux<T>(v, b, S, d, dt, P, st); });
-        if (v.is_child)
-          n += timed(c, K_TFRONTIER, [&] { return launch_tfrontier<T>(v, S, d, st); });
-        n += timed(c, K_TMOM, [&] { return launch_tmom<T>(v, b, S, d, dt, P, st); });
-        n += timed(c, K_TUPDATE, [&] { return launch_tupdate<T>(v, b, S, d, st); });
+long long plan_run(const Plan& plan, Exec& x, bool events) {
+  long long n = 0;
+  const unsigned char* items = (const unsigned char*)plan.d_items;
+  for (const LaunchDesc& L : plan.launches) {
+    unsigned grid = (unsigned)x.sm_count * (unsigned)x.bps[L.op];
+    const Item<T>* it = (const Item<T>*)(items + L.item0 * plan.item_size);
+    const unsigned* st = plan.d_starts + L.start0;
+    const Item<T>* hi = (L.nitems == 1 && x.single_fast)
+                            ? (const Item<T>*)(plan.items.data() + L.item0 * plan.item_size)
+                            : nullptr;
+    if (events) {
+      if (x.ev_used == x.evpool.size()) {
+        Exec::EvPair p;
+        cudaEventCreate(&p.a);
+        cudaEventCreate(&p.b);
+        x.evpool.push_back(p);
       }
-      n += timed(c, K_VREC_SOURCE,
-                 [&] { return launch_vrec_source<T>(v, b, S, dt, gm1, P, st); });
-    }
-    return n;
-  }
-
-  static long long advance(df_ctx* c, int l, int m_out) {
-    long long n = 0;
-    if (l + 1 < c->nl) {
-      Level& ch = c->L[l + 1];
-      cudaMemsetAsync(ch.acc, 0, ch.acc_elems * sizeof(double), c->st);
-      int xi = c->xi[l];
-      for (int s = 0; s < xi; ++s) n += advance(c, l + 1, (xi - 1 - s) * kReach);
-    }
-    n += level_step(c, l, m_out);
-    if (l + 1 < c->nl) {
-      const LevelView &cv = c->L[l].v, &fv = c->L[l + 1].v;
-      n += timed(c, K_COMMUP, [&] { return launch_commup<T>(cv, fv, c->st); });
-      n += timed(c, K_COMMMEAN, [&] { return launch_commmean<T>(cv, fv, c->P.band, c->st); });
-    }
-    return n;
-  }
-
-  static void prods(const df_ctx* c, double* out /* 5*nl */) {
-    double pr = 1.0;
-    for (int l = 0; l < c->nl; ++l) {
-      if (l > 0) pr *= c->xi[l - 1];
-      out[l] = pr;
-      const LevelView& v = c->L[l].v;
-      double lim = INFINITY;
-      if (c->P.chi > 0.0) {
-        double sinv = 0.0;
-        for (int d = 0; d < 3; ++d) sinv += 1.0 / (v.dx[d] * v.dx[d]);
-        lim = c->P.cfl_diff / (2.0 * c->P.chi * sinv);
-      }
-      out[c->nl + l] = lim;
-      for (int d = 0; d < 3; ++d)
-        out[2 * c->nl + 3 * l + d] = c->P.hydro_on ? c->P.cfl * v.dx[d] : 0.0;
+      Exec::EvPair& p = x.evpool[x.ev_used++];
+      p.kind = L.kind;
+      cudaEventRecord(p.a, x.st);
+      n += launch_batch<T>(L.op, L.d, it, st, L.nitems, L.nchunks, grid, x.st, hi);
+      cudaEventRecord(p.b, x.st);
+    } else {
+      n += launch_batch<T>(L.op, L.d, it, st, L.nitems, L.nchunks, grid, x.st, hi);
     }
   }
+  return n;
+}
 
-  static long long dt_levels(df_ctx* c) {
-    long long n = 0;
-    for (int l = 0; l < c->nl; ++l)
-      n += timed(c, K_DT, [&] { return launch_dt_level<T>(c->L[l].v, l, c->P, c->ds, c->st); });
-    return n;
-  }
-
-  static long long force(df_ctx* c, bool ring) {
-    long long n = 0;
-    int off = 0;
-    for (int l = 0; l < c->nl; ++l) {
-      n += timed(c, K_FORCE,
-                 [&] { return launch_force_level<T>(c->L[l].v, c->P, c->partials, off, c->st); });
-      off += force_partials_per_level(c->L[l].v);
-    }
-    n += timed(c, K_FORCE, [&] {
-      return launch_force_finalize(c->partials, off, c->ds, ring ? c->ring : nullptr,
-                                   c->ring_cap, c->ring_pos, c->st);
-    });
-    return n;
-  }
-
-  // one coarse step with the current xi word
-  static long long coarse_step(df_ctx* c) {
-    long long n = dt_levels(c);
-    double pr[5 * DF_MAX_LEVELS];
-    prods(c, pr);
-    n += timed(c, K_DT, [&] { return launch_dt_finalize(c->ds, c->nl, pr, c->P.dt_fixed, c->st); });
-    n += advance(c, 0, 0);
-    n += force(c, true);
-    n += timed(c, K_OTHER, [&] { return launch_time_advance(c->ds, c->st); });
-    return n;
-  }
-};
-
+// nsteps coarse steps of every run of the plan: graph replay, or direct launches
+// bracketed by events in timing mode
 template <class T>
-int run_steps(df_ctx* c, int nsteps) {
-  if (c->P.dt_fixed <= 0.0 && c->P.hydro_on == 0 && !(c->P.chi > 0.0))
-    return fail(DF_EINVAL, "no time-step limit: set dt_fixed, hydro_on or chi");
-  if (c->prm.xi_mode == 1 && c->nl > 1) {
-    // Eq. 55-56 search each coarse step: per-level limits come back to the host
-    for (int s = 0; s < nsteps; ++s) {
-      c->launches += Ops<T>::dt_levels(c);
-      unsigned long long bits[3 * DF_MAX_LEVELS];
-      CK(cudaMemcpyAsync(bits, c->ds->dtmin, 3 * c->nl * sizeof(unsigned long long),
-                         cudaMemcpyDeviceToHost, c->st));
-      CK(cudaStreamSynchronize(c->st));
-      double pr[5 * DF_MAX_LEVELS], lim[DF_MAX_LEVELS], cost[DF_MAX_LEVELS];
-      for (int l = 0; l < c->nl; ++l) c->xi[l] = 2;
-      Ops<T>::prods(c, pr);
-      for (int l = 0; l < c->nl; ++l) {
-        lim[l] = pr[c->nl + l];
-        for (int d = 0; d < 3; ++d) {
-          double mx;
-          memcpy(&mx, &bits[3 * l + d], 8);
-          lim[l] = std::min(lim[l], pr[2 * c->nl + 3 * l + d] / mx);
-        }
-        cost[l] = (double)c->n[0] * c->n[1] * c->n[2];
-      }
-      int xiw[DF_MAX_LEVELS];
-      double ratio;
-      df_xi_search(c->nl, lim, cost, xiw, &ratio);
-      for (int l = 0; l + 1 < c->nl; ++l) c->xi[l] = xiw[l];
-      Ops<T>::prods(c, pr);
-      long long n = launch_dt_finalize(c->ds, c->nl, pr, c->P.dt_fixed, c->st);
-      n += Ops<T>::advance(c, 0, 0);
-      n += Ops<T>::force(c, true);
-      n += launch_time_advance(c->ds, c->st);
-      c->launches += n;
-    }
+int plan_step(Plan& plan, Exec& x, int nsteps) {
+  if (x.timing) {
+    for (int s = 0; s < nsteps; ++s) x.launches += plan_run<T>(plan, x, true);
     CK(cudaGetLastError());
     return DF_OK;
   }
-  for (int l = 0; l < c->nl; ++l) c->xi[l] = 2;
-  if (c->timing) {
-    for (int s = 0; s < nsteps; ++s) c->launches += Ops<T>::coarse_step(c);
-    CK(cudaGetLastError());
-    return DF_OK;
-  }
-  if (!c->gexec) {
+  if (!plan.gexec) {
     cudaGraph_t g;
-    CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-    long long n = Ops<T>::coarse_step(c);
-    cudaError_t e = cudaStreamEndCapture(c->st, &g);
+    CK(cudaStreamBeginCapture(x.st, cudaStreamCaptureModeThreadLocal));
+    long long n = plan_run<T>(plan, x, false);
+    cudaError_t e = cudaStreamEndCapture(x.st, &g);
     if (e != cudaSuccess) return fail(DF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    e = cudaGraphInstantiate(&plan.gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(DF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    c->graph_kernels = n;
+    plan.kernels = n;
   }
   for (int s = 0; s < nsteps; ++s) {
-    CK(cudaGraphLaunch(c->gexec, c->st));
-    c->launches += c->graph_kernels;
+    CK(cudaGraphLaunch(plan.gexec, x.st));
+    x.launches += plan.kernels;
   }
   return DF_OK;
 }
 
-int check_ctx(df_ctx* c, bool need_params = true) {
-  if (!c) return fail(DF_EINVAL, "null context");
-  if (need_params && !c->have_params) return fail(DF_EINVAL, "df_set_params not called");
-  return DF_OK;
+// run a list of ops of one run now, without a graph, and wait for it
+int run_ops_now(Run* r, Exec& x, const std::vector<std::pair<int, int>>& ops) {
+  Plan p;
+  int rc = r->prec == DF_FP64 ? plan_build_ops<double>(p, r, ops) : plan_build_ops<float>(p, r, ops);
+  if (!rc) {
+    x.launches += r->prec == DF_FP64 ? plan_run<double>(p, x, false) : plan_run<float>(p, x, false);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x.st);
+    if (e != cudaSuccess) rc = fail(DF_ECUDA, "ops: %s", cudaGetErrorString(e));
+  }
+  plan_free(p);
+  return rc;
 }
 
 struct DevGuard {
@@ -345,72 +841,95 @@ struct DevGuard {
   }
 };
 
-void enter(df_ctx* c) {
-  cudaEventRecord(c->ev_in, c->user);
-  cudaStreamWaitEvent(c->st, c->ev_in, 0);
+// background value of a field (the stored state is the deviation from it)
+double field_bg(const Run* r, int field) {
+  return field == 0 ? r->P.rho0 : field == 1 ? r->P.e0 : r->P.V[field - 2];
 }
-void leave(df_ctx* c) {
-  cudaEventRecord(c->ev_out, c->st);
+
+template <class T>
+int run_io(Run* r, cudaStream_t st, int level, int field, double* out, const double* in, int full,
+           bool raw, long long* launches) {
+  if (level < 0 || level >= r->nl || field < 0 || field > 4)
+    return fail(DF_EINVAL, "level %d / field %d out of range", level, field);
+  LevelView& v = r->L[level].v;
+  size_t n = full ? (size_t)v.nc : (size_t)v.n[0] * v.n[1] * v.n[2];
+  double bgv = raw ? 0.0 : field_bg(r, field);
+  if (in) {
+    CK(cudaMemcpyAsync(r->stage, in, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    *launches += launch_unpack_active<T>(v, field, r->stage, full, bgv, st);
+  } else {
+    *launches += launch_pack_active<T>(v, field, r->stage, full, bgv, st);
+    CK(cudaMemcpyAsync(out, r->stage, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return DF_OK;
+}
+
+int io(Run* r, cudaStream_t st, int level, int field, double* out, const double* in, int full,
+       bool raw, long long* launches) {
+  return r->prec == DF_FP64 ? run_io<double>(r, st, level, field, out, in, full, raw, launches)
+                            : run_io<float>(r, st, level, field, out, in, full, raw, launches);
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------- contexts
+
+struct df_ctx {
+  int device = 0;
+  cudaStream_t user = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  Run* run = nullptr;
+  Plan plan;
+  Exec x;
+  int full_boxes = 0;
+};
+
+struct df_pool {
+  int device = 0, prec = 0;
+  size_t budget = 0, used = 0;
+  cudaStream_t user = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<Run*> slots;
+  Plan plan;
+  Exec x;
+};
+
+namespace {
+
+template <class C>
+void enter(C* c) {
+  cudaEventRecord(c->ev_in, c->user);
+  cudaStreamWaitEvent(c->x.st, c->ev_in, 0);
+}
+template <class C>
+void leave(C* c) {
+  cudaEventRecord(c->ev_out, c->x.st);
   cudaStreamWaitEvent(c->user, c->ev_out, 0);
 }
 
-int sync_health(df_ctx* c) {
-  CK(cudaStreamSynchronize(c->st));
+int check_ctx(df_ctx* c, bool need_params = true) {
+  if (!c || !c->run) return fail(DF_EINVAL, "null context");
+  if (need_params && !c->run->have_params) return fail(DF_EINVAL, "df_set_params not called");
+  return DF_OK;
+}
+
+int sync_health(cudaStream_t st, Run* r) {
+  CK(cudaStreamSynchronize(st));
   int bad = 0;
-  CK(cudaMemcpy(&bad, &c->ds->unhealthy, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&bad, &r->ds->unhealthy, sizeof(int), cudaMemcpyDeviceToHost));
   if (bad) return fail(DF_EUNHEALTHY, "NaN, rho <= 0 or e <= 0 found in the state");
   return DF_OK;
 }
 
-// background value of a field (the stored state is the deviation from it)
-double field_bg(const df_ctx* c, int field) {
-  return field == 0 ? c->P.rho0 : field == 1 ? c->P.e0 : c->P.V[field - 2];
+int build_plan(Plan& p, const std::vector<Run*>& runs, int prec, int full_boxes) {
+  return prec == DF_FP64 ? plan_build<double>(p, runs, full_boxes)
+                         : plan_build<float>(p, runs, full_boxes);
 }
 
-template <class T>
-int do_io(df_ctx* c, int level, int field, double* out, const double* in, int full,
-          bool raw = false) {
-  if (level < 0 || level >= c->nl || field < 0 || field > 4)
-    return fail(DF_EINVAL, "level %d / field %d out of range", level, field);
-  LevelView& v = c->L[level].v;
-  size_t n = full ? (size_t)v.nc : (size_t)v.n[0] * v.n[1] * v.n[2];
-  if (in) {
-    CK(cudaMemcpyAsync(c->stage, in, n * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    double bgv = raw ? 0.0 : field_bg(c, field);
-    c->launches += launch_unpack_active<T>(v, field, c->stage, full, bgv, c->st);
-  } else {
-    double bgv = raw ? 0.0 : field_bg(c, field);
-    c->launches += launch_pack_active<T>(v, field, c->stage, full, bgv, c->st);
-    CK(cudaMemcpyAsync(out, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-  }
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
-  return DF_OK;
-}
-
-void free_ctx(df_ctx* c) {
-  if (!c) return;
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  for (auto& l : c->L) {
-    cudaFree(l.mem);
-    cudaFree(l.acc);
-    cudaFree(l.v.fw);
-  }
-  cudaFree(c->scratch_mem);
-  cudaFree(c->ds);
-  cudaFree(c->partials);
-  cudaFree(c->ring);
-  cudaFree(c->ring_pos);
-  cudaFree(c->wsum);
-  cudaFree(c->stage);
-  if (c->ev_in) cudaEventDestroy(c->ev_in);
-  if (c->ev_out) cudaEventDestroy(c->ev_out);
-  for (auto& p : c->evpool) {
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
-  }
-  if (c->st) cudaStreamDestroy(c->st);
-  delete c;
+int step_plan(Plan& p, Exec& x, int prec, int n) {
+  return prec == DF_FP64 ? plan_step<double>(p, x, n) : plan_step<float>(p, x, n);
 }
 
 }  // namespace
@@ -446,230 +965,106 @@ int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], co
               int G, int precision, int device, void* stream) {
   if (!out || !n || !lo || !hi) return fail(DF_EINVAL, "null argument");
   *out = nullptr;
-  if (n_levels < 1 || n_levels > DF_MAX_LEVELS) return fail(DF_EINVAL, "n_levels out of range");
-  if (G < 2 || G % 2) return fail(DF_EINVAL, "G must be even and >= 2");
-  if (precision != DF_FP64 && precision != DF_FP32_STATE)
-    return fail(DF_EINVAL, "unknown precision %d", precision);
-  for (int d = 0; d < 3; ++d) {
-    if (n[d] < 8 || n[d] % 4 || n[d] < G) return fail(DF_EINVAL, "n[%d]=%d: need n%%4==0, n>=8, n>=G", d, n[d]);
-    if (!(hi[d] > lo[d])) return fail(DF_EINVAL, "empty box on axis %d", d);
-  }
-  long long s3 = 1;
-  for (int d = 0; d < 3; ++d) s3 *= (n[d] + 2 * G);
-  if (s3 >= (1LL << 31) / 5) return fail(DF_EINVAL, "level too large (%lld elements)", s3);
+  int rc = check_shape(n_levels, n, lo, hi, G, precision);  // before touching the device
+  if (rc) return rc;
   CK(cudaSetDevice(device));
   df_ctx* c = new (std::nothrow) df_ctx;
   if (!c) return fail(DF_ENOMEM, "host allocation");
-  c->nl = n_levels;
-  c->prec = precision;
   c->device = device;
-  c->G = G;
-  c->esz = precision == DF_FP64 ? 8 : 4;
   c->user = (cudaStream_t)stream;
-  for (int d = 0; d < 3; ++d) {
-    c->n[d] = n[d];
-    c->lo[d] = lo[d];
-    c->hi[d] = hi[d];
+  rc = run_create(&c->run, n_levels, n, lo, hi, G, precision);
+  if (rc) {
+    delete c;
+    return rc;
   }
-  for (int l = 0; l < DF_MAX_LEVELS; ++l) c->xi[l] = 2;
-#define CKF(call)                                                            \
-  do {                                                                       \
-    cudaError_t e_ = (call);                                                 \
-    if (e_ != cudaSuccess) {                                                 \
-      int r_ = fail(e_ == cudaErrorMemoryAllocation ? DF_ENOMEM : DF_ECUDA,  \
-                    "%s failed: %s", #call, cudaGetErrorString(e_));         \
-      free_ctx(c);                                                           \
-      return r_;                                                             \
-    }                                                                        \
-  } while (0)
-  CKF(cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking));
-  CKF(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
-  CKF(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
-  c->L.resize(n_levels);
-  size_t nc = (size_t)s3;
-  for (int l = 0; l < n_levels; ++l) {
-    LevelView& v = c->L[l].v;
-    memset(&v, 0, sizeof v);
-    double scale = std::ldexp(1.0, -l);
-    v.G = G;
-    v.nc = (int)nc;
-    for (int d = 0; d < 3; ++d) {
-      v.n[d] = n[d];
-      v.s[d] = n[d] + 2 * G;
-      v.lo[d] = lo[d] * scale;
-      v.dx[d] = (hi[d] - lo[d]) * scale / n[d];
-    }
-    v.st[0] = 1;
-    v.st[1] = v.s[0];
-    v.st[2] = v.s[0] * v.s[1];
-    v.vol = v.dx[0] * v.dx[1] * v.dx[2];
-    v.area[0] = v.dx[1] * v.dx[2];
-    v.area[1] = v.dx[0] * v.dx[2];
-    v.area[2] = v.dx[0] * v.dx[1];
-    v.inv_vol = 1.0 / v.vol;
-    for (int d = 0; d < 3; ++d) {
-      v.inv_dx[d] = 1.0 / v.dx[d];
-      v.dcoef[d] = v.area[d] / v.dx[d];
-    }
-    v.dt_scale = scale;
-    v.is_child = l > 0;
-    if (l > 0) {
-      const LevelView& p = c->L[l - 1].v;
-      for (int d = 0; d < 3; ++d) {
-        double o = (v.lo[d] - p.lo[d]) / p.dx[d];
-        int oi = (int)std::floor(o + 0.5);
-        if (std::fabs(o - oi) > 1e-9 || oi < G / 2 + 1 || oi + n[d] / 2 + G / 2 + 1 > p.n[d]) {
-          int r = fail(DF_EINVAL,
-                       "level %d: offset %.3f on axis %d must be an integer in [%d, %d]", l, o,
-                       d, G / 2 + 1, p.n[d] - n[d] / 2 - G / 2 - 1);
-          free_ctx(c);
-          return r;
-        }
-        v.off[d] = oi;
-      }
-    }
-    // one allocation: 5 fields + potential + luminosity weights, 256-B aligned planes
-    size_t plane = ((nc * c->esz + 255) / 256) * 256;
-    CKF(cudaMalloc(&c->L[l].mem, plane * 7));
-    char* base = (char*)c->L[l].mem;
-    for (int f = 0; f < 5; ++f) v.q[f] = base + plane * f;
-    v.phi = base + plane * 5;
-    v.lumw = base + plane * 6;
-    // frontier accumulators (this level as a child): 6 sides x 3 quantities
-    int slots = 0;
-    for (int d = 0; d < 3; ++d) {
-      int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-      slots = std::max(slots, (n[t1] / 2) * (n[t2] / 2));
-    }
-    v.acc_slots = slots;
-    c->L[l].acc_elems = (size_t)18 * slots;
-    CKF(cudaMalloc(&c->L[l].acc, c->L[l].acc_elems * sizeof(double)));
-    CKF(cudaMalloc(&v.fw, (size_t)n[0] * n[1] * n[2] * sizeof(double)));
-    CKF(cudaMemset(c->L[l].acc, 0, c->L[l].acc_elems * sizeof(double)));
-    v.acc = c->L[l].acc;
+  exec_init(c->x, device);
+  if (cudaStreamCreateWithFlags(&c->x.st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    run_free(c->run);
+    delete c;
+    return fail(DF_ECUDA, "stream/event creation failed");
   }
-  for (int l = 0; l + 1 < n_levels; ++l) {
-    LevelView& v = c->L[l].v;
-    const LevelView& ch = c->L[l + 1].v;
-    v.has_child = 1;
-    for (int d = 0; d < 3; ++d) {
-      v.coff[d] = ch.off[d];
-      v.cn[d] = ch.n[d];
-    }
-    v.cacc = ch.acc;
-    v.cacc_slots = ch.acc_slots;
-  }
-  // shared scratch: pi[3], eps, w[3], F, E, P[3]
-  size_t plane = ((nc * c->esz + 255) / 256) * 256;
-  CKF(cudaMalloc(&c->scratch_mem, plane * 12));
-  CKF(cudaMemset(c->scratch_mem, 0, plane * 12));
-  {
-    char* b = (char*)c->scratch_mem;
-    for (int m = 0; m < 3; ++m) c->S.pi[m] = b + plane * m;
-    c->S.eps = b + plane * 3;
-    for (int m = 0; m < 3; ++m) c->S.w[m] = b + plane * (4 + m);
-    c->S.F = b + plane * 7;
-    c->S.E = b + plane * 8;
-    for (int m = 0; m < 3; ++m) c->S.P[m] = b + plane * (9 + m);
-  }
-  CKF(cudaMalloc(&c->ds, sizeof(DevScalars)));
-  CKF(cudaMemset(c->ds, 0, sizeof(DevScalars)));
-  // partials: 3 per force block of every level, and one per 256 active cells of a
-  // level for the luminosity normalisation (the two uses never overlap in time)
-  int np = 0;
-  for (int l = 0; l < n_levels; ++l) np += force_partials_per_level(c->L[l].v);
-  c->n_partials = np;
-  size_t lum_blocks = ((size_t)n[0] * n[1] * n[2] + 255) / 256;
-  size_t pelems = std::max(3 * (size_t)np, lum_blocks);
-  CKF(cudaMalloc(&c->partials, pelems * sizeof(double)));
-  CKF(cudaMalloc(&c->ring, 3 * (size_t)c->ring_cap * sizeof(double)));
-  CKF(cudaMalloc(&c->ring_pos, sizeof(long long)));
-  CKF(cudaMemset(c->ring_pos, 0, sizeof(long long)));
-  CKF(cudaMalloc(&c->wsum, sizeof(double)));
-  c->stage_elems = nc;
-  CKF(cudaMalloc(&c->stage, nc * sizeof(double)));
-#undef CKF
   *out = c;
   return DF_OK;
 }
 
 int df_set_params(df_ctx* c, const df_params* p) {
   if (check_ctx(c, false)) return DF_EINVAL;
-  if (!p) return fail(DF_EINVAL, "null params");
-  if (!(p->gamma > 1.0) || !(p->rho0 > 0.0) || !(p->cs > 0.0) || p->chi < 0.0 ||
-      !(p->cfl > 0.0) || p->band < 1 || p->mach < 0.0)
-    return fail(DF_EINVAL, "invalid physical parameters");
-  if (p->chi > 0.0 && !(p->cfl_diff > 0.0)) return fail(DF_EINVAL, "cfl_diff must be > 0");
-  for (int k = 0; k < 6; ++k)
-    if (p->bc[k] < 0 || p->bc[k] > 3) return fail(DF_EINVAL, "bad boundary type");
+  if (check_params(p)) return DF_EINVAL;
   DevGuard g(c->device);
-  c->prm = *p;
-  Phys& P = c->P;
-  P.gamma = p->gamma;
-  P.rho0 = p->rho0;
-  P.e0 = p->cs * p->cs * p->rho0 / (p->gamma * (p->gamma - 1.0));  // Sec. 3.4
-  for (int d = 0; d < 3; ++d) P.V[d] = p->mach * p->cs * p->flow_dir[d];
-  P.GM = p->GM;
-  P.eps = p->eps;
-  P.chi = p->chi;
-  P.L = p->L;
-  P.cfl = p->cfl;
-  P.cfl_diff = p->cfl_diff;
-  P.dt_fixed = p->dt_fixed;
-  P.diff_face_rho = p->diff_face_rho;
-  P.hydro_on = p->hydro_on;
-  P.band = p->band;
-  for (int k = 0; k < 6; ++k) P.bc[k] = p->bc[k];
   enter(c);
-  for (int l = 0; l < c->nl; ++l) {
-    LevelView& v = c->L[l].v;
-    c->launches += c->prec == DF_FP64 ? launch_init_uniform<double>(v, P, c->st)
-                                      : launch_init_uniform<float>(v, P, c->st);
-    if (c->prec == DF_FP64) {
-      c->launches += launch_static_fields<double>(v, P, p->lum_sigma, c->wsum, c->partials, c->st);
-      if (p->lum_sigma > 0.0) c->launches += launch_normalise_lum<double>(v, c->wsum, c->st);
-    } else {
-      c->launches += launch_static_fields<float>(v, P, p->lum_sigma, c->wsum, c->partials, c->st);
-      if (p->lum_sigma > 0.0) c->launches += launch_normalise_lum<float>(v, c->wsum, c->st);
-    }
-    CK(cudaMemsetAsync(c->L[l].acc, 0, c->L[l].acc_elems * sizeof(double), c->st));
-    c->launches += launch_force_weights(v, P, c->st);
-  }
-  DevScalars h;
-  memset(&h, 0, sizeof h);
-  // per-axis maxima start at +0.0 (bit pattern 0)
-  CK(cudaMemcpyAsync(c->ds, &h, sizeof h, cudaMemcpyHostToDevice, c->st));
-  CK(cudaMemsetAsync(c->ring_pos, 0, sizeof(long long), c->st));
+  int rc = DF_OK;
+  c->x.launches += run_set_params(c->run, p, c->x.st, &rc);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
+  CK(cudaStreamSynchronize(c->x.st));
   leave(c);
-  if (c->gexec) {
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
-  }
-  c->have_params = true;
-  c->stepped = false;
-  return DF_OK;
+  plan_invalidate(c->plan);
+  return rc;
 }
 
 int df_step(df_ctx* c, int n) {
   if (check_ctx(c)) return DF_EINVAL;
   if (n < 0) return fail(DF_EINVAL, "negative step count");
   if (n == 0) return DF_OK;
+  Run* r = c->run;
+  if (r->P.dt_fixed <= 0.0 && r->P.hydro_on == 0 && !(r->P.chi > 0.0))
+    return fail(DF_EINVAL, "no time-step limit: set dt_fixed, hydro_on or chi");
   DevGuard g(c->device);
   enter(c);
-  int r = c->prec == DF_FP64 ? run_steps<double>(c, n) : run_steps<float>(c, n);
+  int rc = DF_OK;
+  std::vector<Run*> runs{r};
+  if (r->prm.xi_mode == 1 && r->nl > 1) {
+    // Eq. 55-56 search each coarse step: the per-level limits come back to the
+    // host, the plan is rebuilt for the chosen word and launched without a graph
+    for (int s = 0; s < n && !rc; ++s) {
+      std::vector<std::pair<int, int>> ops;
+      for (int l = 0; l < r->nl; ++l) ops.push_back({OP_DT_LEVEL, l});
+      rc = run_ops_now(r, c->x, ops);
+      if (rc) break;
+      unsigned long long bits[3 * DF_MAX_LEVELS];
+      CK(cudaMemcpy(bits, r->ds->dtmin, 3 * r->nl * sizeof(unsigned long long),
+                    cudaMemcpyDeviceToHost));
+      for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
+      DtFinal fin;
+      fill_fin(*r, fin);
+      double lim[DF_MAX_LEVELS], cost[DF_MAX_LEVELS];
+      for (int l = 0; l < r->nl; ++l) {
+        lim[l] = fin.diff_lim[l];
+        for (int d = 0; d < 3; ++d) {
+          double mx;
+          memcpy(&mx, &bits[3 * l + d], 8);
+          lim[l] = std::min(lim[l], fin.cfl_dx[l][d] / mx);
+        }
+        cost[l] = (double)r->n[0] * r->n[1] * r->n[2];
+      }
+      int xiw[DF_MAX_LEVELS];
+      double ratio;
+      df_xi_search(r->nl, lim, cost, xiw, &ratio);
+      for (int l = 0; l + 1 < r->nl; ++l) r->xi[l] = xiw[l];
+      rc = build_plan(c->plan, runs, r->prec, c->full_boxes);
+      if (rc) break;
+      c->x.launches += r->prec == DF_FP64 ? plan_run<double>(c->plan, c->x, c->x.timing)
+                                          : plan_run<float>(c->plan, c->x, c->x.timing);
+      plan_invalidate(c->plan);
+    }
+    for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
+  } else {
+    for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
+    if (!c->plan.valid) rc = build_plan(c->plan, runs, r->prec, c->full_boxes);
+    if (!rc) rc = step_plan(c->plan, c->x, r->prec, n);
+  }
   leave(c);
-  c->stepped = true;
-  return r;
+  r->stepped = true;
+  return rc;
 }
 
 int df_status(df_ctx* c, double* t, double* dt_last, int* unhealthy) {
   if (check_ctx(c)) return DF_EINVAL;
   DevGuard g(c->device);
-  CK(cudaStreamSynchronize(c->st));
+  CK(cudaStreamSynchronize(c->x.st));
   DevScalars h;
-  CK(cudaMemcpy(&h, c->ds, sizeof h, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&h, c->run->ds, sizeof h, cudaMemcpyDeviceToHost));
   if (t) *t = h.t;
   if (dt_last) *dt_last = h.dt;
   if (unhealthy) *unhealthy = h.unhealthy;
@@ -681,12 +1076,14 @@ int df_force_now(df_ctx* c, double F[3]) {
   if (!F) return fail(DF_EINVAL, "null output");
   DevGuard g(c->device);
   enter(c);
-  c->launches += c->prec == DF_FP64 ? Ops<double>::force(c, false) : Ops<float>::force(c, false);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
+  std::vector<std::pair<int, int>> ops;
+  for (int l = 0; l < c->run->nl; ++l) ops.push_back({OP_FORCE_LEVEL, l});
+  ops.push_back({OP_FORCE_FINAL, 0});
+  int rc = run_ops_now(c->run, c->x, ops);
   leave(c);
+  if (rc) return rc;
   DevScalars h;
-  CK(cudaMemcpy(&h, c->ds, sizeof h, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&h, c->run->ds, sizeof h, cudaMemcpyDeviceToHost));
   for (int d = 0; d < 3; ++d) F[d] = h.F[d];
   return DF_OK;
 }
@@ -695,20 +1092,21 @@ int df_force(df_ctx* c, double F[3], double* along) {
   if (check_ctx(c)) return DF_EINVAL;
   if (!F) return fail(DF_EINVAL, "null output");
   DevGuard g(c->device);
-  int r;
-  if (!c->stepped) {
-    r = df_force_now(c, F);
-    if (r) return r;
+  Run* r = c->run;
+  int rc;
+  if (!r->stepped) {
+    rc = df_force_now(c, F);
+    if (rc) return rc;
   } else {
-    r = sync_health(c);
+    rc = sync_health(c->x.st, r);
     DevScalars h;
-    CK(cudaMemcpy(&h, c->ds, sizeof h, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&h, r->ds, sizeof h, cudaMemcpyDeviceToHost));
     for (int d = 0; d < 3; ++d) F[d] = h.F[d];
-    if (r) return r;
+    if (rc) return rc;
   }
   if (along) {
-    double nv = std::sqrt(c->P.V[0] * c->P.V[0] + c->P.V[1] * c->P.V[1] + c->P.V[2] * c->P.V[2]);
-    *along = nv > 0 ? -(F[0] * c->P.V[0] + F[1] * c->P.V[1] + F[2] * c->P.V[2]) / nv : 0.0;
+    double nv = std::sqrt(r->P.V[0] * r->P.V[0] + r->P.V[1] * r->P.V[1] + r->P.V[2] * r->P.V[2]);
+    *along = nv > 0 ? -(F[0] * r->P.V[0] + F[1] * r->P.V[1] + F[2] * r->P.V[2]) / nv : 0.0;
   }
   return DF_OK;
 }
@@ -716,29 +1114,27 @@ int df_force(df_ctx* c, double F[3], double* along) {
 int df_compute_dt(df_ctx* c, double* dt, double* dt_level) {
   if (check_ctx(c)) return DF_EINVAL;
   DevGuard g(c->device);
+  Run* r = c->run;
   enter(c);
-  long long n =
-      c->prec == DF_FP64 ? Ops<double>::dt_levels(c) : Ops<float>::dt_levels(c);
-  double pr[5 * DF_MAX_LEVELS];
-  for (int l = 0; l < c->nl; ++l) c->xi[l] = 2;
-  if (c->prec == DF_FP64)
-    Ops<double>::prods(c, pr);
-  else
-    Ops<float>::prods(c, pr);
-  // the finalize kernel overwrites the coarse step; keep the last one taken
+  for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
   DevScalars before;
-  CK(cudaMemcpyAsync(&before, c->ds, sizeof before, cudaMemcpyDeviceToHost, c->st));
-  n += launch_dt_finalize(c->ds, c->nl, pr, c->P.dt_fixed, c->st);
+  CK(cudaMemcpyAsync(&before, r->ds, sizeof before, cudaMemcpyDeviceToHost, c->x.st));
+  CK(cudaStreamSynchronize(c->x.st));
+  std::vector<std::pair<int, int>> ops;
+  for (int l = 0; l < r->nl; ++l) ops.push_back({OP_DT_LEVEL, l});
+  ops.push_back({OP_DT_FINAL, 0});
+  int rc = run_ops_now(r, c->x, ops);
+  if (rc) return rc;
   DevScalars after;
-  CK(cudaMemcpyAsync(&after, c->ds, sizeof after, cudaMemcpyDeviceToHost, c->st));
-  CK(cudaStreamSynchronize(c->st));
-  CK(cudaMemcpyAsync(&c->ds->dt, &before.dt, sizeof(double), cudaMemcpyHostToDevice, c->st));
-  CK(cudaStreamSynchronize(c->st));
+  CK(cudaMemcpy(&after, r->ds, sizeof after, cudaMemcpyDeviceToHost));
+  // keep the last coarse step taken (df_status reports it)
+  CK(cudaMemcpy(&r->ds->dt, &before.dt, sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(r->ds->dtl, before.dtl, sizeof before.dtl, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(r->ds->dtf, before.dtf, sizeof before.dtf, cudaMemcpyHostToDevice));
   leave(c);
-  c->launches += n;
   if (dt) *dt = after.dt;
   if (dt_level)
-    for (int l = 0; l < c->nl; ++l) dt_level[l] = after.dtlev[l];
+    for (int l = 0; l < r->nl; ++l) dt_level[l] = after.dtlev[l];
   return DF_OK;
 }
 
@@ -747,8 +1143,7 @@ int df_get_field(df_ctx* c, int level, int field, double* out) {
   if (!out) return fail(DF_EINVAL, "null output");
   DevGuard g(c->device);
   enter(c);
-  int r = c->prec == DF_FP64 ? do_io<double>(c, level, field, out, nullptr, 0)
-                             : do_io<float>(c, level, field, out, nullptr, 0);
+  int r = io(c->run, c->x.st, level, field, out, nullptr, 0, false, &c->x.launches);
   leave(c);
   return r;
 }
@@ -758,8 +1153,7 @@ int df_set_field(df_ctx* c, int level, int field, const double* in) {
   if (!in) return fail(DF_EINVAL, "null input");
   DevGuard g(c->device);
   enter(c);
-  int r = c->prec == DF_FP64 ? do_io<double>(c, level, field, nullptr, in, 0)
-                             : do_io<float>(c, level, field, nullptr, in, 0);
+  int r = io(c->run, c->x.st, level, field, nullptr, in, 0, false, &c->x.launches);
   leave(c);
   return r;
 }
@@ -769,8 +1163,7 @@ int df_get_full(df_ctx* c, int level, int field, double* out) {
   if (!out) return fail(DF_EINVAL, "null output");
   DevGuard g(c->device);
   enter(c);
-  int r = c->prec == DF_FP64 ? do_io<double>(c, level, field, out, nullptr, 1)
-                             : do_io<float>(c, level, field, out, nullptr, 1);
+  int r = io(c->run, c->x.st, level, field, out, nullptr, 1, false, &c->x.launches);
   leave(c);
   return r;
 }
@@ -780,29 +1173,27 @@ int df_set_full(df_ctx* c, int level, int field, const double* in) {
   if (!in) return fail(DF_EINVAL, "null input");
   DevGuard g(c->device);
   enter(c);
-  int r = c->prec == DF_FP64 ? do_io<double>(c, level, field, nullptr, in, 1)
-                             : do_io<float>(c, level, field, nullptr, in, 1);
+  int r = io(c->run, c->x.st, level, field, nullptr, in, 1, false, &c->x.launches);
   leave(c);
   return r;
 }
 
 size_t df_state_size(const df_ctx* c) {
-  if (!c) return 0;
-  return (size_t)c->nl * 5 * (size_t)c->L[0].v.nc;
+  if (!c || !c->run) return 0;
+  return (size_t)c->run->nl * 5 * (size_t)c->run->L[0].v.nc;
 }
 
 int df_get_state(df_ctx* c, double* out, double* t_out) {
   if (check_ctx(c)) return DF_EINVAL;
   if (!out) return fail(DF_EINVAL, "null output");
-  size_t nc = (size_t)c->L[0].v.nc;
+  Run* r = c->run;
+  size_t nc = (size_t)r->L[0].v.nc;
   DevGuard g(c->device);
   enter(c);
-  for (int l = 0; l < c->nl; ++l)
+  for (int l = 0; l < r->nl; ++l)
     for (int f = 0; f < 5; ++f) {
-      int r = c->prec == DF_FP64
-                  ? do_io<double>(c, l, f, out + (l * 5 + f) * nc, nullptr, 1, true)
-                  : do_io<float>(c, l, f, out + (l * 5 + f) * nc, nullptr, 1, true);
-      if (r) return r;
+      int rc = io(r, c->x.st, l, f, out + (l * 5 + f) * nc, nullptr, 1, true, &c->x.launches);
+      if (rc) return rc;
     }
   leave(c);
   if (t_out) return df_status(c, t_out, nullptr, nullptr);
@@ -812,73 +1203,62 @@ int df_get_state(df_ctx* c, double* out, double* t_out) {
 int df_set_state(df_ctx* c, const double* in, double t) {
   if (check_ctx(c)) return DF_EINVAL;
   if (!in) return fail(DF_EINVAL, "null input");
-  size_t nc = (size_t)c->L[0].v.nc;
+  Run* r = c->run;
+  size_t nc = (size_t)r->L[0].v.nc;
   DevGuard g(c->device);
   enter(c);
-  for (int l = 0; l < c->nl; ++l)
+  for (int l = 0; l < r->nl; ++l)
     for (int f = 0; f < 5; ++f) {
-      int r = c->prec == DF_FP64
-                  ? do_io<double>(c, l, f, nullptr, in + (l * 5 + f) * nc, 1, true)
-                  : do_io<float>(c, l, f, nullptr, in + (l * 5 + f) * nc, 1, true);
-      if (r) return r;
+      int rc = io(r, c->x.st, l, f, nullptr, in + (l * 5 + f) * nc, 1, true, &c->x.launches);
+      if (rc) return rc;
     }
   leave(c);
-  CK(cudaMemcpy(&c->ds->t, &t, sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(&r->ds->t, &t, sizeof(double), cudaMemcpyHostToDevice));
   int zero = 0;
-  CK(cudaMemcpy(&c->ds->unhealthy, &zero, sizeof(int), cudaMemcpyHostToDevice));
-  c->stepped = false;
+  CK(cudaMemcpy(&r->ds->unhealthy, &zero, sizeof(int), cudaMemcpyHostToDevice));
+  r->stepped = false;
   return DF_OK;
 }
 
 int df_prolong(df_ctx* c, int cl) {
   if (check_ctx(c, false)) return DF_EINVAL;
-  if (cl < 0 || cl + 1 >= c->nl) return fail(DF_EINVAL, "no level below %d", cl);
+  if (cl < 0 || cl + 1 >= c->run->nl) return fail(DF_EINVAL, "no level below %d", cl);
   DevGuard g(c->device);
   enter(c);
-  c->launches += c->prec == DF_FP64 ? launch_commup<double>(c->L[cl].v, c->L[cl + 1].v, c->st)
-                                    : launch_commup<float>(c->L[cl].v, c->L[cl + 1].v, c->st);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
+  int rc = run_ops_now(c->run, c->x, {{OP_COMMUP, cl}});
   leave(c);
-  return DF_OK;
+  return rc;
 }
 
 int df_restrict(df_ctx* c, int cl) {
   if (check_ctx(c)) return DF_EINVAL;
-  if (cl < 0 || cl + 1 >= c->nl) return fail(DF_EINVAL, "no level below %d", cl);
+  if (cl < 0 || cl + 1 >= c->run->nl) return fail(DF_EINVAL, "no level below %d", cl);
   DevGuard g(c->device);
   enter(c);
-  c->launches += c->prec == DF_FP64
-                     ? launch_commmean<double>(c->L[cl].v, c->L[cl + 1].v, c->P.band, c->st)
-                     : launch_commmean<float>(c->L[cl].v, c->L[cl + 1].v, c->P.band, c->st);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
+  int rc = run_ops_now(c->run, c->x, {{OP_COMMMEAN, cl}});
   leave(c);
-  return DF_OK;
+  return rc;
 }
 
 int df_fill_bc(df_ctx* c) {
   if (check_ctx(c)) return DF_EINVAL;
   DevGuard g(c->device);
   enter(c);
-  c->launches += c->prec == DF_FP64 ? launch_bc_fill<double>(c->L[0].v, c->P, c->st)
-                                    : launch_bc_fill<float>(c->L[0].v, c->P, c->st);
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->st));
+  int rc = run_ops_now(c->run, c->x, {{OP_BC, 0}});
   leave(c);
-  return DF_OK;
+  return rc;
 }
 
-long long df_kernel_launches(const df_ctx* c) { return c ? c->launches : -1; }
+long long df_kernel_launches(const df_ctx* c) { return c ? c->x.launches : -1; }
 
 int df_set_timing(df_ctx* c, int on) {
   if (!c) return fail(DF_EINVAL, "null context");
   DevGuard g(c->device);
-  harvest_timing(c);
-  c->timing = on != 0;
+  harvest_timing(c->x);
+  c->x.timing = on != 0;
   for (int k = 0; k < K_NKINDS; ++k) {
-    c->k_ms[k] = 0.0;
-    c->k_n[k] = 0;
+    c->x.k_ms[k] = 0.0;
+    c->x.k_n[k] = 0;
   }
   return DF_OK;
 }
@@ -886,9 +1266,9 @@ int df_set_timing(df_ctx* c, int on) {
 int df_kernel_time(df_ctx* c, int kind, double* ms, long long* launches) {
   if (!c || kind < 0 || kind >= K_NKINDS) return fail(DF_EINVAL, "bad timing query");
   DevGuard g(c->device);
-  harvest_timing(c);
-  if (ms) *ms = c->k_ms[kind];
-  if (launches) *launches = c->k_n[kind];
+  harvest_timing(c->x);
+  if (ms) *ms = c->x.k_ms[kind];
+  if (launches) *launches = c->x.k_n[kind];
   return DF_OK;
 }
 
@@ -903,10 +1283,7 @@ const char* df_kernel_name(int kind) {
 int df_debug_full_boxes(df_ctx* c, int on) {
   if (!c) return fail(DF_EINVAL, "null context");
   c->full_boxes = on != 0;
-  if (c->gexec) {
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
-  }
+  plan_invalidate(c->plan);
   return DF_OK;
 }
 
@@ -931,8 +1308,292 @@ int df_check_division(const double* a_host, const double* b_host, int n, double*
 int df_destroy(df_ctx* c) {
   if (!c) return DF_OK;
   DevGuard g(c->device);
-  cudaStreamSynchronize(c->st);
-  free_ctx(c);
+  cudaStreamSynchronize(c->x.st);
+  plan_free(c->plan);
+  exec_free(c->x);
+  run_free(c->run);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->x.st) cudaStreamDestroy(c->x.st);
+  delete c;
+  return DF_OK;
+}
+
+// ------------------------------------------------------------------------ pools
+
+size_t df_run_bytes(int n_levels, const int n[3], int G, int precision) {
+  if (!n || n_levels < 1 || G < 0) return 0;
+  return run_bytes(n_levels, n, G, precision);
+}
+
+int df_pool_create(df_pool** out, size_t budget, int precision, int device, void* stream) {
+  if (!out) return fail(DF_EINVAL, "null argument");
+  *out = nullptr;
+  if (precision != DF_FP64 && precision != DF_FP32_STATE)
+    return fail(DF_EINVAL, "unknown precision %d", precision);
+  CK(cudaSetDevice(device));
+  df_pool* p = new (std::nothrow) df_pool;
+  if (!p) return fail(DF_ENOMEM, "host allocation");
+  p->device = device;
+  p->prec = precision;
+  p->budget = budget;
+  p->user = (cudaStream_t)stream;
+  exec_init(p->x, device);
+  // every pool launch goes through the work-list kernel, so a run's arithmetic is
+  // the same alone in a pool and in any mix of runs (bitwise)
+  p->x.single_fast = false;
+  if (cudaStreamCreateWithFlags(&p->x.st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    delete p;
+    return fail(DF_ECUDA, "stream/event creation failed");
+  }
+  *out = p;
+  return DF_OK;
+}
+
+int df_pool_admit(df_pool* p, int n_levels, const int n[3], const double lo[3],
+                  const double hi[3], int G, const df_params* prm, int* slot_out) {
+  if (!p || !n || !lo || !hi || !slot_out) return fail(DF_EINVAL, "null argument");
+  if (check_params(prm)) return DF_EINVAL;
+  if (prm->xi_mode != 0) return fail(DF_EINVAL, "a pool steps every run with xi = 2");
+  int rc = check_shape(n_levels, n, lo, hi, G, p->prec);
+  if (rc) return rc;
+  size_t need = run_bytes(n_levels, n, G, p->prec);
+  if (p->used + need > p->budget)
+    return fail(DF_EBUSY, "HBM budget: %zu used + %zu needed > %zu", p->used, need, p->budget);
+  DevGuard g(p->device);
+  Run* r = nullptr;
+  rc = run_create(&r, n_levels, n, lo, hi, G, p->prec);
+  if (rc) return rc;
+  enter(p);
+  rc = DF_OK;
+  p->x.launches += run_set_params(r, prm, p->x.st, &rc);
+  cudaError_t e = cudaStreamSynchronize(p->x.st);
+  leave(p);
+  if (rc || e != cudaSuccess) {
+    run_free(r);
+    return rc ? rc : fail(DF_ECUDA, "admission: %s", cudaGetErrorString(e));
+  }
+  int slot = -1;
+  for (size_t i = 0; i < p->slots.size(); ++i)
+    if (!p->slots[i]) {
+      slot = (int)i;
+      break;
+    }
+  if (slot < 0) {
+    slot = (int)p->slots.size();
+    p->slots.push_back(nullptr);
+  }
+  p->slots[slot] = r;
+  p->used += r->bytes;
+  plan_invalidate(p->plan);
+  *slot_out = slot;
+  return DF_OK;
+}
+
+int df_pool_release(df_pool* p, int slot) {
+  if (!p || slot < 0 || slot >= (int)p->slots.size() || !p->slots[slot])
+    return fail(DF_EINVAL, "no run in slot %d", slot);
+  DevGuard g(p->device);
+  cudaStreamSynchronize(p->x.st);
+  p->used -= p->slots[slot]->bytes;
+  run_free(p->slots[slot]);
+  p->slots[slot] = nullptr;
+  plan_invalidate(p->plan);
+  return DF_OK;
+}
+
+int df_pool_step(df_pool* p, int n) {
+  if (!p) return fail(DF_EINVAL, "null pool");
+  if (n < 0) return fail(DF_EINVAL, "negative step count");
+  std::vector<Run*> runs;
+  for (Run* r : p->slots)
+    if (r) runs.push_back(r);
+  if (runs.empty() || n == 0) return DF_OK;
+  DevGuard g(p->device);
+  int rc = DF_OK;
+  if (!p->plan.valid) rc = build_plan(p->plan, runs, p->prec, 0);
+  if (rc) return rc;
+  enter(p);
+  rc = step_plan(p->plan, p->x, p->prec, n);
+  leave(p);
+  for (Run* r : runs) r->stepped = true;
+  return rc;
+}
+
+int df_pool_query(df_pool* p, double* out, int max_slots) {
+  if (!p || !out) return fail(DF_EINVAL, "null argument");
+  DevGuard g(p->device);
+  CK(cudaStreamSynchronize(p->x.st));
+  int ns = std::min((int)p->slots.size(), max_slots);
+  std::vector<DevScalars> h(ns);
+  for (int i = 0; i < ns; ++i)
+    if (p->slots[i])
+      CK(cudaMemcpyAsync(&h[i], p->slots[i]->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                         p->x.st));
+  CK(cudaStreamSynchronize(p->x.st));
+  for (int i = 0; i < ns; ++i) {
+    double* o = out + 6 * i;
+    if (!p->slots[i]) {
+      for (int k = 0; k < 6; ++k) o[k] = NAN;
+      continue;
+    }
+    o[0] = h[i].F[0];
+    o[1] = h[i].F[1];
+    o[2] = h[i].F[2];
+    o[3] = h[i].t;
+    o[4] = h[i].dt;
+    o[5] = h[i].unhealthy;
+  }
+  return ns;
+}
+
+int df_pool_get_field(df_pool* p, int slot, int level, int field, double* out) {
+  if (!p || slot < 0 || slot >= (int)p->slots.size() || !p->slots[slot] || !out)
+    return fail(DF_EINVAL, "no run in slot %d", slot);
+  DevGuard g(p->device);
+  enter(p);
+  int rc = io(p->slots[slot], p->x.st, level, field, out, nullptr, 0, false, &p->x.launches);
+  leave(p);
+  return rc;
+}
+
+int df_pool_info(df_pool* p, int* active, size_t* used, size_t* budget, long long* launches) {
+  if (!p) return fail(DF_EINVAL, "null pool");
+  int a = 0;
+  for (Run* r : p->slots)
+    if (r) ++a;
+  if (active) *active = a;
+  if (used) *used = p->used;
+  if (budget) *budget = p->budget;
+  if (launches) *launches = p->x.launches;
+  return DF_OK;
+}
+
+int df_pool_set_tiles(df_pool* p, const int* blocks_per_sm) {
+  if (!p || !blocks_per_sm) return fail(DF_EINVAL, "null argument");
+  for (int o = 0; o < OP_COUNT; ++o)
+    if (blocks_per_sm[o] < 1 || blocks_per_sm[o] > 64) return fail(DF_EINVAL, "bad tile setting");
+  for (int o = 0; o < OP_COUNT; ++o) p->x.bps[o] = blocks_per_sm[o];
+  plan_invalidate(p->plan);
+  return DF_OK;
+}
+
+int df_pool_autotune(df_pool* p, int* blocks_per_sm_out) {
+  if (!p) return fail(DF_EINVAL, "null pool");
+  std::vector<Run*> runs;
+  for (Run* r : p->slots)
+    if (r) runs.push_back(r);
+  if (runs.empty()) return fail(DF_EINVAL, "empty pool");
+  DevGuard g(p->device);
+  CK(cudaStreamSynchronize(p->x.st));
+  // tuning steps run on the live state, which is restored afterwards
+  std::vector<std::vector<char>> snap(runs.size());
+  std::vector<DevScalars> snap_ds(runs.size());
+  std::vector<long long> snap_pos(runs.size());
+  for (size_t i = 0; i < runs.size(); ++i) {
+    Run* r = runs[i];
+    size_t plane = plane_bytes((size_t)r->L[0].v.nc, r->esz);
+    snap[i].resize(plane * 5 * r->nl);
+    for (int l = 0; l < r->nl; ++l)
+      CK(cudaMemcpy(snap[i].data() + plane * 5 * l, r->L[l].mem, plane * 5,
+                    cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&snap_ds[i], r->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&snap_pos[i], r->ring_pos, sizeof(long long), cudaMemcpyDeviceToHost));
+  }
+  int rc = build_plan(p->plan, runs, p->prec, 0);
+  if (rc) return rc;
+  const int cand[] = {1, 2, 4, 8, 16, 32};
+  const int nc = (int)(sizeof cand / sizeof cand[0]);
+  double best_ms[OP_COUNT];
+  int best[OP_COUNT];
+  for (int o = 0; o < OP_COUNT; ++o) {
+    best_ms[o] = INFINITY;
+    best[o] = p->x.bps[o];
+  }
+  const unsigned char* items = (const unsigned char*)p->plan.d_items;
+  std::vector<cudaEvent_t> ev(2 * p->plan.launches.size());
+  for (auto& e : ev) cudaEventCreate(&e);
+  for (int ci = 0; ci < nc; ++ci) {
+    for (int rep = 0; rep < 2; ++rep)
+      for (size_t i = 0; i < p->plan.launches.size(); ++i) {
+        const LaunchDesc& L = p->plan.launches[i];
+        unsigned grid = (unsigned)p->x.sm_count * (unsigned)cand[ci];
+        if (rep == 1) cudaEventRecord(ev[2 * i], p->x.st);
+        // the multi-item path is the one tuned (single items use one block per chunk)
+        if (p->prec == DF_FP64)
+          launch_batch<double>(L.op, L.d, (const Item<double>*)(items + L.item0 * p->plan.item_size),
+                               p->plan.d_starts + L.start0, L.nitems, L.nchunks, grid, p->x.st,
+                               nullptr);
+        else
+          launch_batch<float>(L.op, L.d, (const Item<float>*)(items + L.item0 * p->plan.item_size),
+                              p->plan.d_starts + L.start0, L.nitems, L.nchunks, grid, p->x.st,
+                              nullptr);
+        if (rep == 1) cudaEventRecord(ev[2 * i + 1], p->x.st);
+      }
+    CK(cudaStreamSynchronize(p->x.st));
+    double per_op[OP_COUNT] = {};
+    for (size_t i = 0; i < p->plan.launches.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+      per_op[p->plan.launches[i].op] += ms;
+    }
+    for (int o = 0; o < OP_COUNT; ++o)
+      if (per_op[o] > 0 && per_op[o] < best_ms[o]) {
+        best_ms[o] = per_op[o];
+        best[o] = cand[ci];
+      }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  for (int o = 0; o < OP_COUNT; ++o) p->x.bps[o] = best[o];
+  if (blocks_per_sm_out)
+    for (int o = 0; o < OP_COUNT; ++o) blocks_per_sm_out[o] = best[o];
+  for (size_t i = 0; i < runs.size(); ++i) {
+    Run* r = runs[i];
+    size_t plane = plane_bytes((size_t)r->L[0].v.nc, r->esz);
+    for (int l = 0; l < r->nl; ++l)
+      CK(cudaMemcpy(r->L[l].mem, snap[i].data() + plane * 5 * l, plane * 5,
+                    cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(r->ds, &snap_ds[i], sizeof(DevScalars), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(r->ring_pos, &snap_pos[i], sizeof(long long), cudaMemcpyHostToDevice));
+  }
+  plan_invalidate(p->plan);
+  return DF_OK;
+}
+
+int df_pool_set_timing(df_pool* p, int on) {
+  if (!p) return fail(DF_EINVAL, "null pool");
+  DevGuard g(p->device);
+  harvest_timing(p->x);
+  p->x.timing = on != 0;
+  for (int k = 0; k < K_NKINDS; ++k) {
+    p->x.k_ms[k] = 0.0;
+    p->x.k_n[k] = 0;
+  }
+  return DF_OK;
+}
+
+int df_pool_kernel_time(df_pool* p, int kind, double* ms, long long* launches) {
+  if (!p || kind < 0 || kind >= K_NKINDS) return fail(DF_EINVAL, "bad timing query");
+  DevGuard g(p->device);
+  harvest_timing(p->x);
+  if (ms) *ms = p->x.k_ms[kind];
+  if (launches) *launches = p->x.k_n[kind];
+  return DF_OK;
+}
+
+int df_pool_destroy(df_pool* p) {
+  if (!p) return DF_OK;
+  DevGuard g(p->device);
+  cudaStreamSynchronize(p->x.st);
+  plan_free(p->plan);
+  exec_free(p->x);
+  for (Run* r : p->slots) run_free(r);
+  if (p->ev_in) cudaEventDestroy(p->ev_in);
+  if (p->ev_out) cudaEventDestroy(p->ev_out);
+  if (p->x.st) cudaStreamDestroy(p->x.st);
+  delete p;
   return DF_OK;
 }
 

@@ -73,53 +73,92 @@ struct DevScalars {
   int pad;
 };
 
-// ---- launchers (kernels.cu); T = double or float, all asynchronous on `st`.
-// Every launcher returns the number of kernels it launched.
-// dt: device pointer to this level's step in T (DevScalars::dtl or ::dtf)
-template <class T> int launch_source(const LevelView& L, const Box& b, const Scratch& S,
-                                     const T* dt, int write_pi, double gm1, const Phys& P,
-                                     cudaStream_t st);
-template <class T> int launch_compress_lum(const LevelView& L, const Box& b, const Scratch& S,
-                                           const T* dt, const Phys& P, int do_ss3, int do_lum,
-                                           int do_eps, cudaStream_t st);
-template <class T> int launch_diffuse(const LevelView& L, const Box& b, const Scratch& S,
-                                      const T* dt, const Phys& P, cudaStream_t st);
-template <class T> int launch_frontier_diff(const LevelView& L, const Scratch& S, const T* dt,
-                                            const Phys& P, cudaStream_t st);
-template <class T> int launch_tprep(const LevelView& L, const Box& b, const Scratch& S,
-                                    const Phys& P, cudaStream_t st);
-template <class T> int launch_tflux(const LevelView& L, const Box& b, const Scratch& S, int d,
-                                    const T* dt, const Phys& P, cudaStream_t st);
-template <class T> int launch_tfrontier(const LevelView& L, const Scratch& S, int d,
-                                        cudaStream_t st);
-template <class T> int launch_tmom(const LevelView& L, const Box& b, const Scratch& S, int d,
-                                   const T* dt, const Phys& P, cudaStream_t st);
-template <class T> int launch_tupdate(const LevelView& L, const Box& b, const Scratch& S, int d,
-                                      cudaStream_t st);
-
-// kernel kinds for the timing hook (df_kernel_time / df_kernel_name)
-enum KernelKind {
-  K_BC = 0, K_SOURCE, K_COMPRESS, K_DIFFUSE, K_FRONTIER_DIFF, K_TPREP, K_TFLUX, K_TFRONTIER,
-  K_TMOM, K_TUPDATE, K_VREC_SOURCE, K_COMMUP, K_COMMMEAN, K_DT, K_FORCE, K_OTHER, K_NKINDS
+// per-level geometry constants in the kernels' arithmetic type (no FP64 work in
+// FP32 kernels: GB300's FP64 pipe is 1/64 of its FP32 rate)
+template <class T>
+struct Geo {
+  T inv_dx[3], area[3], dcoef[3], inv_vol;
 };
-template <class T> int launch_vrec_source(const LevelView& L, const Box& b, const Scratch& S,
-                                          const T* dt, double gm1, const Phys& P,
-                                          cudaStream_t st);
-template <class T> int launch_bc_fill(const LevelView& L, const Phys& P, cudaStream_t st);
-template <class T> int launch_commup(const LevelView& C, const LevelView& F, cudaStream_t st);
-template <class T> int launch_commmean(const LevelView& C, const LevelView& F, int band,
-                                       cudaStream_t st);
-template <class T> int launch_dt_level(const LevelView& L, int level, const Phys& P,
-                                       DevScalars* ds, cudaStream_t st);
-int launch_dt_finalize(DevScalars* ds, int n_levels, const double* prod, double dt_fixed,
-                       cudaStream_t st);
-template <class T> int launch_force_level(const LevelView& L, const Phys& P, double* partials,
-                                          int offset, cudaStream_t st);
+
+template <class T>
+inline Geo<T> make_geo(const LevelView& L) {
+  Geo<T> g;
+  for (int d = 0; d < 3; ++d) {
+    g.inv_dx[d] = (T)L.inv_dx[d];
+    g.area[d] = (T)L.area[d];
+    g.dcoef[d] = (T)L.dcoef[d];
+  }
+  g.inv_vol = (T)L.inv_vol;
+  return g;
+}
+
+// uniform background of Sec. 3.4 in the kernels' arithmetic type
+template <class T>
+struct Bg {
+  T rho0, e0, eps0, V[3];
+};
+
+template <class T>
+inline Bg<T> make_bg(const Phys& P) {
+  Bg<T> b;
+  b.rho0 = (T)P.rho0;
+  b.e0 = (T)P.e0;
+  b.eps0 = (T)(P.e0 / P.rho0);
+  for (int d = 0; d < 3; ++d) b.V[d] = (T)P.V[d];
+  return b;
+}
+
+// constants of the Eq. 55 finalisation of one run
+struct DtFinal {
+  double prod[16];       // prod_{m<l} xi_m
+  double diff_lim[16];   // explicit-diffusion limit of each level
+  double cfl_dx[16][3];  // cfl * dx_d (0 when hydro is off)
+};
+
+// Ops of the work-list kernel.  Every launch runs one op over a list of work
+// items; an item is one (run, level) with its box and its own parameters.
+enum Op {
+  OP_SOURCE = 0, OP_COMPRESS, OP_FRONTIER_DIFF, OP_DIFFUSE, OP_TPREP, OP_TFLUX, OP_TFRONTIER,
+  OP_TMOM, OP_TUPDATE, OP_VREC, OP_BC, OP_COMMUP, OP_COMMMEAN, OP_ZERO_ACC, OP_DT_LEVEL,
+  OP_DT_FINAL, OP_FORCE_LEVEL, OP_FORCE_FINAL, OP_TIME, OP_COUNT
+};
+
+enum ItemFlags {
+  FL_WRITE_PI = 1, FL_SS3 = 2, FL_LUM = 4, FL_EPS = 8, FL_DFR = 16, FL_HYDRO = 32
+};
+
+// One work item.  Plain data, copied to shared memory by the kernel; size a
+// multiple of 16 bytes.
+template <class T>
+struct __align__(16) Item {
+  LevelView L;          // the level (coarse level of CommUp / CommMean)
+  LevelView F;          // fine level of CommUp / CommMean
+  Scratch S;            // the run's scratch
+  Box b;                // box of stencil ops
+  Bg<T> bg;
+  Geo<T> g;
+  const void* dt;       // this level's step, T
+  DevScalars* ds;       // the run's scalars
+  const DtFinal* fin;   // OP_DT_FINAL constants
+  double* partials;     // force partials (this level's first, or the run's for the final sum)
+  double* ring;         // force history
+  long long* ring_pos;
+  T gm1, lum, chi;
+  double gg, rho0d, e0d, V[3], dt_fixed;
+  int ring_cap, npart, level, band, flags, bc_lo, bc_hi;
+  unsigned count;       // index-space size of the item
+};
+
+// ---- kernels.cu: all asynchronous on `st`; return the number of kernels launched.
+// host_item (nullable): host copy of the item when nitems == 1; such a launch
+// passes the item by value and uses one block per chunk
+template <class T>
+int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, int nitems,
+                 unsigned nchunks, unsigned grid, cudaStream_t st, const Item<T>* host_item);
+int op_chunk_elems(int op);
+unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const Box& b);
 int force_partials_per_level(const LevelView& L);
 int launch_force_weights(const LevelView& L, const Phys& P, cudaStream_t st);
-int launch_force_finalize(const double* partials, int n, DevScalars* ds, double* ring,
-                          int ring_cap, long long* ring_pos, cudaStream_t st);
-int launch_time_advance(DevScalars* ds, cudaStream_t st);
 template <class T> int launch_init_uniform(const LevelView& L, const Phys& P, cudaStream_t st);
 template <class T> int launch_static_fields(const LevelView& L, const Phys& P, double lum_sigma,
                                             double* wsum, double* partials, cudaStream_t st);
@@ -130,6 +169,12 @@ template <class T> int launch_pack_active(const LevelView& L, int field, double*
                                           double bgv, cudaStream_t st);
 template <class T> int launch_unpack_active(const LevelView& L, int field, const double* in,
                                             int full, double bgv, cudaStream_t st);
+
+// kernel kinds for the timing hook (df_kernel_time / df_kernel_name)
+enum KernelKind {
+  K_BC = 0, K_SOURCE, K_COMPRESS, K_DIFFUSE, K_FRONTIER_DIFF, K_TPREP, K_TFLUX, K_TFRONTIER,
+  K_TMOM, K_TUPDATE, K_VREC_SOURCE, K_COMMUP, K_COMMMEAN, K_DT, K_FORCE, K_OTHER, K_NKINDS
+};
 
 // hot-path FP64 division versus IEEE division (device arrays; max_ulp zeroed by caller)
 int launch_hdiv_check(const double* a, const double* b, int n, double* max_ulp, cudaStream_t st);

@@ -81,41 +81,6 @@ __device__ __forceinline__ T upwind(const T* __restrict__ q, int c, int st, T u,
   return a - T(0.5) * (T(1) + cour) * sr;
 }
 
-// per-level geometry constants in the kernels' arithmetic type (no FP64 work in
-// FP32 kernels: GB300's FP64 pipe is 1/64 of its FP32 rate)
-template <class T>
-struct Geo {
-  T inv_dx[3], area[3], dcoef[3], inv_vol;
-};
-
-template <class T>
-Geo<T> make_geo(const LevelView& L) {
-  Geo<T> g;
-  for (int d = 0; d < 3; ++d) {
-    g.inv_dx[d] = (T)L.inv_dx[d];
-    g.area[d] = (T)L.area[d];
-    g.dcoef[d] = (T)L.dcoef[d];
-  }
-  g.inv_vol = (T)L.inv_vol;
-  return g;
-}
-
-// uniform background in the kernels' arithmetic type
-template <class T>
-struct Bg {
-  T rho0, e0, eps0, V[3];
-};
-
-template <class T>
-Bg<T> make_bg(const Phys& P) {
-  Bg<T> b;
-  b.rho0 = (T)P.rho0;
-  b.e0 = (T)P.e0;
-  b.eps0 = (T)(P.e0 / P.rho0);
-  for (int d = 0; d < 3; ++d) b.V[d] = (T)P.V[d];
-  return b;
-}
-
 inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
 // coarse frontier face test: returns side (0/1) and the slot, or -1
@@ -135,11 +100,11 @@ __device__ __forceinline__ int coarse_frontier(const LevelView& L, int d, int f0
 // ------------------------------------------------------------------ source S
 // S(h) of Eq. 15: v_d -= h [ (p_c - p_m)/(dx rho_face) + (Phi_c - Phi_m)/dx ]
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_source(LevelView L, Box b, Scratch S,
+__device__ __forceinline__ void el_source(const LevelView& L, const Box& b, const Scratch& S,
                                                    const T* __restrict__ dtp, int write_pi, T gm1,
-                                                   Bg<T> bg, Geo<T> g) {
+                                                   const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, tid, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const T* __restrict__ e = (const T*)L.q[F_E];
   const T* __restrict__ phi = (const T*)L.phi;
@@ -167,12 +132,12 @@ __global__ void __launch_bounds__(kBlock) k_source(LevelView L, Box b, Scratch S
 
 // ------------------------------------------------- SubStep3 + luminosity + e/rho
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_compress_lum(LevelView L, Box b, Scratch S,
+__device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b, const Scratch& S,
                                                          const T* __restrict__ dtp, T gm1,
                                                          T lum, int do_ss3, int do_lum,
-                                                         int do_eps, Bg<T> bg, Geo<T> g) {
+                                                         int do_eps, const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, tid, i, j, k)) return;
   const T dt = dtp[0];
   const int c = cidx(L, i, j, k);
   T* e = (T*)L.q[F_E];
@@ -210,11 +175,11 @@ __device__ __forceinline__ T diff_flux(const LevelView& L, const Geo<T>& g,
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_diffuse(LevelView L, Box b, Scratch S,
+__device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, const Scratch& S,
                                                     const T* __restrict__ dtp, T chi, T rho0,
-                                                    int dfr, Geo<T> g) {
+                                                    int dfr, const Geo<T>& g, unsigned tid) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, tid, i, j, k)) return;
   if (i < 1 || j < 1 || k < 1 || i >= L.s[0] - 1 || j >= L.s[1] - 1 || k >= L.s[2] - 1) return;
   const T dt = dtp[0];
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
@@ -274,11 +239,11 @@ __device__ __forceinline__ bool slot_of(const LevelView& L, long long t, int sid
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_frontier_diff(LevelView L, Scratch S,
+__device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scratch& S,
                                                           const T* __restrict__ dtp, T chi,
-                                                          T rho0, int dfr, Geo<T> g) {
+                                                          T rho0, int dfr, const Geo<T>& g, unsigned tid) {
   int side, a, b;
-  if (!slot_of(L, blockIdx.x * (long long)kBlock + threadIdx.x, 0, 6, side, a, b)) return;
+  if (!slot_of(L, tid, 0, 6, side, a, b)) return;
   const T dt = dtp[0];
   const int d = side >> 1;
   const int t1 = d == 0 ? 1 : 0;
@@ -299,9 +264,9 @@ __global__ void __launch_bounds__(kBlock) k_frontier_diff(LevelView L, Scratch S
 
 // --------------------------------------------------------------- transport
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_tprep(LevelView L, Box b, Scratch S, Bg<T> bg) {
+__device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const Scratch& S, const Bg<T>& bg, unsigned tid) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, tid, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
@@ -323,10 +288,10 @@ __global__ void __launch_bounds__(kBlock) k_tprep(LevelView L, Box b, Scratch S,
 // the sweep direction is a template parameter: every per-axis constant is then a
 // fixed kernel-parameter operand instead of a dynamically indexed load
 template <class T, int d>
-__global__ void __launch_bounds__(kBlock) k_tflux(LevelView L, Box b, Scratch S,
-                                                  const T* __restrict__ dtp, Bg<T> bg, Geo<T> g) {
+__device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const Scratch& S,
+                                                  const T* __restrict__ dtp, const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   T Fv = T(0), Ev = T(0);
@@ -349,9 +314,9 @@ __global__ void __launch_bounds__(kBlock) k_tflux(LevelView L, Box b, Scratch S,
 
 // child frontier capture of the transport fluxes of axis d (sides 2d, 2d+1)
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_tfrontier(LevelView L, Scratch S, int d) {
+__device__ __forceinline__ void el_tfrontier(const LevelView& L, const Scratch& S, int d, unsigned tid) {
   int side, a, b;
-  if (!slot_of(L, blockIdx.x * (long long)kBlock + threadIdx.x, 2 * d, 2, side, a, b)) return;
+  if (!slot_of(L, tid, 2 * d, 2, side, a, b)) return;
   const int t1 = d == 0 ? 1 : 0;
   const int slot = b * (L.n[t1] >> 1) + a;
   double* accF = L.acc + (side * 3 + 0) * L.acc_slots + slot;
@@ -373,10 +338,10 @@ __global__ void __launch_bounds__(kBlock) k_tfrontier(LevelView L, Scratch S, in
 // staggered momentum fluxes of sweep d
 // staggered momentum fluxes of sweep d (deviation: P - V_m rho0 V_d A dt)
 template <class T, int d>
-__global__ void __launch_bounds__(kBlock) k_tmom(LevelView L, Box b, Scratch S,
-                                                 const T* __restrict__ dtp, Bg<T> bg, Geo<T> g) {
+__device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const Scratch& S,
+                                                 const T* __restrict__ dtp, const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const T dt = dtp[0];
@@ -407,9 +372,9 @@ __global__ void __launch_bounds__(kBlock) k_tmom(LevelView L, Box b, Scratch S,
 }
 
 template <class T, int d>
-__global__ void __launch_bounds__(kBlock) k_tupdate(LevelView L, Box b, Scratch S, Geo<T> g) {
+__device__ __forceinline__ void el_tupdate(const LevelView& L, const Box& b, const Scratch& S, const Geo<T>& g, unsigned tid) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const int st = L.st[d];
@@ -450,11 +415,11 @@ __global__ void __launch_bounds__(kBlock) k_tupdate(LevelView L, Box b, Scratch 
 
 // velocity from the transported momenta, then the second half kick S(dt/2)
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_vrec_source(LevelView L, Box b, Scratch S,
-                                                        const T* __restrict__ dtp, T gm1, Bg<T> bg,
-                                                        Geo<T> g) {
+__device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b, const Scratch& S,
+                                                        const T* __restrict__ dtp, T gm1, const Bg<T>& bg,
+                                                        const Geo<T>& g, unsigned tid) {
   int i, j, k;
-  if (!decode(b, blockIdx.x * kBlock + threadIdx.x, i, j, k)) return;
+  if (!decode(b, tid, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const T* __restrict__ e = (const T*)L.q[F_E];
   const T* __restrict__ phi = (const T*)L.phi;
@@ -476,10 +441,10 @@ __global__ void __launch_bounds__(kBlock) k_vrec_source(LevelView L, Box b, Scra
 
 // ------------------------------------------------------ level-0 boundaries
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_bc_axis(LevelView L, int d, int type_lo, int type_hi,
-                                                    T rho0, T e0, T V0, T V1, T V2) {
+__device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_lo, int type_hi,
+                                                    T rho0, T e0, T V0, T V1, T V2, unsigned tid) {
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  long long t = tid;
   const int G = L.G, n = L.n[d];
   long long per = (long long)L.s[t1] * L.s[t2];
   long long total = per * 2 * G * 5;
@@ -558,10 +523,10 @@ __global__ void __launch_bounds__(kBlock) k_bc_axis(LevelView L, int d, int type
 // 1 per (z,y) offset -- the same arithmetic per fine element as interpolating each
 // one alone, with the slopes computed once.
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_commup(LevelView C, LevelView F) {
+__device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F, unsigned tid) {
   const int G = F.G, hg = G >> 1;
   const int nh0 = (F.n[0] >> 1) + G, nh1 = (F.n[1] >> 1) + G, nh2 = (F.n[2] >> 1) + G;
-  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+  long long t = tid;
   long long per = (long long)nh0 * nh1 * nh2;
   if (t >= 5 * per) return;
   const int f = (int)(t / per);
@@ -640,8 +605,8 @@ __device__ __forceinline__ bool in_band(const LevelView& F, int band, int a0, in
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_commmean(LevelView C, LevelView F, int band) {
-  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
+__device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView& F, int band, unsigned tid) {
+  long long t = tid;
   int h0 = F.n[0] >> 1, h1 = F.n[1] >> 1, h2 = F.n[2] >> 1;
   if (t >= (long long)h0 * h1 * h2) return;
   int a = (int)(t % h0), b = (int)((t / h0) % h1), cc = (int)(t / ((long long)h0 * h1));
@@ -711,16 +676,28 @@ __device__ __forceinline__ double warp_max(double v) {
 // cfl dx_d / max(cs + |v_d|): the kernel reduces the per-axis maxima (one division
 // per level instead of three per cell).  Also flags NaN, rho <= 0 or e <= 0.
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_dt_level(LevelView L, int level, double gg,
-                                                     int hydro, DevScalars* ds, double rho0,
-                                                     double e0, double V0, double V1,
-                                                     double V2) {
-  __shared__ double sm[3][kBlock / 32];
+__device__ __forceinline__ T warp_max_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Per-level Courant limit: min over active cells and axes of cfl dx_d / (cs + |v_d|).
+// Division is correctly rounded and monotone, so that minimum equals
+// cfl dx_d / max(cs + |v_d|): the kernel reduces the per-axis maxima (one division
+// per level instead of three per cell); a maximum is exact in any precision, so it
+// is taken in the state's type and widened once per block.  Also flags NaN,
+// rho <= 0 or e <= 0.
+template <class T>
+__device__ __forceinline__ void el_dt_level(const LevelView& L, int level, double gg, int hydro,
+                                            DevScalars* ds, double rho0, double e0, double V0,
+                                            double V1, double V2, unsigned tid) {
+  __shared__ T sm[3][kBlock / 32];
   __shared__ int bad_s;
   if (threadIdx.x == 0) bad_s = 0;
   __syncthreads();
-  long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
-  double mx[3] = {0.0, 0.0, 0.0};
+  long long t = tid;
+  T mx[3] = {T(0), T(0), T(0)};
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
   if (t < na) {
     int i = L.G + (int)(t % L.n[0]);
@@ -739,38 +716,34 @@ __global__ void __launch_bounds__(kBlock) k_dt_level(LevelView L, int level, dou
       for (int d = 0; d < 3; ++d) {
         const T* v = (const T*)L.q[F_VX + d];
         T v0 = fabs(Vb[d] + v[c]), v1 = fabs(Vb[d] + v[c + L.st[d]]);
-        mx[d] = (double)(cs + (v0 > v1 ? v0 : v1));
+        mx[d] = cs + (v0 > v1 ? v0 : v1);
       }
     }
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    double v = warp_max(mx[d]);
+    T v = warp_max_t(mx[d]);
     if ((threadIdx.x & 31) == 0) sm[d][threadIdx.x >> 5] = v;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      double v = threadIdx.x < kBlock / 32 ? sm[d][threadIdx.x] : 0.0;
-      v = warp_max(v);
+      T v = threadIdx.x < kBlock / 32 ? sm[d][threadIdx.x] : T(0);
+      v = warp_max_t(v);
       // non-negative doubles order like their bit patterns (NaN is caught above)
-      if (threadIdx.x == 0 && v > 0.0)
-        atomicMax(&ds->dtmin[3 * level + d], (unsigned long long)__double_as_longlong(v));
+      if (threadIdx.x == 0 && v > T(0))
+        atomicMax(&ds->dtmin[3 * level + d],
+                  (unsigned long long)__double_as_longlong((double)v));
     }
     if (threadIdx.x == 0 && bad_s) atomicOr(&ds->unhealthy, 1);
   }
 }
 
-struct DtFinal {
-  double prod[16];
-  double diff_lim[16];
-  double cfl_dx[16][3];
-};
-
 // Eq. 55: dt = min_l dt_l prod_{m<l} xi_m; resets the per-level maxima
-__global__ void k_dt_finalize(DevScalars* ds, int n_levels, DtFinal fin, double dt_fixed) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void el_dt_finalize(DevScalars* ds, int n_levels, const DtFinal& fin,
+                                               double dt_fixed) {
+  if (threadIdx.x != 0) return;
   double dt = INFINITY;
   for (int l = 0; l < n_levels; ++l) {
     double lim = fin.diff_lim[l];
@@ -794,26 +767,30 @@ __global__ void k_dt_finalize(DevScalars* ds, int n_levels, DtFinal fin, double 
   }
 }
 
-__global__ void k_time_advance(DevScalars* ds) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) ds->t += ds->dt;
+__device__ __forceinline__ void el_time_advance(DevScalars* ds) {
+  if (threadIdx.x == 0) ds->t += ds->dt;
 }
 
 // ------------------------------------------------------------------ force
-// Eq. 18 on one level: F += (rho - rho0) w_c r_c over uncovered active cells, with
-// the static weight w_c = GM V_c / (r^2 + eps^2)^(3/2) precomputed in FP64.  Each
-// thread accumulates kForceCells cells (strided by the block size), then a fixed
-// warp-shuffle tree and the 8 warp sums give one partial per block.
-constexpr int kForceCells = 4;
+// Eq. 18 on one level: F += (rho - rho0) w_c over uncovered active cells, with the
+// static FP64 weight vectors w_c = GM V_c r_c / (r^2 + eps^2)^(3/2) precomputed
+// (x, y and z components in three planes of fw).  Each thread accumulates
+// kForceCells cells (strided by the block size) in FP64, then a fixed warp-shuffle
+// tree and the 8 warp sums give one partial per block.
+constexpr int kForceCells = 8;
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_force_level(LevelView L, const double* __restrict__ fw,
-                                                        double* partials) {
+__device__ __forceinline__ void el_force_level(const LevelView& L, const double* __restrict__ fw,
+                                               double* partials, unsigned tid) {
   __shared__ double sw[3][kBlock / 32];
-  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  const long long na = (long long)L.n[0] * L.n[1] * L.n[2];
+  const double* fx = fw;
+  const double* fy = fw + na;
+  const double* fz = fw + 2 * na;
   double f[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int u = 0; u < kForceCells; ++u) {
-    long long t = (long long)blockIdx.x * kBlock * kForceCells + u * kBlock + threadIdx.x;
+    long long t = (long long)(tid / kBlock) * kBlock * kForceCells + u * kBlock + threadIdx.x;
     if (t >= na) break;
     int ai = (int)(t % L.n[0]);
     int aj = (int)((t / L.n[0]) % L.n[1]);
@@ -822,11 +799,10 @@ __global__ void __launch_bounds__(kBlock) k_force_level(LevelView L, const doubl
                    aj >= L.coff[1] && aj < L.coff[1] + (L.cn[1] >> 1) && ak >= L.coff[2] &&
                    ak < L.coff[2] + (L.cn[2] >> 1);
     if (covered) continue;
-    int c = ((L.G + ak) * L.s[1] + L.G + aj) * L.s[0] + L.G + ai;
-    double mw = (double)((const T*)L.q[F_RHO])[c] * fw[t];
-    f[0] += mw * (L.lo[0] + (ai + 0.5) * L.dx[0]);
-    f[1] += mw * (L.lo[1] + (aj + 0.5) * L.dx[1]);
-    f[2] += mw * (L.lo[2] + (ak + 0.5) * L.dx[2]);
+    double dr = (double)((const T*)L.q[F_RHO])[((L.G + ak) * L.s[1] + L.G + aj) * L.s[0] + L.G + ai];
+    f[0] += dr * fx[t];
+    f[1] += dr * fy[t];
+    f[2] += dr * fz[t];
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -839,7 +815,7 @@ __global__ void __launch_bounds__(kBlock) k_force_level(LevelView L, const doubl
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < kBlock / 32; ++w) s += sw[threadIdx.x][w];
-    partials[3 * blockIdx.x + threadIdx.x] = s;
+    partials[3 * (tid / kBlock) + threadIdx.x] = s;
   }
 }
 
@@ -856,45 +832,47 @@ __global__ void __launch_bounds__(kBlock) k_force_weights(LevelView L, double GM
   double y = L.lo[1] + (aj + 0.5) * L.dx[1];
   double z = L.lo[2] + (ak + 0.5) * L.dx[2];
   double r2 = x * x + y * y + z * z + eps * eps;
-  fw[t] = GM * L.vol / (r2 * sqrt(r2));
+  double w = GM * L.vol / (r2 * sqrt(r2));
+  fw[t] = w * x;
+  fw[t + na] = w * y;
+  fw[t + 2 * na] = w * z;
 }
 
-// fixed-order compensated (Neumaier) sum of the block partials, one warp per component
-__global__ void k_force_finalize(const double* __restrict__ partials, int n, DevScalars* ds,
-                                 double* ring, int ring_cap, long long* ring_pos) {
+// fixed-order compensated (Neumaier) sum of the block partials, one warp per
+// component (threads 96.. of the block only take part in the barrier)
+__device__ __forceinline__ void el_force_finalize(const double* __restrict__ partials, int n,
+                                                  DevScalars* ds, double* ring, int ring_cap,
+                                                  long long* ring_pos) {
   int comp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (comp >= 3) return;
-  double s = 0.0, cmp = 0.0;
-  for (int p = lane; p < n; p += 32) {
-    double v = partials[3 * p + comp];
-    double tt = s + v;
-    if (fabs(s) >= fabs(v))
-      cmp += (s - tt) + v;
-    else
-      cmp += (v - tt) + s;
-    s = tt;
-  }
-  // fixed butterfly over the lanes, then fold the compensation in
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    double so = __shfl_down_sync(0xffffffffu, s, o);
-    double co = __shfl_down_sync(0xffffffffu, cmp, o);
-    if (lane < o) {
-      double tt = s + so;
-      if (fabs(s) >= fabs(so))
-        cmp += (s - tt) + so;
+  if (comp < 3) {
+    double s = 0.0, cmp = 0.0;
+    for (int p = lane; p < n; p += 32) {
+      double v = partials[3 * p + comp];
+      double tt = s + v;
+      if (fabs(s) >= fabs(v))
+        cmp += (s - tt) + v;
       else
-        cmp += (so - tt) + s;
+        cmp += (v - tt) + s;
       s = tt;
-      cmp += co;
     }
-  }
-  if (lane == 0) {
-    double F = s + cmp;
-    ds->F[comp] = F;
-    if (ring) {
-      long long pos = *ring_pos;
-      ring[3 * (pos % ring_cap) + comp] = F;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      double so = __shfl_down_sync(0xffffffffu, s, o);
+      double co = __shfl_down_sync(0xffffffffu, cmp, o);
+      if (lane < o) {
+        double tt = s + so;
+        if (fabs(s) >= fabs(so))
+          cmp += (s - tt) + so;
+        else
+          cmp += (so - tt) + s;
+        s = tt;
+        cmp += co;
+      }
+    }
+    if (lane == 0) {
+      double F = s + cmp;
+      ds->F[comp] = F;
+      if (ring) ring[3 * (*ring_pos % ring_cap) + comp] = F;
     }
   }
   __syncthreads();
@@ -1046,155 +1024,196 @@ int launch_hdiv_check(const double* a, const double* b, int n, double* max_ulp, 
   return 1;
 }
 
-// =================================================================== launchers
+// =================================================================== work lists
 
-template <class T>
-int launch_source(const LevelView& L, const Box& b, const Scratch& S, const T* dt, int write_pi,
-                  double gm1, const Phys& P, cudaStream_t st) {
-  k_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, write_pi, (T)gm1,
-                                                       make_bg<T>(P), make_geo<T>(L));
-  return 1;
+// One op on one work item: maps the item's fields onto the element function.
+template <class T, int OP, int D>
+__device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
+  if (OP == OP_SOURCE)
+    el_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.flags & FL_WRITE_PI, it.gm1, it.bg, it.g,
+                 tid);
+  else if (OP == OP_COMPRESS)
+    el_compress_lum<T>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.lum, it.flags & FL_SS3,
+                       it.flags & FL_LUM, it.flags & FL_EPS, it.bg, it.g, tid);
+  else if (OP == OP_FRONTIER_DIFF)
+    el_frontier_diff<T>(it.L, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
+                        tid);
+  else if (OP == OP_DIFFUSE)
+    el_diffuse<T>(it.L, it.b, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
+                  tid);
+  else if (OP == OP_TPREP)
+    el_tprep<T>(it.L, it.b, it.S, it.bg, tid);
+  else if (OP == OP_TFLUX)
+    el_tflux<T, D>(it.L, it.b, it.S, (const T*)it.dt, it.bg, it.g, tid);
+  else if (OP == OP_TFRONTIER)
+    el_tfrontier<T>(it.L, it.S, D, tid);
+  else if (OP == OP_TMOM)
+    el_tmom<T, D>(it.L, it.b, it.S, (const T*)it.dt, it.bg, it.g, tid);
+  else if (OP == OP_TUPDATE)
+    el_tupdate<T, D>(it.L, it.b, it.S, it.g, tid);
+  else if (OP == OP_VREC)
+    el_vrec_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.bg, it.g, tid);
+  else if (OP == OP_BC)
+    el_bc_axis<T>(it.L, D, it.bc_lo, it.bc_hi, it.bg.rho0, it.bg.e0, it.bg.V[0], it.bg.V[1],
+                  it.bg.V[2], tid);
+  else if (OP == OP_COMMUP)
+    el_commup<T>(it.L, it.F, tid);
+  else if (OP == OP_COMMMEAN)
+    el_commmean<T>(it.L, it.F, it.band, tid);
+  else if (OP == OP_ZERO_ACC) {
+    if (tid < it.count) it.L.acc[tid] = 0.0;
+  } else if (OP == OP_DT_LEVEL)
+    el_dt_level<T>(it.L, it.level, it.gg, it.flags & FL_HYDRO, it.ds, it.rho0d, it.e0d, it.V[0],
+                   it.V[1], it.V[2], tid);
+  else if (OP == OP_DT_FINAL)
+    el_dt_finalize(it.ds, it.level, *it.fin, it.dt_fixed);
+  else if (OP == OP_FORCE_LEVEL)
+    el_force_level<T>(it.L, it.L.fw, it.partials, tid);
+  else if (OP == OP_FORCE_FINAL)
+    el_force_finalize(it.partials, it.npart, it.ds, it.ring, it.ring_cap, it.ring_pos);
+  else if (OP == OP_TIME)
+    el_time_advance(it.ds);
 }
 
-template <class T>
-int launch_compress_lum(const LevelView& L, const Box& b, const Scratch& S, const T* dt,
-                        const Phys& P, int do_ss3, int do_lum, int do_eps, cudaStream_t st) {
-  k_compress_lum<T><<<grid_for(b.count()), kBlock, 0, st>>>(
-      L, b, S, dt, (T)(P.gamma - 1.0), (T)P.L, do_ss3, do_lum, do_eps, make_bg<T>(P),
-      make_geo<T>(L));
-  return 1;
-}
-
-template <class T>
-int launch_diffuse(const LevelView& L, const Box& b, const Scratch& S, const T* dt,
-                   const Phys& P, cudaStream_t st) {
-  k_diffuse<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, (T)P.chi, (T)P.rho0,
-                                                        P.diff_face_rho, make_geo<T>(L));
-  return 1;
-}
-
-static long long slots_total(const LevelView& L, int sides_lo, int n_sides) {
-  long long tot = 0;
-  for (int s = sides_lo; s < sides_lo + n_sides; ++s) {
-    int d = s >> 1;
-    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    tot += (long long)(L.n[t1] >> 1) * (L.n[t2] >> 1);
+// Persistent work-list kernel: block b takes the contiguous chunks
+// [b*nchunks/grid, (b+1)*nchunks/grid) of the concatenated items, stages the item of
+// each chunk in shared memory (re-staging only when the item changes) and runs the
+// op on the chunk's elements.  starts[i] is the first chunk of item i.
+template <class T, int OP, int D>
+__global__ void __launch_bounds__(kBlock) k_batch(const Item<T>* __restrict__ items,
+                                                  const unsigned* __restrict__ starts, int nitems,
+                                                  unsigned nchunks) {
+  __shared__ __align__(16) unsigned char s_raw[sizeof(Item<T>)];
+  const Item<T>& it = *reinterpret_cast<const Item<T>*>(s_raw);
+  unsigned c0 = (unsigned)((unsigned long long)nchunks * blockIdx.x / gridDim.x);
+  unsigned c1 = (unsigned)((unsigned long long)nchunks * (blockIdx.x + 1) / gridDim.x);
+  int cur = -1;
+  for (unsigned ch = c0; ch < c1; ++ch) {
+    int lo = cur < 0 ? 0 : cur, hi = nitems - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (starts[mid] <= ch)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    if (lo != cur) {
+      __syncthreads();
+      const int4* src = reinterpret_cast<const int4*>(items + lo);
+      int4* dst = reinterpret_cast<int4*>(s_raw);
+      for (int w = threadIdx.x; w < (int)(sizeof(Item<T>) / 16); w += kBlock) dst[w] = src[w];
+      __syncthreads();
+      cur = lo;
+    }
+    // private copy where it scalarises (global stores cannot alias it, so the
+    // fields the op uses stay in registers); ops that index the item's arrays with
+    // run-time indices read it from shared memory instead
+    constexpr bool kLocal =
+        !(OP == OP_COMPRESS || OP == OP_FRONTIER_DIFF || OP == OP_BC || OP == OP_COMMUP);
+    if (kLocal) {
+      const Item<T> loc = it;
+      run_op<T, OP, D>(loc, (ch - starts[cur]) * kBlock + threadIdx.x);
+    } else {
+      run_op<T, OP, D>(it, (ch - starts[cur]) * kBlock + threadIdx.x);
+    }
+    __syncthreads();
   }
-  return tot;
+}
+
+// One work item: passed by value (kernel-parameter space), one block per chunk.
+template <class T, int OP, int D>
+__global__ void __launch_bounds__(kBlock) k_single(const Item<T> it) {
+  run_op<T, OP, D>(it, blockIdx.x * kBlock + threadIdx.x);
+}
+
+template <class T, int OP, int D>
+static void launch_one(const Item<T>* items, const unsigned* starts, int nitems, unsigned nchunks,
+                       unsigned grid, cudaStream_t st, const Item<T>* host_item) {
+  if (nitems == 1 && host_item)
+    k_single<T, OP, D><<<nchunks, kBlock, 0, st>>>(*host_item);
+  else
+    k_batch<T, OP, D><<<grid, kBlock, 0, st>>>(items, starts, nitems, nchunks);
 }
 
 template <class T>
-int launch_frontier_diff(const LevelView& L, const Scratch& S, const T* dt, const Phys& P,
-                         cudaStream_t st) {
-  k_frontier_diff<T><<<grid_for(slots_total(L, 0, 6)), kBlock, 0, st>>>(
-      L, S, dt, (T)P.chi, (T)P.rho0, P.diff_face_rho, make_geo<T>(L));
-  return 1;
-}
-
-template <class T>
-int launch_tprep(const LevelView& L, const Box& b, const Scratch& S, const Phys& P,
-                 cudaStream_t st) {
-  k_tprep<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, make_bg<T>(P));
-  return 1;
-}
-
-template <class T>
-int launch_tflux(const LevelView& L, const Box& b, const Scratch& S, int d, const T* dt,
-                 const Phys& P, cudaStream_t st) {
-  unsigned gr = grid_for(b.count());
-  Bg<T> bg = make_bg<T>(P);
-  Geo<T> g = make_geo<T>(L);
-  if (d == 0) k_tflux<T, 0><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
-  if (d == 1) k_tflux<T, 1><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
-  if (d == 2) k_tflux<T, 2><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
-  return 1;
-}
-
-template <class T>
-int launch_tfrontier(const LevelView& L, const Scratch& S, int d, cudaStream_t st) {
-  k_tfrontier<T><<<grid_for(slots_total(L, 2 * d, 2)), kBlock, 0, st>>>(L, S, d);
-  return 1;
-}
-
-template <class T>
-int launch_tmom(const LevelView& L, const Box& b, const Scratch& S, int d, const T* dt,
-                const Phys& P, cudaStream_t st) {
-  unsigned gr = grid_for(b.count());
-  Bg<T> bg = make_bg<T>(P);
-  Geo<T> g = make_geo<T>(L);
-  if (d == 0) k_tmom<T, 0><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
-  if (d == 1) k_tmom<T, 1><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
-  if (d == 2) k_tmom<T, 2><<<gr, kBlock, 0, st>>>(L, b, S, dt, bg, g);
-  return 1;
-}
-
-template <class T>
-int launch_tupdate(const LevelView& L, const Box& b, const Scratch& S, int d, cudaStream_t st) {
-  unsigned gr = grid_for(b.count());
-  Geo<T> g = make_geo<T>(L);
-  if (d == 0) k_tupdate<T, 0><<<gr, kBlock, 0, st>>>(L, b, S, g);
-  if (d == 1) k_tupdate<T, 1><<<gr, kBlock, 0, st>>>(L, b, S, g);
-  if (d == 2) k_tupdate<T, 2><<<gr, kBlock, 0, st>>>(L, b, S, g);
-  return 1;
-}
-
-template <class T>
-int launch_vrec_source(const LevelView& L, const Box& b, const Scratch& S, const T* dt,
-                       double gm1, const Phys& P, cudaStream_t st) {
-  k_vrec_source<T><<<grid_for(b.count()), kBlock, 0, st>>>(L, b, S, dt, (T)gm1, make_bg<T>(P),
-                                                            make_geo<T>(L));
-  return 1;
-}
-
-template <class T>
-int launch_bc_fill(const LevelView& L, const Phys& P, cudaStream_t st) {
-  int n = 0;
-  for (int d = 0; d < 3; ++d) {
-    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    long long total = (long long)L.s[t1] * L.s[t2] * 2 * L.G * 5;
-    k_bc_axis<T><<<grid_for(total), kBlock, 0, st>>>(L, d, P.bc[2 * d], P.bc[2 * d + 1],
-                                                      (T)P.rho0, (T)P.e0, (T)P.V[0], (T)P.V[1],
-                                                      (T)P.V[2]);
-    ++n;
+int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, int nitems,
+                 unsigned nchunks, unsigned grid, cudaStream_t st, const Item<T>* host_item) {
+  if (nchunks == 0 || nitems == 0) return 0;
+  if (grid > nchunks) grid = nchunks;
+#define DFN_OP(O)                                                          \
+  case O:                                                                  \
+    launch_one<T, O, 0>(items, starts, nitems, nchunks, grid, st, host_item); \
+    break;
+#define DFN_OPD(O)                                                         \
+  case O:                                                                  \
+    if (d == 0) launch_one<T, O, 0>(items, starts, nitems, nchunks, grid, st, host_item); \
+    if (d == 1) launch_one<T, O, 1>(items, starts, nitems, nchunks, grid, st, host_item); \
+    if (d == 2) launch_one<T, O, 2>(items, starts, nitems, nchunks, grid, st, host_item); \
+    break;
+  switch (op) {
+    DFN_OP(OP_SOURCE)
+    DFN_OP(OP_COMPRESS)
+    DFN_OP(OP_FRONTIER_DIFF)
+    DFN_OP(OP_DIFFUSE)
+    DFN_OP(OP_TPREP)
+    DFN_OPD(OP_TFLUX)
+    DFN_OPD(OP_TFRONTIER)
+    DFN_OPD(OP_TMOM)
+    DFN_OPD(OP_TUPDATE)
+    DFN_OP(OP_VREC)
+    DFN_OPD(OP_BC)
+    DFN_OP(OP_COMMUP)
+    DFN_OP(OP_COMMMEAN)
+    DFN_OP(OP_ZERO_ACC)
+    DFN_OP(OP_DT_LEVEL)
+    DFN_OP(OP_DT_FINAL)
+    DFN_OP(OP_FORCE_LEVEL)
+    DFN_OP(OP_FORCE_FINAL)
+    DFN_OP(OP_TIME)
+    default:
+      return 0;
   }
-  return n;
-}
-
-template <class T>
-int launch_commup(const LevelView& C, const LevelView& F, cudaStream_t st) {
-  long long hosts = (long long)((F.n[0] >> 1) + F.G) * ((F.n[1] >> 1) + F.G) * ((F.n[2] >> 1) + F.G);
-  k_commup<T><<<grid_for(5 * hosts), kBlock, 0, st>>>(C, F);
+#undef DFN_OP
+#undef DFN_OPD
   return 1;
 }
 
-template <class T>
-int launch_commmean(const LevelView& C, const LevelView& F, int band, cudaStream_t st) {
-  long long n = (long long)(F.n[0] >> 1) * (F.n[1] >> 1) * (F.n[2] >> 1);
-  k_commmean<T><<<grid_for(n), kBlock, 0, st>>>(C, F, band);
-  return 1;
-}
+// elements per chunk of each op (one chunk = one block pass)
+int op_chunk_elems(int op) { return op == OP_FORCE_LEVEL ? kBlock * kForceCells : kBlock; }
 
-template <class T>
-int launch_dt_level(const LevelView& L, int level, const Phys& P, DevScalars* ds,
-                    cudaStream_t st) {
-  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
-  k_dt_level<T><<<grid_for(na), kBlock, 0, st>>>(L, level, P.gamma * (P.gamma - 1.0),
-                                                  P.hydro_on, ds, P.rho0, P.e0, P.V[0], P.V[1],
-                                                  P.V[2]);
-  return 1;
-}
-
-int launch_dt_finalize(DevScalars* ds, int n_levels, const double* prod, double dt_fixed,
-                       cudaStream_t st) {
-  // prod[0..n) xi products, [n..2n) diffusion limits, [2n..5n) cfl*dx per axis
-  DtFinal fin;
-  for (int l = 0; l < 16; ++l) {
-    fin.prod[l] = l < n_levels ? prod[l] : 1.0;
-    fin.diff_lim[l] = l < n_levels ? prod[n_levels + l] : INFINITY;
-    for (int d = 0; d < 3; ++d) fin.cfl_dx[l][d] = l < n_levels ? prod[2 * n_levels + 3 * l + d] : 0.0;
+// index-space size of one item of an op (host side, from the item's views)
+unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const Box& b) {
+  long long n = 0;
+  auto slots = [&](int lo, int ns) {
+    long long tot = 0;
+    for (int s = lo; s < lo + ns; ++s) {
+      int a = s >> 1;
+      int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
+      tot += (long long)(L.n[t1] >> 1) * (L.n[t2] >> 1);
+    }
+    return tot;
+  };
+  switch (op) {
+    case OP_SOURCE: case OP_COMPRESS: case OP_DIFFUSE: case OP_TPREP: case OP_TFLUX:
+    case OP_TMOM: case OP_TUPDATE: case OP_VREC:
+      n = b.count();
+      break;
+    case OP_FRONTIER_DIFF: n = slots(0, 6); break;
+    case OP_TFRONTIER: n = slots(2 * d, 2); break;
+    case OP_BC: {
+      int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      n = (long long)L.s[t1] * L.s[t2] * 2 * L.G * 5;
+      break;
+    }
+    case OP_COMMUP:
+      n = 5LL * ((F.n[0] >> 1) + F.G) * ((F.n[1] >> 1) + F.G) * ((F.n[2] >> 1) + F.G);
+      break;
+    case OP_COMMMEAN: n = (long long)(F.n[0] >> 1) * (F.n[1] >> 1) * (F.n[2] >> 1); break;
+    case OP_ZERO_ACC: n = 18LL * L.acc_slots; break;
+    case OP_DT_LEVEL: case OP_FORCE_LEVEL: n = (long long)L.n[0] * L.n[1] * L.n[2]; break;
+    default: n = 1; break;
   }
-  k_dt_finalize<<<1, 32, 0, st>>>(ds, n_levels, fin, dt_fixed);
-  return 1;
+  return (unsigned)n;
 }
 
 int force_partials_per_level(const LevelView& L) {
@@ -1202,28 +1221,9 @@ int force_partials_per_level(const LevelView& L) {
   return (int)((na + kBlock * kForceCells - 1) / (kBlock * kForceCells));
 }
 
-template <class T>
-int launch_force_level(const LevelView& L, const Phys& P, double* partials, int offset,
-                       cudaStream_t st) {
-  (void)P;
-  k_force_level<T><<<force_partials_per_level(L), kBlock, 0, st>>>(L, L.fw, partials + 3 * offset);
-  return 1;
-}
-
 int launch_force_weights(const LevelView& L, const Phys& P, cudaStream_t st) {
   k_force_weights<<<grid_for((long long)L.n[0] * L.n[1] * L.n[2]), kBlock, 0, st>>>(L, P.GM, P.eps,
                                                                                    L.fw);
-  return 1;
-}
-
-int launch_force_finalize(const double* partials, int n, DevScalars* ds, double* ring,
-                          int ring_cap, long long* ring_pos, cudaStream_t st) {
-  k_force_finalize<<<1, 96, 0, st>>>(partials, n, ds, ring, ring_cap, ring_pos);
-  return 1;
-}
-
-int launch_time_advance(DevScalars* ds, cudaStream_t st) {
-  k_time_advance<<<1, 32, 0, st>>>(ds);
   return 1;
 }
 
@@ -1274,32 +1274,8 @@ int launch_unpack_active(const LevelView& L, int field, const double* in, int fu
 }
 
 #define DFN_INSTANTIATE(T)                                                                     \
-  template int launch_source<T>(const LevelView&, const Box&, const Scratch&, const T*, int,    \
-                                double, const Phys&, cudaStream_t);                            \
-  template int launch_compress_lum<T>(const LevelView&, const Box&, const Scratch&, const T*,  \
-                                      const Phys&, int, int, int, cudaStream_t);               \
-  template int launch_diffuse<T>(const LevelView&, const Box&, const Scratch&, const T*,       \
-                                 const Phys&, cudaStream_t);                                   \
-  template int launch_frontier_diff<T>(const LevelView&, const Scratch&, const T*,             \
-                                       const Phys&, cudaStream_t);                             \
-  template int launch_tprep<T>(const LevelView&, const Box&, const Scratch&, const Phys&,      \
-                               cudaStream_t);                                                  \
-  template int launch_tflux<T>(const LevelView&, const Box&, const Scratch&, int, const T*,    \
-                               const Phys&, cudaStream_t);                                     \
-  template int launch_tfrontier<T>(const LevelView&, const Scratch&, int, cudaStream_t);       \
-  template int launch_tmom<T>(const LevelView&, const Box&, const Scratch&, int, const T*,     \
-                              const Phys&, cudaStream_t);                                      \
-  template int launch_tupdate<T>(const LevelView&, const Box&, const Scratch&, int,            \
-                                 cudaStream_t);                                                \
-  template int launch_vrec_source<T>(const LevelView&, const Box&, const Scratch&, const T*,   \
-                                     double, const Phys&, cudaStream_t);                       \
-  template int launch_bc_fill<T>(const LevelView&, const Phys&, cudaStream_t);                 \
-  template int launch_commup<T>(const LevelView&, const LevelView&, cudaStream_t);             \
-  template int launch_commmean<T>(const LevelView&, const LevelView&, int, cudaStream_t);      \
-  template int launch_dt_level<T>(const LevelView&, int, const Phys&, DevScalars*,             \
-                                  cudaStream_t);                                               \
-  template int launch_force_level<T>(const LevelView&, const Phys&, double*, int,              \
-                                     cudaStream_t);                                            \
+  template int launch_batch<T>(int, int, const Item<T>*, const unsigned*, int, unsigned,       \
+                               unsigned, cudaStream_t, const Item<T>*);                        \
   template int launch_init_uniform<T>(const LevelView&, const Phys&, cudaStream_t);            \
   template int launch_static_fields<T>(const LevelView&, const Phys&, double, double*,         \
                                        double*, cudaStream_t);                                 \

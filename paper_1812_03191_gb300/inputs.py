@@ -11,6 +11,13 @@ Workloads (all synthetic; the paper uses no dataset):
                          chi=1, luminosity L_c = 4 pi GM rho0 chi / gamma (Eq. 49)
                          deposited as a Gaussian of sigma = softening = 2 finest cells.
   * ``precision``     -- 5 levels of 128^3 on [-16,16]^3, Mach 1.2, same physics.
+  * ``batched``       -- 64 independent runs (seed 1812031910): levels uniform in 2..4,
+                         per-run mesh from {32,48,64,96}^3, Mach log-uniform in
+                         [0.1,3], chi log-uniform in [0.3,3], GM=0.01, L = 0 or L_c(chi)
+                         with probability 1/2, coarse box [-8,8]^3.
+  * ``requests``      -- the serving stream (seed 1812031911): Poisson arrivals, levels
+                         2..6, mesh from {48,64,96,128}^3, Mach uniform in [0.05,4],
+                         chi log-uniform in [0.3,3], L on/off.
 """
 from __future__ import annotations
 
@@ -96,4 +103,45 @@ def random_state(n, n_levels, seed, amp=1e-2):
     out = []
     for _ in range(n_levels):
         out.append([rng.standard_normal((n, n, n)) * amp for _ in range(5)])
+    return out
+
+
+def _run_params(rng, mach, chi, lum_on, n, n_levels, half):
+    dx_f = 2 * half / n / 2 ** (n_levels - 1)
+    eps = 2 * dx_f
+    L = critical_luminosity(0.01, 1.0, chi, 5.0 / 3.0) if lum_on else 0.0
+    return base_params(mach=mach, chi=chi, GM=0.01, eps=eps, L=L,
+                       lum_sigma=eps if lum_on else 0.0)
+
+
+def batched(n_runs=64, seed=1812031910, half=8.0, sizes=(32, 48, 64, 96), levels=(2, 3, 4)):
+    """Independent runs of the batched form (see the module docstring)."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for _ in range(n_runs):
+        nl = int(rng.choice(levels))
+        n = int(rng.choice(sizes))
+        mach = float(np.exp(rng.uniform(np.log(0.1), np.log(3.0))))
+        chi = float(np.exp(rng.uniform(np.log(0.3), np.log(3.0))))
+        lum_on = bool(rng.random() < 0.5)
+        runs.append(dict(n_levels=nl, n=n, lo=(-half,) * 3, hi=(half,) * 3, G=DEFAULT_G,
+                         params=_run_params(rng, mach, chi, lum_on, n, nl, half)))
+    return runs
+
+
+def requests(n_req, rate, seed=1812031911, half=8.0, sizes=(48, 64, 96, 128),
+             levels=(2, 3, 4, 5, 6)):
+    """Serving stream: (arrival time, run spec) with Poisson arrivals of `rate` per s."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n_req):
+        t += float(rng.exponential(1.0 / rate))
+        nl = int(rng.choice(levels))
+        n = int(rng.choice(sizes))
+        mach = float(rng.uniform(0.05, 4.0))
+        chi = float(np.exp(rng.uniform(np.log(0.3), np.log(3.0))))
+        lum_on = bool(rng.random() < 0.5)
+        out.append((t, dict(n_levels=nl, n=n, lo=(-half,) * 3, hi=(half,) * 3, G=DEFAULT_G,
+                            params=_run_params(rng, mach, chi, lum_on, n, nl, half))))
     return out
