@@ -303,6 +303,62 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Poisson stream of requests (levels 2..6, mesh {48,64,96,128}^3, Mach U[0.05,4],
+    chi log-U[0.3,3], L on/off) through the continuous-batching server (FP32 state,
+    FP64 reductions), against the same stream solved one request at a time with
+    plain FP64 contexts.  Same stopping rule and step cap for both."""
+    import torch
+
+    from paper_1812_03191_gb300 import binding
+    from paper_1812_03191_gb300 import serve as S
+    if args.impl == "reference":
+        return 0
+    torch.cuda.set_device(0)
+    budget = 16 << 30
+    # capacity: all requests resident in one pool, cell-updates/s of a few steps
+    probe = I.requests(args.requests, 1.0)
+    cu = [sp["n"] ** 3 * (2 ** sp["n_levels"] - 1) for _, sp in probe]
+    pool = binding.Pool(64 << 30, precision=binding.DF_FP32_STATE)
+    for _, sp in probe:
+        pool.admit(sp["n_levels"], sp["n"], sp["lo"], sp["hi"], sp["G"], sp["params"])
+    tiles = pool.autotune()
+    pool.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pool.step(5)
+    pool.query()
+    rate_cu = 5 * sum(cu) / (time.perf_counter() - t0)
+    pool.close()
+    capacity = rate_cu / (args.step_cap * float(np.mean(cu)))  # requests/s at the cap
+    rate = 0.8 * capacity
+    reqs = I.requests(args.requests, rate)
+    srv = S.Server(budget, precision=binding.DF_FP32_STATE, tol=1e-3, step_cap=args.step_cap,
+                   tiles=tiles)
+    with ClockSampler(0) as clk:
+        res, summ = srv.run(reqs)
+    max_active = srv.max_active
+    srv.close()
+    seq, summ_seq = S.solve_sequential(reqs, precision=binding.DF_FP64, tol=1e-3,
+                                       step_cap=args.step_cap)
+    line = {
+        "metric": "serving requests/s", "value": summ["throughput_req_per_s"],
+        "unit": "requests/s", "n_gpus": 1, "steps": args.requests, "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-state/f64-reductions", "data": "synthetic",
+        "config": {"workload": f"serving_{args.requests}_requests", "arrival_rate_per_s": rate,
+                   "capacity_req_per_s": capacity, "step_cap": args.step_cap, "tol": 1e-3,
+                   "budget_bytes": budget, "max_active": max_active,
+                   "seed": 1812031911},
+        "serving": summ, "sequential_fp64": summ_seq,
+        "throughput_ratio_vs_sequential_fp64":
+            summ["throughput_req_per_s"] / summ_seq["throughput_req_per_s"],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -310,7 +366,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nested",
-                    choices=["nested", "single", "precision", "batched"])
+                    choices=["nested", "single", "precision", "batched", "serving"])
+    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--step-cap", type=int, default=200)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -318,6 +376,8 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     cfg = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, cfg)
