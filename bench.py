@@ -135,6 +135,15 @@ ARRAYS_PER_ELEM = {
 }
 
 
+# FP64 flops executed per box element (DADD + DMUL + 2 DFMA, from the ncu capture in
+# profiles/k_sweeps_nested_3x64_fp64.md) of the FP64 sweep kernels
+FP64_FLOPS_PER_ELEM = {"tflux": 55.0, "tmom": 94.3, "tupdate": 14.1}
+# FP64 peak of GB300 derived from unit counts and the clock: 2 DFMA lanes per SM per
+# cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 2),
+# x 2 flops x 152 SMs x 2.07 GHz
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+
 def level_step_boxes(cfg):
     """box elements of every level step of one coarse step (level 0: margin 4;
     finer levels: first sub-cycle margin 8, second margin 4, capped at the array)."""
@@ -303,6 +312,57 @@ def run_batched(args):
     return 0
 
 
+def run_precision_compare(args):
+    """The precision workload (5 x 128^3, Mach 1.2, L_c) in FP32 state and in FP64,
+    K coarse steps each (each computes its own time steps): per-field relative L2
+    error of the FP32 state and relative force error against FP64."""
+    import torch
+
+    from paper_1812_03191_gb300 import binding
+    cfg = I.precision()
+    out = {}
+    sims = {}
+    for prec in (binding.DF_FP64, binding.DF_FP32_STATE):
+        sim = binding.Sim(cfg["n_levels"], cfg["n"], cfg["lo"], cfg["hi"], cfg["G"],
+                          cfg["params"], precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(args.steps)
+        F, Fm = sim.force()
+        out[prec] = dict(F=F, Fm=Fm, t=sim.status()[0], wall=time.perf_counter() - t0)
+        sims[prec] = sim
+    errs = {}
+    names = ["rho", "e", "vx", "vy", "vz"]
+    for f in range(5):
+        num = den = 0.0
+        for l in range(cfg["n_levels"]):
+            a = sims[binding.DF_FP32_STATE].get_field(l, f)
+            b = sims[binding.DF_FP64].get_field(l, f)
+            pr = cfg["params"]
+            e0 = pr["cs"] ** 2 * pr["rho0"] / (pr["gamma"] * (pr["gamma"] - 1))
+            V = [pr["mach"] * pr["cs"] * c for c in pr["flow_dir"]]
+            base = pr["rho0"] if f == 0 else (e0 if f == 1 else V[f - 2])
+            num += float(((a - b) ** 2).sum())
+            den += float(((b - base) ** 2).sum())  # relative to the perturbation
+        errs[names[f]] = (num / max(den, 1e-300)) ** 0.5
+    F64, F32 = out[binding.DF_FP64]["Fm"], out[binding.DF_FP32_STATE]["Fm"]
+    cu = cell_updates_per_step(cfg)
+    line = {
+        "metric": "FP32-state error vs FP64", "value": abs(F32 - F64) / abs(F64),
+        "unit": "relative force error", "n_gpus": 1, "steps": args.steps, "warmup": 0,
+        "higher_is_better": False, "dtype": "f32-state vs f64", "data": "synthetic",
+        "config": {"workload": cfg["name"], "coarse_steps": args.steps},
+        "force_along_motion": {"fp64": F64, "fp32_state": F32},
+        "time": {"fp64": out[binding.DF_FP64]["t"], "fp32_state": out[binding.DF_FP32_STATE]["t"]},
+        "field_rel_l2_error_of_perturbation": errs,
+        "cell_updates_per_s": {k: cu * args.steps / v["wall"] for k, v in
+                               (("fp64", out[binding.DF_FP64]),
+                                ("fp32_state", out[binding.DF_FP32_STATE]))},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     """Poisson stream of requests (levels 2..6, mesh {48,64,96,128}^3, Mach U[0.05,4],
     chi log-U[0.3,3], L on/off) through the continuous-batching server (FP32 state,
@@ -366,7 +426,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nested",
-                    choices=["nested", "single", "precision", "batched", "serving"])
+                    choices=["nested", "single", "precision", "batched", "serving",
+                             "precision_compare"])
     ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--step-cap", type=int, default=200)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
@@ -378,6 +439,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "precision_compare":
+        return run_precision_compare(args)
     cfg = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, cfg)
@@ -461,14 +524,31 @@ def main():
     avg_s = dom_ms / dom_n / 1e3
     achieved = bpl / avg_s / 1e9
     peak, peak_kind = peaks()
-    roofline = {
-        "kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-        "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-        "algorithmic_bytes_per_launch": bpl, "launches_timed": dom_n,
-        "avg_launch_ms": dom_ms / dom_n,
-        "share_of_kernel_time": dom_ms / total_k if total_k else None,
-        "top_kernel": ranked[0],
-    }
+    hbm = {"achieved_gbs": achieved, "peak_gbs": peak, "frac": achieved / peak,
+           "peak_source": peak_kind, "algorithmic_bytes_per_launch": bpl}
+    if prec == binding.DF_FP64 and dom in FP64_FLOPS_PER_ELEM:
+        # the FP64 kernels are bound by GB300's FP64 pipe (ncu: ~85 % busy, DRAM < 4 %)
+        boxes = level_step_boxes(cfg)
+        flops = FP64_FLOPS_PER_ELEM[dom] * sum(boxes) / len(boxes)
+        ach = flops / avg_s / 1e12
+        roofline = {
+            "kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz",
+            "fp64_flops_per_launch": flops, "launches_timed": dom_n,
+            "avg_launch_ms": dom_ms / dom_n,
+            "share_of_kernel_time": dom_ms / total_k if total_k else None,
+            "top_kernel": ranked[0], "hbm": hbm,
+        }
+    else:
+        roofline = {
+            "kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": bpl, "launches_timed": dom_n,
+            "avg_launch_ms": dom_ms / dom_n,
+            "share_of_kernel_time": dom_ms / total_k if total_k else None,
+            "top_kernel": ranked[0],
+        }
 
     # ---- e2e: state from pinned host memory, one step, force back, every step
     nstate = sim.state_size()

@@ -287,3 +287,23 @@ def test_hot_path_division_within_one_ulp():
                         np.exp(rng.uniform(-300, 300, n // 2)) * rng.choice([-1, 1], n // 2)])
     a = rng.standard_normal(n) * np.exp(rng.uniform(-30, 30, n))
     assert binding.check_division(a, b) <= 1.0
+
+
+def test_adiabatic_subsonic_drag_on_the_gpu():
+    """The GPU path at twice the oracle pin's resolution: 4 levels of 64^3 on
+    [-16,16]^3, chi = 0, Mach 0.5: the drag settles near the linear-theory value
+    -F0 I / M^2 (Ostriker 1999, the paper's Eq. 54 with F0 of Eq. 50)."""
+    import math
+    M, GM, nl, n, half = 0.5, 0.01, 4, 64, 16.0
+    dxf = 2 * half / n / 2 ** (nl - 1)
+    p = I.base_params(mach=M, GM=GM, chi=0.0, L=0.0, eps=2 * dxf)
+    sim = binding.Sim(nl, n, (-half,) * 3, (half,) * 3, I.DEFAULT_G, p)
+    Fth = -4 * math.pi * GM**2 * (0.5 * math.log((1 + M) / (1 - M)) - M) / M**2
+    ratios = []
+    while sim.t < 7.0:
+        sim.step(4)
+        F, along = sim.force()
+        assert abs(along - F[0]) < 1e-18
+        ratios.append((sim.t, along / Fth))
+    late = [r for t, r in ratios if 3.5 < t < 7.0]
+    assert late and all(0.95 < r < 1.06 for r in late), ratios

@@ -560,3 +560,28 @@ def test_transverse_momentum_advected_at_wind_speed(adv, comp):
     shift = np.angle(z1 / z0) / k  # distance travelled by the pattern
     assert abs(shift - U * o.t) < 0.01 * U * o.t
     assert 0.9 < abs(z1) / abs(z0) <= 1.0
+
+
+# ---------------------------------------------------------------- T11
+
+def _ostriker_subsonic(mach):
+    """Linear-theory drag factor of a subsonic perturber (Ostriker 1999, the adiabatic
+    force F_adi = F0 M^-2 I the paper quotes as Eq. 54), valid once c_s t > r_min/(1-M)."""
+    return 0.5 * math.log((1 + mach) / (1 - mach)) - mach
+
+
+def test_adiabatic_subsonic_drag_approaches_linear_theory():
+    """chi = 0, L = 0, Mach 0.5, weak perturber (GM well below the finest cell): the
+    force along the motion settles near -F0 I / M^2 (Eqs. 50, 54) while the sound
+    sphere is still inside the box."""
+    M, GM, nl, n, half = 0.5, 0.01, 4, 32, 16.0
+    dxf = 2 * half / n / 2 ** (nl - 1)
+    o = make(nl, n, half, mach=M, GM=GM, chi=0.0, L=0.0, eps=2 * dxf)
+    F0 = 4 * math.pi * GM**2  # rho0 = c_s = 1
+    Fth = -F0 * _ostriker_subsonic(M) / M**2
+    ratios = []
+    while o.t < 7.0:
+        o.step(4)
+        ratios.append((o.t, o.force()[0] / Fth))  # the perturber moves along +x
+    late = [r for t, r in ratios if 3.5 < t < 7.0]
+    assert late and all(0.95 < r < 1.06 for r in late), ratios
