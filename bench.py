@@ -166,6 +166,14 @@ def bytes_per_launch(cfg, kind, esz):
     return None
 
 
+def tile_summary(shapes):
+    """{op: [shape of x, y, z sweep]} for the ops whose tuned shape is not flat"""
+    if shapes is None:
+        return "flat"
+    from paper_1812_03191_gb300 import binding
+    return {binding.OP_NAMES[o]: row for o, row in enumerate(shapes) if any(row)}
+
+
 def cpu_oracle_rate(cfg, budget_s, steps_cap=None):
     """Oracle cell-updates/s on a bounded sample: whole coarse steps until budget."""
     from oracle import Oracle
@@ -433,6 +441,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tiles", default="auto", choices=["auto", "flat"],
+                    help="tile shapes of the stencil launches: autotuned (before the "
+                         "warm-up, untimed) or flat enumeration")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.workload == "batched":
@@ -473,6 +484,7 @@ def main():
     cu = cell_updates_per_step(cfg)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    shapes = sim.autotune() if args.tiles == "auto" else None
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize()
@@ -577,7 +589,8 @@ def main():
                        "box": [cfg["lo"][0], cfg["hi"][0]], "ghost": cfg["G"],
                        "cell_updates_per_step": cu, "l2": "flushed between timed steps "
                        "(256 MB write outside the step events)",
-                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
+                       "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
+                       "tile_shapes": tile_summary(shapes)},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -145,6 +145,17 @@ int df_set_timing(df_ctx* ctx, int on);
 int df_kernel_time(df_ctx* ctx, int kind, double* ms, long long* launches);
 const char* df_kernel_name(int kind);
 
+/* Tile autotuner: times every operator and sweep direction of one coarse step for
+ * each of the library's tile shapes (the order in which a block enumerates the
+ * elements of a box: flat, or 256-element (x,y,z) tiles 32x8x1, 32x1x8, 32x4x2,
+ * 64x4x1), keeps the fastest, and restores the state, so tuning does not advance
+ * the run.  tiles_out (nullable) receives DF_POOL_OPS x 3 shape indices.  The choice
+ * changes the order of work only: results are bitwise unchanged. */
+int df_autotune(df_ctx* ctx, int* tiles_out);
+/* Set the tile shape (0..4, in the order above) of every operator and direction:
+ * shapes[3 * op + d].  DF_EINVAL for a null pointer or a shape out of range. */
+int df_set_tile_shapes(df_ctx* ctx, const int* shapes);
+
 /* Verification switch: with on != 0 every operator runs over its whole stencil
  * range in the padded array (the ghost layers evolve exactly as in a plain
  * sweep of the whole array) instead of the active box plus the reach margin.
@@ -227,13 +238,17 @@ int df_pool_get_field(df_pool* pool, int slot, int level, int field, double* hos
 /* Active runs, bytes in use, the budget, kernels launched so far. */
 int df_pool_info(df_pool* pool, int* active, size_t* used, size_t* budget, long long* launches);
 
-/* Tile (grid) shape of the work-list launches: persistent blocks per SM for each
- * of the DF_POOL_OPS operators.  df_pool_autotune times every operator of one
- * coarse step of the current runs for 1..32 blocks per SM, keeps the fastest per
- * operator (written to blocks_per_sm_out, nullable) and restores the runs' state. */
+/* Tile and grid shape of the work-list launches.  df_pool_set_tiles sets the
+ * persistent blocks per SM of each of the DF_POOL_OPS operators.  df_pool_autotune
+ * times every operator of one coarse step of the current runs for 1..32 blocks per
+ * SM and for each tile shape (as df_autotune), keeps the fastest per operator
+ * (blocks per SM written to blocks_per_sm_out, nullable) and restores the runs'
+ * state. */
 #define DF_POOL_OPS 19
 int df_pool_set_tiles(df_pool* pool, const int* blocks_per_sm);
 int df_pool_autotune(df_pool* pool, int* blocks_per_sm_out);
+/* As df_set_tile_shapes, for every run of the pool. */
+int df_pool_set_tile_shapes(df_pool* pool, const int* shapes);
 
 /* Timing hook of a pool (as df_set_timing / df_kernel_time). */
 int df_pool_set_timing(df_pool* pool, int on);

@@ -29,8 +29,13 @@ EXPORTS = (
     "df_run_bytes", "df_pool_create", "df_pool_admit", "df_pool_release", "df_pool_step",
     "df_pool_query", "df_pool_get_field", "df_pool_info", "df_pool_set_tiles",
     "df_pool_autotune", "df_pool_destroy", "df_pool_set_timing", "df_pool_kernel_time",
+    "df_autotune", "df_set_tile_shapes", "df_pool_set_tile_shapes",
 )
 POOL_OPS = 19
+# operator order of the per-op tables (tile shapes, blocks per SM)
+OP_NAMES = ("source", "compress", "frontier_diff", "diffuse", "tprep", "tflux", "tfrontier",
+            "tmom", "tupdate", "vrec_source", "bc", "commup", "commmean", "zero_acc",
+            "dt_level", "dt_final", "force_level", "force_final", "time")
 NOALLOC_MAX_CELLS = 4194304
 
 
@@ -98,6 +103,9 @@ def load(path: str = LIB_PATH):
         "df_kernel_time": (C.c_int, [vp, C.c_int, dp, P(C.c_longlong)]),
         "df_kernel_name": (C.c_char_p, [C.c_int]),
         "df_debug_full_boxes": (C.c_int, [vp, C.c_int]),
+        "df_autotune": (C.c_int, [vp, P(C.c_int)]),
+        "df_set_tile_shapes": (C.c_int, [vp, P(C.c_int)]),
+        "df_pool_set_tile_shapes": (C.c_int, [vp, P(C.c_int)]),
         "df_destroy": (C.c_int, [vp]),
         "df_xi_search": (C.c_int, [C.c_int, dp, dp, P(C.c_int), dp]),
         "df_last_error": (C.c_char_p, []),
@@ -175,6 +183,16 @@ def force_level_noalloc(rho_dev_ptr, n, G, lo, dx, child_off=None, child_n=None,
                                       ci(child_off), ci(child_n), float(GM), float(eps),
                                       float(rho0), C.c_void_p(F_dev_ptr),
                                       C.c_void_p(stream) if stream else None))
+
+
+def _shapes(shapes):
+    if isinstance(shapes, int):
+        flat = [shapes] * (3 * POOL_OPS)
+    else:
+        flat = [int(v) for row in shapes for v in row]
+    if len(flat) != 3 * POOL_OPS:
+        raise ValueError(f"need {POOL_OPS} x 3 tile shapes")
+    return (C.c_int * (3 * POOL_OPS))(*flat)
 
 
 class Sim:
@@ -316,6 +334,16 @@ class Sim:
         _check(self.lib.df_kernel_time(self.h, kind, C.byref(ms), C.byref(n)))
         return ms.value, n.value
 
+    def autotune(self):
+        """tile shape index per (operator, direction), chosen by timing"""
+        out = (C.c_int * (3 * POOL_OPS))()
+        _check(self.lib.df_autotune(self.h, out))
+        return [list(out[3 * o:3 * o + 3]) for o in range(POOL_OPS)]
+
+    def set_tile_shapes(self, shapes):
+        """shapes: POOL_OPS x 3 tile shape indices (or one index for all)"""
+        _check(self.lib.df_set_tile_shapes(self.h, _shapes(shapes)))
+
     def debug_full_boxes(self, on):
         _check(self.lib.df_debug_full_boxes(self.h, 1 if on else 0))
 
@@ -405,6 +433,9 @@ class Pool:
         n = C.c_longlong()
         _check(self.lib.df_pool_kernel_time(self.h, kind, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def set_tile_shapes(self, shapes):
+        _check(self.lib.df_pool_set_tile_shapes(self.h, _shapes(shapes)))
 
     def set_tiles(self, blocks_per_sm):
         arr = (C.c_int * POOL_OPS)(*blocks_per_sm)

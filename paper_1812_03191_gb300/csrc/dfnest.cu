@@ -428,6 +428,15 @@ void fill_fin(const Run& r, DtFinal& fin) {
   }
 }
 
+// tile shape (index into kTileShapes) of each stencil op and sweep direction
+struct TileTable {
+  int t[OP_COUNT][3];
+  TileTable() {
+    for (int o = 0; o < OP_COUNT; ++o)
+      for (int d = 0; d < 3; ++d) t[o][d] = 0;
+  }
+};
+
 template <class T>
 struct Builder {
   struct Entry {
@@ -437,6 +446,7 @@ struct Builder {
   std::vector<std::vector<Entry>> per_run;
   int full_boxes = 0;
   const DtFinal* d_fins = nullptr;
+  TileTable tiles;
 
   Item<T> base(const Run& r, int l) const {
     Item<T> it;
@@ -468,6 +478,7 @@ struct Builder {
 
   Box box(const LevelView& v, int margin) const {
     Box b;
+    b.tile = 0;
     int M = full_boxes ? v.G : margin;
     for (int d = 0; d < 3; ++d) {
       b.lo[d] = std::max(0, v.G - M);
@@ -476,7 +487,8 @@ struct Builder {
     return b;
   }
 
-  static void add(std::vector<Entry>& out, int op, int d, Item<T> it) {
+  void add(std::vector<Entry>& out, int op, int d, Item<T> it) const {
+    it.b.tile = is_box_op(op) ? tiles.t[op][d] : 0;
     it.count = op_count(op, d, it.L, it.F, it.b);
     out.push_back({op, d, it});
   }
@@ -631,7 +643,8 @@ int plan_upload(Plan& plan) {
 }
 
 template <class T>
-int plan_build(Plan& plan, const std::vector<Run*>& runs, int full_boxes) {
+int plan_build(Plan& plan, const std::vector<Run*>& runs, int full_boxes,
+               const TileTable& tiles = TileTable()) {
   plan_invalidate(plan);
   plan.prec = sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE;
   size_t nr = runs.size();
@@ -644,6 +657,7 @@ int plan_build(Plan& plan, const std::vector<Run*>& runs, int full_boxes) {
   Builder<T> B;
   B.full_boxes = full_boxes;
   B.d_fins = plan.d_fins;
+  B.tiles = tiles;
   B.per_run.resize(nr);
   for (size_t r = 0; r < nr; ++r) B.coarse_step(*runs[r], (int)r, B.per_run[r]);
   B.merge(plan);
@@ -884,6 +898,7 @@ struct df_ctx {
   Plan plan;
   Exec x;
   int full_boxes = 0;
+  TileTable tiles;
 };
 
 struct df_pool {
@@ -894,6 +909,7 @@ struct df_pool {
   std::vector<Run*> slots;
   Plan plan;
   Exec x;
+  TileTable tiles;
 };
 
 namespace {
@@ -923,9 +939,155 @@ int sync_health(cudaStream_t st, Run* r) {
   return DF_OK;
 }
 
-int build_plan(Plan& p, const std::vector<Run*>& runs, int prec, int full_boxes) {
-  return prec == DF_FP64 ? plan_build<double>(p, runs, full_boxes)
-                         : plan_build<float>(p, runs, full_boxes);
+int build_plan(Plan& p, const std::vector<Run*>& runs, int prec, int full_boxes,
+               const TileTable& tiles) {
+  return prec == DF_FP64 ? plan_build<double>(p, runs, full_boxes, tiles)
+                         : plan_build<float>(p, runs, full_boxes, tiles);
+}
+
+// state of the runs that tuning steps disturb (fields, scalars, force-ring cursor)
+struct Snapshot {
+  std::vector<std::vector<char>> fields, acc, ring;
+  std::vector<DevScalars> ds;
+  std::vector<long long> pos;
+};
+
+int snapshot(const std::vector<Run*>& runs, Snapshot& sn) {
+  sn.fields.assign(runs.size(), {});
+  sn.acc.assign(runs.size(), {});
+  sn.ring.assign(runs.size(), {});
+  sn.ds.resize(runs.size());
+  sn.pos.resize(runs.size());
+  for (size_t i = 0; i < runs.size(); ++i) {
+    Run* r = runs[i];
+    size_t plane = plane_bytes((size_t)r->L[0].v.nc, r->esz);
+    size_t ab = r->L[0].acc_elems * sizeof(double);
+    sn.fields[i].resize(plane * 5 * r->nl);
+    sn.acc[i].resize(ab * r->nl);
+    for (int l = 0; l < r->nl; ++l) {
+      CK(cudaMemcpy(sn.fields[i].data() + plane * 5 * l, r->L[l].mem, plane * 5,
+                    cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(sn.acc[i].data() + ab * l, r->L[l].acc, ab, cudaMemcpyDeviceToHost));
+    }
+    sn.ring[i].resize(3 * (size_t)r->ring_cap * sizeof(double));
+    CK(cudaMemcpy(sn.ring[i].data(), r->ring, sn.ring[i].size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&sn.ds[i], r->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&sn.pos[i], r->ring_pos, sizeof(long long), cudaMemcpyDeviceToHost));
+  }
+  return DF_OK;
+}
+
+int restore(const std::vector<Run*>& runs, const Snapshot& sn) {
+  for (size_t i = 0; i < runs.size(); ++i) {
+    Run* r = runs[i];
+    size_t plane = plane_bytes((size_t)r->L[0].v.nc, r->esz);
+    size_t ab = r->L[0].acc_elems * sizeof(double);
+    for (int l = 0; l < r->nl; ++l) {
+      CK(cudaMemcpy(r->L[l].mem, sn.fields[i].data() + plane * 5 * l, plane * 5,
+                    cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(r->L[l].acc, sn.acc[i].data() + ab * l, ab, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(r->ring, sn.ring[i].data(), sn.ring[i].size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(r->ds, &sn.ds[i], sizeof(DevScalars), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(r->ring_pos, &sn.pos[i], sizeof(long long), cudaMemcpyHostToDevice));
+  }
+  return DF_OK;
+}
+
+// Device time of every launch of one coarse step of `p`, summed per (op, direction):
+// two coarse steps run back to back and the second is timed.  bps > 0 overrides
+// the persistent blocks per SM of every launch.
+int time_plan(const Plan& p, Exec& x, int prec, int bps, bool single_fast,
+              double per[OP_COUNT][3]) {
+  for (int o = 0; o < OP_COUNT; ++o)
+    for (int d = 0; d < 3; ++d) per[o][d] = 0.0;
+  std::vector<cudaEvent_t> ev(2 * p.launches.size());
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  const unsigned char* items = (const unsigned char*)p.d_items;
+  for (int rep = 0; rep < 2; ++rep)
+    for (size_t i = 0; i < p.launches.size(); ++i) {
+      const LaunchDesc& L = p.launches[i];
+      unsigned grid = (unsigned)x.sm_count * (unsigned)(bps > 0 ? bps : x.bps[L.op]);
+      const void* hi = (L.nitems == 1 && single_fast)
+                           ? (const void*)(p.items.data() + L.item0 * p.item_size)
+                           : nullptr;
+      if (rep == 1) cudaEventRecord(ev[2 * i], x.st);
+      if (prec == DF_FP64)
+        launch_batch<double>(L.op, L.d, (const Item<double>*)(items + L.item0 * p.item_size),
+                             p.d_starts + L.start0, L.nitems, L.nchunks, grid, x.st,
+                             (const Item<double>*)hi);
+      else
+        launch_batch<float>(L.op, L.d, (const Item<float>*)(items + L.item0 * p.item_size),
+                            p.d_starts + L.start0, L.nitems, L.nchunks, grid, x.st,
+                            (const Item<float>*)hi);
+      if (rep == 1) cudaEventRecord(ev[2 * i + 1], x.st);
+    }
+  cudaError_t e = cudaStreamSynchronize(x.st);
+  for (size_t i = 0; e == cudaSuccess && i < p.launches.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+    per[p.launches[i].op][p.launches[i].d] += ms;
+  }
+  for (auto& v : ev) cudaEventDestroy(v);
+  if (e != cudaSuccess) return fail(DF_ECUDA, "autotune: %s", cudaGetErrorString(e));
+  return DF_OK;
+}
+
+// Autotuner: first the tile shape of every (op, direction) -- each shape timed on
+// one coarse step of `runs`, the fastest kept -- then, when tune_grid, the
+// persistent blocks per SM of every op with those tiles.  The runs' state is
+// restored afterwards, so tuning does not advance them.
+int autotune(const std::vector<Run*>& runs, Exec& x, int prec, TileTable& tiles, bool tune_grid,
+             bool single_fast) {
+  Snapshot sn;
+  int rc = snapshot(runs, sn);
+  if (rc) return rc;
+  double best[OP_COUNT][3], per[OP_COUNT][3];
+  for (int o = 0; o < OP_COUNT; ++o)
+    for (int d = 0; d < 3; ++d) best[o][d] = INFINITY;
+  TileTable chosen = tiles;
+  for (int tk = 0; tk < kNumTiles && !rc; ++tk) {
+    TileTable tt;
+    for (int o = 0; o < OP_COUNT; ++o)
+      for (int d = 0; d < 3; ++d) tt.t[o][d] = tk;
+    Plan p;
+    rc = build_plan(p, runs, prec, 0, tt);
+    if (!rc) rc = time_plan(p, x, prec, 0, single_fast, per);
+    plan_free(p);
+    for (int o = 0; o < OP_COUNT && !rc; ++o)
+      for (int d = 0; d < 3 && is_box_op(o); ++d)
+        if (per[o][d] > 0 && per[o][d] < best[o][d]) {
+          best[o][d] = per[o][d];
+          chosen.t[o][d] = tk;
+        }
+  }
+  if (!rc) tiles = chosen;
+  if (!rc && tune_grid) {
+    const int cand[] = {1, 2, 4, 8, 16, 32};
+    double best_g[OP_COUNT];
+    int best_bps[OP_COUNT];
+    for (int o = 0; o < OP_COUNT; ++o) {
+      best_g[o] = INFINITY;
+      best_bps[o] = x.bps[o];
+    }
+    Plan p;
+    rc = build_plan(p, runs, prec, 0, tiles);
+    for (int gi = 0; gi < 6 && !rc; ++gi) {
+      rc = time_plan(p, x, prec, cand[gi], single_fast, per);
+      for (int o = 0; o < OP_COUNT && !rc; ++o) {
+        double s = per[o][0] + per[o][1] + per[o][2];
+        if (s > 0 && s < best_g[o]) {
+          best_g[o] = s;
+          best_bps[o] = cand[gi];
+        }
+      }
+    }
+    plan_free(p);
+    if (!rc)
+      for (int o = 0; o < OP_COUNT; ++o) x.bps[o] = best_bps[o];
+  }
+  int rc2 = restore(runs, sn);
+  return rc ? rc : rc2;
 }
 
 int step_plan(Plan& p, Exec& x, int prec, int n) {
@@ -1042,7 +1204,7 @@ int df_step(df_ctx* c, int n) {
       double ratio;
       df_xi_search(r->nl, lim, cost, xiw, &ratio);
       for (int l = 0; l + 1 < r->nl; ++l) r->xi[l] = xiw[l];
-      rc = build_plan(c->plan, runs, r->prec, c->full_boxes);
+      rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles);
       if (rc) break;
       c->x.launches += r->prec == DF_FP64 ? plan_run<double>(c->plan, c->x, c->x.timing)
                                           : plan_run<float>(c->plan, c->x, c->x.timing);
@@ -1051,7 +1213,7 @@ int df_step(df_ctx* c, int n) {
     for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
   } else {
     for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
-    if (!c->plan.valid) rc = build_plan(c->plan, runs, r->prec, c->full_boxes);
+    if (!c->plan.valid) rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles);
     if (!rc) rc = step_plan(c->plan, c->x, r->prec, n);
   }
   leave(c);
@@ -1280,6 +1442,37 @@ const char* df_kernel_name(int kind) {
   return kind >= 0 && kind < K_NKINDS ? names[kind] : "";
 }
 
+int df_autotune(df_ctx* c, int* tiles_out) {
+  if (check_ctx(c)) return DF_EINVAL;
+  DevGuard g(c->device);
+  CK(cudaStreamSynchronize(c->x.st));
+  std::vector<Run*> runs{c->run};
+  for (int l = 0; l < c->run->nl; ++l) c->run->xi[l] = 2;
+  int rc = autotune(runs, c->x, c->run->prec, c->tiles, false, true);
+  if (rc) return rc;
+  if (tiles_out)
+    for (int o = 0; o < OP_COUNT; ++o)
+      for (int d = 0; d < 3; ++d) tiles_out[3 * o + d] = c->tiles.t[o][d];
+  plan_invalidate(c->plan);
+  return DF_OK;
+}
+
+int set_shapes(TileTable& t, const int* shapes) {
+  if (!shapes) return fail(DF_EINVAL, "null argument");
+  for (int i = 0; i < 3 * OP_COUNT; ++i)
+    if (shapes[i] < 0 || shapes[i] >= kNumTiles) return fail(DF_EINVAL, "bad tile shape %d", shapes[i]);
+  for (int o = 0; o < OP_COUNT; ++o)
+    for (int d = 0; d < 3; ++d) t.t[o][d] = shapes[3 * o + d];
+  return DF_OK;
+}
+
+int df_set_tile_shapes(df_ctx* c, const int* shapes) {
+  if (check_ctx(c)) return DF_EINVAL;
+  int rc = set_shapes(c->tiles, shapes);
+  if (!rc) plan_invalidate(c->plan);
+  return rc;
+}
+
 int df_debug_full_boxes(df_ctx* c, int on) {
   if (!c) return fail(DF_EINVAL, "null context");
   c->full_boxes = on != 0;
@@ -1413,7 +1606,7 @@ int df_pool_step(df_pool* p, int n) {
   if (runs.empty() || n == 0) return DF_OK;
   DevGuard g(p->device);
   int rc = DF_OK;
-  if (!p->plan.valid) rc = build_plan(p->plan, runs, p->prec, 0);
+  if (!p->plan.valid) rc = build_plan(p->plan, runs, p->prec, 0, p->tiles);
   if (rc) return rc;
   enter(p);
   rc = step_plan(p->plan, p->x, p->prec, n);
@@ -1480,6 +1673,13 @@ int df_pool_set_tiles(df_pool* p, const int* blocks_per_sm) {
   return DF_OK;
 }
 
+int df_pool_set_tile_shapes(df_pool* p, const int* shapes) {
+  if (!p) return fail(DF_EINVAL, "null pool");
+  int rc = set_shapes(p->tiles, shapes);
+  if (!rc) plan_invalidate(p->plan);
+  return rc;
+}
+
 int df_pool_autotune(df_pool* p, int* blocks_per_sm_out) {
   if (!p) return fail(DF_EINVAL, "null pool");
   std::vector<Run*> runs;
@@ -1488,76 +1688,10 @@ int df_pool_autotune(df_pool* p, int* blocks_per_sm_out) {
   if (runs.empty()) return fail(DF_EINVAL, "empty pool");
   DevGuard g(p->device);
   CK(cudaStreamSynchronize(p->x.st));
-  // tuning steps run on the live state, which is restored afterwards
-  std::vector<std::vector<char>> snap(runs.size());
-  std::vector<DevScalars> snap_ds(runs.size());
-  std::vector<long long> snap_pos(runs.size());
-  for (size_t i = 0; i < runs.size(); ++i) {
-    Run* r = runs[i];
-    size_t plane = plane_bytes((size_t)r->L[0].v.nc, r->esz);
-    snap[i].resize(plane * 5 * r->nl);
-    for (int l = 0; l < r->nl; ++l)
-      CK(cudaMemcpy(snap[i].data() + plane * 5 * l, r->L[l].mem, plane * 5,
-                    cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&snap_ds[i], r->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(&snap_pos[i], r->ring_pos, sizeof(long long), cudaMemcpyDeviceToHost));
-  }
-  int rc = build_plan(p->plan, runs, p->prec, 0);
+  int rc = autotune(runs, p->x, p->prec, p->tiles, true, false);
   if (rc) return rc;
-  const int cand[] = {1, 2, 4, 8, 16, 32};
-  const int nc = (int)(sizeof cand / sizeof cand[0]);
-  double best_ms[OP_COUNT];
-  int best[OP_COUNT];
-  for (int o = 0; o < OP_COUNT; ++o) {
-    best_ms[o] = INFINITY;
-    best[o] = p->x.bps[o];
-  }
-  const unsigned char* items = (const unsigned char*)p->plan.d_items;
-  std::vector<cudaEvent_t> ev(2 * p->plan.launches.size());
-  for (auto& e : ev) cudaEventCreate(&e);
-  for (int ci = 0; ci < nc; ++ci) {
-    for (int rep = 0; rep < 2; ++rep)
-      for (size_t i = 0; i < p->plan.launches.size(); ++i) {
-        const LaunchDesc& L = p->plan.launches[i];
-        unsigned grid = (unsigned)p->x.sm_count * (unsigned)cand[ci];
-        if (rep == 1) cudaEventRecord(ev[2 * i], p->x.st);
-        // the multi-item path is the one tuned (single items use one block per chunk)
-        if (p->prec == DF_FP64)
-          launch_batch<double>(L.op, L.d, (const Item<double>*)(items + L.item0 * p->plan.item_size),
-                               p->plan.d_starts + L.start0, L.nitems, L.nchunks, grid, p->x.st,
-                               nullptr);
-        else
-          launch_batch<float>(L.op, L.d, (const Item<float>*)(items + L.item0 * p->plan.item_size),
-                              p->plan.d_starts + L.start0, L.nitems, L.nchunks, grid, p->x.st,
-                              nullptr);
-        if (rep == 1) cudaEventRecord(ev[2 * i + 1], p->x.st);
-      }
-    CK(cudaStreamSynchronize(p->x.st));
-    double per_op[OP_COUNT] = {};
-    for (size_t i = 0; i < p->plan.launches.size(); ++i) {
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
-      per_op[p->plan.launches[i].op] += ms;
-    }
-    for (int o = 0; o < OP_COUNT; ++o)
-      if (per_op[o] > 0 && per_op[o] < best_ms[o]) {
-        best_ms[o] = per_op[o];
-        best[o] = cand[ci];
-      }
-  }
-  for (auto& e : ev) cudaEventDestroy(e);
-  for (int o = 0; o < OP_COUNT; ++o) p->x.bps[o] = best[o];
   if (blocks_per_sm_out)
-    for (int o = 0; o < OP_COUNT; ++o) blocks_per_sm_out[o] = best[o];
-  for (size_t i = 0; i < runs.size(); ++i) {
-    Run* r = runs[i];
-    size_t plane = plane_bytes((size_t)r->L[0].v.nc, r->esz);
-    for (int l = 0; l < r->nl; ++l)
-      CK(cudaMemcpy(r->L[l].mem, snap[i].data() + plane * 5 * l, plane * 5,
-                    cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(r->ds, &snap_ds[i], sizeof(DevScalars), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(r->ring_pos, &snap_pos[i], sizeof(long long), cudaMemcpyHostToDevice));
-  }
+    for (int o = 0; o < OP_COUNT; ++o) blocks_per_sm_out[o] = p->x.bps[o];
   plan_invalidate(p->plan);
   return DF_OK;
 }

@@ -46,12 +46,28 @@ struct Scratch {
   void* P[3];   // momentum fluxes of the current sweep
 };
 
+// Box of a stencil op.  tile = 0: elements enumerated x fastest over the box;
+// tile = k > 0: in 256-element tiles of tile_extent(k, .) (x, y, z), tiles x
+// fastest, so a block's neighbour rows come from its own SM's L1.
 struct Box {
   int lo[3], hi[3];
+  int tile;
   long long count() const {
     return (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
   }
 };
+
+constexpr int kNumTiles = 5;
+// tile extents (x, y, z) with x*y*z = 256 of shape k (k = 0: flat enumeration)
+__host__ __device__ inline int tile_extent(int k, int axis) {
+  switch (k) {
+    case 1: return axis == 0 ? 32 : (axis == 1 ? 8 : 1);
+    case 2: return axis == 0 ? 32 : (axis == 1 ? 1 : 8);
+    case 3: return axis == 0 ? 32 : (axis == 1 ? 4 : 2);
+    case 4: return axis == 0 ? 64 : (axis == 1 ? 4 : 1);
+    default: return 1;
+  }
+}
 
 struct Phys {
   double gamma, rho0, e0, V[3], GM, eps, chi, L, cfl, cfl_diff, dt_fixed;
@@ -122,6 +138,12 @@ enum Op {
   OP_TMOM, OP_TUPDATE, OP_VREC, OP_BC, OP_COMMUP, OP_COMMMEAN, OP_ZERO_ACC, OP_DT_LEVEL,
   OP_DT_FINAL, OP_FORCE_LEVEL, OP_FORCE_FINAL, OP_TIME, OP_COUNT
 };
+
+// ops that enumerate the elements of a box (the ones a tile shape applies to)
+__host__ __device__ inline bool is_box_op(int op) {
+  return op == OP_SOURCE || op == OP_COMPRESS || op == OP_DIFFUSE || op == OP_TPREP ||
+         op == OP_TFLUX || op == OP_TMOM || op == OP_TUPDATE || op == OP_VREC;
+}
 
 enum ItemFlags {
   FL_WRITE_PI = 1, FL_SS3 = 2, FL_LUM = 4, FL_EPS = 8, FL_DFR = 16, FL_HYDRO = 32

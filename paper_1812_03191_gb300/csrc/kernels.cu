@@ -27,12 +27,28 @@ constexpr int kBlock = 256;
 // box element t -> (i, j, k); boxes hold fewer than 2^31 elements
 __device__ __forceinline__ bool decode(const Box& b, unsigned t, int& i, int& j, int& k) {
   unsigned bx = b.hi[0] - b.lo[0], by = b.hi[1] - b.lo[1], bz = b.hi[2] - b.lo[2];
-  unsigned plane = bx * by;
-  if (t >= plane * bz) return false;
-  unsigned kk = t / plane;
-  unsigned r = t - kk * plane;
-  unsigned jj = r / bx;
-  i = b.lo[0] + (int)(r - jj * bx);
+  if (b.tile == 0) {
+    unsigned plane = bx * by;
+    if (t >= plane * bz) return false;
+    unsigned kk = t / plane;
+    unsigned r = t - kk * plane;
+    unsigned jj = r / bx;
+    i = b.lo[0] + (int)(r - jj * bx);
+    j = b.lo[1] + (int)jj;
+    k = b.lo[2] + (int)kk;
+    return true;
+  }
+  const unsigned tx = tile_extent(b.tile, 0), ty = tile_extent(b.tile, 1);
+  const unsigned tz = tile_extent(b.tile, 2);
+  unsigned nx = (bx + tx - 1) / tx, ny = (by + ty - 1) / ty;
+  unsigned T = t >> 8, l = t & 255u;
+  unsigned Tz = T / (nx * ny), r = T - Tz * nx * ny;
+  unsigned Ty = r / nx, Tx = r - Ty * nx;
+  unsigned lz = l / (tx * ty), r2 = l - lz * tx * ty;
+  unsigned ly = r2 / tx, lx = r2 - ly * tx;
+  unsigned ii = Tx * tx + lx, jj = Ty * ty + ly, kk = Tz * tz + lz;
+  if (ii >= bx || jj >= by || kk >= bz) return false;
+  i = b.lo[0] + (int)ii;
   j = b.lo[1] + (int)jj;
   k = b.lo[2] + (int)kk;
   return true;
@@ -68,17 +84,14 @@ __device__ __forceinline__ T vanleer(T dl, T dr) {
   return pr <= T(0) ? T(0) : hdiv(T(2) * pr, dl + dr);
 }
 
-// time-centred upwind value at the face between elements c-st and c
+// time-centred upwind value at the face between elements c-st and c.  The four
+// candidate elements are loaded before the upwind side is chosen, so the loads
+// do not wait for the face velocity.
 template <class T>
 __device__ __forceinline__ T upwind(const T* __restrict__ q, int c, int st, T u, T cour) {
-  if (u > T(0)) {
-    T a = q[c - st];
-    T sl = vanleer(a - q[c - 2 * st], q[c] - a);
-    return a + T(0.5) * (T(1) - cour) * sl;
-  }
-  T a = q[c];
-  T sr = vanleer(a - q[c - st], q[c + st] - a);
-  return a - T(0.5) * (T(1) + cour) * sr;
+  const T qmm = q[c - 2 * st], qm = q[c - st], q0 = q[c], qp = q[c + st];
+  if (u > T(0)) return qm + T(0.5) * (T(1) - cour) * vanleer(qm - qmm, q0 - qm);
+  return q0 - T(0.5) * (T(1) + cour) * vanleer(q0 - qm, qp - q0);
 }
 
 inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
@@ -1195,8 +1208,17 @@ unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const B
   };
   switch (op) {
     case OP_SOURCE: case OP_COMPRESS: case OP_DIFFUSE: case OP_TPREP: case OP_TFLUX:
-    case OP_TMOM: case OP_TUPDATE: case OP_VREC:
-      n = b.count();
+    case OP_TMOM: case OP_TUPDATE: case OP_VREC:  // is_box_op
+      if (b.tile == 0) {
+        n = b.count();
+      } else {
+        long long nt = 1;
+        for (int a = 0; a < 3; ++a) {
+          int e = tile_extent(b.tile, a);
+          nt *= (b.hi[a] - b.lo[a] + e - 1) / e;
+        }
+        n = nt * 256;
+      }
       break;
     case OP_FRONTIER_DIFF: n = slots(0, 6); break;
     case OP_TFRONTIER: n = slots(2 * d, 2); break;

@@ -160,6 +160,39 @@ def test_margin_boxes_equal_full_boxes():
     assert np.array_equal(a.force()[0], b.force()[0])
 
 
+@pytest.mark.parametrize("precision", [binding.DF_FP64, binding.DF_FP32_STATE])
+def test_tile_shapes_bitwise_equal(precision):
+    """Tile shapes change only the order in which blocks visit a box: every shape gives
+    the flat enumeration's result bit for bit, and autotuning does not advance the run."""
+    p = I.base_params(GM=0.01, eps=0.125, chi=1.0, L=0.05, lum_sigma=0.125, mach=0.9)
+    sims = []
+    for shape in range(5):
+        s = binding.Sim(3, 24, (-6.0,) * 3, (6.0,) * 3, I.DEFAULT_G, p, precision=precision)
+        for l in range(3):
+            for f in range(5):
+                base = s.get_field(l, f)
+                s.set_field(l, f, base + I.smooth_perturbation((24,) * 3, 70 + 5 * l + f, 5e-3))
+        s.set_tile_shapes(shape)
+        sims.append(s)
+    tuned = sims[0]
+    tuned.step(2)
+    before = [tuned.get_field(l, f) for l in range(3) for f in range(5)]
+    t0 = tuned.status()[0]
+    shapes = tuned.autotune()
+    assert all(0 <= v < 5 for row in shapes for v in row)
+    assert tuned.status()[0] == t0
+    assert all(np.array_equal(a, tuned.get_field(l, f))
+               for (l, f), a in zip([(l, f) for l in range(3) for f in range(5)], before))
+    tuned.step(8)
+    for s in sims[1:]:
+        s.step(10)
+    for s in sims[1:]:
+        for l in range(3):
+            for f in range(5):
+                assert np.array_equal(tuned.get_field(l, f), s.get_field(l, f)), (l, f)
+        assert np.array_equal(tuned.force()[0], s.force()[0])
+
+
 def test_inter_level_operators():
     p = I.base_params()
     sim, orc = pair(2, 24, 6.0, p)

@@ -97,6 +97,7 @@ def test_autotune_keeps_state_and_results():
         pool.step(2)
     tiles = pb.autotune()
     assert len(tiles) == binding.POOL_OPS and all(1 <= t <= 32 for t in tiles)
+    pa.set_tile_shapes(3)  # a fixed tile shape on one side, the tuned ones on the other
     pa.step(3)
     pb.step(3)
     for slot in (0, 1):
