@@ -131,7 +131,8 @@ ARRAYS_PER_ELEM = {
     "tflux": 5,          # rho, e/rho, v_d -> F, E
     "tmom": 8,           # w3, F, v_d -> P3
     "tupdate": 15,       # F, E, P3, rho, e, pi3 -> rho, e, pi3
-    "vrec_source": 9,    # rho, e, phi, pi3 -> v3
+    "vrec_source": 9,    # rho, e, phi, pi3 -> v3 (after fused sweeps also -> rho, e)
+    "sweep": 11,         # fused sweep: rho, e, pi3, v_d -> rho, e, pi3
 }
 
 
@@ -154,11 +155,12 @@ def level_step_boxes(cfg):
     return [min(n + 2 * m, n + 2 * G) ** 3 for m in margins]
 
 
-def bytes_per_launch(cfg, kind, esz):
+def bytes_per_launch(cfg, kind, esz, fused=False):
     boxes = level_step_boxes(cfg)
     n, G = cfg["n"], cfg["G"]
     if kind in ARRAYS_PER_ELEM:
-        return ARRAYS_PER_ELEM[kind] * esz * sum(boxes) / len(boxes)
+        arrays = ARRAYS_PER_ELEM[kind] + (2 if fused and kind == "vrec_source" else 0)
+        return arrays * esz * sum(boxes) / len(boxes)
     if kind == "commup":  # write every fine ghost element, read each coarse host once
         return 5 * esz * (((n + 2 * G) ** 3 - n**3) + (n // 2 + G + 2) ** 3)
     if kind == "commmean":  # read 8 fine cells / 4 faces, write the covered coarse cell
@@ -277,8 +279,9 @@ def run_batched(args):
     per_step_bytes = 0.0
     for r in runs:
         boxes = level_step_boxes(dict(n=r["n"], G=r["G"], n_levels=r["n_levels"]))
-        mult = 3 if dom in ("tprep", "tflux", "tmom", "tupdate") else 1
-        per_step_bytes += ARRAYS_PER_ELEM[dom] * esz * sum(boxes) * mult
+        mult = 3 if dom in ("tprep", "tflux", "tmom", "tupdate", "sweep") else 1
+        arrays = ARRAYS_PER_ELEM[dom] + (2 if dom == "vrec_source" else 0)  # fused sweeps
+        per_step_bytes += arrays * esz * sum(boxes) * mult
     dom_ms, dom_n = kinds[dom]
     achieved = per_step_bytes * args.steps / (dom_ms / 1e3) / 1e9
     peak, peak_kind = peaks()
@@ -441,6 +444,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--transport", default="auto", choices=["auto", "separate", "fused"],
+                    help="transport kernels: fused sweeps (default for the FP32 state) or "
+                         "separate kernels (default for FP64)")
     ap.add_argument("--tiles", default="auto", choices=["auto", "flat"],
                     help="tile shapes of the stencil launches: autotuned (before the "
                          "warm-up, untimed) or flat enumeration")
@@ -484,6 +490,11 @@ def main():
     cu = cell_updates_per_step(cfg)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    transport = {"auto": binding.TRANSPORT_AUTO, "separate": binding.TRANSPORT_SEPARATE,
+                 "fused": binding.TRANSPORT_FUSED}[args.transport]
+    sim.set_transport(transport)
+    fused = transport == binding.TRANSPORT_FUSED or (
+        transport == binding.TRANSPORT_AUTO and prec == binding.DF_FP32_STATE)
     shapes = sim.autotune() if args.tiles == "auto" else None
     for _ in range(args.warmup):
         sim.step(1)
@@ -530,9 +541,9 @@ def main():
     esz = 8 if prec == binding.DF_FP64 else 4
     # dominant kernel with a defined algorithmic byte count
     ranked = sorted(kinds, key=lambda k: -kinds[k][0])
-    dom = next(k for k in ranked if bytes_per_launch(cfg, k, esz) is not None)
+    dom = next(k for k in ranked if bytes_per_launch(cfg, k, esz, fused) is not None)
     dom_ms, dom_n = kinds[dom]
-    bpl = bytes_per_launch(cfg, dom, esz)
+    bpl = bytes_per_launch(cfg, dom, esz, fused)
     avg_s = dom_ms / dom_n / 1e3
     achieved = bpl / avg_s / 1e9
     peak, peak_kind = peaks()
@@ -590,7 +601,8 @@ def main():
                        "cell_updates_per_step": cu, "l2": "flushed between timed steps "
                        "(256 MB write outside the step events)",
                        "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
-                       "tile_shapes": tile_summary(shapes)},
+                       "tile_shapes": tile_summary(shapes),
+                       "transport": "fused sweeps" if fused else "separate kernels"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

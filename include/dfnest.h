@@ -140,7 +140,7 @@ long long df_kernel_launches(const df_ctx* ctx);
  * then returns the summed device time (ms) and launch count of one kernel kind
  * since df_set_timing; df_kernel_name(kind) names the kinds 0..DF_KERNEL_KINDS-1.
  * df_set_timing resets the totals. */
-#define DF_KERNEL_KINDS 16
+#define DF_KERNEL_KINDS 17
 int df_set_timing(df_ctx* ctx, int on);
 int df_kernel_time(df_ctx* ctx, int kind, double* ms, long long* launches);
 const char* df_kernel_name(int kind);
@@ -155,6 +155,20 @@ int df_autotune(df_ctx* ctx, int* tiles_out);
 /* Set the tile shape (0..4, in the order above) of every operator and direction:
  * shapes[3 * op + d].  DF_EINVAL for a null pointer or a shape out of range. */
 int df_set_tile_shapes(df_ctx* ctx, const int* shapes);
+
+/* Transport kernels (Sec. 3.1 sweeps).  DF_TRANSPORT_SEPARATE: four kernels per sweep
+ * (e/rho and Pi/rho_face; mass and energy fluxes; momentum fluxes; conservative
+ * update) exchanging their results through HBM.  DF_TRANSPORT_FUSED: one kernel per
+ * sweep that keeps them in shared memory for a tile plus its halo (the halo's
+ * quotients and fluxes are recomputed by neighbouring tiles) and ping-pongs the
+ * state through a second copy; about a third of the memory traffic.  The two give
+ * the same arithmetic on every active cell (equal up to the compiler's contraction
+ * of multiply-adds).  DF_TRANSPORT_AUTO (default): fused for DF_FP32_STATE,
+ * separate for DF_FP64, whose kernels are bound by the FP64 pipe. */
+#define DF_TRANSPORT_AUTO 0
+#define DF_TRANSPORT_SEPARATE 1
+#define DF_TRANSPORT_FUSED 2
+int df_set_transport(df_ctx* ctx, int mode);
 
 /* Verification switch: with on != 0 every operator runs over its whole stencil
  * range in the padded array (the ghost layers evolve exactly as in a plain
@@ -244,9 +258,11 @@ int df_pool_info(df_pool* pool, int* active, size_t* used, size_t* budget, long 
  * SM and for each tile shape (as df_autotune), keeps the fastest per operator
  * (blocks per SM written to blocks_per_sm_out, nullable) and restores the runs'
  * state. */
-#define DF_POOL_OPS 19
+#define DF_POOL_OPS 20
 int df_pool_set_tiles(df_pool* pool, const int* blocks_per_sm);
 int df_pool_autotune(df_pool* pool, int* blocks_per_sm_out);
+/* As df_set_transport, for every run of the pool. */
+int df_pool_set_transport(df_pool* pool, int mode);
 /* As df_set_tile_shapes, for every run of the pool. */
 int df_pool_set_tile_shapes(df_pool* pool, const int* shapes);
 

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libdfnest.so")
 
 DF_OK, DF_EINVAL, DF_ENOMEM, DF_ECUDA, DF_EUNHEALTHY, DF_ETIMEOUT, DF_EBUSY = 0, -1, -2, -3, -4, -5, -6
 DF_FP64, DF_FP32_STATE = 0, 1
-KERNEL_KINDS = 16
+KERNEL_KINDS = 17
 
 # every symbol include/dfnest.h declares
 EXPORTS = (
@@ -29,13 +29,15 @@ EXPORTS = (
     "df_run_bytes", "df_pool_create", "df_pool_admit", "df_pool_release", "df_pool_step",
     "df_pool_query", "df_pool_get_field", "df_pool_info", "df_pool_set_tiles",
     "df_pool_autotune", "df_pool_destroy", "df_pool_set_timing", "df_pool_kernel_time",
-    "df_autotune", "df_set_tile_shapes", "df_pool_set_tile_shapes",
+    "df_autotune", "df_set_tile_shapes", "df_pool_set_tile_shapes", "df_set_transport",
+    "df_pool_set_transport",
 )
-POOL_OPS = 19
+POOL_OPS = 20
 # operator order of the per-op tables (tile shapes, blocks per SM)
 OP_NAMES = ("source", "compress", "frontier_diff", "diffuse", "tprep", "tflux", "tfrontier",
             "tmom", "tupdate", "vrec_source", "bc", "commup", "commmean", "zero_acc",
-            "dt_level", "dt_final", "force_level", "force_final", "time")
+            "dt_level", "dt_final", "force_level", "force_final", "time", "sweep")
+TRANSPORT_AUTO, TRANSPORT_SEPARATE, TRANSPORT_FUSED = 0, 1, 2
 NOALLOC_MAX_CELLS = 4194304
 
 
@@ -105,6 +107,8 @@ def load(path: str = LIB_PATH):
         "df_debug_full_boxes": (C.c_int, [vp, C.c_int]),
         "df_autotune": (C.c_int, [vp, P(C.c_int)]),
         "df_set_tile_shapes": (C.c_int, [vp, P(C.c_int)]),
+        "df_set_transport": (C.c_int, [vp, C.c_int]),
+        "df_pool_set_transport": (C.c_int, [vp, C.c_int]),
         "df_pool_set_tile_shapes": (C.c_int, [vp, P(C.c_int)]),
         "df_destroy": (C.c_int, [vp]),
         "df_xi_search": (C.c_int, [C.c_int, dp, dp, P(C.c_int), dp]),
@@ -344,6 +348,9 @@ class Sim:
         """shapes: POOL_OPS x 3 tile shape indices (or one index for all)"""
         _check(self.lib.df_set_tile_shapes(self.h, _shapes(shapes)))
 
+    def set_transport(self, mode):
+        _check(self.lib.df_set_transport(self.h, int(mode)))
+
     def debug_full_boxes(self, on):
         _check(self.lib.df_debug_full_boxes(self.h, 1 if on else 0))
 
@@ -436,6 +443,9 @@ class Pool:
 
     def set_tile_shapes(self, shapes):
         _check(self.lib.df_pool_set_tile_shapes(self.h, _shapes(shapes)))
+
+    def set_transport(self, mode):
+        _check(self.lib.df_pool_set_transport(self.h, int(mode)))
 
     def set_tiles(self, blocks_per_sm):
         arr = (C.c_int * POOL_OPS)(*blocks_per_sm)

@@ -269,6 +269,9 @@ int run_create(Run** out, int n_levels, const int n[3], const double lo[3], cons
     r->S.F = b + plane * 7;
     r->S.E = b + plane * 8;
     for (int m = 0; m < 3; ++m) r->S.P[m] = b + plane * (9 + m);
+    r->S.qb[0] = r->S.eps;
+    for (int m = 0; m < 3; ++m) r->S.qb[1 + m] = r->S.w[m];
+    r->S.qb[4] = r->S.P[0];
   }
   CKR(cudaMalloc(&r->ds, sizeof(DevScalars)));
   CKR(cudaMemset(r->ds, 0, sizeof(DevScalars)));
@@ -404,6 +407,7 @@ int kind_of(int op) {
     case OP_COMMMEAN: return K_COMMMEAN;
     case OP_DT_LEVEL: case OP_DT_FINAL: return K_DT;
     case OP_FORCE_LEVEL: case OP_FORCE_FINAL: return K_FORCE;
+    case OP_SWEEP: return K_SWEEP;
     default: return K_OTHER;
   }
 }
@@ -447,6 +451,7 @@ struct Builder {
   int full_boxes = 0;
   const DtFinal* d_fins = nullptr;
   TileTable tiles;
+  bool fused = false;  // transport as one fused kernel per sweep
 
   Item<T> base(const Run& r, int l) const {
     Item<T> it;
@@ -476,9 +481,23 @@ struct Builder {
     return it;
   }
 
+  // planes per chunk of a fused sweep's marching axis: enough chunks for about 600
+  // blocks, at least 8 planes (16 when marching along the sweep, whose chunks start
+  // 3 planes early and finish 2 planes late)
+  static int sweep_chunk(const Box& b, int d) {
+    const int ra = sweep_row_axis(d), mu = sweep_march_axis(d), ow = sweep_own_x(d);
+    const int ncols = ((b.hi[0] - b.lo[0] + ow - 1) / ow) *
+                      ((b.hi[ra] - b.lo[ra] + kSweepRows - 1) / kSweepRows);
+    const int nm = b.hi[mu] - b.lo[mu];
+    const int chunks = std::max(1, 600 / std::max(1, ncols));
+    const int zc = (nm + chunks - 1) / chunks;
+    return std::min(nm, std::max(zc, d == 0 ? 8 : 16));
+  }
+
   Box box(const LevelView& v, int margin) const {
     Box b;
     b.tile = 0;
+    b.zc = 0;
     int M = full_boxes ? v.G : margin;
     for (int d = 0; d < 3; ++d) {
       b.lo[d] = std::max(0, v.G - M);
@@ -489,6 +508,7 @@ struct Builder {
 
   void add(std::vector<Entry>& out, int op, int d, Item<T> it) const {
     it.b.tile = is_box_op(op) ? tiles.t[op][d] : 0;
+    it.b.zc = op == OP_SWEEP ? sweep_chunk(it.b, d) : 0;
     it.count = op_count(op, d, it.L, it.F, it.b);
     out.push_back({op, d, it});
   }
@@ -510,7 +530,15 @@ struct Builder {
       if (it.L.is_child) add(out, OP_FRONTIER_DIFF, 0, it);
       add(out, OP_DIFFUSE, 0, it);
     }
-    if (P.hydro_on) {
+    if (P.hydro_on && fused) {
+      for (int d = 0; d < 3; ++d) {
+        add(out, OP_SWEEP, d, it);
+        if (it.L.is_child) add(out, OP_TFRONTIER, d, it);
+      }
+      Item<T> vr = it;
+      vr.flags |= FL_FUSED;
+      add(out, OP_VREC, 0, vr);
+    } else if (P.hydro_on) {
       for (int d = 0; d < 3; ++d) {
         add(out, OP_TPREP, 0, it);
         add(out, OP_TFLUX, d, it);
@@ -644,7 +672,7 @@ int plan_upload(Plan& plan) {
 
 template <class T>
 int plan_build(Plan& plan, const std::vector<Run*>& runs, int full_boxes,
-               const TileTable& tiles = TileTable()) {
+               const TileTable& tiles, bool fused) {
   plan_invalidate(plan);
   plan.prec = sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE;
   size_t nr = runs.size();
@@ -658,6 +686,7 @@ int plan_build(Plan& plan, const std::vector<Run*>& runs, int full_boxes,
   B.full_boxes = full_boxes;
   B.d_fins = plan.d_fins;
   B.tiles = tiles;
+  B.fused = fused;
   B.per_run.resize(nr);
   for (size_t r = 0; r < nr; ++r) B.coarse_step(*runs[r], (int)r, B.per_run[r]);
   B.merge(plan);
@@ -744,10 +773,11 @@ struct Exec {
   }
 };
 
-void exec_init(Exec& x, int device) {
+bool exec_init(Exec& x, int device) {
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms)
     x.sm_count = sms;
+  return true;
 }
 
 void exec_free(Exec& x) {
@@ -899,6 +929,7 @@ struct df_ctx {
   Exec x;
   int full_boxes = 0;
   TileTable tiles;
+  int transport = DF_TRANSPORT_AUTO;
 };
 
 struct df_pool {
@@ -910,6 +941,7 @@ struct df_pool {
   Plan plan;
   Exec x;
   TileTable tiles;
+  int transport = DF_TRANSPORT_AUTO;
 };
 
 namespace {
@@ -939,10 +971,18 @@ int sync_health(cudaStream_t st, Run* r) {
   return DF_OK;
 }
 
+// transport mode: DF_TRANSPORT_AUTO (fused sweeps for the FP32 state, separate
+// kernels for FP64, whose kernels are bound by the FP64 pipe and would repeat the
+// halo arithmetic), DF_TRANSPORT_SEPARATE or DF_TRANSPORT_FUSED
+bool fused_for(int mode, int prec) {
+  return mode == DF_TRANSPORT_FUSED || (mode == DF_TRANSPORT_AUTO && prec == DF_FP32_STATE);
+}
+
 int build_plan(Plan& p, const std::vector<Run*>& runs, int prec, int full_boxes,
-               const TileTable& tiles) {
-  return prec == DF_FP64 ? plan_build<double>(p, runs, full_boxes, tiles)
-                         : plan_build<float>(p, runs, full_boxes, tiles);
+               const TileTable& tiles, int transport) {
+  bool f = fused_for(transport, prec);
+  return prec == DF_FP64 ? plan_build<double>(p, runs, full_boxes, tiles, f)
+                         : plan_build<float>(p, runs, full_boxes, tiles, f);
 }
 
 // state of the runs that tuning steps disturb (fields, scalars, force-ring cursor)
@@ -1037,8 +1077,8 @@ int time_plan(const Plan& p, Exec& x, int prec, int bps, bool single_fast,
 // one coarse step of `runs`, the fastest kept -- then, when tune_grid, the
 // persistent blocks per SM of every op with those tiles.  The runs' state is
 // restored afterwards, so tuning does not advance them.
-int autotune(const std::vector<Run*>& runs, Exec& x, int prec, TileTable& tiles, bool tune_grid,
-             bool single_fast) {
+int autotune(const std::vector<Run*>& runs, Exec& x, int prec, int transport, TileTable& tiles,
+             bool tune_grid, bool single_fast) {
   Snapshot sn;
   int rc = snapshot(runs, sn);
   if (rc) return rc;
@@ -1051,7 +1091,7 @@ int autotune(const std::vector<Run*>& runs, Exec& x, int prec, TileTable& tiles,
     for (int o = 0; o < OP_COUNT; ++o)
       for (int d = 0; d < 3; ++d) tt.t[o][d] = tk;
     Plan p;
-    rc = build_plan(p, runs, prec, 0, tt);
+    rc = build_plan(p, runs, prec, 0, tt, transport);
     if (!rc) rc = time_plan(p, x, prec, 0, single_fast, per);
     plan_free(p);
     for (int o = 0; o < OP_COUNT && !rc; ++o)
@@ -1071,7 +1111,7 @@ int autotune(const std::vector<Run*>& runs, Exec& x, int prec, TileTable& tiles,
       best_bps[o] = x.bps[o];
     }
     Plan p;
-    rc = build_plan(p, runs, prec, 0, tiles);
+    rc = build_plan(p, runs, prec, 0, tiles, transport);
     for (int gi = 0; gi < 6 && !rc; ++gi) {
       rc = time_plan(p, x, prec, cand[gi], single_fast, per);
       for (int o = 0; o < OP_COUNT && !rc; ++o) {
@@ -1139,8 +1179,8 @@ int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], co
     delete c;
     return rc;
   }
-  exec_init(c->x, device);
-  if (cudaStreamCreateWithFlags(&c->x.st, cudaStreamNonBlocking) != cudaSuccess ||
+  if (!exec_init(c->x, device) ||
+      cudaStreamCreateWithFlags(&c->x.st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
     run_free(c->run);
@@ -1204,7 +1244,7 @@ int df_step(df_ctx* c, int n) {
       double ratio;
       df_xi_search(r->nl, lim, cost, xiw, &ratio);
       for (int l = 0; l + 1 < r->nl; ++l) r->xi[l] = xiw[l];
-      rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles);
+      rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles, c->transport);
       if (rc) break;
       c->x.launches += r->prec == DF_FP64 ? plan_run<double>(c->plan, c->x, c->x.timing)
                                           : plan_run<float>(c->plan, c->x, c->x.timing);
@@ -1213,7 +1253,7 @@ int df_step(df_ctx* c, int n) {
     for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
   } else {
     for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
-    if (!c->plan.valid) rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles);
+    if (!c->plan.valid) rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles, c->transport);
     if (!rc) rc = step_plan(c->plan, c->x, r->prec, n);
   }
   leave(c);
@@ -1438,7 +1478,7 @@ const char* df_kernel_name(int kind) {
   static const char* names[K_NKINDS] = {
       "bc_fill",  "source",   "compress_lum", "diffuse",  "frontier_diff", "tprep",
       "tflux",    "tfrontier", "tmom",        "tupdate",  "vrec_source",   "commup",
-      "commmean", "dt",       "force",        "other"};
+      "commmean", "dt",       "force",        "sweep",    "other"};
   return kind >= 0 && kind < K_NKINDS ? names[kind] : "";
 }
 
@@ -1448,7 +1488,7 @@ int df_autotune(df_ctx* c, int* tiles_out) {
   CK(cudaStreamSynchronize(c->x.st));
   std::vector<Run*> runs{c->run};
   for (int l = 0; l < c->run->nl; ++l) c->run->xi[l] = 2;
-  int rc = autotune(runs, c->x, c->run->prec, c->tiles, false, true);
+  int rc = autotune(runs, c->x, c->run->prec, c->transport, c->tiles, false, true);
   if (rc) return rc;
   if (tiles_out)
     for (int o = 0; o < OP_COUNT; ++o)
@@ -1471,6 +1511,15 @@ int df_set_tile_shapes(df_ctx* c, const int* shapes) {
   int rc = set_shapes(c->tiles, shapes);
   if (!rc) plan_invalidate(c->plan);
   return rc;
+}
+
+int df_set_transport(df_ctx* c, int mode) {
+  if (check_ctx(c)) return DF_EINVAL;
+  if (mode < DF_TRANSPORT_AUTO || mode > DF_TRANSPORT_FUSED)
+    return fail(DF_EINVAL, "unknown transport mode %d", mode);
+  c->transport = mode;
+  plan_invalidate(c->plan);
+  return DF_OK;
 }
 
 int df_debug_full_boxes(df_ctx* c, int on) {
@@ -1531,11 +1580,11 @@ int df_pool_create(df_pool** out, size_t budget, int precision, int device, void
   p->prec = precision;
   p->budget = budget;
   p->user = (cudaStream_t)stream;
-  exec_init(p->x, device);
+  bool ok = exec_init(p->x, device);
   // every pool launch goes through the work-list kernel, so a run's arithmetic is
   // the same alone in a pool and in any mix of runs (bitwise)
   p->x.single_fast = false;
-  if (cudaStreamCreateWithFlags(&p->x.st, cudaStreamNonBlocking) != cudaSuccess ||
+  if (!ok || cudaStreamCreateWithFlags(&p->x.st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess) {
     delete p;
@@ -1606,7 +1655,7 @@ int df_pool_step(df_pool* p, int n) {
   if (runs.empty() || n == 0) return DF_OK;
   DevGuard g(p->device);
   int rc = DF_OK;
-  if (!p->plan.valid) rc = build_plan(p->plan, runs, p->prec, 0, p->tiles);
+  if (!p->plan.valid) rc = build_plan(p->plan, runs, p->prec, 0, p->tiles, p->transport);
   if (rc) return rc;
   enter(p);
   rc = step_plan(p->plan, p->x, p->prec, n);
@@ -1673,6 +1722,15 @@ int df_pool_set_tiles(df_pool* p, const int* blocks_per_sm) {
   return DF_OK;
 }
 
+int df_pool_set_transport(df_pool* p, int mode) {
+  if (!p) return fail(DF_EINVAL, "null pool");
+  if (mode < DF_TRANSPORT_AUTO || mode > DF_TRANSPORT_FUSED)
+    return fail(DF_EINVAL, "unknown transport mode %d", mode);
+  p->transport = mode;
+  plan_invalidate(p->plan);
+  return DF_OK;
+}
+
 int df_pool_set_tile_shapes(df_pool* p, const int* shapes) {
   if (!p) return fail(DF_EINVAL, "null pool");
   int rc = set_shapes(p->tiles, shapes);
@@ -1688,7 +1746,7 @@ int df_pool_autotune(df_pool* p, int* blocks_per_sm_out) {
   if (runs.empty()) return fail(DF_EINVAL, "empty pool");
   DevGuard g(p->device);
   CK(cudaStreamSynchronize(p->x.st));
-  int rc = autotune(runs, p->x, p->prec, p->tiles, true, false);
+  int rc = autotune(runs, p->x, p->prec, p->transport, p->tiles, true, false);
   if (rc) return rc;
   if (blocks_per_sm_out)
     for (int o = 0; o < OP_COUNT; ++o) blocks_per_sm_out[o] = p->x.bps[o];

@@ -44,6 +44,9 @@ struct Scratch {
   void* F;      // mass flux of the current sweep
   void* E;      // energy flux of the current sweep
   void* P[3];   // momentum fluxes of the current sweep
+  // second copy of (rho, e, Pi_x, Pi_y, Pi_z) for the fused sweeps (planes of eps,
+  // w and P[0], which the fused path does not use): x writes it, y reads it, z writes it
+  void* qb[5];
 };
 
 // Box of a stencil op.  tile = 0: elements enumerated x fastest over the box;
@@ -52,6 +55,7 @@ struct Scratch {
 struct Box {
   int lo[3], hi[3];
   int tile;
+  int zc;  // fused sweeps: planes per chunk of the marching axis
   long long count() const {
     return (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
   }
@@ -67,6 +71,22 @@ __host__ __device__ inline int tile_extent(int k, int axis) {
     case 4: return axis == 0 ? 64 : (axis == 1 ? 4 : 1);
     default: return 1;
   }
+}
+
+// Fused transport sweep: a block of kSweepRows + 1 warps; each warp holds one row
+// of 32 consecutive x positions (a few of them halo for the x-stencil), the extra
+// warp the row below the block's rows, and the block marches through zc planes of
+// the marching axis (z for the x sweep, the sweep axis itself for y and z).
+constexpr int kSweepRows = 8;
+constexpr int kSweepThreads = 32 * (kSweepRows + 1);
+__host__ __device__ inline int sweep_own_x(int d) { return d == 0 ? 27 : 31; }
+__host__ __device__ inline int sweep_row_axis(int d) { return d == 1 ? 2 : 1; }
+__host__ __device__ inline int sweep_march_axis(int d) { return d == 0 ? 2 : d; }
+__host__ __device__ inline int sweep_units(const Box& b, int d) {
+  const int ra = sweep_row_axis(d), mu = sweep_march_axis(d), ow = sweep_own_x(d);
+  const int nsx = (b.hi[0] - b.lo[0] + ow - 1) / ow;
+  const int nsr = (b.hi[ra] - b.lo[ra] + kSweepRows - 1) / kSweepRows;
+  return nsx * nsr * ((b.hi[mu] - b.lo[mu] + b.zc - 1) / b.zc);
 }
 
 struct Phys {
@@ -136,7 +156,7 @@ struct DtFinal {
 enum Op {
   OP_SOURCE = 0, OP_COMPRESS, OP_FRONTIER_DIFF, OP_DIFFUSE, OP_TPREP, OP_TFLUX, OP_TFRONTIER,
   OP_TMOM, OP_TUPDATE, OP_VREC, OP_BC, OP_COMMUP, OP_COMMMEAN, OP_ZERO_ACC, OP_DT_LEVEL,
-  OP_DT_FINAL, OP_FORCE_LEVEL, OP_FORCE_FINAL, OP_TIME, OP_COUNT
+  OP_DT_FINAL, OP_FORCE_LEVEL, OP_FORCE_FINAL, OP_TIME, OP_SWEEP, OP_COUNT
 };
 
 // ops that enumerate the elements of a box (the ones a tile shape applies to)
@@ -146,7 +166,8 @@ __host__ __device__ inline bool is_box_op(int op) {
 }
 
 enum ItemFlags {
-  FL_WRITE_PI = 1, FL_SS3 = 2, FL_LUM = 4, FL_EPS = 8, FL_DFR = 16, FL_HYDRO = 32
+  FL_WRITE_PI = 1, FL_SS3 = 2, FL_LUM = 4, FL_EPS = 8, FL_DFR = 16, FL_HYDRO = 32,
+  FL_FUSED = 64  // VREC: the transport ran as fused sweeps (state in Scratch::qb)
 };
 
 // One work item.  Plain data, copied to shared memory by the kernel; size a
@@ -195,7 +216,8 @@ template <class T> int launch_unpack_active(const LevelView& L, int field, const
 // kernel kinds for the timing hook (df_kernel_time / df_kernel_name)
 enum KernelKind {
   K_BC = 0, K_SOURCE, K_COMPRESS, K_DIFFUSE, K_FRONTIER_DIFF, K_TPREP, K_TFLUX, K_TFRONTIER,
-  K_TMOM, K_TUPDATE, K_VREC_SOURCE, K_COMMUP, K_COMMMEAN, K_DT, K_FORCE, K_OTHER, K_NKINDS
+  K_TMOM, K_TUPDATE, K_VREC_SOURCE, K_COMMUP, K_COMMMEAN, K_DT, K_FORCE, K_SWEEP, K_OTHER,
+  K_NKINDS
 };
 
 // hot-path FP64 division versus IEEE division (device arrays; max_ulp zeroed by caller)

@@ -88,10 +88,14 @@ __device__ __forceinline__ T vanleer(T dl, T dr) {
 // candidate elements are loaded before the upwind side is chosen, so the loads
 // do not wait for the face velocity.
 template <class T>
-__device__ __forceinline__ T upwind(const T* __restrict__ q, int c, int st, T u, T cour) {
-  const T qmm = q[c - 2 * st], qm = q[c - st], q0 = q[c], qp = q[c + st];
+__device__ __forceinline__ T upwind_v(T qmm, T qm, T q0, T qp, T u, T cour) {
   if (u > T(0)) return qm + T(0.5) * (T(1) - cour) * vanleer(qm - qmm, q0 - qm);
   return q0 - T(0.5) * (T(1) + cour) * vanleer(q0 - qm, qp - q0);
+}
+
+template <class T>
+__device__ __forceinline__ T upwind(const T* __restrict__ q, int c, int st, T u, T cour) {
+  return upwind_v(q[c - 2 * st], q[c - st], q[c], q[c + st], u, cour);
 }
 
 inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
@@ -426,15 +430,361 @@ __device__ __forceinline__ void el_tupdate(const LevelView& L, const Box& b, con
   }
 }
 
+// ------------------------------------------------------- fused transport sweep
+// One sweep along d (Sec. 3.1 transport: the mass flux F = rho* v A dt with the
+// time-centred van Leer value rho*, e and the momenta carried as (q/rho)* F) with
+// the arithmetic of tprep + tflux + tmom + tupdate, fused and register-blocked.
+// A block is kSweepRows + 1 warps; warp w holds row row0 - 1 + w (the first is the
+// halo row below the block's rows), lane l the x position x0 - hx + l, and the block
+// marches through a chunk of planes of the marching axis.  Values along the marching
+// axis stay in per-thread registers, x neighbours come by warp shuffle, the row
+// below through one shared-memory exchange per plane.
+//   y, z sweeps: march along the sweep; the stencil along d is the register window.
+//   x sweep: march along z; the stencil along x is a shuffle (3 halo lanes below,
+//            2 above), the z neighbour is the previous plane's registers.
+// Ping-pong state: the sweep reads `src` inside the box and the level's own arrays
+// outside it (the values the separate kernels, which update in place, read there)
+// and writes every box cell it owns to `dst`: x and z sweeps from the level's
+// arrays to Scratch::qb, the y sweep back.  For a child level the fluxes through
+// its frontier faces also go to Scratch::F/E (frontier capture).
+
+template <class T>
+__device__ __forceinline__ T shfl_up(T v, int k) {
+  return __shfl_up_sync(0xffffffffu, v, k);
+}
+template <class T>
+__device__ __forceinline__ T shfl_dn(T v, int k) {
+  return __shfl_down_sync(0xffffffffu, v, k);
+}
+
+// coarse-level frontier substitution of the low/high d-face fluxes of cell (g)
+template <class T>
+__device__ __forceinline__ void frontier_fluxes(const LevelView& L, int d, const int g[3], T& Flo,
+                                                T& Fhi, T& Elo, T& Ehi) {
+  int slot, f3[3] = {g[0], g[1], g[2]};
+  int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+  if (side >= 0) {
+    Flo = (T)L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot];
+    Elo = (T)L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot];
+  }
+  f3[d] += 1;
+  side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+  if (side >= 0) {
+    Fhi = (T)L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot];
+    Ehi = (T)L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot];
+  }
+}
+
+template <class T, int d>
+__device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __restrict__ xch) {
+  constexpr int RA = d == 1 ? 2 : 1;  // row axis
+  constexpr int MU = d == 0 ? 2 : d;  // marching axis
+  constexpr int HX = d == 0 ? 3 : 1;  // halo lanes below the owned x range
+  constexpr int OWNX = d == 0 ? 27 : 31;
+  constexpr int NT = kSweepThreads;
+  constexpr bool kFromB = d == 1;  // x: A -> B, y: B -> A, z: A -> B
+  const LevelView& L = it.L;
+  const Box& b = it.b;
+  const Scratch& S = it.S;
+  const Bg<T>& bg = it.bg;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nsx = (b.hi[0] - b.lo[0] + OWNX - 1) / OWNX;
+  const int nsr = (b.hi[RA] - b.lo[RA] + kSweepRows - 1) / kSweepRows;
+  const int cm = (int)unit / (nsx * nsr), crem = (int)unit - cm * nsx * nsr;
+  const int sr = crem / nsx, sx = crem - sr * nsx;
+  const int x = b.lo[0] + sx * OWNX - HX + lane;
+  const int row = b.lo[RA] + sr * kSweepRows - 1 + warp;
+  const int m0 = b.lo[MU] + cm * b.zc, m1 = min(m0 + b.zc, b.hi[MU]);
+  const int s0 = L.s[0], sRA = L.s[RA], sMU = L.s[MU];
+  const int stR = L.st[RA], stM = L.st[MU];
+  const bool pos = (unsigned)x < (unsigned)s0 && (unsigned)row < (unsigned)sRA;
+  const bool owned = warp >= 1 && lane >= HX && lane < HX + OWNX && x < b.hi[0] &&
+                     row < b.hi[RA];
+  const bool xrbox = x >= b.lo[0] && x < b.hi[0] && row >= b.lo[RA] && row < b.hi[RA];
+  const int cxr = x + row * stR;
+  const T* rhoA = (const T*)L.q[F_RHO];
+  const T* eA = (const T*)L.q[F_E];
+  const T* rhoS = kFromB ? (const T*)S.qb[0] : rhoA;
+  const T* eS = kFromB ? (const T*)S.qb[1] : eA;
+  const T* __restrict__ vd = (const T*)L.q[F_VX + d];
+  T* rhoD = kFromB ? (T*)L.q[F_RHO] : (T*)S.qb[0];
+  T* eD = kFromB ? (T*)L.q[F_E] : (T*)S.qb[1];
+  const T* piA[3] = {(const T*)S.pi[0], (const T*)S.pi[1], (const T*)S.pi[2]};
+  const T* piS[3] = {kFromB ? (const T*)S.qb[2] : piA[0], kFromB ? (const T*)S.qb[3] : piA[1],
+                     kFromB ? (const T*)S.qb[4] : piA[2]};
+  T* piD[3] = {kFromB ? (T*)S.pi[0] : (T*)S.qb[2], kFromB ? (T*)S.pi[1] : (T*)S.qb[3],
+               kFromB ? (T*)S.pi[2] : (T*)S.qb[4]};
+  const T dt = ((const T*)it.dt)[0];
+  const T Adt = it.g.area[d] * dt;
+  const T dtdx = dt * it.g.inv_dx[d];
+  const T F0 = bg.rho0 * bg.V[d] * Adt;
+  const T iv = it.g.inv_vol;
+  const int sd = L.s[d];
+
+  // state of plane p at this thread's (x, row); zero outside the array
+  auto load = [&](int p, T& r_, T& e_, T& v_, T (&pi_)[3]) {
+    r_ = e_ = v_ = T(0);
+    pi_[0] = pi_[1] = pi_[2] = T(0);
+    if (pos && (unsigned)p < (unsigned)sMU) {
+      const int c = cxr + p * stM;
+      const bool own = !kFromB || (xrbox && p >= b.lo[MU] && p < b.hi[MU]);
+      r_ = (own ? rhoS : rhoA)[c];
+      e_ = (own ? eS : eA)[c];
+      v_ = vd[c];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) pi_[m] = (own ? piS[m] : piA[m])[c];
+    }
+  };
+  auto gcoord = [&](int p, int (&g)[3]) {
+    g[0] = x;
+    g[RA] = row;
+    g[MU] = p;
+  };
+  T nr, ne, nv, np[3];
+
+  if constexpr (d != 0) {
+    // ================================================= march along the sweep axis
+    // windows, oldest first, at step r: rho, eps planes r-3..r; e, v_d, Pi planes
+    // r-2..r; w planes r-3..r; F, E faces r-2, r-1; P_d planes r-3, r-2; P_x and
+    // P_row planes r-2, r-1.  The update is of plane r - 2.
+    constexpr int mx = 0, mr = RA;
+    T rw[4] = {}, sw[4] = {}, er[3] = {}, vw[3] = {}, pw[3][3] = {}, ww[3][4] = {};
+    T Fw[2] = {}, Ew[2] = {}, Pd[2] = {}, Pm[2][2] = {};
+    const int nit = m1 - m0 + 5;
+    load(m0 - 3, nr, ne, nv, np);
+    for (int i = 0; i < nit; ++i) {
+      const int r = m0 - 3 + i;
+      rw[0] = rw[1]; rw[1] = rw[2]; rw[2] = rw[3]; rw[3] = nr;
+      sw[0] = sw[1]; sw[1] = sw[2]; sw[2] = sw[3];
+      sw[3] = hdiv(ne - bg.eps0 * nr, bg.rho0 + nr);
+      er[0] = er[1]; er[1] = er[2]; er[2] = ne;
+      vw[0] = vw[1]; vw[1] = vw[2]; vw[2] = nv;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        pw[m][0] = pw[m][1]; pw[m][1] = pw[m][2]; pw[m][2] = np[m];
+      }
+      if (i + 1 < nit) load(r + 1, nr, ne, nv, np);
+      // mass and energy flux of face plane f = r - 1
+      const int f = r - 1;
+      T Fv = T(0), Evv = T(0);
+      if (pos && f >= 2 && f < sd - 1) {
+        const T du = vw[1];
+        const T u = bg.V[d] + du;
+        const T cour = u * dtdx;
+        const T drs = upwind_v(rw[0], rw[1], rw[2], rw[3], u, cour);
+        Fv = (bg.rho0 * du + drs * u) * Adt;
+        const T des = upwind_v(sw[0], sw[1], sw[2], sw[3], u, cour);
+        Evv = bg.eps0 * Fv + des * (F0 + Fv);
+      }
+      Fw[0] = Fw[1]; Fw[1] = Fv;
+      Ew[0] = Ew[1]; Ew[1] = Evv;
+      if (L.is_child && owned && f >= m0 && f < m1 && (f == L.G || f == L.G + L.n[d])) {
+        const int c = cxr + f * stM;
+        ((T*)S.F)[c] = Fv;
+        ((T*)S.E)[c] = Evv;
+      }
+      // rho_r, v_{r-1}, F_{r-1} of the row below (shared) and of x - 1 (shuffle)
+      T* xb = xch + (i & 1) * 3 * NT;
+      xb[tid] = rw[3];
+      xb[NT + tid] = vw[1];
+      xb[2 * NT + tid] = Fv;
+      __syncthreads();
+      const int tb = warp > 0 ? tid - 32 : tid;
+      const T r_rb = xb[tb], v_rb = xb[NT + tb], F_rb = xb[2 * NT + tb];
+      const T r_xb = shfl_up(rw[3], 1), v_xb = shfl_up(vw[1], 1), F_xb = shfl_up(Fv, 1);
+      // w = (dPi - V drf) / (rho0 + drf) of plane r
+      const bool pok = pos && (unsigned)r < (unsigned)sMU;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const T rn = m == mx ? r_xb : (m == mr ? r_rb : rw[2]);
+        const bool g1 = m == mx ? x >= 1 : (m == mr ? row >= 1 : r >= 1);
+        T wv = T(0);
+        if (pok && g1) {
+          const T drf = T(0.5) * (rn + rw[3]);
+          wv = hdiv(pw[m][2] - bg.V[m] * drf, bg.rho0 + drf);
+        }
+        ww[m][0] = ww[m][1]; ww[m][1] = ww[m][2]; ww[m][2] = ww[m][3]; ww[m][3] = wv;
+      }
+      // P_x, P_row of plane q = r - 1 (d-m edges)
+      const int q = r - 1;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int m = j == 0 ? mx : mr;
+        T P = T(0);
+        if (pos && q >= 2 && q < sd - 1 && (j == 0 ? x >= 1 : row >= 1)) {
+          const T ue = bg.V[d] + T(0.5) * ((j == 0 ? v_xb : v_rb) + vw[1]);
+          const T Fe = T(0.5) * ((j == 0 ? F_xb : F_rb) + Fv);
+          const T wsv = upwind_v(ww[m][0], ww[m][1], ww[m][2], ww[m][3], ue, ue * dtdx);
+          P = bg.V[m] * Fe + wsv * (F0 + Fe);
+        }
+        Pm[j][0] = Pm[j][1];
+        Pm[j][1] = P;
+      }
+      // P_d of plane p = r - 2 (cell-centred)
+      {
+        const int p = r - 2;
+        T P = T(0);
+        if (pos && p >= 2 && p < sd - 2) {
+          const T uc = bg.V[d] + T(0.5) * (vw[0] + vw[1]);
+          const T Fc = T(0.5) * (Fw[0] + Fw[1]);
+          const T wsv = upwind_v(ww[d][0], ww[d][1], ww[d][2], ww[d][3], uc, uc * dtdx);
+          P = bg.V[d] * Fc + wsv * (F0 + Fc);
+        }
+        Pd[0] = Pd[1];
+        Pd[1] = P;
+      }
+      // conservative update of plane u = r - 2
+      const int u = r - 2;
+      if (owned && u >= m0 && u < m1) {
+        const int c = cxr + u * stM;
+        T rv = rw[1], evv = er[0];
+        if (u >= 2 && u < sd - 2) {
+          T Flo = Fw[0], Fhi = Fw[1], Elo = Ew[0], Ehi = Ew[1];
+          if (L.has_child) {
+            int g[3];
+            gcoord(u, g);
+            frontier_fluxes(L, d, g, Flo, Fhi, Elo, Ehi);
+          }
+          rv = rv - (Fhi - Flo) * iv;
+          evv = evv - (Ehi - Elo) * iv;
+        }
+        rhoD[c] = rv;
+        eD[c] = evv;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          T pv = pw[m][0];
+          if (m == d) {
+            if (u >= 3 && u < sd - 2) pv = pv - (Pd[1] - Pd[0]) * iv;
+          } else {
+            const int j = m == mx ? 0 : 1;
+            if (u >= 2 && u < sd - 2 && (j == 0 ? x >= 1 : row >= 1))
+              pv = pv - (Pm[j][1] - Pm[j][0]) * iv;
+          }
+          piD[m][c] = pv;
+        }
+      }
+    }
+  } else {
+    // ======================================================== x sweep, march in z
+    T pr_r = T(0), pr_v = T(0), pr_F = T(0);  // plane r - 1 at (x, row)
+    const int nit = m1 - m0 + 1;
+    load(m0 - 1, nr, ne, nv, np);
+    for (int i = 0; i < nit; ++i) {
+      const int r = m0 - 1 + i;
+      const T rc = nr, ec = ne, vc = nv, pi0 = np[0], pi1 = np[1], pi2 = np[2];
+      if (i + 1 < nit) load(r + 1, nr, ne, nv, np);
+      const T ep = hdiv(ec - bg.eps0 * rc, bg.rho0 + rc);
+      const T r_m2 = shfl_up(rc, 2), r_m1 = shfl_up(rc, 1), r_p1 = shfl_dn(rc, 1);
+      const T e_m2 = shfl_up(ep, 2), e_m1 = shfl_up(ep, 1), e_p1 = shfl_dn(ep, 1);
+      const bool pok = pos && (unsigned)r < (unsigned)sMU;
+      // mass and energy flux at the x-face of this cell
+      T Fv = T(0), Evv = T(0);
+      if (pok && x >= 2 && x < sd - 1) {
+        const T u = bg.V[0] + vc;
+        const T cour = u * dtdx;
+        const T drs = upwind_v(r_m2, r_m1, rc, r_p1, u, cour);
+        Fv = (bg.rho0 * vc + drs * u) * Adt;
+        const T des = upwind_v(e_m2, e_m1, ep, e_p1, u, cour);
+        Evv = bg.eps0 * Fv + des * (F0 + Fv);
+      }
+      if (L.is_child && owned && r >= m0 && r < m1 && (x == L.G || x == L.G + L.n[0])) {
+        const int c = cxr + r * stM;
+        ((T*)S.F)[c] = Fv;
+        ((T*)S.E)[c] = Evv;
+      }
+      // rho, v_x, F of the row below
+      T* xb = xch + (i & 1) * 3 * NT;
+      xb[tid] = rc;
+      xb[NT + tid] = vc;
+      xb[2 * NT + tid] = Fv;
+      __syncthreads();
+      if (i > 0) {  // plane m0 - 1 only feeds the z-fluxes of plane m0
+        const int tb = warp > 0 ? tid - 32 : tid;
+        const T r_rb = xb[tb], v_rb = xb[NT + tb], F_rb = xb[2 * NT + tb];
+        // w of this plane: along x (lane below), y (row below), z (previous plane)
+        T wx = T(0), wy = T(0), wz = T(0);
+        if (pok && x >= 1) {
+          const T drf = T(0.5) * (r_m1 + rc);
+          wx = hdiv(pi0 - bg.V[0] * drf, bg.rho0 + drf);
+        }
+        if (pok && row >= 1) {
+          const T drf = T(0.5) * (r_rb + rc);
+          wy = hdiv(pi1 - bg.V[1] * drf, bg.rho0 + drf);
+        }
+        if (pok && r >= 1) {
+          const T drf = T(0.5) * (pr_r + rc);
+          wz = hdiv(pi2 - bg.V[2] * drf, bg.rho0 + drf);
+        }
+        const T wx_m1 = shfl_up(wx, 1), wx_p1 = shfl_dn(wx, 1), wx_p2 = shfl_dn(wx, 2);
+        const T wy_m2 = shfl_up(wy, 2), wy_m1 = shfl_up(wy, 1), wy_p1 = shfl_dn(wy, 1);
+        const T wz_m2 = shfl_up(wz, 2), wz_m1 = shfl_up(wz, 1), wz_p1 = shfl_dn(wz, 1);
+        const T v_p1 = shfl_dn(vc, 1), F_p1 = shfl_dn(Fv, 1), E_p1 = shfl_dn(Evv, 1);
+        // momentum fluxes: P_x cell-centred, P_y and P_z on the x-y and x-z edges
+        T Px = T(0), Py = T(0), Pz = T(0);
+        if (pok && x >= 2 && x < sd - 2) {
+          const T uc = bg.V[0] + T(0.5) * (vc + v_p1);
+          const T Fc = T(0.5) * (Fv + F_p1);
+          const T wsv = upwind_v(wx_m1, wx, wx_p1, wx_p2, uc, uc * dtdx);
+          Px = bg.V[0] * Fc + wsv * (F0 + Fc);
+        }
+        if (pok && x >= 2 && x < sd - 1 && row >= 1) {
+          const T ue = bg.V[0] + T(0.5) * (v_rb + vc);
+          const T Fe = T(0.5) * (F_rb + Fv);
+          const T wsv = upwind_v(wy_m2, wy_m1, wy, wy_p1, ue, ue * dtdx);
+          Py = bg.V[1] * Fe + wsv * (F0 + Fe);
+        }
+        if (pok && x >= 2 && x < sd - 1 && r >= 1) {
+          const T ue = bg.V[0] + T(0.5) * (pr_v + vc);
+          const T Fe = T(0.5) * (pr_F + Fv);
+          const T wsv = upwind_v(wz_m2, wz_m1, wz, wz_p1, ue, ue * dtdx);
+          Pz = bg.V[2] * Fe + wsv * (F0 + Fe);
+        }
+        const T Px_m1 = shfl_up(Px, 1), Py_p1 = shfl_dn(Py, 1), Pz_p1 = shfl_dn(Pz, 1);
+        // conservative update of this cell
+        if (owned && r >= m0 && r < m1) {
+          const int c = cxr + r * stM;
+          T rv = rc, evv = ec;
+          if (x >= 2 && x < sd - 2) {
+            T Flo = Fv, Fhi = F_p1, Elo = Evv, Ehi = E_p1;
+            if (L.has_child) {
+              int g[3];
+              gcoord(r, g);
+              frontier_fluxes(L, 0, g, Flo, Fhi, Elo, Ehi);
+            }
+            rv = rv - (Fhi - Flo) * iv;
+            evv = evv - (Ehi - Elo) * iv;
+          }
+          rhoD[c] = rv;
+          eD[c] = evv;
+          T p0 = pi0, p1 = pi1, p2 = pi2;
+          if (x >= 3 && x < sd - 2) p0 = p0 - (Px - Px_m1) * iv;
+          if (x >= 2 && x < sd - 2 && row >= 1) p1 = p1 - (Py_p1 - Py) * iv;
+          if (x >= 2 && x < sd - 2 && r >= 1) p2 = p2 - (Pz_p1 - Pz) * iv;
+          piD[0][c] = p0;
+          piD[1][c] = p1;
+          piD[2][c] = p2;
+        }
+      }
+      pr_r = rc;
+      pr_v = vc;
+      pr_F = Fv;
+    }
+  }
+}
+
 // velocity from the transported momenta, then the second half kick S(dt/2)
 template <class T>
 __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b, const Scratch& S,
                                                         const T* __restrict__ dtp, T gm1, const Bg<T>& bg,
-                                                        const Geo<T>& g, unsigned tid) {
+                                                        const Geo<T>& g, int fused, unsigned tid) {
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
-  const T* __restrict__ rho = (const T*)L.q[F_RHO];
-  const T* __restrict__ e = (const T*)L.q[F_E];
+  T* rhoA = (T*)L.q[F_RHO];
+  T* eA = (T*)L.q[F_E];
+  // after fused sweeps the box's state is in Scratch::qb; outside the box it is in
+  // the level's arrays, which this op then updates for the box
+  const T* rho = fused ? (const T*)S.qb[0] : rhoA;
+  const T* e = fused ? (const T*)S.qb[1] : eA;
   const T* __restrict__ phi = (const T*)L.phi;
   const T h = T(0.5) * dtp[0];
   const int c = cidx(L, i, j, k);
@@ -444,11 +794,19 @@ __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b,
   for (int d = 0; d < 3; ++d) {
     if (c3[d] < 1) continue;
     int m = c - L.st[d];
-    T drf = T(0.5) * (rho[m] + rc);
+    const bool own = !fused || c3[d] - 1 >= b.lo[d];
+    const T rm = own ? rho[m] : rhoA[m];
+    const T em = own ? e[m] : eA[m];
+    T drf = T(0.5) * (rm + rc);
     T rinv = hdiv(T(1), bg.rho0 + drf);
-    T v = (((const T*)S.pi[d])[c] - bg.V[d] * drf) * rinv;
-    T acc = (gm1 * (ec - e[m]) * rinv + (fc - phi[m])) * g.inv_dx[d];
+    const T* pi = (const T*)(fused ? S.qb[2 + d] : S.pi[d]);
+    T v = (pi[c] - bg.V[d] * drf) * rinv;
+    T acc = (gm1 * (ec - em) * rinv + (fc - phi[m])) * g.inv_dx[d];
     ((T*)L.q[F_VX + d])[c] = v - h * acc;
+  }
+  if (fused) {
+    rhoA[c] = rc;
+    eA[c] = ec;
   }
 }
 
@@ -1065,7 +1423,8 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
   else if (OP == OP_TUPDATE)
     el_tupdate<T, D>(it.L, it.b, it.S, it.g, tid);
   else if (OP == OP_VREC)
-    el_vrec_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.bg, it.g, tid);
+    el_vrec_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.bg, it.g,
+                      it.flags & FL_FUSED, tid);
   else if (OP == OP_BC)
     el_bc_axis<T>(it.L, D, it.bc_lo, it.bc_hi, it.bg.rho0, it.bg.e0, it.bg.V[0], it.bg.V[1],
                   it.bg.V[2], tid);
@@ -1139,6 +1498,57 @@ __global__ void __launch_bounds__(kBlock) k_single(const Item<T> it) {
   run_op<T, OP, D>(it, blockIdx.x * kBlock + threadIdx.x);
 }
 
+// Fused sweep: one block per (column, chunk) unit; the work-list form stages the
+// item as k_batch does.
+template <class T, int D>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_single(const Item<T> it) {
+  __shared__ __align__(16) T s_x[2 * 3 * kSweepThreads];
+  el_sweep<T, D>(it, blockIdx.x, s_x);
+}
+
+template <class T, int D>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_batch(const Item<T>* __restrict__ items,
+                                                              const unsigned* __restrict__ starts,
+                                                              int nitems, unsigned nchunks) {
+  __shared__ __align__(16) T s_x[2 * 3 * kSweepThreads];
+  __shared__ __align__(16) unsigned char s_raw[sizeof(Item<T>)];
+  const Item<T>& it = *reinterpret_cast<const Item<T>*>(s_raw);
+  unsigned c0 = (unsigned)((unsigned long long)nchunks * blockIdx.x / gridDim.x);
+  unsigned c1 = (unsigned)((unsigned long long)nchunks * (blockIdx.x + 1) / gridDim.x);
+  int cur = -1;
+  for (unsigned ch = c0; ch < c1; ++ch) {
+    int lo = cur < 0 ? 0 : cur, hi = nitems - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (starts[mid] <= ch)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    if (lo != cur) {
+      __syncthreads();
+      const int4* src = reinterpret_cast<const int4*>(items + lo);
+      int4* dst = reinterpret_cast<int4*>(s_raw);
+      for (int w = threadIdx.x; w < (int)(sizeof(Item<T>) / 16); w += kSweepThreads)
+        dst[w] = src[w];
+      __syncthreads();
+      cur = lo;
+    }
+    el_sweep<T, D>(it, ch - starts[cur], s_x);
+    __syncthreads();
+  }
+}
+
+template <class T, int D>
+static void launch_sweep(const Item<T>* items, const unsigned* starts, int nitems,
+                         unsigned nchunks, unsigned grid, cudaStream_t st,
+                         const Item<T>* host_item) {
+  if (nitems == 1 && host_item)
+    k_sweep_single<T, D><<<nchunks, kSweepThreads, 0, st>>>(*host_item);
+  else
+    k_sweep_batch<T, D><<<grid, kSweepThreads, 0, st>>>(items, starts, nitems, nchunks);
+}
+
 template <class T, int OP, int D>
 static void launch_one(const Item<T>* items, const unsigned* starts, int nitems, unsigned nchunks,
                        unsigned grid, cudaStream_t st, const Item<T>* host_item) {
@@ -1183,6 +1593,11 @@ int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, in
     DFN_OP(OP_FORCE_LEVEL)
     DFN_OP(OP_FORCE_FINAL)
     DFN_OP(OP_TIME)
+    case OP_SWEEP:
+      if (d == 0) launch_sweep<T, 0>(items, starts, nitems, nchunks, grid, st, host_item);
+      if (d == 1) launch_sweep<T, 1>(items, starts, nitems, nchunks, grid, st, host_item);
+      if (d == 2) launch_sweep<T, 2>(items, starts, nitems, nchunks, grid, st, host_item);
+      break;
     default:
       return 0;
   }
@@ -1219,6 +1634,9 @@ unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const B
         }
         n = nt * 256;
       }
+      break;
+    case OP_SWEEP:
+      n = (long long)sweep_units(b, d) * kBlock;  // one chunk per (column, chunk) unit
       break;
     case OP_FRONTIER_DIFF: n = slots(0, 6); break;
     case OP_TFRONTIER: n = slots(2 * d, 2); break;

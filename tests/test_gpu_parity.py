@@ -27,10 +27,16 @@ def _built():
     binding.load()
 
 
-def pair(nl, n, half, params, G=I.DEFAULT_G, precision=binding.DF_FP64):
+TRANSPORTS = [binding.TRANSPORT_SEPARATE, binding.TRANSPORT_FUSED]
+TRANSPORT_IDS = ["separate", "fused"]
+
+
+def pair(nl, n, half, params, G=I.DEFAULT_G, precision=binding.DF_FP64,
+         transport=binding.TRANSPORT_AUTO):
     lo = tuple(-h for h in half) if not np.isscalar(half) else (-half,) * 3
     hi = tuple(half) if not np.isscalar(half) else (half,) * 3
     sim = binding.Sim(nl, n, lo, hi, G, params, precision=precision)
+    sim.set_transport(transport)
     orc = Oracle(nl, n, lo, hi, G, params)
     return sim, orc
 
@@ -93,9 +99,10 @@ def perturb_both(sim, orc, seed, amp=1e-2):
         sim.prolong(l)
 
 
-def test_uniform_flow_bitwise():
+@pytest.mark.parametrize("transport", TRANSPORTS, ids=TRANSPORT_IDS)
+def test_uniform_flow_bitwise(transport):
     p = I.base_params(GM=0.0, L=0.0, chi=1.0, mach=0.7, flow_dir=(-0.6, 0.0, 0.8))
-    sim, orc = pair(3, 24, 6.0, p)
+    sim, orc = pair(3, 24, 6.0, p, transport=transport)
     init = [[orc.get_field(l, f) for f in range(5)] for l in range(3)]
     sim.step(10)
     for l in range(3):
@@ -114,11 +121,12 @@ def test_single_mesh_100_steps():
     assert abs(sim.force()[0][0]) > 0
 
 
-def test_nested_100_coarse_steps():
+@pytest.mark.parametrize("transport", TRANSPORTS, ids=TRANSPORT_IDS)
+def test_nested_100_coarse_steps(transport):
     """3 nested levels (ratio 2) of 32^3 with a Gaussian luminosity: 100 coarse steps."""
     p = I.base_params(GM=0.01, eps=0.125, chi=1.0, L=I.critical_luminosity(0.01, 1, 1, 5 / 3),
                       lum_sigma=0.125, mach=0.5)
-    sim, orc = pair(3, 32, 8.0, p)
+    sim, orc = pair(3, 32, 8.0, p, transport=transport)
     sim.step(100)
     orc.step(100)
     assert_parity(sim, orc, p)
@@ -129,21 +137,25 @@ def test_nested_100_coarse_steps():
     (I.BC_REFLECT, I.BC_OUTFLOW, I.BC_REFLECT, I.BC_INFLOW, I.BC_OUTFLOW, I.BC_REFLECT),
     I.wind_bcs((0.0, 0.6, -0.8)),
 ])
-def test_perturbed_nested_boundaries(bc):
+@pytest.mark.parametrize("transport", TRANSPORTS, ids=TRANSPORT_IDS)
+def test_perturbed_nested_boundaries(bc, transport):
     p = I.base_params(GM=0.02, eps=0.3, chi=0.4, L=0.03, lum_sigma=0.0, mach=0.8,
                       flow_dir=(0.0, 0.6, -0.8), bc=bc)
-    sim, orc = pair(2, (24, 28, 32), (6.0, 7.0, 8.0), p)
+    sim, orc = pair(2, (24, 28, 32), (6.0, 7.0, 8.0), p, transport=transport)
     perturb_both(sim, orc, seed=3)
     sim.step(12)
     orc.step(12)
     assert_parity(sim, orc, p)
 
 
-def test_margin_boxes_equal_full_boxes():
+@pytest.mark.parametrize("transport", TRANSPORTS, ids=TRANSPORT_IDS)
+def test_margin_boxes_equal_full_boxes(transport):
     """The active cells do not depend on the ghost margin the kernels sweep."""
     p = I.base_params(GM=0.01, eps=0.125, chi=1.0, L=0.05, lum_sigma=0.125, mach=0.9)
     a = binding.Sim(3, 24, (-6.0,) * 3, (6.0,) * 3, I.DEFAULT_G, p)
     b = binding.Sim(3, 24, (-6.0,) * 3, (6.0,) * 3, I.DEFAULT_G, p)
+    a.set_transport(transport)
+    b.set_transport(transport)
     b.debug_full_boxes(True)
     for s in (a, b):
         for l in range(3):
@@ -191,6 +203,34 @@ def test_tile_shapes_bitwise_equal(precision):
             for f in range(5):
                 assert np.array_equal(tuned.get_field(l, f), s.get_field(l, f)), (l, f)
         assert np.array_equal(tuned.force()[0], s.force()[0])
+
+
+def test_fused_and_separate_transport_agree_fp32():
+    """FP32 state: the fused sweeps and the separate kernels evaluate the same
+    expressions; they differ only by the contraction of multiply-adds, so after 15
+    coarse steps the fields agree to a few FP32 roundings of the perturbation."""
+    p = I.base_params(GM=0.01, eps=0.125, chi=1.0, L=0.05, lum_sigma=0.125, mach=1.3,
+                      flow_dir=(-0.6, 0.0, 0.8), bc=I.wind_bcs((-0.6, 0.0, 0.8)))
+    sims = []
+    for tr in TRANSPORTS:
+        s = binding.Sim(3, (24, 28, 32), (-6.0, -7.0, -8.0), (6.0, 7.0, 8.0), I.DEFAULT_G, p,
+                        precision=binding.DF_FP32_STATE)
+        s.set_transport(tr)
+        for l in range(3):
+            for f in range(5):
+                base = s.get_field(l, f)
+                s.set_field(l, f, base + I.smooth_perturbation(base.shape, 90 + 5 * l + f, 5e-3))
+        s.step(15)
+        sims.append(s)
+    a, b = sims
+    vs = 1.3
+    for l in range(3):
+        for f in range(5):
+            x, y = a.get_field(l, f), b.get_field(l, f)
+            scale = 1.0 if f < 2 else vs
+            assert np.abs(x - y).max() <= 2e-5 * scale, (l, f, np.abs(x - y).max())
+    Fa, Fb = a.force()[0], b.force()[0]
+    assert np.abs(Fa - Fb).max() <= 1e-4 * np.abs(Fb).max()
 
 
 def test_inter_level_operators():
@@ -252,12 +292,13 @@ def test_xi_search_mode_parity():
     assert_parity(sim, orc, p)
 
 
-def test_full_size_nested_config():
+@pytest.mark.parametrize("transport", TRANSPORTS, ids=TRANSPORT_IDS)
+def test_full_size_nested_config(transport):
     """The benchmarked configuration (3 levels of 64^3, coarse box [-8,8]^3, Mach 0.5,
     chi=1, Gaussian luminosity L_c) in the launch configuration the bench times."""
     cfg = I.nested()
     p = cfg["params"]
-    sim, orc = pair(cfg["n_levels"], cfg["n"], cfg["hi"][0], p)
+    sim, orc = pair(cfg["n_levels"], cfg["n"], cfg["hi"][0], p, transport=transport)
     sim.step(3)
     orc.step(3)
     assert_parity(sim, orc, p)
