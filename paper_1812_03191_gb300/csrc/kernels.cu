@@ -58,22 +58,30 @@ __device__ __forceinline__ int cidx(const LevelView& L, int i, int j, int k) {
   return (k * L.s[1] + j) * L.s[0] + i;
 }
 
-// Division on the hot path.  FP64: Newton-Raphson refinement of the hardware
-// reciprocal estimate (two steps r <- r + r(1 - b r), then one residual correction
-// q <- q + r(a - b q), after Markstein, IBM J. Res. Dev. 34 (1990)); accurate to
-// about one ulp for the normal, non-zero divisors used here (densities, 1 + a,
-// and the sum of two same-signed slopes).  FP32: the fast reciprocal-based divide.
+// Division on the hot path.  FP64: one Newton-Raphson refinement of the hardware
+// reciprocal estimate (r <- r + r(1 - b r)), then one residual correction
+// q <- q + r(a - b q) (Markstein, IBM J. Res. Dev. 34 (1990)): the corrected
+// quotient's error is the square of the refined reciprocal's plus the final
+// rounding, within one ulp for the normal, non-zero divisors used here (densities,
+// 1 + a, and the sum of two same-signed slopes).  FP32: the fast reciprocal-based
+// divide.
 __device__ __forceinline__ double hdiv(double a, double b) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
-  double e = fma(-b, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-b, r, 1.0);
-  r = fma(r, e, r);
+  r = fma(r, fma(-b, r, 1.0), r);
   double q = a * r;
   return fma(r, fma(-b, q, a), q);
 }
 __device__ __forceinline__ float hdiv(float a, float b) { return __fdividef(a, b); }
+
+// sign tests; for FP64 on the integer pipe (the FP64 pipe bounds the FP64 kernels):
+// the bit pattern of a non-NaN double, read as a signed integer, has the sign of the
+// value, with +0 -> 0 and -0 -> negative.  (A NaN's sign bit decides instead; a NaN
+// state is caught by the health check of the time-step reduction.)
+__device__ __forceinline__ bool gt0(float v) { return v > 0.f; }
+__device__ __forceinline__ bool le0(float v) { return v <= 0.f; }
+__device__ __forceinline__ bool gt0(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool le0(double v) { return __double_as_longlong(v) <= 0; }
 
 // van Leer (1977) harmonic limited slope (Sec. 3.2.1 cites it for the interpolation).
 // When the product underflows to zero the slope is zero, so the divisor dl + dr is
@@ -81,16 +89,24 @@ __device__ __forceinline__ float hdiv(float a, float b) { return __fdividef(a, b
 template <class T>
 __device__ __forceinline__ T vanleer(T dl, T dr) {
   T pr = dl * dr;
-  return pr <= T(0) ? T(0) : hdiv(T(2) * pr, dl + dr);
+  return le0(pr) ? T(0) : hdiv(T(2) * pr, dl + dr);
 }
 
 // time-centred upwind value at the face between elements c-st and c.  The four
 // candidate elements are loaded before the upwind side is chosen, so the loads
 // do not wait for the face velocity.
+// The upwind side's value, slopes and coefficient are selected first, so one limiter
+// (one division) serves both flow directions: u > 0 gives qm + (1 - cour)/2 * slope,
+// u <= 0 gives q0 + (-1 - cour)/2 * slope = q0 - (1 + cour)/2 * slope.
 template <class T>
 __device__ __forceinline__ T upwind_v(T qmm, T qm, T q0, T qp, T u, T cour) {
-  if (u > T(0)) return qm + T(0.5) * (T(1) - cour) * vanleer(qm - qmm, q0 - qm);
-  return q0 - T(0.5) * (T(1) + cour) * vanleer(q0 - qm, qp - q0);
+  const bool up = gt0(u);
+  const T dm = q0 - qm;
+  const T a = up ? qm : q0;
+  const T dl = up ? qm - qmm : dm;
+  const T dr = up ? dm : qp - q0;
+  const T coef = T(0.5) * ((up ? T(1) : T(-1)) - cour);
+  return a + coef * vanleer(dl, dr);
 }
 
 template <class T>
@@ -112,6 +128,13 @@ __device__ __forceinline__ int coarse_frontier(const LevelView& L, int d, int f0
   int side = f[d] == lo ? 0 : (f[d] == lo + (L.cn[d] >> 1) ? 1 : -1);
   slot = b * h1 + a;
   return side;
+}
+
+// does the low or the high d-face of a cell with d-index gd lie on one of the two
+// d-planes that carry the child's frontier faces?
+__device__ __forceinline__ bool near_frontier(const LevelView& L, int d, int gd) {
+  const int lo = L.G + L.coff[d], hi = lo + (L.cn[d] >> 1);
+  return gd == lo || gd == hi || gd + 1 == lo || gd + 1 == hi;
 }
 
 // ------------------------------------------------------------------ source S
@@ -209,7 +232,7 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
     int up = c + L.st[d];
     T qlo = diff_flux(L, g, rho, eps, c, d, chi, dt, rho0, dfr);
     T qhi = diff_flux(L, g, rho, eps, up, d, chi, dt, rho0, dfr);
-    if (L.has_child) {
+    if (L.has_child && near_frontier(L, d, c3[d])) {
       int slot, f3[3] = {c3[0], c3[1], c3[2]};
       int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
       if (side >= 0) qlo = (T)L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot];
@@ -399,7 +422,7 @@ __device__ __forceinline__ void el_tupdate(const LevelView& L, const Box& b, con
   if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
     T Flo = ((const T*)S.F)[c], Fhi = ((const T*)S.F)[c + st];
     T Elo = ((const T*)S.E)[c], Ehi = ((const T*)S.E)[c + st];
-    if (L.has_child) {
+    if (L.has_child && near_frontier(L, d, c3[d])) {
       int slot, f3[3] = {c3[0], c3[1], c3[2]};
       int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
       if (side >= 0) {
@@ -457,10 +480,12 @@ __device__ __forceinline__ T shfl_dn(T v, int k) {
   return __shfl_down_sync(0xffffffffu, v, k);
 }
 
-// coarse-level frontier substitution of the low/high d-face fluxes of cell (g)
+// coarse-level frontier substitution of the low/high d-face fluxes of cell (g); the
+// frontier faces lie on two d-planes, tested first
 template <class T>
 __device__ __forceinline__ void frontier_fluxes(const LevelView& L, int d, const int g[3], T& Flo,
                                                 T& Fhi, T& Elo, T& Ehi) {
+  if (!near_frontier(L, d, g[d])) return;
   int slot, f3[3] = {g[0], g[1], g[2]};
   int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
   if (side >= 0) {
@@ -589,8 +614,8 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
       xb[NT + tid] = vw[1];
       xb[2 * NT + tid] = Fv;
       __syncthreads();
-      const int tb = warp > 0 ? tid - 32 : tid;
-      const T r_rb = xb[tb], v_rb = xb[NT + tb], F_rb = xb[2 * NT + tb];
+      if (warp == 0) continue;  // the halo row only supplies rho, v_d and F
+      const T r_rb = xb[tid - 32], v_rb = xb[NT + tid - 32], F_rb = xb[2 * NT + tid - 32];
       const T r_xb = shfl_up(rw[3], 1), v_xb = shfl_up(vw[1], 1), F_xb = shfl_up(Fv, 1);
       // w = (dPi - V drf) / (rho0 + drf) of plane r
       const bool pok = pos && (unsigned)r < (unsigned)sMU;
@@ -698,9 +723,10 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
       xb[NT + tid] = vc;
       xb[2 * NT + tid] = Fv;
       __syncthreads();
-      if (i > 0) {  // plane m0 - 1 only feeds the z-fluxes of plane m0
-        const int tb = warp > 0 ? tid - 32 : tid;
-        const T r_rb = xb[tb], v_rb = xb[NT + tb], F_rb = xb[2 * NT + tb];
+      // plane m0 - 1 only feeds the z-fluxes of plane m0; the halo row only supplies
+      // rho, v_x and F
+      if (i > 0 && warp > 0) {
+        const T r_rb = xb[tid - 32], v_rb = xb[NT + tid - 32], F_rb = xb[2 * NT + tid - 32];
         // w of this plane: along x (lane below), y (row below), z (previous plane)
         T wx = T(0), wy = T(0), wz = T(0);
         if (pok && x >= 1) {
