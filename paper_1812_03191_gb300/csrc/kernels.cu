@@ -83,21 +83,21 @@ __device__ __forceinline__ bool le0(float v) { return v <= 0.f; }
 __device__ __forceinline__ bool gt0(double v) { return __double_as_longlong(v) > 0; }
 __device__ __forceinline__ bool le0(double v) { return __double_as_longlong(v) <= 0; }
 
-// van Leer (1977) harmonic limited slope (Sec. 3.2.1 cites it for the interpolation).
-// When the product underflows to zero the slope is zero, so the divisor dl + dr is
-// never zero or subnormal.
+// Half the van Leer (1977) harmonic limited slope (Sec. 3.2.1 cites it for the
+// interpolation): dl dr / (dl + dr) where dl dr > 0, else 0.  Callers fold the
+// factor 2 into their coefficients; scaling by 2 is exact, so the results equal
+// those of the full slope bit for bit.  When the product underflows to zero the
+// slope is zero, so the divisor dl + dr is never zero or subnormal.
 template <class T>
-__device__ __forceinline__ T vanleer(T dl, T dr) {
+__device__ __forceinline__ T hslope(T dl, T dr) {
   T pr = dl * dr;
-  return le0(pr) ? T(0) : hdiv(T(2) * pr, dl + dr);
+  return le0(pr) ? T(0) : hdiv(pr, dl + dr);
 }
 
-// time-centred upwind value at the face between elements c-st and c.  The four
-// candidate elements are loaded before the upwind side is chosen, so the loads
-// do not wait for the face velocity.
 // The upwind side's value, slopes and coefficient are selected first, so one limiter
 // (one division) serves both flow directions: u > 0 gives qm + (1 - cour)/2 * slope,
-// u <= 0 gives q0 + (-1 - cour)/2 * slope = q0 - (1 + cour)/2 * slope.
+// u <= 0 gives q0 + (-1 - cour)/2 * slope = q0 - (1 + cour)/2 * slope, with
+// (+-1 - cour)/2 * slope = (+-1 - cour) * hslope.
 template <class T>
 __device__ __forceinline__ T upwind_v(T qmm, T qm, T q0, T qp, T u, T cour) {
   const bool up = gt0(u);
@@ -105,8 +105,7 @@ __device__ __forceinline__ T upwind_v(T qmm, T qm, T q0, T qp, T u, T cour) {
   const T a = up ? qm : q0;
   const T dl = up ? qm - qmm : dm;
   const T dr = up ? dm : qp - q0;
-  const T coef = T(0.5) * ((up ? T(1) : T(-1)) - cour);
-  return a + coef * vanleer(dl, dr);
+  return a + ((up ? T(1) : T(-1)) - cour) * hslope(dl, dr);
 }
 
 template <class T>
@@ -936,11 +935,12 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
   for (int a = 0; a < 3; ++a) all_active = all_active && hh[a] >= 0 && 2 * hh[a] + 1 < F.n[a];
   if (all_active) return;
   const int sa = f >= F_VX ? f - F_VX : -1;
+  // offsets of the two fine positions in coarse cells, doubled for the half slope
   T dl[3], dh[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    dl[a] = a == sa ? T(0) : T(-0.25);
-    dh[a] = a == sa ? T(0.5) : T(0.25);
+    dl[a] = a == sa ? T(0) : T(-0.5);
+    dh[a] = a == sa ? T(1) : T(0.5);
   }
   const T* q = (const T*)C.q[f];
   const int base = ((C.G + F.off[2] + h2) * C.s[1] + C.G + F.off[1] + h1) * C.s[0] + C.G +
@@ -953,7 +953,7 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
     for (int dx = 0; dx < 3; ++dx) {
       int b = base + (dy - 1) * C.st[1] + (dx - 1);
       T qm = q[b - C.st[2]], q0 = q[b], qp = q[b + C.st[2]];
-      T s = vanleer(q0 - qm, qp - q0);
+      T s = hslope(q0 - qm, qp - q0);
       vz[0][dy][dx] = q0 + dl[2] * s;
       vz[1][dy][dx] = q0 + dh[2] * s;
     }
@@ -964,7 +964,7 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) {
       T qm = vz[iz][0][dx], q0 = vz[iz][1][dx], qp = vz[iz][2][dx];
-      T s = vanleer(q0 - qm, qp - q0);
+      T s = hslope(q0 - qm, qp - q0);
       vy[iz][0][dx] = q0 + dl[1] * s;
       vy[iz][1][dx] = q0 + dh[1] * s;
     }
@@ -975,7 +975,7 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
 #pragma unroll
     for (int iy = 0; iy < 2; ++iy) {
       T qm = vy[iz][iy][0], q0 = vy[iz][iy][1], qp = vy[iz][iy][2];
-      T s = vanleer(q0 - qm, qp - q0);
+      T s = hslope(q0 - qm, qp - q0);
 #pragma unroll
       for (int ix = 0; ix < 2; ++ix) {
         int fi = G + 2 * h0 + ix, fj = G + 2 * h1 + iy, fk = G + 2 * h2 + iz;
