@@ -138,11 +138,18 @@ ARRAYS_PER_ELEM = {
 
 # FP64 flops executed per box element (DADD + DMUL + 2 DFMA, from the ncu capture in
 # profiles/k_sweeps_nested_3x64_fp64.md) of the FP64 sweep kernels
-FP64_FLOPS_PER_ELEM = {"tflux": 55.0, "tmom": 94.3, "tupdate": 14.1}
+FP64_FLOPS_PER_ELEM = {"tflux": 40.9, "tmom": 80.4, "tupdate": 14.1}
 # FP64 peak of GB300 derived from unit counts and the clock: 2 DFMA lanes per SM per
 # cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 2),
 # x 2 flops x 152 SMs x 2.07 GHz
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+# DRAM bytes (read + write) per box element of a launch, from the ncu captures in
+# profiles/ (k_sweeps_nested_3x64_fp64.md: tmom, 80^3 box, 20.1 MB;
+# k_sweep_fused_precision_5x128_fp32.md: fused sweeps, 144^3 box, 87.7 / 97.6 / 84.9 MB);
+# `traffic` scales them to the mean box of the timed launches
+TRAFFIC_PER_ELEM = {("nested_3x64^3_fp64", 8, "tmom"): 20.1e6 / 80**3,
+                    ("precision_5x128^3", 4, "sweep"): (87.7e6 + 97.6e6 + 84.9e6) / 3 / 144**3}
 
 
 def level_step_boxes(cfg):
@@ -547,6 +554,10 @@ def main():
     avg_s = dom_ms / dom_n / 1e3
     achieved = bpl / avg_s / 1e9
     peak, peak_kind = peaks()
+    # DRAM traffic per launch (ncu, scaled to the mean box), when the capture exists
+    boxes_all = level_step_boxes(cfg)
+    tpe = TRAFFIC_PER_ELEM.get((cfg["name"], esz, dom))
+    traffic = tpe * sum(boxes_all) / len(boxes_all) if tpe is not None else None
     hbm = {"achieved_gbs": achieved, "peak_gbs": peak, "frac": achieved / peak,
            "peak_source": peak_kind, "algorithmic_bytes_per_launch": bpl}
     if prec == binding.DF_FP64 and dom in FP64_FLOPS_PER_ELEM:
@@ -556,7 +567,7 @@ def main():
         ach = flops / avg_s / 1e12
         roofline = {
             "kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
             "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz",
             "fp64_flops_per_launch": flops, "launches_timed": dom_n,
             "avg_launch_ms": dom_ms / dom_n,
@@ -566,7 +577,7 @@ def main():
     else:
         roofline = {
             "kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": bpl, "launches_timed": dom_n,
             "avg_launch_ms": dom_ms / dom_n,
             "share_of_kernel_time": dom_ms / total_k if total_k else None,
