@@ -381,6 +381,40 @@ def run_precision_compare(args):
     return 0
 
 
+def run_heating_ladder(args):
+    """Heating force by differencing (Eq. 5) over a ladder of 4..7 nested levels at
+    Mach 3 (Sec. 4.1 set-up): the hot and cold run of every level count in one pool
+    (FP32 state, FP64 reductions), stepped to 100 tau; each added level should raise
+    the heating force by the Eq. 24 increment (its asymptotic value; the finite
+    resolution of Eq. 10-12 lowers it)."""
+    import torch
+
+    from paper_1812_03191_gb300 import ladder
+    if args.impl == "reference":
+        return 0
+    torch.cuda.set_device(0)
+    with ClockSampler(0) as clk:
+        out = ladder.run(levels=(4, 5, 6, 7), sample_every=8)
+    pred = out["predicted_increment"]
+    ratios = {k: v / pred for k, v in out["increments"].items()}
+    line = {
+        "metric": "heating-force increment per added level / Eq. 24", "value":
+            float(np.mean(list(ratios.values()))), "unit": "ratio", "n_gpus": 1,
+        "steps": sum(r["steps"] for r in out["runs"].values()), "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32-state/f64-reductions", "data": "synthetic",
+        "config": {"workload": "heating_ladder_mach3", "levels": out["levels"], "n": 32,
+                   "gamma": 1.4, "GM": 1e-3, "chi": 0.1, "L": 2e-4, "half_width": out["half"],
+                   "t_end": out["t_end"]},
+        "heating_force_final": {k: r["final"] for k, r in out["runs"].items()},
+        "increments": out["increments"], "eq24_increment": pred, "ratios": ratios,
+        "pool_cell_updates_per_s": out["cell_updates"] / out["wall_s"],
+        "wall_s": out["wall_s"], "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     """Poisson stream of requests (levels 2..6, mesh {48,64,96,128}^3, Mach U[0.05,4],
     chi log-U[0.3,3], L on/off) through the continuous-batching server (FP32 state,
@@ -445,7 +479,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nested",
                     choices=["nested", "single", "precision", "batched", "serving",
-                             "precision_compare"])
+                             "precision_compare", "heating_ladder"])
     ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--step-cap", type=int, default=200)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
@@ -465,6 +499,8 @@ def main():
         return run_serving(args)
     if args.workload == "precision_compare":
         return run_precision_compare(args)
+    if args.workload == "heating_ladder":
+        return run_heating_ladder(args)
     cfg = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, cfg)

@@ -1,0 +1,131 @@
+"""Heating-force differencing over a ladder of nested levels (Sec. 4.1, Eq. 5, Eq. 24).
+
+The heating force is the difference between the force on a luminous perturber and
+on a cold one in otherwise identical runs (Eq. 5).  For every level count of the
+ladder a hot run (luminosity L) and a cold run (L = 0) are admitted to one pool and
+stepped together with the same fixed time step, so their force histories share
+their time points; the heating force is their difference along the perturber's
+motion.  Adding a level halves the finest cell: in the supersonic regime the
+heating force then grows by (gamma - 1) GM L ln 2 / (chi V^2) (Eq. 24, from the
+logarithm of Eq. 13), independent of the level count.
+
+Set-up (Sec. 4 and 4.1): gamma = 1.4, rho0 = c_s = 1, GM = 1e-3, chi = 0.1,
+L = 2e-4, no softening, the energy L dt split over the eight cells around the
+perturber's vertex, a coarse box [-l, l]^3 with l = 100 lambda and
+lambda = chi / (gamma V) (Eq. 7), n = 32 cells per level and axis (the paper's
+16 x 16 x 32 quadrant meshes over [0, l]^2 x [-l, l], here as a full box, so that
+6 levels reach its finest cell of 25/128 lambda), run to 100 tau with
+tau = chi / (gamma^2 V^2) (Eq. 9).
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+
+from . import binding
+from . import inputs as I
+
+
+def lam(chi, gamma, V):
+    """cut-off length of the hot plume (Eq. 7)"""
+    return chi / (gamma * V)
+
+
+def tau(chi, gamma, V):
+    """settling time of the heating force (Eq. 9)"""
+    return chi / (gamma * gamma * V * V)
+
+
+def eq24_increment(gamma, GM, L, chi, V):
+    """growth of the supersonic heating force when the resolution doubles (Eq. 24)"""
+    return (gamma - 1.0) * GM * L * math.log(2.0) / (chi * V * V)
+
+
+def fixed_dt(n_levels, n, half, params, safety=0.8):
+    """coarse step from the Courant and diffusion limits of every level (Eq. 55 with
+    xi = 2), for the background flow, times a safety factor for the perturbation"""
+    V = params["mach"] * params["cs"]
+    best = math.inf
+    for l in range(n_levels):
+        dx = 2.0 * half / n / 2**l
+        lim = params["cfl"] * dx / (params["cs"] + V)
+        if params["chi"] > 0:
+            lim = min(lim, params["cfl_diff"] * dx * dx / (6.0 * params["chi"]))
+        best = min(best, lim * 2**l)
+    return safety * best
+
+
+def setup(mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32, box_lambdas=100.0):
+    """parameter dicts of the hot and cold runs and the coarse half-width"""
+    half = box_lambdas * lam(chi, gamma, mach)
+    base = I.base_params(gamma=gamma, rho0=1.0, cs=1.0, mach=mach, GM=GM, eps=0.0, chi=chi,
+                         L=0.0, lum_sigma=0.0)
+    hot = dict(base, L=L)
+    cold = dict(base, L=0.0)
+    return hot, cold, half
+
+
+def run(levels=(4, 5, 6, 7), mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32,
+        t_end_taus=100.0, precision=binding.DF_FP32_STATE, sample_every=4,
+        budget=32 << 30):
+    """Step hot/cold pairs for every level count to t_end = t_end_taus * tau.
+
+    Returns a dict with, per level count, the time points and the heating force
+    along the motion, its final value (mean over the last tenth of the run), the
+    increments between successive level counts and the Eq. 24 prediction."""
+    hot, cold, half = setup(mach, chi, GM, L, gamma, n)
+    V = mach
+    t_end = t_end_taus * tau(chi, gamma, V)
+    lo, hi = (-half,) * 3, (half,) * 3
+    pool = binding.Pool(budget, precision=precision)
+    pairs = {}
+    for nl in levels:
+        dt = fixed_dt(nl, n, half, hot)
+        sh = pool.admit(nl, n, lo, hi, I.DEFAULT_G, dict(hot, dt_fixed=dt))
+        sc = pool.admit(nl, n, lo, hi, I.DEFAULT_G, dict(cold, dt_fixed=dt))
+        if sh is None or sc is None:
+            raise RuntimeError("ladder does not fit the pool budget")
+        pairs[nl] = dict(slots=(sh, sc), dt=dt, steps=0, t=[], F=[], done=False)
+    d = np.asarray(hot["flow_dir"], dtype=float)
+    d = d / np.linalg.norm(d)
+    t0 = time.perf_counter()
+    cell_updates = 0
+    while not all(p["done"] for p in pairs.values()):
+        pool.step(sample_every)
+        q = pool.query()
+        for nl, p in pairs.items():
+            if p["done"]:
+                continue
+            sh, sc = p["slots"]
+            p["steps"] += sample_every
+            cell_updates += 2 * sample_every * n**3 * (2**nl - 1)
+            if q[sh, 5] != 0 or q[sc, 5] != 0:
+                raise RuntimeError(f"{nl} levels: unhealthy state")
+            if q[sh, 3] != q[sc, 3]:
+                raise RuntimeError("hot and cold runs out of step")
+            Fh = -float(np.dot(q[sh, :3], d))
+            Fc = -float(np.dot(q[sc, :3], d))
+            p["t"].append(float(q[sh, 3]))
+            p["F"].append(Fh - Fc)
+            if q[sh, 3] >= t_end:
+                p["done"] = True
+                pool.release(sh)
+                pool.release(sc)
+    wall = time.perf_counter() - t0
+    pool.close()
+    out = dict(levels=list(levels), t_end=t_end, half=half, wall_s=wall,
+               cell_updates=cell_updates,
+               predicted_increment=eq24_increment(gamma, GM, L, chi, V), runs={})
+    final = {}
+    for nl, p in pairs.items():
+        t = np.array(p["t"])
+        F = np.array(p["F"])
+        tail = t >= 0.9 * t[-1]
+        final[nl] = float(F[tail].mean())
+        out["runs"][nl] = dict(dt=p["dt"], steps=p["steps"], t=t.tolist(), F_heating=F.tolist(),
+                               final=final[nl],
+                               finest_dx=2.0 * half / n / 2**(nl - 1))
+    out["increments"] = {f"{a}->{b}": final[b] - final[a] for a, b in zip(levels, levels[1:])}
+    return out
