@@ -175,6 +175,22 @@ def bytes_per_launch(cfg, kind, esz, fused=False):
     return None
 
 
+def job_time_ms(ms, dist, device):
+    """The job's timed-region duration: the slowest rank's (replicas run independent
+    runs; the only collective is this reduction, outside the timed region)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank_step, steps, world, ms):
+    """whole-job throughput: the units every rank processed / the job's time"""
+    return units_per_rank_step * steps * world / (ms / 1e3)
+
+
 def tile_summary(shapes):
     """{op: [shape of x, y, z sweep]} for the ops whose tuned shape is not flat"""
     if shapes is None:
@@ -560,12 +576,8 @@ def main():
     if dist:
         dist.barrier()
     launches = sim.kernel_launches() - l0
-    ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = cu * args.steps * world / (ms / 1e3)
+    ms = job_time_ms(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
+    value = job_value(cu, args.steps, world, ms)
     clocks = clk.summary()
     F, Fmot = sim.force()
 
