@@ -43,6 +43,16 @@ def eq24_increment(gamma, GM, L, chi, V):
     return (gamma - 1.0) * GM * L * math.log(2.0) / (chi * V * V)
 
 
+def eq8_force(gamma, GM, L, chi, cs=1.0):
+    """low-Mach heating force M a_{0,L,chi} of the linear steady state (Eq. 8)"""
+    return gamma * (gamma - 1.0) * GM * L / (2.0 * chi * cs * cs)
+
+
+def h_fraction(rp):
+    """share of the low-Mach heating force from within r' = r / 2 lambda (Eq. 23)"""
+    return (1.0 - 2.0 * rp - math.exp(-2.0 * rp)) / (2.0 * rp * rp) + 1.0
+
+
 def fixed_dt(n_levels, n, half, params, safety=0.8):
     """coarse step from the Courant and diffusion limits of every level (Eq. 55 with
     xi = 2), for the background flow, times a safety factor for the perturbation"""
@@ -65,6 +75,25 @@ def setup(mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32, box_lambdas=100.0
     hot = dict(base, L=L)
     cold = dict(base, L=0.0)
     return hot, cold, half
+
+
+def low_mach(mach=0.1, n_levels=6, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32,
+             t_end_taus=100.0, precision=binding.DF_FP32_STATE, sample_every=8):
+    """One hot/cold pair at low Mach (Sec. 4.1.1): the heating force against Eq. 8
+    times the share h(r'_max) - h(r'_min) of Eq. 23 that the box (r'_max = l / 2
+    lambda) and the finest cell (r'_min = dx / 2 lambda) can hold."""
+    out = run(levels=(n_levels,), mach=mach, chi=chi, GM=GM, L=L, gamma=gamma, n=n,
+              t_end_taus=t_end_taus, precision=precision, sample_every=sample_every)
+    lam_ = lam(chi, gamma, mach)
+    r = out["runs"][n_levels]
+    rp_min = r["finest_dx"] / (2.0 * lam_)
+    rp_max = out["half"] / (2.0 * lam_)
+    share = h_fraction(rp_max) - h_fraction(rp_min)
+    out["eq8_force"] = eq8_force(gamma, GM, L, chi)
+    out["eq23_share"] = share
+    out["expected"] = out["eq8_force"] * share
+    out["ratio"] = r["final"] / out["expected"]
+    return out
 
 
 def run(levels=(4, 5, 6, 7), mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32,

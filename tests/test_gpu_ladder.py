@@ -37,3 +37,12 @@ def test_heating_force_grows_by_the_eq24_increment_per_level():
         F = np.array(out["runs"][nl]["F_heating"])
         k = len(F)
         assert abs(F[-1] - F[3 * k // 4]) < 0.02 * abs(F[-1])
+
+
+def test_low_mach_heating_force_matches_eq8_within_the_box_share():
+    """Mach 0.1, 6 levels, 100 tau: the heating force equals Eq. 8 times the share
+    h(r'_max) - h(r'_min) = 0.918 of Eq. 23 that the box and the finest cell hold
+    (measured: within 0.6 %; the paper's Fig. 6 inset: within ~3 %)."""
+    out = ladder.low_mach(mach=0.1)
+    assert out["eq23_share"] == pytest.approx(0.918, abs=1e-3)
+    assert abs(out["ratio"] - 1.0) < 0.03, out["ratio"]
