@@ -412,6 +412,7 @@ def run_heating_ladder(args):
     with ClockSampler(0) as clk:
         out = ladder.run(levels=(4, 5, 6, 7), sample_every=8)
         low = ladder.low_mach(mach=0.1)
+        cold = ladder.cold_thermal(mach=0.1)
     pred = out["predicted_increment"]
     ratios = {k: v / pred for k, v in out["increments"].items()}
     line = {
@@ -427,6 +428,9 @@ def run_heating_ladder(args):
         "increments": out["increments"], "eq24_increment": pred, "ratios": ratios,
         "low_mach": {"mach": 0.1, "levels": 6, "heating_force": low["runs"][6]["final"],
                      "eq8_times_eq23_share": low["expected"], "ratio": low["ratio"]},
+        "cold_thermal_low_mach": {"mach": 0.1, "levels": 6, "force": cold["runs"][6]["final"],
+                                  "eq51_times_eq23_share": cold["expected"],
+                                  "ratio": cold["ratio"]},
         "pool_cell_updates_per_s": out["cell_updates"] / out["wall_s"],
         "wall_s": out["wall_s"], "clocks": clk.summary(),
     }

@@ -96,65 +96,94 @@ def low_mach(mach=0.1, n_levels=6, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32,
     return out
 
 
-def run(levels=(4, 5, 6, 7), mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32,
-        t_end_taus=100.0, precision=binding.DF_FP32_STATE, sample_every=4,
-        budget=32 << 30):
-    """Step hot/cold pairs for every level count to t_end = t_end_taus * tau.
-
-    Returns a dict with, per level count, the time points and the heating force
-    along the motion, its final value (mean over the last tenth of the run), the
-    increments between successive level counts and the Eq. 24 prediction."""
-    hot, cold, half = setup(mach, chi, GM, L, gamma, n)
-    V = mach
-    t_end = t_end_taus * tau(chi, gamma, V)
+def pairs(levels, pa, pb, half, n=32, t_end=1.0, precision=binding.DF_FP32_STATE,
+          sample_every=8, budget=32 << 30):
+    """Runs with parameters pa and pb for every level count, one pool, the same fixed
+    coarse step per level count (from pa's limits); the history of F_a - F_b along
+    the motion and its final value (mean over the last tenth of the run)."""
     lo, hi = (-half,) * 3, (half,) * 3
     pool = binding.Pool(budget, precision=precision)
-    pairs = {}
+    runs = {}
     for nl in levels:
-        dt = fixed_dt(nl, n, half, hot)
-        sh = pool.admit(nl, n, lo, hi, I.DEFAULT_G, dict(hot, dt_fixed=dt))
-        sc = pool.admit(nl, n, lo, hi, I.DEFAULT_G, dict(cold, dt_fixed=dt))
-        if sh is None or sc is None:
-            raise RuntimeError("ladder does not fit the pool budget")
-        pairs[nl] = dict(slots=(sh, sc), dt=dt, steps=0, t=[], F=[], done=False)
-    d = np.asarray(hot["flow_dir"], dtype=float)
+        dt = fixed_dt(nl, n, half, pa)
+        sa = pool.admit(nl, n, lo, hi, I.DEFAULT_G, dict(pa, dt_fixed=dt))
+        sb = pool.admit(nl, n, lo, hi, I.DEFAULT_G, dict(pb, dt_fixed=dt))
+        if sa is None or sb is None:
+            raise RuntimeError("the runs do not fit the pool budget")
+        runs[nl] = dict(slots=(sa, sb), dt=dt, steps=0, t=[], F=[], done=False)
+    d = np.asarray(pa["flow_dir"], dtype=float)
     d = d / np.linalg.norm(d)
     t0 = time.perf_counter()
     cell_updates = 0
-    while not all(p["done"] for p in pairs.values()):
+    while not all(p["done"] for p in runs.values()):
         pool.step(sample_every)
         q = pool.query()
-        for nl, p in pairs.items():
+        for nl, p in runs.items():
             if p["done"]:
                 continue
-            sh, sc = p["slots"]
+            sa, sb = p["slots"]
             p["steps"] += sample_every
             cell_updates += 2 * sample_every * n**3 * (2**nl - 1)
-            if q[sh, 5] != 0 or q[sc, 5] != 0:
+            if q[sa, 5] != 0 or q[sb, 5] != 0:
                 raise RuntimeError(f"{nl} levels: unhealthy state")
-            if q[sh, 3] != q[sc, 3]:
-                raise RuntimeError("hot and cold runs out of step")
-            Fh = -float(np.dot(q[sh, :3], d))
-            Fc = -float(np.dot(q[sc, :3], d))
-            p["t"].append(float(q[sh, 3]))
-            p["F"].append(Fh - Fc)
-            if q[sh, 3] >= t_end:
+            if q[sa, 3] != q[sb, 3]:
+                raise RuntimeError("paired runs out of step")
+            Fa = -float(np.dot(q[sa, :3], d))
+            Fb = -float(np.dot(q[sb, :3], d))
+            p["t"].append(float(q[sa, 3]))
+            p["F"].append(Fa - Fb)
+            if q[sa, 3] >= t_end:
                 p["done"] = True
-                pool.release(sh)
-                pool.release(sc)
+                pool.release(sa)
+                pool.release(sb)
     wall = time.perf_counter() - t0
     pool.close()
     out = dict(levels=list(levels), t_end=t_end, half=half, wall_s=wall,
-               cell_updates=cell_updates,
-               predicted_increment=eq24_increment(gamma, GM, L, chi, V), runs={})
-    final = {}
-    for nl, p in pairs.items():
+               cell_updates=cell_updates, runs={})
+    for nl, p in runs.items():
         t = np.array(p["t"])
         F = np.array(p["F"])
         tail = t >= 0.9 * t[-1]
-        final[nl] = float(F[tail].mean())
-        out["runs"][nl] = dict(dt=p["dt"], steps=p["steps"], t=t.tolist(), F_heating=F.tolist(),
-                               final=final[nl],
+        out["runs"][nl] = dict(dt=p["dt"], steps=p["steps"], t=t.tolist(), F=F.tolist(),
+                               final=float(F[tail].mean()),
                                finest_dx=2.0 * half / n / 2**(nl - 1))
+    return out
+
+
+def run(levels=(4, 5, 6, 7), mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32,
+        t_end_taus=100.0, precision=binding.DF_FP32_STATE, sample_every=4,
+        budget=32 << 30):
+    """Heating force (hot minus cold run, Eq. 5) for every level count, stepped to
+    t_end = t_end_taus * tau, with the increments between successive level counts
+    and the Eq. 24 prediction."""
+    hot, cold, half = setup(mach, chi, GM, L, gamma, n)
+    out = pairs(levels, hot, cold, half, n=n, t_end=t_end_taus * tau(chi, gamma, mach),
+                precision=precision, sample_every=sample_every, budget=budget)
+    out["predicted_increment"] = eq24_increment(gamma, GM, L, chi, mach)
+    for r in out["runs"].values():
+        r["F_heating"] = r.pop("F")
+    final = {nl: r["final"] for nl, r in out["runs"].items()}
     out["increments"] = {f"{a}->{b}": final[b] - final[a] for a, b in zip(levels, levels[1:])}
+    return out
+
+
+def cold_thermal(mach=0.1, n_levels=6, chi=0.1, GM=1e-3, gamma=1.4, n=32, t_end_taus=100.0,
+                 precision=binding.DF_FP32_STATE, sample_every=8):
+    """Cold thermal force (Sec. 4.2): a cold perturber with thermal diffusion minus the
+    same in an adiabatic gas, at low Mach, against -(gamma - 1)/2 F0 (Eq. 48, Eq. 50,
+    Eq. 51) times the Eq. 23 share of the box (the perturbation is that of a heat sink
+    of luminosity -L_c, Eq. 49)."""
+    _, cold, half = setup(mach, chi, GM, 0.0, gamma, n)
+    adiabatic = dict(cold, chi=0.0)
+    out = pairs((n_levels,), cold, adiabatic, half, n=n,
+                t_end=t_end_taus * tau(chi, gamma, mach), precision=precision,
+                sample_every=sample_every)
+    lam_ = lam(chi, gamma, mach)
+    r = out["runs"][n_levels]
+    share = h_fraction(half / (2.0 * lam_)) - h_fraction(r["finest_dx"] / (2.0 * lam_))
+    F0 = 4.0 * math.pi * GM * GM
+    out["eq51_force"] = -(gamma - 1.0) / 2.0 * F0
+    out["eq23_share"] = share
+    out["expected"] = out["eq51_force"] * share
+    out["ratio"] = r["final"] / out["expected"]
     return out
