@@ -88,8 +88,11 @@ int df_set_params(df_ctx* ctx, const df_params* p);
 
 /* Advance n coarse steps: per step the time step of Eq. 55 (reductions on the
  * device), then the recursion of Sec. 3.3 (finer levels first, xi sub-cycles,
- * CommFlux, CommUp, CommMean), then the force of Eq. 18.  Asynchronous on the
- * context's stream; DF_EUNHEALTHY is reported by the next synchronising call. */
+ * CommFlux, CommUp, CommMean), then the force of Eq. 18.  With xi_mode = 1 the
+ * Eq. 55-56 search also runs on the device each step and the second sub-cycles
+ * of levels with xi = 1 do no work, so either mode replays one CUDA graph.
+ * Asynchronous on the context's stream; DF_EUNHEALTHY is reported by the next
+ * synchronising call. */
 int df_step(df_ctx* ctx, int n_coarse_steps);
 
 /* Synchronise, then return time, last coarse step and health (0 healthy). */
@@ -231,7 +234,8 @@ int df_pool_create(df_pool** out, size_t hbm_budget_bytes, int precision, int de
 
 /* Admit one run (arguments as df_create + df_set_params); returns its slot.
  * DF_EBUSY when the budget would be exceeded (nothing is allocated then);
- * DF_EINVAL for bad shapes or parameters (xi_mode must be 0). */
+ * DF_EINVAL for bad shapes or parameters.  Runs with xi_mode = 1 choose their
+ * sub-cycling on the device each coarse step, as in a context. */
 int df_pool_admit(df_pool* pool, int n_levels, const int n[3], const double lo[3],
                   const double hi[3], int G, const df_params* p, int* slot_out);
 
@@ -248,6 +252,8 @@ int df_pool_query(df_pool* pool, double* out, int max_slots);
 
 /* Active cells of one field of one level of a slot's run, FP64 (as df_get_field). */
 int df_pool_get_field(df_pool* pool, int slot, int level, int field, double* host_out);
+/* Set the active cells of one field of one level of a slot's run (as df_set_field). */
+int df_pool_set_field(df_pool* pool, int slot, int level, int field, const double* host_in);
 
 /* Active runs, bytes in use, the budget, kernels launched so far. */
 int df_pool_info(df_pool* pool, int* active, size_t* used, size_t* budget, long long* launches);

@@ -30,7 +30,7 @@ EXPORTS = (
     "df_pool_query", "df_pool_get_field", "df_pool_info", "df_pool_set_tiles",
     "df_pool_autotune", "df_pool_destroy", "df_pool_set_timing", "df_pool_kernel_time",
     "df_autotune", "df_set_tile_shapes", "df_pool_set_tile_shapes", "df_set_transport",
-    "df_pool_set_transport",
+    "df_pool_set_transport", "df_pool_set_field",
 )
 POOL_OPS = 20
 # operator order of the per-op tables (tile shapes, blocks per SM)
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH):
         "df_set_tile_shapes": (C.c_int, [vp, P(C.c_int)]),
         "df_set_transport": (C.c_int, [vp, C.c_int]),
         "df_pool_set_transport": (C.c_int, [vp, C.c_int]),
+        "df_pool_set_field": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, dp]),
         "df_pool_set_tile_shapes": (C.c_int, [vp, P(C.c_int)]),
         "df_destroy": (C.c_int, [vp]),
         "df_xi_search": (C.c_int, [C.c_int, dp, dp, P(C.c_int), dp]),
@@ -413,6 +414,13 @@ class Pool:
         if ns < 0:
             _check(ns)
         return out[:6 * ns].reshape(ns, 6)
+
+    def set_field(self, slot, level, field, values):
+        nl, n = self.shapes[slot]
+        a = np.ascontiguousarray(values, dtype=np.float64).reshape(-1)
+        if a.size != n[0] * n[1] * n[2]:
+            raise ValueError("field size does not match the run's mesh")
+        _check(self.lib.df_pool_set_field(self.h, int(slot), level, field, _dp(a)))
 
     def get_field(self, slot, level, field):
         nl, n = self.shapes[slot]

@@ -414,8 +414,11 @@ int kind_of(int op) {
 
 void fill_fin(const Run& r, DtFinal& fin) {
   double pr = 1.0;
+  fin.search = 0;
+  fin.pad = 0;
   for (int l = 0; l < 16; ++l) {
     fin.prod[l] = 1.0;
+    fin.cost[l] = 0.0;
     fin.diff_lim[l] = INFINITY;
     for (int d = 0; d < 3; ++d) fin.cfl_dx[l][d] = 0.0;
   }
@@ -429,7 +432,9 @@ void fill_fin(const Run& r, DtFinal& fin) {
       fin.diff_lim[l] = r.P.cfl_diff / (2.0 * r.P.chi * sinv);
     }
     for (int d = 0; d < 3; ++d) fin.cfl_dx[l][d] = r.P.hydro_on ? r.P.cfl * v.dx[d] : 0.0;
+    fin.cost[l] = (double)v.n[0] * v.n[1] * v.n[2];
   }
+  fin.search = r.prm.xi_mode == 1 && r.nl > 1;
 }
 
 // tile shape (index into kTileShapes) of each stencil op and sweep direction
@@ -452,6 +457,7 @@ struct Builder {
   const DtFinal* d_fins = nullptr;
   TileTable tiles;
   bool fused = false;  // transport as one fused kernel per sweep
+  mutable unsigned br = 0;  // second sub-cycles enclosing the items being added
 
   Item<T> base(const Run& r, int l) const {
     Item<T> it;
@@ -509,6 +515,7 @@ struct Builder {
   void add(std::vector<Entry>& out, int op, int d, Item<T> it) const {
     it.b.tile = is_box_op(op) ? tiles.t[op][d] : 0;
     it.b.zc = op == OP_SWEEP ? sweep_chunk(it.b, d) : 0;
+    it.br = br;
     it.count = op_count(op, d, it.L, it.F, it.b);
     out.push_back({op, d, it});
   }
@@ -554,7 +561,14 @@ struct Builder {
     if (l + 1 < r.nl) {
       add(out, OP_ZERO_ACC, 0, base(r, l + 1));
       int xi = r.xi[l];
-      for (int s = 0; s < xi; ++s) advance(r, l + 1, (xi - 1 - s) * kReach, out);
+      for (int s = 0; s < xi; ++s) {
+        // the second sub-cycle (and all it encloses) is dropped on the device when
+        // the Eq. 55-56 search picks xi_l = 1; the first keeps the margin of two
+        const unsigned saved = br;
+        if (s == 1) br |= 1u << l;
+        advance(r, l + 1, (xi - 1 - s) * kReach, out);
+        br = saved;
+      }
     }
     level_step(r, l, m_out, out);
     if (l + 1 < r.nl) {
@@ -1216,46 +1230,11 @@ int df_step(df_ctx* c, int n) {
   enter(c);
   int rc = DF_OK;
   std::vector<Run*> runs{r};
-  if (r->prm.xi_mode == 1 && r->nl > 1) {
-    // Eq. 55-56 search each coarse step: the per-level limits come back to the
-    // host, the plan is rebuilt for the chosen word and launched without a graph
-    for (int s = 0; s < n && !rc; ++s) {
-      std::vector<std::pair<int, int>> ops;
-      for (int l = 0; l < r->nl; ++l) ops.push_back({OP_DT_LEVEL, l});
-      rc = run_ops_now(r, c->x, ops);
-      if (rc) break;
-      unsigned long long bits[3 * DF_MAX_LEVELS];
-      CK(cudaMemcpy(bits, r->ds->dtmin, 3 * r->nl * sizeof(unsigned long long),
-                    cudaMemcpyDeviceToHost));
-      for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
-      DtFinal fin;
-      fill_fin(*r, fin);
-      double lim[DF_MAX_LEVELS], cost[DF_MAX_LEVELS];
-      for (int l = 0; l < r->nl; ++l) {
-        lim[l] = fin.diff_lim[l];
-        for (int d = 0; d < 3; ++d) {
-          double mx;
-          memcpy(&mx, &bits[3 * l + d], 8);
-          lim[l] = std::min(lim[l], fin.cfl_dx[l][d] / mx);
-        }
-        cost[l] = (double)r->n[0] * r->n[1] * r->n[2];
-      }
-      int xiw[DF_MAX_LEVELS];
-      double ratio;
-      df_xi_search(r->nl, lim, cost, xiw, &ratio);
-      for (int l = 0; l + 1 < r->nl; ++l) r->xi[l] = xiw[l];
-      rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles, c->transport);
-      if (rc) break;
-      c->x.launches += r->prec == DF_FP64 ? plan_run<double>(c->plan, c->x, c->x.timing)
-                                          : plan_run<float>(c->plan, c->x, c->x.timing);
-      plan_invalidate(c->plan);
-    }
-    for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
-  } else {
-    for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
-    if (!c->plan.valid) rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles, c->transport);
-    if (!rc) rc = step_plan(c->plan, c->x, r->prec, n);
-  }
+  // fixed sub-cycling and the Eq. 55-56 search share one plan (xi = 2 everywhere;
+  // the search drops second sub-cycles on the device), replayed from a graph
+  for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
+  if (!c->plan.valid) rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles, c->transport);
+  if (!rc) rc = step_plan(c->plan, c->x, r->prec, n);
   leave(c);
   r->stepped = true;
   return rc;
@@ -1333,6 +1312,7 @@ int df_compute_dt(df_ctx* c, double* dt, double* dt_level) {
   CK(cudaMemcpy(&r->ds->dt, &before.dt, sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(r->ds->dtl, before.dtl, sizeof before.dtl, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(r->ds->dtf, before.dtf, sizeof before.dtf, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(&r->ds->xi1, &before.xi1, sizeof before.xi1, cudaMemcpyHostToDevice));
   leave(c);
   if (dt) *dt = after.dt;
   if (dt_level)
@@ -1598,7 +1578,6 @@ int df_pool_admit(df_pool* p, int n_levels, const int n[3], const double lo[3],
                   const double hi[3], int G, const df_params* prm, int* slot_out) {
   if (!p || !n || !lo || !hi || !slot_out) return fail(DF_EINVAL, "null argument");
   if (check_params(prm)) return DF_EINVAL;
-  if (prm->xi_mode != 0) return fail(DF_EINVAL, "a pool steps every run with xi = 2");
   int rc = check_shape(n_levels, n, lo, hi, G, p->prec);
   if (rc) return rc;
   size_t need = run_bytes(n_levels, n, G, p->prec);
@@ -1697,6 +1676,16 @@ int df_pool_get_field(df_pool* p, int slot, int level, int field, double* out) {
   DevGuard g(p->device);
   enter(p);
   int rc = io(p->slots[slot], p->x.st, level, field, out, nullptr, 0, false, &p->x.launches);
+  leave(p);
+  return rc;
+}
+
+int df_pool_set_field(df_pool* p, int slot, int level, int field, const double* in) {
+  if (!p || slot < 0 || slot >= (int)p->slots.size() || !p->slots[slot] || !in)
+    return fail(DF_EINVAL, "no run in slot %d", slot);
+  DevGuard g(p->device);
+  enter(p);
+  int rc = io(p->slots[slot], p->x.st, level, field, nullptr, in, 0, false, &p->x.launches);
   leave(p);
   return rc;
 }

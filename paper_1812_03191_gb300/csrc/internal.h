@@ -106,7 +106,7 @@ struct DevScalars {
   double dtl[16];                // level step of each level: dt / prod_{m<l} xi_m
   float dtf[16];                 // the same in FP32
   int unhealthy;
-  int pad;
+  unsigned xi1;  // bit m set when the Eq. 55-56 search chose xi_m = 1 this coarse step
 };
 
 // per-level geometry constants in the kernels' arithmetic type (no FP64 work in
@@ -146,9 +146,12 @@ inline Bg<T> make_bg(const Phys& P) {
 
 // constants of the Eq. 55 finalisation of one run
 struct DtFinal {
-  double prod[16];       // prod_{m<l} xi_m
+  double prod[16];       // prod_{m<l} xi_m (fixed sub-cycling)
   double diff_lim[16];   // explicit-diffusion limit of each level
   double cfl_dx[16][3];  // cfl * dx_d (0 when hydro is off)
+  double cost[16];       // Eq. 56 cost of a level step of each level (cells)
+  int search;            // 1: choose xi_m in {1, 2} each coarse step (Eq. 55-56)
+  int pad;
 };
 
 // Ops of the work-list kernel.  Every launch runs one op over a list of work
@@ -190,6 +193,8 @@ struct __align__(16) Item {
   double gg, rho0d, e0d, V[3], dt_fixed;
   int ring_cap, npart, level, band, flags, bc_lo, bc_hi;
   unsigned count;       // index-space size of the item
+  unsigned br;          // bit m: inside the second sub-cycle of level m + 1 (skipped
+                        // when the search chose xi_m = 1)
 };
 
 // ---- kernels.cu: all asynchronous on `st`; return the number of kernels launched.

@@ -1140,25 +1140,85 @@ __device__ __forceinline__ void el_dt_level(const LevelView& L, int level, doubl
 // Eq. 55: dt = min_l dt_l prod_{m<l} xi_m; resets the per-level maxima
 __device__ __forceinline__ void el_dt_finalize(DevScalars* ds, int n_levels, const DtFinal& fin,
                                                double dt_fixed) {
+  __shared__ double s_lim[16];
+  __shared__ double s_ratio[kBlock];
+  __shared__ int s_word[kBlock];
+  if (threadIdx.x == 0) {
+    for (int l = 0; l < n_levels; ++l) {
+      double lim = fin.diff_lim[l];
+      for (int d = 0; d < 3; ++d) {
+        double mx = __longlong_as_double((long long)ds->dtmin[3 * l + d]);
+        double t = fin.cfl_dx[l][d] / mx;  // +inf when the maximum is 0
+        if (t < lim) lim = t;
+        ds->dtmin[3 * l + d] = 0ull;
+      }
+      ds->dtlev[l] = lim;
+      s_lim[l] = lim;
+    }
+  }
+  __syncthreads();
+  double prod[16];
+  unsigned xi1 = 0;
+  if (fin.search && n_levels > 1) {
+    // Eq. 55-56: the word xi_m in {1, 2} (bit m of w set: xi_m = 2) with the largest
+    // step per unit cost; ties go to the smallest w, as a sequential scan keeps the
+    // first maximum
+    const int nw = n_levels - 1;
+    double best = -1.0;
+    int bw = 0;
+    for (int w = threadIdx.x; w < (1 << nw); w += kBlock) {
+      double dt = INFINITY, C = 0.0, pr = 1.0;
+      for (int l = 0; l < n_levels; ++l) {
+        if (l > 0) pr *= ((w >> (l - 1)) & 1) ? 2.0 : 1.0;
+        const double t = s_lim[l] * pr;
+        if (t < dt) dt = t;
+        C += fin.cost[l] * pr;
+      }
+      const double ratio = dt / C;
+      if (ratio > best) {
+        best = ratio;
+        bw = w;
+      }
+    }
+    s_ratio[threadIdx.x] = best;
+    s_word[threadIdx.x] = bw;
+    __syncthreads();
+    for (int h = kBlock / 2; h > 0; h >>= 1) {
+      if ((int)threadIdx.x < h) {
+        const double r2 = s_ratio[threadIdx.x + h];
+        const int w2 = s_word[threadIdx.x + h];
+        if (r2 > s_ratio[threadIdx.x] || (r2 == s_ratio[threadIdx.x] && w2 < s_word[threadIdx.x])) {
+          s_ratio[threadIdx.x] = r2;
+          s_word[threadIdx.x] = w2;
+        }
+      }
+      __syncthreads();
+    }
+    const int w = s_word[0];
+    double pr = 1.0;
+    for (int l = 0; l < n_levels; ++l) {
+      if (l > 0) {
+        const bool two = (w >> (l - 1)) & 1;
+        pr *= two ? 2.0 : 1.0;
+        if (!two) xi1 |= 1u << (l - 1);
+      }
+      prod[l] = pr;
+    }
+  } else {
+    for (int l = 0; l < n_levels; ++l) prod[l] = fin.prod[l];
+  }
   if (threadIdx.x != 0) return;
   double dt = INFINITY;
   for (int l = 0; l < n_levels; ++l) {
-    double lim = fin.diff_lim[l];
-    for (int d = 0; d < 3; ++d) {
-      double mx = __longlong_as_double((long long)ds->dtmin[3 * l + d]);
-      double t = fin.cfl_dx[l][d] / mx;  // +inf when the maximum is 0
-      if (t < lim) lim = t;
-      ds->dtmin[3 * l + d] = 0ull;
-    }
-    ds->dtlev[l] = lim;
-    double t = lim * fin.prod[l];
+    double t = s_lim[l] * prod[l];
     if (t < dt) dt = t;
   }
   if (dt_fixed > 0.0) dt = dt_fixed;
   ds->dt = dt;
+  ds->xi1 = xi1;
   // level steps take dt / prod_{m<l} xi_m (a power of two: exact)
   for (int l = 0; l < n_levels; ++l) {
-    double dl = dt / fin.prod[l];
+    double dl = dt / prod[l];
     ds->dtl[l] = dl;
     ds->dtf[l] = (float)dl;
   }
@@ -1424,8 +1484,15 @@ int launch_hdiv_check(const double* a, const double* b, int n, double* max_ulp, 
 // =================================================================== work lists
 
 // One op on one work item: maps the item's fields onto the element function.
+// items inside a second sub-cycle that the Eq. 55-56 search dropped do nothing
+template <class T>
+__device__ __forceinline__ bool skipped(const Item<T>& it) {
+  return it.br != 0u && (it.br & it.ds->xi1) != 0u;
+}
+
 template <class T, int OP, int D>
 __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
+  if (skipped(it)) return;
   if (OP == OP_SOURCE)
     el_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.flags & FL_WRITE_PI, it.gm1, it.bg, it.g,
                  tid);
@@ -1529,6 +1596,7 @@ __global__ void __launch_bounds__(kBlock) k_single(const Item<T> it) {
 template <class T, int D>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_single(const Item<T> it) {
   __shared__ __align__(16) T s_x[2 * 3 * kSweepThreads];
+  if (skipped(it)) return;
   el_sweep<T, D>(it, blockIdx.x, s_x);
 }
 
@@ -1560,7 +1628,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_batch(const Item<T>* __
       __syncthreads();
       cur = lo;
     }
-    el_sweep<T, D>(it, ch - starts[cur], s_x);
+    if (!skipped(it)) el_sweep<T, D>(it, ch - starts[cur], s_x);
     __syncthreads();
   }
 }

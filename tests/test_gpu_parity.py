@@ -282,14 +282,65 @@ def test_time_step_matches():
     assert np.allclose(lv, lvo, rtol=1e-15, atol=0)
 
 
-def test_xi_search_mode_parity():
-    """Eq. 55-56 search each coarse step (advective limit dominant: chi small)."""
+@pytest.mark.parametrize("transport", TRANSPORTS, ids=TRANSPORT_IDS)
+def test_xi_search_mode_parity(transport):
+    """Eq. 55-56 search each coarse step on the device (advective limit dominant:
+    chi small, so the search drops sub-cycles), replayed from the CUDA graph."""
+    from oracle import xi_search
     p = I.base_params(GM=0.02, eps=0.3, chi=0.005, mach=1.2, xi_mode=1)
-    sim, orc = pair(3, 24, 6.0, p)
+    sim, orc = pair(3, 24, 6.0, p, transport=transport)
     perturb_both(sim, orc, seed=12, amp=2e-2)
+    # a fast stream in a corner of level 0, away from the finer levels: the coarse
+    # Courant limit binds, so the search drops second sub-cycles
+    ax = -6.0 + (np.arange(24) + 0.5) * 0.5
+    z, y, x = np.meshgrid(ax, ax, ax, indexing="ij")
+    bump = 3.0 * np.exp(-((x + 4.5) ** 2 + (y + 4.5) ** 2 + (z + 4.5) ** 2) / 0.5)
+    for s_ in (sim, orc):
+        s_.set_field(0, 2, s_.get_field(0, 2) - bump)
+    dt, lim = sim.compute_dt()
+    _, word = xi_search(lim, [24.0**3] * 3)
+    assert 1 in word, word  # the case exercises dropped second sub-cycles
     sim.step(6)
     orc.step(6)
     assert_parity(sim, orc, p)
+
+
+@pytest.mark.parametrize("precision", [binding.DF_FP64, binding.DF_FP32_STATE])
+def test_xi_search_runs_in_pools(precision):
+    """A run with the Eq. 55-56 search gives the same result in a pool, alone or
+    mixed with fixed-sub-cycling runs, and agrees with a context."""
+    p = I.base_params(GM=0.02, eps=0.3, chi=0.005, mach=1.2, xi_mode=1)
+    q = I.base_params(GM=0.01, eps=0.3, chi=0.5, mach=0.6)
+    lo, hi = (-6.0,) * 3, (6.0,) * 3
+    ax = -6.0 + (np.arange(24) + 0.5) * 0.5
+    z, y, x = np.meshgrid(ax, ax, ax, indexing="ij")
+    bump = 3.0 * np.exp(-((x + 4.5) ** 2 + (y + 4.5) ** 2 + (z + 4.5) ** 2) / 0.5)
+    alone = binding.Pool(1 << 33, precision=precision)
+    mix = binding.Pool(1 << 34, precision=precision)
+    a = alone.admit(3, 24, lo, hi, I.DEFAULT_G, p)
+    mix.admit(2, 32, lo, hi, I.DEFAULT_G, q)
+    m = mix.admit(3, 24, lo, hi, I.DEFAULT_G, p)
+    mix.admit(3, 24, lo, hi, I.DEFAULT_G, q)
+    sim = binding.Sim(3, 24, lo, hi, I.DEFAULT_G, p, precision=precision)
+    # the corner stream of test_xi_search_mode_parity: the search drops sub-cycles
+    v0 = sim.get_field(0, 2) - bump
+    sim.set_field(0, 2, v0)
+    alone.set_field(a, 0, 2, v0)
+    mix.set_field(m, 0, 2, v0)
+    alone.step(5)
+    mix.step(5)
+    for l in range(3):
+        for f in range(5):
+            assert np.array_equal(alone.get_field(a, l, f), mix.get_field(m, l, f)), (l, f)
+    qa, qm = alone.query()[a], mix.query()[m]
+    assert np.array_equal(qa, qm)
+    sim.step(5)
+    tol = 1e-10 if precision == binding.DF_FP64 else 1e-5
+    t, _, _ = sim.status()
+    assert abs(t - qa[3]) <= 1e-12 * t
+    for f in range(5):
+        x, y = sim.get_field(2, f), alone.get_field(a, 2, f)
+        assert np.abs(x - y).max() <= tol * (1.0 if f < 2 else 1.2), f
 
 
 @pytest.mark.parametrize("transport", TRANSPORTS, ids=TRANSPORT_IDS)
