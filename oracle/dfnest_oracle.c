@@ -60,6 +60,9 @@
  * R13  Level-0 boundary fill: periodic, outflow (copy of the nearest active
  *      element), inflow (background rho0, e0, V in every ghost element) or reflect
  *      (mirror, normal velocity odd with the wall face set to 0).
+ * R15  SubStep2 (named in Sec. 3.3 after ZEUS) is the von Neumann-Richtmyer
+ *      artificial viscosity of ZEUS (Stone & Norman 1992), applied after the first
+ *      kick when av_c2 > 0 (off by default: the paper's flows are nearly linear).
  */
 #include "dfnest_oracle.h"
 
@@ -358,6 +361,59 @@ static void source_step(or_sim* S, olevel* L, double h) {
   }
 }
 
+/* SubStep2, reading R15: the von Neumann-Richtmyer artificial viscosity in the form
+   of ZEUS (Stone & Norman 1992, ApJS 80, 753), whose stage names Sec. 3.3 uses.  Along
+   each axis d a compressed cell (dv = v_d at its upper face - v_d at its lower face
+   < 0) carries the viscous pressure q = C2 rho dv^2; every q is formed from the
+   state after the first kick, then the internal energy of each cell loses
+   dt q dv / dx_d (heating, since dv < 0) and the face velocity v_d gains
+   -dt (q_c - q_m) / (dx_d rho_face).  The topmost cell of an axis has no upper face
+   and no q; faces of index 0 are not updated (as in the kick). */
+static void viscosity_step(or_sim* S, olevel* L, double dt) {
+  double c2 = S->p.av_c2;
+  double* q[3];
+  for (int d = 0; d < 3; ++d) q[d] = (double*)calloc(L->nc, sizeof(double));
+  for (int d = 0; d < 3; ++d) {
+    size_t st = L->st[d];
+    for (int k = 0; k < L->s[2]; ++k)
+      for (int j = 0; j < L->s[1]; ++j)
+        for (int i = 0; i < L->s[0]; ++i) {
+          int c3[3] = {i, j, k};
+          if (c3[d] >= L->s[d] - 1) continue;
+          size_t c = idx(L, i, j, k);
+          double dv = L->q[VXF + d][c + st] - L->q[VXF + d][c];
+          q[d][c] = dv < 0.0 ? c2 * L->q[RHO][c] * dv * dv : 0.0;
+        }
+  }
+  /* heating, from the velocities before this stage */
+  for (int k = 0; k < L->s[2]; ++k)
+    for (int j = 0; j < L->s[1]; ++j)
+      for (int i = 0; i < L->s[0]; ++i) {
+        int c3[3] = {i, j, k};
+        size_t c = idx(L, i, j, k);
+        double h = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          if (c3[d] >= L->s[d] - 1) continue;
+          double dv = L->q[VXF + d][c + L->st[d]] - L->q[VXF + d][c];
+          h += q[d][c] * dv / L->dx[d];
+        }
+        L->q[ENE][c] = L->q[ENE][c] - dt * h;
+      }
+  for (int d = 0; d < 3; ++d) {
+    size_t st = L->st[d];
+    for (int k = 0; k < L->s[2]; ++k)
+      for (int j = 0; j < L->s[1]; ++j)
+        for (int i = 0; i < L->s[0]; ++i) {
+          int c3[3] = {i, j, k};
+          if (c3[d] < 1) continue;
+          size_t c = idx(L, i, j, k), m = c - st;
+          double rf = 0.5 * (L->q[RHO][m] + L->q[RHO][c]);
+          L->q[VXF + d][c] = L->q[VXF + d][c] - dt * (q[d][c] - q[d][m]) / (L->dx[d] * rf);
+        }
+  }
+  for (int d = 0; d < 3; ++d) free(q[d]);
+}
+
 /* SubStep3, reading R3 */
 static void compress_step(or_sim* S, olevel* L, double dt) {
   double gm1 = S->p.gamma - 1.0;
@@ -593,6 +649,7 @@ static void level_step(or_sim* S, int l, double dt) {
   if (l == 0) or_fill_bc(S);
   if (S->p.hydro_on) {
     source_step(S, L, 0.5 * dt);
+    if (S->p.av_c2 > 0.0) viscosity_step(S, L, dt);
     compress_step(S, L, dt);
   }
   if (S->p.L != 0.0) luminosity_step(S, L, dt);

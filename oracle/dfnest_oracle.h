@@ -40,6 +40,7 @@ typedef struct {
   int diff_face_rho;   /* 0: face density = mean of the two cells (Eq. 3); 1: rho0 (Eqs. 19-21) */
   int hydro_on;        /* 0 freezes rho and v (pure diffusion tests) */
   int band;            /* CommMean band width in coarse cells (Sec. 3.2.2) */
+  double av_c2;        /* SubStep2 artificial viscosity coefficient; 0 = off (reading R15) */
 } or_params;
 
 typedef struct or_sim or_sim;

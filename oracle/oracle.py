@@ -46,6 +46,7 @@ class OracleParams(C.Structure):
         ("diff_face_rho", C.c_int),
         ("hydro_on", C.c_int),
         ("band", C.c_int),
+        ("av_c2", C.c_double),
     ]
 
 

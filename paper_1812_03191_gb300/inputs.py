@@ -38,7 +38,7 @@ def base_params(**over) -> dict:
         GM=0.01, eps=0.5, chi=1.0, L=0.0, lum_sigma=0.0,
         cfl=0.44, cfl_diff=0.44, dt_fixed=0.0, xi_mode=0,
         bc=(BC_OUTFLOW, BC_INFLOW, BC_OUTFLOW, BC_OUTFLOW, BC_OUTFLOW, BC_OUTFLOW),
-        diff_face_rho=0, hydro_on=1, band=DEFAULT_BAND,
+        diff_face_rho=0, hydro_on=1, band=DEFAULT_BAND, av_c2=0.0,
     )
     p.update(over)
     return p

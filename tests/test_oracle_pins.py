@@ -37,11 +37,12 @@ def centres(o, level, n, lo, hi):
 
 # ---------------------------------------------------------------- T1
 
-@pytest.mark.parametrize("rho0", [1.0, 1.3])
-def test_uniform_flow_stays_uniform(rho0):
-    """No perturber: a uniform wind is a steady solution of Eqs. 1-3."""
+@pytest.mark.parametrize("rho0,av", [(1.0, 0.0), (1.3, 0.0), (1.0, 1.5)])
+def test_uniform_flow_stays_uniform(rho0, av):
+    """No perturber: a uniform wind is a steady solution of Eqs. 1-3 (and of the
+    artificial viscosity, which needs compression)."""
     o = make(3, 24, 6.0, GM=0.0, L=0.0, chi=1.0, rho0=rho0, mach=0.7,
-             flow_dir=(-0.6, 0.0, 0.8))
+             flow_dir=(-0.6, 0.0, 0.8), av_c2=av)
     init = [[o.get_field(l, f).copy() for f in range(5)] for l in range(3)]
     o.step(8)
     for l in range(3):
@@ -445,14 +446,23 @@ def test_xi_search_appendix_cases():
 
 # ---------------------------------------------------------------- T10
 
-def test_ghost_and_band_width_sufficient():
+@pytest.mark.parametrize("av", [0.0, 2.0])
+def test_ghost_and_band_width_sufficient(av):
     """Widening the ghost buffer (Sec. 3.2.1) or the CommMean band (Sec. 3.2.2) leaves
-    every active cell -- and the force -- bitwise unchanged."""
+    every active cell -- and the force -- bitwise unchanged, with and without the
+    artificial viscosity."""
     n, nl, half = 24, 3, 6.0
 
     def run(G, band):
-        o = make(nl, n, half, G=G, band=band, GM=0.01, eps=0.25, L=0.05, lum_sigma=0.25)
+        o = make(nl, n, half, G=G, band=band, GM=0.01, eps=0.25, L=0.05, lum_sigma=0.25,
+                 av_c2=av)
         _perturb(o, nl, n, seed=11)
+        if av:
+            for l in range(nl):  # strong enough to compress: the viscosity acts
+                v = o.get_field(l, VX)
+                o.set_field(l, VX, v - 0.4 * np.sin(2 * np.pi * np.arange(n) / n)[None, None, :])
+            for l in range(nl - 1):
+                o.commup(l)
         o.step(3)
         out = []
         for l in range(nl):
@@ -511,13 +521,15 @@ def test_gravity_kick_points_to_perturber():
 
 # ---------------------------------------------------------------- momentum
 
-def test_momentum_conserved_periodic():
-    """Without gravity, the pressure kick and the flux-form momentum transport keep
+@pytest.mark.parametrize("av", [0.0, 2.0])
+def test_momentum_conserved_periodic(av):
+    """Without gravity, the pressure kick, the artificial viscosity (a difference of
+    viscous pressures across each face) and the flux-form momentum transport keep
     sum_faces rho_face v (each component) constant in a periodic box."""
     n = 16
     o = make(1, n, 4.0, GM=0.0, L=0.0, chi=0.2, mach=0.6, flow_dir=(0.36, 0.48, 0.8),
-             bc=(I.BC_PERIODIC,) * 6)
-    _perturb(o, 1, n, seed=21, amp=3e-2)
+             bc=(I.BC_PERIODIC,) * 6, av_c2=av)
+    _perturb(o, 1, n, seed=21, amp=3e-2 if av == 0 else 0.3)
     G = I.DEFAULT_G
 
     def momentum():
