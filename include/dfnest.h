@@ -67,6 +67,9 @@ typedef struct {
   int diff_face_rho;  /* 0: face density = mean of the two cells (Eq. 3); 1: rho0 (Eqs. 19-21) */
   int hydro_on;       /* 0 freezes rho and v (pure diffusion) */
   int band;           /* CommMean band width in coarse cells (Sec. 3.2.2); default 5 */
+  double av_c2;       /* SubStep2 (Sec. 3.3): von Neumann-Richtmyer artificial viscosity
+                         coefficient in the ZEUS form (Stone & Norman 1992); 0 = off.
+                         With it on, every operator sweeps the whole padded array. */
 } df_params;
 
 typedef struct df_ctx df_ctx;
@@ -143,7 +146,7 @@ long long df_kernel_launches(const df_ctx* ctx);
  * then returns the summed device time (ms) and launch count of one kernel kind
  * since df_set_timing; df_kernel_name(kind) names the kinds 0..DF_KERNEL_KINDS-1.
  * df_set_timing resets the totals. */
-#define DF_KERNEL_KINDS 17
+#define DF_KERNEL_KINDS 18
 int df_set_timing(df_ctx* ctx, int on);
 int df_kernel_time(df_ctx* ctx, int kind, double* ms, long long* launches);
 const char* df_kernel_name(int kind);
@@ -264,7 +267,7 @@ int df_pool_info(df_pool* pool, int* active, size_t* used, size_t* budget, long 
  * SM and for each tile shape (as df_autotune), keeps the fastest per operator
  * (blocks per SM written to blocks_per_sm_out, nullable) and restores the runs'
  * state. */
-#define DF_POOL_OPS 20
+#define DF_POOL_OPS 22
 int df_pool_set_tiles(df_pool* pool, const int* blocks_per_sm);
 int df_pool_autotune(df_pool* pool, int* blocks_per_sm_out);
 /* As df_set_transport, for every run of the pool. */

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libdfnest.so")
 
 DF_OK, DF_EINVAL, DF_ENOMEM, DF_ECUDA, DF_EUNHEALTHY, DF_ETIMEOUT, DF_EBUSY = 0, -1, -2, -3, -4, -5, -6
 DF_FP64, DF_FP32_STATE = 0, 1
-KERNEL_KINDS = 17
+KERNEL_KINDS = 18
 
 # every symbol include/dfnest.h declares
 EXPORTS = (
@@ -32,11 +32,12 @@ EXPORTS = (
     "df_autotune", "df_set_tile_shapes", "df_pool_set_tile_shapes", "df_set_transport",
     "df_pool_set_transport", "df_pool_set_field",
 )
-POOL_OPS = 20
+POOL_OPS = 22
 # operator order of the per-op tables (tile shapes, blocks per SM)
 OP_NAMES = ("source", "compress", "frontier_diff", "diffuse", "tprep", "tflux", "tfrontier",
             "tmom", "tupdate", "vrec_source", "bc", "commup", "commmean", "zero_acc",
-            "dt_level", "dt_final", "force_level", "force_final", "time", "sweep")
+            "dt_level", "dt_final", "force_level", "force_final", "time", "sweep",
+            "visc_q", "visc_v")
 TRANSPORT_AUTO, TRANSPORT_SEPARATE, TRANSPORT_FUSED = 0, 1, 2
 NOALLOC_MAX_CELLS = 4194304
 
@@ -54,7 +55,7 @@ class Params(C.Structure):
         ("chi", C.c_double), ("L", C.c_double), ("lum_sigma", C.c_double),
         ("cfl", C.c_double), ("cfl_diff", C.c_double), ("dt_fixed", C.c_double),
         ("xi_mode", C.c_int), ("bc", C.c_int * 6), ("diff_face_rho", C.c_int),
-        ("hydro_on", C.c_int), ("band", C.c_int),
+        ("hydro_on", C.c_int), ("band", C.c_int), ("av_c2", C.c_double),
     ]
 
     @classmethod

@@ -298,6 +298,8 @@ int check_params(const df_params* p) {
       !(p->cfl > 0.0) || p->band < 1 || p->mach < 0.0)
     return fail(DF_EINVAL, "invalid physical parameters");
   if (p->chi > 0.0 && !(p->cfl_diff > 0.0)) return fail(DF_EINVAL, "cfl_diff must be > 0");
+  if (!(p->av_c2 >= 0.0) || !std::isfinite(p->av_c2))
+    return fail(DF_EINVAL, "av_c2 must be finite and >= 0");
   for (int k = 0; k < 6; ++k)
     if (p->bc[k] < 0 || p->bc[k] > 3) return fail(DF_EINVAL, "bad boundary type");
   return DF_OK;
@@ -322,6 +324,7 @@ long long run_set_params(Run* r, const df_params* p, cudaStream_t st, int* rc) {
   P.diff_face_rho = p->diff_face_rho;
   P.hydro_on = p->hydro_on;
   P.band = p->band;
+  P.av_c2 = p->av_c2;
   for (int k = 0; k < 6; ++k) P.bc[k] = p->bc[k];
   long long n = 0;
   for (int l = 0; l < r->nl; ++l) {
@@ -408,6 +411,7 @@ int kind_of(int op) {
     case OP_DT_LEVEL: case OP_DT_FINAL: return K_DT;
     case OP_FORCE_LEVEL: case OP_FORCE_FINAL: return K_FORCE;
     case OP_SWEEP: return K_SWEEP;
+    case OP_VISC_Q: case OP_VISC_V: return K_VISC;
     default: return K_OTHER;
   }
 }
@@ -471,6 +475,7 @@ struct Builder {
     it.gm1 = (T)(r.P.gamma - 1.0);
     it.lum = (T)r.P.L;
     it.chi = (T)r.P.chi;
+    it.av = (T)r.P.av_c2;
     it.gg = r.P.gamma * (r.P.gamma - 1.0);
     it.rho0d = r.P.rho0;
     it.e0d = r.P.e0;
@@ -500,11 +505,15 @@ struct Builder {
     return std::min(nm, std::max(zc, d == 0 ? 8 : 16));
   }
 
-  Box box(const LevelView& v, int margin) const {
+  // margin boxes (active cells +- margin) unless verifying with whole arrays or the
+  // artificial viscosity is on (its viscous pressures one cell below a box edge are
+  // not formed by a margin box, and the reach behind the margins was measured
+  // without it): then every operator sweeps the whole padded array
+  Box box(const LevelView& v, int margin, bool whole = false) const {
     Box b;
     b.tile = 0;
     b.zc = 0;
-    int M = full_boxes ? v.G : margin;
+    int M = (full_boxes || whole) ? v.G : margin;
     for (int d = 0; d < 3; ++d) {
       b.lo[d] = std::max(0, v.G - M);
       b.hi[d] = std::min(v.s[d], v.G + v.n[d] + M);
@@ -522,7 +531,7 @@ struct Builder {
 
   void level_step(const Run& r, int l, int m_out, std::vector<Entry>& out) const {
     Item<T> it = base(r, l);
-    it.b = box(it.L, m_out + kReach);
+    it.b = box(it.L, m_out + kReach, r.P.av_c2 > 0.0);
     const Phys& P = r.P;
     if (l == 0)
       for (int d = 0; d < 3; ++d) {
@@ -532,6 +541,10 @@ struct Builder {
         add(out, OP_BC, d, bc);
       }
     if (P.hydro_on) add(out, OP_SOURCE, 0, it);
+    if (P.hydro_on && P.av_c2 > 0.0) {
+      add(out, OP_VISC_Q, 0, it);
+      add(out, OP_VISC_V, 0, it);
+    }
     if (P.hydro_on || P.L != 0.0 || P.chi > 0.0) add(out, OP_COMPRESS, 0, it);
     if (P.chi > 0.0) {
       if (it.L.is_child) add(out, OP_FRONTIER_DIFF, 0, it);
@@ -1458,7 +1471,7 @@ const char* df_kernel_name(int kind) {
   static const char* names[K_NKINDS] = {
       "bc_fill",  "source",   "compress_lum", "diffuse",  "frontier_diff", "tprep",
       "tflux",    "tfrontier", "tmom",        "tupdate",  "vrec_source",   "commup",
-      "commmean", "dt",       "force",        "sweep",    "other"};
+      "commmean", "dt",       "force",        "sweep",    "viscosity",     "other"};
   return kind >= 0 && kind < K_NKINDS ? names[kind] : "";
 }
 

@@ -90,7 +90,7 @@ __host__ __device__ inline int sweep_units(const Box& b, int d) {
 }
 
 struct Phys {
-  double gamma, rho0, e0, V[3], GM, eps, chi, L, cfl, cfl_diff, dt_fixed;
+  double gamma, rho0, e0, V[3], GM, eps, chi, L, cfl, cfl_diff, dt_fixed, av_c2;
   int diff_face_rho, hydro_on, band;
   int bc[6];
 };
@@ -159,13 +159,15 @@ struct DtFinal {
 enum Op {
   OP_SOURCE = 0, OP_COMPRESS, OP_FRONTIER_DIFF, OP_DIFFUSE, OP_TPREP, OP_TFLUX, OP_TFRONTIER,
   OP_TMOM, OP_TUPDATE, OP_VREC, OP_BC, OP_COMMUP, OP_COMMMEAN, OP_ZERO_ACC, OP_DT_LEVEL,
-  OP_DT_FINAL, OP_FORCE_LEVEL, OP_FORCE_FINAL, OP_TIME, OP_SWEEP, OP_COUNT
+  OP_DT_FINAL, OP_FORCE_LEVEL, OP_FORCE_FINAL, OP_TIME, OP_SWEEP, OP_VISC_Q, OP_VISC_V,
+  OP_COUNT
 };
 
 // ops that enumerate the elements of a box (the ones a tile shape applies to)
 __host__ __device__ inline bool is_box_op(int op) {
   return op == OP_SOURCE || op == OP_COMPRESS || op == OP_DIFFUSE || op == OP_TPREP ||
-         op == OP_TFLUX || op == OP_TMOM || op == OP_TUPDATE || op == OP_VREC;
+         op == OP_TFLUX || op == OP_TMOM || op == OP_TUPDATE || op == OP_VREC ||
+         op == OP_VISC_Q || op == OP_VISC_V;
 }
 
 enum ItemFlags {
@@ -189,7 +191,7 @@ struct __align__(16) Item {
   double* partials;     // force partials (this level's first, or the run's for the final sum)
   double* ring;         // force history
   long long* ring_pos;
-  T gm1, lum, chi;
+  T gm1, lum, chi, av;
   double gg, rho0d, e0d, V[3], dt_fixed;
   int ring_cap, npart, level, band, flags, bc_lo, bc_hi;
   unsigned count;       // index-space size of the item
@@ -221,8 +223,8 @@ template <class T> int launch_unpack_active(const LevelView& L, int field, const
 // kernel kinds for the timing hook (df_kernel_time / df_kernel_name)
 enum KernelKind {
   K_BC = 0, K_SOURCE, K_COMPRESS, K_DIFFUSE, K_FRONTIER_DIFF, K_TPREP, K_TFLUX, K_TFRONTIER,
-  K_TMOM, K_TUPDATE, K_VREC_SOURCE, K_COMMUP, K_COMMMEAN, K_DT, K_FORCE, K_SWEEP, K_OTHER,
-  K_NKINDS
+  K_TMOM, K_TUPDATE, K_VREC_SOURCE, K_COMMUP, K_COMMMEAN, K_DT, K_FORCE, K_SWEEP, K_VISC,
+  K_OTHER, K_NKINDS
 };
 
 // hot-path FP64 division versus IEEE division (device arrays; max_ulp zeroed by caller)

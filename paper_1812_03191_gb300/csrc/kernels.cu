@@ -169,6 +169,62 @@ __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, cons
   }
 }
 
+// ------------------------------------------------------- SubStep2 viscosity
+// SubStep2 (Sec. 3.3 stage list, ZEUS naming): the von Neumann-Richtmyer artificial
+// viscosity of ZEUS (Stone & Norman 1992).  First pass: along each axis a compressed
+// cell (dv = v_d(upper face) - v_d(lower face) < 0) gets q_d = C2 rho dv^2, stored in
+// the momentum-flux scratch, and the cell's internal energy loses dt sum_d q_d dv/dx_d
+// (from the velocities after the first kick; dv is the same in deviations).
+template <class T>
+__device__ __forceinline__ void el_visc_q(const LevelView& L, const Box& b, const Scratch& S,
+                                          const T* __restrict__ dtp, T av, const Bg<T>& bg,
+                                          const Geo<T>& g, unsigned tid) {
+  int i, j, k;
+  if (!decode(b, tid, i, j, k)) return;
+  const int c = cidx(L, i, j, k);
+  const int c3[3] = {i, j, k};
+  const T rc = bg.rho0 + ((const T*)L.q[F_RHO])[c];
+  T heat = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T q = T(0);
+    if (c3[d] < L.s[d] - 1) {
+      const T* v = (const T*)L.q[F_VX + d];
+      const T dv = v[c + L.st[d]] - v[c];
+      if (dv < T(0)) q = av * rc * dv * dv;
+      heat += q * dv * g.inv_dx[d];
+    }
+    ((T*)S.P[d])[c] = q;
+  }
+  T* e = (T*)L.q[F_E];
+  e[c] = e[c] - dtp[0] * heat;
+}
+
+// Second pass: v_d -= dt (q_c - q_m) / (dx_d rho_face) on faces 1.. of each axis, and
+// the staggered momenta the transport starts from follow the new velocity.
+template <class T>
+__device__ __forceinline__ void el_visc_v(const LevelView& L, const Box& b, const Scratch& S,
+                                          const T* __restrict__ dtp, int write_pi,
+                                          const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
+  int i, j, k;
+  if (!decode(b, tid, i, j, k)) return;
+  const T* __restrict__ rho = (const T*)L.q[F_RHO];
+  const int c = cidx(L, i, j, k);
+  const int c3[3] = {i, j, k};
+  const T dt = dtp[0];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (c3[d] < 1) continue;
+    const int m = c - L.st[d];
+    const T* q = (const T*)S.P[d];
+    T* v = (T*)L.q[F_VX + d];
+    const T drf = T(0.5) * (rho[m] + rho[c]);
+    const T vn = v[c] - dt * hdiv(q[c] - q[m], bg.rho0 + drf) * g.inv_dx[d];
+    v[c] = vn;
+    if (write_pi) ((T*)S.pi[d])[c] = bg.rho0 * vn + drf * (bg.V[d] + vn);
+  }
+}
+
 // ------------------------------------------------- SubStep3 + luminosity + e/rho
 template <class T>
 __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b, const Scratch& S,
@@ -1515,6 +1571,10 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
     el_tmom<T, D>(it.L, it.b, it.S, (const T*)it.dt, it.bg, it.g, tid);
   else if (OP == OP_TUPDATE)
     el_tupdate<T, D>(it.L, it.b, it.S, it.g, tid);
+  else if (OP == OP_VISC_Q)
+    el_visc_q<T>(it.L, it.b, it.S, (const T*)it.dt, it.av, it.bg, it.g, tid);
+  else if (OP == OP_VISC_V)
+    el_visc_v<T>(it.L, it.b, it.S, (const T*)it.dt, it.flags & FL_WRITE_PI, it.bg, it.g, tid);
   else if (OP == OP_VREC)
     el_vrec_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.bg, it.g,
                       it.flags & FL_FUSED, tid);
@@ -1687,6 +1747,8 @@ int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, in
     DFN_OP(OP_FORCE_LEVEL)
     DFN_OP(OP_FORCE_FINAL)
     DFN_OP(OP_TIME)
+    DFN_OP(OP_VISC_Q)
+    DFN_OP(OP_VISC_V)
     case OP_SWEEP:
       if (d == 0) launch_sweep<T, 0>(items, starts, nitems, nchunks, grid, st, host_item);
       if (d == 1) launch_sweep<T, 1>(items, starts, nitems, nchunks, grid, st, host_item);
@@ -1717,7 +1779,7 @@ unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const B
   };
   switch (op) {
     case OP_SOURCE: case OP_COMPRESS: case OP_DIFFUSE: case OP_TPREP: case OP_TFLUX:
-    case OP_TMOM: case OP_TUPDATE: case OP_VREC:  // is_box_op
+    case OP_TMOM: case OP_TUPDATE: case OP_VREC: case OP_VISC_Q: case OP_VISC_V:  // is_box_op
       if (b.tile == 0) {
         n = b.count();
       } else {

@@ -233,6 +233,40 @@ def test_fused_and_separate_transport_agree_fp32():
     assert np.abs(Fa - Fb).max() <= 1e-4 * np.abs(Fb).max()
 
 
+@pytest.mark.parametrize("transport", TRANSPORTS, ids=TRANSPORT_IDS)
+def test_artificial_viscosity_parity(transport):
+    """SubStep2 on: 3 nested levels with a strong compressive perturbation, the
+    viscosity acting on every level; 10 coarse steps against the oracle."""
+    p = I.base_params(GM=0.02, eps=0.3, chi=0.3, L=0.03, lum_sigma=0.3, mach=1.1, av_c2=2.0,
+                      flow_dir=(0.0, 0.6, -0.8), bc=I.wind_bcs((0.0, 0.6, -0.8)))
+    sim, orc = pair(3, 24, 6.0, p, transport=transport)
+    perturb_both(sim, orc, seed=31, amp=0.15)
+    sim.step(10)
+    orc.step(10)
+    assert_parity(sim, orc, p)
+
+
+@pytest.mark.parametrize("precision", [binding.DF_FP64, binding.DF_FP32_STATE])
+def test_sod_shock_tube_on_the_gpu(precision):
+    """Sod's shock tube (t = 0.2, 200 cells, C2 = 2): FP64 equals the oracle to 1e-10;
+    both precisions are within the oracle's L1 errors of the exact solution."""
+    from test_oracle_sod import run_sod, sod_errors, sod_setup
+    p, shape, lo, hi, fields, xc = sod_setup(2.0)
+    sim = binding.Sim(1, shape, lo, hi, I.DEFAULT_G, p, precision=precision)
+    for f in range(5):
+        sim.set_field(0, f, fields[f])
+    sim.step(250)
+    t, _, bad = sim.status()
+    assert bad == 0 and t == pytest.approx(0.2, rel=1e-12)
+    er, ep, eu = sod_errors(lambda f: sim.get_field(0, f), t, xc)
+    assert er < 0.005 and ep < 0.004 and eu < 0.009, (er, ep, eu)
+    if precision == binding.DF_FP64:
+        orc, _ = run_sod(2.0)
+        for f in range(5):
+            a, b = sim.get_field(0, f), orc.get_field(0, f)
+            assert np.abs(a - b).max() <= TOL, (f, np.abs(a - b).max())
+
+
 def test_inter_level_operators():
     p = I.base_params()
     sim, orc = pair(2, 24, 6.0, p)
