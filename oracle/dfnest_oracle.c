@@ -35,9 +35,12 @@
  *      at least twice the reach of one level step for the active cells to be exact.
  *  R7  CommUp: z, then y, then x 3-point van Leer-limited interpolation from the 27
  *      coarse elements around the host element; centred fields at fine offsets
- *      -1/4, +1/4 of a coarse cell, staggered fields at 0 or +1/2 along their own
- *      axis.  Every fine element outside the active set is filled (for v_d the
- *      upper frontier face counts as a ghost).
+ *      -1/4, +1/4 of a coarse cell.  A staggered field along its own axis has fine
+ *      faces on a coarse face (copied) or midway between two (the mean of the two:
+ *      a position equidistant from two coarse faces favours neither, so a
+ *      mirror-symmetric state stays symmetric; the mean is exact for linear data and
+ *      bounded by its neighbours).  Every fine element outside the active set is
+ *      filled (for v_d the upper frontier face counts as a ghost).
  *  R8  CommMean: coarse cells within `band` layers of the contour of the covered
  *      box take the mean of their 8 fine cells; a staggered coarse face strictly
  *      inside the covered box takes the mean of its 4 coplanar fine faces when
@@ -63,6 +66,22 @@
  * R15  SubStep2 (named in Sec. 3.3 after ZEUS) is the von Neumann-Richtmyer
  *      artificial viscosity of ZEUS (Stone & Norman 1992), applied after the first
  *      kick when av_c2 > 0 (off by default: the paper's flows are nearly linear).
+ * R16  Mirror planes (the quadrant domain of Sec. 3.4): an axis whose lower domain
+ *      face lies at coordinate 0 with a reflect boundary is a symmetry plane through
+ *      the perturber, and the run stands for the domain unfolded across it.  Every
+ *      level then starts on the plane (child offset 0 along that axis); a finer
+ *      level's step starts with the reflect fill of its mirror sides, and CommUp
+ *      first refreshes the parent's mirror ghosts from the parent's current state;
+ *      a mirror face is no coarse/fine frontier and does not bound CommMean's band,
+ *      and a coarse frontier face in the ghost layer across a mirror takes the fine
+ *      flux sum of its image;
+ *      the luminosity weights of R10 also cover the mirror images of active cells in
+ *      the ghost layers (part of the unfolded domain; a vertex on the plane has four
+ *      of its eight cells there), and Gaussian weights are normalised over the
+ *      unfolded domain, 2^(mirror axes) times the active cells; the force (R12) is
+ *      the unfolded one:
+ *      its components along mirror axes vanish, the others are 2^(mirror axes)
+ *      times the sum over the simulated part.
  */
 #include "dfnest_oracle.h"
 
@@ -77,6 +96,7 @@ typedef struct {
   size_t nc, st[3];
   double dx[3], lo[3], vol, area[3];
   int off[3]; /* lower corner of the active box in the parent's active indices */
+  int mir[3]; /* mirror axes of the run (R16) */
   double* q[5];
   double* phi;
   double* lumw; /* w_c / V_c on active cells */
@@ -92,6 +112,8 @@ struct or_sim {
   or_params p;
   double t, dt_last, e0, V[3];
   int xi[OR_MAX_LEVELS];
+  int mir[3];  /* mirror axes (R16) */
+  double mult; /* copies of the simulated part in the unfolded domain */
 };
 
 static size_t idx(const olevel* L, int i, int j, int k) {
@@ -136,11 +158,15 @@ static void level_free(olevel* L) {
   free(L->E);
 }
 
+/* element kept by CommUp (R7): centred fields on the active cells; v_d on the faces
+ * strictly between two active cells along d, so both frontier faces come from the
+ * parent */
 static int is_active_elem(const olevel* L, int field, int i, int j, int k) {
   int c[3] = {i, j, k};
-  (void)field;
-  for (int d = 0; d < 3; ++d)
-    if (c[d] < L->G || c[d] >= L->G + L->n[d]) return 0;
+  for (int d = 0; d < 3; ++d) {
+    int lo = field == VXF + d ? L->G + 1 : L->G;
+    if (c[d] < lo || c[d] >= L->G + L->n[d]) return 0;
+  }
   return 1;
 }
 
@@ -158,12 +184,18 @@ or_sim* or_create(int n_levels, const int n[3], const double lo[3], const double
   S->e0 = p->cs * p->cs * p->rho0 / (g * (g - 1.0)); /* Sec. 3.4 */
   for (int d = 0; d < 3; ++d) S->V[d] = p->mach * p->cs * p->flow_dir[d];
   for (int l = 0; l < n_levels; ++l) S->xi[l] = 2;
+  S->mult = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    S->mir[d] = lo[d] == 0.0 && p->bc[2 * d] == OR_BC_REFLECT;
+    if (S->mir[d]) S->mult *= 2.0;
+  }
   for (int l = 0; l < n_levels; ++l) {
     olevel* L = &S->L[l];
     double scale = ldexp(1.0, -l);
     L->G = G;
     L->nc = 1;
     for (int d = 0; d < 3; ++d) {
+      L->mir[d] = S->mir[d];
       L->n[d] = n[d];
       L->s[d] = n[d] + 2 * G;
       L->lo[d] = lo[d] * scale;
@@ -183,8 +215,9 @@ or_sim* or_create(int n_levels, const int n[3], const double lo[3], const double
         double o = (L->lo[d] - Pp->lo[d]) / Pp->dx[d];
         int oi = (int)floor(o + 0.5);
         /* child must sit on parent faces, with its ghosts and the CommUp stencil
-         * inside the parent's active region */
-        if (fabs(o - oi) > 1e-9 || oi < G / 2 + 1 || oi + n[d] / 2 + G / 2 + 1 > Pp->n[d]) {
+         * inside the parent's active region, or start on a mirror plane (R16) */
+        int lo_ok = S->mir[d] ? oi == 0 : oi >= G / 2 + 1;
+        if (fabs(o - oi) > 1e-9 || !lo_ok || oi + n[d] / 2 + G / 2 + 1 > Pp->n[d]) {
           for (int m = 0; m <= l; ++m) level_free(&S->L[m]);
           free(S);
           return NULL;
@@ -226,30 +259,34 @@ or_sim* or_create(int n_levels, const int n[3], const double lo[3], const double
           double z = L->lo[2] + (k - G + 0.5) * L->dx[2];
           L->phi[c] = -p->GM / sqrt(x * x + y * y + z * z + p->eps * p->eps);
         }
-    /* luminosity weights (reading R10) */
+    /* luminosity weights (reading R10) on the active cells and on their mirror
+     * images in the ghost layers, which belong to the unfolded domain (R16) */
+    int w0[3];
+    for (int d = 0; d < 3; ++d) w0[d] = S->mir[d] ? 0 : G;
     if (p->lum_sigma > 0.0) {
       double sum = 0.0;
-      for (int k = G; k < G + n[2]; ++k)
-        for (int j = G; j < G + n[1]; ++j)
-          for (int i = G; i < G + n[0]; ++i) {
+      for (int k = w0[2]; k < G + n[2]; ++k)
+        for (int j = w0[1]; j < G + n[1]; ++j)
+          for (int i = w0[0]; i < G + n[0]; ++i) {
             double x = L->lo[0] + (i - G + 0.5) * L->dx[0];
             double y = L->lo[1] + (j - G + 0.5) * L->dx[1];
             double z = L->lo[2] + (k - G + 0.5) * L->dx[2];
             double wgt = exp(-(x * x + y * y + z * z) / (2.0 * p->lum_sigma * p->lum_sigma));
             L->lumw[idx(L, i, j, k)] = wgt;
-            sum += wgt;
+            if (i >= G && j >= G && k >= G) sum += wgt;
           }
-      for (int k = G; k < G + n[2]; ++k)
-        for (int j = G; j < G + n[1]; ++j)
-          for (int i = G; i < G + n[0]; ++i) L->lumw[idx(L, i, j, k)] /= sum * L->vol;
+      /* the unfolded domain holds mult copies of every simulated cell (R16) */
+      for (int k = w0[2]; k < G + n[2]; ++k)
+        for (int j = w0[1]; j < G + n[1]; ++j)
+          for (int i = w0[0]; i < G + n[0]; ++i) L->lumw[idx(L, i, j, k)] /= S->mult * sum * L->vol;
     } else {
       int v[3], ok = 1;
       for (int d = 0; d < 3; ++d) {
         double o = -L->lo[d] / L->dx[d];
         v[d] = (int)floor(o + 0.5);
-        if (fabs(o - v[d]) > 1e-9 || v[d] < 1 || v[d] > n[d] - 1) ok = 0;
+        if (fabs(o - v[d]) > 1e-9 || v[d] < (S->mir[d] ? 0 : 1) || v[d] > n[d] - 1) ok = 0;
       }
-      if (ok)
+      if (ok) /* a vertex on a mirror plane has four of its cells in the ghost layer */
         for (int c = 0; c < 8; ++c) {
           int i = G + v[0] - 1 + (c & 1), j = G + v[1] - 1 + ((c >> 1) & 1),
               k = G + v[2] - 1 + ((c >> 2) & 1);
@@ -431,10 +468,11 @@ static void compress_step(or_sim* S, olevel* L, double dt) {
 
 /* Luminosity deposit, reading R10 */
 static void luminosity_step(or_sim* S, olevel* L, double dt) {
-  int G = L->G;
-  for (int k = G; k < G + L->n[2]; ++k)
-    for (int j = G; j < G + L->n[1]; ++j)
-      for (int i = G; i < G + L->n[0]; ++i) {
+  int G = L->G, w0[3];
+  for (int d = 0; d < 3; ++d) w0[d] = S->mir[d] ? 0 : G; /* mirror images too (R16) */
+  for (int k = w0[2]; k < G + L->n[2]; ++k)
+    for (int j = w0[1]; j < G + L->n[1]; ++j)
+      for (int i = w0[0]; i < G + L->n[0]; ++i) {
         size_t c = idx(L, i, j, k);
         L->q[ENE][c] = L->q[ENE][c] + S->p.L * dt * L->lumw[c];
       }
@@ -450,7 +488,7 @@ static size_t acc_index_fine(const olevel* C, int d, const int c3[3]) {
 static int fine_frontier_side(const olevel* C, int d, const int c3[3]) {
   int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2, G = C->G;
   if (c3[t1] < G || c3[t1] >= G + C->n[t1] || c3[t2] < G || c3[t2] >= G + C->n[t2]) return -1;
-  if (c3[d] == G) return 0;
+  if (c3[d] == G && !C->mir[d]) return 0; /* a mirror face is no frontier (R16) */
   if (c3[d] == G + C->n[d]) return 1;
   return -1;
 }
@@ -460,9 +498,12 @@ static int coarse_frontier_side(const olevel* L, const olevel* C, int d, const i
                                 size_t* slot) {
   int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2, G = L->G;
   int a = c3[t1] - G - C->off[t1], b = c3[t2] - G - C->off[t2];
+  /* a ghost face across a mirror plane takes the slot of its image (R16) */
+  if (a < 0 && C->mir[t1]) a = -1 - a;
+  if (b < 0 && C->mir[t2]) b = -1 - b;
   if (a < 0 || a >= C->n[t1] / 2 || b < 0 || b >= C->n[t2] / 2) return -1;
   int side = -1;
-  if (c3[d] == G + C->off[d]) side = 0;
+  if (c3[d] == G + C->off[d] && !C->mir[d]) side = 0;
   if (c3[d] == G + C->off[d] + C->n[d] / 2) side = 1;
   if (side >= 0) *slot = (size_t)b * (C->n[t1] / 2) + a;
   return side;
@@ -647,6 +688,8 @@ static void level_step(or_sim* S, int l, double dt) {
   olevel* child = l + 1 < S->nl ? &S->L[l + 1] : NULL;
   int is_child = l > 0;
   if (l == 0) or_fill_bc(S);
+  for (int d = 0; d < 3 && l > 0; ++d)
+    if (S->mir[d]) bc_axis(S, L, d, 0, OR_BC_REFLECT); /* R16 */
   if (S->p.hydro_on) {
     source_step(S, L, 0.5 * dt);
     if (S->p.av_c2 > 0.0) viscosity_step(S, L, dt);
@@ -666,6 +709,14 @@ static double interp3(double qm, double q0, double qp, double delta) {
   return q0 + delta * vanleer(q0 - qm, qp - q0);
 }
 
+/* one pass of R7 along an axis: centred positions at -1/4 (even) or +1/4 (odd) of
+ * the host; along a staggered field's own axis the host face (even) or the mean of
+ * the host face and the next one (odd) */
+static double interp_pass(double qm, double q0, double qp, int own, int odd) {
+  if (own) return odd ? 0.5 * (q0 + qp) : q0;
+  return interp3(qm, q0, qp, odd ? 0.25 : -0.25);
+}
+
 /* floor division by 2 for possibly negative integers */
 static int fdiv2(int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
 
@@ -673,22 +724,20 @@ void or_commup(or_sim* S, int cl) {
   olevel* Cc = &S->L[cl];
   olevel* F = &S->L[cl + 1];
   int Gf = F->G, Gc = Cc->G;
+  /* the stencil may reach across a mirror plane into the parent's ghosts (R16) */
+  for (int d = 0; d < 3; ++d)
+    if (S->mir[d]) bc_axis(S, Cc, d, 0, OR_BC_REFLECT);
   for (int f = 0; f < 5; ++f) {
     int sa = f >= VXF ? f - VXF : -1;
     for (int k = 0; k < F->s[2]; ++k)
       for (int j = 0; j < F->s[1]; ++j)
         for (int i = 0; i < F->s[0]; ++i) {
           if (is_active_elem(F, f, i, j, k)) continue;
-          int c3[3] = {i, j, k}, host[3];
-          double delta[3];
+          int c3[3] = {i, j, k}, host[3], odd[3];
           for (int a = 0; a < 3; ++a) {
             int rel = c3[a] - Gf;
-            int odd = rel - 2 * fdiv2(rel);
+            odd[a] = rel - 2 * fdiv2(rel);
             host[a] = Gc + F->off[a] + fdiv2(rel);
-            if (a == sa)
-              delta[a] = odd ? 0.5 : 0.0;
-            else
-              delta[a] = odd ? 0.25 : -0.25;
           }
           /* z pass: 27 -> 9, then y: 9 -> 3, then x: 3 -> 1 (Sec. 3.2.1, Fig. 2) */
           double v9[3][3], v3[3];
@@ -697,11 +746,11 @@ void or_commup(or_sim* S, int cl) {
               double q[3];
               for (int dz = -1; dz <= 1; ++dz)
                 q[dz + 1] = Cc->q[f][idx(Cc, host[0] + dx, host[1] + dy, host[2] + dz)];
-              v9[dy + 1][dx + 1] = interp3(q[0], q[1], q[2], delta[2]);
+              v9[dy + 1][dx + 1] = interp_pass(q[0], q[1], q[2], sa == 2, odd[2]);
             }
           for (int dx = -1; dx <= 1; ++dx)
-            v3[dx + 1] = interp3(v9[0][dx + 1], v9[1][dx + 1], v9[2][dx + 1], delta[1]);
-          F->q[f][idx(F, i, j, k)] = interp3(v3[0], v3[1], v3[2], delta[0]);
+            v3[dx + 1] = interp_pass(v9[0][dx + 1], v9[1][dx + 1], v9[2][dx + 1], sa == 1, odd[1]);
+          F->q[f][idx(F, i, j, k)] = interp_pass(v3[0], v3[1], v3[2], sa == 0, odd[0]);
         }
   }
 }
@@ -713,6 +762,7 @@ static int in_band(const olevel* F, int band, const int a3[3]) {
   for (int d = 0; d < 3; ++d) {
     int lo = a3[d] - F->off[d], hi = F->off[d] + F->n[d] / 2 - 1 - a3[d];
     if (lo < 0 || hi < 0) return 0;
+    if (F->mir[d]) lo = 1 << 30; /* a mirror face bounds no band (R16) */
     if (lo < dist) dist = lo;
     if (hi < dist) dist = hi;
   }
@@ -900,6 +950,8 @@ void or_force(const or_sim* S, double F[3]) {
           F[2] += p->GM * m * z * inv3;
         }
   }
+  /* the force of the unfolded domain (R16) */
+  for (int d = 0; d < 3; ++d) F[d] = S->mir[d] ? 0.0 : S->mult * F[d];
 }
 
 /* ------------------------------------------------------------- field I/O */

@@ -973,7 +973,10 @@ __device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_l
 // one coarse element share their van Leer slopes: the z pass gives 9 slopes (one
 // per (y,x) column) for both fine z offsets, the y pass 3 per z offset, the x pass
 // 1 per (z,y) offset -- the same arithmetic per fine element as interpolating each
-// one alone, with the slopes computed once.
+// one alone, with the slopes computed once.  Along a staggered field's own axis the
+// fine faces lie on the host face (copied) or midway to the next one (mean of the
+// two, which favours neither side), and both frontier faces of v_d are filled, so a
+// mirror-symmetric coarse state gives mirror-symmetric fine ghosts.
 template <class T>
 __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F, unsigned tid) {
   const int G = F.G, hg = G >> 1;
@@ -986,18 +989,16 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
   const int h0 = r % nh0 - hg, h1 = (r / nh0) % nh1 - hg, h2 = r / (nh0 * nh1) - hg;
   // hosted fine elements: rel = 2h + {0,1} on each axis; skip if all are active
   const int hh[3] = {h0, h1, h2};
+  const int sa = f >= F_VX ? f - F_VX : -1;
+  // kept fine elements: active cells; for v_d the faces strictly inside along d
   bool all_active = true;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) all_active = all_active && hh[a] >= 0 && 2 * hh[a] + 1 < F.n[a];
+  for (int a = 0; a < 3; ++a)
+    all_active = all_active && hh[a] >= (a == sa ? 1 : 0) && 2 * hh[a] + 1 < F.n[a];
   if (all_active) return;
-  const int sa = f >= F_VX ? f - F_VX : -1;
-  // offsets of the two fine positions in coarse cells, doubled for the half slope
-  T dl[3], dh[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    dl[a] = a == sa ? T(0) : T(-0.5);
-    dh[a] = a == sa ? T(1) : T(0.5);
-  }
+  // offsets of the two centred fine positions in coarse cells, doubled for the half
+  // slope
+  const T dl = T(-0.5), dh = T(0.5);
   const T* q = (const T*)C.q[f];
   const int base = ((C.G + F.off[2] + h2) * C.s[1] + C.G + F.off[1] + h1) * C.s[0] + C.G +
                    F.off[0] + h0;
@@ -1009,9 +1010,14 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
     for (int dx = 0; dx < 3; ++dx) {
       int b = base + (dy - 1) * C.st[1] + (dx - 1);
       T qm = q[b - C.st[2]], q0 = q[b], qp = q[b + C.st[2]];
-      T s = hslope(q0 - qm, qp - q0);
-      vz[0][dy][dx] = q0 + dl[2] * s;
-      vz[1][dy][dx] = q0 + dh[2] * s;
+      if (sa == 2) {
+        vz[0][dy][dx] = q0;
+        vz[1][dy][dx] = T(0.5) * (q0 + qp);
+      } else {
+        T s = hslope(q0 - qm, qp - q0);
+        vz[0][dy][dx] = q0 + dl * s;
+        vz[1][dy][dx] = q0 + dh * s;
+      }
     }
   // y pass
   T vy[2][2][3];
@@ -1020,9 +1026,14 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
 #pragma unroll
     for (int dx = 0; dx < 3; ++dx) {
       T qm = vz[iz][0][dx], q0 = vz[iz][1][dx], qp = vz[iz][2][dx];
-      T s = hslope(q0 - qm, qp - q0);
-      vy[iz][0][dx] = q0 + dl[1] * s;
-      vy[iz][1][dx] = q0 + dh[1] * s;
+      if (sa == 1) {
+        vy[iz][0][dx] = q0;
+        vy[iz][1][dx] = T(0.5) * (q0 + qp);
+      } else {
+        T s = hslope(q0 - qm, qp - q0);
+        vy[iz][0][dx] = q0 + dl * s;
+        vy[iz][1][dx] = q0 + dh * s;
+      }
     }
   // x pass and stores
   T* out = (T*)F.q[f];
@@ -1031,15 +1042,23 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
 #pragma unroll
     for (int iy = 0; iy < 2; ++iy) {
       T qm = vy[iz][iy][0], q0 = vy[iz][iy][1], qp = vy[iz][iy][2];
-      T s = hslope(q0 - qm, qp - q0);
+      T v[2];
+      if (sa == 0) {
+        v[0] = q0;
+        v[1] = T(0.5) * (q0 + qp);
+      } else {
+        T s = hslope(q0 - qm, qp - q0);
+        v[0] = q0 + dl * s;
+        v[1] = q0 + dh * s;
+      }
 #pragma unroll
       for (int ix = 0; ix < 2; ++ix) {
         int fi = G + 2 * h0 + ix, fj = G + 2 * h1 + iy, fk = G + 2 * h2 + iz;
-        bool act = fi >= G && fi < G + F.n[0] && fj >= G && fj < G + F.n[1] && fk >= G &&
-                   fk < G + F.n[2];
+        bool act = fi >= G + (sa == 0) && fi < G + F.n[0] && fj >= G + (sa == 1) &&
+                   fj < G + F.n[1] && fk >= G + (sa == 2) && fk < G + F.n[2];
         bool inside = fi >= 0 && fi < F.s[0] && fj >= 0 && fj < F.s[1] && fk >= 0 &&
                       fk < F.s[2];
-        if (!act && inside) out[(fk * F.s[1] + fj) * F.s[0] + fi] = q0 + (ix ? dh[0] : dl[0]) * s;
+        if (!act && inside) out[(fk * F.s[1] + fj) * F.s[0] + fi] = v[ix];
       }
     }
 }

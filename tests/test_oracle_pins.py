@@ -358,9 +358,45 @@ def test_commup_reproduces_linear_fields():
         got = o.get_full(1, f)
         want = coef[0] + 0.1 * f + coef[1] * x + coef[2] * y + coef[3] * z
         ghost = np.ones(got.shape, dtype=bool)
-        ghost[G:G + n, G:G + n, G:G + n] = False
+        lo = [G, G, G]
+        if f >= VX:  # both frontier faces of v_d come from the parent
+            lo[2 - (f - VX)] = G + 1
+        ghost[lo[0]:G + n, lo[1]:G + n, lo[2]:G + n] = False
         assert np.abs(got[ghost] - want[ghost]).max() < 1e-13, f
         assert np.isnan(got[~ghost]).all()  # active elements untouched
+
+
+def test_commup_keeps_a_mirror_symmetric_state_symmetric():
+    """CommUp of a state that is even in x (v_x odd) about the centre of the box
+    gives fine ghosts with the same symmetry: the midway faces of v_x take the mean
+    of their two coarse faces, and the two x frontier faces of v_x both come from
+    the parent.  A one-sided reconstruction at the midway faces, or a lower
+    frontier face left to the fine level, breaks it."""
+    n, nl, half, G = 24, 2, 6.0, I.DEFAULT_G
+    o = make(nl, n, half)
+    rng = np.random.default_rng(11)
+    s = n + 2 * G
+    for f in range(5):
+        r = rng.uniform(0.5, 1.5, (s, s, s))
+        if f == VX:  # face I mirrors face s - I; face s/2 lies on the plane x = 0
+            q = r.copy()
+            q[:, :, 1:] = r[:, :, 1:] - r[:, :, :0:-1]
+        else:  # cell I mirrors cell s - 1 - I
+            q = 0.5 * (r + r[:, :, ::-1])
+        o.set_full(0, f, q)
+        o.set_full(1, f, rng.uniform(0.5, 1.5, (s, s, s)))
+    o.commup(0)
+    for f in range(5):
+        a = o.get_full(1, f)
+        kept = np.zeros(a.shape, dtype=bool)
+        kept[G:G + n, G:G + n, (G + 1 if f == VX else G):G + n] = True
+        if f == VX:
+            filled = ~kept[:, :, 1:] & ~kept[:, :, :0:-1]
+            d = np.abs(a[:, :, 1:] + a[:, :, :0:-1])[filled]
+        else:
+            filled = ~kept & ~kept[:, :, ::-1]
+            d = np.abs(a - a[:, :, ::-1])[filled]
+        assert d.size > 0 and d.max() == 0.0, (f, d.max())
 
 
 def test_commup_is_bounded_by_neighbours():
