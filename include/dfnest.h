@@ -43,6 +43,12 @@ extern "C" {
 #define DF_BC_OUTFLOW 1 /* zero gradient: copy of the nearest active element */
 #define DF_BC_INFLOW 2  /* background rho0, e0, V in every ghost element (injection) */
 #define DF_BC_REFLECT 3 /* mirror, normal velocity odd (Sec. 3.4 symmetric/antisymmetric) */
+/* A reflecting LOWER face at coordinate 0 (lo[d] == 0) is a mirror plane through the
+ * perturber: the quadrant domain of Sec. 3.4.  The run then stands for the domain
+ * unfolded across the plane.  Every level starts on the plane and takes the reflect
+ * fill there.  The luminosity goes to the unfolded domain's cells.  The force is the
+ * unfolded one: zero along a mirror axis, 2^planes times the simulated part's sum for
+ * the other components. */
 
 /* state precision */
 #define DF_FP64 0       /* FP64 state and arithmetic */
@@ -77,7 +83,9 @@ typedef struct df_ctx df_ctx;
 /* Create a hierarchy (Sec. 3, Sec. 3.4).  n[d] % 4 == 0, n[d] >= 8, n[d] >= G; G even
  * and >= 2 (G >= 8 makes the active cells independent of the ghost width); every finer level
  * must sit on parent faces with its ghosts and the 27-point CommUp stencil inside
- * the parent's active cells (offset >= G/2+1 parent cells on each side).
+ * the parent's active cells (offset >= G/2+1 parent cells on each side), except on an
+ * axis with lo[d] == 0, where every level starts on that face (offset 0, so n[d] >= G+2)
+ * and df_set_params then requires bc[2d] == DF_BC_REFLECT (a mirror plane).
  * precision: DF_FP64 or DF_FP32_STATE.  device: CUDA ordinal (made current).
  * stream: cudaStream_t or NULL.  The state is uninitialised until df_set_params.
  * Errors: DF_EINVAL (geometry), DF_ENOMEM, DF_ECUDA. */
@@ -86,7 +94,8 @@ int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], co
 
 /* Copy the parameters, precompute the static potential (Eq. 16) and luminosity
  * weights, and set every level to the uniform background (Sec. 3.4): rho0, e0, V.
- * Resets t to 0 and clears the force history.  DF_EINVAL on bad values. */
+ * Resets t to 0 and clears the force history.  DF_EINVAL on bad values, and when
+ * finer levels start on a lower face at coordinate 0 that does not reflect. */
 int df_set_params(df_ctx* ctx, const df_params* p);
 
 /* Advance n coarse steps: per step the time step of Eq. 55 (reductions on the

@@ -155,17 +155,39 @@ int check_shape(int n_levels, const int n[3], const double lo[3], const double h
   long long s3 = 1;
   for (int d = 0; d < 3; ++d) s3 *= (n[d] + 2 * G);
   if (s3 >= (1LL << 31) / 5) return fail(DF_EINVAL, "level too large (%lld elements)", s3);
-  // every finer level on parent faces, ghosts and CommUp stencil inside the parent
+  // every finer level on parent faces, ghosts and CommUp stencil inside the parent;
+  // a lower domain face at coordinate 0 keeps every level on it (offset 0), which
+  // df_set_params accepts only when that face is a mirror plane
   for (int l = 1; l < n_levels; ++l)
     for (int d = 0; d < 3; ++d) {
       double ps = std::ldexp(1.0, -(l - 1)), cs = std::ldexp(1.0, -l);
       double plo = lo[d] * ps, pdx = (hi[d] - lo[d]) * ps / n[d];
       double o = (lo[d] * cs - plo) / pdx;
       int oi = (int)std::floor(o + 0.5);
-      if (std::fabs(o - oi) > 1e-9 || oi < G / 2 + 1 || oi + n[d] / 2 + G / 2 + 1 > n[d])
+      bool lo_ok = lo[d] == 0.0 ? oi == 0 : oi >= G / 2 + 1;
+      if (std::fabs(o - oi) > 1e-9 || !lo_ok || oi + n[d] / 2 + G / 2 + 1 > n[d])
         return fail(DF_EINVAL, "level %d: offset %.3f on axis %d must be an integer in [%d, %d]",
-                    l, o, d, G / 2 + 1, n[d] - n[d] / 2 - G / 2 - 1);
+                    l, o, d, lo[d] == 0.0 ? 0 : G / 2 + 1, n[d] - n[d] / 2 - G / 2 - 1);
     }
+  return DF_OK;
+}
+
+// mirror planes: bit d set when the lower d-face lies at coordinate 0 and reflects
+int mirror_mask(const double lo[3], const df_params* p) {
+  int m = 0;
+  for (int d = 0; d < 3; ++d)
+    if (lo[d] == 0.0 && p->bc[2 * d] == DF_BC_REFLECT) m |= 1 << d;
+  return m;
+}
+
+// finer levels may only sit on the domain's lower face across a mirror plane
+int check_mirror(int n_levels, const double lo[3], const df_params* p) {
+  if (n_levels < 2) return DF_OK;
+  int m = mirror_mask(lo, p);
+  for (int d = 0; d < 3; ++d)
+    if (lo[d] == 0.0 && !(m >> d & 1))
+      return fail(DF_EINVAL,
+                  "axis %d: finer levels start on the lower face, which must then reflect", d);
   return DF_OK;
 }
 
@@ -326,17 +348,22 @@ long long run_set_params(Run* r, const df_params* p, cudaStream_t st, int* rc) {
   P.band = p->band;
   P.av_c2 = p->av_c2;
   for (int k = 0; k < 6; ++k) P.bc[k] = p->bc[k];
+  const int mir = mirror_mask(r->lo, p);
+  P.mult = 1.0;
+  for (int d = 0; d < 3; ++d)
+    if (mir >> d & 1) P.mult *= 2.0;
   long long n = 0;
+  for (int l = 0; l < r->nl; ++l) r->L[l].v.mir = mir;
   for (int l = 0; l < r->nl; ++l) {
     LevelView& v = r->L[l].v;
     if (r->prec == DF_FP64) {
       n += launch_init_uniform<double>(v, P, st);
       n += launch_static_fields<double>(v, P, p->lum_sigma, r->wsum, r->partials, st);
-      if (p->lum_sigma > 0.0) n += launch_normalise_lum<double>(v, r->wsum, st);
+      if (p->lum_sigma > 0.0) n += launch_normalise_lum<double>(v, r->wsum, P.mult, st);
     } else {
       n += launch_init_uniform<float>(v, P, st);
       n += launch_static_fields<float>(v, P, p->lum_sigma, r->wsum, r->partials, st);
-      if (p->lum_sigma > 0.0) n += launch_normalise_lum<float>(v, r->wsum, st);
+      if (p->lum_sigma > 0.0) n += launch_normalise_lum<float>(v, r->wsum, P.mult, st);
     }
     if (cudaMemsetAsync(r->L[l].acc, 0, r->L[l].acc_elems * sizeof(double), st) != cudaSuccess)
       *rc = fail(DF_ECUDA, "memset");
@@ -529,6 +556,17 @@ struct Builder {
     out.push_back({op, d, it});
   }
 
+  // reflect fill of the mirror sides only (type -1: the upper side is left alone)
+  void mirror_fill(const Item<T>& it, std::vector<Entry>& out) const {
+    for (int d = 0; d < 3; ++d)
+      if (it.L.mir >> d & 1) {
+        Item<T> bc = it;
+        bc.bc_lo = DF_BC_REFLECT;
+        bc.bc_hi = -1;
+        add(out, OP_BC, d, bc);
+      }
+  }
+
   void level_step(const Run& r, int l, int m_out, std::vector<Entry>& out) const {
     Item<T> it = base(r, l);
     it.b = box(it.L, m_out + kReach, r.P.av_c2 > 0.0);
@@ -540,6 +578,8 @@ struct Builder {
         bc.bc_hi = P.bc[2 * d + 1];
         add(out, OP_BC, d, bc);
       }
+    else
+      mirror_fill(it, out);  // CommUp filled the rest of the ghosts
     if (P.hydro_on) add(out, OP_SOURCE, 0, it);
     if (P.hydro_on && P.av_c2 > 0.0) {
       add(out, OP_VISC_Q, 0, it);
@@ -586,6 +626,7 @@ struct Builder {
     level_step(r, l, m_out, out);
     if (l + 1 < r.nl) {
       Item<T> it = base(r, l);
+      mirror_fill(it, out);  // the CommUp stencil reaches across a mirror plane
       it.F = r.L[l + 1].v;
       add(out, OP_COMMUP, 0, it);
       add(out, OP_COMMMEAN, 0, it);
@@ -744,6 +785,10 @@ int plan_build_ops(Plan& plan, Run* r, const std::vector<std::pair<int, int>>& o
     it.b = B.box(it.L, it.L.G);
     switch (op) {
       case OP_COMMUP:
+        B.mirror_fill(it, v);  // as in the coarse step: the stencil reaches across a plane
+        it.F = r->L[l + 1].v;
+        B.add(v, op, 0, it);
+        break;
       case OP_COMMMEAN:
         it.F = r->L[l + 1].v;
         B.add(v, op, 0, it);
@@ -1221,6 +1266,7 @@ int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], co
 int df_set_params(df_ctx* c, const df_params* p) {
   if (check_ctx(c, false)) return DF_EINVAL;
   if (check_params(p)) return DF_EINVAL;
+  if (check_mirror(c->run->nl, c->run->lo, p)) return DF_EINVAL;
   DevGuard g(c->device);
   enter(c);
   int rc = DF_OK;
@@ -1593,6 +1639,7 @@ int df_pool_admit(df_pool* p, int n_levels, const int n[3], const double lo[3],
   if (check_params(prm)) return DF_EINVAL;
   int rc = check_shape(n_levels, n, lo, hi, G, p->prec);
   if (rc) return rc;
+  if (check_mirror(n_levels, lo, prm)) return DF_EINVAL;
   size_t need = run_bytes(n_levels, n, G, p->prec);
   if (p->used + need > p->budget)
     return fail(DF_EBUSY, "HBM budget: %zu used + %zu needed > %zu", p->used, need, p->budget);

@@ -34,6 +34,10 @@ struct LevelView {
   const double* cacc;
   int cacc_slots;
   int is_child;
+  // bit d: the lower d-face of the domain is a mirror plane through the perturber
+  // (coordinate 0, reflecting) and the run stands for the domain unfolded across it;
+  // the same on every level of a run
+  int mir;
 };
 
 // Scratch shared by all levels of a context (levels are advanced one at a time).
@@ -91,6 +95,7 @@ __host__ __device__ inline int sweep_units(const Box& b, int d) {
 
 struct Phys {
   double gamma, rho0, e0, V[3], GM, eps, chi, L, cfl, cfl_diff, dt_fixed, av_c2;
+  double mult;  // copies of the simulated part in the unfolded domain (2^mirror planes)
   int diff_face_rho, hydro_on, band;
   int bc[6];
 };
@@ -213,7 +218,7 @@ template <class T> int launch_init_uniform(const LevelView& L, const Phys& P, cu
 template <class T> int launch_static_fields(const LevelView& L, const Phys& P, double lum_sigma,
                                             double* wsum, double* partials, cudaStream_t st);
 template <class T> int launch_normalise_lum(const LevelView& L, const double* wsum,
-                                            cudaStream_t st);
+                                            double mult, cudaStream_t st);
 // host I/O; bgv = background value of the field (0 moves the stored deviations)
 template <class T> int launch_pack_active(const LevelView& L, int field, double* out, int full,
                                           double bgv, cudaStream_t st);

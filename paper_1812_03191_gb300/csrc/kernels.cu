@@ -115,16 +115,19 @@ __device__ __forceinline__ T upwind(const T* __restrict__ q, int c, int st, T u,
 
 inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-// coarse frontier face test: returns side (0/1) and the slot, or -1
+// coarse frontier face test: returns side (0/1) and the slot, or -1.  A mirror
+// plane is no frontier, and a ghost face across one takes its image's slot.
 __device__ __forceinline__ int coarse_frontier(const LevelView& L, int d, int f0, int f1, int f2,
                                                int& slot) {
   int f[3] = {f0, f1, f2};
   int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
   int a = f[t1] - L.G - L.coff[t1], b = f[t2] - L.G - L.coff[t2];
+  if (a < 0 && (L.mir >> t1 & 1)) a = -1 - a;
+  if (b < 0 && (L.mir >> t2 & 1)) b = -1 - b;
   int h1 = L.cn[t1] >> 1, h2 = L.cn[t2] >> 1;
   if (a < 0 || a >= h1 || b < 0 || b >= h2) return -1;
   int lo = L.G + L.coff[d];
-  int side = f[d] == lo ? 0 : (f[d] == lo + (L.cn[d] >> 1) ? 1 : -1);
+  int side = f[d] == lo && !(L.mir >> d & 1) ? 0 : (f[d] == lo + (L.cn[d] >> 1) ? 1 : -1);
   slot = b * h1 + a;
   return side;
 }
@@ -247,7 +250,9 @@ __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b
     // (e0 + de)(1 - a)/(1 + a) - e0
     ec = hdiv(ec * (T(1) - a) - T(2) * a * bg.e0, T(1) + a);
   }
-  if (do_lum && i >= L.G && i < L.G + L.n[0] && j >= L.G && j < L.G + L.n[1] && k >= L.G &&
+  // active cells and their mirror images in the ghost layers
+  if (do_lum && i >= (L.mir & 1 ? 0 : L.G) && i < L.G + L.n[0] &&
+      j >= (L.mir & 2 ? 0 : L.G) && j < L.G + L.n[1] && k >= (L.mir & 4 ? 0 : L.G) &&
       k < L.G + L.n[2])
     ec = ec + lum * dt * ((const T*)L.lumw)[c];
   e[c] = ec;
@@ -910,6 +915,7 @@ __device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_l
   int b = (int)(r / L.s[t1]);
   int a = (int)(r - (long long)b * L.s[t1]);
   int type = side ? type_hi : type_lo;
+  if (type < 0) return;  // this side is left alone (mirror fill of finer levels)
   int normal = (f == F_VX + d);
   int dst = side == 0 ? G - g : G + n - 1 + g, src = -1;
   (void)rho0;
@@ -1071,6 +1077,7 @@ __device__ __forceinline__ bool in_band(const LevelView& F, int band, int a0, in
   for (int d = 0; d < 3; ++d) {
     int lo = a3[d] - F.off[d], hi = F.off[d] + (F.n[d] >> 1) - 1 - a3[d];
     if (lo < 0 || hi < 0) return false;
+    if (F.mir >> d & 1) lo = 1 << 30;  // a mirror face bounds no band
     dist = min(dist, min(lo, hi));
   }
   return dist < band;
@@ -1351,9 +1358,11 @@ __device__ __forceinline__ void el_force_level(const LevelView& L, const double*
   }
 }
 
-// static force weights of the active cells
+// static force weights of the active cells; with mirror planes the force is that of
+// the unfolded domain: no component along a mirror axis, the others mult times the
+// sum over the simulated part (mult = 2^planes scales exactly)
 __global__ void __launch_bounds__(kBlock) k_force_weights(LevelView L, double GM, double eps,
-                                                          double* fw) {
+                                                          double mult, double* fw) {
   long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
   if (t >= na) return;
@@ -1365,9 +1374,9 @@ __global__ void __launch_bounds__(kBlock) k_force_weights(LevelView L, double GM
   double z = L.lo[2] + (ak + 0.5) * L.dx[2];
   double r2 = x * x + y * y + z * z + eps * eps;
   double w = GM * L.vol / (r2 * sqrt(r2));
-  fw[t] = w * x;
-  fw[t + na] = w * y;
-  fw[t + 2 * na] = w * z;
+  fw[t] = L.mir & 1 ? 0.0 : mult * (w * x);
+  fw[t + na] = L.mir & 2 ? 0.0 : mult * (w * y);
+  fw[t + 2 * na] = L.mir & 4 ? 0.0 : mult * (w * z);
 }
 
 // fixed-order compensated (Neumaier) sum of the block partials, one warp per
@@ -1427,7 +1436,8 @@ __global__ void __launch_bounds__(kBlock) k_init_uniform(LevelView L, T rho0, T 
 }
 
 // Plummer potential (Eq. 16, attractive sign) at every cell centre; luminosity
-// weights on active cells (Gaussian weights are normalised afterwards)
+// weights on active cells and on their mirror images in the ghost layers (Gaussian
+// weights are normalised afterwards)
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_static(LevelView L, double GM, double eps,
                                                    double sigma, int vertex_ok, int vx0, int vx1,
@@ -1440,8 +1450,9 @@ __global__ void __launch_bounds__(kBlock) k_static(LevelView L, double GM, doubl
   double y = L.lo[1] + (j - L.G + 0.5) * L.dx[1];
   double z = L.lo[2] + (k - L.G + 0.5) * L.dx[2];
   ((T*)L.phi)[c] = (T)(-GM / sqrt(x * x + y * y + z * z + eps * eps));
-  bool act = i >= L.G && i < L.G + L.n[0] && j >= L.G && j < L.G + L.n[1] && k >= L.G &&
-             k < L.G + L.n[2];
+  bool act = i >= (L.mir & 1 ? 0 : L.G) && i < L.G + L.n[0] &&
+             j >= (L.mir & 2 ? 0 : L.G) && j < L.G + L.n[1] &&
+             k >= (L.mir & 4 ? 0 : L.G) && k < L.G + L.n[2];
   double lw = 0.0;
   if (act) {
     if (sigma > 0.0) {
@@ -1492,11 +1503,13 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int n, doubl
 }
 
 template <class T>
-__global__ void __launch_bounds__(kBlock) k_normalise_lum(LevelView L, const double* wsum) {
+__global__ void __launch_bounds__(kBlock) k_normalise_lum(LevelView L, const double* wsum,
+                                                          double mult) {
   long long c = blockIdx.x * (long long)kBlock + threadIdx.x;
   if (c >= L.nc) return;
   T* lw = (T*)L.lumw;
-  lw[c] = (T)((double)lw[c] / (wsum[0] * L.vol));
+  // the unfolded domain holds mult copies of the active cells
+  lw[c] = (T)((double)lw[c] / (mult * wsum[0] * L.vol));
 }
 
 // host I/O: full values = background + stored deviation (bgv = 0 for raw state)
@@ -1837,8 +1850,8 @@ int force_partials_per_level(const LevelView& L) {
 }
 
 int launch_force_weights(const LevelView& L, const Phys& P, cudaStream_t st) {
-  k_force_weights<<<grid_for((long long)L.n[0] * L.n[1] * L.n[2]), kBlock, 0, st>>>(L, P.GM, P.eps,
-                                                                                   L.fw);
+  k_force_weights<<<grid_for((long long)L.n[0] * L.n[1] * L.n[2]), kBlock, 0, st>>>(
+      L, P.GM, P.eps, P.mult, L.fw);
   return 1;
 }
 
@@ -1856,7 +1869,8 @@ int launch_static_fields(const LevelView& L, const Phys& P, double lum_sigma, do
   for (int d = 0; d < 3; ++d) {
     double o = -L.lo[d] / L.dx[d];
     v[d] = (int)floor(o + 0.5);
-    if (fabs(o - v[d]) > 1e-9 || v[d] < 1 || v[d] > L.n[d] - 1) ok = 0;
+    // a vertex on a mirror plane has four of its eight cells in the ghost layer
+    if (fabs(o - v[d]) > 1e-9 || v[d] < (L.mir >> d & 1 ? 0 : 1) || v[d] > L.n[d] - 1) ok = 0;
   }
   k_static<T><<<grid_for(L.nc), kBlock, 0, st>>>(L, P.GM, P.eps, lum_sigma, ok, v[0], v[1], v[2]);
   if (lum_sigma <= 0.0) return 1;
@@ -1867,8 +1881,8 @@ int launch_static_fields(const LevelView& L, const Phys& P, double lum_sigma, do
 }
 
 template <class T>
-int launch_normalise_lum(const LevelView& L, const double* wsum, cudaStream_t st) {
-  k_normalise_lum<T><<<grid_for(L.nc), kBlock, 0, st>>>(L, wsum);
+int launch_normalise_lum(const LevelView& L, const double* wsum, double mult, cudaStream_t st) {
+  k_normalise_lum<T><<<grid_for(L.nc), kBlock, 0, st>>>(L, wsum, mult);
   return 1;
 }
 
@@ -1894,7 +1908,7 @@ int launch_unpack_active(const LevelView& L, int field, const double* in, int fu
   template int launch_init_uniform<T>(const LevelView&, const Phys&, cudaStream_t);            \
   template int launch_static_fields<T>(const LevelView&, const Phys&, double, double*,         \
                                        double*, cudaStream_t);                                 \
-  template int launch_normalise_lum<T>(const LevelView&, const double*, cudaStream_t);         \
+  template int launch_normalise_lum<T>(const LevelView&, const double*, double, cudaStream_t); \
   template int launch_pack_active<T>(const LevelView&, int, double*, int, double, cudaStream_t); \
   template int launch_unpack_active<T>(const LevelView&, int, const double*, int, double,      \
                                        cudaStream_t);

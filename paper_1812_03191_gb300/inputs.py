@@ -83,6 +83,22 @@ def precision(n=128, n_levels=5, half=16.0):
     return cfg
 
 
+def quadrant(n=32, n_levels=6, half=8.0, mach=3.0, **over):
+    """The set-up of Sec. 3.4 on its quadrant domain: flow along +z, the perturber
+    at the corner vertex of x, y >= 0; every level spans [0, l 2^-k]^2 x
+    [-l 2^-k, l 2^-k] with n/2 x n/2 x n cells.  The planes x = 0 and y = 0 are
+    mirror planes (the run stands for the whole domain, whose force it reports);
+    the outer x and y faces reflect too, and both z faces hold the background."""
+    p = base_params(gamma=1.4, mach=mach, flow_dir=(0.0, 0.0, 1.0), eps=0.0,
+                    bc=(BC_REFLECT,) * 4 + (BC_INFLOW,) * 2)
+    p.update(over)
+    return dict(
+        name=f"quadrant_{n_levels}x{n // 2}x{n // 2}x{n}",
+        n_levels=n_levels, n=(n // 2, n // 2, n), lo=(0.0, 0.0, -half), hi=(half,) * 3,
+        G=DEFAULT_G, params=p,
+    )
+
+
 def smooth_perturbation(shape, seed, amp, n_modes=4):
     """Sum of a few random low-wavenumber periodic modes (shape = (nz, ny, nx))."""
     rng = np.random.default_rng(seed)

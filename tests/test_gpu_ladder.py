@@ -51,10 +51,12 @@ def test_low_mach_heating_force_matches_eq8_within_the_box_share():
 def test_low_mach_cold_thermal_force_is_a_drag_of_the_eq51_order():
     """Cold perturber with thermal diffusion minus the adiabatic one at Mach 0.1:
     a drag, as Sec. 4.2 finds, of the order of -(gamma - 1)/2 F0 (Eq. 51) times the
-    Eq. 23 share.  Measured: 0.77 of it at 100 tau and still growing slowly (it is
-    the V -> 0 limit and the paper corroborates it in a box 32 times larger), so
-    the bound is loose: the sign, and 0.6-1.05 of the asymptote."""
+    Eq. 23 share.  Measured: 0.94 of it at 100 tau, settled from about 50 tau on
+    (it is the V -> 0 limit, which the paper corroborates in a box 32 times
+    larger), so the bound is loose: the sign, 0.8-1.05 of the asymptote, and a
+    second half of the run within 10 % of the final value."""
     out = ladder.cold_thermal(mach=0.1)
-    assert out["ratio"] > 0.6 and out["ratio"] < 1.05, out["ratio"]
+    assert out["ratio"] > 0.8 and out["ratio"] < 1.05, out["ratio"]
     F = np.array(out["runs"][6]["F"])
-    assert F[-1] < 0 and abs(F[-1]) > abs(F[len(F) // 2])  # a drag, still building up
+    late = F[len(F) // 2:]
+    assert F[-1] < 0 and np.abs(late - F[-1]).max() <= 0.1 * abs(F[-1])  # a settled drag

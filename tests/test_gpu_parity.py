@@ -58,6 +58,10 @@ def force_term_scale(sim, params):
     GM, eps, rho0 = params["GM"], params["eps"], params["rho0"]
     tot = 0.0
     n = np.array(sim.n)
+    mult = 1.0
+    for d in range(3):  # a mirror plane doubles the sum (the unfolded domain's force)
+        if sim.lo[d] == 0.0 and params["bc"][2 * d] == I.BC_REFLECT:
+            mult *= 2.0
     for l in range(sim.n_levels):
         dx = (np.array(sim.hi) - np.array(sim.lo)) / 2**l / n
         lo = np.array(sim.lo) / 2**l
@@ -66,10 +70,10 @@ def force_term_scale(sim, params):
         r2 = x**2 + y**2 + z**2 + eps**2
         w = GM * np.prod(dx) * np.sqrt(x**2 + y**2 + z**2) / r2**1.5
         if l + 1 < sim.n_levels:
-            q = n // 4
+            q = np.rint((lo / 2 - lo) / dx).astype(int)
             w[q[2]:q[2] + n[2] // 2, q[1]:q[1] + n[1] // 2, q[0]:q[0] + n[0] // 2] = 0
         tot += w.sum()
-    return rho0 * tot
+    return mult * rho0 * tot
 
 
 def assert_parity(sim, orc, params, tol=TOL, ftol=TOL):
