@@ -174,9 +174,14 @@ static int is_active_elem(const olevel* L, int field, int i, int j, int k) {
 
 or_sim* or_create(int n_levels, const int n[3], const double lo[3], const double hi[3], int G,
                   const or_params* p) {
+  return or_create_ground(n_levels, n, n, lo, hi, G, p);
+}
+
+or_sim* or_create_ground(int n_levels, const int n0[3], const int nf[3], const double lo[3],
+                         const double hi[3], int G, const or_params* p) {
   if (n_levels < 1 || n_levels > OR_MAX_LEVELS || G < 2 || !p) return NULL;
   for (int d = 0; d < 3; ++d)
-    if (n[d] < 4 || n[d] % 4 || !(hi[d] > lo[d])) return NULL;
+    if (n0[d] < 4 || n0[d] % 4 || nf[d] < 4 || nf[d] % 4 || !(hi[d] > lo[d])) return NULL;
   or_sim* S = (or_sim*)calloc(1, sizeof(or_sim));
   S->nl = n_levels;
   S->p = *p;
@@ -191,10 +196,12 @@ or_sim* or_create(int n_levels, const int n[3], const double lo[3], const double
   }
   for (int l = 0; l < n_levels; ++l) {
     olevel* L = &S->L[l];
-    double scale = ldexp(1.0, -l);
+    const int* n = l == 0 ? n0 : nf;
     L->G = G;
     L->nc = 1;
     for (int d = 0; d < 3; ++d) {
+      /* the level's box is the ground's scaled about the origin, its cell dx0 2^-l */
+      double scale = ldexp((double)n[d] / n0[d], -l);
       L->mir[d] = S->mir[d];
       L->n[d] = n[d];
       L->s[d] = n[d] + 2 * G;

@@ -49,6 +49,12 @@ typedef struct or_sim or_sim;
  * ghost layers; fill the uniform initial state (Sec. 3.4).  NULL on bad input. */
 or_sim* or_create(int n_levels, const int n[3], const double lo[3], const double hi[3],
                   int G, const or_params* p);
+/* Same with a ground level of n0[3] cells over [lo, hi] and finer levels of n[3]
+ * cells: the cell halves from level to level, and level l >= 1 spans [lo, hi] scaled
+ * about the origin by (n/n0) 2^-l per axis.  n0 = 2n gives the hierarchy of
+ * Sec. 4.1.1 whose first level covers a quarter of the ground's extent. */
+or_sim* or_create_ground(int n_levels, const int n0[3], const int n[3], const double lo[3],
+                         const double hi[3], int G, const or_params* p);
 void or_destroy(or_sim* s);
 
 /* Advance n coarse steps (Sec. 3.3 recursion, Eq. 55 time step). */

@@ -74,6 +74,9 @@ def _load():
         dp = P(C.c_double)
         lib.or_create.restype = C.c_void_p
         lib.or_create.argtypes = [C.c_int, P(C.c_int), dp, dp, C.c_int, P(OracleParams)]
+        lib.or_create_ground.restype = C.c_void_p
+        lib.or_create_ground.argtypes = [C.c_int, P(C.c_int), P(C.c_int), dp, dp, C.c_int,
+                                         P(OracleParams)]
         lib.or_destroy.argtypes = [C.c_void_p]
         lib.or_step.argtypes = [C.c_void_p, C.c_int]
         lib.or_compute_dt.restype = C.c_double
@@ -116,12 +119,16 @@ def xi_search(dt_level, cost):
 class Oracle:
     """One nested hierarchy advanced by the FP64 oracle."""
 
-    def __init__(self, n_levels, n, lo, hi, G, params: dict):
+    def __init__(self, n_levels, n, lo, hi, G, params: dict, n0=None):
+        """n: cells per axis of every level; n0 (optional): of the ground level only"""
         lib = _load()
         self.lib = lib
         if isinstance(n, int):
             n = (n, n, n)
         self.n = tuple(int(x) for x in n)
+        if isinstance(n0, int):
+            n0 = (n0, n0, n0)
+        self.n0 = self.n if n0 is None else tuple(int(x) for x in n0)
         self.n_levels = int(n_levels)
         self.G = int(G)
         p = OracleParams()
@@ -136,7 +143,8 @@ class Oracle:
         na = (C.c_int * 3)(*self.n)
         lo_ = (C.c_double * 3)(*lo)
         hi_ = (C.c_double * 3)(*hi)
-        self.h = lib.or_create(self.n_levels, na, lo_, hi_, self.G, C.byref(p))
+        n0_ = (C.c_int * 3)(*self.n0)
+        self.h = lib.or_create_ground(self.n_levels, n0_, na, lo_, hi_, self.G, C.byref(p))
         if not self.h:
             raise ValueError("oracle rejected the hierarchy (sizes, offsets or ghost width)")
 
@@ -172,8 +180,11 @@ class Oracle:
         self.lib.or_force(self.h, _dp(F))
         return F
 
+    def level_n(self, level):
+        return self.n0 if level == 0 else self.n
+
     def get_field(self, level, field):
-        nx, ny, nz = self.n
+        nx, ny, nz = self.level_n(level)
         out = np.zeros(nx * ny * nz)
         if self.lib.or_get_field(self.h, level, field, _dp(out)):
             raise IndexError
@@ -181,18 +192,19 @@ class Oracle:
 
     def set_field(self, level, field, arr):
         a = np.ascontiguousarray(arr, dtype=np.float64).ravel()
-        assert a.size == self.n[0] * self.n[1] * self.n[2]
+        m = self.level_n(level)
+        assert a.size == m[0] * m[1] * m[2]
         if self.lib.or_set_field(self.h, level, field, _dp(a)):
             raise IndexError
 
-    def full_shape(self):
-        return tuple(x + 2 * self.G for x in self.n[::-1])
+    def full_shape(self, level=0):
+        return tuple(x + 2 * self.G for x in self.level_n(level)[::-1])
 
     def get_full(self, level, field):
-        out = np.zeros(int(np.prod(self.full_shape())))
+        out = np.zeros(int(np.prod(self.full_shape(level))))
         if self.lib.or_get_full(self.h, level, field, _dp(out)):
             raise IndexError
-        return out.reshape(self.full_shape())
+        return out.reshape(self.full_shape(level))
 
     def set_full(self, level, field, arr):
         a = np.ascontiguousarray(arr, dtype=np.float64).ravel()
