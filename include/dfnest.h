@@ -92,6 +92,18 @@ typedef struct df_ctx df_ctx;
 int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], const double hi[3],
               int G, int precision, int device, void* stream);
 
+/* df_create with a ground level of its own: level 0 has n0[3] cells over [lo, hi],
+ * every finer level n[3] cells.  The cell halves from level to level, so level
+ * l >= 1 spans [lo, hi] scaled about the origin by (n[d]/n0[d]) 2^-l per axis.
+ * n0 = 2n is the hierarchy of Sec. 4.1.1 whose first level covers a quarter of the
+ * ground's extent (a 64x64x128 ground under levels of 32x32x64); n0 = n is
+ * df_create.  The nesting rules of df_create hold level by level (the ground has
+ * its own count in them), and n0 obeys the same size rules as n.  Ownership and
+ * errors as df_create. */
+int df_create_ground(df_ctx** out, int n_levels, const int n0[3], const int n[3],
+                     const double lo[3], const double hi[3], int G, int precision, int device,
+                     void* stream);
+
 /* Copy the parameters, precompute the static potential (Eq. 16) and luminosity
  * weights, and set every level to the uniform background (Sec. 3.4): rho0, e0, V.
  * Resets t to 0 and clears the force history.  DF_EINVAL on bad values, and when
@@ -132,8 +144,10 @@ int df_set_full(df_ctx* ctx, int level, int field, const double* host_in);
 
 /* Checkpoint: every padded field of every level as stored -- the deviation from
  * the uniform background (rho - rho0, e - e0, v - V), converted to FP64 -- in the
- * order level-major, field-minor, plus the time t.  df_state_size gives the
- * element count.  Restoring a saved state resumes a run bitwise. */
+ * order level-major, field-minor, plus the time t; each (level, field) block has
+ * the element count of the largest level (a smaller level fills the start of its
+ * block).  df_state_size gives the element count.  Restoring a saved state resumes
+ * a run bitwise. */
 size_t df_state_size(const df_ctx* ctx);
 int df_get_state(df_ctx* ctx, double* host_out, double* t_out);
 int df_set_state(df_ctx* ctx, const double* host_in, double t);
@@ -238,6 +252,8 @@ typedef struct df_pool df_pool;
 
 /* Device bytes one run of this shape holds (the pool's admission measure). */
 size_t df_run_bytes(int n_levels, const int n[3], int G, int precision);
+/* The same for a run with a ground level of n0[3] cells (df_create_ground). */
+size_t df_run_bytes_ground(int n_levels, const int n0[3], const int n[3], int G, int precision);
 
 /* Create an empty pool that admits runs while their bytes stay within
  * hbm_budget_bytes.  precision as in df_create (one precision per pool). */
@@ -250,6 +266,10 @@ int df_pool_create(df_pool** out, size_t hbm_budget_bytes, int precision, int de
  * sub-cycling on the device each coarse step, as in a context. */
 int df_pool_admit(df_pool* pool, int n_levels, const int n[3], const double lo[3],
                   const double hi[3], int G, const df_params* p, int* slot_out);
+/* Admit a run with a ground level of n0[3] cells (geometry as df_create_ground). */
+int df_pool_admit_ground(df_pool* pool, int n_levels, const int n0[3], const int n[3],
+                         const double lo[3], const double hi[3], int G, const df_params* p,
+                         int* slot_out);
 
 /* Free a run's slot and memory (synchronises the pool's stream first). */
 int df_pool_release(df_pool* pool, int slot);

@@ -30,7 +30,8 @@ EXPORTS = (
     "df_pool_query", "df_pool_get_field", "df_pool_info", "df_pool_set_tiles",
     "df_pool_autotune", "df_pool_destroy", "df_pool_set_timing", "df_pool_kernel_time",
     "df_autotune", "df_set_tile_shapes", "df_pool_set_tile_shapes", "df_set_transport",
-    "df_pool_set_transport", "df_pool_set_field",
+    "df_pool_set_transport", "df_pool_set_field", "df_create_ground", "df_run_bytes_ground",
+    "df_pool_admit_ground",
 )
 POOL_OPS = 22
 # operator order of the per-op tables (tile shapes, blocks per SM)
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH):
     P, dp, vp = C.POINTER, C.POINTER(C.c_double), C.c_void_p
     sig = {
         "df_create": (C.c_int, [P(vp), C.c_int, P(C.c_int), dp, dp, C.c_int, C.c_int, C.c_int, vp]),
+        "df_create_ground": (C.c_int, [P(vp), C.c_int, P(C.c_int), P(C.c_int), dp, dp, C.c_int,
+                                       C.c_int, C.c_int, vp]),
         "df_set_params": (C.c_int, [vp, P(Params)]),
         "df_step": (C.c_int, [vp, C.c_int]),
         "df_status": (C.c_int, [vp, dp, dp, P(C.c_int)]),
@@ -117,9 +120,12 @@ def load(path: str = LIB_PATH):
         "df_last_error": (C.c_char_p, []),
         "df_check_division": (C.c_int, [dp, dp, C.c_int, dp]),
         "df_run_bytes": (C.c_size_t, [C.c_int, P(C.c_int), C.c_int, C.c_int]),
+        "df_run_bytes_ground": (C.c_size_t, [C.c_int, P(C.c_int), P(C.c_int), C.c_int, C.c_int]),
         "df_pool_create": (C.c_int, [P(vp), C.c_size_t, C.c_int, C.c_int, vp]),
         "df_pool_admit": (C.c_int, [vp, C.c_int, P(C.c_int), dp, dp, C.c_int, P(Params),
                                     P(C.c_int)]),
+        "df_pool_admit_ground": (C.c_int, [vp, C.c_int, P(C.c_int), P(C.c_int), dp, dp, C.c_int,
+                                           P(Params), P(C.c_int)]),
         "df_pool_release": (C.c_int, [vp, C.c_int]),
         "df_pool_step": (C.c_int, [vp, C.c_int]),
         "df_pool_query": (C.c_int, [vp, dp, C.c_int]),
@@ -205,23 +211,29 @@ class Sim:
     """One nested hierarchy resident on one GPU (a df_ctx)."""
 
     def __init__(self, n_levels, n, lo, hi, G, params: dict | None = None,
-                 precision=DF_FP64, device=0, stream=None):
+                 precision=DF_FP64, device=0, stream=None, n0=None):
+        """n: cells per axis of every level; n0 (optional): of the ground level only
+        (df_create_ground: n0 = 2n puts the first level over a quarter of the ground)"""
         lib = load()
         self.lib = lib
         if isinstance(n, int):
             n = (n, n, n)
         self.n = tuple(int(x) for x in n)
+        if isinstance(n0, int):
+            n0 = (n0, n0, n0)
+        self.n0 = self.n if n0 is None else tuple(int(x) for x in n0)
         self.lo, self.hi = tuple(float(x) for x in lo), tuple(float(x) for x in hi)
         self.n_levels = int(n_levels)
         self.G = int(G)
         self.precision = precision
         h = C.c_void_p()
         na = (C.c_int * 3)(*self.n)
+        n0_ = (C.c_int * 3)(*self.n0)
         lo_ = (C.c_double * 3)(*lo)
         hi_ = (C.c_double * 3)(*hi)
         st = C.c_void_p(stream) if stream else None
-        _check(lib.df_create(C.byref(h), self.n_levels, na, lo_, hi_, self.G, precision,
-                             device, st))
+        _check(lib.df_create_ground(C.byref(h), self.n_levels, n0_, na, lo_, hi_, self.G,
+                                    precision, device, st))
         self.h = h
         if params is not None:
             self.set_params(params)
@@ -279,29 +291,33 @@ class Sim:
         _check(self.lib.df_compute_dt(self.h, C.byref(dt), _dp(lv)))
         return dt.value, lv
 
+    def level_n(self, level):
+        return self.n0 if level == 0 else self.n
+
     def get_field(self, level, field):
-        nx, ny, nz = self.n
+        nx, ny, nz = self.level_n(level)
         out = np.empty(nx * ny * nz)
         _check(self.lib.df_get_field(self.h, level, field, _dp(out)))
         return out.reshape(nz, ny, nx)
 
     def set_field(self, level, field, arr):
         a = np.ascontiguousarray(arr, dtype=np.float64).ravel()
-        if a.size != self.n[0] * self.n[1] * self.n[2]:
+        m = self.level_n(level)
+        if a.size != m[0] * m[1] * m[2]:
             raise ValueError("wrong size")
         _check(self.lib.df_set_field(self.h, level, field, _dp(a)))
 
-    def full_shape(self):
-        return tuple(x + 2 * self.G for x in self.n[::-1])
+    def full_shape(self, level=0):
+        return tuple(x + 2 * self.G for x in self.level_n(level)[::-1])
 
     def get_full(self, level, field):
-        out = np.empty(int(np.prod(self.full_shape())))
+        out = np.empty(int(np.prod(self.full_shape(level))))
         _check(self.lib.df_get_full(self.h, level, field, _dp(out)))
-        return out.reshape(self.full_shape())
+        return out.reshape(self.full_shape(level))
 
     def set_full(self, level, field, arr):
         a = np.ascontiguousarray(arr, dtype=np.float64).ravel()
-        if a.size != int(np.prod(self.full_shape())):
+        if a.size != int(np.prod(self.full_shape(level))):
             raise ValueError("wrong size")
         _check(self.lib.df_set_full(self.h, level, field, _dp(a)))
 
@@ -357,10 +373,14 @@ class Sim:
         _check(self.lib.df_debug_full_boxes(self.h, 1 if on else 0))
 
 
-def run_bytes(n_levels, n, G, precision=DF_FP64):
+def run_bytes(n_levels, n, G, precision=DF_FP64, n0=None):
     if isinstance(n, int):
         n = (n, n, n)
-    return int(load().df_run_bytes(n_levels, (C.c_int * 3)(*n), G, precision))
+    if isinstance(n0, int):
+        n0 = (n0, n0, n0)
+    n0 = n if n0 is None else n0
+    return int(load().df_run_bytes_ground(n_levels, (C.c_int * 3)(*n0), (C.c_int * 3)(*n), G,
+                                          precision))
 
 
 class Pool:
@@ -387,18 +407,22 @@ class Pool:
         except Exception:
             pass
 
-    def admit(self, n_levels, n, lo, hi, G, params: dict):
-        """slot index, or None when the HBM budget is full"""
+    def admit(self, n_levels, n, lo, hi, G, params: dict, n0=None):
+        """slot index, or None when the HBM budget is full; n0 as in Sim"""
         if isinstance(n, int):
             n = (n, n, n)
+        if isinstance(n0, int):
+            n0 = (n0, n0, n0)
+        n0 = tuple(n) if n0 is None else tuple(n0)
         slot = C.c_int()
-        rc = self.lib.df_pool_admit(self.h, int(n_levels), (C.c_int * 3)(*n),
-                                    (C.c_double * 3)(*lo), (C.c_double * 3)(*hi), int(G),
-                                    C.byref(Params.from_dict(params)), C.byref(slot))
+        rc = self.lib.df_pool_admit_ground(self.h, int(n_levels), (C.c_int * 3)(*n0),
+                                           (C.c_int * 3)(*n), (C.c_double * 3)(*lo),
+                                           (C.c_double * 3)(*hi), int(G),
+                                           C.byref(Params.from_dict(params)), C.byref(slot))
         if rc == DF_EBUSY:
             return None
         _check(rc)
-        self.shapes[slot.value] = (int(n_levels), tuple(n))
+        self.shapes[slot.value] = (int(n_levels), tuple(n), n0)
         return slot.value
 
     def release(self, slot):
@@ -417,14 +441,16 @@ class Pool:
         return out[:6 * ns].reshape(ns, 6)
 
     def set_field(self, slot, level, field, values):
-        nl, n = self.shapes[slot]
+        nl, n, n0 = self.shapes[slot]
+        n = n0 if level == 0 else n
         a = np.ascontiguousarray(values, dtype=np.float64).reshape(-1)
         if a.size != n[0] * n[1] * n[2]:
             raise ValueError("field size does not match the run's mesh")
         _check(self.lib.df_pool_set_field(self.h, int(slot), level, field, _dp(a)))
 
     def get_field(self, slot, level, field):
-        nl, n = self.shapes[slot]
+        nl, n, n0 = self.shapes[slot]
+        n = n0 if level == 0 else n
         out = np.empty(n[0] * n[1] * n[2])
         _check(self.lib.df_pool_get_field(self.h, int(slot), level, field, _dp(out)))
         return out.reshape(n[2], n[1], n[0])

@@ -80,7 +80,9 @@ namespace {
 
 struct Run {
   int nl = 0, prec = 0, G = 0;
-  int n[3] = {0, 0, 0};
+  int n0[3] = {0, 0, 0};  // cells per axis of the ground level
+  int n[3] = {0, 0, 0};   // of every finer level
+  size_t nc_max = 0;      // elements per field of the largest level
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   size_t esz = 8;
   std::vector<Level> L;
@@ -104,24 +106,41 @@ struct Run {
 
 size_t plane_bytes(size_t nc, size_t esz) { return ((nc * esz + 255) / 256) * 256; }
 
+// cells per axis of level l: the ground's own counts, then the finer levels'
+inline const int* level_n(int l, const int n0[3], const int n[3]) { return l == 0 ? n0 : n; }
+
+// level l's box is the ground's scaled about the origin by this factor along d: the
+// cell halves from level to level (n0 == n: 2^-l; n0 == 2n: level 1 spans a quarter)
+inline double level_scale(int l, int d, const int n0[3], const int n[3]) {
+  return std::ldexp((double)level_n(l, n0, n)[d] / n0[d], -l);
+}
+
+size_t level_elems(const int n[3], int G) {
+  size_t nc = 1;
+  for (int d = 0; d < 3; ++d) nc *= (size_t)(n[d] + 2 * G);
+  return nc;
+}
+
 // device bytes a run of this shape allocates (admission control uses the same sum)
-size_t run_bytes(int nl, const int n[3], int G, int prec) {
+size_t run_bytes(int nl, const int n0[3], const int n[3], int G, int prec) {
   size_t esz = prec == DF_FP64 ? 8 : 4;
-  size_t nc = 1, na = 1;
-  for (int d = 0; d < 3; ++d) {
-    nc *= (size_t)(n[d] + 2 * G);
-    na *= (size_t)n[d];
+  size_t total = 0, nc_max = 0, na_max = 0, np = 0;
+  for (int l = 0; l < nl; ++l) {
+    const int* m = level_n(l, n0, n);
+    size_t nc = level_elems(m, G), na = (size_t)m[0] * m[1] * m[2];
+    int slots = 0;
+    for (int d = 0; d < 3; ++d) {
+      int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+      slots = std::max(slots, (m[t1] / 2) * (m[t2] / 2));
+    }
+    total += plane_bytes(nc, esz) * 7 + 18 * (size_t)slots * 8 + 3 * na * 8;
+    np += (na + 2047) / 2048;
+    nc_max = std::max(nc_max, nc);
+    na_max = std::max(na_max, na);
   }
-  int slots = 0;
-  for (int d = 0; d < 3; ++d) {
-    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    slots = std::max(slots, (n[t1] / 2) * (n[t2] / 2));
-  }
-  size_t per_level = plane_bytes(nc, esz) * 7 + 18 * (size_t)slots * 8 + 3 * na * 8;
-  size_t np = (size_t)nl * ((na + 2047) / 2048);
-  size_t pel = std::max(3 * np, (na + 255) / 256);
-  return per_level * nl + plane_bytes(nc, esz) * 12 + sizeof(DevScalars) + pel * 8 +
-         3 * 4096 * 8 + 8 + 8 + nc * 8;
+  size_t pel = std::max(3 * np, (na_max + 255) / 256);
+  return total + plane_bytes(nc_max, esz) * 12 + sizeof(DevScalars) + pel * 8 +
+         3 * 4096 * 8 + 8 + 8 + nc_max * 8;
 }
 
 void run_free(Run* r) {
@@ -141,33 +160,38 @@ void run_free(Run* r) {
   delete r;
 }
 
-int check_shape(int n_levels, const int n[3], const double lo[3], const double hi[3], int G,
-                int precision) {
+int check_shape(int n_levels, const int n0[3], const int n[3], const double lo[3],
+                const double hi[3], int G, int precision) {
   if (n_levels < 1 || n_levels > DF_MAX_LEVELS) return fail(DF_EINVAL, "n_levels out of range");
   if (G < 2 || G % 2) return fail(DF_EINVAL, "G must be even and >= 2");
   if (precision != DF_FP64 && precision != DF_FP32_STATE)
     return fail(DF_EINVAL, "unknown precision %d", precision);
-  for (int d = 0; d < 3; ++d) {
-    if (n[d] < 8 || n[d] % 4 || n[d] < G)
-      return fail(DF_EINVAL, "n[%d]=%d: need n%%4==0, n>=8, n>=G", d, n[d]);
-    if (!(hi[d] > lo[d])) return fail(DF_EINVAL, "empty box on axis %d", d);
+  for (int l = 0; l < std::min(n_levels, 2); ++l) {
+    const int* m = level_n(l, n0, n);
+    for (int d = 0; d < 3; ++d)
+      if (m[d] < 8 || m[d] % 4 || m[d] < G)
+        return fail(DF_EINVAL, "level %d: n[%d]=%d: need n%%4==0, n>=8, n>=G", l, d, m[d]);
+    long long s3 = 1;
+    for (int d = 0; d < 3; ++d) s3 *= (m[d] + 2 * G);
+    if (s3 >= (1LL << 31) / 5)
+      return fail(DF_EINVAL, "level %d too large (%lld elements)", l, s3);
   }
-  long long s3 = 1;
-  for (int d = 0; d < 3; ++d) s3 *= (n[d] + 2 * G);
-  if (s3 >= (1LL << 31) / 5) return fail(DF_EINVAL, "level too large (%lld elements)", s3);
+  for (int d = 0; d < 3; ++d)
+    if (!(hi[d] > lo[d])) return fail(DF_EINVAL, "empty box on axis %d", d);
   // every finer level on parent faces, ghosts and CommUp stencil inside the parent;
   // a lower domain face at coordinate 0 keeps every level on it (offset 0), which
   // df_set_params accepts only when that face is a mirror plane
   for (int l = 1; l < n_levels; ++l)
     for (int d = 0; d < 3; ++d) {
-      double ps = std::ldexp(1.0, -(l - 1)), cs = std::ldexp(1.0, -l);
-      double plo = lo[d] * ps, pdx = (hi[d] - lo[d]) * ps / n[d];
+      const int pn = level_n(l - 1, n0, n)[d], cn = n[d];
+      double ps = level_scale(l - 1, d, n0, n), cs = level_scale(l, d, n0, n);
+      double plo = lo[d] * ps, pdx = (hi[d] - lo[d]) * ps / pn;
       double o = (lo[d] * cs - plo) / pdx;
       int oi = (int)std::floor(o + 0.5);
       bool lo_ok = lo[d] == 0.0 ? oi == 0 : oi >= G / 2 + 1;
-      if (std::fabs(o - oi) > 1e-9 || !lo_ok || oi + n[d] / 2 + G / 2 + 1 > n[d])
+      if (std::fabs(o - oi) > 1e-9 || !lo_ok || oi + cn / 2 + G / 2 + 1 > pn)
         return fail(DF_EINVAL, "level %d: offset %.3f on axis %d must be an integer in [%d, %d]",
-                    l, o, d, lo[d] == 0.0 ? 0 : G / 2 + 1, n[d] - n[d] / 2 - G / 2 - 1);
+                    l, o, d, lo[d] == 0.0 ? 0 : G / 2 + 1, pn - cn / 2 - G / 2 - 1);
     }
   return DF_OK;
 }
@@ -191,10 +215,10 @@ int check_mirror(int n_levels, const double lo[3], const df_params* p) {
   return DF_OK;
 }
 
-int run_create(Run** out, int n_levels, const int n[3], const double lo[3], const double hi[3],
-               int G, int precision) {
+int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const double lo[3],
+               const double hi[3], int G, int precision) {
   *out = nullptr;
-  int rc0 = check_shape(n_levels, n, lo, hi, G, precision);
+  int rc0 = check_shape(n_levels, n0, n, lo, hi, G, precision);
   if (rc0) return rc0;
   Run* r = new (std::nothrow) Run;
   if (!r) return fail(DF_ENOMEM, "host allocation");
@@ -203,12 +227,13 @@ int run_create(Run** out, int n_levels, const int n[3], const double lo[3], cons
   r->G = G;
   r->esz = precision == DF_FP64 ? 8 : 4;
   for (int d = 0; d < 3; ++d) {
+    r->n0[d] = n0[d];
     r->n[d] = n[d];
     r->lo[d] = lo[d];
     r->hi[d] = hi[d];
   }
   for (int l = 0; l < DF_MAX_LEVELS; ++l) r->xi[l] = 2;
-  r->bytes = run_bytes(n_levels, n, G, precision);
+  r->bytes = run_bytes(n_levels, n0, n, G, precision);
 #define CKR(call)                                                            \
   do {                                                                       \
     cudaError_t e_ = (call);                                                 \
@@ -220,16 +245,22 @@ int run_create(Run** out, int n_levels, const int n[3], const double lo[3], cons
     }                                                                        \
   } while (0)
   r->L.resize(n_levels);
-  size_t nc = 1, na = (size_t)n[0] * n[1] * n[2];
-  for (int d = 0; d < 3; ++d) nc *= (size_t)(n[d] + 2 * G);
-  size_t plane = plane_bytes(nc, r->esz);
+  size_t na_max = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    const int* m = level_n(l, n0, n);
+    r->nc_max = std::max(r->nc_max, level_elems(m, G));
+    na_max = std::max(na_max, (size_t)m[0] * m[1] * m[2]);
+  }
   for (int l = 0; l < n_levels; ++l) {
     LevelView& v = r->L[l].v;
     memset(&v, 0, sizeof v);
-    double scale = std::ldexp(1.0, -l);
+    const int* n = level_n(l, n0, r->n);
+    const size_t nc = level_elems(n, G), na = (size_t)n[0] * n[1] * n[2];
+    const size_t plane = plane_bytes(nc, r->esz);
     v.G = G;
     v.nc = (int)nc;
     for (int d = 0; d < 3; ++d) {
+      const double scale = level_scale(l, d, n0, r->n);
       v.n[d] = n[d];
       v.s[d] = n[d] + 2 * G;
       v.lo[d] = lo[d] * scale;
@@ -247,7 +278,7 @@ int run_create(Run** out, int n_levels, const int n[3], const double lo[3], cons
       v.inv_dx[d] = 1.0 / v.dx[d];
       v.dcoef[d] = v.area[d] / v.dx[d];
     }
-    v.dt_scale = scale;
+    v.dt_scale = std::ldexp(1.0, -l);
     v.is_child = l > 0;
     if (l > 0) {
       const LevelView& p = r->L[l - 1].v;
@@ -281,6 +312,8 @@ int run_create(Run** out, int n_levels, const int n[3], const double lo[3], cons
     v.cacc = ch.acc;
     v.cacc_slots = ch.acc_slots;
   }
+  // scratch is shared by the levels (advanced one at a time): sized for the largest
+  const size_t plane = plane_bytes(r->nc_max, r->esz);
   CKR(cudaMalloc(&r->scratch_mem, plane * 12));
   CKR(cudaMemset(r->scratch_mem, 0, plane * 12));
   {
@@ -302,13 +335,13 @@ int run_create(Run** out, int n_levels, const int n[3], const double lo[3], cons
   int np = 0;
   for (int l = 0; l < n_levels; ++l) np += force_partials_per_level(r->L[l].v);
   r->n_partials = np;
-  size_t pelems = std::max(3 * (size_t)np, (na + 255) / 256);
+  size_t pelems = std::max(3 * (size_t)np, (na_max + 255) / 256);
   CKR(cudaMalloc(&r->partials, pelems * sizeof(double)));
   CKR(cudaMalloc(&r->ring, 3 * (size_t)r->ring_cap * sizeof(double)));
   CKR(cudaMalloc(&r->ring_pos, sizeof(long long)));
   CKR(cudaMemset(r->ring_pos, 0, sizeof(long long)));
   CKR(cudaMalloc(&r->wsum, sizeof(double)));
-  CKR(cudaMalloc(&r->stage, nc * sizeof(double)));
+  CKR(cudaMalloc(&r->stage, r->nc_max * sizeof(double)));
 #undef CKR
   *out = r;
   return DF_OK;
@@ -1072,14 +1105,17 @@ int snapshot(const std::vector<Run*>& runs, Snapshot& sn) {
   sn.pos.resize(runs.size());
   for (size_t i = 0; i < runs.size(); ++i) {
     Run* r = runs[i];
-    size_t plane = plane_bytes((size_t)r->L[0].v.nc, r->esz);
-    size_t ab = r->L[0].acc_elems * sizeof(double);
-    sn.fields[i].resize(plane * 5 * r->nl);
-    sn.acc[i].resize(ab * r->nl);
+    // level l at offset l * (largest level's size): levels differ with a ground level
+    size_t pmax = plane_bytes(r->nc_max, r->esz), amax = 0;
+    for (int l = 0; l < r->nl; ++l) amax = std::max(amax, r->L[l].acc_elems * sizeof(double));
+    sn.fields[i].resize(pmax * 5 * r->nl);
+    sn.acc[i].resize(amax * r->nl);
     for (int l = 0; l < r->nl; ++l) {
-      CK(cudaMemcpy(sn.fields[i].data() + plane * 5 * l, r->L[l].mem, plane * 5,
+      size_t plane = plane_bytes((size_t)r->L[l].v.nc, r->esz);
+      size_t ab = r->L[l].acc_elems * sizeof(double);
+      CK(cudaMemcpy(sn.fields[i].data() + pmax * 5 * l, r->L[l].mem, plane * 5,
                     cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(sn.acc[i].data() + ab * l, r->L[l].acc, ab, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(sn.acc[i].data() + amax * l, r->L[l].acc, ab, cudaMemcpyDeviceToHost));
     }
     sn.ring[i].resize(3 * (size_t)r->ring_cap * sizeof(double));
     CK(cudaMemcpy(sn.ring[i].data(), r->ring, sn.ring[i].size(), cudaMemcpyDeviceToHost));
@@ -1092,12 +1128,14 @@ int snapshot(const std::vector<Run*>& runs, Snapshot& sn) {
 int restore(const std::vector<Run*>& runs, const Snapshot& sn) {
   for (size_t i = 0; i < runs.size(); ++i) {
     Run* r = runs[i];
-    size_t plane = plane_bytes((size_t)r->L[0].v.nc, r->esz);
-    size_t ab = r->L[0].acc_elems * sizeof(double);
+    size_t pmax = plane_bytes(r->nc_max, r->esz), amax = 0;
+    for (int l = 0; l < r->nl; ++l) amax = std::max(amax, r->L[l].acc_elems * sizeof(double));
     for (int l = 0; l < r->nl; ++l) {
-      CK(cudaMemcpy(r->L[l].mem, sn.fields[i].data() + plane * 5 * l, plane * 5,
+      size_t plane = plane_bytes((size_t)r->L[l].v.nc, r->esz);
+      size_t ab = r->L[l].acc_elems * sizeof(double);
+      CK(cudaMemcpy(r->L[l].mem, sn.fields[i].data() + pmax * 5 * l, plane * 5,
                     cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(r->L[l].acc, sn.acc[i].data() + ab * l, ab, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(r->L[l].acc, sn.acc[i].data() + amax * l, ab, cudaMemcpyHostToDevice));
     }
     CK(cudaMemcpy(r->ring, sn.ring[i].data(), sn.ring[i].size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(r->ds, &sn.ds[i], sizeof(DevScalars), cudaMemcpyHostToDevice));
@@ -1237,16 +1275,22 @@ int df_xi_search(int n, const double* dtl, const double* cost, int* xi_out, doub
 
 int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], const double hi[3],
               int G, int precision, int device, void* stream) {
-  if (!out || !n || !lo || !hi) return fail(DF_EINVAL, "null argument");
+  return df_create_ground(out, n_levels, n, n, lo, hi, G, precision, device, stream);
+}
+
+int df_create_ground(df_ctx** out, int n_levels, const int n0[3], const int n[3],
+                     const double lo[3], const double hi[3], int G, int precision, int device,
+                     void* stream) {
+  if (!out || !n0 || !n || !lo || !hi) return fail(DF_EINVAL, "null argument");
   *out = nullptr;
-  int rc = check_shape(n_levels, n, lo, hi, G, precision);  // before touching the device
+  int rc = check_shape(n_levels, n0, n, lo, hi, G, precision);  // before touching the device
   if (rc) return rc;
   CK(cudaSetDevice(device));
   df_ctx* c = new (std::nothrow) df_ctx;
   if (!c) return fail(DF_ENOMEM, "host allocation");
   c->device = device;
   c->user = (cudaStream_t)stream;
-  rc = run_create(&c->run, n_levels, n, lo, hi, G, precision);
+  rc = run_create(&c->run, n_levels, n0, n, lo, hi, G, precision);
   if (rc) {
     delete c;
     return rc;
@@ -1421,14 +1465,14 @@ int df_set_full(df_ctx* c, int level, int field, const double* in) {
 
 size_t df_state_size(const df_ctx* c) {
   if (!c || !c->run) return 0;
-  return (size_t)c->run->nl * 5 * (size_t)c->run->L[0].v.nc;
+  return (size_t)c->run->nl * 5 * c->run->nc_max;
 }
 
 int df_get_state(df_ctx* c, double* out, double* t_out) {
   if (check_ctx(c)) return DF_EINVAL;
   if (!out) return fail(DF_EINVAL, "null output");
   Run* r = c->run;
-  size_t nc = (size_t)r->L[0].v.nc;
+  size_t nc = r->nc_max;
   DevGuard g(c->device);
   enter(c);
   for (int l = 0; l < r->nl; ++l)
@@ -1445,7 +1489,7 @@ int df_set_state(df_ctx* c, const double* in, double t) {
   if (check_ctx(c)) return DF_EINVAL;
   if (!in) return fail(DF_EINVAL, "null input");
   Run* r = c->run;
-  size_t nc = (size_t)r->L[0].v.nc;
+  size_t nc = r->nc_max;
   DevGuard g(c->device);
   enter(c);
   for (int l = 0; l < r->nl; ++l)
@@ -1603,8 +1647,12 @@ int df_destroy(df_ctx* c) {
 // ------------------------------------------------------------------------ pools
 
 size_t df_run_bytes(int n_levels, const int n[3], int G, int precision) {
-  if (!n || n_levels < 1 || G < 0) return 0;
-  return run_bytes(n_levels, n, G, precision);
+  return df_run_bytes_ground(n_levels, n, n, G, precision);
+}
+
+size_t df_run_bytes_ground(int n_levels, const int n0[3], const int n[3], int G, int precision) {
+  if (!n0 || !n || n_levels < 1 || n_levels > DF_MAX_LEVELS || G < 0) return 0;
+  return run_bytes(n_levels, n0, n, G, precision);
 }
 
 int df_pool_create(df_pool** out, size_t budget, int precision, int device, void* stream) {
@@ -1635,17 +1683,23 @@ int df_pool_create(df_pool** out, size_t budget, int precision, int device, void
 
 int df_pool_admit(df_pool* p, int n_levels, const int n[3], const double lo[3],
                   const double hi[3], int G, const df_params* prm, int* slot_out) {
-  if (!p || !n || !lo || !hi || !slot_out) return fail(DF_EINVAL, "null argument");
+  return df_pool_admit_ground(p, n_levels, n, n, lo, hi, G, prm, slot_out);
+}
+
+int df_pool_admit_ground(df_pool* p, int n_levels, const int n0[3], const int n[3],
+                         const double lo[3], const double hi[3], int G, const df_params* prm,
+                         int* slot_out) {
+  if (!p || !n0 || !n || !lo || !hi || !slot_out) return fail(DF_EINVAL, "null argument");
   if (check_params(prm)) return DF_EINVAL;
-  int rc = check_shape(n_levels, n, lo, hi, G, p->prec);
+  int rc = check_shape(n_levels, n0, n, lo, hi, G, p->prec);
   if (rc) return rc;
   if (check_mirror(n_levels, lo, prm)) return DF_EINVAL;
-  size_t need = run_bytes(n_levels, n, G, p->prec);
+  size_t need = run_bytes(n_levels, n0, n, G, p->prec);
   if (p->used + need > p->budget)
     return fail(DF_EBUSY, "HBM budget: %zu used + %zu needed > %zu", p->used, need, p->budget);
   DevGuard g(p->device);
   Run* r = nullptr;
-  rc = run_create(&r, n_levels, n, lo, hi, G, p->prec);
+  rc = run_create(&r, n_levels, n0, n, lo, hi, G, p->prec);
   if (rc) return rc;
   enter(p);
   rc = DF_OK;

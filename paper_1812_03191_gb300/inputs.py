@@ -83,18 +83,23 @@ def precision(n=128, n_levels=5, half=16.0):
     return cfg
 
 
-def quadrant(n=32, n_levels=6, half=8.0, mach=3.0, **over):
+def quadrant(n=32, n_levels=6, half=8.0, mach=3.0, quarter=False, **over):
     """The set-up of Sec. 3.4 on its quadrant domain: flow along +z, the perturber
     at the corner vertex of x, y >= 0; every level spans [0, l 2^-k]^2 x
     [-l 2^-k, l 2^-k] with n/2 x n/2 x n cells.  The planes x = 0 and y = 0 are
     mirror planes (the run stands for the whole domain, whose force it reports);
-    the outer x and y faces reflect too, and both z faces hold the background."""
+    the outer x and y faces reflect too, and both z faces hold the background.
+    quarter=True: the low-Mach hierarchy of Sec. 4.1.1, a ground of n x n x 2n cells
+    over [0, l]^2 x [-l, l] and levels of n/2 x n/2 x n, the first over a quarter of
+    the ground's extent (n0 in the returned dict)."""
     p = base_params(gamma=1.4, mach=mach, flow_dir=(0.0, 0.0, 1.0), eps=0.0,
                     bc=(BC_REFLECT,) * 4 + (BC_INFLOW,) * 2)
     p.update(over)
+    nf = (n // 2, n // 2, n)
+    n0 = (n, n, 2 * n) if quarter else nf
     return dict(
-        name=f"quadrant_{n_levels}x{n // 2}x{n // 2}x{n}",
-        n_levels=n_levels, n=(n // 2, n // 2, n), lo=(0.0, 0.0, -half), hi=(half,) * 3,
+        name=f"quadrant_{n_levels}x{n // 2}x{n // 2}x{n}" + ("_quarter" if quarter else ""),
+        n_levels=n_levels, n=nf, n0=n0, lo=(0.0, 0.0, -half), hi=(half,) * 3,
         G=DEFAULT_G, params=p,
     )
 
