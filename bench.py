@@ -301,9 +301,13 @@ def run_batched(args):
     esz = 4
     per_step_bytes = 0.0
     for r in runs:
+        swept = True  # the library's choice for the FP32 state in a pool of several runs
+        if (dom == "sweep" and not swept) or (dom in ("tprep", "tflux", "tmom", "tupdate")
+                                              and swept):
+            continue
         boxes = level_step_boxes(dict(n=r["n"], G=r["G"], n_levels=r["n_levels"]))
         mult = 3 if dom in ("tprep", "tflux", "tmom", "tupdate", "sweep") else 1
-        arrays = ARRAYS_PER_ELEM[dom] + (2 if dom == "vrec_source" else 0)  # fused sweeps
+        arrays = ARRAYS_PER_ELEM[dom] + (2 if dom == "vrec_source" and swept else 0)
         per_step_bytes += arrays * esz * sum(boxes) * mult
     dom_ms, dom_n = kinds[dom]
     achieved = per_step_bytes * args.steps / (dom_ms / 1e3) / 1e9
@@ -494,6 +498,75 @@ def run_serving(args):
     return 0
 
 
+def run_paper_hierarchy(args):
+    """The paper's cold-thermal-force hierarchy (Sec. 4.2, set up as in Sec. 4.1.1):
+    the quadrant domain with mirror planes x = 0 and y = 0, a ground of 64 x 64 x 128
+    cells and 11 levels of 32 x 32 x 64, the first over a quarter of the ground,
+    l = 3200 lambda, Mach 0.1, chi = 0.1, GM = 1e-3, a cold perturber; xi = 2 on every
+    level, so one coarse step is 2^11 finest-level steps.  Graph-replayed coarse
+    steps, timed with CUDA events."""
+    import torch
+
+    from paper_1812_03191_gb300 import binding
+    if args.impl == "reference":
+        return 0
+    torch.cuda.set_device(0)
+    chi, gamma, mach = 0.1, 1.4, 0.1
+    half = 3200.0 * chi / (gamma * mach)  # l = 3200 lambda (Eq. 7)
+    cfg = I.quadrant(n=64, n_levels=12, half=half, mach=mach, quarter=True, GM=1e-3, chi=chi,
+                     L=0.0)
+    prec = binding.DF_FP64 if args.precision == "fp64" else binding.DF_FP32_STATE
+    stream = torch.cuda.current_stream()
+    sim = binding.Sim(cfg["n_levels"], cfg["n"], cfg["lo"], cfg["hi"], cfg["G"], cfg["params"],
+                      precision=prec, stream=stream.cuda_stream, n0=cfg["n0"])
+    n0, n = cfg["n0"], cfg["n"]
+    cu = n0[0] * n0[1] * n0[2] + sum(n[0] * n[1] * n[2] * 2**l for l in range(1, 12))
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    l0 = sim.kernel_launches()
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = sim.kernel_launches() - l0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    sim.set_timing(True)
+    sim.step(1)
+    kinds = {}
+    for kind in range(binding.KERNEL_KINDS):
+        kms, kn = sim.kernel_time(kind)
+        if kn:
+            kinds[binding.kernel_name(kind)] = (kms, kn)
+    sim.set_timing(False)
+    F, Fmot = sim.force()
+    bad = sim.status()[2]
+    line = {
+        "metric": METRIC, "value": cu * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == binding.DF_FP64 else "f32-state/f64-reductions",
+        "data": "synthetic",
+        "config": {"workload": "paper_hierarchy_quadrant_64x64x128+11x32x32x64",
+                   "n0": n0, "n": n, "n_levels": 12, "half_width": half, "mach": mach,
+                   "chi": chi, "GM": 1e-3, "cell_updates_per_step": cu,
+                   "l2": "not flushed (the working set, 0.3 GB, is the run itself)"},
+        "gpu_launches": launches, "launches_per_step": launches / args.steps,
+        "kernel_busy_frac": sum(v[0] for v in kinds.values()) / (ms / args.steps),
+        "kernels_ms_one_step": {k: round(v[0], 3) for k, v in sorted(kinds.items(),
+                                                                   key=lambda x: -x[1][0])},
+        "force": {"F": list(F), "F_along_motion": Fmot}, "unhealthy": bad,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,15 +575,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nested",
                     choices=["nested", "single", "precision", "batched", "serving",
-                             "precision_compare", "heating_ladder"])
+                             "precision_compare", "heating_ladder", "paper_hierarchy"])
     ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--step-cap", type=int, default=200)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--transport", default="auto", choices=["auto", "separate", "fused"],
-                    help="transport kernels: fused sweeps (default for the FP32 state) or "
-                         "separate kernels (default for FP64)")
+                    help="transport kernels: fused sweeps or separate kernels (default: "
+                         "the library's choice: fused sweeps for the FP32 state in pools and "
+                         "on levels of at least 512 Ki cells)")
     ap.add_argument("--tiles", default="auto", choices=["auto", "flat"],
                     help="tile shapes of the stencil launches: autotuned (before the "
                          "warm-up, untimed) or flat enumeration")
@@ -524,6 +598,8 @@ def main():
         return run_precision_compare(args)
     if args.workload == "heating_ladder":
         return run_heating_ladder(args)
+    if args.workload == "paper_hierarchy":
+        return run_paper_hierarchy(args)
     cfg = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, cfg)
@@ -559,8 +635,10 @@ def main():
     transport = {"auto": binding.TRANSPORT_AUTO, "separate": binding.TRANSPORT_SEPARATE,
                  "fused": binding.TRANSPORT_FUSED}[args.transport]
     sim.set_transport(transport)
+    n3 = cfg["n"] ** 3 if isinstance(cfg["n"], int) else int(np.prod(cfg["n"]))
     fused = transport == binding.TRANSPORT_FUSED or (
-        transport == binding.TRANSPORT_AUTO and prec == binding.DF_FP32_STATE)
+        transport == binding.TRANSPORT_AUTO and prec == binding.DF_FP32_STATE
+        and n3 >= 512 * 1024)  # the library's per-level choice
     shapes = sim.autotune() if args.tiles == "auto" else None
     for _ in range(args.warmup):
         sim.step(1)

@@ -192,8 +192,10 @@ int df_set_tile_shapes(df_ctx* ctx, const int* shapes);
  * quotients and fluxes are recomputed by neighbouring tiles) and ping-pongs the
  * state through a second copy; about a third of the memory traffic.  The two give
  * the same arithmetic on every active cell (equal up to the compiler's contraction
- * of multiply-adds).  DF_TRANSPORT_AUTO (default): fused for DF_FP32_STATE,
- * separate for DF_FP64, whose kernels are bound by the FP64 pipe. */
+ * of multiply-adds).  DF_TRANSPORT_AUTO (default): separate for DF_FP64 (its
+ * kernels are bound by the FP64 pipe); for DF_FP32_STATE fused in pools of several
+ * runs and, for a single run, on levels of at least 512 Ki active cells (the sweeps
+ * leave one small box short of blocks). */
 #define DF_TRANSPORT_AUTO 0
 #define DF_TRANSPORT_SEPARATE 1
 #define DF_TRANSPORT_FUSED 2

@@ -510,6 +510,23 @@ struct TileTable {
   }
 };
 
+// Transport of one level step: DF_TRANSPORT_FUSED or DF_TRANSPORT_SEPARATE as set.
+// DF_TRANSPORT_AUTO picks separate kernels for FP64, whose kernels are bound by the
+// FP64 pipe, which the halo arithmetic the sweeps repeat would load further.  For
+// the FP32 state it picks fused sweeps in pools, whose merged launches give the
+// sweeps blocks enough (and a run must get the same bits whatever it shares its
+// pool with), and for a context's levels of at least kFusedMinCells active cells.
+// A fused sweep's blocks march through whole columns, so one small box leaves the
+// GPU short of blocks: on GB300 the separate kernels win for one run of 3 x 64^3
+// levels, the sweeps from 3 x 96^3, and the sweeps win for pools of small runs.
+constexpr long long kFusedMinCells = 512 * 1024;
+
+bool sweeps_fused(int mode, int prec, const LevelView& v, bool pool) {
+  if (mode != DF_TRANSPORT_AUTO) return mode == DF_TRANSPORT_FUSED;
+  return prec == DF_FP32_STATE &&
+         (pool || (long long)v.n[0] * v.n[1] * v.n[2] >= kFusedMinCells);
+}
+
 template <class T>
 struct Builder {
   struct Entry {
@@ -520,7 +537,8 @@ struct Builder {
   int full_boxes = 0;
   const DtFinal* d_fins = nullptr;
   TileTable tiles;
-  bool fused = false;  // transport as one fused kernel per sweep
+  int transport = DF_TRANSPORT_AUTO;  // per level: fused sweeps or separate kernels
+  bool pool = false;                  // the plan steps a pool (else a context)
   mutable unsigned br = 0;  // second sub-cycles enclosing the items being added
 
   Item<T> base(const Run& r, int l) const {
@@ -623,7 +641,8 @@ struct Builder {
       if (it.L.is_child) add(out, OP_FRONTIER_DIFF, 0, it);
       add(out, OP_DIFFUSE, 0, it);
     }
-    if (P.hydro_on && fused) {
+    if (P.hydro_on &&
+        sweeps_fused(transport, sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE, it.L, pool)) {
       for (int d = 0; d < 3; ++d) {
         add(out, OP_SWEEP, d, it);
         if (it.L.is_child) add(out, OP_TFRONTIER, d, it);
@@ -773,7 +792,7 @@ int plan_upload(Plan& plan) {
 
 template <class T>
 int plan_build(Plan& plan, const std::vector<Run*>& runs, int full_boxes,
-               const TileTable& tiles, bool fused) {
+               const TileTable& tiles, int transport, bool pool) {
   plan_invalidate(plan);
   plan.prec = sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE;
   size_t nr = runs.size();
@@ -787,7 +806,8 @@ int plan_build(Plan& plan, const std::vector<Run*>& runs, int full_boxes,
   B.full_boxes = full_boxes;
   B.d_fins = plan.d_fins;
   B.tiles = tiles;
-  B.fused = fused;
+  B.transport = transport;
+  B.pool = pool;
   B.per_run.resize(nr);
   for (size_t r = 0; r < nr; ++r) B.coarse_step(*runs[r], (int)r, B.per_run[r]);
   B.merge(plan);
@@ -1076,18 +1096,10 @@ int sync_health(cudaStream_t st, Run* r) {
   return DF_OK;
 }
 
-// transport mode: DF_TRANSPORT_AUTO (fused sweeps for the FP32 state, separate
-// kernels for FP64, whose kernels are bound by the FP64 pipe and would repeat the
-// halo arithmetic), DF_TRANSPORT_SEPARATE or DF_TRANSPORT_FUSED
-bool fused_for(int mode, int prec) {
-  return mode == DF_TRANSPORT_FUSED || (mode == DF_TRANSPORT_AUTO && prec == DF_FP32_STATE);
-}
-
 int build_plan(Plan& p, const std::vector<Run*>& runs, int prec, int full_boxes,
-               const TileTable& tiles, int transport) {
-  bool f = fused_for(transport, prec);
-  return prec == DF_FP64 ? plan_build<double>(p, runs, full_boxes, tiles, f)
-                         : plan_build<float>(p, runs, full_boxes, tiles, f);
+               const TileTable& tiles, int transport, bool pool) {
+  return prec == DF_FP64 ? plan_build<double>(p, runs, full_boxes, tiles, transport, pool)
+                         : plan_build<float>(p, runs, full_boxes, tiles, transport, pool);
 }
 
 // state of the runs that tuning steps disturb (fields, scalars, force-ring cursor)
@@ -1201,7 +1213,7 @@ int autotune(const std::vector<Run*>& runs, Exec& x, int prec, int transport, Ti
     for (int o = 0; o < OP_COUNT; ++o)
       for (int d = 0; d < 3; ++d) tt.t[o][d] = tk;
     Plan p;
-    rc = build_plan(p, runs, prec, 0, tt, transport);
+    rc = build_plan(p, runs, prec, 0, tt, transport, !single_fast);
     if (!rc) rc = time_plan(p, x, prec, 0, single_fast, per);
     plan_free(p);
     for (int o = 0; o < OP_COUNT && !rc; ++o)
@@ -1221,7 +1233,7 @@ int autotune(const std::vector<Run*>& runs, Exec& x, int prec, int transport, Ti
       best_bps[o] = x.bps[o];
     }
     Plan p;
-    rc = build_plan(p, runs, prec, 0, tiles, transport);
+    rc = build_plan(p, runs, prec, 0, tiles, transport, !single_fast);
     for (int gi = 0; gi < 6 && !rc; ++gi) {
       rc = time_plan(p, x, prec, cand[gi], single_fast, per);
       for (int o = 0; o < OP_COUNT && !rc; ++o) {
@@ -1336,7 +1348,8 @@ int df_step(df_ctx* c, int n) {
   // fixed sub-cycling and the Eq. 55-56 search share one plan (xi = 2 everywhere;
   // the search drops second sub-cycles on the device), replayed from a graph
   for (int l = 0; l < r->nl; ++l) r->xi[l] = 2;
-  if (!c->plan.valid) rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles, c->transport);
+  if (!c->plan.valid)
+    rc = build_plan(c->plan, runs, r->prec, c->full_boxes, c->tiles, c->transport, false);
   if (!rc) rc = step_plan(c->plan, c->x, r->prec, n);
   leave(c);
   r->stepped = true;
@@ -1748,7 +1761,7 @@ int df_pool_step(df_pool* p, int n) {
   if (runs.empty() || n == 0) return DF_OK;
   DevGuard g(p->device);
   int rc = DF_OK;
-  if (!p->plan.valid) rc = build_plan(p->plan, runs, p->prec, 0, p->tiles, p->transport);
+  if (!p->plan.valid) rc = build_plan(p->plan, runs, p->prec, 0, p->tiles, p->transport, true);
   if (rc) return rc;
   enter(p);
   rc = step_plan(p->plan, p->x, p->prec, n);
