@@ -596,6 +596,7 @@ struct Builder {
       b.lo[d] = std::max(0, v.G - M);
       b.hi[d] = std::min(v.s[d], v.G + v.n[d] + M);
     }
+    b.set_divisors();
     return b;
   }
 

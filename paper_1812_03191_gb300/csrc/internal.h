@@ -60,8 +60,27 @@ struct Box {
   int lo[3], hi[3];
   int tile;
   int zc;  // fused sweeps: planes per chunk of the marching axis
+  // flat enumeration: element t -> plane t / (x y extent), row r / (x extent) as
+  // multiply-shifts (set by set_divisors; exact for t < 2^31)
+  unsigned long long mx, mp;
+  int sx, sp;
   long long count() const {
     return (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+  }
+  // q = floor(t / d) = (t m) >> s for every t < 2^31 with s = 31 + ceil(log2 d) and
+  // m = ceil(2^s / d): m d = 2^s + e with 0 <= e < d <= 2^(s-31), so
+  // t m / 2^s = t / d + t e / (d 2^s) and t e < 2^s keeps the error below 1 / d, too
+  // small to carry the quotient over an integer (Granlund & Montgomery, PLDI 1994)
+  static void magic(unsigned d, unsigned long long& m, int& s) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    s = 31 + l;
+    m = ((1ull << s) + d - 1) / d;
+  }
+  void set_divisors() {
+    const unsigned bx = (unsigned)(hi[0] - lo[0]), by = (unsigned)(hi[1] - lo[1]);
+    magic(bx > 0 ? bx : 1u, mx, sx);
+    magic(bx * by > 0 ? bx * by : 1u, mp, sp);
   }
 };
 

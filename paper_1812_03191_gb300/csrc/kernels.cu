@@ -32,9 +32,9 @@ __device__ __forceinline__ bool decode(const Box& b, unsigned t, int& i, int& j,
   if (b.tile == 0) {
     unsigned plane = bx * by;
     if (t >= plane * bz) return false;
-    unsigned kk = t / plane;
+    unsigned kk = (unsigned)(((unsigned long long)t * b.mp) >> b.sp);  // t / plane
     unsigned r = t - kk * plane;
-    unsigned jj = r / bx;
+    unsigned jj = (unsigned)(((unsigned long long)r * b.mx) >> b.sx);  // r / bx
     i = b.lo[0] + (int)(r - jj * bx);
     j = b.lo[1] + (int)jj;
     k = b.lo[2] + (int)kk;
