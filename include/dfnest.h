@@ -78,6 +78,22 @@ typedef struct {
                          With it on, every operator sweeps the whole padded array. */
 } df_params;
 
+/* Device memory.  By default the library allocates with cudaMalloc and frees with
+ * cudaFree.  df_set_allocator makes every context and pool created afterwards take
+ * all its device buffers from alloc(bytes, user), for example PyTorch's caching
+ * allocator.  It returns them through dealloc(ptr, user) when the owner is
+ * destroyed (or a plan buffer grows).  Each owner keeps the allocator it was
+ * created with (a pool's runs: the one current at their admission), so changing
+ * it later affects only new owners.  alloc returns NULL on failure, which the
+ * creating call reports as DF_ENOMEM.  It must return 256-byte aligned device
+ * memory of the current device; a misaligned block is handed back and reported as
+ * DF_ECUDA.  (NULL, NULL, NULL) restores cudaMalloc / cudaFree.  alloc and dealloc
+ * are set together (DF_EINVAL otherwise).  Not synchronised with concurrent
+ * df_create / df_pool_create / df_pool_admit calls. */
+typedef void* (*df_alloc_fn)(size_t bytes, void* user);
+typedef void (*df_free_fn)(void* ptr, void* user);
+int df_set_allocator(df_alloc_fn alloc, df_free_fn dealloc, void* user);
+
 typedef struct df_ctx df_ctx;
 
 /* Create a hierarchy (Sec. 3, Sec. 3.4).  n[d] % 4 == 0, n[d] >= 8, n[d] >= G; G even

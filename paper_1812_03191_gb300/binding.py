@@ -31,7 +31,7 @@ EXPORTS = (
     "df_pool_autotune", "df_pool_destroy", "df_pool_set_timing", "df_pool_kernel_time",
     "df_autotune", "df_set_tile_shapes", "df_pool_set_tile_shapes", "df_set_transport",
     "df_pool_set_transport", "df_pool_set_field", "df_create_ground", "df_run_bytes_ground",
-    "df_pool_admit_ground",
+    "df_pool_admit_ground", "df_set_allocator",
 )
 POOL_OPS = 22
 # operator order of the per-op tables (tile shapes, blocks per SM)
@@ -41,6 +41,12 @@ OP_NAMES = ("source", "compress", "frontier_diff", "diffuse", "tprep", "tflux", 
             "visc_q", "visc_v")
 TRANSPORT_AUTO, TRANSPORT_SEPARATE, TRANSPORT_FUSED = 0, 1, 2
 NOALLOC_MAX_CELLS = 4194304
+
+
+# device allocator callbacks (df_set_allocator)
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_KEEP = []  # every callback pair ever handed to the library: its owners may outlive a switch
 
 
 class DfError(RuntimeError):
@@ -120,6 +126,7 @@ def load(path: str = LIB_PATH):
         "df_last_error": (C.c_char_p, []),
         "df_check_division": (C.c_int, [dp, dp, C.c_int, dp]),
         "df_run_bytes": (C.c_size_t, [C.c_int, P(C.c_int), C.c_int, C.c_int]),
+        "df_set_allocator": (C.c_int, [vp, vp, vp]),
         "df_run_bytes_ground": (C.c_size_t, [C.c_int, P(C.c_int), P(C.c_int), C.c_int, C.c_int]),
         "df_pool_create": (C.c_int, [P(vp), C.c_size_t, C.c_int, C.c_int, vp]),
         "df_pool_admit": (C.c_int, [vp, C.c_int, P(C.c_int), dp, dp, C.c_int, P(Params),
@@ -172,6 +179,31 @@ def xi_search(dt_level, cost):
     r = C.c_double()
     _check(lib.df_xi_search(n, _dp(a), _dp(b), xi, C.byref(r)))
     return r.value, [xi[i] for i in range(n - 1)]
+
+
+def use_torch_allocator(on=True):
+    """Contexts and pools created from now on take their device memory from PyTorch's
+    caching allocator (it then shows in torch.cuda.memory_allocated and shares
+    torch's cache); on=False goes back to cudaMalloc.  Owners keep the allocator
+    they were created with."""
+    lib = load()
+    if not on:
+        _check(lib.df_set_allocator(None, None, None))
+        return
+    import torch
+
+    def _alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes))
+        except Exception:  # out of memory: the library reports DF_ENOMEM
+            return None
+
+    def _free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    pair = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _KEEP.append(pair)
+    _check(lib.df_set_allocator(C.cast(pair[0], C.c_void_p), C.cast(pair[1], C.c_void_p), None))
 
 
 def check_division(a, b):

@@ -76,6 +76,37 @@ int dfn::set_error(int code, const char* fmt, ...) {
 
 namespace {
 
+// ------------------------------------------------------------------ device memory
+
+// Where a context's or pool's device memory comes from: cudaMalloc / cudaFree, or
+// the caller's allocator (df_set_allocator), captured when the owner is created.
+struct Allocator {
+  df_alloc_fn alloc = nullptr;
+  df_free_fn dealloc = nullptr;
+  void* user = nullptr;
+};
+Allocator g_allocator;  // applies to owners created from now on
+
+cudaError_t dev_alloc(const Allocator& a, void** p, size_t bytes) {
+  if (!a.alloc) return cudaMalloc(p, bytes);
+  *p = a.alloc(bytes, a.user);
+  if (!*p) return cudaErrorMemoryAllocation;
+  if ((uintptr_t)*p % 256) {  // the kernels' planes and vector loads assume it
+    a.dealloc(*p, a.user);
+    *p = nullptr;
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+void dev_free(const Allocator& a, void* p) {
+  if (!p) return;
+  if (!a.alloc)
+    cudaFree(p);
+  else
+    a.dealloc(p, a.user);
+}
+
 // ------------------------------------------------------------------------- runs
 
 struct Run {
@@ -85,6 +116,7 @@ struct Run {
   size_t nc_max = 0;      // elements per field of the largest level
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   size_t esz = 8;
+  Allocator al;  // every device buffer of the run
   std::vector<Level> L;
   Scratch S{};
   void* scratch_mem = nullptr;
@@ -145,18 +177,19 @@ size_t run_bytes(int nl, const int n0[3], const int n[3], int G, int prec) {
 
 void run_free(Run* r) {
   if (!r) return;
+  const Allocator& a = r->al;
   for (auto& l : r->L) {
-    cudaFree(l.mem);
-    cudaFree(l.acc);
-    cudaFree(l.v.fw);
+    dev_free(a, l.mem);
+    dev_free(a, l.acc);
+    dev_free(a, l.v.fw);
   }
-  cudaFree(r->scratch_mem);
-  cudaFree(r->ds);
-  cudaFree(r->partials);
-  cudaFree(r->ring);
-  cudaFree(r->ring_pos);
-  cudaFree(r->wsum);
-  cudaFree(r->stage);
+  dev_free(a, r->scratch_mem);
+  dev_free(a, r->ds);
+  dev_free(a, r->partials);
+  dev_free(a, r->ring);
+  dev_free(a, r->ring_pos);
+  dev_free(a, r->wsum);
+  dev_free(a, r->stage);
   delete r;
 }
 
@@ -225,6 +258,7 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
   r->nl = n_levels;
   r->prec = precision;
   r->G = G;
+  r->al = g_allocator;
   r->esz = precision == DF_FP64 ? 8 : 4;
   for (int d = 0; d < 3; ++d) {
     r->n0[d] = n0[d];
@@ -284,7 +318,7 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
       const LevelView& p = r->L[l - 1].v;
       for (int d = 0; d < 3; ++d) v.off[d] = (int)std::floor((v.lo[d] - p.lo[d]) / p.dx[d] + 0.5);
     }
-    CKR(cudaMalloc(&r->L[l].mem, plane * 7));
+    CKR(dev_alloc(r->al, &r->L[l].mem, plane * 7));
     char* base = (char*)r->L[l].mem;
     for (int f = 0; f < 5; ++f) v.q[f] = base + plane * f;
     v.phi = base + plane * 5;
@@ -296,10 +330,10 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
     }
     v.acc_slots = slots;
     r->L[l].acc_elems = (size_t)18 * slots;
-    CKR(cudaMalloc(&r->L[l].acc, r->L[l].acc_elems * sizeof(double)));
+    CKR(dev_alloc(r->al, (void**)&r->L[l].acc, r->L[l].acc_elems * sizeof(double)));
     CKR(cudaMemset(r->L[l].acc, 0, r->L[l].acc_elems * sizeof(double)));
     v.acc = r->L[l].acc;
-    CKR(cudaMalloc(&v.fw, 3 * na * sizeof(double)));
+    CKR(dev_alloc(r->al, (void**)&v.fw, 3 * na * sizeof(double)));
   }
   for (int l = 0; l + 1 < n_levels; ++l) {
     LevelView& v = r->L[l].v;
@@ -314,7 +348,7 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
   }
   // scratch is shared by the levels (advanced one at a time): sized for the largest
   const size_t plane = plane_bytes(r->nc_max, r->esz);
-  CKR(cudaMalloc(&r->scratch_mem, plane * 12));
+  CKR(dev_alloc(r->al, &r->scratch_mem, plane * 12));
   CKR(cudaMemset(r->scratch_mem, 0, plane * 12));
   {
     char* b = (char*)r->scratch_mem;
@@ -328,7 +362,7 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
     for (int m = 0; m < 3; ++m) r->S.qb[1 + m] = r->S.w[m];
     r->S.qb[4] = r->S.P[0];
   }
-  CKR(cudaMalloc(&r->ds, sizeof(DevScalars)));
+  CKR(dev_alloc(r->al, (void**)&r->ds, sizeof(DevScalars)));
   CKR(cudaMemset(r->ds, 0, sizeof(DevScalars)));
   // partials: 3 per force block of every level, and one per 256 active cells of a
   // level for the luminosity normalisation (the two uses never overlap in time)
@@ -336,12 +370,12 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
   for (int l = 0; l < n_levels; ++l) np += force_partials_per_level(r->L[l].v);
   r->n_partials = np;
   size_t pelems = std::max(3 * (size_t)np, (na_max + 255) / 256);
-  CKR(cudaMalloc(&r->partials, pelems * sizeof(double)));
-  CKR(cudaMalloc(&r->ring, 3 * (size_t)r->ring_cap * sizeof(double)));
-  CKR(cudaMalloc(&r->ring_pos, sizeof(long long)));
+  CKR(dev_alloc(r->al, (void**)&r->partials, pelems * sizeof(double)));
+  CKR(dev_alloc(r->al, (void**)&r->ring, 3 * (size_t)r->ring_cap * sizeof(double)));
+  CKR(dev_alloc(r->al, (void**)&r->ring_pos, sizeof(long long)));
   CKR(cudaMemset(r->ring_pos, 0, sizeof(long long)));
-  CKR(cudaMalloc(&r->wsum, sizeof(double)));
-  CKR(cudaMalloc(&r->stage, r->nc_max * sizeof(double)));
+  CKR(dev_alloc(r->al, (void**)&r->wsum, sizeof(double)));
+  CKR(dev_alloc(r->al, (void**)&r->stage, r->nc_max * sizeof(double)));
 #undef CKR
   *out = r;
   return DF_OK;
@@ -435,14 +469,17 @@ struct Plan {
   cudaGraphExec_t gexec = nullptr;
   long long kernels = 0;
   bool valid = false;
+  Allocator al;  // the owner's
 };
 
 void plan_free(Plan& p) {
   if (p.gexec) cudaGraphExecDestroy(p.gexec);
-  cudaFree(p.d_items);
-  cudaFree(p.d_starts);
-  cudaFree(p.d_fins);
+  dev_free(p.al, p.d_items);
+  dev_free(p.al, p.d_starts);
+  dev_free(p.al, p.d_fins);
+  const Allocator al = p.al;
   p = Plan();
+  p.al = al;
 }
 
 void plan_invalidate(Plan& p) {
@@ -767,21 +804,21 @@ struct Builder {
   }
 };
 
-int grow(void** p, size_t* cap, size_t need) {
+int grow(const Allocator& a, void** p, size_t* cap, size_t need) {
   if (need <= *cap) return DF_OK;
-  cudaFree(*p);
+  dev_free(a, *p);
   *p = nullptr;
   *cap = 0;
   size_t c = std::max(need, (size_t)4096);
-  CK(cudaMalloc(p, c));
+  CK(dev_alloc(a, p, c));
   *cap = c;
   return DF_OK;
 }
 
 int plan_upload(Plan& plan) {
-  int rc = grow(&plan.d_items, &plan.cap_items, plan.items.size());
+  int rc = grow(plan.al, &plan.d_items, &plan.cap_items, plan.items.size());
   if (rc) return rc;
-  rc = grow((void**)&plan.d_starts, &plan.cap_starts, plan.starts.size() * sizeof(unsigned));
+  rc = grow(plan.al, (void**)&plan.d_starts, &plan.cap_starts, plan.starts.size() * sizeof(unsigned));
   if (rc) return rc;
   if (!plan.items.empty())
     CK(cudaMemcpy(plan.d_items, plan.items.data(), plan.items.size(), cudaMemcpyHostToDevice));
@@ -799,7 +836,7 @@ int plan_build(Plan& plan, const std::vector<Run*>& runs, int full_boxes,
   size_t nr = runs.size();
   plan.fins.resize(std::max<size_t>(nr, 1));
   for (size_t r = 0; r < nr; ++r) fill_fin(*runs[r], plan.fins[r]);
-  int rc = grow((void**)&plan.d_fins, &plan.cap_fins, plan.fins.size() * sizeof(DtFinal));
+  int rc = grow(plan.al, (void**)&plan.d_fins, &plan.cap_fins, plan.fins.size() * sizeof(DtFinal));
   if (rc) return rc;
   CK(cudaMemcpy(plan.d_fins, plan.fins.data(), plan.fins.size() * sizeof(DtFinal),
                 cudaMemcpyHostToDevice));
@@ -826,7 +863,7 @@ int plan_build_ops(Plan& plan, Run* r, const std::vector<std::pair<int, int>>& o
   plan.prec = sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE;
   plan.fins.resize(1);
   fill_fin(*r, plan.fins[0]);
-  int rc = grow((void**)&plan.d_fins, &plan.cap_fins, sizeof(DtFinal));
+  int rc = grow(plan.al, (void**)&plan.d_fins, &plan.cap_fins, sizeof(DtFinal));
   if (rc) return rc;
   CK(cudaMemcpy(plan.d_fins, plan.fins.data(), sizeof(DtFinal), cudaMemcpyHostToDevice));
   Builder<T> B;
@@ -987,6 +1024,7 @@ int plan_step(Plan& plan, Exec& x, int nsteps) {
 // run a list of ops of one run now, without a graph, and wait for it
 int run_ops_now(Run* r, Exec& x, const std::vector<std::pair<int, int>>& ops) {
   Plan p;
+  p.al = r->al;
   int rc = r->prec == DF_FP64 ? plan_build_ops<double>(p, r, ops) : plan_build_ops<float>(p, r, ops);
   if (!rc) {
     x.launches += r->prec == DF_FP64 ? plan_run<double>(p, x, false) : plan_run<float>(p, x, false);
@@ -1214,6 +1252,7 @@ int autotune(const std::vector<Run*>& runs, Exec& x, int prec, int transport, Ti
     for (int o = 0; o < OP_COUNT; ++o)
       for (int d = 0; d < 3; ++d) tt.t[o][d] = tk;
     Plan p;
+    p.al = runs.empty() ? Allocator() : runs[0]->al;
     rc = build_plan(p, runs, prec, 0, tt, transport, !single_fast);
     if (!rc) rc = time_plan(p, x, prec, 0, single_fast, per);
     plan_free(p);
@@ -1234,6 +1273,7 @@ int autotune(const std::vector<Run*>& runs, Exec& x, int prec, int transport, Ti
       best_bps[o] = x.bps[o];
     }
     Plan p;
+    p.al = runs.empty() ? Allocator() : runs[0]->al;
     rc = build_plan(p, runs, prec, 0, tiles, transport, !single_fast);
     for (int gi = 0; gi < 6 && !rc; ++gi) {
       rc = time_plan(p, x, prec, cand[gi], single_fast, per);
@@ -1308,6 +1348,7 @@ int df_create_ground(df_ctx** out, int n_levels, const int n0[3], const int n[3]
     delete c;
     return rc;
   }
+  c->plan.al = c->run->al;
   if (!exec_init(c->x, device) ||
       cudaStreamCreateWithFlags(&c->x.st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -1669,6 +1710,15 @@ size_t df_run_bytes_ground(int n_levels, const int n0[3], const int n[3], int G,
   return run_bytes(n_levels, n0, n, G, precision);
 }
 
+int df_set_allocator(df_alloc_fn alloc, df_free_fn dealloc, void* user) {
+  if ((alloc == nullptr) != (dealloc == nullptr))
+    return fail(DF_EINVAL, "alloc and dealloc are set together");
+  g_allocator.alloc = alloc;
+  g_allocator.dealloc = dealloc;
+  g_allocator.user = alloc ? user : nullptr;
+  return DF_OK;
+}
+
 int df_pool_create(df_pool** out, size_t budget, int precision, int device, void* stream) {
   if (!out) return fail(DF_EINVAL, "null argument");
   *out = nullptr;
@@ -1681,6 +1731,7 @@ int df_pool_create(df_pool** out, size_t budget, int precision, int device, void
   p->prec = precision;
   p->budget = budget;
   p->user = (cudaStream_t)stream;
+  p->plan.al = g_allocator;
   bool ok = exec_init(p->x, device);
   // every pool launch goes through the work-list kernel, so a run's arithmetic is
   // the same alone in a pool and in any mix of runs (bitwise)
