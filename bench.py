@@ -417,6 +417,7 @@ def run_heating_ladder(args):
         out = ladder.run(levels=(4, 5, 6, 7), sample_every=8)
         low = ladder.low_mach(mach=0.1)
         cold = ladder.cold_thermal(mach=0.1)
+        paper = ladder.paper_cold_thermal(n_levels=10)
     pred = out["predicted_increment"]
     ratios = {k: v / pred for k, v in out["increments"].items()}
     line = {
@@ -435,6 +436,11 @@ def run_heating_ladder(args):
         "cold_thermal_low_mach": {"mach": 0.1, "levels": 6, "force": cold["runs"][6]["final"],
                                   "eq51_times_eq23_share": cold["expected"],
                                   "ratio": cold["ratio"]},
+        "cold_thermal_paper_geometry": {
+            "mach": 0.1, "levels": 10, "box_half_width": paper["half"],
+            "geometry": "quadrant, ground 64x64x128, levels 32x32x64, first over a quarter",
+            "force": paper["final"], "eq51_times_eq23_share": paper["expected"],
+            "ratio": paper["ratio"], "wall_s": paper["wall_s"]},
         "pool_cell_updates_per_s": out["cell_updates"] / out["wall_s"],
         "wall_s": out["wall_s"], "clocks": clk.summary(),
     }

@@ -187,3 +187,54 @@ def cold_thermal(mach=0.1, n_levels=6, chi=0.1, GM=1e-3, gamma=1.4, n=32, t_end_
     out["expected"] = out["eq51_force"] * share
     out["ratio"] = r["final"] / out["expected"]
     return out
+
+
+def paper_cold_thermal(mach=0.1, n_levels=10, chi=0.1, GM=1e-3, gamma=1.4, n=64,
+                       box_lambdas=3200.0, t_end_taus=100.0,
+                       precision=binding.DF_FP32_STATE, sample_every=8):
+    """Cold thermal force (Sec. 4.2) in the paper's own geometry for it: the quadrant
+    domain with mirror planes x = 0 and y = 0, a ground of n x n x 2n cells and
+    levels of n/2 x n/2 x n, the first over a quarter of the ground (Sec. 4.1.1),
+    l = box_lambdas lambda.  A cold perturber with diffusion minus the same in an
+    adiabatic gas, both stepped with the same fixed coarse step to t_end_taus tau,
+    against -(gamma - 1)/2 F0 (Eq. 51) times the Eq. 23 share of the box and the
+    finest cell.  The two runs are contexts, stepped alternately."""
+    lam_ = lam(chi, gamma, mach)
+    half = box_lambdas * lam_
+    q = I.quadrant(n=n, n_levels=n_levels, half=half, mach=mach, quarter=True, GM=GM,
+                   chi=chi, L=0.0, gamma=gamma)
+    cold = q["params"]
+    adiabatic = dict(cold, chi=0.0)
+    dt = fixed_dt(n_levels, 2 * n, half, cold)  # the ground's cell is half / n
+    sims = [binding.Sim(n_levels, q["n"], q["lo"], q["hi"], q["G"], dict(p, dt_fixed=dt),
+                        precision=precision, n0=q["n0"]) for p in (cold, adiabatic)]
+    d = np.asarray(cold["flow_dir"], dtype=float)
+    t_end = t_end_taus * tau(chi, gamma, mach)
+    ts, F = [], []
+    t0 = time.perf_counter()
+    t = 0.0
+    steps = 0
+    while t < t_end:
+        for s in sims:
+            s.step(sample_every)
+        steps += sample_every
+        fa, fb = (-float(np.dot(s.force()[0], d)) for s in sims)
+        t = sims[0].status()[0]
+        if sims[0].status()[2] or sims[1].status()[2]:
+            raise RuntimeError("unhealthy state")
+        ts.append(t)
+        F.append(fa - fb)
+    wall = time.perf_counter() - t0
+    for s in sims:
+        s.close()
+    ts, F = np.array(ts), np.array(F)
+    finest_dx = half / n / 2 ** (n_levels - 1)
+    share = h_fraction(half / (2.0 * lam_)) - h_fraction(finest_dx / (2.0 * lam_))
+    F0 = 4.0 * math.pi * GM * GM
+    final = float(F[ts >= 0.9 * ts[-1]].mean())
+    expected = -(gamma - 1.0) / 2.0 * F0 * share
+    return dict(mach=mach, n_levels=n_levels, half=half, dt=dt, steps=steps, t=ts.tolist(),
+                F=F.tolist(), final=final, finest_dx=finest_dx, eq23_share=share,
+                eq51_force=-(gamma - 1.0) / 2.0 * F0, expected=expected,
+                ratio=final / expected, wall_s=wall)
+

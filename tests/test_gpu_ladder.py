@@ -60,3 +60,17 @@ def test_low_mach_cold_thermal_force_is_a_drag_of_the_eq51_order():
     F = np.array(out["runs"][6]["F"])
     late = F[len(F) // 2:]
     assert F[-1] < 0 and np.abs(late - F[-1]).max() <= 0.1 * abs(F[-1])  # a settled drag
+
+
+def test_cold_thermal_force_in_the_papers_geometry():
+    """Sec. 4.2 in the geometry the paper uses for it: the quadrant domain with its
+    mirror planes, a ground of 64 x 64 x 128 under levels of 32 x 32 x 64 (the first
+    over a quarter of the ground), l = 3200 lambda, here 9 levels, Mach 0.1, 100 tau.
+    The paper matches the V -> 0 value -(gamma - 1)/2 F0 to within a few per cent.
+    Measured: 0.992 of it times the Eq. 23 share of this box and finest cell (0.993
+    and 0.994 with 10 and 11 levels)."""
+    out = ladder.paper_cold_thermal(n_levels=9)
+    assert 0.97 < out["ratio"] < 1.03, out["ratio"]
+    F = np.array(out["F"])
+    assert F[-1] < 0 and np.abs(F[len(F) // 2:] - F[-1]).max() <= 0.1 * abs(F[-1])
+
