@@ -12,10 +12,11 @@ logarithm of Eq. 13), independent of the level count.
 Set-up (Sec. 4 and 4.1): gamma = 1.4, rho0 = c_s = 1, GM = 1e-3, chi = 0.1,
 L = 2e-4, no softening, the energy L dt split over the eight cells around the
 perturber's vertex, a coarse box [-l, l]^3 with l = 100 lambda and
-lambda = chi / (gamma V) (Eq. 7), n = 32 cells per level and axis (the paper's
-16 x 16 x 32 quadrant meshes over [0, l]^2 x [-l, l], here as a full box, so that
-6 levels reach its finest cell of 25/128 lambda), run to 100 tau with
-tau = chi / (gamma^2 V^2) (Eq. 9).
+lambda = chi / (gamma V) (Eq. 7), n = 32 cells per level and axis, so that 6 levels
+reach the paper's finest cell of 25/128 lambda, run to 100 tau with
+tau = chi / (gamma^2 V^2) (Eq. 9).  quadrant=True runs the paper's own 16 x 16 x 32
+quadrant meshes over [0, l]^2 x [-l, l] with mirror planes x = 0 and y = 0 and the
+flow along +z (the same cells, a quarter of the work).
 """
 from __future__ import annotations
 
@@ -67,23 +68,39 @@ def fixed_dt(n_levels, n, half, params, safety=0.8):
     return safety * best
 
 
-def setup(mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32, box_lambdas=100.0):
-    """parameter dicts of the hot and cold runs and the coarse half-width"""
+def setup(mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32, box_lambdas=100.0,
+          quadrant=False):
+    """parameter dicts of the hot and cold runs and the coarse half-width; with
+    quadrant=True the flow is along +z and the planes x = 0, y = 0 are mirror planes
+    (the paper's n/2 x n/2 x n quadrant meshes, Sec. 3.4)"""
     half = box_lambdas * lam(chi, gamma, mach)
     base = I.base_params(gamma=gamma, rho0=1.0, cs=1.0, mach=mach, GM=GM, eps=0.0, chi=chi,
                          L=0.0, lum_sigma=0.0)
+    if quadrant:
+        base = I.quadrant(n=n, n_levels=1, half=half, mach=mach, gamma=gamma, GM=GM, eps=0.0,
+                          chi=chi, L=0.0, lum_sigma=0.0)["params"]
     hot = dict(base, L=L)
     cold = dict(base, L=0.0)
     return hot, cold, half
 
 
+def geometry(n, half, quadrant):
+    """cells per axis and box of every level: a full box of n^3, or the quadrant's
+    n/2 x n/2 x n over [0, l]^2 x [-l, l] (the same cells)"""
+    if quadrant:
+        return (n // 2, n // 2, n), (0.0, 0.0, -half), (half,) * 3
+    return (n, n, n), (-half,) * 3, (half,) * 3
+
+
 def low_mach(mach=0.1, n_levels=6, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32,
-             t_end_taus=100.0, precision=binding.DF_FP32_STATE, sample_every=8):
+             t_end_taus=100.0, precision=binding.DF_FP32_STATE, sample_every=8,
+             quadrant=False):
     """One hot/cold pair at low Mach (Sec. 4.1.1): the heating force against Eq. 8
     times the share h(r'_max) - h(r'_min) of Eq. 23 that the box (r'_max = l / 2
     lambda) and the finest cell (r'_min = dx / 2 lambda) can hold."""
     out = run(levels=(n_levels,), mach=mach, chi=chi, GM=GM, L=L, gamma=gamma, n=n,
-              t_end_taus=t_end_taus, precision=precision, sample_every=sample_every)
+              t_end_taus=t_end_taus, precision=precision, sample_every=sample_every,
+              quadrant=quadrant)
     lam_ = lam(chi, gamma, mach)
     r = out["runs"][n_levels]
     rp_min = r["finest_dx"] / (2.0 * lam_)
@@ -97,17 +114,17 @@ def low_mach(mach=0.1, n_levels=6, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32,
 
 
 def pairs(levels, pa, pb, half, n=32, t_end=1.0, precision=binding.DF_FP32_STATE,
-          sample_every=8, budget=32 << 30):
+          sample_every=8, budget=32 << 30, quadrant=False):
     """Runs with parameters pa and pb for every level count, one pool, the same fixed
     coarse step per level count (from pa's limits); the history of F_a - F_b along
     the motion and its final value (mean over the last tenth of the run)."""
-    lo, hi = (-half,) * 3, (half,) * 3
+    nn, lo, hi = geometry(n, half, quadrant)
     pool = binding.Pool(budget, precision=precision)
     runs = {}
     for nl in levels:
         dt = fixed_dt(nl, n, half, pa)
-        sa = pool.admit(nl, n, lo, hi, I.DEFAULT_G, dict(pa, dt_fixed=dt))
-        sb = pool.admit(nl, n, lo, hi, I.DEFAULT_G, dict(pb, dt_fixed=dt))
+        sa = pool.admit(nl, nn, lo, hi, I.DEFAULT_G, dict(pa, dt_fixed=dt))
+        sb = pool.admit(nl, nn, lo, hi, I.DEFAULT_G, dict(pb, dt_fixed=dt))
         if sa is None or sb is None:
             raise RuntimeError("the runs do not fit the pool budget")
         runs[nl] = dict(slots=(sa, sb), dt=dt, steps=0, t=[], F=[], done=False)
@@ -123,7 +140,7 @@ def pairs(levels, pa, pb, half, n=32, t_end=1.0, precision=binding.DF_FP32_STATE
                 continue
             sa, sb = p["slots"]
             p["steps"] += sample_every
-            cell_updates += 2 * sample_every * n**3 * (2**nl - 1)
+            cell_updates += 2 * sample_every * nn[0] * nn[1] * nn[2] * (2**nl - 1)
             if q[sa, 5] != 0 or q[sb, 5] != 0:
                 raise RuntimeError(f"{nl} levels: unhealthy state")
             if q[sa, 3] != q[sb, 3]:
@@ -152,13 +169,14 @@ def pairs(levels, pa, pb, half, n=32, t_end=1.0, precision=binding.DF_FP32_STATE
 
 def run(levels=(4, 5, 6, 7), mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32,
         t_end_taus=100.0, precision=binding.DF_FP32_STATE, sample_every=4,
-        budget=32 << 30):
+        budget=32 << 30, quadrant=False):
     """Heating force (hot minus cold run, Eq. 5) for every level count, stepped to
     t_end = t_end_taus * tau, with the increments between successive level counts
     and the Eq. 24 prediction."""
-    hot, cold, half = setup(mach, chi, GM, L, gamma, n)
+    hot, cold, half = setup(mach, chi, GM, L, gamma, n, quadrant=quadrant)
     out = pairs(levels, hot, cold, half, n=n, t_end=t_end_taus * tau(chi, gamma, mach),
-                precision=precision, sample_every=sample_every, budget=budget)
+                precision=precision, sample_every=sample_every, budget=budget,
+                quadrant=quadrant)
     out["predicted_increment"] = eq24_increment(gamma, GM, L, chi, mach)
     for r in out["runs"].values():
         r["F_heating"] = r.pop("F")
