@@ -146,10 +146,10 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) per box element of a launch, from the ncu captures in
 # profiles/ (k_sweeps_nested_3x64_fp64.md: tmom, 80^3 box, 20.1 MB;
-# k_sweep_fused_precision_5x128_fp32.md: fused sweeps, 144^3 box, 86.9 / 97.7 / 83.9 MB);
+# k_sweep_fused_precision_5x128_fp32.md: fused sweeps, 144^3 box, 86.8 / 94.4 / 81.4 MB);
 # `traffic` scales them to the mean box of the timed launches
 TRAFFIC_PER_ELEM = {("nested_3x64^3_fp64", 8, "tmom"): 20.1e6 / 80**3,
-                    ("precision_5x128^3", 4, "sweep"): (86.9e6 + 97.7e6 + 83.9e6) / 3 / 144**3}
+                    ("precision_5x128^3", 4, "sweep"): (86.8e6 + 94.4e6 + 81.4e6) / 3 / 144**3}
 
 
 def level_step_boxes(cfg):
