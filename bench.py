@@ -562,7 +562,8 @@ def run_paper_hierarchy(args):
                    "chi": chi, "GM": 1e-3, "cell_updates_per_step": cu,
                    "l2": "not flushed (the working set, 0.3 GB, is the run itself)"},
         "gpu_launches": launches, "launches_per_step": launches / args.steps,
-        "kernel_busy_frac": sum(v[0] for v in kinds.values()) / (ms / args.steps),
+        # one step with an event pair around every launch (no graph): the shares, not
+        # the sum, are comparable with ms_per_step
         "kernels_ms_one_step": {k: round(v[0], 3) for k, v in sorted(kinds.items(),
                                                                    key=lambda x: -x[1][0])},
         "force": {"F": list(F), "F_along_motion": Fmot}, "unhealthy": bad,
