@@ -160,12 +160,14 @@ size_t run_bytes(int nl, const int n0[3], const int n[3], int G, int prec) {
   for (int l = 0; l < nl; ++l) {
     const int* m = level_n(l, n0, n);
     size_t nc = level_elems(m, G), na = (size_t)m[0] * m[1] * m[2];
+    const int sp[3] = {m[0] + 2 * G, m[1] + 2 * G, m[2] + 2 * G};
     int slots = 0;
     for (int d = 0; d < 3; ++d) {
       int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
       slots = std::max(slots, (m[t1] / 2) * (m[t2] / 2));
     }
-    total += plane_bytes(nc, esz) * 7 + 18 * (size_t)slots * 8 + 3 * na * 8;
+    total += plane_bytes(nc, esz) * 7 + ((size_t)rec_elems(sp) + 18 * (size_t)slots) * 8 +
+             3 * na * 8;
     np += (na + 2047) / 2048;
     nc_max = std::max(nc_max, nc);
     na_max = std::max(na_max, na);
@@ -329,7 +331,7 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
       slots = std::max(slots, (n[t1] / 2) * (n[t2] / 2));
     }
     v.acc_slots = slots;
-    r->L[l].acc_elems = (size_t)18 * slots;
+    r->L[l].acc_elems = (size_t)rec_elems(v.s) + (size_t)18 * slots;
     CKR(dev_alloc(r->al, (void**)&r->L[l].acc, r->L[l].acc_elems * sizeof(double)));
     CKR(cudaMemset(r->L[l].acc, 0, r->L[l].acc_elems * sizeof(double)));
     v.acc = r->L[l].acc;
@@ -343,7 +345,9 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
       v.coff[d] = ch.off[d];
       v.cn[d] = ch.n[d];
     }
-    v.cacc = ch.acc;
+    v.crec = ch.acc;
+    v.csum = ch.acc + rec_elems(ch.s);
+    v.cacc = v.csum;
     v.cacc_slots = ch.acc_slots;
   }
   // scratch is shared by the levels (advanced one at a time): sized for the largest
@@ -577,6 +581,7 @@ struct Builder {
   int transport = DF_TRANSPORT_AUTO;  // per level: fused sweeps or separate kernels
   bool pool = false;                  // the plan steps a pool (else a context)
   mutable unsigned br = 0;  // second sub-cycles enclosing the items being added
+  mutable int sub_of[DF_MAX_LEVELS] = {};  // sub-cycle of each level being added
 
   Item<T> base(const Run& r, int l) const {
     Item<T> it;
@@ -597,6 +602,7 @@ struct Builder {
     for (int d = 0; d < 3; ++d) it.V[d] = r.P.V[d];
     it.dt_fixed = r.P.dt_fixed;
     it.level = l;
+    it.sub = sub_of[l];
     it.band = r.P.band;
     int fl = 0;
     if (r.P.hydro_on) fl |= FL_HYDRO | FL_SS3 | FL_WRITE_PI;
@@ -683,7 +689,6 @@ struct Builder {
         sweeps_fused(transport, sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE, it.L, pool)) {
       for (int d = 0; d < 3; ++d) {
         add(out, OP_SWEEP, d, it);
-        if (it.L.is_child) add(out, OP_TFRONTIER, d, it);
       }
       Item<T> vr = it;
       vr.flags |= FL_FUSED;
@@ -692,7 +697,6 @@ struct Builder {
       for (int d = 0; d < 3; ++d) {
         add(out, OP_TPREP, 0, it);
         add(out, OP_TFLUX, d, it);
-        if (it.L.is_child) add(out, OP_TFRONTIER, d, it);
         add(out, OP_TMOM, d, it);
         add(out, OP_TUPDATE, d, it);
       }
@@ -702,16 +706,19 @@ struct Builder {
 
   void advance(const Run& r, int l, int m_out, std::vector<Entry>& out) const {
     if (l + 1 < r.nl) {
-      add(out, OP_ZERO_ACC, 0, base(r, l + 1));
       int xi = r.xi[l];
       for (int s = 0; s < xi; ++s) {
         // the second sub-cycle (and all it encloses) is dropped on the device when
-        // the Eq. 55-56 search picks xi_l = 1; the first keeps the margin of two
+        // the Eq. 55-56 search picks xi_l = 1; the first keeps the margin of two.
+        // Each sub-cycle writes its own part of the child's CommFlux record, so the
+        // record needs no clearing: the parent sums the parts of the sub-cycles run.
         const unsigned saved = br;
         if (s == 1) br |= 1u << l;
+        sub_of[l + 1] = s;
         advance(r, l + 1, (xi - 1 - s) * kReach, out);
         br = saved;
       }
+      sub_of[l + 1] = 0;
     }
     level_step(r, l, m_out, out);
     if (l + 1 < r.nl) {

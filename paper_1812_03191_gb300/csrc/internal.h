@@ -26,13 +26,17 @@ struct LevelView {
   void* phi;          // potential at cell centres (Eq. 16)
   void* lumw;         // luminosity weight / cell volume on active cells
   double* fw;         // static force weights GM V_c / (r^2 + eps^2)^(3/2), active cells
-  double* acc;        // frontier flux sums of this level as a child: [side][quantity][slot]
-  int acc_slots;      // slots per (side, quantity) block
+  double* acc;        // frontier fluxes of this level as a child (CommFlux record, see
+                      // rec_index): mass, transported energy, diffused energy; followed
+                      // by their sums per coarse slot [side][quantity][slot]
+  int acc_slots;      // coarse slots per (side, quantity) of the sums
   // child geometry (coarse frontier overwrite, covered mask), has_child = 0 if none
   int has_child;
   int coff[3], cn[3];
-  const double* cacc;
+  const double* cacc;  // the child's sums (read by the frontier substitutions)
   int cacc_slots;
+  const double* crec;  // the child's record, summed into csum (= cacc) by the parent
+  double* csum;
   int is_child;
   // bit d: the lower d-face of the domain is a mirror plane through the perturber
   // (coordinate 0, reflecting) and the run stands for the domain unfolded across it;
@@ -221,7 +225,26 @@ struct __align__(16) Item {
   unsigned count;       // index-space size of the item
   unsigned br;          // bit m: inside the second sub-cycle of level m + 1 (skipped
                         // when the search chose xi_m = 1)
+  int sub;              // sub-cycle of this level step within its parent step (0, 1)
+  int pad_;
 };
+
+// CommFlux record of a child level (Sec. 3.2.3): for each axis d, the faces of its
+// two frontier planes at every transverse position of the padded array (s_t1 x s_t2,
+// so a writer needs no bounds test), per side, quantity (mass, transported energy,
+// diffused energy) and sub-cycle.  Axis blocks x, y, z one after the other.
+__host__ __device__ inline int rec_index(const int s[3], int d, int side, int q, int sub, int c1,
+                                         int c2) {
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  int off = 0;
+  if (d >= 1) off += 12 * s[1] * s[2];
+  if (d >= 2) off += 12 * s[0] * s[2];
+  return off + (((side * 3 + q) * 2 + sub) * s[t2] + c2) * s[t1] + c1;
+}
+
+__host__ __device__ inline long long rec_elems(const int s[3]) {
+  return 12LL * ((long long)s[1] * s[2] + (long long)s[0] * s[2] + (long long)s[0] * s[1]);
+}
 
 // ---- kernels.cu: all asynchronous on `st`; return the number of kernels launched.
 // host_item (nullable): host copy of the item when nitems == 1; such a launch

@@ -280,6 +280,47 @@ __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b
   }
 }
 
+// CommFlux record (Sec. 3.2.3).  A child level writes the flux through each of its
+// frontier faces into its record (rec_index), once per sub-cycle; the parent sums the
+// entries of a coarse face when it substitutes its own frontier flux, in a fixed
+// order: sub-cycle, then the fine faces (u, v) = (0,0), (1,0), (0,1), (1,1).  The
+// record is written, never accumulated, so it needs no clearing, and the sub-cycles
+// run decide what is summed.
+
+// record a child's flux through the frontier face with index f along d (f = G or
+// G + n_d) at transverse position (c1, c2) of the padded array
+__device__ __forceinline__ void fr_put(const LevelView& L, int d, int f, int c1, int c2, int q,
+                                       int sub, double v) {
+  L.acc[rec_index(L.s, d, f == L.G ? 0 : 1, q, sub, c1, c2)] = v;
+}
+
+// The parent's substitute for its frontier faces: at the start of its level step
+// (in the compression kernel, which every level step that has a consumer runs) one
+// thread per (side, quantity, coarse slot) sums the child's record over the
+// sub-cycles the child ran (one when the Eq. 55-56 search dropped the second) and
+// the 4 fine faces, and the consumers read the sum with one load.
+__device__ __forceinline__ void fr_sums(const LevelView& L, const DevScalars* ds, int level,
+                                        unsigned tid) {
+  if (tid >= 18u * (unsigned)L.cacc_slots) return;
+  const int blk = (int)tid / L.cacc_slots, slot = (int)tid - blk * L.cacc_slots;
+  const int side = blk / 3, q = blk - 3 * side, d = side >> 1;
+  const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  const int h1 = L.cn[t1] >> 1;
+  if (slot >= h1 * (L.cn[t2] >> 1)) return;
+  const int a = slot % h1, b = slot / h1;
+  const int cs[3] = {L.cn[0] + 2 * L.G, L.cn[1] + 2 * L.G, L.cn[2] + 2 * L.G};
+  const bool two = ((ds->xi1 >> level) & 1u) == 0u;
+  double sum = 0.0;
+  for (int sub = 0; sub < (two ? 2 : 1); ++sub)
+#pragma unroll
+    for (int v = 0; v < 2; ++v)
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        sum += L.crec[rec_index(cs, d, side & 1, q, sub, L.G + 2 * a + u, L.G + 2 * b + v)];
+  L.csum[blk * L.cacc_slots + slot] = sum;
+}
+
+
 // --------------------------------------------------------------- diffusion
 // energy moved in +d across a face during dt: -chi rho_f d(e/rho)/dx * area * dt
 template <class T>
@@ -323,60 +364,35 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
   e[c] = e[c] - div * g.inv_vol;
 }
 
-// fine frontier faces of one side: the 4 faces of one coarse slot, accumulated in
-// the order (u,v) = (0,0), (1,0), (0,1), (1,1)
-__device__ __forceinline__ void fine_face(const LevelView& L, int side, int a, int b, int u,
-                                          int v, int& f) {
-  int d = side >> 1, hi = side & 1;
-  int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-  int c3[3];
-  c3[d] = L.G + (hi ? L.n[d] : 0);
-  c3[t1] = L.G + 2 * a + u;
-  c3[t2] = L.G + 2 * b + v;
-  f = (c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0];
-}
-
-__device__ __forceinline__ bool slot_of(const LevelView& L, long long t, int sides_lo,
-                                        int n_sides, int& side, int& a, int& b) {
-  // slots are laid out side-major; every side of axis d has (n_t1/2)*(n_t2/2) slots
-  int rem = (int)t;
-  for (int s = sides_lo; s < sides_lo + n_sides; ++s) {
-    int d = s >> 1;
-    int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    int h1 = L.n[t1] >> 1, h2 = L.n[t2] >> 1;
-    if (rem < h1 * h2) {
-      side = s;
-      a = rem % h1;
-      b = rem / h1;
-      return true;
-    }
-    rem -= h1 * h2;
-  }
-  return false;
-}
-
+// CommFlux record of the diffusive energy fluxes through a child's frontier faces:
+// one thread per (side, coarse slot) evaluates its 4 fine faces (a launch of its own:
+// inside the diffusion kernel the record code would cost that kernel occupancy)
 template <class T>
 __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scratch& S,
-                                                          const T* __restrict__ dtp, T chi,
-                                                          T rho0, int dfr, const Geo<T>& g, unsigned tid) {
-  int side, a, b;
-  if (!slot_of(L, tid, 0, 6, side, a, b)) return;
+                                                 const T* __restrict__ dtp, T chi, T rho0,
+                                                 int dfr, const Geo<T>& g, int sub,
+                                                 unsigned tid) {
+  if (tid >= 6u * (unsigned)L.acc_slots) return;
+  const int side = (int)tid / L.acc_slots, slot = (int)tid - side * L.acc_slots;
+  const int d = side >> 1, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  const int h1 = L.n[t1] >> 1;
+  if (slot >= h1 * (L.n[t2] >> 1)) return;
+  const int a = slot % h1, b = slot / h1;
   const T dt = dtp[0];
-  const int d = side >> 1;
-  const int t1 = d == 0 ? 1 : 0;
-  const int slot = b * (L.n[t1] >> 1) + a;
-  double* acc = L.acc + (side * 3 + 2) * L.acc_slots + slot;
-  double s = *acc;
+  const int fd = (side & 1) ? L.G + L.n[d] : L.G;
 #pragma unroll
   for (int v = 0; v < 2; ++v)
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
-      int f;
-      fine_face(L, side, a, b, u, v, f);
-      s += (double)diff_flux(L, g, (const T*)L.q[F_RHO], (const T*)S.eps, f, d, chi, dt, rho0,
-                             dfr);
+      int f3[3];
+      f3[d] = fd;
+      f3[t1] = L.G + 2 * a + u;
+      f3[t2] = L.G + 2 * b + v;
+      const int f = (f3[2] * L.s[1] + f3[1]) * L.s[0] + f3[0];
+      fr_put(L, d, fd, f3[t1], f3[t2], 2, sub,
+             (double)diff_flux(L, g, (const T*)L.q[F_RHO], (const T*)S.eps, f, d, chi, dt, rho0,
+                               dfr));
     }
-  *acc = s;
 }
 
 // --------------------------------------------------------------- transport
@@ -406,7 +422,8 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
 // fixed kernel-parameter operand instead of a dynamically indexed load
 template <class T, int d>
 __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const Scratch& S,
-                                                  const T* __restrict__ dtp, const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
+                                                  const T* __restrict__ dtp, const Bg<T>& bg,
+                                                  const Geo<T>& g, int sub, unsigned tid) {
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
@@ -427,29 +444,11 @@ __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const
   }
   ((T*)S.F)[c] = Fv;
   ((T*)S.E)[c] = Ev;
-}
-
-// child frontier capture of the transport fluxes of axis d (sides 2d, 2d+1)
-template <class T>
-__device__ __forceinline__ void el_tfrontier(const LevelView& L, const Scratch& S, int d, unsigned tid) {
-  int side, a, b;
-  if (!slot_of(L, tid, 2 * d, 2, side, a, b)) return;
-  const int t1 = d == 0 ? 1 : 0;
-  const int slot = b * (L.n[t1] >> 1) + a;
-  double* accF = L.acc + (side * 3 + 0) * L.acc_slots + slot;
-  double* accE = L.acc + (side * 3 + 1) * L.acc_slots + slot;
-  double sF = *accF, sE = *accE;
-#pragma unroll
-  for (int v = 0; v < 2; ++v)
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      int f;
-      fine_face(L, side, a, b, u, v, f);
-      sF += (double)((const T*)S.F)[f];
-      sE += (double)((const T*)S.E)[f];
-    }
-  *accF = sF;
-  *accE = sE;
+  if (L.is_child && (c3[d] == L.G || c3[d] == L.G + L.n[d])) {  // CommFlux record
+    constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+    fr_put(L, d, c3[d], c3[t1], c3[t2], 0, sub, (double)Fv);
+    fr_put(L, d, c3[d], c3[t1], c3[t2], 1, sub, (double)Ev);
+  }
 }
 
 // staggered momentum fluxes of sweep d
@@ -489,7 +488,8 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
 }
 
 template <class T, int d>
-__device__ __forceinline__ void el_tupdate(const LevelView& L, const Box& b, const Scratch& S, const Geo<T>& g, unsigned tid) {
+__device__ __forceinline__ void el_tupdate(const LevelView& L, const Box& b, const Scratch& S,
+                                           const Geo<T>& g, unsigned tid) {
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
@@ -681,9 +681,9 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
       Fw[0] = Fw[1]; Fw[1] = Fv;
       Ew[0] = Ew[1]; Ew[1] = Evv;
       if (L.is_child && owned && f >= m0 && f < m1 && (f == L.G || f == L.G + L.n[d])) {
-        const int c = cxr + f * stM;
-        ((T*)S.F)[c] = Fv;
-        ((T*)S.E)[c] = Evv;
+        // CommFlux record: transverse axes x and the row axis
+        fr_put(L, d, f, x, row, 0, it.sub, (double)Fv);
+        fr_put(L, d, f, x, row, 1, it.sub, (double)Evv);
       }
       // rho_r, v_{r-1}, F_{r-1} of the row below (shared) and of x - 1 (shuffle)
       T* xb = xch + (i & 1) * 3 * NT;
@@ -790,9 +790,9 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
         Evv = bg.eps0 * Fv + des * (F0 + Fv);
       }
       if (L.is_child && owned && r >= m0 && r < m1 && (x == L.G || x == L.G + L.n[0])) {
-        const int c = cxr + r * stM;
-        ((T*)S.F)[c] = Fv;
-        ((T*)S.E)[c] = Evv;
+        // CommFlux record: transverse axes y (the row) and z (the march)
+        fr_put(L, 0, x, row, r, 0, it.sub, (double)Fv);
+        fr_put(L, 0, x, row, r, 1, it.sub, (double)Evv);
       }
       // rho, v_x, F of the row below
       T* xb = xch + (i & 1) * 3 * NT;
@@ -1601,21 +1601,21 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
   if (OP == OP_SOURCE)
     el_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.flags & FL_WRITE_PI, it.gm1, it.bg, it.g,
                  tid);
-  else if (OP == OP_COMPRESS)
+  else if (OP == OP_COMPRESS) {
+    if (it.L.has_child) fr_sums(it.L, it.ds, it.level, tid);  // before any consumer
     el_compress_lum<T>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.lum, it.flags & FL_SS3,
                        it.flags & FL_LUM, it.flags & FL_EPS, it.bg, it.g, tid);
+  }
   else if (OP == OP_FRONTIER_DIFF)
     el_frontier_diff<T>(it.L, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
-                        tid);
+                        it.sub, tid);
   else if (OP == OP_DIFFUSE)
     el_diffuse<T>(it.L, it.b, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
                   tid);
   else if (OP == OP_TPREP)
     el_tprep<T>(it.L, it.b, it.S, it.bg, tid);
   else if (OP == OP_TFLUX)
-    el_tflux<T, D>(it.L, it.b, it.S, (const T*)it.dt, it.bg, it.g, tid);
-  else if (OP == OP_TFRONTIER)
-    el_tfrontier<T>(it.L, it.S, D, tid);
+    el_tflux<T, D>(it.L, it.b, it.S, (const T*)it.dt, it.bg, it.g, it.sub, tid);
   else if (OP == OP_TMOM)
     el_tmom<T, D>(it.L, it.b, it.S, (const T*)it.dt, it.bg, it.g, tid);
   else if (OP == OP_TUPDATE)
@@ -1634,9 +1634,7 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
     el_commup<T>(it.L, it.F, tid);
   else if (OP == OP_COMMMEAN)
     el_commmean<T>(it.L, it.F, it.band, tid);
-  else if (OP == OP_ZERO_ACC) {
-    if (tid < it.count) it.L.acc[tid] = 0.0;
-  } else if (OP == OP_DT_LEVEL)
+  else if (OP == OP_DT_LEVEL)
     el_dt_level<T>(it.L, it.level, it.gg, it.flags & FL_HYDRO, it.ds, it.rho0d, it.e0d, it.V[0],
                    it.V[1], it.V[2], tid);
   else if (OP == OP_DT_FINAL)
@@ -1809,14 +1807,12 @@ int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, in
     DFN_OP(OP_DIFFUSE)
     DFN_OP(OP_TPREP)
     DFN_OPD(OP_TFLUX)
-    DFN_OPD(OP_TFRONTIER)
     DFN_OPD(OP_TMOM)
     DFN_OPD(OP_TUPDATE)
     DFN_OP(OP_VREC)
     DFN_OPD(OP_BC)
     DFN_OP(OP_COMMUP)
     DFN_OP(OP_COMMMEAN)
-    DFN_OP(OP_ZERO_ACC)
     DFN_OP(OP_DT_LEVEL)
     DFN_OP(OP_DT_FINAL)
     DFN_OP(OP_FORCE_LEVEL)
@@ -1843,15 +1839,6 @@ int op_chunk_elems(int op) { return op == OP_FORCE_LEVEL ? kBlock * kForceCells 
 // index-space size of one item of an op (host side, from the item's views)
 unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const Box& b) {
   long long n = 0;
-  auto slots = [&](int lo, int ns) {
-    long long tot = 0;
-    for (int s = lo; s < lo + ns; ++s) {
-      int a = s >> 1;
-      int t1 = a == 0 ? 1 : 0, t2 = a == 2 ? 1 : 2;
-      tot += (long long)(L.n[t1] >> 1) * (L.n[t2] >> 1);
-    }
-    return tot;
-  };
   switch (op) {
     case OP_SOURCE: case OP_COMPRESS: case OP_DIFFUSE: case OP_TPREP: case OP_TFLUX:
     case OP_TMOM: case OP_TUPDATE: case OP_VREC: case OP_VISC_Q: case OP_VISC_V:  // is_box_op
@@ -1869,8 +1856,7 @@ unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const B
     case OP_SWEEP:
       n = (long long)sweep_units(b, d) * kBlock;  // one chunk per (column, chunk) unit
       break;
-    case OP_FRONTIER_DIFF: n = slots(0, 6); break;
-    case OP_TFRONTIER: n = slots(2 * d, 2); break;
+    case OP_FRONTIER_DIFF: n = 6LL * L.acc_slots; break;
     case OP_BC: {
       int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
       n = (long long)L.s[t1] * L.s[t2] * 2 * L.G * 5;
@@ -1880,7 +1866,6 @@ unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const B
       n = 5LL * ((F.n[0] >> 1) + F.G) * ((F.n[1] >> 1) + F.G) * ((F.n[2] >> 1) + F.G);
       break;
     case OP_COMMMEAN: n = (long long)(F.n[0] >> 1) * (F.n[1] >> 1) * (F.n[2] >> 1); break;
-    case OP_ZERO_ACC: n = 18LL * L.acc_slots; break;
     case OP_DT_LEVEL: case OP_FORCE_LEVEL: n = (long long)L.n[0] * L.n[1] * L.n[2]; break;
     default: n = 1; break;
   }
