@@ -1869,6 +1869,9 @@ unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const B
     case OP_DT_LEVEL: case OP_FORCE_LEVEL: n = (long long)L.n[0] * L.n[1] * L.n[2]; break;
     default: n = 1; break;
   }
+  // the compression kernel also sums the child's CommFlux record (fr_sums): enough
+  // threads for it whatever the box (elements beyond the box decode to nothing)
+  if (op == OP_COMPRESS && L.has_child && n < 18LL * L.cacc_slots) n = 18LL * L.cacc_slots;
   return (unsigned)n;
 }
 
