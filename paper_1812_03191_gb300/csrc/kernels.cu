@@ -992,98 +992,187 @@ __device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_l
 }
 
 // ---------------------------------------------------------------- CommUp
-// One thread per (coarse host element, field).  The 2x2x2 fine elements hosted by
-// one coarse element share their van Leer slopes: the z pass gives 9 slopes (one
-// per (y,x) column) for both fine z offsets, the y pass 3 per z offset, the x pass
-// 1 per (z,y) offset -- the same arithmetic per fine element as interpolating each
-// one alone, with the slopes computed once.  Along a staggered field's own axis the
-// fine faces lie on the host face (copied) or midway to the next one (mean of the
-// two, which favours neither side), and both frontier faces of v_d are filled, so a
-// mirror-symmetric coarse state gives mirror-symmetric fine ghosts.
+// A coarse host element holds 2 x 2 x 2 fine elements; CommUp fills the fine ghosts.
+// Per field, the hosts with a ghost among their fine elements form the shell of
+// their host box around the hosts whose fine elements are all kept (active cells;
+// for v_d the faces strictly inside along d, so both frontier faces of v_d are
+// filled).  The shell is cut into six disjoint boxes (two slabs across z over the
+// whole x-y range, two across y, two across x), each into tiles of at most
+// kCuHosts hosts in one host z-plane, one 256-thread chunk per tile.  The z pass
+// interpolates each coarse column of a tile and its halo once (to both fine z
+// offsets) into shared memory, the y pass each x-column once (to both fine y
+// offsets), and the x pass gives a host's 8 fine elements: the arithmetic of
+// interpolating each fine element alone along z, then y, then x, with every slope
+// computed once per tile.  Along a staggered field's own axis the fine faces lie on
+// the host face (copied) or midway to the next one (mean of the two, which favours
+// neither side), so a mirror-symmetric coarse state gives mirror-symmetric ghosts.
+constexpr int kCuHosts = kBlock;  // hosts per tile, at most 64 per side
+constexpr int kCuZ = 396;         // max (tx + 2)(ty + 2) over tx, ty <= 64, tx ty <= 256
+constexpr int kCuY = 384;         // max ty (tx + 2) over the same tiles
+
+struct CuBox {
+  int x0, y0, z0, ex, ey, ez;  // first host and extents
+  int tx, ty, ntx, nty;        // tile size and tiles per plane
+};
+
+// host range along an axis: 0 lower ghost hosts, 1 upper ghost hosts, 2 kept hosts,
+// 3 all hosts; m = n/2 hosts span the active cells, k0 = 1 on a field's own axis
+__host__ __device__ inline void cu_range(int which, int m, int hg, int k0, int& lo, int& e) {
+  if (which == 0) {
+    lo = -hg;
+    e = hg + k0;
+  } else if (which == 1) {
+    lo = m;
+    e = hg;
+  } else if (which == 2) {
+    lo = k0;
+    e = m - k0;
+  } else {
+    lo = -hg;
+    e = m + 2 * hg;
+  }
+}
+
+// box b (0..5) of the shell of a field whose own axis is sa (-1 for a cell field)
+__host__ __device__ inline CuBox cu_box(const int* n, int G, int sa, int b) {
+  // x: all, all, all, all, lower, upper; y: all, all, lower, upper, kept, kept;
+  // z: lower, upper, then kept
+  CuBox B;
+  const int hg = G >> 1;
+  cu_range(b < 4 ? 3 : b - 4, n[0] >> 1, hg, sa == 0, B.x0, B.ex);
+  cu_range(b < 2 ? 3 : b < 4 ? b - 2 : 2, n[1] >> 1, hg, sa == 1, B.y0, B.ey);
+  cu_range(b < 2 ? b : 2, n[2] >> 1, hg, sa == 2, B.z0, B.ez);
+  if (B.ex <= 0 || B.ey <= 0 || B.ez <= 0) {
+    B.ez = 0;
+    B.tx = B.ty = 1;
+    B.ntx = B.nty = 0;
+    return B;
+  }
+  const int sx = (B.ex + 63) / 64;
+  B.tx = (B.ex + sx - 1) / sx;
+  int ty = B.ey < 64 ? B.ey : 64;
+  if (ty > kCuHosts / B.tx) ty = kCuHosts / B.tx;
+  B.nty = (B.ey + ty - 1) / ty;
+  B.ty = (B.ey + B.nty - 1) / B.nty;
+  B.ntx = (B.ex + B.tx - 1) / B.tx;
+  return B;
+}
+
+// chunks of one CommUp launch into a fine level
+__host__ __device__ inline long long cu_chunks(const int* n, int G) {
+  long long c = 0;
+  for (int f = 0; f < 5; ++f)
+    for (int b = 0; b < 6; ++b) {
+      const CuBox B = cu_box(n, G, f >= F_VX ? f - F_VX : -1, b);
+      c += (long long)B.ez * B.ntx * B.nty;
+    }
+  return c;
+}
+
 template <class T>
 __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F, unsigned tid) {
-  const int G = F.G, hg = G >> 1;
-  const int nh0 = (F.n[0] >> 1) + G, nh1 = (F.n[1] >> 1) + G, nh2 = (F.n[2] >> 1) + G;
-  long long t = tid;
-  long long per = (long long)nh0 * nh1 * nh2;
-  if (t >= 5 * per) return;
-  const int f = (int)(t / per);
-  int r = (int)(t - (long long)f * per);
-  const int h0 = r % nh0 - hg, h1 = (r / nh0) % nh1 - hg, h2 = r / (nh0 * nh1) - hg;
-  // hosted fine elements: rel = 2h + {0,1} on each axis; skip if all are active
-  const int hh[3] = {h0, h1, h2};
-  const int sa = f >= F_VX ? f - F_VX : -1;
-  // kept fine elements: active cells; for v_d the faces strictly inside along d
-  bool all_active = true;
+  __shared__ T s_z[2][kCuZ];  // [fine z offset][column (y, x) of the tile and halo]
+  __shared__ T s_y[4][kCuY];  // [fine z offset * 2 + fine y offset][(host y, x column)]
+  __shared__ CuBox s_box;
+  __shared__ int s_fr[2];     // field (-1: past the last tile) and tile within the box
+  const int lt = (int)(tid % kBlock);
+  // warp 0 finds the chunk's field and box: lane i takes box i % 6 of field i / 6
+  if (lt < 32) {
+    const int r = (int)(tid / kBlock);
+    const int fb = lt < 30 ? lt : 29;
+    const CuBox B = cu_box(F.n, F.G, fb / 6 >= F_VX ? fb / 6 - F_VX : -1, fb % 6);
+    const int c = lt < 30 ? B.ez * B.ntx * B.nty : 0;
+    int incl = c;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-    all_active = all_active && hh[a] >= (a == sa ? 1 : 0) && 2 * hh[a] + 1 < F.n[a];
-  if (all_active) return;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lt >= o) incl += v;
+    }
+    const bool hit = r >= incl - c && r < incl;
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (hit) {
+      s_box = B;
+      s_fr[0] = fb / 6;
+      s_fr[1] = r - (incl - c);
+    }
+    if (lt == 0 && m == 0u) s_fr[0] = -1;
+  }
+  __syncthreads();
+  const int f = s_fr[0];
+  if (f < 0) return;  // uniform over the block
+  const CuBox B = s_box;
+  const int r = s_fr[1];
+  const int sa = f >= F_VX ? f - F_VX : -1;
+  const int per = B.ntx * B.nty;
+  const int pz = r / per, rt = r - pz * per;
+  const int tyi = rt / B.ntx, txi = rt - tyi * B.ntx;
+  const int h2 = B.z0 + pz;
+  const int X0 = B.x0 + txi * B.tx, Y0 = B.y0 + tyi * B.ty;
+  const int wx = min(B.tx, B.x0 + B.ex - X0), wy = min(B.ty, B.y0 + B.ey - Y0);
+  const int P = wx + 2;  // pitch of a row of columns
   // offsets of the two centred fine positions in coarse cells, doubled for the half
   // slope
   const T dl = T(-0.5), dh = T(0.5);
   const T* q = (const T*)C.q[f];
-  const int base = ((C.G + F.off[2] + h2) * C.s[1] + C.G + F.off[1] + h1) * C.s[0] + C.G +
-                   F.off[0] + h0;
-  // z pass
-  T vz[2][3][3];
-#pragma unroll
-  for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-    for (int dx = 0; dx < 3; ++dx) {
-      int b = base + (dy - 1) * C.st[1] + (dx - 1);
-      T qm = q[b - C.st[2]], q0 = q[b], qp = q[b + C.st[2]];
-      if (sa == 2) {
-        vz[0][dy][dx] = q0;
-        vz[1][dy][dx] = T(0.5) * (q0 + qp);
-      } else {
-        T s = hslope(q0 - qm, qp - q0);
-        vz[0][dy][dx] = q0 + dl * s;
-        vz[1][dy][dx] = q0 + dh * s;
-      }
+  // z pass: the tile's columns and a halo of one (hosts in [-G/2 - 1, n/2 + G/2])
+  for (int e = lt; e < P * (wy + 2); e += kBlock) {
+    const int cy = e / P, cx = e - cy * P;
+    const int hx = X0 - 1 + cx, hy = Y0 - 1 + cy;
+    const int k = ((C.G + F.off[2] + h2) * C.s[1] + C.G + F.off[1] + hy) * C.s[0] + C.G +
+                  F.off[0] + hx;
+    const T qm = q[k - C.st[2]], q0 = q[k], qp = q[k + C.st[2]];
+    if (sa == 2) {
+      s_z[0][e] = q0;
+      s_z[1][e] = T(0.5) * (q0 + qp);
+    } else {
+      const T sl = hslope(q0 - qm, qp - q0);
+      s_z[0][e] = q0 + dl * sl;
+      s_z[1][e] = q0 + dh * sl;
     }
-  // y pass
-  T vy[2][2][3];
-#pragma unroll
-  for (int iz = 0; iz < 2; ++iz)
-#pragma unroll
-    for (int dx = 0; dx < 3; ++dx) {
-      T qm = vz[iz][0][dx], q0 = vz[iz][1][dx], qp = vz[iz][2][dx];
-      if (sa == 1) {
-        vy[iz][0][dx] = q0;
-        vy[iz][1][dx] = T(0.5) * (q0 + qp);
-      } else {
-        T s = hslope(q0 - qm, qp - q0);
-        vy[iz][0][dx] = q0 + dl * s;
-        vy[iz][1][dx] = q0 + dh * s;
-      }
+  }
+  __syncthreads();
+  // y pass: every x column of the tile's host rows
+  for (int e = lt; e < 2 * wy * P; e += kBlock) {
+    const int iz = e / (wy * P), rem = e - iz * wy * P;
+    const T qm = s_z[iz][rem], q0 = s_z[iz][rem + P], qp = s_z[iz][rem + 2 * P];
+    if (sa == 1) {
+      s_y[2 * iz][rem] = q0;
+      s_y[2 * iz + 1][rem] = T(0.5) * (q0 + qp);
+    } else {
+      const T sl = hslope(q0 - qm, qp - q0);
+      s_y[2 * iz][rem] = q0 + dl * sl;
+      s_y[2 * iz + 1][rem] = q0 + dh * sl;
     }
-  // x pass and stores
+  }
+  __syncthreads();
+  // x pass and stores: one host per thread
+  if (lt >= wx * wy) return;
+  const int ty = lt / wx, tx = lt - ty * wx;
+  const int h0 = X0 + tx, h1 = Y0 + ty;
   T* out = (T*)F.q[f];
+  const int G = F.G;
 #pragma unroll
-  for (int iz = 0; iz < 2; ++iz)
-#pragma unroll
-    for (int iy = 0; iy < 2; ++iy) {
-      T qm = vy[iz][iy][0], q0 = vy[iz][iy][1], qp = vy[iz][iy][2];
-      T v[2];
-      if (sa == 0) {
-        v[0] = q0;
-        v[1] = T(0.5) * (q0 + qp);
-      } else {
-        T s = hslope(q0 - qm, qp - q0);
-        v[0] = q0 + dl * s;
-        v[1] = q0 + dh * s;
-      }
-#pragma unroll
-      for (int ix = 0; ix < 2; ++ix) {
-        int fi = G + 2 * h0 + ix, fj = G + 2 * h1 + iy, fk = G + 2 * h2 + iz;
-        bool act = fi >= G + (sa == 0) && fi < G + F.n[0] && fj >= G + (sa == 1) &&
-                   fj < G + F.n[1] && fk >= G + (sa == 2) && fk < G + F.n[2];
-        bool inside = fi >= 0 && fi < F.s[0] && fj >= 0 && fj < F.s[1] && fk >= 0 &&
-                      fk < F.s[2];
-        if (!act && inside) out[(fk * F.s[1] + fj) * F.s[0] + fi] = v[ix];
-      }
+  for (int j = 0; j < 4; ++j) {
+    const int iz = j >> 1, iy = j & 1;
+    const T* row = s_y[j] + ty * P + tx;
+    const T qm = row[0], q0 = row[1], qp = row[2];
+    T v[2];
+    if (sa == 0) {
+      v[0] = q0;
+      v[1] = T(0.5) * (q0 + qp);
+    } else {
+      const T sl = hslope(q0 - qm, qp - q0);
+      v[0] = q0 + dl * sl;
+      v[1] = q0 + dh * sl;
     }
+#pragma unroll
+    for (int ix = 0; ix < 2; ++ix) {
+      const int fi = G + 2 * h0 + ix, fj = G + 2 * h1 + iy, fk = G + 2 * h2 + iz;
+      const bool act = fi >= G + (sa == 0) && fi < G + F.n[0] && fj >= G + (sa == 1) &&
+                       fj < G + F.n[1] && fk >= G + (sa == 2) && fk < G + F.n[2];
+      if (!act) out[(fk * F.s[1] + fj) * F.s[0] + fi] = v[ix];
+    }
+  }
 }
 
 // -------------------------------------------------------------- CommMean
@@ -1862,8 +1951,8 @@ unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const B
       n = (long long)L.s[t1] * L.s[t2] * 2 * L.G * 5;
       break;
     }
-    case OP_COMMUP:
-      n = 5LL * ((F.n[0] >> 1) + F.G) * ((F.n[1] >> 1) + F.G) * ((F.n[2] >> 1) + F.G);
+    case OP_COMMUP:  // one chunk per tile of the ghost hosts' shell
+      n = cu_chunks(F.n, F.G) * kBlock;
       break;
     case OP_COMMMEAN: n = (long long)(F.n[0] >> 1) * (F.n[1] >> 1) * (F.n[2] >> 1); break;
     case OP_DT_LEVEL: case OP_FORCE_LEVEL: n = (long long)L.n[0] * L.n[1] * L.n[2]; break;
