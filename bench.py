@@ -199,11 +199,12 @@ def tile_summary(shapes):
     return {binding.OP_NAMES[o]: row for o, row in enumerate(shapes) if any(row)}
 
 
-def cpu_oracle_rate(cfg, budget_s, steps_cap=None):
-    """Oracle cell-updates/s on a bounded sample: whole coarse steps until budget."""
+def cpu_oracle_rate(cfg, budget_s, steps_cap=None, omp=False):
+    """Oracle cell-updates/s on a bounded sample: whole coarse steps until budget
+    (omp: the OpenMP build of the oracle on every host core)."""
     from oracle import Oracle
     lo, hi = cfg["lo"], cfg["hi"]
-    orc = Oracle(cfg["n_levels"], cfg["n"], lo, hi, cfg["G"], cfg["params"])
+    orc = Oracle(cfg["n_levels"], cfg["n"], lo, hi, cfg["G"], cfg["params"], omp=omp)
     cu = cell_updates_per_step(cfg)
     done = 0
     t0 = time.perf_counter()
@@ -215,6 +216,21 @@ def cpu_oracle_rate(cfg, budget_s, steps_cap=None):
             break
     orc.close()
     return cu * done / el, done, el
+
+
+def oracle_openmp_rate(cfg, budget_s):
+    """The same oracle loops on every host core (its OpenMP build, bitwise the plain
+    build's results; sums stay serial), or why that build is unavailable."""
+    try:
+        import oracle
+        oracle.build_oracle(omp=True)
+        cores = oracle.threads(os.cpu_count() or 1)
+    except Exception as exc:  # a host compiler without OpenMP
+        return {"unavailable": f"{type(exc).__name__}: {exc}".splitlines()[0][:200]}
+    rate, nsteps, el = cpu_oracle_rate(cfg, budget_s, omp=True)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle (OpenMP build)",
+            "sample": f"{nsteps} whole coarse steps of {cfg['name']} ({el:.1f} s, "
+                      f"{cores} threads, plane loops in parallel, sums serial)"}
 
 
 def run_reference(args, cfg):
@@ -631,6 +647,7 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{nsteps} whole coarse steps of {cfg['name']} ({el:.1f} s, "
                          f"single-threaded C, -O2)"}
+        cpu["openmp"] = oracle_openmp_rate(cfg, args.cpu_budget / 2)
 
     prec = binding.DF_FP64 if args.precision == "fp64" else binding.DF_FP32_STATE
     stream = torch.cuda.current_stream()

@@ -7,6 +7,13 @@
  * cpu_baseline / reference legs of bench.py.  It shares no code with the CUDA path.
  * Compiled with -O2 -ffp-contract=off so no multiply-add is fused.
  *
+ * The "omp parallel for" lines act only in a second build with -fopenmp, used to
+ * time the oracle on all host cores.  Each marks a loop over planes whose
+ * iterations write disjoint elements from values that no iteration of it writes, so
+ * both builds compute the same bits.  Sums stay serial: the Delta t minima, the
+ * force, the luminosity normalisation and a child's frontier record, whose loops
+ * carry "if (!is_child)".
+ *
  * Layout: every level holds (n+2G)^3 elements per field, x fastest.  rho and e are
  * cell-centred; v_d is stored at the lower d-face of the cell with the same index
  * (staggered mesh, Sec. 3.2.1 "centred and staggered quantities").
@@ -88,6 +95,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { RHO = 0, ENE = 1, VXF = 2 };
 
@@ -391,6 +401,7 @@ static void source_step(or_sim* S, olevel* L, double h) {
   double gm1 = S->p.gamma - 1.0;
   for (int d = 0; d < 3; ++d) {
     size_t st = L->st[d];
+#pragma omp parallel for
     for (int k = 0; k < L->s[2]; ++k)
       for (int j = 0; j < L->s[1]; ++j)
         for (int i = 0; i < L->s[0]; ++i) {
@@ -419,6 +430,7 @@ static void viscosity_step(or_sim* S, olevel* L, double dt) {
   for (int d = 0; d < 3; ++d) q[d] = (double*)calloc(L->nc, sizeof(double));
   for (int d = 0; d < 3; ++d) {
     size_t st = L->st[d];
+#pragma omp parallel for
     for (int k = 0; k < L->s[2]; ++k)
       for (int j = 0; j < L->s[1]; ++j)
         for (int i = 0; i < L->s[0]; ++i) {
@@ -430,6 +442,7 @@ static void viscosity_step(or_sim* S, olevel* L, double dt) {
         }
   }
   /* heating, from the velocities before this stage */
+#pragma omp parallel for
   for (int k = 0; k < L->s[2]; ++k)
     for (int j = 0; j < L->s[1]; ++j)
       for (int i = 0; i < L->s[0]; ++i) {
@@ -445,6 +458,7 @@ static void viscosity_step(or_sim* S, olevel* L, double dt) {
       }
   for (int d = 0; d < 3; ++d) {
     size_t st = L->st[d];
+#pragma omp parallel for
     for (int k = 0; k < L->s[2]; ++k)
       for (int j = 0; j < L->s[1]; ++j)
         for (int i = 0; i < L->s[0]; ++i) {
@@ -461,6 +475,7 @@ static void viscosity_step(or_sim* S, olevel* L, double dt) {
 /* SubStep3, reading R3 */
 static void compress_step(or_sim* S, olevel* L, double dt) {
   double gm1 = S->p.gamma - 1.0;
+#pragma omp parallel for
   for (int k = 0; k < L->s[2] - 1; ++k)
     for (int j = 0; j < L->s[1] - 1; ++j)
       for (int i = 0; i < L->s[0] - 1; ++i) {
@@ -477,6 +492,7 @@ static void compress_step(or_sim* S, olevel* L, double dt) {
 static void luminosity_step(or_sim* S, olevel* L, double dt) {
   int G = L->G, w0[3];
   for (int d = 0; d < 3; ++d) w0[d] = S->mir[d] ? 0 : G; /* mirror images too (R16) */
+#pragma omp parallel for
   for (int k = w0[2]; k < G + L->n[2]; ++k)
     for (int j = w0[1]; j < G + L->n[1]; ++j)
       for (int i = w0[0]; i < G + L->n[0]; ++i) {
@@ -520,11 +536,14 @@ static int coarse_frontier_side(const olevel* L, const olevel* C, int d, const i
 static void diffusion_step(or_sim* S, olevel* L, double dt, olevel* child, int is_child) {
   double chi = S->p.chi;
   size_t nc = L->nc;
+#pragma omp parallel for
   for (size_t c = 0; c < nc; ++c) L->eps[c] = L->q[ENE][c] / L->q[RHO][c];
   /* face energy moved in +d during dt: Qdt = -chi rho_f (eps_c - eps_m) / dx * A * dt */
   for (int d = 0; d < 3; ++d) {
     size_t st = L->st[d];
     double* Q = L->P[d];
+    /* a child adds its frontier faces into the record in loop order: serial */
+#pragma omp parallel for if (!is_child)
     for (int k = 0; k < L->s[2]; ++k)
       for (int j = 0; j < L->s[1]; ++j)
         for (int i = 0; i < L->s[0]; ++i) {
@@ -548,6 +567,7 @@ static void diffusion_step(or_sim* S, olevel* L, double dt, olevel* child, int i
           }
         }
   }
+#pragma omp parallel for
   for (int k = 1; k < L->s[2] - 1; ++k)
     for (int j = 1; j < L->s[1] - 1; ++j)
       for (int i = 1; i < L->s[0] - 1; ++i) {
@@ -566,8 +586,10 @@ static void transport_sweep(or_sim* S, olevel* L, int d, double dt, olevel* chil
   double ad = L->area[d], dxd = L->dx[d];
   int sd = L->s[d];
   (void)S;
+#pragma omp parallel for
   for (size_t c = 0; c < nc; ++c) L->eps[c] = e[c] / rho[c];
   for (int m = 0; m < 3; ++m)
+#pragma omp parallel for
     for (int k = 0; k < L->s[2]; ++k)
       for (int j = 0; j < L->s[1]; ++j)
         for (int i = 0; i < L->s[0]; ++i) {
@@ -579,6 +601,8 @@ static void transport_sweep(or_sim* S, olevel* L, int d, double dt, olevel* chil
   double* Fm = L->F;   /* solver's own mass flux (the momenta use this one) */
   double* Fo = L->Fo;  /* mass flux after the frontier overwrite (rho update) */
   double* Ex = L->E;   /* energy flux after the frontier overwrite (e update) */
+  /* a child adds its frontier faces into the record in loop order: serial */
+#pragma omp parallel for if (!is_child)
   for (int k = 0; k < L->s[2]; ++k)
     for (int j = 0; j < L->s[1]; ++j)
       for (int i = 0; i < L->s[0]; ++i) {
@@ -620,6 +644,7 @@ static void transport_sweep(or_sim* S, olevel* L, int d, double dt, olevel* chil
   for (int m = 0; m < 3; ++m) {
     double* Pm = L->P[m];
     size_t sm = L->st[m];
+#pragma omp parallel for
     for (int k = 0; k < L->s[2]; ++k)
       for (int j = 0; j < L->s[1]; ++j)
         for (int i = 0; i < L->s[0]; ++i) {
@@ -644,6 +669,7 @@ static void transport_sweep(or_sim* S, olevel* L, int d, double dt, olevel* chil
         }
   }
   /* updates */
+#pragma omp parallel for
   for (int k = 0; k < L->s[2]; ++k)
     for (int j = 0; j < L->s[1]; ++j)
       for (int i = 0; i < L->s[0]; ++i) {
@@ -669,6 +695,7 @@ static void transport_step(or_sim* S, olevel* L, double dt, olevel* child, int i
   size_t nc = L->nc;
   for (int m = 0; m < 3; ++m) memcpy(L->vp[m], L->q[VXF + m], nc * sizeof(double));
   for (int m = 0; m < 3; ++m)
+#pragma omp parallel for
     for (int k = 0; k < L->s[2]; ++k)
       for (int j = 0; j < L->s[1]; ++j)
         for (int i = 0; i < L->s[0]; ++i) {
@@ -679,6 +706,7 @@ static void transport_step(or_sim* S, olevel* L, double dt, olevel* child, int i
         }
   for (int d = 0; d < 3; ++d) transport_sweep(S, L, d, dt, child, is_child);
   for (int m = 0; m < 3; ++m)
+#pragma omp parallel for
     for (int k = 0; k < L->s[2]; ++k)
       for (int j = 0; j < L->s[1]; ++j)
         for (int i = 0; i < L->s[0]; ++i) {
@@ -736,6 +764,7 @@ void or_commup(or_sim* S, int cl) {
     if (S->mir[d]) bc_axis(S, Cc, d, 0, OR_BC_REFLECT);
   for (int f = 0; f < 5; ++f) {
     int sa = f >= VXF ? f - VXF : -1;
+#pragma omp parallel for
     for (int k = 0; k < F->s[2]; ++k)
       for (int j = 0; j < F->s[1]; ++j)
         for (int i = 0; i < F->s[0]; ++i) {
@@ -781,6 +810,7 @@ void or_commmean(or_sim* S, int cl) {
   olevel* F = &S->L[cl + 1];
   int Gc = Cc->G, Gf = F->G, band = S->p.band;
   /* centred fields: mean of 8 fine cells */
+#pragma omp parallel for
   for (int c = 0; c < F->n[2] / 2; ++c)
     for (int b = 0; b < F->n[1] / 2; ++b)
       for (int a = 0; a < F->n[0] / 2; ++a) {
@@ -804,6 +834,7 @@ void or_commmean(or_sim* S, int cl) {
   /* staggered fields: mean of the 4 coplanar fine faces */
   for (int sa = 0; sa < 3; ++sa) {
     int t1 = sa == 0 ? 1 : 0, t2 = sa == 2 ? 1 : 2;
+#pragma omp parallel for
     for (int c = 0; c < F->n[2] / 2; ++c)
       for (int b = 0; b < F->n[1] / 2; ++b)
         for (int a = 0; a < F->n[0] / 2; ++a) {
@@ -925,6 +956,18 @@ void or_step(or_sim* S, int nsteps) {
     S->t += dt;
     S->dt_last = dt;
   }
+}
+
+/* ------------------------------------------------------------- threads */
+
+int or_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* ---------------------------------------------------------------- force */

@@ -66,6 +66,8 @@ double or_last_dt(const or_sim* s);
 
 /* Force on the perturber, Eq. 18, with rho - rho0 and the covered-cell mask. */
 void or_force(const or_sim* s, double F[3]);
+/* threads of the OpenMP build (n > 0 sets them); the plain build returns 1 */
+int or_threads(int n);
 
 /* Active cells (n0*n1*n2, x fastest) of one field: 0 rho, 1 e, 2 vx, 3 vy, 4 vz. */
 int or_get_field(const or_sim* s, int level, int field, double* out);

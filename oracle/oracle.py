@@ -1,7 +1,10 @@
 """ctypes wrapper of the plain-C FP64 oracle (``dfnest_oracle.c``).
 
 Test infrastructure only (see the package docstring).  ``build_oracle()`` compiles
-the C file with ``gcc -O2 -ffp-contract=off`` next to this module.
+the C file with ``gcc -O2 -ffp-contract=off`` next to this module;
+``build_oracle(omp=True)`` compiles the same file with ``-fopenmp`` as well, a build
+that runs the oracle's plane loops on several host cores with the same results (it
+exists to time the oracle on all cores).
 """
 from __future__ import annotations
 
@@ -15,8 +18,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dfnest_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
 class BC:
@@ -50,26 +54,26 @@ class OracleParams(C.Structure):
     ]
 
 
-def build_oracle(force: bool = False) -> str:
-    """Compile liboracle.so (plain C, FP64, no fused multiply-add)."""
+def build_oracle(force: bool = False, omp: bool = False) -> str:
+    """Compile liboracle.so (plain C, FP64, no fused multiply-add), or with omp the
+    OpenMP build liboracle_omp.so of the same file."""
+    out = _LIB_OMP if omp else _LIB
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
+        if force or not os.path.exists(out) or os.path.getmtime(out) < max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "dfnest_oracle.h"))
         ):
-            tmp = _LIB + f".tmp{os.getpid()}"
+            tmp = out + f".tmp{os.getpid()}"
             subprocess.check_call(
-                ["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared",
-                 "-o", tmp, _SRC, "-lm"]
+                ["gcc", "-O2", "-ffp-contract=off", "-std=c99", "-fPIC", "-shared"]
+                + (["-fopenmp"] if omp else []) + ["-o", tmp, _SRC, "-lm"]
             )
-            os.replace(tmp, _LIB)
-    return _LIB
+            os.replace(tmp, out)
+    return out
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        build_oracle()
-        lib = C.CDLL(_LIB)
+def _load(omp: bool = False):
+    if omp not in _libs:
+        lib = C.CDLL(build_oracle(omp=omp))
         P = C.POINTER
         dp = P(C.c_double)
         lib.or_create.restype = C.c_void_p
@@ -97,8 +101,15 @@ def _load():
         lib.or_fill_bc.argtypes = [C.c_void_p]
         lib.or_xi_search.restype = C.c_double
         lib.or_xi_search.argtypes = [C.c_int, dp, dp, P(C.c_int)]
-        _lib = lib
-    return _lib
+        lib.or_threads.restype = C.c_int
+        lib.or_threads.argtypes = [C.c_int]
+        _libs[omp] = lib
+    return _libs[omp]
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the OpenMP build (n > 0 sets them first)."""
+    return _load(omp=True).or_threads(int(n))
 
 
 def _dp(a: np.ndarray):
@@ -119,9 +130,10 @@ def xi_search(dt_level, cost):
 class Oracle:
     """One nested hierarchy advanced by the FP64 oracle."""
 
-    def __init__(self, n_levels, n, lo, hi, G, params: dict, n0=None):
-        """n: cells per axis of every level; n0 (optional): of the ground level only"""
-        lib = _load()
+    def __init__(self, n_levels, n, lo, hi, G, params: dict, n0=None, omp=False):
+        """n: cells per axis of every level; n0 (optional): of the ground level only;
+        omp: run on the OpenMP build (same results, several host cores)"""
+        lib = _load(omp)
         self.lib = lib
         if isinstance(n, int):
             n = (n, n, n)
