@@ -791,7 +791,7 @@ struct Builder {
       L.start0 = plan.starts.size();
       L.nitems = 0;
       unsigned chunks = 0;
-      unsigned ce = (unsigned)op_chunk_elems(L.op);
+      unsigned ce = (unsigned)op_chunk_elems(L.op, (int)sizeof(T));
       for (size_t r = 0; r < nr; ++r) {
         if (pos[r] >= per_run[r].size()) continue;
         const Entry& e = per_run[r][pos[r]];

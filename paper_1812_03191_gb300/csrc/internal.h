@@ -198,6 +198,12 @@ __host__ __device__ inline bool is_box_op(int op) {
          op == OP_VISC_Q || op == OP_VISC_V;
 }
 
+// cells per thread of an op: the FP32 state's compression and diffusion ops take two
+// (with one they are latency-bound: too few bytes in flight per thread)
+__host__ __device__ constexpr int cells_per_thread(int op, int esz) {
+  return esz == 4 && (op == OP_COMPRESS || op == OP_DIFFUSE) ? 2 : 1;
+}
+
 enum ItemFlags {
   FL_WRITE_PI = 1, FL_SS3 = 2, FL_LUM = 4, FL_EPS = 8, FL_DFR = 16, FL_HYDRO = 32,
   FL_FUSED = 64  // VREC: the transport ran as fused sweeps (state in Scratch::qb)
@@ -252,7 +258,7 @@ __host__ __device__ inline long long rec_elems(const int s[3]) {
 template <class T>
 int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, int nitems,
                  unsigned nchunks, unsigned grid, cudaStream_t st, const Item<T>* host_item);
-int op_chunk_elems(int op);
+int op_chunk_elems(int op, int esz);  // elements per chunk for state elements of esz bytes
 unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const Box& b);
 int force_partials_per_level(const LevelView& L);
 int launch_force_weights(const LevelView& L, const Phys& P, cudaStream_t st);

@@ -245,38 +245,69 @@ __device__ __forceinline__ void el_visc_v(const LevelView& L, const Box& b, cons
   }
 }
 
+// The compression and diffusion element functions take NC cells per thread: 2 for the
+// FP32 state (elements e and e + 256 of a 512-element chunk), 1 otherwise.  Every
+// load of both cells is issued before the first store, so a thread keeps twice the
+// bytes in flight.  A cell past the end of the box takes an in-bounds stand-in index
+// for its loads and stores nothing.  The arithmetic of each cell is unchanged.
+
 // ------------------------------------------------- SubStep3 + luminosity + e/rho
-template <class T>
-__device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b, const Scratch& S,
-                                                         const T* __restrict__ dtp, T gm1,
-                                                         T lum, int do_ss3, int do_lum,
-                                                         int do_eps, const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
-  int i, j, k;
-  if (!decode(b, tid, i, j, k)) return;
-  const T dt = dtp[0];
-  const int c = cidx(L, i, j, k);
-  T* e = (T*)L.q[F_E];
-  T ec = e[c];
-  if (do_ss3 && i < L.s[0] - 1 && j < L.s[1] - 1 && k < L.s[2] - 1) {
-    const T* vx = (const T*)L.q[F_VX];
-    const T* vy = (const T*)L.q[F_VX + 1];
-    const T* vz = (const T*)L.q[F_VX + 2];
-    T div = (vx[c + L.st[0]] - vx[c]) * g.inv_dx[0] + (vy[c + L.st[1]] - vy[c]) * g.inv_dx[1] +
-            (vz[c + L.st[2]] - vz[c]) * g.inv_dx[2];
-    T a = T(0.5) * dt * gm1 * div;
-    // (e0 + de)(1 - a)/(1 + a) - e0
-    ec = hdiv(ec * (T(1) - a) - T(2) * a * bg.e0, T(1) + a);
+template <class T, int NC>
+__device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b,
+                                                const Scratch& S, const T* __restrict__ dtp,
+                                                T gm1, T lum, int do_ss3, int do_lum,
+                                                int do_eps, const Bg<T>& bg, const Geo<T>& g,
+                                                const unsigned* el) {
+  int c[NC];
+  bool ok[NC], ss3[NC], lm[NC];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    int i, j, k;
+    ok[n] = decode(b, el[n], i, j, k);
+    if (NC == 1 && !ok[n]) return;
+    if (!ok[n]) i = j = k = 0;
+    c[n] = cidx(L, i, j, k);
+    ss3[n] = do_ss3 && i < L.s[0] - 1 && j < L.s[1] - 1 && k < L.s[2] - 1;
+    // active cells and their mirror images in the ghost layers
+    lm[n] = do_lum && i >= (L.mir & 1 ? 0 : L.G) && i < L.G + L.n[0] &&
+            j >= (L.mir & 2 ? 0 : L.G) && j < L.G + L.n[1] && k >= (L.mir & 4 ? 0 : L.G) &&
+            k < L.G + L.n[2];
   }
-  // active cells and their mirror images in the ghost layers
-  if (do_lum && i >= (L.mir & 1 ? 0 : L.G) && i < L.G + L.n[0] &&
-      j >= (L.mir & 2 ? 0 : L.G) && j < L.G + L.n[1] && k >= (L.mir & 4 ? 0 : L.G) &&
-      k < L.G + L.n[2])
-    ec = ec + lum * dt * ((const T*)L.lumw)[c];
-  e[c] = ec;
-  if (do_eps) {
+  T* e = (T*)L.q[F_E];
+  const T* vx = (const T*)L.q[F_VX];
+  const T* vy = (const T*)L.q[F_VX + 1];
+  const T* vz = (const T*)L.q[F_VX + 2];
+  T ec[NC], x0[NC], x1[NC], y0[NC], y1[NC], z0[NC], z1[NC], lw[NC], dr[NC];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    ec[n] = e[c[n]];
+    if (ss3[n]) {
+      x0[n] = vx[c[n]];
+      x1[n] = vx[c[n] + L.st[0]];
+      y0[n] = vy[c[n]];
+      y1[n] = vy[c[n] + L.st[1]];
+      z0[n] = vz[c[n]];
+      z1[n] = vz[c[n] + L.st[2]];
+    }
+    if (lm[n]) lw[n] = ((const T*)L.lumw)[c[n]];
+    if (do_eps) dr[n] = ((const T*)L.q[F_RHO])[c[n]];
+  }
+  const T dt = dtp[0];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    if (!ok[n]) continue;
+    T ecn = ec[n];
+    if (ss3[n]) {
+      T div = (x1[n] - x0[n]) * g.inv_dx[0] + (y1[n] - y0[n]) * g.inv_dx[1] +
+              (z1[n] - z0[n]) * g.inv_dx[2];
+      T a = T(0.5) * dt * gm1 * div;
+      // (e0 + de)(1 - a)/(1 + a) - e0
+      ecn = hdiv(ecn * (T(1) - a) - T(2) * a * bg.e0, T(1) + a);
+    }
+    if (lm[n]) ecn = ecn + lum * dt * lw[n];
+    e[c[n]] = ecn;
     // e/rho - e0/rho0 = (de - eps0 drho)/(rho0 + drho)
-    T dr = ((const T*)L.q[F_RHO])[c];
-    ((T*)S.eps)[c] = hdiv(ec - bg.eps0 * dr, bg.rho0 + dr);
+    if (do_eps) ((T*)S.eps)[c[n]] = hdiv(ecn - bg.eps0 * dr[n], bg.rho0 + dr[n]);
   }
 }
 
@@ -332,36 +363,60 @@ __device__ __forceinline__ T diff_flux(const LevelView& L, const Geo<T>& g,
   return -chi * rf * (eps[f] - eps[m]) * g.dcoef[d] * dt;
 }
 
-template <class T>
+template <class T, int NC>
 __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, const Scratch& S,
-                                                    const T* __restrict__ dtp, T chi, T rho0,
-                                                    int dfr, const Geo<T>& g, unsigned tid) {
-  int i, j, k;
-  if (!decode(b, tid, i, j, k)) return;
-  if (i < 1 || j < 1 || k < 1 || i >= L.s[0] - 1 || j >= L.s[1] - 1 || k >= L.s[2] - 1) return;
+                                           const T* __restrict__ dtp, T chi, T rho0, int dfr,
+                                           const Geo<T>& g, const unsigned* el) {
+  int c[NC], c3[NC][3];
+  bool ok[NC];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    int i, j, k;
+    ok[n] = decode(b, el[n], i, j, k) && i >= 1 && j >= 1 && k >= 1 && i < L.s[0] - 1 &&
+            j < L.s[1] - 1 && k < L.s[2] - 1;
+    if (NC == 1 && !ok[n]) return;
+    if (!ok[n]) i = j = k = 1;
+    c[n] = cidx(L, i, j, k);
+    c3[n][0] = i;
+    c3[n][1] = j;
+    c3[n][2] = k;
+  }
   const T dt = dtp[0];
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const T* __restrict__ eps = (const T*)S.eps;
-  const int c = cidx(L, i, j, k);
-  const int c3[3] = {i, j, k};
-  T div = T(0);
+  T q[NC][3][2];  // flux through the lower and the upper d-face
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    int up = c + L.st[d];
-    T qlo = diff_flux(L, g, rho, eps, c, d, chi, dt, rho0, dfr);
-    T qhi = diff_flux(L, g, rho, eps, up, d, chi, dt, rho0, dfr);
-    if (L.has_child && near_frontier(L, d, c3[d])) {
-      int slot, f3[3] = {c3[0], c3[1], c3[2]};
-      int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
-      if (side >= 0) qlo = (T)L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot];
-      f3[d] += 1;
-      side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
-      if (side >= 0) qhi = (T)L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot];
+  for (int n = 0; n < NC; ++n)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      q[n][d][0] = diff_flux(L, g, rho, eps, c[n], d, chi, dt, rho0, dfr);
+      q[n][d][1] = diff_flux(L, g, rho, eps, c[n] + L.st[d], d, chi, dt, rho0, dfr);
     }
-    div += qhi - qlo;
+  if (L.has_child) {
+#pragma unroll
+    for (int n = 0; n < NC; ++n)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (!near_frontier(L, d, c3[n][d])) continue;
+        int slot, f3[3] = {c3[n][0], c3[n][1], c3[n][2]};
+        int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+        if (side >= 0) q[n][d][0] = (T)L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot];
+        f3[d] += 1;
+        side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+        if (side >= 0) q[n][d][1] = (T)L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot];
+      }
   }
   T* e = (T*)L.q[F_E];
-  e[c] = e[c] - div * g.inv_vol;
+  T ev[NC];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) ev[n] = e[c[n]];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    T div = T(0);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) div += q[n][d][1] - q[n][d][0];
+    if (ok[n]) e[c[n]] = ev[n] - div * g.inv_vol;
+  }
 }
 
 // CommFlux record of the diffusive energy fluxes through a child's frontier faces:
@@ -1687,20 +1742,30 @@ __device__ __forceinline__ bool skipped(const Item<T>& it) {
 template <class T, int OP, int D>
 __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
   if (skipped(it)) return;
+  // elements of this thread: tid, or for the two-cell ops the same lane of both
+  // halves of its 512-element chunk
+  constexpr int NC = cells_per_thread(OP, (int)sizeof(T));
+  unsigned el[NC];
+  el[0] = NC == 1 ? tid : (tid / kBlock) * (NC * kBlock) + tid % kBlock;
+#pragma unroll
+  for (int n = 1; n < NC; ++n) el[n] = el[0] + n * kBlock;
   if (OP == OP_SOURCE)
     el_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.flags & FL_WRITE_PI, it.gm1, it.bg, it.g,
                  tid);
   else if (OP == OP_COMPRESS) {
-    if (it.L.has_child) fr_sums(it.L, it.ds, it.level, tid);  // before any consumer
-    el_compress_lum<T>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.lum, it.flags & FL_SS3,
-                       it.flags & FL_LUM, it.flags & FL_EPS, it.bg, it.g, tid);
+    if (it.L.has_child)  // before any consumer
+#pragma unroll 1
+      for (int n = 0; n < NC; ++n) fr_sums(it.L, it.ds, it.level, el[n]);
+    el_compress_lum<T, NC>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.lum,
+                           it.flags & FL_SS3, it.flags & FL_LUM, it.flags & FL_EPS, it.bg, it.g,
+                           el);
   }
   else if (OP == OP_FRONTIER_DIFF)
     el_frontier_diff<T>(it.L, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
                         it.sub, tid);
   else if (OP == OP_DIFFUSE)
-    el_diffuse<T>(it.L, it.b, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
-                  tid);
+    el_diffuse<T, NC>(it.L, it.b, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR,
+                      it.g, el);
   else if (OP == OP_TPREP)
     el_tprep<T>(it.L, it.b, it.S, it.bg, tid);
   else if (OP == OP_TFLUX)
@@ -1740,8 +1805,11 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
 // [b*nchunks/grid, (b+1)*nchunks/grid) of the concatenated items, stages the item of
 // each chunk in shared memory (re-staging only when the item changes) and runs the
 // op on the chunk's elements.  starts[i] is the first chunk of item i.
+// (two-cell ops: at least 4 blocks per SM, so as many cells stay in flight as with
+// one cell per thread at full occupancy)
 template <class T, int OP, int D>
-__global__ void __launch_bounds__(kBlock) k_batch(const Item<T>* __restrict__ items,
+__global__ void __launch_bounds__(kBlock, cells_per_thread(OP, (int)sizeof(T)) == 2 ? 4 : 1)
+    k_batch(const Item<T>* __restrict__ items,
                                                   const unsigned* __restrict__ starts, int nitems,
                                                   unsigned nchunks) {
   __shared__ __align__(16) unsigned char s_raw[sizeof(Item<T>)];
@@ -1923,7 +1991,9 @@ int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, in
 }
 
 // elements per chunk of each op (one chunk = one block pass)
-int op_chunk_elems(int op) { return op == OP_FORCE_LEVEL ? kBlock * kForceCells : kBlock; }
+int op_chunk_elems(int op, int esz) {
+  return op == OP_FORCE_LEVEL ? kBlock * kForceCells : kBlock * cells_per_thread(op, esz);
+}
 
 // index-space size of one item of an op (host side, from the item's views)
 unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const Box& b) {
