@@ -1299,18 +1299,6 @@ __device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView&
 }
 
 // ------------------------------------------------------------- time step
-__device__ __forceinline__ double warp_min(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
 // Per-level Courant limit: min over active cells and axes of cfl dx_d / (cs + |v_d|).
 // Division is correctly rounded and monotone, so that minimum equals
 // cfl dx_d / max(cs + |v_d|): the kernel reduces the per-axis maxima (one division
