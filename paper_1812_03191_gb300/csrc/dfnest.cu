@@ -694,10 +694,20 @@ struct Builder {
       vr.flags |= FL_FUSED;
       add(out, OP_VREC, 0, vr);
     } else if (P.hydro_on) {
+      // At the x sweep the staggered momenta were just formed from v and rho (the
+      // kick, or the viscosity stage after it, wrote them; nothing since has changed
+      // v or rho), so Pi/rho_face - V is the velocity deviation itself: that sweep's
+      // momentum fluxes read v, and its preparation forms e/rho only.  The y and z
+      // sweeps divide the updated momenta.
       for (int d = 0; d < 3; ++d) {
-        add(out, OP_TPREP, 0, it);
+        Item<T> tp = it, tm = it;
+        if (d == 0) {
+          tp.flags |= FL_EPS_ONLY;
+          for (int m = 0; m < 3; ++m) tm.S.w[m] = it.L.q[F_VX + m];
+        }
+        add(out, OP_TPREP, 0, tp);
         add(out, OP_TFLUX, d, it);
-        add(out, OP_TMOM, d, it);
+        add(out, OP_TMOM, d, tm);
         add(out, OP_TUPDATE, d, it);
       }
       add(out, OP_VREC, 0, it);

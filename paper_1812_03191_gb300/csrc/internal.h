@@ -206,7 +206,8 @@ __host__ __device__ constexpr int cells_per_thread(int op, int esz) {
 
 enum ItemFlags {
   FL_WRITE_PI = 1, FL_SS3 = 2, FL_LUM = 4, FL_EPS = 8, FL_DFR = 16, FL_HYDRO = 32,
-  FL_FUSED = 64  // VREC: the transport ran as fused sweeps (state in Scratch::qb)
+  FL_FUSED = 64,  // VREC: the transport ran as fused sweeps (state in Scratch::qb)
+  FL_EPS_ONLY = 128  // TPREP: e/rho only (the x sweep reads Pi/rho_face - V from v)
 };
 
 // One work item.  Plain data, copied to shared memory by the kernel; size a

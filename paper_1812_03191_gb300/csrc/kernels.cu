@@ -452,7 +452,8 @@ __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scrat
 
 // --------------------------------------------------------------- transport
 template <class T>
-__device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const Scratch& S, const Bg<T>& bg, unsigned tid) {
+__device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const Scratch& S,
+                                        const Bg<T>& bg, int eps_only, unsigned tid) {
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
@@ -460,6 +461,7 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
   const int c3[3] = {i, j, k};
   const T rc = rho[c];
   ((T*)S.eps)[c] = hdiv(((const T*)L.q[F_E])[c] - bg.eps0 * rc, bg.rho0 + rc);
+  if (eps_only) return;
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     T wv = T(0);
@@ -1755,7 +1757,7 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
     el_diffuse<T, NC>(it.L, it.b, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR,
                       it.g, el);
   else if (OP == OP_TPREP)
-    el_tprep<T>(it.L, it.b, it.S, it.bg, tid);
+    el_tprep<T>(it.L, it.b, it.S, it.bg, it.flags & FL_EPS_ONLY, tid);
   else if (OP == OP_TFLUX)
     el_tflux<T, D>(it.L, it.b, it.S, (const T*)it.dt, it.bg, it.g, it.sub, tid);
   else if (OP == OP_TMOM)
