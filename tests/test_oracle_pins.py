@@ -537,6 +537,30 @@ def test_luminosity_deposit_total(sigma):
         assert np.allclose(d[d > 0], d[d > 0][0], rtol=0, atol=1e-14)
 
 
+def test_gaussian_luminosity_profile():
+    """The Gaussian deposit (reading R10): per level step every active cell gains
+    energy in proportion to exp(-r_c^2 / (2 sigma^2)) of its centre; the total is
+    L dt."""
+    n, half, L, sigma, dt = 16, 2.0, 0.37, 0.6, 1e-3
+    o = make(1, n, half, GM=0.0, L=L, lum_sigma=sigma, chi=0.0, hydro_on=0, dt_fixed=dt,
+             bc=(I.BC_PERIODIC,) * 6)
+    e0 = o.get_field(0, ENE).copy()
+    o.step(1)
+    d = o.get_field(0, ENE) - e0
+    x, y, z = centres(o, 0, n, (-half,) * 3, (half,) * 3)
+    r2 = (x**2 + y**2 + z**2).ravel()
+    dv = d.ravel()
+    assert np.all(dv > 0)
+    # log d + r^2/(2 sigma^2) is one constant; a wrong width, centre or power of r
+    # leaves a trend.  Each increment is a difference of energies ~1 apart from it,
+    # so its relative rounding error is a few ulps of e / d.
+    c = np.log(dv) + r2 / (2 * sigma**2)
+    tol = 8 * np.finfo(float).eps * np.abs(o.get_field(0, ENE)).ravel() / dv
+    ref = int(np.argmax(dv))
+    assert np.all(np.abs(c - c[ref]) <= tol + tol[ref]), np.max(np.abs(c - c[ref]) / tol)
+    assert d.sum() * (2 * half / n) ** 3 == pytest.approx(L * dt, rel=1e-12)
+
+
 def test_gravity_kick_points_to_perturber():
     """First-order check of S (Eq. 15) with the attractive Plummer potential:
     a gas at rest acquires v = -dt grad Phi, Phi = -GM/sqrt(r^2+eps^2)."""
