@@ -1,0 +1,63 @@
+"""bench.py on the CPU: the reference arm's JSON line (the oracle timed on whole coarse
+steps of the default workload), the silence of ranks other than 0, and the
+cell-update accounting of the workloads (Sigma_l n_l^3 2^l per coarse step)."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from paper_1812_03191_gb300 import inputs as I  # noqa: E402
+
+
+def _run(args, env=None):
+    e = dict(os.environ)
+    e.update(env or {})
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args,
+                         capture_output=True, text=True, timeout=600, env=e, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    return [json.loads(l) for l in out.stdout.splitlines() if l.startswith("{")]
+
+
+def test_reference_arm_line():
+    (line,) = _run(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert line["impl"] == "reference"
+    assert line["metric"] == "cell-updates/s" and line["unit"] == "cell-updates/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["steps"] == 1 and line["warmup"] == 3 and line["n_gpus"] == 1
+    assert line["config"]["workload"] == "nested_3x64^3_fp64"
+    assert line["ms_per_step"] == pytest.approx(
+        1e3 * bench.cell_updates_per_step(I.nested()) / line["value"], rel=1e-9)
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] == 1 and cpu["value"] == line["value"]
+    assert cpu["unit"] == line["unit"] and cpu["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"],
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    assert _run(["--impl", "reference", "--steps", "1", "--warmup", "3"],
+                env={"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_cell_updates_per_coarse_step():
+    """n^3 (1 + 2 + ... + 2^(L-1)): 3 x 64^3 -> 1.835e6, 5 x 128^3 -> 6.50e7"""
+    assert bench.cell_updates_per_step(I.nested()) == 64**3 * 7
+    assert bench.cell_updates_per_step(I.precision()) == 128**3 * 31
+    assert bench.cell_updates_per_step({"n": (8, 8, 16), "n_levels": 2}) == 8 * 8 * 16 * 3
+
+
+def test_level_step_boxes():
+    """one box per level step: level 0 once with margin 4; level l >= 1 2^(l-1) times
+    per sub-cycle pair, margins 8 then 4, capped at the padded array"""
+    cfg = I.nested()
+    n, G = cfg["n"], cfg["G"]
+    boxes = bench.level_step_boxes(cfg)
+    assert len(boxes) == 2 ** cfg["n_levels"] - 1
+    assert boxes[0] == (n + 8) ** 3
+    assert sorted(set(boxes)) == sorted({(n + 8) ** 3, min(n + 16, n + 2 * G) ** 3})
