@@ -184,6 +184,9 @@ struct DtFinal {
 
 // Ops of the work-list kernel.  Every launch runs one op over a list of work
 // items; an item is one (run, level) with its box and its own parameters.
+// OP_TFRONTIER and OP_ZERO_ACC are no longer emitted (the CommFlux record replaced
+// them); they keep their numbers so that op indices (tile-shape controls, timing
+// kinds, the binding's op names) stay stable.
 enum Op {
   OP_SOURCE = 0, OP_COMPRESS, OP_FRONTIER_DIFF, OP_DIFFUSE, OP_TPREP, OP_TFLUX, OP_TFRONTIER,
   OP_TMOM, OP_TUPDATE, OP_VREC, OP_BC, OP_COMMUP, OP_COMMMEAN, OP_ZERO_ACC, OP_DT_LEVEL,
