@@ -11,8 +11,10 @@
  * time the oracle on all host cores.  Each marks a loop over planes whose
  * iterations write disjoint elements from values that no iteration of it writes, so
  * both builds compute the same bits.  Sums stay serial: the Delta t minima, the
- * force, the luminosity normalisation and a child's frontier record, whose loops
- * carry "if (!is_child)".
+ * force and the luminosity normalisation.  A child's frontier record is a sum too:
+ * the flux loops that add into it run over pairs of planes (2p, 2p+1).  The fine
+ * faces of one coarse slot lie in one pair (G is even), and within a pair the order
+ * is that of the plain loops, so every slot is summed in the same order.
  *
  * Layout: every level holds (n+2G)^3 elements per field, x fastest.  rho and e are
  * cell-centred; v_d is stored at the lower d-face of the cell with the same index
@@ -542,9 +544,10 @@ static void diffusion_step(or_sim* S, olevel* L, double dt, olevel* child, int i
   for (int d = 0; d < 3; ++d) {
     size_t st = L->st[d];
     double* Q = L->P[d];
-    /* a child adds its frontier faces into the record in loop order: serial */
-#pragma omp parallel for if (!is_child)
-    for (int k = 0; k < L->s[2]; ++k)
+    /* planes in pairs: see the note on the record at the top of this file */
+#pragma omp parallel for
+    for (int kp = 0; kp < (L->s[2] + 1) / 2; ++kp)
+      for (int k = 2 * kp; k < 2 * kp + 2 && k < L->s[2]; ++k)
       for (int j = 0; j < L->s[1]; ++j)
         for (int i = 0; i < L->s[0]; ++i) {
           int c3[3] = {i, j, k};
@@ -601,9 +604,10 @@ static void transport_sweep(or_sim* S, olevel* L, int d, double dt, olevel* chil
   double* Fm = L->F;   /* solver's own mass flux (the momenta use this one) */
   double* Fo = L->Fo;  /* mass flux after the frontier overwrite (rho update) */
   double* Ex = L->E;   /* energy flux after the frontier overwrite (e update) */
-  /* a child adds its frontier faces into the record in loop order: serial */
-#pragma omp parallel for if (!is_child)
-  for (int k = 0; k < L->s[2]; ++k)
+  /* planes in pairs: see the note on the record at the top of this file */
+#pragma omp parallel for
+  for (int kp = 0; kp < (L->s[2] + 1) / 2; ++kp)
+    for (int k = 2 * kp; k < 2 * kp + 2 && k < L->s[2]; ++k)
     for (int j = 0; j < L->s[1]; ++j)
       for (int i = 0; i < L->s[0]; ++i) {
         int c3[3] = {i, j, k};
