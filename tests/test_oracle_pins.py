@@ -172,6 +172,33 @@ def test_heat_kernel_variance_growth():
     assert abs(p1 / p0 - (s0 / s1) ** 3) < 0.03
 
 
+def test_heat_kernel_second_order_convergence():
+    """Heat kernel at a fixed time on 24^3 and 48^3 cells (dt proportional to dx^2):
+    the largest deviation from the analytic Gaussian falls by ~4 when dx halves
+    (second order in space; first order in time is O(dx^2) here too)."""
+    half, chi, s0, T, amp = 6.0, 1.0, 1.0, 0.25, 0.1
+
+    def max_error(n):
+        dx = 2 * half / n
+        dt = 0.2 * dx * dx / chi
+        steps = int(round(T / dt))
+        assert math.isclose(steps * dt, T)
+        o = make(1, n, half, GM=0.0, L=0.0, chi=chi, hydro_on=0, dt_fixed=dt,
+                 bc=(I.BC_PERIODIC,) * 6)
+        x, y, z = centres(o, 0, n, (-half,) * 3, (half,) * 3)
+        r2 = x**2 + y**2 + z**2
+        e0 = o.get_field(0, ENE)[0, 0, 0]
+        o.set_field(0, ENE, e0 + amp * np.exp(-r2 / (2 * s0**2)))
+        o.step(steps)
+        s1 = math.sqrt(s0**2 + 2 * chi * T)
+        exact = amp * (s0 / s1) ** 3 * np.exp(-r2 / (2 * s1**2))
+        return np.abs(o.get_field(0, ENE) - e0 - exact).max() / exact.max()
+
+    coarse, fine = max_error(24), max_error(48)
+    assert coarse < 0.03
+    assert 3.5 < coarse / fine < 4.5, (coarse, fine)
+
+
 def test_heat_kernel_nested_spreads():
     """Nested variant: a bump crossing level frontiers spreads as sigma^2 + 2 chi t."""
     n, nl, half, chi = 24, 3, 6.0, 0.2
