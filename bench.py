@@ -127,7 +127,7 @@ ARRAYS_PER_ELEM = {
     "source": 12,        # rho, e, phi, v3 -> v3, pi3
     "compress_lum": 8,   # e, v3, rho, lumw -> e, e/rho
     "diffuse": 4,        # rho, e/rho, e -> e
-    "tprep": 9,          # rho, e, pi3 -> e/rho, w3
+    "tprep": 7,          # rho, e, pi3 -> e/rho, w3 (9); the x sweep's: rho, e -> e/rho (3)
     "tflux": 5,          # rho, e/rho, v_d -> F, E
     "tmom": 8,           # w3, F, v_d -> P3
     "tupdate": 15,       # F, E, P3, rho, e, pi3 -> rho, e, pi3
@@ -173,6 +173,20 @@ def bytes_per_launch(cfg, kind, esz, fused=False):
     if kind == "commmean":  # read 8 fine cells / 4 faces, write the covered coarse cell
         return 5 * esz * (n**3 + (n // 2) ** 3)
     return None
+
+
+def kernel_hbm_table(cfg, kinds, esz, fused, peak):
+    """Algorithmic HBM bandwidth of every timed kernel kind with a byte count: bytes
+    per launch (ARRAYS_PER_ELEM over the mean box) / mean event-timed launch, and its
+    fraction of the peak."""
+    out = {}
+    for kind, (ms, n) in kinds.items():
+        bpl = bytes_per_launch(cfg, kind, esz, fused)
+        if bpl is None or not n or ms <= 0:
+            continue
+        gbs = bpl / (ms / n / 1e3) / 1e9
+        out[kind] = {"gbs": round(gbs, 1), "frac": round(gbs / peak, 3)}
+    return out
 
 
 def job_time_ms(ms, dist, device):
@@ -778,6 +792,7 @@ def main():
             "clocks": clocks,
             "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kinds.items(),
                                                                  key=lambda x: -x[1][0])},
+            "kernels_hbm": kernel_hbm_table(cfg, kinds, esz, fused, peak),
             "force": {"F": list(F), "F_along_motion": Fmot},
         }
         print(json.dumps(line), flush=True)

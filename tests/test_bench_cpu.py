@@ -61,3 +61,19 @@ def test_level_step_boxes():
     assert len(boxes) == 2 ** cfg["n_levels"] - 1
     assert boxes[0] == (n + 8) ** 3
     assert sorted(set(boxes)) == sorted({(n + 8) ** 3, min(n + 16, n + 2 * G) ** 3})
+
+
+def test_kernel_hbm_table():
+    """bytes per launch over the mean box / mean launch time; kinds without a byte
+    count are left out"""
+    cfg = I.precision()
+    boxes = bench.level_step_boxes(cfg)
+    mean_box = sum(boxes) / len(boxes)
+    kinds = {"source": (10.0, 310), "sweep": (68.5, 930), "dt": (1.5, 100)}
+    t = bench.kernel_hbm_table(cfg, kinds, 4, True, 6800.0)
+    assert set(t) == {"source", "sweep"}
+    gbs = 12 * 4 * mean_box / (10.0 / 310 / 1e3) / 1e9
+    assert t["source"]["gbs"] == pytest.approx(gbs, abs=0.1)
+    assert t["source"]["frac"] == pytest.approx(gbs / 6800.0, abs=1e-3)
+    assert t["sweep"]["gbs"] == pytest.approx(11 * 4 * mean_box / (68.5 / 930 / 1e3) / 1e9,
+                                              abs=0.1)
