@@ -1063,68 +1063,7 @@ __device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_l
 // computed once per tile.  Along a staggered field's own axis the fine faces lie on
 // the host face (copied) or midway to the next one (mean of the two, which favours
 // neither side), so a mirror-symmetric coarse state gives mirror-symmetric ghosts.
-constexpr int kCuHosts = kBlock;  // hosts per tile, at most 64 per side
-constexpr int kCuZ = 396;         // max (tx + 2)(ty + 2) over tx, ty <= 64, tx ty <= 256
-constexpr int kCuY = 384;         // max ty (tx + 2) over the same tiles
-
-struct CuBox {
-  int x0, y0, z0, ex, ey, ez;  // first host and extents
-  int tx, ty, ntx, nty;        // tile size and tiles per plane
-};
-
-// host range along an axis: 0 lower ghost hosts, 1 upper ghost hosts, 2 kept hosts,
-// 3 all hosts; m = n/2 hosts span the active cells, k0 = 1 on a field's own axis
-__host__ __device__ inline void cu_range(int which, int m, int hg, int k0, int& lo, int& e) {
-  if (which == 0) {
-    lo = -hg;
-    e = hg + k0;
-  } else if (which == 1) {
-    lo = m;
-    e = hg;
-  } else if (which == 2) {
-    lo = k0;
-    e = m - k0;
-  } else {
-    lo = -hg;
-    e = m + 2 * hg;
-  }
-}
-
-// box b (0..5) of the shell of a field whose own axis is sa (-1 for a cell field)
-__host__ __device__ inline CuBox cu_box(const int* n, int G, int sa, int b) {
-  // x: all, all, all, all, lower, upper; y: all, all, lower, upper, kept, kept;
-  // z: lower, upper, then kept
-  CuBox B;
-  const int hg = G >> 1;
-  cu_range(b < 4 ? 3 : b - 4, n[0] >> 1, hg, sa == 0, B.x0, B.ex);
-  cu_range(b < 2 ? 3 : b < 4 ? b - 2 : 2, n[1] >> 1, hg, sa == 1, B.y0, B.ey);
-  cu_range(b < 2 ? b : 2, n[2] >> 1, hg, sa == 2, B.z0, B.ez);
-  if (B.ex <= 0 || B.ey <= 0 || B.ez <= 0) {
-    B.ez = 0;
-    B.tx = B.ty = 1;
-    B.ntx = B.nty = 0;
-    return B;
-  }
-  const int sx = (B.ex + 63) / 64;
-  B.tx = (B.ex + sx - 1) / sx;
-  int ty = B.ey < 64 ? B.ey : 64;
-  if (ty > kCuHosts / B.tx) ty = kCuHosts / B.tx;
-  B.nty = (B.ey + ty - 1) / ty;
-  B.ty = (B.ey + B.nty - 1) / B.nty;
-  B.ntx = (B.ex + B.tx - 1) / B.tx;
-  return B;
-}
-
-// chunks of one CommUp launch into a fine level
-__host__ __device__ inline long long cu_chunks(const int* n, int G) {
-  long long c = 0;
-  for (int f = 0; f < 5; ++f)
-    for (int b = 0; b < 6; ++b) {
-      const CuBox B = cu_box(n, G, f >= F_VX ? f - F_VX : -1, b);
-      c += (long long)B.ez * B.ntx * B.nty;
-    }
-  return c;
-}
+static_assert(kCuHosts == kBlock, "one thread per host of a CommUp tile");
 
 template <class T>
 __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F, unsigned tid) {

@@ -1,0 +1,23 @@
+"""The CommUp tiling (host-callable helpers of the kernel, internal.h) checked on the
+CPU by brute force: compiled as host code with nvcc, no GPU needed."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1812_03191_gb300", "csrc")
+
+
+def test_commup_tiles_cover_the_ghost_hosts_exactly(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    exe = str(tmp_path / "commup_tiles_check")
+    subprocess.run([nvcc, "-std=c++17", "-O1", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+                    "-o", exe, os.path.join(ROOT, "tests", "commup_tiles_check.cu")],
+                   check=True, capture_output=True, timeout=300)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout[-2000:]
+    assert out.stdout.startswith("OK ")
