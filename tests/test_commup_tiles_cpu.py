@@ -21,3 +21,18 @@ def test_commup_tiles_cover_the_ghost_hosts_exactly(tmp_path):
     out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stdout[-2000:]
     assert out.stdout.startswith("OK ")
+
+
+def test_box_decode_division_is_exact(tmp_path):
+    """Box::magic: (t m) >> s == t / d for t < 2^31 at every quotient boundary tried
+    and at pseudo-random t, divisors 1..4096 and sampled plane sizes up to 1.5 Mi"""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    exe = str(tmp_path / "magic_div_check")
+    subprocess.run([nvcc, "-std=c++17", "-O2", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+                    "-o", exe, os.path.join(ROOT, "tests", "magic_div_check.cu")],
+                   check=True, capture_output=True, timeout=300)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout[-2000:]
+    assert out.stdout.startswith("OK ")
