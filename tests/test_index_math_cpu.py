@@ -1,5 +1,6 @@
-"""The CommUp tiling (host-callable helpers of the kernel, internal.h) checked on the
-CPU by brute force: compiled as host code with nvcc, no GPU needed."""
+"""Index arithmetic of the kernels, checked on the CPU by brute force: the CommUp
+tiling and the box decode's multiply-shift division (host-callable helpers in
+internal.h, compiled as host code with nvcc; no GPU needed)."""
 import os
 import shutil
 import subprocess
