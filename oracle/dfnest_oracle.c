@@ -71,7 +71,12 @@
  *      the child's active box.
  * R13  Level-0 boundary fill: periodic, outflow (copy of the nearest active
  *      element), inflow (background rho0, e0, V in every ghost element) or reflect
- *      (mirror, normal velocity odd with the wall face set to 0).
+ *      (mirror, normal velocity odd with the wall face set to 0).  The two boundary
+ *      faces of the normal velocity v_d (index G below the first active cell, G+n
+ *      above the last) are treated alike, so the fill is mirror-symmetric, as the
+ *      Sec. 3.4 problem is: under outflow both are left to the solver and the ghost
+ *      faces beyond copy them; an injection face holds V on its boundary face on
+ *      either side; a wall face is 0 on either side.
  * R15  SubStep2 (named in Sec. 3.3 after ZEUS) is the von Neumann-Richtmyer
  *      artificial viscosity of ZEUS (Stone & Norman 1992), applied after the first
  *      kick when av_c2 > 0 (off by default: the paper's flows are nearly linear).
@@ -346,7 +351,13 @@ static void bc_axis(or_sim* S, olevel* L, int d, int side, int type) {
               src = side == 0 ? dst + n : dst - n;
               break;
             case OR_BC_OUTFLOW:
-              src = side == 0 ? G : G + n - 1;
+              /* the nearest active element; for v_d that is the boundary face itself
+               * (G or G+n), which the solver owns on both sides (R13) */
+              if (normal && side == 1) {
+                if (g == 1) continue;
+                src = G + n;
+              } else
+                src = side == 0 ? G : G + n - 1;
               break;
             case OR_BC_INFLOW:
               use_fixed = 1;
@@ -382,9 +393,11 @@ static void bc_axis(or_sim* S, olevel* L, int d, int side, int type) {
           }
         }
       }
-      if (type == OR_BC_REFLECT && side == 0) {
+      /* the lower boundary face G of v_d: zero at a wall, V on an injection face (the
+       * upper boundary face G+n is the g = 1 ghost element of the upper side) */
+      if ((type == OR_BC_REFLECT || type == OR_BC_INFLOW) && side == 0) {
         c[d] = G;
-        L->q[VXF + d][idx(L, c[0], c[1], c[2])] = 0.0;
+        L->q[VXF + d][idx(L, c[0], c[1], c[2])] = type == OR_BC_INFLOW ? S->V[d] : 0.0;
       }
     }
 }
