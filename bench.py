@@ -1,11 +1,13 @@
 #!/usr/bin/env python3
 """Benchmark of one coarse step of the nested-mesh solver on GB300.
 
-Workload (default): 3 nested levels of 64^3 cells, ratio 2, coarse box [-8,8]^3,
-Mach 0.5 wind, GM=0.01, chi=1, Gaussian luminosity L_c, FP64 state (the nested
-configuration the metric is quoted on).  A step is one coarse step: the Eq. 55
-time-step reduction, the Sec. 3.3 recursion over all levels (7 level steps),
-CommFlux/CommUp/CommMean, and the Eq. 18 force reduction.
+Workload (default): the precision configuration, the largest single-GPU one: 5
+nested levels of 128^3 cells (10.5 M cells), ratio 2, coarse box [-16,16]^3, Mach
+1.2 wind, GM=0.01, chi=1, Gaussian luminosity L_c.  The headline run holds the
+state in FP64; the same workload in FP32 state (FP64 force, time step and frontier
+flux sums) runs beside it in the same line, with its error against the FP64 run.
+A step is one coarse step: the Eq. 55 time-step reduction, the Sec. 3.3 recursion
+over all levels (31 level steps), CommFlux/CommUp/CommMean, and the Eq. 18 force.
 
 Metric: cell-updates/s summed over levels (sub-cycles counted).  `value` is timed
 with inputs resident in HBM; `e2e` through the C ABI with the state uploaded from
@@ -13,7 +15,7 @@ pinned host memory and the force read back every step.  Multi-GPU runs are
 independent replicas (weak scaling, no collective on the data path).
 
 --impl reference times the FP64 CPU oracle (the reference arm of this build) on
-bounded samples of the same workload.
+whole coarse steps of the same workload.
 """
 from __future__ import annotations
 
@@ -139,10 +141,6 @@ ARRAYS_PER_ELEM = {
 # FP64 flops executed per box element (DADD + DMUL + 2 DFMA, from the ncu capture in
 # profiles/k_sweeps_nested_3x64_fp64.md) of the FP64 sweep kernels
 FP64_FLOPS_PER_ELEM = {"tflux": 40.9, "tmom": 80.4, "tupdate": 14.1}
-# FP64 peak of GB300 derived from unit counts and the clock: 2 DFMA lanes per SM per
-# cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on peak_sustained = 2),
-# x 2 flops x 152 SMs x 2.07 GHz
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) per box element of a launch, from the ncu captures in
 # profiles/ (k_sweeps_nested_3x64_fp64.md: tmom, 80^3 box, 20.1 MB;
@@ -153,13 +151,14 @@ TRAFFIC_PER_ELEM = {("nested_3x64^3_fp64", 8, "tmom"): 20.1e6 / 80**3,
 
 
 def level_step_boxes(cfg):
-    """box elements of every level step of one coarse step (level 0: margin 4;
-    finer levels: first sub-cycle margin 8, second margin 4, capped at the array)."""
+    """box elements of every level step of one coarse step (level 0: margin 4, one
+    more element on the upper side; finer levels: first sub-cycle margin 8, second
+    margin 4; capped at the array)."""
     n, G = cfg["n"], cfg["G"]
-    margins = [4]
+    out = [min(n + 9, n + 2 * G) ** 3]
     for l in range(1, cfg["n_levels"]):
-        margins += [8, 4] * 2 ** (l - 1)
-    return [min(n + 2 * m, n + 2 * G) ** 3 for m in margins]
+        out += [min(n + 2 * m, n + 2 * G) ** 3 for m in (8, 4)] * 2 ** (l - 1)
+    return out
 
 
 def bytes_per_launch(cfg, kind, esz, fused=False):
@@ -248,12 +247,23 @@ def oracle_openmp_rate(cfg, budget_s):
 
 
 def run_reference(args, cfg):
+    """The reference arm: the FP64 oracle timed on whole coarse steps of the workload,
+    on the host cores.  The precision workload (6.5e7 cell-updates per coarse step,
+    about 25 s single-threaded) runs on the oracle's OpenMP build, bitwise the plain
+    build's results, so that W + K steps end within a few minutes; the smaller
+    workloads run single-threaded."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     cu = cell_updates_per_step(cfg)
     from oracle import Oracle
-    orc = Oracle(cfg["n_levels"], cfg["n"], cfg["lo"], cfg["hi"], cfg["G"], cfg["params"])
+    omp = cfg["name"].startswith("precision")
+    cores = 1
+    if omp:
+        import oracle
+        cores = oracle.threads(os.cpu_count() or 1)
+    orc = Oracle(cfg["n_levels"], cfg["n"], cfg["lo"], cfg["hi"], cfg["G"], cfg["params"],
+                 omp=omp)
     for _ in range(args.warmup):
         orc.step(1)
     times = []
@@ -271,9 +281,12 @@ def run_reference(args, cfg):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": cfg["name"], "n_levels": cfg["n_levels"], "n": cfg["n"],
                    "box": [cfg["lo"][0], cfg["hi"][0]], "ghost": cfg["G"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                         "kind": "oracle (OpenMP build)" if omp else "oracle",
                          "sample": f"{args.steps} whole coarse steps of {cfg['name']} "
-                                   f"after {args.warmup} warm-up steps, single-threaded C"},
+                                   f"after {args.warmup} warm-up steps, "
+                                   + (f"{cores} threads (plane loops in parallel, sums "
+                                      f"serial)" if omp else "single-threaded C")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -604,18 +617,127 @@ def run_paper_hierarchy(args):
     return 0
 
 
+def time_sim(sim, cfg, args, stream, flush, local, fused):
+    """Autotune (state restored), W warm-up coarse steps, then K graph-replayed coarse
+    steps bracketed by CUDA events on the launching stream with the L2 flushed between
+    steps; then K more steps with an event pair around every launch (no graph) for
+    the per-kernel times.  Returns the measurements."""
+    from paper_1812_03191_gb300 import binding
+    import torch
+    shapes = sim.autotune() if args.tiles == "auto" else None
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    l0 = sim.kernel_launches()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            sim.step(1)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = sim.kernel_launches() - l0
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    sim.set_timing(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        sim.step(1)
+    kinds = {}
+    for kind in range(binding.KERNEL_KINDS):
+        kms, kn = sim.kernel_time(kind)
+        if kn:
+            kinds[binding.kernel_name(kind)] = (kms, kn)
+    sim.set_timing(False)
+    F, Fmot = sim.force()
+    return dict(ms=ms, launches=launches, clocks=clk.summary(), kinds=kinds, F=F, Fmot=Fmot,
+                shapes=shapes, fused=fused)
+
+
+# SURVEY-defined algorithmic bytes per cell-update of a whole level step: the five
+# fields read and written once (rho, e, v_x, v_y, v_z)
+B_ALG = {8: 80, 4: 40}
+# kernels launched once per level step (or per sweep of one), each over one level's
+# active cells: the units one launch processes are that level's cells
+LEVEL_STEP_KERNELS = ("source", "compress_lum", "diffuse", "tprep", "tflux", "tmom",
+                      "tupdate", "vrec_source", "sweep", "frontier_diff")
+
+
+def roofline_block(cfg, m, cu, esz, peak, peak_kind, fp64_peak=None):
+    """Roofline of the dominant level-step kernel and of the whole step on the
+    algorithmic bytes per cell-update (B_ALG), plus, for FP64, its FP64-pipe
+    roofline against the measured FP64 peak."""
+    kinds, ms = m["kinds"], m["ms"] / (m["steps"])
+    n = cfg["n"]
+    units = n**3 if isinstance(n, int) else int(np.prod(n))  # every level: n^3 cells
+    total_k = sum(v[0] for v in kinds.values())
+    dom = max((k for k in kinds if k in LEVEL_STEP_KERNELS), key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    avg_s = dom_ms / dom_n / 1e3
+    b_alg = B_ALG[esz]
+    achieved = b_alg * units / avg_s / 1e9
+    boxes_all = level_step_boxes(cfg)
+    tpe = TRAFFIC_PER_ELEM.get((cfg["name"], esz, dom))
+    traffic = tpe * sum(boxes_all) / len(boxes_all) if tpe is not None else None
+    step_gbs = cu * b_alg / (ms / 1e3) / 1e9
+    out = {
+        "kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+        "algorithmic_bytes_per_launch": b_alg * units,
+        "units_per_launch": f"{units} cell-updates (one level step of one {n}^3 level) "
+                            f"x {b_alg} B",
+        "launches_timed": dom_n, "avg_launch_ms": dom_ms / dom_n,
+        "share_of_kernel_time": dom_ms / total_k if total_k else None,
+        "step": {"achieved": step_gbs, "frac": step_gbs / peak,
+                 "algorithmic_bytes_per_step": cu * b_alg},
+    }
+    if esz == 8 and fp64_peak and dom in FP64_FLOPS_PER_ELEM:
+        boxes = level_step_boxes(cfg)
+        flops = FP64_FLOPS_PER_ELEM[dom] * sum(boxes) / len(boxes)
+        ach = flops / avg_s / 1e12
+        out["alu"] = {"achieved": ach, "peak": fp64_peak["tflops"], "unit": "TFLOP/s",
+                      "frac": ach / fp64_peak["tflops"],
+                      "peak_source": "measured: FP64 multiply-add probe "
+                                     "(df_measure_fp64_peak)",
+                      "fp64_flops_per_launch": flops}
+    return out
+
+
+def state_errors(cfg, s32, s64):
+    """per-field relative L2 error of the FP32-state perturbation against FP64 over
+    every level's active cells, and the relative error of the force along the motion"""
+    names = ["rho", "e", "vx", "vy", "vz"]
+    pr = cfg["params"]
+    e0 = pr["cs"] ** 2 * pr["rho0"] / (pr["gamma"] * (pr["gamma"] - 1))
+    V = [pr["mach"] * pr["cs"] * c for c in pr["flow_dir"]]
+    errs = {}
+    for f in range(5):
+        num = den = 0.0
+        base = pr["rho0"] if f == 0 else (e0 if f == 1 else V[f - 2])
+        for l in range(cfg["n_levels"]):
+            a, b = s32.get_field(l, f), s64.get_field(l, f)
+            num += float(((a - b) ** 2).sum())
+            den += float(((b - base) ** 2).sum())
+        errs[names[f]] = (num / max(den, 1e-300)) ** 0.5
+    return errs
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="nested",
+    ap.add_argument("--workload", default="precision",
                     choices=["nested", "single", "precision", "batched", "serving",
                              "precision_compare", "heating_ladder", "paper_hierarchy"])
     ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--step-cap", type=int, default=200)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="state precision of the headline run (the precision workload also "
+                         "runs the FP32 state beside its FP64 run)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--transport", default="auto", choices=["auto", "separate", "fused"],
@@ -657,110 +779,82 @@ def main():
     # CPU baseline first (oracle on the host cores, rank 0 only, bounded sample)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, nsteps, el = cpu_oracle_rate(cfg, args.cpu_budget)
+        rate, nsteps, el = cpu_oracle_rate(cfg, args.cpu_budget, steps_cap=1)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{nsteps} whole coarse steps of {cfg['name']} ({el:.1f} s, "
+               "sample": f"{nsteps} whole coarse step(s) of {cfg['name']} ({el:.1f} s, "
                          f"single-threaded C, -O2)"}
         cpu["openmp"] = oracle_openmp_rate(cfg, args.cpu_budget / 2)
 
     prec = binding.DF_FP64 if args.precision == "fp64" else binding.DF_FP32_STATE
+    both = args.workload == "precision" and prec == binding.DF_FP64
     stream = torch.cuda.current_stream()
-    sim = binding.Sim(cfg["n_levels"], cfg["n"], cfg["lo"], cfg["hi"], cfg["G"], cfg["params"],
-                      precision=prec, device=local, stream=stream.cuda_stream)
     cu = cell_updates_per_step(cfg)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
     transport = {"auto": binding.TRANSPORT_AUTO, "separate": binding.TRANSPORT_SEPARATE,
                  "fused": binding.TRANSPORT_FUSED}[args.transport]
-    sim.set_transport(transport)
     n3 = cfg["n"] ** 3 if isinstance(cfg["n"], int) else int(np.prod(cfg["n"]))
-    fused = transport == binding.TRANSPORT_FUSED or (
-        transport == binding.TRANSPORT_AUTO and prec == binding.DF_FP32_STATE
-        and n3 >= 512 * 1024)  # the library's per-level choice
-    shapes = sim.autotune() if args.tiles == "auto" else None
-    for _ in range(args.warmup):
-        sim.step(1)
-    torch.cuda.synchronize()
-
-    # ---- timed region: K graph-replayed coarse steps, L2 flushed between steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    l0 = sim.kernel_launches()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            sim.step(1)
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    launches = sim.kernel_launches() - l0
-    ms = job_time_ms(sum(a.elapsed_time(b) for a, b in ev), dist, "cuda")
-    value = job_value(cu, args.steps, world, ms)
-    clocks = clk.summary()
-    F, Fmot = sim.force()
-
-    # ---- per-kernel device time over the same number of steps (events per launch)
-    sim.set_timing(True)
-    for k in range(args.steps):
-        flush.zero_()
-        sim.step(1)
-    kinds = {}
-    for kind in range(binding.KERNEL_KINDS):
-        kms, kn = sim.kernel_time(kind)
-        if kn:
-            kinds[binding.kernel_name(kind)] = (kms, kn)
-    sim.set_timing(False)
-    total_k = sum(v[0] for v in kinds.values())
-    esz = 8 if prec == binding.DF_FP64 else 4
-    # dominant kernel with a defined algorithmic byte count
-    ranked = sorted(kinds, key=lambda k: -kinds[k][0])
-    dom = next(k for k in ranked if bytes_per_launch(cfg, k, esz, fused) is not None)
-    dom_ms, dom_n = kinds[dom]
-    bpl = bytes_per_launch(cfg, dom, esz, fused)
-    avg_s = dom_ms / dom_n / 1e3
-    achieved = bpl / avg_s / 1e9
     peak, peak_kind = peaks()
-    # DRAM traffic per launch (ncu, scaled to the mean box), when the capture exists
-    boxes_all = level_step_boxes(cfg)
-    tpe = TRAFFIC_PER_ELEM.get((cfg["name"], esz, dom))
-    traffic = tpe * sum(boxes_all) / len(boxes_all) if tpe is not None else None
-    hbm = {"achieved_gbs": achieved, "peak_gbs": peak, "frac": achieved / peak,
-           "peak_source": peak_kind, "algorithmic_bytes_per_launch": bpl}
-    if prec == binding.DF_FP64 and dom in FP64_FLOPS_PER_ELEM:
-        # the FP64 kernels are bound by GB300's FP64 pipe (ncu: ~85 % busy, DRAM < 4 %)
-        boxes = level_step_boxes(cfg)
-        flops = FP64_FLOPS_PER_ELEM[dom] * sum(boxes) / len(boxes)
-        ach = flops / avg_s / 1e12
-        roofline = {
-            "kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": traffic,
-            "peak_source": "derived: 2 DFMA/clk/SM x 2 flop x 152 SMs x 2.07 GHz",
-            "fp64_flops_per_launch": flops, "launches_timed": dom_n,
-            "avg_launch_ms": dom_ms / dom_n,
-            "share_of_kernel_time": dom_ms / total_k if total_k else None,
-            "top_kernel": ranked[0], "hbm": hbm,
+
+    # measured FP64 peak (the FP64 kernels are bound by the FP64 pipe), clocks sampled
+    with ClockSampler(local) as pclk:
+        tf, tf_ms = binding.measure_fp64_peak(local, repeats=5)
+    fp64_peak = {"tflops": tf, "best_launch_ms": tf_ms, "clocks": pclk.summary()}
+
+    def make(pr):
+        sim = binding.Sim(cfg["n_levels"], cfg["n"], cfg["lo"], cfg["hi"], cfg["G"],
+                          cfg["params"], precision=pr, device=local, stream=stream.cuda_stream)
+        sim.set_transport(transport)
+        fused = transport == binding.TRANSPORT_FUSED or (
+            transport == binding.TRANSPORT_AUTO and pr == binding.DF_FP32_STATE
+            and n3 >= 512 * 1024)  # the library's per-level choice
+        return sim, fused
+
+    sim, fused = make(prec)
+    if dist:
+        dist.barrier()
+    m = time_sim(sim, cfg, args, stream, flush, local, fused)
+    m["steps"] = args.steps
+    if dist:
+        dist.barrier()
+    ms = job_time_ms(m["ms"], dist, "cuda")
+    value = job_value(cu, args.steps, world, ms)
+    esz = 8 if prec == binding.DF_FP64 else 4
+    roofline = roofline_block(cfg, m, cu, esz, peak, peak_kind, fp64_peak)
+    kinds = m["kinds"]
+
+    # the FP32-state run of the same workload beside the FP64 one, the same number of
+    # coarse steps (each takes its own time steps), and its error against FP64
+    fp32 = None
+    if both:
+        s32, fused32 = make(binding.DF_FP32_STATE)
+        m32 = time_sim(s32, cfg, args, stream, flush, local, fused32)
+        m32["steps"] = args.steps
+        errs = state_errors(cfg, s32, sim)
+        F64, F32 = m["Fmot"], m32["Fmot"]
+        fp32 = {
+            "value": cu * args.steps / (m32["ms"] / 1e3), "unit": UNIT,
+            "ms_per_step": m32["ms"] / args.steps, "dtype": "f32-state/f64-reductions",
+            "transport": "fused sweeps" if fused32 else "separate kernels",
+            "roofline": roofline_block(cfg, m32, cu, 4, peak, peak_kind),
+            "gpu_launches": m32["launches"], "clocks": m32["clocks"],
+            "kernels_ms": {k: round(v[0], 4) for k, v in sorted(m32["kinds"].items(),
+                                                                 key=lambda x: -x[1][0])},
+            "kernels_hbm": kernel_hbm_table(cfg, m32["kinds"], 4, fused32, peak),
+            "error_vs_fp64": {
+                "coarse_steps": args.warmup + 2 * args.steps,
+                "force_along_motion_rel": abs(F32 - F64) / abs(F64),
+                "force_along_motion": {"fp64": F64, "fp32_state": F32},
+                "time": {"fp64": sim.status()[0], "fp32_state": s32.status()[0]},
+                "field_rel_l2_error_of_perturbation": errs},
         }
-    else:
-        roofline = {
-            "kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": bpl, "launches_timed": dom_n,
-            "avg_launch_ms": dom_ms / dom_n,
-            "share_of_kernel_time": dom_ms / total_k if total_k else None,
-            "top_kernel": ranked[0],
-        }
+        s32.close()
 
     # ---- e2e: state from pinned host memory, one step, force back, every step
     nstate = sim.state_size()
     host = torch.empty(nstate, dtype=torch.float64, pin_memory=True)
     st_np, t_now = sim.get_state(host.numpy())
     e2e_times = []
-    for k in range(max(3, min(args.steps, 20))):
+    for k in range(max(3, min(args.steps, 10))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim.set_state(st_np, t_now)
@@ -778,23 +872,30 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec == binding.DF_FP64 else "f32-state/f64-reductions",
             "data": "synthetic",
-            "config": {"workload": cfg["name"], "n_levels": cfg["n_levels"], "n": cfg["n"],
+            "config": {"workload": cfg["name"] + ("_fp64" if prec == binding.DF_FP64
+                                                  else "_fp32_state"),
+                       "n_levels": cfg["n_levels"], "n": cfg["n"],
                        "box": [cfg["lo"][0], cfg["hi"][0]], "ghost": cfg["G"],
+                       "mach": cfg["params"]["mach"], "chi": cfg["params"]["chi"],
+                       "luminosity": cfg["params"]["L"],
                        "cell_updates_per_step": cu, "l2": "flushed between timed steps "
-                       "(256 MB write outside the step events)",
+                       "(256 MB write outside the step events); working set above L2",
                        "parallelism": f"replicas{world}" if world > 1 else "single-gpu",
-                       "tile_shapes": tile_summary(shapes),
+                       "tile_shapes": tile_summary(m["shapes"]),
                        "transport": "fused sweeps" if fused else "separate kernels"},
             "roofline": roofline,
+            "fp64_peak_measured": fp64_peak,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clocks,
+            "gpu_launches": m["launches"],
+            "clocks": m["clocks"],
             "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kinds.items(),
                                                                  key=lambda x: -x[1][0])},
             "kernels_hbm": kernel_hbm_table(cfg, kinds, esz, fused, peak),
-            "force": {"F": list(F), "F_along_motion": Fmot},
+            "force": {"F": list(m["F"]), "F_along_motion": m["Fmot"]},
         }
+        if fp32 is not None:
+            line["fp32_state"] = fp32
         print(json.dumps(line), flush=True)
     sim.close()
     if dist:

@@ -120,6 +120,22 @@ int df_create_ground(df_ctx** out, int n_levels, const int n0[3], const int n[3]
                      const double lo[3], const double hi[3], int G, int precision, int device,
                      void* stream);
 
+/* The problem statement's constructor (Sec. 3: n_levels nested meshes, refinement
+ * ratio 2, centred on the perturber; Sec. 3.4: the coarse box): N^3 active cells on
+ * every level, level l spanning [coarse_lo 2^-l, coarse_hi 2^-l], and
+ * DF_DEFAULT_GHOST ghost layers (twice the reach of one level step, so the active
+ * cells do not depend on the ghost width).  Equivalent to df_create with
+ * n = (N, N, N) and G = DF_DEFAULT_GHOST, except that device memory comes from
+ * alloc(bytes, user) / dealloc(ptr, user) when they are given (both or neither;
+ * same contract as df_set_allocator: 256-byte aligned memory of `device`, NULL on
+ * failure); with both NULL, from the allocator df_set_allocator installed, else
+ * cudaMalloc.  The context keeps the callbacks until df_destroy.  Errors as
+ * df_create; DF_EINVAL when only one callback is given. */
+#define DF_DEFAULT_GHOST 8
+int df_create_levels(df_ctx** out, int n_levels, int N, const double coarse_lo[3],
+                     const double coarse_hi[3], int precision, int device, void* stream,
+                     df_alloc_fn alloc, df_free_fn dealloc, void* user);
+
 /* Copy the parameters, precompute the static potential (Eq. 16) and luminosity
  * weights, and set every level to the uniform background (Sec. 3.4): rho0, e0, V.
  * Resets t to 0 and clears the force history.  DF_EINVAL on bad values, and when
@@ -131,9 +147,10 @@ int df_set_params(df_ctx* ctx, const df_params* p);
  * CommFlux, CommUp, CommMean), then the force of Eq. 18.  With xi_mode = 1 the
  * Eq. 55-56 search also runs on the device each step and the second sub-cycles
  * of levels with xi = 1 do no work, so either mode replays one CUDA graph.
- * Asynchronous on the context's stream; DF_EUNHEALTHY is reported by the next
- * synchronising call. */
-int df_step(df_ctx* ctx, int n_coarse_steps);
+ * t_out NULL: asynchronous on the context's stream, and DF_EUNHEALTHY is reported
+ * by the next synchronising call.  t_out given: the call synchronises, writes the
+ * simulated time after the steps and returns DF_EUNHEALTHY if the state went bad. */
+int df_step(df_ctx* ctx, int n_coarse_steps, double* t_out);
 
 /* Synchronise, then return time, last coarse step and health (0 healthy). */
 int df_status(df_ctx* ctx, double* t, double* dt_last, int* unhealthy);
@@ -231,33 +248,51 @@ int df_destroy(df_ctx* ctx);
  * in units in the last place of the IEEE quotient.  Synchronous. */
 int df_check_division(const double* a, const double* b, int n, double* max_ulp);
 
+/* Measured FP64 throughput of the device: a kernel of independent chains of
+ * dependent fused multiply-adds over 8 blocks of 256 threads per SM, timed with CUDA
+ * events (best of `repeats` after one warm-up launch).  *tflops receives the FP64
+ * flops per second / 1e12 (a multiply-add counts 2), *ms_best (nullable) the best
+ * launch's duration.  It is the denominator of the FP64 kernels' ALU roofline.
+ * Allocates 8 bytes of device memory for the duration of the call. */
+int df_measure_fp64_peak(int device, int repeats, double* tflops, double* ms_best);
+
 /* Force of one level without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- a host whose
  * device memory is entirely reserved by another allocator, a latency-critical loop
  * that cannot afford cudaMalloc's implicit device synchronisation, or a sandboxed
- * plug-in that is not allowed to allocate.  It computes the same per-level sum as
- * the context's force reduction (Eq. 18 terms with rho - rho0, cells whose centre
- * lies in the child box excluded), with its scratch -- one triple of partial sums
- * per 256 active cells -- in a fixed file-scope device array of
- * DF_NOALLOC_MAX_CELLS/256 triples (384 KiB) that every GPU loading the library
- * holds until the process exits.
- *  rho: device pointer to the padded density array of the level, ((n+2G)^3, x fastest);
+ * plug-in that is not allowed to allocate.  It sums, over the active cells of one
+ * level whose centre lies outside the covered box, GM times (rho - rho0) times the
+ * cell volume times r / (r^2 + eps^2)^(3/2), r the cell centre's position relative
+ * to the perturber at the origin -- the same per-level sum as the context's force
+ * reduction.  Its scratch -- one triple of partial sums per 256 active cells -- is a
+ * fixed file-scope device array of DF_NOALLOC_MAX_CELLS/256 triples (384 KiB) that
+ * every GPU loading the library holds until the process exits.
+ *  rho: device pointer to the padded FULL density of the level ((n+2G)^3, x fastest),
+ *    as df_get_full returns it -- not the deviation rho - rho0 a context stores;
  *  n, G, lo (lower corner of the active box), dx: the level's geometry (host arrays);
- *  child_off, child_n: the covered box in this level's active cells and the child's
- *    cell counts halved (both NULL for a level without a child);
- *  GM, eps, rho0: Eq. 18 parameters; F_out: device pointer to 3 doubles (written).
+ *  child_off, child_n: the covered box in this level's active cells (offset and
+ *    extent, the child's cell counts halved; 0 <= child_off[d], 1 <= child_n[d],
+ *    child_off[d] + child_n[d] <= n[d]), both NULL for a level without a child;
+ *  GM, eps, rho0: perturber mass, softening length, background density;
+ *  mirror: bit d set when the lower face of axis d is a mirror plane through the
+ *    perturber (a quadrant-domain context): the result is then the unfolded domain's,
+ *    as df_force_now gives it -- 0 along each mirror axis, 2^(bits set) times the
+ *    simulated part's sum for the others; 0 for a whole-domain level;
+ *  F_out: device pointer to 3 doubles (written).
  * The first call on a device looks up the array's device address once (with that
  * device current); make that first call before any stream capture.  Every call uses
  * the same array and leaves its contents behind; each call writes every partial it
  * reads, so nothing needs clearing, but calls whose work overlaps on the GPU (on
  * different streams, or from several threads) race on the array and give wrong sums.
- * Asynchronous on `stream`.  DF_EINVAL for null pointers, bad sizes or more than
- * DF_NOALLOC_MAX_CELLS active cells; DF_ECUDA if the lookup or a launch fails.
- * It calls no cudaMalloc, cudaFree or allocating library routine. */
+ * Asynchronous on `stream`.  DF_EINVAL for null pointers, bad sizes, a covered box
+ * outside the level, a mirror mask outside 0..7 or more than DF_NOALLOC_MAX_CELLS
+ * active cells; DF_ECUDA if the lookup or a launch fails.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine. */
 #define DF_NOALLOC_MAX_CELLS 4194304
 int df_force_level_noalloc(const double* rho, const int n[3], int G, const double lo[3],
                            const double dx[3], const int child_off[3], const int child_n[3],
-                           double GM, double eps, double rho0, double* F_out, void* stream);
+                           double GM, double eps, double rho0, int mirror, double* F_out,
+                           void* stream);
 
 /* ---- Batched runs (pools).  A pool holds many independent hierarchies ("runs",
  * e.g. a parameter sweep or a stream of simulation requests) on one GPU and
@@ -299,6 +334,20 @@ int df_pool_step(df_pool* pool, int n_coarse_steps);
  * F_z of the last coarse step, t, the last coarse dt, and the health flag (NaN for
  * empty slots).  Returns the number of slots written. */
 int df_pool_query(df_pool* pool, double* out, int max_slots);
+
+/* Force on the perturber of one slot's run after its last coarse step (Eq. 18, as
+ * df_force) and its simulated time (t_out nullable).  Synchronises the pool's
+ * stream.  DF_EINVAL for an empty slot; DF_EUNHEALTHY (outputs still written) when
+ * that run's state went bad -- the other slots are unaffected. */
+int df_pool_force(df_pool* pool, int slot, double F_out[3], double* t_out);
+
+/* Force history of one slot's run: the last min(k, steps taken, 4096) coarse steps,
+ * oldest first, 4 doubles each -- F_x, F_y, F_z after the step (Eq. 18) and the time
+ * at its end -- written to out (4k doubles); *got receives the entry count.
+ * Synchronises the pool's stream.  A server can step a run several coarse steps
+ * between two reads and still test a convergence rule at every step.  DF_EINVAL for
+ * an empty slot, a null pointer or k < 0. */
+int df_pool_history(df_pool* pool, int slot, int k, double* out, int* got);
 
 /* Active cells of one field of one level of a slot's run, FP64 (as df_get_field). */
 int df_pool_get_field(df_pool* pool, int slot, int level, int field, double* host_out);

@@ -31,7 +31,8 @@ EXPORTS = (
     "df_pool_autotune", "df_pool_destroy", "df_pool_set_timing", "df_pool_kernel_time",
     "df_autotune", "df_set_tile_shapes", "df_pool_set_tile_shapes", "df_set_transport",
     "df_pool_set_transport", "df_pool_set_field", "df_create_ground", "df_run_bytes_ground",
-    "df_pool_admit_ground", "df_set_allocator",
+    "df_pool_admit_ground", "df_set_allocator", "df_create_levels", "df_pool_force",
+    "df_pool_history", "df_measure_fp64_peak",
 )
 POOL_OPS = 22
 # operator order of the per-op tables (tile shapes, blocks per SM)
@@ -95,7 +96,12 @@ def load(path: str = LIB_PATH):
         "df_create_ground": (C.c_int, [P(vp), C.c_int, P(C.c_int), P(C.c_int), dp, dp, C.c_int,
                                        C.c_int, C.c_int, vp]),
         "df_set_params": (C.c_int, [vp, P(Params)]),
-        "df_step": (C.c_int, [vp, C.c_int]),
+        "df_step": (C.c_int, [vp, C.c_int, dp]),
+        "df_create_levels": (C.c_int, [P(vp), C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, vp,
+                                       vp, vp, vp]),
+        "df_pool_force": (C.c_int, [vp, C.c_int, dp, dp]),
+        "df_pool_history": (C.c_int, [vp, C.c_int, C.c_int, dp, P(C.c_int)]),
+        "df_measure_fp64_peak": (C.c_int, [C.c_int, C.c_int, dp, dp]),
         "df_status": (C.c_int, [vp, dp, dp, P(C.c_int)]),
         "df_force": (C.c_int, [vp, dp, dp]),
         "df_force_now": (C.c_int, [vp, dp]),
@@ -146,7 +152,7 @@ def load(path: str = LIB_PATH):
         "df_pool_kernel_time": (C.c_int, [vp, C.c_int, dp, P(C.c_longlong)]),
         "df_force_level_noalloc": (C.c_int, [vp, P(C.c_int), C.c_int, dp, dp, P(C.c_int),
                                              P(C.c_int), C.c_double, C.c_double, C.c_double,
-                                             vp, vp]),
+                                             C.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -206,6 +212,14 @@ def use_torch_allocator(on=True):
     _check(lib.df_set_allocator(C.cast(pair[0], C.c_void_p), C.cast(pair[1], C.c_void_p), None))
 
 
+def measure_fp64_peak(device=0, repeats=5):
+    """(TFLOP/s, best launch ms) of the library's FP64 multiply-add probe"""
+    lib = load()
+    tf, ms = C.c_double(), C.c_double()
+    _check(lib.df_measure_fp64_peak(int(device), int(repeats), C.byref(tf), C.byref(ms)))
+    return tf.value, ms.value
+
+
 def check_division(a, b):
     """max ulp difference of the kernels' FP64 division from IEEE division"""
     lib = load()
@@ -217,15 +231,16 @@ def check_division(a, b):
 
 
 def force_level_noalloc(rho_dev_ptr, n, G, lo, dx, child_off=None, child_n=None, GM=0.0,
-                        eps=0.0, rho0=1.0, F_dev_ptr=0, stream=None):
-    """Per-level Eq. 18 force on device buffers, with no device allocation (see the
-    C declaration).  rho_dev_ptr / F_dev_ptr are device addresses (ints)."""
+                        eps=0.0, rho0=1.0, F_dev_ptr=0, stream=None, mirror=0):
+    """Per-level force on device buffers, with no device allocation (see the C
+    declaration).  rho_dev_ptr (the FULL density) / F_dev_ptr are device addresses
+    (ints); mirror: bit d for a mirror plane at the lower face of axis d."""
     lib = load()
     ci = lambda v: (C.c_int * 3)(*v) if v is not None else None  # noqa: E731
     cd = lambda v: (C.c_double * 3)(*v)  # noqa: E731
     _check(lib.df_force_level_noalloc(C.c_void_p(rho_dev_ptr), ci(n), int(G), cd(lo), cd(dx),
                                       ci(child_off), ci(child_n), float(GM), float(eps),
-                                      float(rho0), C.c_void_p(F_dev_ptr),
+                                      float(rho0), int(mirror), C.c_void_p(F_dev_ptr),
                                       C.c_void_p(stream) if stream else None))
 
 
@@ -293,8 +308,14 @@ class Sim:
         self.params = dict(params)
         _check(self.lib.df_set_params(self.h, C.byref(Params.from_dict(params))))
 
-    def step(self, n=1):
-        _check(self.lib.df_step(self.h, int(n)))
+    def step(self, n=1, want_t=False):
+        """advance n coarse steps (asynchronous); want_t: synchronise and return t"""
+        if not want_t:
+            _check(self.lib.df_step(self.h, int(n), None))
+            return None
+        t = C.c_double()
+        _check(self.lib.df_step(self.h, int(n), C.byref(t)))
+        return t.value
 
     def status(self):
         t, dt = C.c_double(), C.c_double()
@@ -471,6 +492,22 @@ class Pool:
         if ns < 0:
             _check(ns)
         return out[:6 * ns].reshape(ns, 6)
+
+    def force(self, slot):
+        """(F, t) of one slot's run after its last coarse step; raises DfError with
+        DF_EUNHEALTHY when that run's state went bad"""
+        F = np.zeros(3)
+        t = C.c_double()
+        _check(self.lib.df_pool_force(self.h, int(slot), _dp(F), C.byref(t)))
+        return F, t.value
+
+    def history(self, slot, k):
+        """array (m, 4) of the last m <= k coarse steps of a slot's run, oldest first:
+        F_x, F_y, F_z after the step and the time at its end"""
+        out = np.empty(4 * max(int(k), 1))
+        got = C.c_int()
+        _check(self.lib.df_pool_history(self.h, int(slot), int(k), _dp(out), C.byref(got)))
+        return out[:4 * got.value].reshape(got.value, 4)
 
     def set_field(self, slot, level, field, values):
         nl, n, n0 = self.shapes[slot]

@@ -174,7 +174,7 @@ size_t run_bytes(int nl, const int n0[3], const int n[3], int G, int prec) {
   }
   size_t pel = std::max(3 * np, (na_max + 255) / 256);
   return total + plane_bytes(nc_max, esz) * 12 + sizeof(DevScalars) + pel * 8 +
-         3 * 4096 * 8 + 8 + 8 + nc_max * 8;
+         kRingStride * 4096 * 8 + 8 + 8 + nc_max * 8;
 }
 
 void run_free(Run* r) {
@@ -251,7 +251,7 @@ int check_mirror(int n_levels, const double lo[3], const df_params* p) {
 }
 
 int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const double lo[3],
-               const double hi[3], int G, int precision) {
+               const double hi[3], int G, int precision, const Allocator& al) {
   *out = nullptr;
   int rc0 = check_shape(n_levels, n0, n, lo, hi, G, precision);
   if (rc0) return rc0;
@@ -260,7 +260,7 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
   r->nl = n_levels;
   r->prec = precision;
   r->G = G;
-  r->al = g_allocator;
+  r->al = al;
   r->esz = precision == DF_FP64 ? 8 : 4;
   for (int d = 0; d < 3; ++d) {
     r->n0[d] = n0[d];
@@ -375,7 +375,7 @@ int run_create(Run** out, int n_levels, const int n0[3], const int n[3], const d
   r->n_partials = np;
   size_t pelems = std::max(3 * (size_t)np, (na_max + 255) / 256);
   CKR(dev_alloc(r->al, (void**)&r->partials, pelems * sizeof(double)));
-  CKR(dev_alloc(r->al, (void**)&r->ring, 3 * (size_t)r->ring_cap * sizeof(double)));
+  CKR(dev_alloc(r->al, (void**)&r->ring, kRingStride * (size_t)r->ring_cap * sizeof(double)));
   CKR(dev_alloc(r->al, (void**)&r->ring_pos, sizeof(long long)));
   CKR(cudaMemset(r->ring_pos, 0, sizeof(long long)));
   CKR(dev_alloc(r->al, (void**)&r->wsum, sizeof(double)));
@@ -630,14 +630,18 @@ struct Builder {
   // artificial viscosity is on (its viscous pressures one cell below a box edge are
   // not formed by a margin box, and the reach behind the margins was measured
   // without it): then every operator sweeps the whole padded array
-  Box box(const LevelView& v, int margin, bool whole = false) const {
+  // On level 0 the upper boundary face G + n of v_d is the solver's and keeps its
+  // value from one level step to the next, as the lower face G does, so the box
+  // reaches one element further up: the margin covers the reach of one level step
+  // above that face too.
+  Box box(const LevelView& v, int margin, bool whole = false, int up = 0) const {
     Box b;
     b.tile = 0;
     b.zc = 0;
     int M = (full_boxes || whole) ? v.G : margin;
     for (int d = 0; d < 3; ++d) {
       b.lo[d] = std::max(0, v.G - M);
-      b.hi[d] = std::min(v.s[d], v.G + v.n[d] + M);
+      b.hi[d] = std::min(v.s[d], v.G + v.n[d] + M + up);
     }
     b.set_divisors();
     return b;
@@ -664,7 +668,7 @@ struct Builder {
 
   void level_step(const Run& r, int l, int m_out, std::vector<Entry>& out) const {
     Item<T> it = base(r, l);
-    it.b = box(it.L, m_out + kReach, r.P.av_c2 > 0.0);
+    it.b = box(it.L, m_out + kReach, r.P.av_c2 > 0.0, l == 0 ? 1 : 0);
     const Phys& P = r.P;
     if (l == 0)
       for (int d = 0; d < 3; ++d) {
@@ -1185,7 +1189,7 @@ int snapshot(const std::vector<Run*>& runs, Snapshot& sn) {
                     cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(sn.acc[i].data() + amax * l, r->L[l].acc, ab, cudaMemcpyDeviceToHost));
     }
-    sn.ring[i].resize(3 * (size_t)r->ring_cap * sizeof(double));
+    sn.ring[i].resize(kRingStride * (size_t)r->ring_cap * sizeof(double));
     CK(cudaMemcpy(sn.ring[i].data(), r->ring, sn.ring[i].size(), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&sn.ds[i], r->ds, sizeof(DevScalars), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&sn.pos[i], r->ring_pos, sizeof(long long), cudaMemcpyDeviceToHost));
@@ -1348,9 +1352,13 @@ int df_create(df_ctx** out, int n_levels, const int n[3], const double lo[3], co
   return df_create_ground(out, n_levels, n, n, lo, hi, G, precision, device, stream);
 }
 
-int df_create_ground(df_ctx** out, int n_levels, const int n0[3], const int n[3],
-                     const double lo[3], const double hi[3], int G, int precision, int device,
-                     void* stream) {
+}  // extern "C"
+
+namespace {
+
+int create_ctx(df_ctx** out, int n_levels, const int n0[3], const int n[3], const double lo[3],
+               const double hi[3], int G, int precision, int device, void* stream,
+               const Allocator& al) {
   if (!out || !n0 || !n || !lo || !hi) return fail(DF_EINVAL, "null argument");
   *out = nullptr;
   int rc = check_shape(n_levels, n0, n, lo, hi, G, precision);  // before touching the device
@@ -1360,7 +1368,7 @@ int df_create_ground(df_ctx** out, int n_levels, const int n0[3], const int n[3]
   if (!c) return fail(DF_ENOMEM, "host allocation");
   c->device = device;
   c->user = (cudaStream_t)stream;
-  rc = run_create(&c->run, n_levels, n0, n, lo, hi, G, precision);
+  rc = run_create(&c->run, n_levels, n0, n, lo, hi, G, precision, al);
   if (rc) {
     delete c;
     return rc;
@@ -1378,6 +1386,32 @@ int df_create_ground(df_ctx** out, int n_levels, const int n0[3], const int n[3]
   return DF_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int df_create_ground(df_ctx** out, int n_levels, const int n0[3], const int n[3],
+                     const double lo[3], const double hi[3], int G, int precision, int device,
+                     void* stream) {
+  return create_ctx(out, n_levels, n0, n, lo, hi, G, precision, device, stream, g_allocator);
+}
+
+int df_create_levels(df_ctx** out, int n_levels, int N, const double coarse_lo[3],
+                     const double coarse_hi[3], int precision, int device, void* stream,
+                     df_alloc_fn alloc, df_free_fn dealloc, void* user) {
+  if ((alloc == nullptr) != (dealloc == nullptr))
+    return fail(DF_EINVAL, "alloc and dealloc are given together");
+  Allocator al = g_allocator;
+  if (alloc) {
+    al.alloc = alloc;
+    al.dealloc = dealloc;
+    al.user = user;
+  }
+  const int n[3] = {N, N, N};
+  return create_ctx(out, n_levels, n, n, coarse_lo, coarse_hi, DF_DEFAULT_GHOST, precision,
+                    device, stream, al);
+}
+
 int df_set_params(df_ctx* c, const df_params* p) {
   if (check_ctx(c, false)) return DF_EINVAL;
   if (check_params(p)) return DF_EINVAL;
@@ -1393,10 +1427,10 @@ int df_set_params(df_ctx* c, const df_params* p) {
   return rc;
 }
 
-int df_step(df_ctx* c, int n) {
+int df_step(df_ctx* c, int n, double* t_out) {
   if (check_ctx(c)) return DF_EINVAL;
   if (n < 0) return fail(DF_EINVAL, "negative step count");
-  if (n == 0) return DF_OK;
+  if (n == 0) return t_out ? df_status(c, t_out, nullptr, nullptr) : DF_OK;
   Run* r = c->run;
   if (r->P.dt_fixed <= 0.0 && r->P.hydro_on == 0 && !(r->P.chi > 0.0))
     return fail(DF_EINVAL, "no time-step limit: set dt_fixed, hydro_on or chi");
@@ -1412,6 +1446,13 @@ int df_step(df_ctx* c, int n) {
   if (!rc) rc = step_plan(c->plan, c->x, r->prec, n);
   leave(c);
   r->stepped = true;
+  if (!rc && t_out) {
+    const int health = sync_health(c->x.st, r);
+    DevScalars h;
+    CK(cudaMemcpy(&h, r->ds, sizeof h, cudaMemcpyDeviceToHost));
+    *t_out = h.t;
+    rc = health;
+  }
   return rc;
 }
 
@@ -1702,6 +1743,36 @@ int df_check_division(const double* a_host, const double* b_host, int n, double*
   return DF_OK;
 }
 
+int df_measure_fp64_peak(int device, int repeats, double* tflops, double* ms_best) {
+  if (!tflops || repeats < 1) return fail(DF_EINVAL, "bad FP64 probe arguments");
+  CK(cudaSetDevice(device));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  double* sink = nullptr;
+  CK(cudaMalloc(&sink, sizeof(double)));
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  const int blocks = 8 * sms, iters = 4096;  // 8 blocks of 256 threads fill an SM
+  long long flops = launch_dfma_probe(blocks, iters, sink, nullptr);  // warm-up
+  float best = 1e30f;
+  for (int r = 0; r < repeats; ++r) {
+    CK(cudaEventRecord(a, nullptr));
+    launch_dfma_probe(blocks, iters, sink, nullptr);
+    CK(cudaEventRecord(b, nullptr));
+    CK(cudaEventSynchronize(b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, a, b));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  *tflops = (double)flops / (best * 1e-3) / 1e12;
+  if (ms_best) *ms_best = best;
+  return DF_OK;
+}
+
 int df_destroy(df_ctx* c) {
   if (!c) return DF_OK;
   DevGuard g(c->device);
@@ -1781,7 +1852,7 @@ int df_pool_admit_ground(df_pool* p, int n_levels, const int n0[3], const int n[
     return fail(DF_EBUSY, "HBM budget: %zu used + %zu needed > %zu", p->used, need, p->budget);
   DevGuard g(p->device);
   Run* r = nullptr;
-  rc = run_create(&r, n_levels, n0, n, lo, hi, G, p->prec);
+  rc = run_create(&r, n_levels, n0, n, lo, hi, G, p->prec, g_allocator);
   if (rc) return rc;
   enter(p);
   rc = DF_OK;
@@ -1864,6 +1935,40 @@ int df_pool_query(df_pool* p, double* out, int max_slots) {
     o[5] = h[i].unhealthy;
   }
   return ns;
+}
+
+int df_pool_force(df_pool* p, int slot, double F_out[3], double* t_out) {
+  if (!p || slot < 0 || slot >= (int)p->slots.size() || !p->slots[slot] || !F_out)
+    return fail(DF_EINVAL, "no run in slot %d, or a null output", slot);
+  DevGuard g(p->device);
+  CK(cudaStreamSynchronize(p->x.st));
+  DevScalars h;
+  CK(cudaMemcpy(&h, p->slots[slot]->ds, sizeof h, cudaMemcpyDeviceToHost));
+  for (int d = 0; d < 3; ++d) F_out[d] = h.F[d];
+  if (t_out) *t_out = h.t;
+  return h.unhealthy ? fail(DF_EUNHEALTHY, "slot %d: NaN, rho <= 0 or e <= 0", slot) : DF_OK;
+}
+
+int df_pool_history(df_pool* p, int slot, int k, double* out, int* got) {
+  if (!p || slot < 0 || slot >= (int)p->slots.size() || !p->slots[slot] || !out || !got ||
+      k < 0)
+    return fail(DF_EINVAL, "no run in slot %d, or a bad output", slot);
+  Run* r = p->slots[slot];
+  DevGuard g(p->device);
+  CK(cudaStreamSynchronize(p->x.st));
+  long long pos = 0;
+  CK(cudaMemcpy(&pos, r->ring_pos, sizeof pos, cudaMemcpyDeviceToHost));
+  const long long m = std::min<long long>(std::min<long long>(k, pos), r->ring_cap);
+  long long done = 0;
+  while (done < m) {  // at most two contiguous pieces of the ring
+    const long long e = pos - m + done, at = e % r->ring_cap;
+    const long long len = std::min(m - done, r->ring_cap - at);
+    CK(cudaMemcpy(out + kRingStride * done, r->ring + kRingStride * at,
+                  kRingStride * len * sizeof(double), cudaMemcpyDeviceToHost));
+    done += len;
+  }
+  *got = (int)m;
+  return DF_OK;
 }
 
 int df_pool_get_field(df_pool* p, int slot, int level, int field, double* out) {

@@ -124,6 +124,9 @@ struct Phys {
 };
 
 // Device scalars of a context.
+// doubles per entry of a run's force history: F_x, F_y, F_z, t at the end of the step
+constexpr int kRingStride = 4;
+
 struct DevScalars {
   double dt;                  // current coarse step
   double t;                   // simulated time
@@ -352,6 +355,8 @@ enum KernelKind {
 
 // hot-path FP64 division versus IEEE division (device arrays; max_ulp zeroed by caller)
 int launch_hdiv_check(const double* a, const double* b, int n, double* max_ulp, cudaStream_t st);
+// launches the FP64 throughput probe; returns the flops it executes
+long long launch_dfma_probe(int blocks, int iters, double* sink, cudaStream_t st);
 
 // set the calling thread's last-error message (df_last_error) and return `code`
 int set_error(int code, const char* fmt, ...);

@@ -1001,8 +1001,14 @@ __device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_l
     case 0:  // periodic
       src = side == 0 ? dst + n : dst - n;
       break;
-    case 1:  // outflow
-      src = side == 0 ? G : G + n - 1;
+    case 1:  // outflow: the nearest active element; for v_d the boundary face itself
+             // (G or G + n), which the solver owns on both sides
+      if (normal && side == 1) {
+        if (g == 1) return;
+        src = G + n;
+      } else {
+        src = side == 0 ? G : G + n - 1;
+      }
       break;
     case 2:  // inflow: the background itself, zero deviation
       use_fixed = true;
@@ -1042,9 +1048,11 @@ __device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_l
     int cs = (c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0];
     q[cd] = sign * q[cs] + shift;
   }
-  if (type == 3 && side == 0 && normal && g == 1) {
+  // the lower boundary face G of v_d: 0 at a wall, V (zero deviation) on an injection
+  // face; the upper boundary face G + n is the g = 1 element of the upper side
+  if ((type == 3 || type == 2) && side == 0 && normal && g == 1) {
     c3[d] = G;
-    q[(c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0]] = -Vd;
+    q[(c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0]] = type == 3 ? -Vd : T(0);
   }
 }
 
@@ -1503,11 +1511,15 @@ __device__ __forceinline__ void el_force_finalize(const double* __restrict__ par
     if (lane == 0) {
       double F = s + cmp;
       ds->F[comp] = F;
-      if (ring) ring[3 * (*ring_pos % ring_cap) + comp] = F;
+      if (ring) ring[kRingStride * (*ring_pos % ring_cap) + comp] = F;
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && ring) *ring_pos += 1;
+  if (threadIdx.x == 0 && ring) {
+    // the time at the end of this coarse step (the time update follows this op)
+    ring[kRingStride * (*ring_pos % ring_cap) + 3] = ds->t + ds->dt;
+    *ring_pos += 1;
+  }
 }
 
 // ----------------------------------------------------------- initialisation
@@ -1652,7 +1664,31 @@ __global__ void k_hdiv_check(const double* a, const double* b, int n, double* ma
     atomicMax((unsigned long long*)max_ulp, (unsigned long long)__double_as_longlong(u));
 }
 
+// FP64 throughput probe: every thread runs kProbeChains independent chains of
+// dependent fused multiply-adds (2 flops each); with a full SM of threads the FP64
+// pipe, not the chain latency, sets the rate.  The result is written only when it
+// takes an impossible value, so the work cannot be dropped and nothing is stored.
+constexpr int kProbeChains = 8;
+__global__ void __launch_bounds__(kBlock) k_dfma_probe(int iters, double* sink) {
+  double a[kProbeChains];
+#pragma unroll
+  for (int i = 0; i < kProbeChains; ++i) a[i] = 1.0 + 1e-3 * (threadIdx.x + i);
+  const double b = 0.999999999, c = 1e-9;
+  for (int k = 0; k < iters; ++k)
+#pragma unroll
+    for (int i = 0; i < kProbeChains; ++i) a[i] = fma(a[i], b, c);
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < kProbeChains; ++i) s += a[i];
+  if (s == -1.0) sink[0] = s;
+}
+
 }  // namespace
+
+long long launch_dfma_probe(int blocks, int iters, double* sink, cudaStream_t st) {
+  k_dfma_probe<<<blocks, kBlock, 0, st>>>(iters, sink);
+  return 2LL * kProbeChains * iters * (long long)kBlock * blocks;
+}
 
 int launch_hdiv_check(const double* a, const double* b, int n, double* max_ulp, cudaStream_t st) {
   k_hdiv_check<<<(n + 255) / 256, 256, 0, st>>>(a, b, n, max_ulp);

@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(kNaBlock)
     k_force_level_na(const double* __restrict__ rho, int n0, int n1, int n2, int G, int s0,
                      int s1, double lo0, double lo1, double lo2, double dx0, double dx1,
                      double dx2, int has_child, int co0, int co1, int co2, int ch0, int ch1,
-                     int ch2, double GM, double eps, double rho0, double* partials) {
+                     int ch2, double GM, double eps, double rho0, int mirror, double mult,
+                     double* partials) {
   __shared__ double sx[kNaBlock], sy[kNaBlock], sz[kNaBlock];
   long long t = blockIdx.x * (long long)kNaBlock + threadIdx.x;
   long long na = (long long)n0 * n1 * n2;
@@ -48,9 +49,11 @@ __global__ void __launch_bounds__(kNaBlock)
       double r2 = x * x + y * y + z * z + eps * eps;
       double inv3 = 1.0 / (r2 * sqrt(r2));
       double m = (rho[c] - rho0) * (dx0 * dx1 * dx2);
-      fx = GM * m * x * inv3;
-      fy = GM * m * y * inv3;
-      fz = GM * m * z * inv3;
+      // the unfolded domain across mirror planes: no component along a mirror axis,
+      // mult copies of the simulated part for the others
+      fx = mirror & 1 ? 0.0 : mult * (GM * m * x * inv3);
+      fy = mirror & 2 ? 0.0 : mult * (GM * m * y * inv3);
+      fz = mirror & 4 ? 0.0 : mult * (GM * m * z * inv3);
     }
   }
   sx[threadIdx.x] = fx;
@@ -101,7 +104,8 @@ __global__ void k_force_sum_na(const double* __restrict__ partials, int n, doubl
 extern "C" int df_force_level_noalloc(const double* rho, const int n[3], int G,
                                       const double lo[3], const double dx[3],
                                       const int child_off[3], const int child_n[3], double GM,
-                                      double eps, double rho0, double* F_out, void* stream) {
+                                      double eps, double rho0, int mirror, double* F_out,
+                                      void* stream) {
   if (!rho || !n || !lo || !dx || !F_out)
     return dfn::set_error(DF_EINVAL, "df_force_level_noalloc: null argument");
   if (G < 0 || n[0] < 1 || n[1] < 1 || n[2] < 1 || !(dx[0] > 0) || !(dx[1] > 0) ||
@@ -115,6 +119,19 @@ extern "C" int df_force_level_noalloc(const double* rho, const int n[3], int G,
                           cells, DF_NOALLOC_MAX_CELLS);
   if ((child_off == nullptr) != (child_n == nullptr))
     return dfn::set_error(DF_EINVAL, "df_force_level_noalloc: give both child_off and child_n");
+  if (child_off)
+    for (int d = 0; d < 3; ++d)
+      if (child_off[d] < 0 || child_n[d] < 1 || child_off[d] > n[d] - child_n[d])
+        return dfn::set_error(DF_EINVAL,
+                              "df_force_level_noalloc: covered box [%d, %d) outside the %d "
+                              "active cells of axis %d",
+                              child_off[d], child_off[d] + child_n[d], n[d], d);
+  if (mirror < 0 || mirror > 7)
+    return dfn::set_error(DF_EINVAL, "df_force_level_noalloc: mirror mask %d not in 0..7",
+                          mirror);
+  double mult = 1.0;
+  for (int d = 0; d < 3; ++d)
+    if (mirror >> d & 1) mult *= 2.0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64)
@@ -139,7 +156,7 @@ extern "C" int df_force_level_noalloc(const double* rho, const int n[3], int G,
   k_force_level_na<<<blocks, kNaBlock, 0, st>>>(
       rho, n[0], n[1], n[2], G, s0, s1, lo[0], lo[1], lo[2], dx[0], dx[1], dx[2], hc,
       hc ? child_off[0] : 0, hc ? child_off[1] : 0, hc ? child_off[2] : 0, hc ? child_n[0] : 0,
-      hc ? child_n[1] : 0, hc ? child_n[2] : 0, GM, eps, rho0, partials);
+      hc ? child_n[1] : 0, hc ? child_n[2] : 0, GM, eps, rho0, mirror, mult, partials);
   k_force_sum_na<<<1, 96, 0, st>>>(partials, blocks, F_out);
   e = cudaGetLastError();
   if (e != cudaSuccess)

@@ -186,16 +186,17 @@ def run(levels=(4, 5, 6, 7), mach=3.0, chi=0.1, GM=1e-3, L=2e-4, gamma=1.4, n=32
 
 
 def cold_thermal(mach=0.1, n_levels=6, chi=0.1, GM=1e-3, gamma=1.4, n=32, t_end_taus=100.0,
-                 precision=binding.DF_FP32_STATE, sample_every=8):
+                 precision=binding.DF_FP32_STATE, sample_every=8, quadrant=False):
     """Cold thermal force (Sec. 4.2): a cold perturber with thermal diffusion minus the
     same in an adiabatic gas, at low Mach, against -(gamma - 1)/2 F0 (Eq. 48, Eq. 50,
     Eq. 51) times the Eq. 23 share of the box (the perturbation is that of a heat sink
-    of luminosity -L_c, Eq. 49)."""
-    _, cold, half = setup(mach, chi, GM, 0.0, gamma, n)
+    of luminosity -L_c, Eq. 49).  quadrant=True: the paper's quadrant meshes and
+    boundaries (Sec. 3.4), as in `setup`."""
+    _, cold, half = setup(mach, chi, GM, 0.0, gamma, n, quadrant=quadrant)
     adiabatic = dict(cold, chi=0.0)
     out = pairs((n_levels,), cold, adiabatic, half, n=n,
                 t_end=t_end_taus * tau(chi, gamma, mach), precision=precision,
-                sample_every=sample_every)
+                sample_every=sample_every, quadrant=quadrant)
     lam_ = lam(chi, gamma, mach)
     r = out["runs"][n_levels]
     share = h_fraction(half / (2.0 * lam_)) - h_fraction(r["finest_dx"] / (2.0 * lam_))

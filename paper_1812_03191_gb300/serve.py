@@ -5,17 +5,29 @@ server admits them first-come first-served while their device memory fits the
 HBM budget, keeps every admitted hierarchy resident on the GPU, advances all of
 them together (one pool step = one coarse step of every active run), and retires
 a run when its force has converged: |F(t) - F(t - t_cross)| <= tol |F(t)| for the
-force along the perturber's motion, checked every coarse step once t >= 2 t_cross,
+force along the perturber's motion, checked at every coarse step once t >= 2 t_cross,
 where t_cross = 2 l_f / (c_s + V) is the crossing time of the finest level (l_f its
 half-width); or when the step cap is reached.  Freed slots take the next queued
 requests at once, so work that arrives while others run overlaps with them.
 
+The host does not wait on every coarse step: it issues a batch of steps, then reads
+each run's force history (the device keeps F and t of every step) and applies the
+rule step by step.  A batch ends early enough that no run can pass its earliest
+possible convergence step by more than `check_every` steps, and that a request
+arriving while there is room is admitted within about one batch.
+
+Failures stay with their request: a run whose state goes bad (NaN, rho <= 0 or
+e <= 0, found by the device's time-step reduction) is retired with an error result
+and its slot freed, and a request that cannot fit even an empty pool is rejected
+with an error result; the other requests are unaffected.
+
 ``solve_sequential`` is the baseline: the same requests, one at a time, each in its
-own FP64 context, with the same stopping rule.
+own context (FP64 or FP32 state), with the same stopping rule.
 """
 from __future__ import annotations
 
 import bisect
+import math
 import time
 from dataclasses import dataclass, field
 
@@ -44,6 +56,7 @@ class Track:
     t_cross: float
     ts: list = field(default_factory=list)
     Fs: list = field(default_factory=list)
+    F3: list = field(default_factory=list)
     steps: int = 0
 
     def converged(self, tol) -> bool:
@@ -66,6 +79,8 @@ class Result:
     F: np.ndarray
     F_along: float
     capped: bool
+    error: str | None = None
+    history: list | None = None  # F along the motion after each coarse step
 
     @property
     def latency(self) -> float:
@@ -73,32 +88,62 @@ class Result:
 
 
 def summarize(results, t_begin, t_end):
-    lat = np.array([r.latency for r in results])
+    ok = [r for r in results if r.error is None]
+    lat = np.array([r.latency for r in ok])
     return {
         "requests": len(results),
-        "throughput_req_per_s": len(results) / max(t_end - t_begin, 1e-12),
+        "failed": len(results) - len(ok),
+        "throughput_req_per_s": len(ok) / max(t_end - t_begin, 1e-12),
         "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
         "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
-        "capped_fraction": float(np.mean([r.capped for r in results])) if results else None,
+        "capped_fraction": float(np.mean([r.capped for r in ok])) if ok else None,
         "makespan_s": t_end - t_begin,
     }
 
 
 class Server:
     def __init__(self, budget_bytes, precision=binding.DF_FP32_STATE, tol=1e-3, step_cap=4000,
-                 device=0, stream=None, tiles=None):
+                 device=0, stream=None, tiles=None, check_every=8, keep_history=False):
         self.pool = binding.Pool(budget_bytes, precision=precision, device=device, stream=stream)
+        self.budget = budget_bytes
+        self.precision = precision
         self.tol = tol
         self.step_cap = step_cap
         self.tiles = tiles
+        self.check_every = max(1, int(check_every))
+        self.keep_history = keep_history
         self.max_active = 0
+        self.batches = 0
+        self.step_s = None  # running estimate of the wall time of one pool step
 
     def close(self):
         self.pool.close()
 
-    def run(self, requests, clock=time.perf_counter, sleep=time.sleep):
+    def _batch(self, active, queue_waiting, next_arrival_in):
+        """coarse steps to issue before the next look at the runs"""
+        k = 4000  # the device keeps 4096 steps of history per run
+        for tr in active.values():
+            k = min(k, self.step_cap - tr.steps)
+            if tr.ts and tr.ts[-1] < 2 * tr.t_cross and len(tr.ts) >= 2:
+                dt = tr.ts[-1] - tr.ts[-2]
+                k = min(k, max(self.check_every,
+                               math.ceil((2 * tr.t_cross - tr.ts[-1]) / max(dt, 1e-300))))
+            else:
+                k = min(k, self.check_every)
+        if queue_waiting or next_arrival_in is not None:
+            # come back for requests waiting for room, or about to arrive
+            horizon = 0.0 if queue_waiting else next_arrival_in
+            if self.step_s:
+                k = min(k, max(1, int(horizon / self.step_s) + 1))
+            else:
+                k = 1
+        return max(1, k)
+
+    def run(self, requests, clock=time.perf_counter, sleep=time.sleep, on_admit=None):
         """requests: list of (arrival time in s from the start, spec).  Returns the
-        per-request results (in completion order) and the summary."""
+        per-request results (in completion order) and the summary.  on_admit(pool,
+        slot, rid), if given, is called after each admission (tests use it to plant a
+        fault in one run's state)."""
         order = sorted(range(len(requests)), key=lambda i: requests[i][0])
         pending = [(requests[i][0], i, requests[i][1]) for i in order]
         queue, active, done = [], {}, []
@@ -114,39 +159,73 @@ class Server:
             # admit FIFO while the budget allows
             while queue:
                 arr, rid, spec = queue[0]
-                slot = self.pool.admit(spec["n_levels"], spec["n"], spec["lo"], spec["hi"],
-                                       spec["G"], spec["params"])
+                try:
+                    slot = self.pool.admit(spec["n_levels"], spec["n"], spec["lo"], spec["hi"],
+                                           spec["G"], spec["params"])
+                except binding.DfError as exc:  # a malformed request fails alone
+                    queue.pop(0)
+                    done.append(self._failed(rid, arr, clock() - t0, str(exc)))
+                    continue
                 if slot is None:
-                    if not active:
-                        raise RuntimeError(f"request {rid} does not fit the empty pool")
+                    need = binding.run_bytes(spec["n_levels"], spec["n"], spec["G"],
+                                             self.precision)
+                    if need > self.budget:  # it would never fit: reject it alone
+                        queue.pop(0)
+                        done.append(self._failed(
+                            rid, arr, clock() - t0,
+                            f"needs {need} bytes, more than the {self.budget}-byte budget"))
+                        continue
                     break
                 queue.pop(0)
                 active[slot] = Track(rid, spec, arr, clock() - t0, crossing_time(spec))
+                if on_admit is not None:
+                    on_admit(self.pool, slot, rid)
             self.max_active = max(self.max_active, len(active))
             if not active:
                 if nxt < len(pending):
                     sleep(max(0.0, pending[nxt][0] - (clock() - t0)))
                 continue
-            self.pool.step(1)
-            q = self.pool.query()
+            nai = pending[nxt][0] - (clock() - t0) if nxt < len(pending) else None
+            k = self._batch(active, bool(queue), nai)
+            tb = clock()
+            self.pool.step(k)
+            q = self.pool.query()  # waits for the batch; health and time of every slot
+            self.batches += 1
+            per = (clock() - tb) / k
+            self.step_s = per if self.step_s is None else 0.7 * self.step_s + 0.3 * per
             finished = []
             for slot, tr in active.items():
                 row = q[slot]
-                tr.steps += 1
-                tr.ts.append(float(row[3]))
-                tr.Fs.append(along_motion(row[:3], tr.spec))
                 if row[5] != 0:
-                    raise RuntimeError(f"request {tr.rid}: unhealthy state")
-                capped = tr.steps >= self.step_cap
-                if tr.converged(self.tol) or capped:
-                    finished.append((slot, tr, row, capped))
-            for slot, tr, row, capped in finished:
-                done.append(Result(tr.rid, tr.arrival, clock() - t0, tr.steps, float(row[3]),
-                                   np.array(row[:3]), tr.Fs[-1], capped))
+                    finished.append((slot, tr, None, "unhealthy state: NaN, rho <= 0 or e <= 0"))
+                    continue
+                hist = self.pool.history(slot, k)
+                for F3 in hist:
+                    tr.steps += 1
+                    tr.ts.append(float(F3[3]))
+                    tr.F3.append(F3[:3].copy())
+                    tr.Fs.append(along_motion(F3[:3], tr.spec))
+                    if tr.converged(self.tol) or tr.steps >= self.step_cap:
+                        finished.append((slot, tr, tr.steps >= self.step_cap
+                                         and not tr.converged(self.tol), None))
+                        break
+            fin_t = clock() - t0
+            for slot, tr, capped, err in finished:
+                if err is not None:
+                    done.append(self._failed(tr.rid, tr.arrival, fin_t, err))
+                else:
+                    done.append(Result(tr.rid, tr.arrival, fin_t, tr.steps, tr.ts[-1],
+                                       np.array(tr.F3[-1]), tr.Fs[-1], bool(capped),
+                                       history=list(tr.Fs) if self.keep_history else None))
                 self.pool.release(slot)
                 del active[slot]
         t_end = clock() - t0
         return done, summarize(done, 0.0, t_end)
+
+    @staticmethod
+    def _failed(rid, arrival, finish, msg):
+        return Result(rid, arrival, finish, 0, float("nan"), np.full(3, np.nan), float("nan"),
+                      False, error=msg)
 
 
 def solve_one(spec, precision, tol, step_cap, device=0, stream=None):
@@ -156,9 +235,8 @@ def solve_one(spec, precision, tol, step_cap, device=0, stream=None):
     tr = Track(-1, spec, 0.0, 0.0, crossing_time(spec))
     capped = False
     while True:
-        sim.step(1)
+        t = sim.step(1, want_t=True)
         F, _ = sim.force()
-        t, _, _ = sim.status()
         tr.steps += 1
         tr.ts.append(t)
         tr.Fs.append(along_motion(F, spec))
@@ -172,7 +250,7 @@ def solve_one(spec, precision, tol, step_cap, device=0, stream=None):
 
 
 def solve_sequential(requests, precision=binding.DF_FP64, tol=1e-3, step_cap=4000,
-                     clock=time.perf_counter, sleep=time.sleep):
+                     clock=time.perf_counter, sleep=time.sleep, keep_history=False):
     """Single-server FIFO baseline: each request solved alone when it arrives and the
     previous one is done."""
     order = sorted(range(len(requests)), key=lambda i: requests[i][0])
@@ -184,6 +262,7 @@ def solve_sequential(requests, precision=binding.DF_FP64, tol=1e-3, step_cap=400
         if wait > 0:
             sleep(wait)
         tr, F, capped = solve_one(spec, precision, tol, step_cap)
-        done.append(Result(i, arr, clock() - t0, tr.steps, tr.ts[-1], F, tr.Fs[-1], capped))
+        done.append(Result(i, arr, clock() - t0, tr.steps, tr.ts[-1], F, tr.Fs[-1], capped,
+                           history=list(tr.Fs) if keep_history else None))
     t_end = clock() - t0
     return done, summarize(done, 0.0, t_end)

@@ -20,7 +20,7 @@ def lib():
 
 def test_header_and_binding_agree():
     hdr = open(os.path.join(ROOT, "include", "dfnest.h")).read()
-    declared = set(re.findall(r"\b(df_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(df_[a-z0-9_]+)\s*\(", hdr))
     assert declared == set(binding.EXPORTS)
 
 
@@ -42,7 +42,35 @@ def test_invalid_geometry_rejected_without_gpu(lib):
     assert lib.df_create(C.byref(h), 1, n2, lo, hi, 8, 7, 0, None) == binding.DF_EINVAL
     big = (C.c_int * 3)(1024, 1024, 1024)
     assert lib.df_create(C.byref(h), 1, big, lo, hi, 8, 0, 0, None) == binding.DF_EINVAL
-    assert lib.df_step(None, 1) == binding.DF_EINVAL
+    assert lib.df_step(None, 1, None) == binding.DF_EINVAL
+    t = C.c_double()
+    assert lib.df_step(None, 1, C.byref(t)) == binding.DF_EINVAL
+
+
+def test_problem_statement_calls_validate_without_gpu(lib):
+    """df_create_levels / df_step / df_pool_force (the hot path's contract calls)
+    reject bad input on the host, before any device work."""
+    h = C.c_void_p()
+    lo = (C.c_double * 3)(-8, -8, -8)
+    hi = (C.c_double * 3)(8, 8, 8)
+    alloc = binding._ALLOC_FN(lambda nbytes, user: None)
+    # one callback without the other
+    assert lib.df_create_levels(C.byref(h), 3, 64, lo, hi, 0, 0, None,
+                                C.cast(alloc, C.c_void_p), None, None) == binding.DF_EINVAL
+    assert b"together" in lib.df_last_error()
+    # N not a multiple of 4; no levels; too many levels; unknown precision
+    assert lib.df_create_levels(C.byref(h), 3, 30, lo, hi, 0, 0, None, None, None,
+                                None) == binding.DF_EINVAL
+    assert lib.df_create_levels(C.byref(h), 0, 64, lo, hi, 0, 0, None, None, None,
+                                None) == binding.DF_EINVAL
+    assert lib.df_create_levels(C.byref(h), 17, 64, lo, hi, 0, 0, None, None, None,
+                                None) == binding.DF_EINVAL
+    assert lib.df_create_levels(C.byref(h), 3, 64, lo, hi, 5, 0, None, None, None,
+                                None) == binding.DF_EINVAL
+    assert not h.value
+    F = (C.c_double * 3)()
+    t = C.c_double()
+    assert lib.df_pool_force(None, 0, F, C.byref(t)) == binding.DF_EINVAL
 
 
 def test_xi_search_matches_appendix_example(lib):

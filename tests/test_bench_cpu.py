@@ -24,8 +24,16 @@ def _run(args, env=None):
     return [json.loads(l) for l in out.stdout.splitlines() if l.startswith("{")]
 
 
+def test_default_workload_is_the_precision_configuration():
+    """the default bench line is the largest single-GPU configuration: 5 x 128^3"""
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert 'ap.add_argument("--workload", default="precision"' in src
+    assert bench.workload("precision")["name"] == "precision_5x128^3"
+
+
 def test_reference_arm_line():
-    (line,) = _run(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    (line,) = _run(["--impl", "reference", "--workload", "nested", "--steps", "1",
+                    "--warmup", "3"])
     assert line["impl"] == "reference"
     assert line["metric"] == "cell-updates/s" and line["unit"] == "cell-updates/s"
     assert line["value"] > 0 and line["higher_is_better"] is True
@@ -41,8 +49,8 @@ def test_reference_arm_line():
 
 
 def test_reference_arm_runs_on_rank_zero_only():
-    assert _run(["--impl", "reference", "--steps", "1", "--warmup", "3"],
-                env={"RANK": "1", "WORLD_SIZE": "2"}) == []
+    assert _run(["--impl", "reference", "--workload", "nested", "--steps", "1", "--warmup",
+                 "3"], env={"RANK": "1", "WORLD_SIZE": "2"}) == []
 
 
 def test_cell_updates_per_coarse_step():
@@ -53,14 +61,15 @@ def test_cell_updates_per_coarse_step():
 
 
 def test_level_step_boxes():
-    """one box per level step: level 0 once with margin 4; level l >= 1 2^(l-1) times
+    """one box per level step: level 0 once with margin 4 (5 above); level l >= 1 2^(l-1) times
     per sub-cycle pair, margins 8 then 4, capped at the padded array"""
     cfg = I.nested()
     n, G = cfg["n"], cfg["G"]
     boxes = bench.level_step_boxes(cfg)
     assert len(boxes) == 2 ** cfg["n_levels"] - 1
-    assert boxes[0] == (n + 8) ** 3
-    assert sorted(set(boxes)) == sorted({(n + 8) ** 3, min(n + 16, n + 2 * G) ** 3})
+    assert boxes[0] == (n + 9) ** 3  # level 0: one more element on the upper side
+    assert sorted(set(boxes)) == sorted({(n + 9) ** 3, (n + 8) ** 3,
+                                         min(n + 16, n + 2 * G) ** 3})
 
 
 def test_kernel_hbm_table():

@@ -8,7 +8,7 @@ import pytest
 from oracle import Oracle
 from paper_1812_03191_gb300 import binding
 from paper_1812_03191_gb300 import inputs as I
-from test_gpu_parity import TRANSPORTS, TRANSPORT_IDS, field_errors
+from test_gpu_parity import TRANSPORTS, TRANSPORT_IDS, field_errors, force_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -52,10 +52,15 @@ def _perturb(runs, seed, amp=1e-2):
 def _assert_parity(sim, orc, p, steps):
     sim.step(steps)
     orc.step(steps)
-    worst = max(field_errors(sim, orc, p), key=lambda e: e[2])
+    errs = field_errors(sim, orc, p)
+    worst = max(errs, key=lambda e: e[2])
     assert worst[2] <= TOL, worst
     F, Fo = sim.force()[0], orc.force()
-    assert np.abs(F - Fo).max() <= 1e-9 * np.abs(Fo).max(), (F, Fo)
+    bound = force_bound(sim, orc, p, max(e for l, f, e in errs if f == 0))
+    dF = np.abs(F - Fo).max()
+    print(f"ground: fields {worst[2]:.2e}; force {dF:.2e} abs, "
+          f"{dF / np.abs(Fo).max():.2e} rel, bound {bound:.2e}")
+    assert dF <= bound, (F, Fo, bound)
     assert sim.status()[2] == 0
 
 

@@ -69,6 +69,55 @@ def test_pool_mix_equals_runs_alone(precision):
     assert mix.info()["launches"] < sum(a.info()["launches"] for a in alone)
 
 
+class _View:
+    def __init__(self, nl, n, half):
+        self.n_levels, self.n, self.n0 = nl, (n,) * 3, (n,) * 3
+        self.lo, self.hi = (-half,) * 3, (half,) * 3
+
+
+def test_pool_runs_match_their_own_oracles():
+    """Uneven FP64 runs stepped together by the batched work-list kernels: each run
+    against its own oracle (fields to 1e-10, the force within the bound the density
+    difference implies, the same time); then the same runs in FP32 state against
+    the FP64 oracle, whose error is printed and bounded by the precision form's
+    targets (force 1e-3 relative)."""
+    from oracle import Oracle
+    from test_gpu_parity import force_bound
+    for precision in (binding.DF_FP64, binding.DF_FP32_STATE):
+        pool = binding.Pool(1 << 36, precision=precision)
+        slots, orcs = [], []
+        for nl, n, half, over in RUNS:
+            p = I.base_params(**over)
+            slots.append(pool.admit(nl, n, (-half,) * 3, (half,) * 3, I.DEFAULT_G, p))
+            orcs.append(Oracle(nl, n, (-half,) * 3, (half,) * 3, I.DEFAULT_G, p))
+        pool.step(8)
+        for k, ((nl, n, half, over), slot, orc) in enumerate(zip(RUNS, slots, orcs)):
+            orc.step(8)
+            p = I.base_params(**over)
+            vs = max(p["mach"] * p["cs"], 1e-3)
+            worst = rho_err = 0.0
+            for l in range(nl):
+                for f in range(5):
+                    e = np.abs(pool.get_field(slot, l, f) - orc.get_field(l, f)).max()
+                    e /= 1.0 if f < 2 else vs
+                    worst = max(worst, e)
+                    rho_err = max(rho_err, e) if f == 0 else rho_err
+            F, t = pool.force(slot)
+            Fo = orc.force()
+            dF = np.abs(F - Fo).max()
+            print(f"precision {precision} run {k}: fields {worst:.2e}, force {dF:.2e} abs, "
+                  f"{dF / np.abs(Fo).max():.2e} rel")
+            if precision == binding.DF_FP64:
+                assert worst <= 1e-10, (k, worst)
+                assert dF <= force_bound(_View(nl, n, half), orc, p, rho_err), (k, F, Fo)
+                assert abs(t - orc.t) <= 1e-13 * orc.t
+            else:
+                assert worst <= 1e-4, (k, worst)
+                assert dF <= 1e-3 * np.abs(Fo).max(), (k, F, Fo)
+            orc.close()
+        pool.close()
+
+
 def test_pool_budget_admission_and_release():
     shape = (2, 24)
     need = binding.run_bytes(shape[0], shape[1], I.DEFAULT_G)

@@ -40,6 +40,87 @@ def test_convergence_rule():
     assert not tr3.converged(1e-3)  # before 2 t_cross
 
 
+def test_batch_sizes_follow_the_stopping_rule():
+    """The host reads the runs after a batch of coarse steps: long before 2 t_cross a
+    batch covers the steps to it, near or past it `check_every` steps, never past the
+    step cap, and a single step while requests wait for room."""
+    srv = S.Server.__new__(S.Server)
+    srv.step_cap, srv.check_every, srv.step_s = 100, 8, 1e-3
+    early = S.Track(0, _spec(), 0.0, 0.0, t_cross=1.0)
+    early.ts, early.steps = [0.0, 0.01], 2  # dt = 0.01: 198 steps to t = 2
+    assert srv._batch({0: early}, False, None) == 98  # the step cap binds
+    srv.step_cap = 1000
+    assert srv._batch({0: early}, False, None) == 199
+    late = S.Track(1, _spec(), 0.0, 0.0, t_cross=1.0)
+    late.ts, late.steps = [2.5, 2.51], 300
+    assert srv._batch({0: early, 1: late}, False, None) == 8
+    assert srv._batch({0: early}, True, None) == 1  # a request waits for room
+    # the next arrival in 50 ms at 1 ms per step
+    assert srv._batch({0: early}, False, 0.05) == 51
+    fresh = S.Track(2, _spec(), 0.0, 0.0, t_cross=1.0)  # no step yet: dt unknown
+    assert srv._batch({2: fresh}, False, None) == 8
+
+
+def test_oversize_request_rejected_alone():
+    """A request that cannot fit even an empty pool gets an error result; the server
+    neither raises nor stops (no GPU work: the pool object is a stand-in)."""
+
+    class FakePool:
+        def admit(self, *a, **k):
+            return None
+
+    srv = S.Server.__new__(S.Server)
+    srv.pool, srv.budget, srv.precision = FakePool(), 1000, binding.DF_FP32_STATE
+    srv.tiles, srv.max_active = None, 0
+    orig = binding.run_bytes
+    binding.run_bytes = lambda *a, **k: 10**9
+    try:
+        results, summary = srv.run([(0.0, _spec())], sleep=lambda s: None)
+    finally:
+        binding.run_bytes = orig
+    assert len(results) == 1 and results[0].error and "budget" in results[0].error
+    assert summary["failed"] == 1 and summary["requests"] == 1
+
+
+@pytest.mark.gpu
+def test_unhealthy_request_fails_alone():
+    """A NaN planted in one run's density (on the host, through the pool API) retires
+    that request with an error; every other request finishes with bitwise the result
+    it has alone."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1812_03191_gb300 import build as B
+    B.build()
+    reqs = [(0.0, _spec(n_levels=2, n=24, mach=0.3 + 0.4 * k, chi=0.5, L=0.02, lum_sigma=0.3))
+            for k in range(4)]
+    bad = 2
+
+    def plant(pool, slot, rid):
+        if rid == bad:
+            rho = pool.get_field(slot, 1, 0)
+            rho[5, 6, 7] = np.nan
+            pool.set_field(slot, 1, 0, rho)
+
+    one = binding.run_bytes(2, 24, I.DEFAULT_G, binding.DF_FP32_STATE)
+    srv = S.Server(8 * one, precision=binding.DF_FP32_STATE, tol=1e-12, step_cap=7)
+    results, summary = srv.run(reqs, on_admit=plant)
+    srv.close()
+    assert summary["requests"] == 4 and summary["failed"] == 1
+    for r in results:
+        if r.rid == bad:
+            assert r.error and "unhealthy" in r.error
+            continue
+        assert r.error is None and r.steps == 7
+        sp = reqs[r.rid][1]
+        alone = binding.Pool(one * 2, precision=binding.DF_FP32_STATE)
+        alone.admit(sp["n_levels"], sp["n"], sp["lo"], sp["hi"], sp["G"], sp["params"])
+        alone.step(r.steps)
+        q = alone.query()[0]
+        alone.close()
+        assert np.array_equal(q[:3], r.F) and q[3] == r.t, r.rid
+
+
 @pytest.mark.gpu
 def test_requests_same_alone_and_in_the_mix():
     import torch
