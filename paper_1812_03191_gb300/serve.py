@@ -21,8 +21,10 @@ e <= 0, found by the device's time-step reduction) is retired with an error resu
 and its slot freed, and a request that cannot fit even an empty pool is rejected
 with an error result; the other requests are unaffected.
 
-``solve_sequential`` is the baseline: the same requests, one at a time, each in its
-own context (FP64 or FP32 state), with the same stopping rule.
+``serve_sequential`` is the baseline: the same requests, one at a time on the same
+machinery (a server with one slot), in FP64 or FP32 state, with the same stepping and
+stopping rule; ``solve_sequential`` does the same with a context per request that
+reads the force after every coarse step.
 """
 from __future__ import annotations
 
@@ -103,8 +105,12 @@ def summarize(results, t_begin, t_end):
 
 class Server:
     def __init__(self, budget_bytes, precision=binding.DF_FP32_STATE, tol=1e-3, step_cap=4000,
-                 device=0, stream=None, tiles=None, check_every=8, keep_history=False):
+                 device=0, stream=None, tiles=None, check_every=8, keep_history=False,
+                 max_slots=None):
+        """max_slots: at most this many runs at once (1: one request at a time, the
+        sequential baseline with the same stepping and stopping machinery)"""
         self.pool = binding.Pool(budget_bytes, precision=precision, device=device, stream=stream)
+        self.max_slots = max_slots
         self.budget = budget_bytes
         self.precision = precision
         self.tol = tol
@@ -130,6 +136,12 @@ class Server:
                                math.ceil((2 * tr.t_cross - tr.ts[-1]) / max(dt, 1e-300))))
             else:
                 k = min(k, self.check_every)
+        full = self.max_slots is not None and len(active) >= self.max_slots
+        if queue_waiting and full:
+            queue_waiting = False  # nothing can be admitted before a run finishes
+            next_arrival_in = None
+        elif full:
+            next_arrival_in = None
         if queue_waiting or next_arrival_in is not None:
             # come back for requests waiting for room, or about to arrive
             horizon = 0.0 if queue_waiting else next_arrival_in
@@ -156,8 +168,8 @@ class Server:
             while nxt < len(pending) and pending[nxt][0] <= now:
                 queue.append(pending[nxt])
                 nxt += 1
-            # admit FIFO while the budget allows
-            while queue:
+            # admit FIFO while the budget (and the slot limit) allows
+            while queue and (self.max_slots is None or len(active) < self.max_slots):
                 arr, rid, spec = queue[0]
                 try:
                     slot = self.pool.admit(spec["n_levels"], spec["n"], spec["lo"], spec["hi"],
@@ -249,10 +261,22 @@ def solve_one(spec, precision, tol, step_cap, device=0, stream=None):
     return tr, F, capped
 
 
+def serve_sequential(requests, budget_bytes, precision=binding.DF_FP64, tol=1e-3,
+                     step_cap=4000, keep_history=False, tiles=None):
+    """Sequential baseline on the serving machinery: one request at a time, FIFO, each
+    alone on the GPU with the same batched stepping and stopping rule."""
+    srv = Server(budget_bytes, precision=precision, tol=tol, step_cap=step_cap,
+                 keep_history=keep_history, max_slots=1, tiles=tiles)
+    try:
+        return srv.run(requests)
+    finally:
+        srv.close()
+
+
 def solve_sequential(requests, precision=binding.DF_FP64, tol=1e-3, step_cap=4000,
                      clock=time.perf_counter, sleep=time.sleep, keep_history=False):
-    """Single-server FIFO baseline: each request solved alone when it arrives and the
-    previous one is done."""
+    """Single-server FIFO baseline in contexts: each request solved alone when it
+    arrives and the previous one is done, reading the force every coarse step."""
     order = sorted(range(len(requests)), key=lambda i: requests[i][0])
     t0 = clock()
     done = []

@@ -45,7 +45,7 @@ def test_batch_sizes_follow_the_stopping_rule():
     batch covers the steps to it, near or past it `check_every` steps, never past the
     step cap, and a single step while requests wait for room."""
     srv = S.Server.__new__(S.Server)
-    srv.step_cap, srv.check_every, srv.step_s = 100, 8, 1e-3
+    srv.step_cap, srv.check_every, srv.step_s, srv.max_slots = 100, 8, 1e-3, None
     early = S.Track(0, _spec(), 0.0, 0.0, t_cross=1.0)
     early.ts, early.steps = [0.0, 0.01], 2  # dt = 0.01: 198 steps to t = 2
     assert srv._batch({0: early}, False, None) == 98  # the step cap binds
@@ -59,6 +59,11 @@ def test_batch_sizes_follow_the_stopping_rule():
     assert srv._batch({0: early}, False, 0.05) == 51
     fresh = S.Track(2, _spec(), 0.0, 0.0, t_cross=1.0)  # no step yet: dt unknown
     assert srv._batch({2: fresh}, False, None) == 8
+    # one slot only (the sequential baseline): a waiting request cannot be admitted
+    # before the run finishes, so it does not shorten the batch
+    srv.max_slots = 1
+    assert srv._batch({0: early}, True, 0.01) == 199
+    srv.max_slots = None
 
 
 def test_oversize_request_rejected_alone():
@@ -71,7 +76,7 @@ def test_oversize_request_rejected_alone():
 
     srv = S.Server.__new__(S.Server)
     srv.pool, srv.budget, srv.precision = FakePool(), 1000, binding.DF_FP32_STATE
-    srv.tiles, srv.max_active = None, 0
+    srv.tiles, srv.max_active, srv.max_slots = None, 0, None
     orig = binding.run_bytes
     binding.run_bytes = lambda *a, **k: 10**9
     try:
