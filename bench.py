@@ -366,6 +366,21 @@ def run_batched(args):
         pool2.query()
     e2e_s = time.perf_counter() - t0
     q = pool.query()
+    # FP32-state error against FP64: the same runs in an FP64 pool, stepped as many
+    # coarse steps as the timed pool took (warm-up, timed steps, timing pass)
+    n_done = args.warmup + 2 * args.steps
+    p64 = binding.Pool(64 << 30, precision=binding.DF_FP64, stream=stream.cuda_stream)
+    for r in runs:
+        p64.admit(r["n_levels"], r["n"], r["lo"], r["hi"], r["G"], r["params"])
+    p64.step(n_done)
+    q64 = p64.query()
+    p64.close()
+    rel = []
+    for k, r in enumerate(runs):
+        d = np.asarray(r["params"]["flow_dir"], dtype=float)
+        f32 = -float(np.dot(q[k, :3], d)) / np.linalg.norm(d)
+        f64 = -float(np.dot(q64[k, :3], d)) / np.linalg.norm(d)
+        rel.append(abs(f32 - f64) / max(abs(f64), 1e-300))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -386,6 +401,9 @@ def run_batched(args):
         "gpu_launches": launches, "clocks": clk.summary(),
         "kernels_ms": {k: round(v[0], 4) for k, v in sorted(kinds.items(), key=lambda x: -x[1][0])},
         "unhealthy_runs": int(np.nansum(q[:, 5])),
+        "fp32_state_force_error_vs_fp64": {
+            "coarse_steps": n_done, "max_rel": max(rel), "median_rel": float(np.median(rel)),
+            "runs": len(rel), "time_equal": bool(np.all(q[:, 3] == q64[:, 3]))},
     }
     print(json.dumps(line), flush=True)
     pool.close()

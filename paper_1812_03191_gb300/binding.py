@@ -32,7 +32,7 @@ EXPORTS = (
     "df_autotune", "df_set_tile_shapes", "df_pool_set_tile_shapes", "df_set_transport",
     "df_pool_set_transport", "df_pool_set_field", "df_create_ground", "df_run_bytes_ground",
     "df_pool_admit_ground", "df_set_allocator", "df_create_levels", "df_pool_force",
-    "df_pool_history", "df_measure_fp64_peak",
+    "df_pool_history", "df_measure_fp64_peak", "df_check_df64",
 )
 POOL_OPS = 22
 # operator order of the per-op tables (tile shapes, blocks per SM)
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "df_pool_force": (C.c_int, [vp, C.c_int, dp, dp]),
         "df_pool_history": (C.c_int, [vp, C.c_int, C.c_int, dp, P(C.c_int)]),
         "df_measure_fp64_peak": (C.c_int, [C.c_int, C.c_int, dp, dp]),
+        "df_check_df64": (C.c_int, [dp, dp, C.c_int, dp]),
         "df_status": (C.c_int, [vp, dp, dp, P(C.c_int)]),
         "df_force": (C.c_int, [vp, dp, dp]),
         "df_force_now": (C.c_int, [vp, dp]),
@@ -218,6 +219,17 @@ def measure_fp64_peak(device=0, repeats=5):
     tf, ms = C.c_double(), C.c_double()
     _check(lib.df_measure_fp64_peak(int(device), int(repeats), C.byref(tf), C.byref(ms)))
     return tf.value, ms.value
+
+
+def check_df64(a, b):
+    """worst errors of the device's double-float conversion, sum, product and
+    quotient against FP64, each in units of its bound (<= 1 passes)"""
+    lib = load()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    w = np.zeros(4)
+    _check(lib.df_check_df64(_dp(a), _dp(b), a.size, _dp(w)))
+    return w
 
 
 def check_division(a, b):

@@ -1,0 +1,210 @@
+// df64.h -- double-float arithmetic for the FP64 stencils.
+//
+// A df64 holds a value as the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2: a 48-bit significand (relative rounding 2^-48, about 3.6e-15)
+// computed entirely on the FP32 pipe.  GB300 executes FP64 at 1/64 of its FP32 rate,
+// so the FP64 state's stencils (bound by that pipe) run their arithmetic in this
+// type; the state itself stays FP64 in memory.
+//
+// Published error-free transformations:
+//   two_sum       Knuth, The Art of Computer Programming vol. 2 (1969), 4.2.2:
+//                 s = fl(a + b) and the exact error e, a + b = s + e, for any a, b;
+//   fast_two_sum  Dekker, Numer. Math. 18 (1971): the same in 3 operations when
+//                 |a| >= |b| (or a = 0);
+//   two_prod      the exact error of a product from one fused multiply-add:
+//                 a b = p + fma(a, b, -p) (no overflow or underflow);
+// and the double-length operations built on them (Dekker 1971, the same algorithms
+// as the double-double library of Hida, Li & Bailey, ARITH 15, 2001, with float in
+// place of double).  Each operation below rounds its result to about 2^-48 of the
+// operands' magnitude; the sums are the "sloppy" variant, whose error is bounded
+// absolutely by 2^-47 (|a| + |b|) rather than relatively to a + b, which is the
+// bound the state's absolute tolerance needs.
+//
+// These functions must be compiled without reassociation of float additions (nvcc's
+// default): the error terms rely on IEEE rounding of every operation.
+#pragma once
+
+#include <math.h>
+
+namespace dfn {
+
+struct df64 {
+  float hi, lo;
+  df64() = default;  // trivial, so it may live in shared memory; {} gives zeros
+  __host__ __device__ constexpr df64(float h) : hi(h), lo(0.f) {}
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+};
+
+__host__ __device__ __forceinline__ df64 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return df64(s, (a - (s - bb)) + (b - bb));
+}
+
+__host__ __device__ __forceinline__ df64 fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return df64(s, b - (s - a));
+}
+
+__host__ __device__ __forceinline__ df64 two_prod(float a, float b) {
+  const float p = a * b;
+  return df64(p, fmaf(a, b, -p));
+}
+
+__host__ __device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+
+__host__ __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  df64 s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__host__ __device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+
+__host__ __device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  df64 p = two_prod(a.hi, b.hi);
+  float e = fmaf(a.hi, b.lo, p.lo);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p.hi, e);
+}
+
+// reciprocal estimate of a float: the hardware approximation on the device (its
+// error is removed by the correction step of the division), IEEE division on the host
+__host__ __device__ __forceinline__ float rcp_est(float b) {
+#ifdef __CUDA_ARCH__
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return r;
+#else
+  return 1.0f / b;
+#endif
+}
+
+// a / b: q1 from the reciprocal estimate, the remainder a - b q1 in double-float,
+// then one correction q2 = remainder / b.hi (the long division of Dekker 1971): the
+// quotient's relative error is about the square of q1's (2^-22 each, so about
+// 2^-44, 6e-14) plus the double-float rounding.
+// For the normal, non-zero divisors of the stencils (densities, 1 + a, sums of two
+// same-signed slopes).
+__host__ __device__ __forceinline__ df64 operator/(df64 a, df64 b) {
+  const float r = rcp_est(b.hi);
+  const float q1 = a.hi * r;
+  // remainder a - b q1, exact up to the double-float rounding
+  df64 p = two_prod(b.hi, q1);
+  p.lo = fmaf(b.lo, q1, p.lo);
+  df64 rem = a - fast_two_sum(p.hi, p.lo);
+  return fast_two_sum(q1, rem.hi * r);
+}
+
+__host__ __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__host__ __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
+
+// sign tests: the sign of hi is the sign of the value (hi = fl(hi + lo))
+__host__ __device__ __forceinline__ bool gt0(df64 v) { return v.hi > 0.f; }
+__host__ __device__ __forceinline__ bool le0(df64 v) { return !(v.hi > 0.f); }
+__host__ __device__ __forceinline__ bool lt0(df64 v) { return v.hi < 0.f; }
+
+// ---- conversions between double and double-float, in integer arithmetic.
+// GB300 converts between double and float on its FP64 pipe (measured: about 2
+// conversions per SM per cycle, the rate of an FP64 add, against 113 FP32 multiply-
+// adds), so (float)x and (double)f would cost the stencils as much as the FP64
+// arithmetic they replace.  These work on the bit patterns instead (integer and FP32
+// instructions only).  Values below 2^-126 in magnitude become 0 (the stencils'
+// tolerance is absolute and far above that), infinities and NaNs are kept.
+
+__host__ __device__ __forceinline__ unsigned f2u(float f) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(f);
+#else
+  unsigned u;
+  __builtin_memcpy(&u, &f, 4);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ float u2f(unsigned u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float f;
+  __builtin_memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+__host__ __device__ __forceinline__ unsigned long long d2u(double d) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(d);
+#else
+  unsigned long long u;
+  __builtin_memcpy(&u, &d, 8);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ double u2d(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double d;
+  __builtin_memcpy(&d, &u, 8);
+  return d;
+#endif
+}
+
+// x = hi + lo: x cut to 24 significant bits plus the remainder (its low 29 bits,
+// rounded to float), then normalised; error at most about 2^-47 |x|.
+__host__ __device__ __forceinline__ df64 to_df64(double x) {
+  const unsigned long long b = d2u(x);
+  const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
+  const unsigned sign = bh & 0x80000000u;
+  const int e = (int)((bh >> 20) & 0x7FFu);  // biased exponent of x
+  const int fe = e - 896;                     // biased float exponent of hi
+  if (fe <= 0) return df64(u2f(sign), 0.f);  // |x| < 2^-126 (and zero)
+  const unsigned top23 = ((bh & 0xFFFFFu) << 3) | (bl >> 29);
+  if (fe >= 255) {  // beyond float range: infinity, or NaN for a NaN
+    const bool nan = e == 0x7FF && (((bh & 0xFFFFFu) | bl) != 0u);
+    return df64(u2f(nan ? 0x7FC00000u : (sign | 0x7F800000u)), 0.f);
+  }
+  const float hi = u2f(sign | ((unsigned)fe << 23) | top23);
+  // remainder r = (bl & (2^29 - 1)) 2^(e - 1075): its top 23 bits as an exact float
+  // (the 2^23 magic-number conversion), then the low 6, then the power of two
+  const unsigned r = bl & 0x1FFFFFFFu;
+  const int le = e - 1069 + 127;  // float exponent field of 2^(e - 1075 + 6)
+  if (r == 0u || le <= 0) return df64(hi, 0.f);
+  const float rh = u2f(0x4B000000u | (r >> 6)) - 8388608.0f;         // r >> 6, exact
+  const float rl = u2f(0x4B000000u | (r & 63u)) - 8388608.0f;        // r & 63, exact
+  const float rf = fmaf(rh, 64.0f, rl);                               // r, rounded
+  const float lo = rf * u2f((unsigned)le << 23) * 0.015625f;          // r 2^(e - 1075)
+  return fast_two_sum(hi, sign ? -lo : lo);  // normalised: |lo| <= ulp(hi) / 2
+}
+
+// hi + lo rounded to double: hi's significand and lo's, aligned in a 64-bit integer
+// (|lo| < ulp(hi), so the sum stays within one binade step of hi)
+__host__ __device__ __forceinline__ double to_double(df64 v) {
+  const unsigned sh = f2u(v.hi), sl = f2u(v.lo);
+  const int eh = (int)((sh >> 23) & 0xFFu), el = (int)((sl >> 23) & 0xFFu);
+  const unsigned long long sign = (unsigned long long)(sh & 0x80000000u) << 32;
+  if (eh == 0) return u2d(sign);  // zero (subnormal hi: flushed)
+  if (eh == 255)                  // infinity or NaN
+    return u2d(sign | 0x7FF0000000000000ull |
+               ((unsigned long long)(sh & 0x7FFFFFu) << 29));
+  unsigned long long S = (unsigned long long)((sh & 0x7FFFFFu) | 0x800000u) << 29;
+  if (el != 0) {
+    const unsigned long long ml = (sl & 0x7FFFFFu) | 0x800000u;
+    const int shift = el - eh + 29;  // lo in units of 2^-52 of hi's binade
+    unsigned long long L = 0;
+    if (shift >= 0)
+      L = ml << shift;
+    else if (shift > -25)
+      L = ml >> (-shift);
+    if ((sl ^ sh) & 0x80000000u)
+      S -= L;
+    else
+      S += L;
+  }
+  int ex = eh - 127 + 1023;
+  if (S < (1ull << 52)) {  // fell below hi's binade: renormalise
+    S <<= 1;
+    ex -= 1;
+  }
+  return u2d(sign | ((unsigned long long)ex << 52) | (S & 0xFFFFFFFFFFFFFull));
+}
+
+}  // namespace dfn

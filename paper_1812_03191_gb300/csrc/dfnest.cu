@@ -588,14 +588,15 @@ struct Builder {
     memset(&it, 0, sizeof it);
     it.L = r.L[l].v;
     it.S = r.S;
-    it.bg = make_bg<T>(r.P);
-    it.g = make_geo<T>(it.L);
-    it.dt = sizeof(T) == 8 ? (const void*)&r.ds->dtl[l] : (const void*)&r.ds->dtf[l];
+    using C = Arith<T>;
+    it.bg = make_bg<C>(r.P);
+    it.g = make_geo<C>(it.L);
+    it.dt = sizeof(T) == 8 ? (const void*)&r.ds->dtd[l] : (const void*)&r.ds->dtf[l];
     it.ds = r.ds;
-    it.gm1 = (T)(r.P.gamma - 1.0);
-    it.lum = (T)r.P.L;
-    it.chi = (T)r.P.chi;
-    it.av = (T)r.P.av_c2;
+    it.gm1 = to_arith<C>(r.P.gamma - 1.0);
+    it.lum = to_arith<C>(r.P.L);
+    it.chi = to_arith<C>(r.P.chi);
+    it.av = to_arith<C>(r.P.av_c2);
     it.gg = r.P.gamma * (r.P.gamma - 1.0);
     it.rho0d = r.P.rho0;
     it.e0d = r.P.e0;
@@ -1528,6 +1529,7 @@ int df_compute_dt(df_ctx* c, double* dt, double* dt_level) {
   CK(cudaMemcpy(&r->ds->dt, &before.dt, sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(r->ds->dtl, before.dtl, sizeof before.dtl, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(r->ds->dtf, before.dtf, sizeof before.dtf, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(r->ds->dtd, before.dtd, sizeof before.dtd, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(&r->ds->xi1, &before.xi1, sizeof before.xi1, cudaMemcpyHostToDevice));
   leave(c);
   if (dt) *dt = after.dt;
@@ -1740,6 +1742,24 @@ int df_check_division(const double* a_host, const double* b_host, int n, double*
   cudaFree(da);
   cudaFree(db);
   cudaFree(dm);
+  return DF_OK;
+}
+
+int df_check_df64(const double* a_host, const double* b_host, int n, double* worst) {
+  if (!a_host || !b_host || !worst || n < 1) return fail(DF_EINVAL, "bad df64 check input");
+  double *da = nullptr, *db = nullptr, *dw = nullptr;
+  CK(cudaMalloc(&da, n * sizeof(double)));
+  CK(cudaMalloc(&db, n * sizeof(double)));
+  CK(cudaMalloc(&dw, 4 * sizeof(double)));
+  CK(cudaMemcpy(da, a_host, n * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(db, b_host, n * sizeof(double), cudaMemcpyHostToDevice));
+  CK(cudaMemset(dw, 0, 4 * sizeof(double)));
+  launch_df64_check(da, db, n, dw, nullptr);
+  CK(cudaGetLastError());
+  CK(cudaMemcpy(worst, dw, 4 * sizeof(double), cudaMemcpyDeviceToHost));
+  cudaFree(da);
+  cudaFree(db);
+  cudaFree(dw);
   return DF_OK;
 }
 

@@ -1,13 +1,14 @@
 // internal.h -- device-side data structures and kernel launchers of libdfnest.
 //
-// One level (Sec. 3: "a full mesh consists of the active cells and the ghost or
-// buffer cells") is a padded box of s = n + 2G elements per axis, x fastest,
+// One level (Sec. 3: a mesh is its active cells surrounded by layers of ghost
+// cells) is a padded box of s = n + 2G elements per axis, x fastest,
 // one structure-of-arrays allocation per field.  rho and e are cell-centred,
 // v_d sits on the lower d-face of the cell with the same index.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include "df64.h"
 
 namespace dfn {
 
@@ -136,42 +137,69 @@ struct DevScalars {
   double dtlev[16];              // per-level limits of the last reduction
   double dtl[16];                // level step of each level: dt / prod_{m<l} xi_m
   float dtf[16];                 // the same in FP32
+  df64 dtd[16];                  // and in double-float
   int unhealthy;
   unsigned xi1;  // bit m set when the Eq. 55-56 search chose xi_m = 1 this coarse step
 };
 
+// Arithmetic type of the stencils of a state type: the FP32 state computes in float;
+// the FP64 state in double-float (df64.h), 48-bit significands on the FP32 pipe,
+// since GB300's FP64 pipe runs at 1/64 of its FP32 rate.  Reductions (time step,
+// force, frontier flux sums) and the inter-level operators stay in the state type or
+// FP64.
+template <class T>
+struct ArithOf {
+  using type = T;
+};
+template <>
+struct ArithOf<double> {
+  using type = df64;
+};
+template <class T>
+using Arith = typename ArithOf<T>::type;
+
+// a double constant in an arithmetic type (host side)
+template <class C>
+inline C to_arith(double x) {
+  return (C)x;
+}
+template <>
+inline df64 to_arith<df64>(double x) {
+  return to_df64(x);
+}
+
 // per-level geometry constants in the kernels' arithmetic type (no FP64 work in
 // FP32 kernels: GB300's FP64 pipe is 1/64 of its FP32 rate)
-template <class T>
+template <class C>
 struct Geo {
-  T inv_dx[3], area[3], dcoef[3], inv_vol;
+  C inv_dx[3], area[3], dcoef[3], inv_vol;
 };
 
-template <class T>
-inline Geo<T> make_geo(const LevelView& L) {
-  Geo<T> g;
+template <class C>
+inline Geo<C> make_geo(const LevelView& L) {
+  Geo<C> g;
   for (int d = 0; d < 3; ++d) {
-    g.inv_dx[d] = (T)L.inv_dx[d];
-    g.area[d] = (T)L.area[d];
-    g.dcoef[d] = (T)L.dcoef[d];
+    g.inv_dx[d] = to_arith<C>(L.inv_dx[d]);
+    g.area[d] = to_arith<C>(L.area[d]);
+    g.dcoef[d] = to_arith<C>(L.dcoef[d]);
   }
-  g.inv_vol = (T)L.inv_vol;
+  g.inv_vol = to_arith<C>(L.inv_vol);
   return g;
 }
 
 // uniform background of Sec. 3.4 in the kernels' arithmetic type
-template <class T>
+template <class C>
 struct Bg {
-  T rho0, e0, eps0, V[3];
+  C rho0, e0, eps0, V[3];
 };
 
-template <class T>
-inline Bg<T> make_bg(const Phys& P) {
-  Bg<T> b;
-  b.rho0 = (T)P.rho0;
-  b.e0 = (T)P.e0;
-  b.eps0 = (T)(P.e0 / P.rho0);
-  for (int d = 0; d < 3; ++d) b.V[d] = (T)P.V[d];
+template <class C>
+inline Bg<C> make_bg(const Phys& P) {
+  Bg<C> b;
+  b.rho0 = to_arith<C>(P.rho0);
+  b.e0 = to_arith<C>(P.e0);
+  b.eps0 = to_arith<C>(P.e0 / P.rho0);
+  for (int d = 0; d < 3; ++d) b.V[d] = to_arith<C>(P.V[d]);
   return b;
 }
 
@@ -290,15 +318,15 @@ struct __align__(16) Item {
   LevelView F;          // fine level of CommUp / CommMean
   Scratch S;            // the run's scratch
   Box b;                // box of stencil ops
-  Bg<T> bg;
-  Geo<T> g;
-  const void* dt;       // this level's step, T
+  Bg<Arith<T>> bg;
+  Geo<Arith<T>> g;
+  const void* dt;       // this level's step, Arith<T>
   DevScalars* ds;       // the run's scalars
   const DtFinal* fin;   // OP_DT_FINAL constants
   double* partials;     // force partials (this level's first, or the run's for the final sum)
   double* ring;         // force history
   long long* ring_pos;
-  T gm1, lum, chi, av;
+  Arith<T> gm1, lum, chi, av;
   double gg, rho0d, e0d, V[3], dt_fixed;
   int ring_cap, npart, level, band, flags, bc_lo, bc_hi;
   unsigned count;       // index-space size of the item
@@ -355,6 +383,8 @@ enum KernelKind {
 
 // hot-path FP64 division versus IEEE division (device arrays; max_ulp zeroed by caller)
 int launch_hdiv_check(const double* a, const double* b, int n, double* max_ulp, cudaStream_t st);
+// double-float arithmetic versus FP64 (device arrays; worst[4] zeroed by the caller)
+int launch_df64_check(const double* a, const double* b, int n, double* worst, cudaStream_t st);
 // launches the FP64 throughput probe; returns the flops it executes
 long long launch_dfma_probe(int blocks, int iters, double* sink, cudaStream_t st);
 

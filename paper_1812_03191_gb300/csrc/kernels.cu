@@ -75,44 +75,61 @@ __device__ __forceinline__ double hdiv(double a, double b) {
   return fma(r, fma(-b, q, a), q);
 }
 __device__ __forceinline__ float hdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ df64 hdiv(df64 a, df64 b) { return a / b; }
 
-// sign tests; for FP64 on the integer pipe (the FP64 pipe bounds the FP64 kernels):
-// the bit pattern of a non-NaN double, read as a signed integer, has the sign of the
-// value, with +0 -> 0 and -0 -> negative.  (A NaN's sign bit decides instead; a NaN
-// state is caught by the health check of the time-step reduction.)
+// The stencils' arithmetic type C = Arith<T> (internal.h): float for the FP32 state,
+// double-float for the FP64 state.  Loads convert the stored value to C, stores round
+// C back to the state type.
+__device__ __forceinline__ float ld(const float* __restrict__ p, int i) { return p[i]; }
+__device__ __forceinline__ df64 ld(const double* __restrict__ p, int i) { return to_df64(p[i]); }
+__device__ __forceinline__ df64 ld(const df64* __restrict__ p, int i) { return p[i]; }
+__device__ __forceinline__ void st(df64* p, int i, df64 v) { p[i] = v; }
+__device__ __forceinline__ void st(float* p, int i, float v) { p[i] = v; }
+__device__ __forceinline__ void st(double* p, int i, df64 v) { p[i] = to_double(v); }
+__device__ __forceinline__ double as_double(float v) { return (double)v; }
+__device__ __forceinline__ double as_double(df64 v) { return to_double(v); }
+template <class C>
+__device__ __forceinline__ C from_double(double x) {
+  return (C)x;
+}
+template <>
+__device__ __forceinline__ df64 from_double<df64>(double x) {
+  return to_df64(x);
+}
+
+// sign tests of the arithmetic types (double-float: df64.h)
 __device__ __forceinline__ bool gt0(float v) { return v > 0.f; }
 __device__ __forceinline__ bool le0(float v) { return v <= 0.f; }
-__device__ __forceinline__ bool gt0(double v) { return __double_as_longlong(v) > 0; }
-__device__ __forceinline__ bool le0(double v) { return __double_as_longlong(v) <= 0; }
+__device__ __forceinline__ bool lt0(float v) { return v < 0.f; }
 
 // Half the van Leer (1977) harmonic limited slope (Sec. 3.2.1 cites it for the
 // interpolation): dl dr / (dl + dr) where dl dr > 0, else 0.  Callers fold the
 // factor 2 into their coefficients; scaling by 2 is exact, so the results equal
 // those of the full slope bit for bit.  When the product underflows to zero the
 // slope is zero, so the divisor dl + dr is never zero or subnormal.
-template <class T>
-__device__ __forceinline__ T hslope(T dl, T dr) {
-  T pr = dl * dr;
-  return le0(pr) ? T(0) : hdiv(pr, dl + dr);
+template <class C>
+__device__ __forceinline__ C hslope(C dl, C dr) {
+  C pr = dl * dr;
+  return le0(pr) ? C(0.f) : hdiv(pr, dl + dr);
 }
 
 // The upwind side's value, slopes and coefficient are selected first, so one limiter
 // (one division) serves both flow directions: u > 0 gives qm + (1 - cour)/2 * slope,
 // u <= 0 gives q0 + (-1 - cour)/2 * slope = q0 - (1 + cour)/2 * slope, with
 // (+-1 - cour)/2 * slope = (+-1 - cour) * hslope.
-template <class T>
-__device__ __forceinline__ T upwind_v(T qmm, T qm, T q0, T qp, T u, T cour) {
+template <class C>
+__device__ __forceinline__ C upwind_v(C qmm, C qm, C q0, C qp, C u, C cour) {
   const bool up = gt0(u);
-  const T dm = q0 - qm;
-  const T a = up ? qm : q0;
-  const T dl = up ? qm - qmm : dm;
-  const T dr = up ? dm : qp - q0;
-  return a + ((up ? T(1) : T(-1)) - cour) * hslope(dl, dr);
+  const C dm = q0 - qm;
+  const C a = up ? qm : q0;
+  const C dl = up ? qm - qmm : dm;
+  const C dr = up ? dm : qp - q0;
+  return a + ((up ? C(1.f) : C(-1.f)) - cour) * hslope(dl, dr);
 }
 
-template <class T>
-__device__ __forceinline__ T upwind(const T* __restrict__ q, int c, int st, T u, T cour) {
-  return upwind_v(q[c - 2 * st], q[c - st], q[c], q[c + st], u, cour);
+template <class P, class C>
+__device__ __forceinline__ C upwind(const P* __restrict__ q, int c, int s, C u, C cour) {
+  return upwind_v(ld(q, c - 2 * s), ld(q, c - s), ld(q, c), ld(q, c + s), u, cour);
 }
 
 inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
@@ -160,31 +177,33 @@ __device__ __forceinline__ bool near_frontier(const LevelView& L, int d, int gd)
 // S(h) of Eq. 15: v_d -= h [ (p_c - p_m)/(dx rho_face) + (Phi_c - Phi_m)/dx ]
 template <class T>
 __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, const Scratch& S,
-                                                   const T* __restrict__ dtp, int write_pi, T gm1,
-                                                   const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
+                                          const Arith<T>* __restrict__ dtp, int write_pi,
+                                          Arith<T> gm1, const Bg<Arith<T>>& bg,
+                                          const Geo<Arith<T>>& g, unsigned tid) {
+  using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const T* __restrict__ e = (const T*)L.q[F_E];
   const T* __restrict__ phi = (const T*)L.phi;
-  const T h = T(0.5) * dtp[0];
+  const C h = C(0.5f) * dtp[0];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T rc = rho[c], ec = e[c], fc = phi[c];
+  const C rc = ld(rho, c), ec = ld(e, c), fc = ld(phi, c);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     T* v = (T*)L.q[F_VX + d];
     if (c3[d] >= 1) {
       int m = c - L.st[d];
-      T drf = T(0.5) * (rho[m] + rc);
-      T rf = bg.rho0 + drf;
-      T acc = (hdiv(gm1 * (ec - e[m]), rf) + (fc - phi[m])) * g.inv_dx[d];
-      T vn = v[c] - h * acc;
-      v[c] = vn;
+      C drf = C(0.5f) * (ld(rho, m) + rc);
+      C rf = bg.rho0 + drf;
+      C acc = (hdiv(gm1 * (ec - ld(e, m)), rf) + (fc - ld(phi, m))) * g.inv_dx[d];
+      C vn = ld(v, c) - h * acc;
+      st(v, c, vn);
       // momentum deviation: rf (V + dv) - rho0 V
-      if (write_pi) ((T*)S.pi[d])[c] = bg.rho0 * vn + drf * (bg.V[d] + vn);
+      if (write_pi) st((Arith<T>*)S.pi[d], c, bg.rho0 * vn + drf * (bg.V[d] + vn));
     } else if (write_pi) {
-      ((T*)S.pi[d])[c] = T(0);
+      ((Arith<T>*)S.pi[d])[c] = C(0.f);
     }
   }
 }
@@ -197,51 +216,55 @@ __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, cons
 // (from the velocities after the first kick; dv is the same in deviations).
 template <class T>
 __device__ __forceinline__ void el_visc_q(const LevelView& L, const Box& b, const Scratch& S,
-                                          const T* __restrict__ dtp, T av, const Bg<T>& bg,
-                                          const Geo<T>& g, unsigned tid) {
+                                          const Arith<T>* __restrict__ dtp, Arith<T> av,
+                                          const Bg<Arith<T>>& bg, const Geo<Arith<T>>& g,
+                                          unsigned tid) {
+  using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T rc = bg.rho0 + ((const T*)L.q[F_RHO])[c];
-  T heat = T(0);
+  const C rc = bg.rho0 + ld((const T*)L.q[F_RHO], c);
+  C heat = C(0.f);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    T q = T(0);
+    C q = C(0.f);
     if (c3[d] < L.s[d] - 1) {
       const T* v = (const T*)L.q[F_VX + d];
-      const T dv = v[c + L.st[d]] - v[c];
-      if (dv < T(0)) q = av * rc * dv * dv;
+      const C dv = ld(v, c + L.st[d]) - ld(v, c);
+      if (lt0(dv)) q = av * rc * dv * dv;
       heat += q * dv * g.inv_dx[d];
     }
-    ((T*)S.P[d])[c] = q;
+    st((Arith<T>*)S.P[d], c, q);
   }
   T* e = (T*)L.q[F_E];
-  e[c] = e[c] - dtp[0] * heat;
+  st(e, c, ld(e, c) - dtp[0] * heat);
 }
 
 // Second pass: v_d -= dt (q_c - q_m) / (dx_d rho_face) on faces 1.. of each axis, and
 // the staggered momenta the transport starts from follow the new velocity.
 template <class T>
 __device__ __forceinline__ void el_visc_v(const LevelView& L, const Box& b, const Scratch& S,
-                                          const T* __restrict__ dtp, int write_pi,
-                                          const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
+                                          const Arith<T>* __restrict__ dtp, int write_pi,
+                                          const Bg<Arith<T>>& bg, const Geo<Arith<T>>& g,
+                                          unsigned tid) {
+  using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T dt = dtp[0];
+  const C dt = dtp[0];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (c3[d] < 1) continue;
     const int m = c - L.st[d];
-    const T* q = (const T*)S.P[d];
+    const Arith<T>* q = (const Arith<T>*)S.P[d];
     T* v = (T*)L.q[F_VX + d];
-    const T drf = T(0.5) * (rho[m] + rho[c]);
-    const T vn = v[c] - dt * hdiv(q[c] - q[m], bg.rho0 + drf) * g.inv_dx[d];
-    v[c] = vn;
-    if (write_pi) ((T*)S.pi[d])[c] = bg.rho0 * vn + drf * (bg.V[d] + vn);
+    const C drf = C(0.5f) * (ld(rho, m) + ld(rho, c));
+    const C vn = ld(v, c) - dt * hdiv(ld(q, c) - ld(q, m), bg.rho0 + drf) * g.inv_dx[d];
+    st(v, c, vn);
+    if (write_pi) st((Arith<T>*)S.pi[d], c, bg.rho0 * vn + drf * (bg.V[d] + vn));
   }
 }
 
@@ -254,10 +277,12 @@ __device__ __forceinline__ void el_visc_v(const LevelView& L, const Box& b, cons
 // ------------------------------------------------- SubStep3 + luminosity + e/rho
 template <class T, int NC>
 __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b,
-                                                const Scratch& S, const T* __restrict__ dtp,
-                                                T gm1, T lum, int do_ss3, int do_lum,
-                                                int do_eps, const Bg<T>& bg, const Geo<T>& g,
-                                                const unsigned* el) {
+                                                const Scratch& S,
+                                                const Arith<T>* __restrict__ dtp, Arith<T> gm1,
+                                                Arith<T> lum, int do_ss3, int do_lum, int do_eps,
+                                                const Bg<Arith<T>>& bg,
+                                                const Geo<Arith<T>>& g, const unsigned* el) {
+  using C = Arith<T>;
   int c[NC];
   bool ok[NC], ss3[NC], lm[NC];
 #pragma unroll
@@ -277,37 +302,37 @@ __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b
   const T* vx = (const T*)L.q[F_VX];
   const T* vy = (const T*)L.q[F_VX + 1];
   const T* vz = (const T*)L.q[F_VX + 2];
-  T ec[NC], x0[NC], x1[NC], y0[NC], y1[NC], z0[NC], z1[NC], lw[NC], dr[NC];
+  C ec[NC], x0[NC], x1[NC], y0[NC], y1[NC], z0[NC], z1[NC], lw[NC], dr[NC];
 #pragma unroll
   for (int n = 0; n < NC; ++n) {
-    ec[n] = e[c[n]];
+    ec[n] = ld(e, c[n]);
     if (ss3[n]) {
-      x0[n] = vx[c[n]];
-      x1[n] = vx[c[n] + L.st[0]];
-      y0[n] = vy[c[n]];
-      y1[n] = vy[c[n] + L.st[1]];
-      z0[n] = vz[c[n]];
-      z1[n] = vz[c[n] + L.st[2]];
+      x0[n] = ld(vx, c[n]);
+      x1[n] = ld(vx, c[n] + L.st[0]);
+      y0[n] = ld(vy, c[n]);
+      y1[n] = ld(vy, c[n] + L.st[1]);
+      z0[n] = ld(vz, c[n]);
+      z1[n] = ld(vz, c[n] + L.st[2]);
     }
-    if (lm[n]) lw[n] = ((const T*)L.lumw)[c[n]];
-    if (do_eps) dr[n] = ((const T*)L.q[F_RHO])[c[n]];
+    if (lm[n]) lw[n] = ld((const T*)L.lumw, c[n]);
+    if (do_eps) dr[n] = ld((const T*)L.q[F_RHO], c[n]);
   }
-  const T dt = dtp[0];
+  const C dt = dtp[0];
 #pragma unroll
   for (int n = 0; n < NC; ++n) {
     if (!ok[n]) continue;
-    T ecn = ec[n];
+    C ecn = ec[n];
     if (ss3[n]) {
-      T div = (x1[n] - x0[n]) * g.inv_dx[0] + (y1[n] - y0[n]) * g.inv_dx[1] +
+      C div = (x1[n] - x0[n]) * g.inv_dx[0] + (y1[n] - y0[n]) * g.inv_dx[1] +
               (z1[n] - z0[n]) * g.inv_dx[2];
-      T a = T(0.5) * dt * gm1 * div;
+      C a = C(0.5f) * dt * gm1 * div;
       // (e0 + de)(1 - a)/(1 + a) - e0
-      ecn = hdiv(ecn * (T(1) - a) - T(2) * a * bg.e0, T(1) + a);
+      ecn = hdiv(ecn * (C(1.f) - a) - C(2.f) * a * bg.e0, C(1.f) + a);
     }
     if (lm[n]) ecn = ecn + lum * dt * lw[n];
-    e[c[n]] = ecn;
+    st(e, c[n], ecn);
     // e/rho - e0/rho0 = (de - eps0 drho)/(rho0 + drho)
-    if (do_eps) ((T*)S.eps)[c[n]] = hdiv(ecn - bg.eps0 * dr[n], bg.rho0 + dr[n]);
+    if (do_eps) st((Arith<T>*)S.eps, c[n], hdiv(ecn - bg.eps0 * dr[n], bg.rho0 + dr[n]));
   }
 }
 
@@ -355,18 +380,22 @@ __device__ __forceinline__ void fr_sums(const LevelView& L, const DevScalars* ds
 // --------------------------------------------------------------- diffusion
 // energy moved in +d across a face during dt: -chi rho_f d(e/rho)/dx * area * dt
 template <class T>
-__device__ __forceinline__ T diff_flux(const LevelView& L, const Geo<T>& g,
-                                       const T* __restrict__ rho, const T* __restrict__ eps, int f,
-                                       int d, T chi, T dt, T rho0, int dfr) {
+__device__ __forceinline__ Arith<T> diff_flux(const LevelView& L, const Geo<Arith<T>>& g,
+                                              const T* __restrict__ rho,
+                                              const Arith<T>* __restrict__ eps, int f, int d,
+                                              Arith<T> chi, Arith<T> dt, Arith<T> rho0, int dfr) {
+  using C = Arith<T>;
   int m = f - L.st[d];
-  T rf = dfr ? rho0 : rho0 + T(0.5) * (rho[m] + rho[f]);
-  return -chi * rf * (eps[f] - eps[m]) * g.dcoef[d] * dt;
+  C rf = dfr ? rho0 : rho0 + C(0.5f) * (ld(rho, m) + ld(rho, f));
+  return -chi * rf * (ld(eps, f) - ld(eps, m)) * g.dcoef[d] * dt;
 }
 
 template <class T, int NC>
 __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, const Scratch& S,
-                                           const T* __restrict__ dtp, T chi, T rho0, int dfr,
-                                           const Geo<T>& g, const unsigned* el) {
+                                           const Arith<T>* __restrict__ dtp, Arith<T> chi,
+                                           Arith<T> rho0, int dfr, const Geo<Arith<T>>& g,
+                                           const unsigned* el) {
+  using C = Arith<T>;
   int c[NC], c3[NC][3];
   bool ok[NC];
 #pragma unroll
@@ -381,10 +410,10 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
     c3[n][1] = j;
     c3[n][2] = k;
   }
-  const T dt = dtp[0];
+  const C dt = dtp[0];
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
-  const T* __restrict__ eps = (const T*)S.eps;
-  T q[NC][3][2];  // flux through the lower and the upper d-face
+  const Arith<T>* __restrict__ eps = (const Arith<T>*)S.eps;
+  C q[NC][3][2];  // flux through the lower and the upper d-face
 #pragma unroll
   for (int n = 0; n < NC; ++n)
 #pragma unroll
@@ -400,22 +429,24 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
         if (!near_frontier(L, d, c3[n][d])) continue;
         int slot, f3[3] = {c3[n][0], c3[n][1], c3[n][2]};
         int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
-        if (side >= 0) q[n][d][0] = (T)L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot];
+        if (side >= 0)
+          q[n][d][0] = from_double<C>(L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot]);
         f3[d] += 1;
         side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
-        if (side >= 0) q[n][d][1] = (T)L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot];
+        if (side >= 0)
+          q[n][d][1] = from_double<C>(L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot]);
       }
   }
   T* e = (T*)L.q[F_E];
-  T ev[NC];
+  C ev[NC];
 #pragma unroll
-  for (int n = 0; n < NC; ++n) ev[n] = e[c[n]];
+  for (int n = 0; n < NC; ++n) ev[n] = ld(e, c[n]);
 #pragma unroll
   for (int n = 0; n < NC; ++n) {
-    T div = T(0);
+    C div = C(0.f);
 #pragma unroll
     for (int d = 0; d < 3; ++d) div += q[n][d][1] - q[n][d][0];
-    if (ok[n]) e[c[n]] = ev[n] - div * g.inv_vol;
+    if (ok[n]) st(e, c[n], ev[n] - div * g.inv_vol);
   }
 }
 
@@ -424,16 +455,17 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
 // inside the diffusion kernel the record code would cost that kernel occupancy)
 template <class T>
 __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scratch& S,
-                                                 const T* __restrict__ dtp, T chi, T rho0,
-                                                 int dfr, const Geo<T>& g, int sub,
-                                                 unsigned tid) {
+                                                 const Arith<T>* __restrict__ dtp, Arith<T> chi,
+                                                 Arith<T> rho0, int dfr,
+                                                 const Geo<Arith<T>>& g, int sub, unsigned tid) {
+  using C = Arith<T>;
   if (tid >= 6u * (unsigned)L.acc_slots) return;
   const int side = (int)tid / L.acc_slots, slot = (int)tid - side * L.acc_slots;
   const int d = side >> 1, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
   const int h1 = L.n[t1] >> 1;
   if (slot >= h1 * (L.n[t2] >> 1)) return;
   const int a = slot % h1, b = slot / h1;
-  const T dt = dtp[0];
+  const C dt = dtp[0];
   const int fd = (side & 1) ? L.G + L.n[d] : L.G;
 #pragma unroll
   for (int v = 0; v < 2; ++v)
@@ -445,32 +477,33 @@ __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scrat
       f3[t2] = L.G + 2 * b + v;
       const int f = (f3[2] * L.s[1] + f3[1]) * L.s[0] + f3[0];
       fr_put(L, d, fd, f3[t1], f3[t2], 2, sub,
-             (double)diff_flux(L, g, (const T*)L.q[F_RHO], (const T*)S.eps, f, d, chi, dt, rho0,
-                               dfr));
+             as_double(diff_flux(L, g, (const T*)L.q[F_RHO], (const Arith<T>*)S.eps, f, d, chi, dt,
+                                 rho0, dfr)));
     }
 }
 
 // --------------------------------------------------------------- transport
 template <class T>
 __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const Scratch& S,
-                                        const Bg<T>& bg, int eps_only, unsigned tid) {
+                                         const Bg<Arith<T>>& bg, int eps_only, unsigned tid) {
+  using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T rc = rho[c];
-  ((T*)S.eps)[c] = hdiv(((const T*)L.q[F_E])[c] - bg.eps0 * rc, bg.rho0 + rc);
+  const C rc = ld(rho, c);
+  st((Arith<T>*)S.eps, c, hdiv(ld((const T*)L.q[F_E], c) - bg.eps0 * rc, bg.rho0 + rc));
   if (eps_only) return;
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    T wv = T(0);
+    C wv = C(0.f);
     if (c3[m] >= 1) {
       // Pi/rho_face - V = (dPi - V drf)/(rho0 + drf)
-      T drf = T(0.5) * (rho[c - L.st[m]] + rc);
-      wv = hdiv(((const T*)S.pi[m])[c] - bg.V[m] * drf, bg.rho0 + drf);
+      C drf = C(0.5f) * (ld(rho, c - L.st[m]) + rc);
+      wv = hdiv(ld((const Arith<T>*)S.pi[m], c) - bg.V[m] * drf, bg.rho0 + drf);
     }
-    ((T*)S.w[m])[c] = wv;
+    st((Arith<T>*)S.w[m], c, wv);
   }
 }
 
@@ -479,32 +512,34 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
 // fixed kernel-parameter operand instead of a dynamically indexed load
 template <class T, int d>
 __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const Scratch& S,
-                                                  const T* __restrict__ dtp, const Bg<T>& bg,
-                                                  const Geo<T>& g, int sub, unsigned tid) {
+                                         const Arith<T>* __restrict__ dtp,
+                                         const Bg<Arith<T>>& bg, const Geo<Arith<T>>& g,
+                                         int sub, unsigned tid) {
+  using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  T Fv = T(0), Ev = T(0);
+  C Fv = C(0.f), Ev = C(0.f);
   if (c3[d] >= 2 && c3[d] < L.s[d] - 1) {
-    const T dt = dtp[0];
-    const int st = L.st[d];
-    const T Adt = g.area[d] * dt;
-    const T du = ((const T*)L.q[F_VX + d])[c];
-    const T u = bg.V[d] + du;
-    const T cour = u * (dt * g.inv_dx[d]);
-    const T F0 = bg.rho0 * bg.V[d] * Adt;
-    T drs = upwind((const T*)L.q[F_RHO], c, st, u, cour);
+    const C dt = dtp[0];
+    const int sd = L.st[d];
+    const C Adt = g.area[d] * dt;
+    const C du = ld((const T*)L.q[F_VX + d], c);
+    const C u = bg.V[d] + du;
+    const C cour = u * (dt * g.inv_dx[d]);
+    const C F0 = bg.rho0 * bg.V[d] * Adt;
+    C drs = upwind((const T*)L.q[F_RHO], c, sd, u, cour);
     Fv = (bg.rho0 * du + drs * u) * Adt;        // F - rho0 V_d A dt
-    T des = upwind((const T*)S.eps, c, st, u, cour);
+    C des = upwind((const Arith<T>*)S.eps, c, sd, u, cour);
     Ev = bg.eps0 * Fv + des * (F0 + Fv);        // E - eps0 rho0 V_d A dt
   }
-  ((T*)S.F)[c] = Fv;
-  ((T*)S.E)[c] = Ev;
+  st((Arith<T>*)S.F, c, Fv);
+  st((Arith<T>*)S.E, c, Ev);
   if (L.is_child && (c3[d] == L.G || c3[d] == L.G + L.n[d])) {  // CommFlux record
     constexpr int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
-    fr_put(L, d, c3[d], c3[t1], c3[t2], 0, sub, (double)Fv);
-    fr_put(L, d, c3[d], c3[t1], c3[t2], 1, sub, (double)Ev);
+    fr_put(L, d, c3[d], c3[t1], c3[t2], 0, sub, as_double(Fv));
+    fr_put(L, d, c3[d], c3[t1], c3[t2], 1, sub, as_double(Ev));
   }
 }
 
@@ -512,77 +547,83 @@ __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const
 // staggered momentum fluxes of sweep d (deviation: P - V_m rho0 V_d A dt)
 template <class T, int d>
 __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const Scratch& S,
-                                                 const T* __restrict__ dtp, const Bg<T>& bg, const Geo<T>& g, unsigned tid) {
+                                        const Arith<T>* __restrict__ dtp, const Bg<Arith<T>>& bg,
+                                        const Geo<Arith<T>>& g, unsigned tid) {
+  using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T dt = dtp[0];
-  const int st = L.st[d];
+  const C dt = dtp[0];
+  const int sd = L.st[d];
   const T* __restrict__ vd = (const T*)L.q[F_VX + d];
-  const T* __restrict__ F = (const T*)S.F;
-  const T dtdx = dt * g.inv_dx[d];
-  const T F0 = bg.rho0 * bg.V[d] * (g.area[d] * dt);
+  const Arith<T>* __restrict__ F = (const Arith<T>*)S.F;
+  const C dtdx = dt * g.inv_dx[d];
+  const C F0 = bg.rho0 * bg.V[d] * (g.area[d] * dt);
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    T P = T(0);
+    C P = C(0.f);
     if (m == d) {
       if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
-        T uc = bg.V[d] + T(0.5) * (vd[c] + vd[c + st]);
-        T Fc = T(0.5) * (F[c] + F[c + st]);
-        T ws = upwind((const T*)S.w[m], c + st, st, uc, uc * dtdx);
+        C uc = bg.V[d] + C(0.5f) * (ld(vd, c) + ld(vd, c + sd));
+        C Fc = C(0.5f) * (ld(F, c) + ld(F, c + sd));
+        C ws = d == 0 ? upwind((const T*)S.w[m], c + sd, sd, uc, uc * dtdx)
+                      : upwind((const Arith<T>*)S.w[m], c + sd, sd, uc, uc * dtdx);
         P = bg.V[m] * Fc + ws * (F0 + Fc);
       }
     } else if (c3[d] >= 2 && c3[d] < L.s[d] - 1 && c3[m] >= 1) {
       const int sm = L.st[m];
-      T ue = bg.V[d] + T(0.5) * (vd[c - sm] + vd[c]);
-      T Fe = T(0.5) * (F[c - sm] + F[c]);
-      T ws = upwind((const T*)S.w[m], c, st, ue, ue * dtdx);
+      C ue = bg.V[d] + C(0.5f) * (ld(vd, c - sm) + ld(vd, c));
+      C Fe = C(0.5f) * (ld(F, c - sm) + ld(F, c));
+      C ws = d == 0 ? upwind((const T*)S.w[m], c, sd, ue, ue * dtdx)
+                    : upwind((const Arith<T>*)S.w[m], c, sd, ue, ue * dtdx);
       P = bg.V[m] * Fe + ws * (F0 + Fe);
     }
-    ((T*)S.P[m])[c] = P;
+    st((Arith<T>*)S.P[m], c, P);
   }
 }
 
 template <class T, int d>
 __device__ __forceinline__ void el_tupdate(const LevelView& L, const Box& b, const Scratch& S,
-                                           const Geo<T>& g, unsigned tid) {
+                                           const Geo<Arith<T>>& g, unsigned tid) {
+  using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const int st = L.st[d];
-  const T iv = g.inv_vol;
+  const int sd = L.st[d];
+  const C iv = g.inv_vol;
   if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
-    T Flo = ((const T*)S.F)[c], Fhi = ((const T*)S.F)[c + st];
-    T Elo = ((const T*)S.E)[c], Ehi = ((const T*)S.E)[c + st];
+    C Flo = ld((const Arith<T>*)S.F, c), Fhi = ld((const Arith<T>*)S.F, c + sd);
+    C Elo = ld((const Arith<T>*)S.E, c), Ehi = ld((const Arith<T>*)S.E, c + sd);
     if (L.has_child && near_frontier(L, d, c3[d])) {
       int slot, f3[3] = {c3[0], c3[1], c3[2]};
       int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
       if (side >= 0) {
-        Flo = (T)L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot];
-        Elo = (T)L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot];
+        Flo = from_double<C>(L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot]);
+        Elo = from_double<C>(L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot]);
       }
       f3[d] += 1;
       side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
       if (side >= 0) {
-        Fhi = (T)L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot];
-        Ehi = (T)L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot];
+        Fhi = from_double<C>(L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot]);
+        Ehi = from_double<C>(L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot]);
       }
     }
     T* rho = (T*)L.q[F_RHO];
     T* e = (T*)L.q[F_E];
-    rho[c] = rho[c] - (Fhi - Flo) * iv;
-    e[c] = e[c] - (Ehi - Elo) * iv;
+    st(rho, c, ld(rho, c) - (Fhi - Flo) * iv);
+    st(e, c, ld(e, c) - (Ehi - Elo) * iv);
   }
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    T* pi = (T*)S.pi[m];
-    const T* P = (const T*)S.P[m];
+    Arith<T>* pi = (Arith<T>*)S.pi[m];
+    const Arith<T>* P = (const Arith<T>*)S.P[m];
     if (m == d) {
-      if (c3[d] >= 3 && c3[d] < L.s[d] - 2) pi[c] = pi[c] - (P[c] - P[c - st]) * iv;
+      if (c3[d] >= 3 && c3[d] < L.s[d] - 2)
+        st(pi, c, ld(pi, c) - (ld(P, c) - ld(P, c - sd)) * iv);
     } else if (c3[d] >= 2 && c3[d] < L.s[d] - 2 && c3[m] >= 1) {
-      pi[c] = pi[c] - (P[c + st] - P[c]) * iv;
+      st(pi, c, ld(pi, c) - (ld(P, c + sd) - ld(P, c)) * iv);
     }
   }
 }
@@ -605,37 +646,43 @@ __device__ __forceinline__ void el_tupdate(const LevelView& L, const Box& b, con
 // arrays to Scratch::qb, the y sweep back.  For a child level the fluxes through
 // its frontier faces also go to Scratch::F/E (frontier capture).
 
-template <class T>
-__device__ __forceinline__ T shfl_up(T v, int k) {
+__device__ __forceinline__ float shfl_up(float v, int k) {
   return __shfl_up_sync(0xffffffffu, v, k);
 }
-template <class T>
-__device__ __forceinline__ T shfl_dn(T v, int k) {
+__device__ __forceinline__ float shfl_dn(float v, int k) {
   return __shfl_down_sync(0xffffffffu, v, k);
+}
+__device__ __forceinline__ df64 shfl_up(df64 v, int k) {
+  return df64(__shfl_up_sync(0xffffffffu, v.hi, k), __shfl_up_sync(0xffffffffu, v.lo, k));
+}
+__device__ __forceinline__ df64 shfl_dn(df64 v, int k) {
+  return df64(__shfl_down_sync(0xffffffffu, v.hi, k), __shfl_down_sync(0xffffffffu, v.lo, k));
 }
 
 // coarse-level frontier substitution of the low/high d-face fluxes of cell (g); the
 // frontier faces lie on two d-planes, tested first
-template <class T>
-__device__ __forceinline__ void frontier_fluxes(const LevelView& L, int d, const int g[3], T& Flo,
-                                                T& Fhi, T& Elo, T& Ehi) {
+template <class C>
+__device__ __forceinline__ void frontier_fluxes(const LevelView& L, int d, const int g[3], C& Flo,
+                                                C& Fhi, C& Elo, C& Ehi) {
   if (!near_frontier(L, d, g[d])) return;
   int slot, f3[3] = {g[0], g[1], g[2]};
   int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
   if (side >= 0) {
-    Flo = (T)L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot];
-    Elo = (T)L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot];
+    Flo = from_double<C>(L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot]);
+    Elo = from_double<C>(L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot]);
   }
   f3[d] += 1;
   side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
   if (side >= 0) {
-    Fhi = (T)L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot];
-    Ehi = (T)L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot];
+    Fhi = from_double<C>(L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot]);
+    Ehi = from_double<C>(L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot]);
   }
 }
 
 template <class T, int d>
-__device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __restrict__ xch) {
+__device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
+                                         Arith<T>* __restrict__ xch) {
+  using C = Arith<T>;
   constexpr int RA = d == 1 ? 2 : 1;  // row axis
   constexpr int MU = d == 0 ? 2 : d;  // marching axis
   constexpr int HX = d == 0 ? 3 : 1;  // halo lanes below the owned x range
@@ -645,7 +692,7 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
   const LevelView& L = it.L;
   const Box& b = it.b;
   const Scratch& S = it.S;
-  const Bg<T>& bg = it.bg;
+  const Bg<C>& bg = it.bg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nsx = (b.hi[0] - b.lo[0] + OWNX - 1) / OWNX;
   const int nsr = (b.hi[RA] - b.lo[RA] + kSweepRows - 1) / kSweepRows;
@@ -668,30 +715,31 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
   const T* __restrict__ vd = (const T*)L.q[F_VX + d];
   T* rhoD = kFromB ? (T*)L.q[F_RHO] : (T*)S.qb[0];
   T* eD = kFromB ? (T*)L.q[F_E] : (T*)S.qb[1];
-  const T* piA[3] = {(const T*)S.pi[0], (const T*)S.pi[1], (const T*)S.pi[2]};
-  const T* piS[3] = {kFromB ? (const T*)S.qb[2] : piA[0], kFromB ? (const T*)S.qb[3] : piA[1],
-                     kFromB ? (const T*)S.qb[4] : piA[2]};
-  T* piD[3] = {kFromB ? (T*)S.pi[0] : (T*)S.qb[2], kFromB ? (T*)S.pi[1] : (T*)S.qb[3],
-               kFromB ? (T*)S.pi[2] : (T*)S.qb[4]};
-  const T dt = ((const T*)it.dt)[0];
-  const T Adt = it.g.area[d] * dt;
-  const T dtdx = dt * it.g.inv_dx[d];
-  const T F0 = bg.rho0 * bg.V[d] * Adt;
-  const T iv = it.g.inv_vol;
+  // the momenta are scratch (arithmetic type), rho and e the state type in both copies
+  const C* piA[3] = {(const C*)S.pi[0], (const C*)S.pi[1], (const C*)S.pi[2]};
+  const C* piS[3] = {kFromB ? (const C*)S.qb[2] : piA[0], kFromB ? (const C*)S.qb[3] : piA[1],
+                     kFromB ? (const C*)S.qb[4] : piA[2]};
+  C* piD[3] = {kFromB ? (C*)S.pi[0] : (C*)S.qb[2], kFromB ? (C*)S.pi[1] : (C*)S.qb[3],
+               kFromB ? (C*)S.pi[2] : (C*)S.qb[4]};
+  const C dt = ((const C*)it.dt)[0];
+  const C Adt = it.g.area[d] * dt;
+  const C dtdx = dt * it.g.inv_dx[d];
+  const C F0 = bg.rho0 * bg.V[d] * Adt;
+  const C iv = it.g.inv_vol;
   const int sd = L.s[d];
 
   // state of plane p at this thread's (x, row); zero outside the array
-  auto load = [&](int p, T& r_, T& e_, T& v_, T (&pi_)[3]) {
-    r_ = e_ = v_ = T(0);
-    pi_[0] = pi_[1] = pi_[2] = T(0);
+  auto load = [&](int p, C& r_, C& e_, C& v_, C (&pi_)[3]) {
+    r_ = e_ = v_ = C(0.f);
+    pi_[0] = pi_[1] = pi_[2] = C(0.f);
     if (pos && (unsigned)p < (unsigned)sMU) {
       const int c = cxr + p * stM;
       const bool own = !kFromB || (xrbox && p >= b.lo[MU] && p < b.hi[MU]);
-      r_ = (own ? rhoS : rhoA)[c];
-      e_ = (own ? eS : eA)[c];
-      v_ = vd[c];
+      r_ = ld(own ? rhoS : rhoA, c);
+      e_ = ld(own ? eS : eA, c);
+      v_ = ld(vd, c);
 #pragma unroll
-      for (int m = 0; m < 3; ++m) pi_[m] = (own ? piS[m] : piA[m])[c];
+      for (int m = 0; m < 3; ++m) pi_[m] = ld(own ? piS[m] : piA[m], c);
     }
   };
   auto gcoord = [&](int p, int (&g)[3]) {
@@ -699,7 +747,7 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
     g[RA] = row;
     g[MU] = p;
   };
-  T nr, ne, nv, np[3];
+  C nr, ne, nv, np[3];
 
   if constexpr (d != 0) {
     // ================================================= march along the sweep axis
@@ -707,8 +755,8 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
     // r-2..r; w planes r-3..r; F, E faces r-2, r-1; P_d planes r-3, r-2; P_x and
     // P_row planes r-2, r-1.  The update is of plane r - 2.
     constexpr int mx = 0, mr = RA;
-    T rw[4] = {}, sw[4] = {}, er[3] = {}, vw[3] = {}, pw[3][3] = {}, ww[3][4] = {};
-    T Fw[2] = {}, Ew[2] = {}, Pd[2] = {}, Pm[2][2] = {};
+    C rw[4] = {}, sw[4] = {}, er[3] = {}, vw[3] = {}, pw[3][3] = {}, ww[3][4] = {};
+    C Fw[2] = {}, Ew[2] = {}, Pd[2] = {}, Pm[2][2] = {};
     const int nit = m1 - m0 + 5;
     load(m0 - 3, nr, ne, nv, np);
     for (int i = 0; i < nit; ++i) {
@@ -725,41 +773,41 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
       if (i + 1 < nit) load(r + 1, nr, ne, nv, np);
       // mass and energy flux of face plane f = r - 1
       const int f = r - 1;
-      T Fv = T(0), Evv = T(0);
+      C Fv = C(0.f), Evv = C(0.f);
       if (pos && f >= 2 && f < sd - 1) {
-        const T du = vw[1];
-        const T u = bg.V[d] + du;
-        const T cour = u * dtdx;
-        const T drs = upwind_v(rw[0], rw[1], rw[2], rw[3], u, cour);
+        const C du = vw[1];
+        const C u = bg.V[d] + du;
+        const C cour = u * dtdx;
+        const C drs = upwind_v(rw[0], rw[1], rw[2], rw[3], u, cour);
         Fv = (bg.rho0 * du + drs * u) * Adt;
-        const T des = upwind_v(sw[0], sw[1], sw[2], sw[3], u, cour);
+        const C des = upwind_v(sw[0], sw[1], sw[2], sw[3], u, cour);
         Evv = bg.eps0 * Fv + des * (F0 + Fv);
       }
       Fw[0] = Fw[1]; Fw[1] = Fv;
       Ew[0] = Ew[1]; Ew[1] = Evv;
       if (L.is_child && owned && f >= m0 && f < m1 && (f == L.G || f == L.G + L.n[d])) {
         // CommFlux record: transverse axes x and the row axis
-        fr_put(L, d, f, x, row, 0, it.sub, (double)Fv);
-        fr_put(L, d, f, x, row, 1, it.sub, (double)Evv);
+        fr_put(L, d, f, x, row, 0, it.sub, as_double(Fv));
+        fr_put(L, d, f, x, row, 1, it.sub, as_double(Evv));
       }
       // rho_r, v_{r-1}, F_{r-1} of the row below (shared) and of x - 1 (shuffle)
-      T* xb = xch + (i & 1) * 3 * NT;
+      C* xb = xch + (i & 1) * 3 * NT;
       xb[tid] = rw[3];
       xb[NT + tid] = vw[1];
       xb[2 * NT + tid] = Fv;
       __syncthreads();
       if (warp == 0) continue;  // the halo row only supplies rho, v_d and F
-      const T r_rb = xb[tid - 32], v_rb = xb[NT + tid - 32], F_rb = xb[2 * NT + tid - 32];
-      const T r_xb = shfl_up(rw[3], 1), v_xb = shfl_up(vw[1], 1), F_xb = shfl_up(Fv, 1);
+      const C r_rb = xb[tid - 32], v_rb = xb[NT + tid - 32], F_rb = xb[2 * NT + tid - 32];
+      const C r_xb = shfl_up(rw[3], 1), v_xb = shfl_up(vw[1], 1), F_xb = shfl_up(Fv, 1);
       // w = (dPi - V drf) / (rho0 + drf) of plane r
       const bool pok = pos && (unsigned)r < (unsigned)sMU;
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        const T rn = m == mx ? r_xb : (m == mr ? r_rb : rw[2]);
+        const C rn = m == mx ? r_xb : (m == mr ? r_rb : rw[2]);
         const bool g1 = m == mx ? x >= 1 : (m == mr ? row >= 1 : r >= 1);
-        T wv = T(0);
+        C wv = C(0.f);
         if (pok && g1) {
-          const T drf = T(0.5) * (rn + rw[3]);
+          const C drf = C(0.5f) * (rn + rw[3]);
           wv = hdiv(pw[m][2] - bg.V[m] * drf, bg.rho0 + drf);
         }
         ww[m][0] = ww[m][1]; ww[m][1] = ww[m][2]; ww[m][2] = ww[m][3]; ww[m][3] = wv;
@@ -769,11 +817,11 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int m = j == 0 ? mx : mr;
-        T P = T(0);
+        C P = C(0.f);
         if (pos && q >= 2 && q < sd - 1 && (j == 0 ? x >= 1 : row >= 1)) {
-          const T ue = bg.V[d] + T(0.5) * ((j == 0 ? v_xb : v_rb) + vw[1]);
-          const T Fe = T(0.5) * ((j == 0 ? F_xb : F_rb) + Fv);
-          const T wsv = upwind_v(ww[m][0], ww[m][1], ww[m][2], ww[m][3], ue, ue * dtdx);
+          const C ue = bg.V[d] + C(0.5f) * ((j == 0 ? v_xb : v_rb) + vw[1]);
+          const C Fe = C(0.5f) * ((j == 0 ? F_xb : F_rb) + Fv);
+          const C wsv = upwind_v(ww[m][0], ww[m][1], ww[m][2], ww[m][3], ue, ue * dtdx);
           P = bg.V[m] * Fe + wsv * (F0 + Fe);
         }
         Pm[j][0] = Pm[j][1];
@@ -782,11 +830,11 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
       // P_d of plane p = r - 2 (cell-centred)
       {
         const int p = r - 2;
-        T P = T(0);
+        C P = C(0.f);
         if (pos && p >= 2 && p < sd - 2) {
-          const T uc = bg.V[d] + T(0.5) * (vw[0] + vw[1]);
-          const T Fc = T(0.5) * (Fw[0] + Fw[1]);
-          const T wsv = upwind_v(ww[d][0], ww[d][1], ww[d][2], ww[d][3], uc, uc * dtdx);
+          const C uc = bg.V[d] + C(0.5f) * (vw[0] + vw[1]);
+          const C Fc = C(0.5f) * (Fw[0] + Fw[1]);
+          const C wsv = upwind_v(ww[d][0], ww[d][1], ww[d][2], ww[d][3], uc, uc * dtdx);
           P = bg.V[d] * Fc + wsv * (F0 + Fc);
         }
         Pd[0] = Pd[1];
@@ -796,9 +844,9 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
       const int u = r - 2;
       if (owned && u >= m0 && u < m1) {
         const int c = cxr + u * stM;
-        T rv = rw[1], evv = er[0];
+        C rv = rw[1], evv = er[0];
         if (u >= 2 && u < sd - 2) {
-          T Flo = Fw[0], Fhi = Fw[1], Elo = Ew[0], Ehi = Ew[1];
+          C Flo = Fw[0], Fhi = Fw[1], Elo = Ew[0], Ehi = Ew[1];
           if (L.has_child) {
             int g[3];
             gcoord(u, g);
@@ -807,11 +855,11 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
           rv = rv - (Fhi - Flo) * iv;
           evv = evv - (Ehi - Elo) * iv;
         }
-        rhoD[c] = rv;
-        eD[c] = evv;
+        st(rhoD, c, rv);
+        st(eD, c, evv);
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          T pv = pw[m][0];
+          C pv = pw[m][0];
           if (m == d) {
             if (u >= 3 && u < sd - 2) pv = pv - (Pd[1] - Pd[0]) * iv;
           } else {
@@ -819,40 +867,40 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
             if (u >= 2 && u < sd - 2 && (j == 0 ? x >= 1 : row >= 1))
               pv = pv - (Pm[j][1] - Pm[j][0]) * iv;
           }
-          piD[m][c] = pv;
+          st(piD[m], c, pv);
         }
       }
     }
   } else {
     // ======================================================== x sweep, march in z
-    T pr_r = T(0), pr_v = T(0), pr_F = T(0);  // plane r - 1 at (x, row)
+    C pr_r = C(0.f), pr_v = C(0.f), pr_F = C(0.f);  // plane r - 1 at (x, row)
     const int nit = m1 - m0 + 1;
     load(m0 - 1, nr, ne, nv, np);
     for (int i = 0; i < nit; ++i) {
       const int r = m0 - 1 + i;
-      const T rc = nr, ec = ne, vc = nv, pi0 = np[0], pi1 = np[1], pi2 = np[2];
+      const C rc = nr, ec = ne, vc = nv, pi0 = np[0], pi1 = np[1], pi2 = np[2];
       if (i + 1 < nit) load(r + 1, nr, ne, nv, np);
-      const T ep = hdiv(ec - bg.eps0 * rc, bg.rho0 + rc);
-      const T r_m2 = shfl_up(rc, 2), r_m1 = shfl_up(rc, 1), r_p1 = shfl_dn(rc, 1);
-      const T e_m2 = shfl_up(ep, 2), e_m1 = shfl_up(ep, 1), e_p1 = shfl_dn(ep, 1);
+      const C ep = hdiv(ec - bg.eps0 * rc, bg.rho0 + rc);
+      const C r_m2 = shfl_up(rc, 2), r_m1 = shfl_up(rc, 1), r_p1 = shfl_dn(rc, 1);
+      const C e_m2 = shfl_up(ep, 2), e_m1 = shfl_up(ep, 1), e_p1 = shfl_dn(ep, 1);
       const bool pok = pos && (unsigned)r < (unsigned)sMU;
       // mass and energy flux at the x-face of this cell
-      T Fv = T(0), Evv = T(0);
+      C Fv = C(0.f), Evv = C(0.f);
       if (pok && x >= 2 && x < sd - 1) {
-        const T u = bg.V[0] + vc;
-        const T cour = u * dtdx;
-        const T drs = upwind_v(r_m2, r_m1, rc, r_p1, u, cour);
+        const C u = bg.V[0] + vc;
+        const C cour = u * dtdx;
+        const C drs = upwind_v(r_m2, r_m1, rc, r_p1, u, cour);
         Fv = (bg.rho0 * vc + drs * u) * Adt;
-        const T des = upwind_v(e_m2, e_m1, ep, e_p1, u, cour);
+        const C des = upwind_v(e_m2, e_m1, ep, e_p1, u, cour);
         Evv = bg.eps0 * Fv + des * (F0 + Fv);
       }
       if (L.is_child && owned && r >= m0 && r < m1 && (x == L.G || x == L.G + L.n[0])) {
         // CommFlux record: transverse axes y (the row) and z (the march)
-        fr_put(L, 0, x, row, r, 0, it.sub, (double)Fv);
-        fr_put(L, 0, x, row, r, 1, it.sub, (double)Evv);
+        fr_put(L, 0, x, row, r, 0, it.sub, as_double(Fv));
+        fr_put(L, 0, x, row, r, 1, it.sub, as_double(Evv));
       }
       // rho, v_x, F of the row below
-      T* xb = xch + (i & 1) * 3 * NT;
+      C* xb = xch + (i & 1) * 3 * NT;
       xb[tid] = rc;
       xb[NT + tid] = vc;
       xb[2 * NT + tid] = Fv;
@@ -860,52 +908,52 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
       // plane m0 - 1 only feeds the z-fluxes of plane m0; the halo row only supplies
       // rho, v_x and F
       if (i > 0 && warp > 0) {
-        const T r_rb = xb[tid - 32], v_rb = xb[NT + tid - 32], F_rb = xb[2 * NT + tid - 32];
+        const C r_rb = xb[tid - 32], v_rb = xb[NT + tid - 32], F_rb = xb[2 * NT + tid - 32];
         // w of this plane: along x (lane below), y (row below), z (previous plane)
-        T wx = T(0), wy = T(0), wz = T(0);
+        C wx = C(0.f), wy = C(0.f), wz = C(0.f);
         if (pok && x >= 1) {
-          const T drf = T(0.5) * (r_m1 + rc);
+          const C drf = C(0.5f) * (r_m1 + rc);
           wx = hdiv(pi0 - bg.V[0] * drf, bg.rho0 + drf);
         }
         if (pok && row >= 1) {
-          const T drf = T(0.5) * (r_rb + rc);
+          const C drf = C(0.5f) * (r_rb + rc);
           wy = hdiv(pi1 - bg.V[1] * drf, bg.rho0 + drf);
         }
         if (pok && r >= 1) {
-          const T drf = T(0.5) * (pr_r + rc);
+          const C drf = C(0.5f) * (pr_r + rc);
           wz = hdiv(pi2 - bg.V[2] * drf, bg.rho0 + drf);
         }
-        const T wx_m1 = shfl_up(wx, 1), wx_p1 = shfl_dn(wx, 1), wx_p2 = shfl_dn(wx, 2);
-        const T wy_m2 = shfl_up(wy, 2), wy_m1 = shfl_up(wy, 1), wy_p1 = shfl_dn(wy, 1);
-        const T wz_m2 = shfl_up(wz, 2), wz_m1 = shfl_up(wz, 1), wz_p1 = shfl_dn(wz, 1);
-        const T v_p1 = shfl_dn(vc, 1), F_p1 = shfl_dn(Fv, 1), E_p1 = shfl_dn(Evv, 1);
+        const C wx_m1 = shfl_up(wx, 1), wx_p1 = shfl_dn(wx, 1), wx_p2 = shfl_dn(wx, 2);
+        const C wy_m2 = shfl_up(wy, 2), wy_m1 = shfl_up(wy, 1), wy_p1 = shfl_dn(wy, 1);
+        const C wz_m2 = shfl_up(wz, 2), wz_m1 = shfl_up(wz, 1), wz_p1 = shfl_dn(wz, 1);
+        const C v_p1 = shfl_dn(vc, 1), F_p1 = shfl_dn(Fv, 1), E_p1 = shfl_dn(Evv, 1);
         // momentum fluxes: P_x cell-centred, P_y and P_z on the x-y and x-z edges
-        T Px = T(0), Py = T(0), Pz = T(0);
+        C Px = C(0.f), Py = C(0.f), Pz = C(0.f);
         if (pok && x >= 2 && x < sd - 2) {
-          const T uc = bg.V[0] + T(0.5) * (vc + v_p1);
-          const T Fc = T(0.5) * (Fv + F_p1);
-          const T wsv = upwind_v(wx_m1, wx, wx_p1, wx_p2, uc, uc * dtdx);
+          const C uc = bg.V[0] + C(0.5f) * (vc + v_p1);
+          const C Fc = C(0.5f) * (Fv + F_p1);
+          const C wsv = upwind_v(wx_m1, wx, wx_p1, wx_p2, uc, uc * dtdx);
           Px = bg.V[0] * Fc + wsv * (F0 + Fc);
         }
         if (pok && x >= 2 && x < sd - 1 && row >= 1) {
-          const T ue = bg.V[0] + T(0.5) * (v_rb + vc);
-          const T Fe = T(0.5) * (F_rb + Fv);
-          const T wsv = upwind_v(wy_m2, wy_m1, wy, wy_p1, ue, ue * dtdx);
+          const C ue = bg.V[0] + C(0.5f) * (v_rb + vc);
+          const C Fe = C(0.5f) * (F_rb + Fv);
+          const C wsv = upwind_v(wy_m2, wy_m1, wy, wy_p1, ue, ue * dtdx);
           Py = bg.V[1] * Fe + wsv * (F0 + Fe);
         }
         if (pok && x >= 2 && x < sd - 1 && r >= 1) {
-          const T ue = bg.V[0] + T(0.5) * (pr_v + vc);
-          const T Fe = T(0.5) * (pr_F + Fv);
-          const T wsv = upwind_v(wz_m2, wz_m1, wz, wz_p1, ue, ue * dtdx);
+          const C ue = bg.V[0] + C(0.5f) * (pr_v + vc);
+          const C Fe = C(0.5f) * (pr_F + Fv);
+          const C wsv = upwind_v(wz_m2, wz_m1, wz, wz_p1, ue, ue * dtdx);
           Pz = bg.V[2] * Fe + wsv * (F0 + Fe);
         }
-        const T Px_m1 = shfl_up(Px, 1), Py_p1 = shfl_dn(Py, 1), Pz_p1 = shfl_dn(Pz, 1);
+        const C Px_m1 = shfl_up(Px, 1), Py_p1 = shfl_dn(Py, 1), Pz_p1 = shfl_dn(Pz, 1);
         // conservative update of this cell
         if (owned && r >= m0 && r < m1) {
           const int c = cxr + r * stM;
-          T rv = rc, evv = ec;
+          C rv = rc, evv = ec;
           if (x >= 2 && x < sd - 2) {
-            T Flo = Fv, Fhi = F_p1, Elo = Evv, Ehi = E_p1;
+            C Flo = Fv, Fhi = F_p1, Elo = Evv, Ehi = E_p1;
             if (L.has_child) {
               int g[3];
               gcoord(r, g);
@@ -914,15 +962,15 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
             rv = rv - (Fhi - Flo) * iv;
             evv = evv - (Ehi - Elo) * iv;
           }
-          rhoD[c] = rv;
-          eD[c] = evv;
-          T p0 = pi0, p1 = pi1, p2 = pi2;
+          st(rhoD, c, rv);
+          st(eD, c, evv);
+          C p0 = pi0, p1 = pi1, p2 = pi2;
           if (x >= 3 && x < sd - 2) p0 = p0 - (Px - Px_m1) * iv;
           if (x >= 2 && x < sd - 2 && row >= 1) p1 = p1 - (Py_p1 - Py) * iv;
           if (x >= 2 && x < sd - 2 && r >= 1) p2 = p2 - (Pz_p1 - Pz) * iv;
-          piD[0][c] = p0;
-          piD[1][c] = p1;
-          piD[2][c] = p2;
+          st(piD[0], c, p0);
+          st(piD[1], c, p1);
+          st(piD[2], c, p2);
         }
       }
       pr_r = rc;
@@ -935,8 +983,10 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit, T* __
 // velocity from the transported momenta, then the second half kick S(dt/2)
 template <class T>
 __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b, const Scratch& S,
-                                                        const T* __restrict__ dtp, T gm1, const Bg<T>& bg,
-                                                        const Geo<T>& g, int fused, unsigned tid) {
+                                               const Arith<T>* __restrict__ dtp, Arith<T> gm1,
+                                               const Bg<Arith<T>>& bg, const Geo<Arith<T>>& g,
+                                               int fused, unsigned tid) {
+  using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   T* rhoA = (T*)L.q[F_RHO];
@@ -946,34 +996,35 @@ __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b,
   const T* rho = fused ? (const T*)S.qb[0] : rhoA;
   const T* e = fused ? (const T*)S.qb[1] : eA;
   const T* __restrict__ phi = (const T*)L.phi;
-  const T h = T(0.5) * dtp[0];
+  const C h = C(0.5f) * dtp[0];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T rc = rho[c], ec = e[c], fc = phi[c];
+  const T rc_s = rho[c], ec_s = e[c];
+  const C rc = ld(rho, c), ec = ld(e, c), fc = ld(phi, c);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (c3[d] < 1) continue;
     int m = c - L.st[d];
     const bool own = !fused || c3[d] - 1 >= b.lo[d];
-    const T rm = own ? rho[m] : rhoA[m];
-    const T em = own ? e[m] : eA[m];
-    T drf = T(0.5) * (rm + rc);
-    T rinv = hdiv(T(1), bg.rho0 + drf);
-    const T* pi = (const T*)(fused ? S.qb[2 + d] : S.pi[d]);
-    T v = (pi[c] - bg.V[d] * drf) * rinv;
-    T acc = (gm1 * (ec - em) * rinv + (fc - phi[m])) * g.inv_dx[d];
-    ((T*)L.q[F_VX + d])[c] = v - h * acc;
+    const C rm = ld(own ? rho : (const T*)rhoA, m);
+    const C em = ld(own ? e : (const T*)eA, m);
+    C drf = C(0.5f) * (rm + rc);
+    C rinv = hdiv(C(1.f), bg.rho0 + drf);
+    const C* pi = (const C*)(fused ? S.qb[2 + d] : S.pi[d]);
+    C v = (ld(pi, c) - bg.V[d] * drf) * rinv;
+    C acc = (gm1 * (ec - em) * rinv + (fc - ld(phi, m))) * g.inv_dx[d];
+    st((T*)L.q[F_VX + d], c, v - h * acc);
   }
   if (fused) {
-    rhoA[c] = rc;
-    eA[c] = ec;
+    rhoA[c] = rc_s;
+    eA[c] = ec_s;
   }
 }
 
 // ------------------------------------------------------ level-0 boundaries
 template <class T>
 __device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_lo, int type_hi,
-                                                    T rho0, T e0, T V0, T V1, T V2, unsigned tid) {
+                                           T V0, T V1, T V2, unsigned tid) {
   const int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
   long long t = tid;
   const int G = L.G, n = L.n[d];
@@ -992,8 +1043,6 @@ __device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_l
   if (type < 0) return;  // this side is left alone (mirror fill of finer levels)
   int normal = (f == F_VX + d);
   int dst = side == 0 ? G - g : G + n - 1 + g, src = -1;
-  (void)rho0;
-  (void)e0;
   T sign = T(1), fixed = T(0), shift = T(0);
   bool use_fixed = false;
   const T Vd = d == 0 ? V0 : (d == 1 ? V1 : V2);
@@ -1401,6 +1450,7 @@ __device__ __forceinline__ void el_dt_finalize(DevScalars* ds, int n_levels, con
     double dl = dt / prod[l];
     ds->dtl[l] = dl;
     ds->dtf[l] = (float)dl;
+    ds->dtd[l] = to_df64(dl);
   }
 }
 
@@ -1683,7 +1733,34 @@ __global__ void __launch_bounds__(kBlock) k_dfma_probe(int iters, double* sink) 
   if (s == -1.0) sink[0] = s;
 }
 
+// double-float arithmetic on the device versus FP64 on n operand pairs: the largest
+// error of conversion, sum, product and quotient, each in units of its bound
+// (2^-46 |a|; 2^-46 (|a| + |b|); 2^-46 |a b| + 2^-120; 2^-42 |a / b| + 2^-120)
+__global__ void k_df64_check(const double* a, const double* b, int n, double* worst) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double w[4] = {0.0, 0.0, 0.0, 0.0};
+  if (t < n) {
+    const df64 x = to_df64(a[t]), y = to_df64(b[t]);
+    const double A = to_double(x), B = to_double(y);
+    w[0] = fabs(A - a[t]) / (0x1.0p-46 * fabs(a[t]) + 1e-300);
+    w[1] = fabs(to_double(x + y) - (A + B)) / (0x1.0p-46 * (fabs(A) + fabs(B)) + 1e-300);
+    w[2] = fabs(to_double(x * y) - A * B) / (0x1.0p-46 * fabs(A * B) + 0x1.0p-120);
+    w[3] = fabs(to_double(x / y) - A / B) / (0x1.0p-42 * fabs(A / B) + 0x1.0p-120);
+  }
+  for (int q = 0; q < 4; ++q) {
+    double u = w[q];
+    for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
+    if ((threadIdx.x & 31) == 0 && u > 0.0)
+      atomicMax((unsigned long long*)&worst[q], (unsigned long long)__double_as_longlong(u));
+  }
+}
+
 }  // namespace
+
+int launch_df64_check(const double* a, const double* b, int n, double* worst, cudaStream_t st) {
+  k_df64_check<<<(n + 255) / 256, 256, 0, st>>>(a, b, n, worst);
+  return 1;
+}
 
 long long launch_dfma_probe(int blocks, int iters, double* sink, cudaStream_t st) {
   k_dfma_probe<<<blocks, kBlock, 0, st>>>(iters, sink);
@@ -1715,40 +1792,39 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
 #pragma unroll
   for (int n = 1; n < NC; ++n) el[n] = el[0] + n * kBlock;
   if (OP == OP_SOURCE)
-    el_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.flags & FL_WRITE_PI, it.gm1, it.bg, it.g,
+    el_source<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.flags & FL_WRITE_PI, it.gm1, it.bg, it.g,
                  tid);
   else if (OP == OP_COMPRESS) {
     if (it.L.has_child)  // before any consumer
 #pragma unroll 1
       for (int n = 0; n < NC; ++n) fr_sums(it.L, it.ds, it.level, el[n]);
-    el_compress_lum<T, NC>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.lum,
+    el_compress_lum<T, NC>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.gm1, it.lum,
                            it.flags & FL_SS3, it.flags & FL_LUM, it.flags & FL_EPS, it.bg, it.g,
                            el);
   }
   else if (OP == OP_FRONTIER_DIFF)
-    el_frontier_diff<T>(it.L, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
+    el_frontier_diff<T>(it.L, it.S, (const Arith<T>*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
                         it.sub, tid);
   else if (OP == OP_DIFFUSE)
-    el_diffuse<T, NC>(it.L, it.b, it.S, (const T*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR,
+    el_diffuse<T, NC>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR,
                       it.g, el);
   else if (OP == OP_TPREP)
     el_tprep<T>(it.L, it.b, it.S, it.bg, it.flags & FL_EPS_ONLY, tid);
   else if (OP == OP_TFLUX)
-    el_tflux<T, D>(it.L, it.b, it.S, (const T*)it.dt, it.bg, it.g, it.sub, tid);
+    el_tflux<T, D>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.bg, it.g, it.sub, tid);
   else if (OP == OP_TMOM)
-    el_tmom<T, D>(it.L, it.b, it.S, (const T*)it.dt, it.bg, it.g, tid);
+    el_tmom<T, D>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.bg, it.g, tid);
   else if (OP == OP_TUPDATE)
     el_tupdate<T, D>(it.L, it.b, it.S, it.g, tid);
   else if (OP == OP_VISC_Q)
-    el_visc_q<T>(it.L, it.b, it.S, (const T*)it.dt, it.av, it.bg, it.g, tid);
+    el_visc_q<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.av, it.bg, it.g, tid);
   else if (OP == OP_VISC_V)
-    el_visc_v<T>(it.L, it.b, it.S, (const T*)it.dt, it.flags & FL_WRITE_PI, it.bg, it.g, tid);
+    el_visc_v<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.flags & FL_WRITE_PI, it.bg, it.g, tid);
   else if (OP == OP_VREC)
-    el_vrec_source<T>(it.L, it.b, it.S, (const T*)it.dt, it.gm1, it.bg, it.g,
+    el_vrec_source<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.gm1, it.bg, it.g,
                       it.flags & FL_FUSED, tid);
   else if (OP == OP_BC)
-    el_bc_axis<T>(it.L, D, it.bc_lo, it.bc_hi, it.bg.rho0, it.bg.e0, it.bg.V[0], it.bg.V[1],
-                  it.bg.V[2], tid);
+    el_bc_axis<T>(it.L, D, it.bc_lo, it.bc_hi, (T)it.V[0], (T)it.V[1], (T)it.V[2], tid);
   else if (OP == OP_COMMUP)
     el_commup<T>(it.L, it.F, tid);
   else if (OP == OP_COMMMEAN)
@@ -1828,7 +1904,7 @@ __global__ void __launch_bounds__(kBlock) k_single(const Item<T> it) {
 // item as k_batch does.
 template <class T, int D>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_single(const Item<T> it) {
-  __shared__ __align__(16) T s_x[2 * 3 * kSweepThreads];
+  __shared__ __align__(16) Arith<T> s_x[2 * 3 * kSweepThreads];
   pdl_enter();
   if (skipped(it)) return;
   el_sweep<T, D>(it, blockIdx.x, s_x);
@@ -1839,7 +1915,7 @@ template <class T, int D>
 __global__ void __launch_bounds__(kSweepThreads) k_sweep_batch(const Item<T>* __restrict__ items,
                                                               const unsigned* __restrict__ starts,
                                                               int nitems, unsigned nchunks) {
-  __shared__ __align__(16) T s_x[2 * 3 * kSweepThreads];
+  __shared__ __align__(16) Arith<T> s_x[2 * 3 * kSweepThreads];
   __shared__ __align__(16) unsigned char s_raw[sizeof(Item<T>)];
   const Item<T>& it = *reinterpret_cast<const Item<T>*>(s_raw);
   pdl_enter();

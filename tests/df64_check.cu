@@ -1,0 +1,101 @@
+// Host-side check of the double-float arithmetic (df64.h) against FP64: for operands
+// spread over 40 decades and both signs, each operation's result, converted back to
+// double, lies within its stated bound of the FP64 result of the same (exactly
+// represented) operands:
+//   conversion   |x - to_double(to_df64(x))| <= 2^-46 |x|
+//   a + b, a - b <= 2^-46 (|a| + |b|)
+//   a * b        <= 2^-46 |a b| + 2^-120
+//   a / b        <= 2^-42 |a / b| + 2^-120  (the device's reciprocal estimate is
+//                                    checked on the GPU; here it is IEEE division)
+// The absolute floor 2^-120: below about 2^-102 the low float of a result leaves the
+// normal range of float, so its relative precision falls (on the device, where
+// subnormals flush to zero, the loss is below 2^-126 absolutely); the stencils' fields
+// are compared with an absolute tolerance far above it.
+// Prints "OK <checks>" and exits 0, or the first failure and exits 1.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+
+#include "df64.h"
+
+using namespace dfn;
+
+static uint64_t rng = 0x2545f4914f6cdd1dull;
+static double uniform() {  // xorshift64*, [0, 1)
+  rng ^= rng >> 12;
+  rng ^= rng << 25;
+  rng ^= rng >> 27;
+  return (double)((rng * 0x2545f4914f6cdd1dull) >> 11) * 0x1.0p-53;
+}
+static double operand() {
+  const double mag = std::pow(10.0, -20.0 + 22.0 * uniform());
+  return (uniform() < 0.5 ? -1.0 : 1.0) * mag * (1.0 + uniform());
+}
+
+int main() {
+  long long n = 0;
+  for (int k = 0; k < 2000000; ++k) {
+    const double x = operand(), y = operand();
+    const df64 a = to_df64(x), b = to_df64(y);
+    const double A = to_double(a), B = to_double(b);
+    ++n;
+    if (std::fabs(A - x) > 0x1.0p-46 * std::fabs(x)) {
+      std::printf("FAIL conversion %.17g -> %.17g\n", x, A);
+      return 1;
+    }
+    const double s = to_double(a + b), d = to_double(a - b);
+    const double m = to_double(a * b), q = to_double(a / b);
+    const double sb = 0x1.0p-46 * (std::fabs(A) + std::fabs(B));
+    if (std::fabs(s - (A + B)) > sb || std::fabs(d - (A - B)) > sb) {
+      std::printf("FAIL add %.17g %.17g: %.17g %.17g\n", A, B, s, d);
+      return 1;
+    }
+    if (std::fabs(m - A * B) > 0x1.0p-46 * std::fabs(A * B) + 0x1.0p-120) {
+      std::printf("FAIL mul %.17g %.17g: %.17g\n", A, B, m);
+      return 1;
+    }
+    if (std::fabs(q - A / B) > 0x1.0p-42 * std::fabs(A / B) + 0x1.0p-120) {
+      std::printf("FAIL div %.17g %.17g: %.17g\n", A, B, q);
+      return 1;
+    }
+    // sign tests follow the value's sign
+    if (gt0(a) != (A > 0) || lt0(a) != (A < 0)) {
+      std::printf("FAIL sign %.17g\n", A);
+      return 1;
+    }
+  }
+  // the conversions against the compiler's: to_double of a normalised pair is the
+  // correctly rounded sum to within one unit in the last place, and a float converts
+  // exactly both ways
+  for (int k = 0; k < 2000000; ++k) {
+    const double x = operand();
+    const float h = (float)x, l = (float)(x - (double)h);
+    const double ref = (double)h + (double)l;
+    const double got = to_double(df64(h, l));
+    if (std::fabs(got - ref) > 0x1.0p-52 * std::fabs(ref)) {
+      std::printf("FAIL to_double %.17g %.9g %.9g: %.17g\n", ref, h, l, got);
+      return 1;
+    }
+    const df64 f = to_df64((double)h);
+    if (f.hi != h || f.lo != 0.f || to_double(df64(h)) != (double)h) {
+      std::printf("FAIL float round trip %.9g\n", h);
+      return 1;
+    }
+    ++n;
+  }
+  // signed zeros, infinities and NaN survive both conversions
+  if (to_double(to_df64(-0.0)) != 0.0 || !std::signbit(to_double(to_df64(-0.0))) ||
+      !std::isinf(to_double(to_df64(1e300))) || !std::isnan(to_double(to_df64(NAN)))) {
+    std::printf("FAIL special values\n");
+    return 1;
+  }
+  // exact cases: zero stays zero, x - x = 0, 1 * x = x
+  const df64 z = df64(0.f);
+  if (to_double(z + z) != 0.0 || to_double(to_df64(0.3) - to_df64(0.3)) != 0.0 ||
+      to_double(df64(1.f) * to_df64(0.3)) != to_double(to_df64(0.3))) {
+    std::printf("FAIL exact cases\n");
+    return 1;
+  }
+  std::printf("OK %lld\n", n);
+  return 0;
+}
