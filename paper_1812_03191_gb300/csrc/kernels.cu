@@ -97,10 +97,13 @@ __device__ __forceinline__ df64 from_double<df64>(double x) {
   return to_df64(x);
 }
 
-// sign tests of the arithmetic types (double-float: df64.h)
+// sign tests of the arithmetic types (double-float: df64.h).  For FP64 (CommUp's
+// limiter) on the integer pipe: the bit pattern of a non-NaN double, read as a signed
+// integer, has the sign of the value, with +0 -> 0 and -0 -> negative.
 __device__ __forceinline__ bool gt0(float v) { return v > 0.f; }
 __device__ __forceinline__ bool le0(float v) { return v <= 0.f; }
 __device__ __forceinline__ bool lt0(float v) { return v < 0.f; }
+__device__ __forceinline__ bool le0(double v) { return __double_as_longlong(v) <= 0; }
 
 // Half the van Leer (1977) harmonic limited slope (Sec. 3.2.1 cites it for the
 // interpolation): dl dr / (dl + dr) where dl dr > 0, else 0.  Callers fold the
