@@ -95,6 +95,11 @@ __host__ __device__ __forceinline__ df64 operator/(df64 a, df64 b) {
   return fast_two_sum(q1, rem.hi * r);
 }
 
+// a times a power of two (exact, both parts scaled; no overflow or underflow)
+__host__ __device__ __forceinline__ df64 scale(df64 a, float p2) {
+  return df64(a.hi * p2, a.lo * p2);
+}
+
 __host__ __device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
 __host__ __device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
 
@@ -148,31 +153,28 @@ __host__ __device__ __forceinline__ double u2d(unsigned long long u) {
 #endif
 }
 
-// x = hi + lo: x cut to 24 significant bits plus the remainder (its low 29 bits,
-// rounded to float), then normalised; error at most about 2^-47 |x|.
+// x = hi + lo: x cut to 24 significant bits (the double's bit pattern shifted and its
+// exponent re-biased) plus the next 23 bits of the remainder as a float (the 2^23
+// magic-number conversion, scaled by a power of two built with the remainder's sign),
+// then normalised; error below 2^-45 |x|.  |x| below 2^-80 keeps hi alone; |x| below
+// 2^-126 becomes 0.
 __host__ __device__ __forceinline__ df64 to_df64(double x) {
   const unsigned long long b = d2u(x);
   const unsigned bh = (unsigned)(b >> 32), bl = (unsigned)b;
   const unsigned sign = bh & 0x80000000u;
-  const int e = (int)((bh >> 20) & 0x7FFu);  // biased exponent of x
-  const int fe = e - 896;                     // biased float exponent of hi
-  if (fe <= 0) return df64(u2f(sign), 0.f);  // |x| < 2^-126 (and zero)
-  const unsigned top23 = ((bh & 0xFFFFFu) << 3) | (bl >> 29);
-  if (fe >= 255) {  // beyond float range: infinity, or NaN for a NaN
-    const bool nan = e == 0x7FF && (((bh & 0xFFFFFu) | bl) != 0u);
+  const unsigned e = (bh >> 20) & 0x7FFu;  // biased exponent of x
+  if (e - 897u >= 254u) {                   // outside float's normal range
+    if (e < 897u) return df64(u2f(sign), 0.f);
+    const bool nan = e == 0x7FFu && (((bh & 0xFFFFFu) | bl) != 0u);
     return df64(u2f(nan ? 0x7FC00000u : (sign | 0x7F800000u)), 0.f);
   }
-  const float hi = u2f(sign | ((unsigned)fe << 23) | top23);
-  // remainder r = (bl & (2^29 - 1)) 2^(e - 1075): its top 23 bits as an exact float
-  // (the 2^23 magic-number conversion), then the low 6, then the power of two
-  const unsigned r = bl & 0x1FFFFFFFu;
-  const int le = e - 1069 + 127;  // float exponent field of 2^(e - 1075 + 6)
-  if (r == 0u || le <= 0) return df64(hi, 0.f);
-  const float rh = u2f(0x4B000000u | (r >> 6)) - 8388608.0f;         // r >> 6, exact
-  const float rl = u2f(0x4B000000u | (r & 63u)) - 8388608.0f;        // r & 63, exact
-  const float rf = fmaf(rh, 64.0f, rl);                               // r, rounded
-  const float lo = rf * u2f((unsigned)le << 23) * 0.015625f;          // r 2^(e - 1075)
-  return fast_two_sum(hi, sign ? -lo : lo);  // normalised: |lo| <= ulp(hi) / 2
+  // sign | exponent | top 23 fraction bits, exponent re-biased from 1023 to 127
+  const unsigned hb = (unsigned)(((b >> 29) & 0x3FFFFFFFFull) - (896ull << 23));
+  const float hi = u2f(sign | hb);
+  // the remainder's next 23 bits, times 2^(e - 1069) carrying x's sign
+  const float r = u2f(0x4B000000u | ((bl >> 6) & 0x7FFFFFu)) - 8388608.0f;
+  const float p2 = e >= 943u ? u2f(sign | ((e - 942u) << 23)) : 0.f;
+  return fast_two_sum(hi, r * p2);
 }
 
 // hi + lo rounded to double: hi's significand and lo's, aligned in a 64-bit integer

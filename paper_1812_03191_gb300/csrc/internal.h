@@ -24,8 +24,8 @@ struct LevelView {
   double dt_scale;    // dt of this level = coarse dt * dt_scale
   int off[3];         // lower corner of the active box in the parent's active cells
   void* q[5];         // rho, e, vx, vy, vz
-  void* phi;          // potential at cell centres (Eq. 16)
-  void* lumw;         // luminosity weight / cell volume on active cells
+  void* phi;          // potential at cell centres (Eq. 16), in the arithmetic type
+  void* lumw;         // luminosity weight / cell volume on active cells, likewise
   double* fw;         // static force weights GM V_c / (r^2 + eps^2)^(3/2), active cells
   double* acc;        // frontier fluxes of this level as a child (CommFlux record, see
                       // rec_index): mass, transported energy, diffused energy; followed

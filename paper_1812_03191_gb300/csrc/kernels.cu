@@ -86,6 +86,11 @@ __device__ __forceinline__ df64 ld(const df64* __restrict__ p, int i) { return p
 __device__ __forceinline__ void st(df64* p, int i, df64 v) { p[i] = v; }
 __device__ __forceinline__ void st(float* p, int i, float v) { p[i] = v; }
 __device__ __forceinline__ void st(double* p, int i, df64 v) { p[i] = to_double(v); }
+// exact scalings by 1/2 and 2
+__device__ __forceinline__ float halve(float v) { return 0.5f * v; }
+__device__ __forceinline__ df64 halve(df64 v) { return scale(v, 0.5f); }
+__device__ __forceinline__ float twice(float v) { return 2.f * v; }
+__device__ __forceinline__ df64 twice(df64 v) { return scale(v, 2.f); }
 __device__ __forceinline__ double as_double(float v) { return (double)v; }
 __device__ __forceinline__ double as_double(df64 v) { return to_double(v); }
 template <class C>
@@ -188,8 +193,8 @@ __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, cons
   if (!decode(b, tid, i, j, k)) return;
   const T* __restrict__ rho = (const T*)L.q[F_RHO];
   const T* __restrict__ e = (const T*)L.q[F_E];
-  const T* __restrict__ phi = (const T*)L.phi;
-  const C h = C(0.5f) * dtp[0];
+  const Arith<T>* __restrict__ phi = (const Arith<T>*)L.phi;
+  const C h = halve(dtp[0]);
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const C rc = ld(rho, c), ec = ld(e, c), fc = ld(phi, c);
@@ -198,7 +203,7 @@ __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, cons
     T* v = (T*)L.q[F_VX + d];
     if (c3[d] >= 1) {
       int m = c - L.st[d];
-      C drf = C(0.5f) * (ld(rho, m) + rc);
+      C drf = halve(ld(rho, m) + rc);
       C rf = bg.rho0 + drf;
       C acc = (hdiv(gm1 * (ec - ld(e, m)), rf) + (fc - ld(phi, m))) * g.inv_dx[d];
       C vn = ld(v, c) - h * acc;
@@ -264,7 +269,7 @@ __device__ __forceinline__ void el_visc_v(const LevelView& L, const Box& b, cons
     const int m = c - L.st[d];
     const Arith<T>* q = (const Arith<T>*)S.P[d];
     T* v = (T*)L.q[F_VX + d];
-    const C drf = C(0.5f) * (ld(rho, m) + ld(rho, c));
+    const C drf = halve(ld(rho, m) + ld(rho, c));
     const C vn = ld(v, c) - dt * hdiv(ld(q, c) - ld(q, m), bg.rho0 + drf) * g.inv_dx[d];
     st(v, c, vn);
     if (write_pi) st((Arith<T>*)S.pi[d], c, bg.rho0 * vn + drf * (bg.V[d] + vn));
@@ -317,7 +322,7 @@ __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b
       z0[n] = ld(vz, c[n]);
       z1[n] = ld(vz, c[n] + L.st[2]);
     }
-    if (lm[n]) lw[n] = ld((const T*)L.lumw, c[n]);
+    if (lm[n]) lw[n] = ld((const Arith<T>*)L.lumw, c[n]);
     if (do_eps) dr[n] = ld((const T*)L.q[F_RHO], c[n]);
   }
   const C dt = dtp[0];
@@ -328,9 +333,9 @@ __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b
     if (ss3[n]) {
       C div = (x1[n] - x0[n]) * g.inv_dx[0] + (y1[n] - y0[n]) * g.inv_dx[1] +
               (z1[n] - z0[n]) * g.inv_dx[2];
-      C a = C(0.5f) * dt * gm1 * div;
+      C a = halve(dt * gm1 * div);
       // (e0 + de)(1 - a)/(1 + a) - e0
-      ecn = hdiv(ecn * (C(1.f) - a) - C(2.f) * a * bg.e0, C(1.f) + a);
+      ecn = hdiv(ecn * (C(1.f) - a) - twice(a * bg.e0), C(1.f) + a);
     }
     if (lm[n]) ecn = ecn + lum * dt * lw[n];
     st(e, c[n], ecn);
@@ -389,7 +394,7 @@ __device__ __forceinline__ Arith<T> diff_flux(const LevelView& L, const Geo<Arit
                                               Arith<T> chi, Arith<T> dt, Arith<T> rho0, int dfr) {
   using C = Arith<T>;
   int m = f - L.st[d];
-  C rf = dfr ? rho0 : rho0 + C(0.5f) * (ld(rho, m) + ld(rho, f));
+  C rf = dfr ? rho0 : rho0 + halve(ld(rho, m) + ld(rho, f));
   return -chi * rf * (ld(eps, f) - ld(eps, m)) * g.dcoef[d] * dt;
 }
 
@@ -503,7 +508,7 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
     C wv = C(0.f);
     if (c3[m] >= 1) {
       // Pi/rho_face - V = (dPi - V drf)/(rho0 + drf)
-      C drf = C(0.5f) * (ld(rho, c - L.st[m]) + rc);
+      C drf = halve(ld(rho, c - L.st[m]) + rc);
       wv = hdiv(ld((const Arith<T>*)S.pi[m], c) - bg.V[m] * drf, bg.rho0 + drf);
     }
     st((Arith<T>*)S.w[m], c, wv);
@@ -568,16 +573,16 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
     C P = C(0.f);
     if (m == d) {
       if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
-        C uc = bg.V[d] + C(0.5f) * (ld(vd, c) + ld(vd, c + sd));
-        C Fc = C(0.5f) * (ld(F, c) + ld(F, c + sd));
+        C uc = bg.V[d] + halve(ld(vd, c) + ld(vd, c + sd));
+        C Fc = halve(ld(F, c) + ld(F, c + sd));
         C ws = d == 0 ? upwind((const T*)S.w[m], c + sd, sd, uc, uc * dtdx)
                       : upwind((const Arith<T>*)S.w[m], c + sd, sd, uc, uc * dtdx);
         P = bg.V[m] * Fc + ws * (F0 + Fc);
       }
     } else if (c3[d] >= 2 && c3[d] < L.s[d] - 1 && c3[m] >= 1) {
       const int sm = L.st[m];
-      C ue = bg.V[d] + C(0.5f) * (ld(vd, c - sm) + ld(vd, c));
-      C Fe = C(0.5f) * (ld(F, c - sm) + ld(F, c));
+      C ue = bg.V[d] + halve(ld(vd, c - sm) + ld(vd, c));
+      C Fe = halve(ld(F, c - sm) + ld(F, c));
       C ws = d == 0 ? upwind((const T*)S.w[m], c, sd, ue, ue * dtdx)
                     : upwind((const Arith<T>*)S.w[m], c, sd, ue, ue * dtdx);
       P = bg.V[m] * Fe + ws * (F0 + Fe);
@@ -810,7 +815,7 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
         const bool g1 = m == mx ? x >= 1 : (m == mr ? row >= 1 : r >= 1);
         C wv = C(0.f);
         if (pok && g1) {
-          const C drf = C(0.5f) * (rn + rw[3]);
+          const C drf = halve(rn + rw[3]);
           wv = hdiv(pw[m][2] - bg.V[m] * drf, bg.rho0 + drf);
         }
         ww[m][0] = ww[m][1]; ww[m][1] = ww[m][2]; ww[m][2] = ww[m][3]; ww[m][3] = wv;
@@ -822,8 +827,8 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
         const int m = j == 0 ? mx : mr;
         C P = C(0.f);
         if (pos && q >= 2 && q < sd - 1 && (j == 0 ? x >= 1 : row >= 1)) {
-          const C ue = bg.V[d] + C(0.5f) * ((j == 0 ? v_xb : v_rb) + vw[1]);
-          const C Fe = C(0.5f) * ((j == 0 ? F_xb : F_rb) + Fv);
+          const C ue = bg.V[d] + halve((j == 0 ? v_xb : v_rb) + vw[1]);
+          const C Fe = halve((j == 0 ? F_xb : F_rb) + Fv);
           const C wsv = upwind_v(ww[m][0], ww[m][1], ww[m][2], ww[m][3], ue, ue * dtdx);
           P = bg.V[m] * Fe + wsv * (F0 + Fe);
         }
@@ -835,8 +840,8 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
         const int p = r - 2;
         C P = C(0.f);
         if (pos && p >= 2 && p < sd - 2) {
-          const C uc = bg.V[d] + C(0.5f) * (vw[0] + vw[1]);
-          const C Fc = C(0.5f) * (Fw[0] + Fw[1]);
+          const C uc = bg.V[d] + halve(vw[0] + vw[1]);
+          const C Fc = halve(Fw[0] + Fw[1]);
           const C wsv = upwind_v(ww[d][0], ww[d][1], ww[d][2], ww[d][3], uc, uc * dtdx);
           P = bg.V[d] * Fc + wsv * (F0 + Fc);
         }
@@ -915,15 +920,15 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
         // w of this plane: along x (lane below), y (row below), z (previous plane)
         C wx = C(0.f), wy = C(0.f), wz = C(0.f);
         if (pok && x >= 1) {
-          const C drf = C(0.5f) * (r_m1 + rc);
+          const C drf = halve(r_m1 + rc);
           wx = hdiv(pi0 - bg.V[0] * drf, bg.rho0 + drf);
         }
         if (pok && row >= 1) {
-          const C drf = C(0.5f) * (r_rb + rc);
+          const C drf = halve(r_rb + rc);
           wy = hdiv(pi1 - bg.V[1] * drf, bg.rho0 + drf);
         }
         if (pok && r >= 1) {
-          const C drf = C(0.5f) * (pr_r + rc);
+          const C drf = halve(pr_r + rc);
           wz = hdiv(pi2 - bg.V[2] * drf, bg.rho0 + drf);
         }
         const C wx_m1 = shfl_up(wx, 1), wx_p1 = shfl_dn(wx, 1), wx_p2 = shfl_dn(wx, 2);
@@ -933,20 +938,20 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
         // momentum fluxes: P_x cell-centred, P_y and P_z on the x-y and x-z edges
         C Px = C(0.f), Py = C(0.f), Pz = C(0.f);
         if (pok && x >= 2 && x < sd - 2) {
-          const C uc = bg.V[0] + C(0.5f) * (vc + v_p1);
-          const C Fc = C(0.5f) * (Fv + F_p1);
+          const C uc = bg.V[0] + halve(vc + v_p1);
+          const C Fc = halve(Fv + F_p1);
           const C wsv = upwind_v(wx_m1, wx, wx_p1, wx_p2, uc, uc * dtdx);
           Px = bg.V[0] * Fc + wsv * (F0 + Fc);
         }
         if (pok && x >= 2 && x < sd - 1 && row >= 1) {
-          const C ue = bg.V[0] + C(0.5f) * (v_rb + vc);
-          const C Fe = C(0.5f) * (F_rb + Fv);
+          const C ue = bg.V[0] + halve(v_rb + vc);
+          const C Fe = halve(F_rb + Fv);
           const C wsv = upwind_v(wy_m2, wy_m1, wy, wy_p1, ue, ue * dtdx);
           Py = bg.V[1] * Fe + wsv * (F0 + Fe);
         }
         if (pok && x >= 2 && x < sd - 1 && r >= 1) {
-          const C ue = bg.V[0] + C(0.5f) * (pr_v + vc);
-          const C Fe = C(0.5f) * (pr_F + Fv);
+          const C ue = bg.V[0] + halve(pr_v + vc);
+          const C Fe = halve(pr_F + Fv);
           const C wsv = upwind_v(wz_m2, wz_m1, wz, wz_p1, ue, ue * dtdx);
           Pz = bg.V[2] * Fe + wsv * (F0 + Fe);
         }
@@ -998,8 +1003,8 @@ __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b,
   // the level's arrays, which this op then updates for the box
   const T* rho = fused ? (const T*)S.qb[0] : rhoA;
   const T* e = fused ? (const T*)S.qb[1] : eA;
-  const T* __restrict__ phi = (const T*)L.phi;
-  const C h = C(0.5f) * dtp[0];
+  const Arith<T>* __restrict__ phi = (const Arith<T>*)L.phi;
+  const C h = halve(dtp[0]);
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const T rc_s = rho[c], ec_s = e[c];
@@ -1011,7 +1016,7 @@ __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b,
     const bool own = !fused || c3[d] - 1 >= b.lo[d];
     const C rm = ld(own ? rho : (const T*)rhoA, m);
     const C em = ld(own ? e : (const T*)eA, m);
-    C drf = C(0.5f) * (rm + rc);
+    C drf = halve(rm + rc);
     C rinv = hdiv(C(1.f), bg.rho0 + drf);
     const C* pi = (const C*)(fused ? S.qb[2 + d] : S.pi[d]);
     C v = (ld(pi, c) - bg.V[d] * drf) * rinv;
@@ -1604,7 +1609,9 @@ __global__ void __launch_bounds__(kBlock) k_static(LevelView L, double GM, doubl
   double x = L.lo[0] + (i - L.G + 0.5) * L.dx[0];
   double y = L.lo[1] + (j - L.G + 0.5) * L.dx[1];
   double z = L.lo[2] + (k - L.G + 0.5) * L.dx[2];
-  ((T*)L.phi)[c] = (T)(-GM / sqrt(x * x + y * y + z * z + eps * eps));
+  // the static fields are held in the stencils' arithmetic type (double-float for the
+  // FP64 state): only the stencils read them
+  ((Arith<T>*)L.phi)[c] = from_double<Arith<T>>(-GM / sqrt(x * x + y * y + z * z + eps * eps));
   bool act = i >= (L.mir & 1 ? 0 : L.G) && i < L.G + L.n[0] &&
              j >= (L.mir & 2 ? 0 : L.G) && j < L.G + L.n[1] &&
              k >= (L.mir & 4 ? 0 : L.G) && k < L.G + L.n[2];
@@ -1619,7 +1626,7 @@ __global__ void __launch_bounds__(kBlock) k_static(LevelView L, double GM, doubl
         lw = 1.0 / (8.0 * L.vol);
     }
   }
-  ((T*)L.lumw)[c] = (T)lw;
+  ((Arith<T>*)L.lumw)[c] = from_double<Arith<T>>(lw);
 }
 
 // Gaussian weights: fixed-order sum over the active cells (block tree, then one
@@ -1633,7 +1640,7 @@ __global__ void __launch_bounds__(kBlock) k_lum_partials(LevelView L, double* pa
   if (t < na) {
     int i = (int)(t % L.n[0]), j = (int)((t / L.n[0]) % L.n[1]),
         k = (int)(t / ((long long)L.n[0] * L.n[1]));
-    w = (double)((const T*)L.lumw)[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G];
+    w = as_double(((const Arith<T>*)L.lumw)[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G]);
   }
   sm[threadIdx.x] = w;
   __syncthreads();
@@ -1662,9 +1669,9 @@ __global__ void __launch_bounds__(kBlock) k_normalise_lum(LevelView L, const dou
                                                           double mult) {
   long long c = blockIdx.x * (long long)kBlock + threadIdx.x;
   if (c >= L.nc) return;
-  T* lw = (T*)L.lumw;
+  Arith<T>* lw = (Arith<T>*)L.lumw;
   // the unfolded domain holds mult copies of the active cells
-  lw[c] = (T)((double)lw[c] / (mult * wsum[0] * L.vol));
+  lw[c] = from_double<Arith<T>>(as_double(lw[c]) / (mult * wsum[0] * L.vol));
 }
 
 // host I/O: full values = background + stored deviation (bgv = 0 for raw state)
@@ -1738,14 +1745,14 @@ __global__ void __launch_bounds__(kBlock) k_dfma_probe(int iters, double* sink) 
 
 // double-float arithmetic on the device versus FP64 on n operand pairs: the largest
 // error of conversion, sum, product and quotient, each in units of its bound
-// (2^-46 |a|; 2^-46 (|a| + |b|); 2^-46 |a b| + 2^-120; 2^-42 |a / b| + 2^-120)
+// (2^-45 |a|; 2^-46 (|a| + |b|); 2^-46 |a b| + 2^-120; 2^-42 |a / b| + 2^-120)
 __global__ void k_df64_check(const double* a, const double* b, int n, double* worst) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   double w[4] = {0.0, 0.0, 0.0, 0.0};
   if (t < n) {
     const df64 x = to_df64(a[t]), y = to_df64(b[t]);
     const double A = to_double(x), B = to_double(y);
-    w[0] = fabs(A - a[t]) / (0x1.0p-46 * fabs(a[t]) + 1e-300);
+    w[0] = fabs(A - a[t]) / (0x1.0p-45 * fabs(a[t]) + 1e-300);
     w[1] = fabs(to_double(x + y) - (A + B)) / (0x1.0p-46 * (fabs(A) + fabs(B)) + 1e-300);
     w[2] = fabs(to_double(x * y) - A * B) / (0x1.0p-46 * fabs(A * B) + 0x1.0p-120);
     w[3] = fabs(to_double(x / y) - A / B) / (0x1.0p-42 * fabs(A / B) + 0x1.0p-120);

@@ -2,7 +2,7 @@
 // spread over 40 decades and both signs, each operation's result, converted back to
 // double, lies within its stated bound of the FP64 result of the same (exactly
 // represented) operands:
-//   conversion   |x - to_double(to_df64(x))| <= 2^-46 |x|
+//   conversion   |x - to_double(to_df64(x))| <= 2^-45 |x|
 //   a + b, a - b <= 2^-46 (|a| + |b|)
 //   a * b        <= 2^-46 |a b| + 2^-120
 //   a / b        <= 2^-42 |a / b| + 2^-120  (the device's reciprocal estimate is
@@ -39,7 +39,7 @@ int main() {
     const df64 a = to_df64(x), b = to_df64(y);
     const double A = to_double(a), B = to_double(b);
     ++n;
-    if (std::fabs(A - x) > 0x1.0p-46 * std::fabs(x)) {
+    if (std::fabs(A - x) > 0x1.0p-45 * std::fabs(x)) {
       std::printf("FAIL conversion %.17g -> %.17g\n", x, A);
       return 1;
     }
