@@ -18,6 +18,7 @@
 
 #include <math.h>
 
+#include <type_traits>
 #include <utility>
 
 namespace dfn {
@@ -766,8 +767,26 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
     C rw[4] = {}, sw[4] = {}, er[3] = {}, vw[3] = {}, pw[3][3] = {}, ww[3][4] = {};
     C Fw[2] = {}, Ew[2] = {}, Pd[2] = {}, Pm[2][2] = {};
     const int nit = m1 - m0 + 5;
-    load(m0 - 3, nr, ne, nv, np);
-    for (int i = 0; i < nit; ++i) {
+    // Planes far from the array's ends, from the chunk's ends and from a child's
+    // frontier planes pass every test on the plane index; their iterations run a
+    // copy of the body without those tests (FAST), the others the full one.
+    const int r_lo = max(5, m0 + 2), r_hi = min(m1, b.hi[MU] - 2);
+    // state of plane p (inside the box and the array) at this thread's (x, row)
+    auto load_in = [&](int p, C& r_, C& e_, C& v_, C (&pi_)[3]) {
+      r_ = e_ = v_ = C(0.f);
+      pi_[0] = pi_[1] = pi_[2] = C(0.f);
+      if (pos) {
+        const int c = cxr + p * stM;
+        const bool own = !kFromB || xrbox;
+        r_ = ld(own ? rhoS : rhoA, c);
+        e_ = ld(own ? eS : eA, c);
+        v_ = ld(vd, c);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) pi_[m] = ld(own ? piS[m] : piA[m], c);
+      }
+    };
+    auto step = [&](int i, auto fast_tag) {
+      constexpr bool FAST = decltype(fast_tag)::value;
       const int r = m0 - 3 + i;
       rw[0] = rw[1]; rw[1] = rw[2]; rw[2] = rw[3]; rw[3] = nr;
       sw[0] = sw[1]; sw[1] = sw[2]; sw[2] = sw[3];
@@ -778,11 +797,14 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
       for (int m = 0; m < 3; ++m) {
         pw[m][0] = pw[m][1]; pw[m][1] = pw[m][2]; pw[m][2] = np[m];
       }
-      if (i + 1 < nit) load(r + 1, nr, ne, nv, np);
+      if (FAST)
+        load_in(r + 1, nr, ne, nv, np);
+      else if (i + 1 < nit)
+        load(r + 1, nr, ne, nv, np);
       // mass and energy flux of face plane f = r - 1
       const int f = r - 1;
       C Fv = C(0.f), Evv = C(0.f);
-      if (pos && f >= 2 && f < sd - 1) {
+      if (pos && (FAST || (f >= 2 && f < sd - 1))) {
         const C du = vw[1];
         const C u = bg.V[d] + du;
         const C cour = u * dtdx;
@@ -793,7 +815,8 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
       }
       Fw[0] = Fw[1]; Fw[1] = Fv;
       Ew[0] = Ew[1]; Ew[1] = Evv;
-      if (L.is_child && owned && f >= m0 && f < m1 && (f == L.G || f == L.G + L.n[d])) {
+      if (!FAST && L.is_child && owned && f >= m0 && f < m1 &&
+          (f == L.G || f == L.G + L.n[d])) {
         // CommFlux record: transverse axes x and the row axis
         fr_put(L, d, f, x, row, 0, it.sub, as_double(Fv));
         fr_put(L, d, f, x, row, 1, it.sub, as_double(Evv));
@@ -804,15 +827,15 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
       xb[NT + tid] = vw[1];
       xb[2 * NT + tid] = Fv;
       __syncthreads();
-      if (warp == 0) continue;  // the halo row only supplies rho, v_d and F
+      if (warp == 0) return;  // the halo row only supplies rho, v_d and F
       const C r_rb = xb[tid - 32], v_rb = xb[NT + tid - 32], F_rb = xb[2 * NT + tid - 32];
       const C r_xb = shfl_up(rw[3], 1), v_xb = shfl_up(vw[1], 1), F_xb = shfl_up(Fv, 1);
       // w = (dPi - V drf) / (rho0 + drf) of plane r
-      const bool pok = pos && (unsigned)r < (unsigned)sMU;
+      const bool pok = pos && (FAST || (unsigned)r < (unsigned)sMU);
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         const C rn = m == mx ? r_xb : (m == mr ? r_rb : rw[2]);
-        const bool g1 = m == mx ? x >= 1 : (m == mr ? row >= 1 : r >= 1);
+        const bool g1 = m == mx ? x >= 1 : (m == mr ? row >= 1 : (FAST || r >= 1));
         C wv = C(0.f);
         if (pok && g1) {
           const C drf = halve(rn + rw[3]);
@@ -826,7 +849,7 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
       for (int j = 0; j < 2; ++j) {
         const int m = j == 0 ? mx : mr;
         C P = C(0.f);
-        if (pos && q >= 2 && q < sd - 1 && (j == 0 ? x >= 1 : row >= 1)) {
+        if (pos && (FAST || (q >= 2 && q < sd - 1)) && (j == 0 ? x >= 1 : row >= 1)) {
           const C ue = bg.V[d] + halve((j == 0 ? v_xb : v_rb) + vw[1]);
           const C Fe = halve((j == 0 ? F_xb : F_rb) + Fv);
           const C wsv = upwind_v(ww[m][0], ww[m][1], ww[m][2], ww[m][3], ue, ue * dtdx);
@@ -839,7 +862,7 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
       {
         const int p = r - 2;
         C P = C(0.f);
-        if (pos && p >= 2 && p < sd - 2) {
+        if (pos && (FAST || (p >= 2 && p < sd - 2))) {
           const C uc = bg.V[d] + halve(vw[0] + vw[1]);
           const C Fc = halve(Fw[0] + Fw[1]);
           const C wsv = upwind_v(ww[d][0], ww[d][1], ww[d][2], ww[d][3], uc, uc * dtdx);
@@ -850,12 +873,12 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
       }
       // conservative update of plane u = r - 2
       const int u = r - 2;
-      if (owned && u >= m0 && u < m1) {
+      if (owned && (FAST || (u >= m0 && u < m1))) {
         const int c = cxr + u * stM;
         C rv = rw[1], evv = er[0];
-        if (u >= 2 && u < sd - 2) {
+        if (FAST || (u >= 2 && u < sd - 2)) {
           C Flo = Fw[0], Fhi = Fw[1], Elo = Ew[0], Ehi = Ew[1];
-          if (L.has_child) {
+          if (!FAST && L.has_child) {
             int g[3];
             gcoord(u, g);
             frontier_fluxes(L, d, g, Flo, Fhi, Elo, Ehi);
@@ -869,15 +892,26 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
         for (int m = 0; m < 3; ++m) {
           C pv = pw[m][0];
           if (m == d) {
-            if (u >= 3 && u < sd - 2) pv = pv - (Pd[1] - Pd[0]) * iv;
+            if (FAST || (u >= 3 && u < sd - 2)) pv = pv - (Pd[1] - Pd[0]) * iv;
           } else {
             const int j = m == mx ? 0 : 1;
-            if (u >= 2 && u < sd - 2 && (j == 0 ? x >= 1 : row >= 1))
+            if ((FAST || (u >= 2 && u < sd - 2)) && (j == 0 ? x >= 1 : row >= 1))
               pv = pv - (Pm[j][1] - Pm[j][0]) * iv;
           }
           st(piD[m], c, pv);
         }
       }
+    };
+    load(m0 - 3, nr, ne, nv, np);
+    for (int i = 0; i < nit; ++i) {
+      const int r = m0 - 3 + i;
+      const bool fast = r >= r_lo && r <= r_hi &&
+                        !(L.is_child && (r - 1 == L.G || r - 1 == L.G + L.n[d])) &&
+                        !(L.has_child && near_frontier(L, d, r - 2));
+      if (fast)
+        step(i, std::true_type{});
+      else
+        step(i, std::false_type{});
     }
   } else {
     // ======================================================== x sweep, march in z
