@@ -1956,7 +1956,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_sweep_single(const Item<T> it
 }
 
 template <class T, int D>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep_batch(const Item<T>* __restrict__ items,
+__global__ void __launch_bounds__(kSweepThreads, sizeof(T) == 4 ? 2 : 1) k_sweep_batch(const Item<T>* __restrict__ items,
                                                               const unsigned* __restrict__ starts,
                                                               int nitems, unsigned nchunks) {
   __shared__ __align__(16) Arith<T> s_x[2 * 3 * kSweepThreads];
@@ -2073,6 +2073,31 @@ int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, in
 #undef DFN_OP
 #undef DFN_OPD
   return 1;
+}
+
+// blocks of a context's sweep kernel resident on the whole device at once (SMs x the
+// blocks one SM holds), per state size and direction; looked up once
+int sweep_slots(int esz, int d) {
+  static int cache[2][3] = {};
+  const int t = esz == 8 ? 1 : 0;
+  if (cache[t][d] == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void* k = nullptr;
+    if (esz == 8)
+      k = d == 0 ? (const void*)k_sweep_single<double, 0>
+                 : d == 1 ? (const void*)k_sweep_single<double, 1>
+                          : (const void*)k_sweep_single<double, 2>;
+    else
+      k = d == 0 ? (const void*)k_sweep_single<float, 0>
+                 : d == 1 ? (const void*)k_sweep_single<float, 1>
+                          : (const void*)k_sweep_single<float, 2>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kSweepThreads, 0) != cudaSuccess)
+      per = 1;
+    cache[t][d] = std::max(1, sms * std::max(1, per));
+  }
+  return cache[t][d];
 }
 
 // elements per chunk of each op (one chunk = one block pass)
