@@ -614,15 +614,19 @@ struct Builder {
     return it;
   }
 
-  // planes per chunk of a fused sweep's marching axis: enough chunks for about 600
-  // blocks, at least 8 planes (16 when marching along the sweep, whose chunks start
-  // 3 planes early and finish 2 planes late)
-  static int sweep_chunk(const Box& b, int d) {
+  // planes per chunk of a fused sweep's marching axis, at least 8 (16 when marching
+  // along the sweep, whose chunks start 3 planes early and finish 2 planes late).
+  // A context's sweep launches one block per (column, chunk): as many chunks as
+  // leave every block resident at once (one wave: the SMs times the blocks of that
+  // kernel an SM holds), since each chunk repeats the planes of its halo.  A pool's
+  // persistent blocks take chunks in turn: about 600 chunks balance them.
+  int sweep_chunk(const Box& b, int d) const {
     const int ra = sweep_row_axis(d), mu = sweep_march_axis(d), ow = sweep_own_x(d);
     const int ncols = ((b.hi[0] - b.lo[0] + ow - 1) / ow) *
                       ((b.hi[ra] - b.lo[ra] + kSweepRows - 1) / kSweepRows);
     const int nm = b.hi[mu] - b.lo[mu];
-    const int chunks = std::max(1, 600 / std::max(1, ncols));
+    const int slots = pool ? 600 : sweep_slots((int)sizeof(T), d);
+    const int chunks = std::max(1, slots / std::max(1, ncols));
     const int zc = (nm + chunks - 1) / chunks;
     return std::min(nm, std::max(zc, d == 0 ? 8 : 16));
   }

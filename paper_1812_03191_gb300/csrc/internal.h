@@ -360,6 +360,7 @@ template <class T>
 int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, int nitems,
                  unsigned nchunks, unsigned grid, cudaStream_t st, const Item<T>* host_item);
 int op_chunk_elems(int op, int esz);  // elements per chunk for state elements of esz bytes
+int sweep_slots(int esz, int d);      // a context's sweep blocks resident at once
 unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const Box& b);
 int force_partials_per_level(const LevelView& L);
 int launch_force_weights(const LevelView& L, const Phys& P, cudaStream_t st);
