@@ -618,8 +618,9 @@ struct Builder {
   // along the sweep, whose chunks start 3 planes early and finish 2 planes late).
   // A context's sweep launches one block per (column, chunk): as many chunks as
   // leave every block resident at once (one wave: the SMs times the blocks of that
-  // kernel an SM holds), since each chunk repeats the planes of its halo.  A pool's
-  // persistent blocks take chunks in turn: about 600 chunks balance them.
+  // kernel an SM holds, when that is at least two), since each chunk repeats the
+  // planes of its halo.  A pool's persistent blocks take chunks in turn: about 600
+  // chunks balance them.
   int sweep_chunk(const Box& b, int d) const {
     const int ra = sweep_row_axis(d), mu = sweep_march_axis(d), ow = sweep_own_x(d);
     const int ncols = ((b.hi[0] - b.lo[0] + ow - 1) / ow) *

@@ -103,13 +103,10 @@ __device__ __forceinline__ df64 from_double<df64>(double x) {
   return to_df64(x);
 }
 
-// sign tests of the arithmetic types (double-float: df64.h).  For FP64 (CommUp's
-// limiter) on the integer pipe: the bit pattern of a non-NaN double, read as a signed
-// integer, has the sign of the value, with +0 -> 0 and -0 -> negative.
+// sign tests of the arithmetic types (double-float: df64.h)
 __device__ __forceinline__ bool gt0(float v) { return v > 0.f; }
 __device__ __forceinline__ bool le0(float v) { return v <= 0.f; }
 __device__ __forceinline__ bool lt0(float v) { return v < 0.f; }
-__device__ __forceinline__ bool le0(double v) { return __double_as_longlong(v) <= 0; }
 
 // Half the van Leer (1977) harmonic limited slope (Sec. 3.2.1 cites it for the
 // interpolation): dl dr / (dl + dr) where dl dr > 0, else 0.  Callers fold the
@@ -1166,8 +1163,9 @@ static_assert(kCuHosts == kBlock, "one thread per host of a CommUp tile");
 
 template <class T>
 __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F, unsigned tid) {
-  __shared__ T s_z[2][kCuZ];  // [fine z offset][column (y, x) of the tile and halo]
-  __shared__ T s_y[4][kCuY];  // [fine z offset * 2 + fine y offset][(host y, x column)]
+  using A = Arith<T>;  // the interpolation runs in the stencils' arithmetic type
+  __shared__ A s_z[2][kCuZ];  // [fine z offset][column (y, x) of the tile and halo]
+  __shared__ A s_y[4][kCuY];  // [fine z offset * 2 + fine y offset][(host y, x column)]
   __shared__ CuBox s_box;
   __shared__ int s_fr[2];     // field (-1: past the last tile) and tile within the box
   const int lt = (int)(tid % kBlock);
@@ -1205,9 +1203,8 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
   const int X0 = B.x0 + txi * B.tx, Y0 = B.y0 + tyi * B.ty;
   const int wx = min(B.tx, B.x0 + B.ex - X0), wy = min(B.ty, B.y0 + B.ey - Y0);
   const int P = wx + 2;  // pitch of a row of columns
-  // offsets of the two centred fine positions in coarse cells, doubled for the half
-  // slope
-  const T dl = T(-0.5), dh = T(0.5);
+  // the two centred fine positions lie at -1/4 and +1/4 of a coarse cell: q0 -+ half
+  // of the half slope hslope returns
   const T* q = (const T*)C.q[f];
   // z pass: the tile's columns and a halo of one (hosts in [-G/2 - 1, n/2 + G/2])
   for (int e = lt; e < P * (wy + 2); e += kBlock) {
@@ -1215,28 +1212,28 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
     const int hx = X0 - 1 + cx, hy = Y0 - 1 + cy;
     const int k = ((C.G + F.off[2] + h2) * C.s[1] + C.G + F.off[1] + hy) * C.s[0] + C.G +
                   F.off[0] + hx;
-    const T qm = q[k - C.st[2]], q0 = q[k], qp = q[k + C.st[2]];
+    const A qm = ld(q, k - C.st[2]), q0 = ld(q, k), qp = ld(q, k + C.st[2]);
     if (sa == 2) {
       s_z[0][e] = q0;
-      s_z[1][e] = T(0.5) * (q0 + qp);
+      s_z[1][e] = halve(q0 + qp);
     } else {
-      const T sl = hslope(q0 - qm, qp - q0);
-      s_z[0][e] = q0 + dl * sl;
-      s_z[1][e] = q0 + dh * sl;
+      const A sl = hslope(q0 - qm, qp - q0);
+      s_z[0][e] = q0 - halve(sl);
+      s_z[1][e] = q0 + halve(sl);
     }
   }
   __syncthreads();
   // y pass: every x column of the tile's host rows
   for (int e = lt; e < 2 * wy * P; e += kBlock) {
     const int iz = e / (wy * P), rem = e - iz * wy * P;
-    const T qm = s_z[iz][rem], q0 = s_z[iz][rem + P], qp = s_z[iz][rem + 2 * P];
+    const A qm = s_z[iz][rem], q0 = s_z[iz][rem + P], qp = s_z[iz][rem + 2 * P];
     if (sa == 1) {
       s_y[2 * iz][rem] = q0;
-      s_y[2 * iz + 1][rem] = T(0.5) * (q0 + qp);
+      s_y[2 * iz + 1][rem] = halve(q0 + qp);
     } else {
-      const T sl = hslope(q0 - qm, qp - q0);
-      s_y[2 * iz][rem] = q0 + dl * sl;
-      s_y[2 * iz + 1][rem] = q0 + dh * sl;
+      const A sl = hslope(q0 - qm, qp - q0);
+      s_y[2 * iz][rem] = q0 - halve(sl);
+      s_y[2 * iz + 1][rem] = q0 + halve(sl);
     }
   }
   __syncthreads();
@@ -1249,23 +1246,23 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int iz = j >> 1, iy = j & 1;
-    const T* row = s_y[j] + ty * P + tx;
-    const T qm = row[0], q0 = row[1], qp = row[2];
-    T v[2];
+    const A* row = s_y[j] + ty * P + tx;
+    const A qm = row[0], q0 = row[1], qp = row[2];
+    A v[2];
     if (sa == 0) {
       v[0] = q0;
-      v[1] = T(0.5) * (q0 + qp);
+      v[1] = halve(q0 + qp);
     } else {
-      const T sl = hslope(q0 - qm, qp - q0);
-      v[0] = q0 + dl * sl;
-      v[1] = q0 + dh * sl;
+      const A sl = hslope(q0 - qm, qp - q0);
+      v[0] = q0 - halve(sl);
+      v[1] = q0 + halve(sl);
     }
 #pragma unroll
     for (int ix = 0; ix < 2; ++ix) {
       const int fi = G + 2 * h0 + ix, fj = G + 2 * h1 + iy, fk = G + 2 * h2 + iz;
       const bool act = fi >= G + (sa == 0) && fi < G + F.n[0] && fj >= G + (sa == 1) &&
                        fj < G + F.n[1] && fk >= G + (sa == 2) && fk < G + F.n[2];
-      if (!act) out[(fk * F.s[1] + fj) * F.s[0] + fi] = v[ix];
+      if (!act) st(out, (fk * F.s[1] + fj) * F.s[0] + fi, v[ix]);
     }
   }
 }
@@ -1339,10 +1336,6 @@ __device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView&
 }
 
 // ------------------------------------------------------------- time step
-// Per-level Courant limit: min over active cells and axes of cfl dx_d / (cs + |v_d|).
-// Division is correctly rounded and monotone, so that minimum equals
-// cfl dx_d / max(cs + |v_d|): the kernel reduces the per-axis maxima (one division
-// per level instead of three per cell).  Also flags NaN, rho <= 0 or e <= 0.
 template <class T>
 __device__ __forceinline__ T warp_max_t(T v) {
 #pragma unroll
@@ -2075,8 +2068,9 @@ int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, in
   return 1;
 }
 
-// blocks of a context's sweep kernel resident on the whole device at once (SMs x the
-// blocks one SM holds), per state size and direction; looked up once
+// blocks of a context's sweep kernel to aim for: those resident on the whole device
+// at once (SMs x the blocks one SM holds), per state size and direction; looked up
+// once
 int sweep_slots(int esz, int d) {
   static int cache[2][3] = {};
   const int t = esz == 8 ? 1 : 0;
@@ -2095,7 +2089,9 @@ int sweep_slots(int esz, int d) {
                           : (const void*)k_sweep_single<float, 2>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kSweepThreads, 0) != cudaSuccess)
       per = 1;
-    cache[t][d] = std::max(1, sms * std::max(1, per));
+    // with a single resident block per SM, several waves hide latency better than
+    // long chunks (measured on the FP64 state's sweeps): keep about 600 blocks
+    cache[t][d] = per >= 2 ? sms * per : 600;
   }
   return cache[t][d];
 }

@@ -298,6 +298,12 @@ def test_sod_shock_tube_on_the_gpu(precision):
 
 
 def test_inter_level_operators():
+    """CommUp then CommMean on random states against the oracle.  CommMean (level 0's
+    band) sums in FP64: within 1e-15.  CommUp interpolates in the stencils'
+    arithmetic, double-float for the FP64 state: each fine ghost is a converted coarse
+    value plus a quarter of a limited slope, each within about 2^-45 of the deviations
+    from the background (up to ~1.5 here), so level 1 is held to 2^-43 of the largest
+    value."""
     p = I.base_params()
     sim, orc = pair(2, 24, 6.0, p)
     rng = np.random.default_rng(9)
@@ -314,7 +320,8 @@ def test_inter_level_operators():
     for l in range(2):
         for f in range(5):
             a, b = sim.get_full(l, f), orc.get_full(l, f)
-            assert np.abs(a - b).max() <= 1e-15 * np.abs(b).max(), (l, f)
+            tol = 1e-15 if l == 0 else 2.0**-43
+            assert np.abs(a - b).max() <= tol * np.abs(b).max(), (l, f)
 
 
 def test_bc_fill_matches():
