@@ -141,10 +141,10 @@ ARRAYS_PER_ELEM = {
 
 # DRAM bytes (read + write) per box element of a launch, from the ncu captures in
 # profiles/ (k_sweep_fused_precision_5x128_fp32.md: fused sweeps, 144^3 box,
-# 86.8 / 94.4 / 81.4 MB; k_tmom_df64_nested_3x64.md: double-float momentum fluxes, 80^3
+# 80.2 / 99.5 / 85.0 MB; k_tmom_df64_nested_3x64.md: double-float momentum fluxes, 80^3
 # box, 20.1 / 20.1 / 13.5 MB, a smaller case of the same kernel, whose traffic grows
 # with the box); `traffic` scales them to the mean box of the timed launches
-TRAFFIC_PER_ELEM = {("precision_5x128^3", 4, "sweep"): (86.8e6 + 94.4e6 + 81.4e6) / 3 / 144**3,
+TRAFFIC_PER_ELEM = {("precision_5x128^3", 4, "sweep"): (80.2e6 + 99.5e6 + 85.0e6) / 3 / 144**3,
                     ("precision_5x128^3", 8, "tmom"): (20.1e6 + 20.1e6 + 13.5e6) / 3 / 80**3,
                     ("nested_3x64^3_fp64", 8, "tmom"): (20.1e6 + 20.1e6 + 13.5e6) / 3 / 80**3}
 
