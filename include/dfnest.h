@@ -51,7 +51,13 @@ extern "C" {
  * the other components. */
 
 /* state precision */
-#define DF_FP64 0       /* FP64 state and arithmetic */
+/* DF_FP64: 8 bytes per state value, each value a double with at most 47 significant
+ * bits (stored as a float pair hi + lo, which the stencils compute with: double-float
+ * arithmetic, 48-bit significands); force, time step, flux sums, CommMean and the
+ * boundary fill in FP64.  Values read out (df_get_field, df_get_state) are exact;
+ * values written in (df_set_field, df_set_state) are rounded to the 47 bits, and a
+ * state read out and written back is restored bit for bit. */
+#define DF_FP64 0
 #define DF_FP32_STATE 1 /* FP32 state and stencils; FP64 force, time step, flux sums */
 
 typedef struct {

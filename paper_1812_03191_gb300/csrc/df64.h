@@ -28,7 +28,7 @@
 
 namespace dfn {
 
-struct df64 {
+struct __align__(8) df64 {  // 8-byte aligned: one 64-bit load or store per value
   float hi, lo;
   df64() = default;  // trivial, so it may live in shared memory; {} gives zeros
   __host__ __device__ constexpr df64(float h) : hi(h), lo(0.f) {}
@@ -207,6 +207,27 @@ __host__ __device__ __forceinline__ double to_double(df64 v) {
     ex -= 1;
   }
   return u2d(sign | ((unsigned long long)ex << 52) | (S & 0xFFFFFFFFFFFFFull));
+}
+
+// ---- the FP64 state as stored.  A double-float pair whose value is a double: lo is
+// cut (toward zero) to a multiple of 2^-23 ulp(hi), so hi + lo has at most 47
+// significant bits and no bit below 2^-46 of hi's binade.  to_double of such a pair is
+// exact and to_df64 of that double gives the same pair back (hi = the 24-bit value
+// nearest to hi + lo, as the error-free transformations leave it), so the state
+// converts to and from FP64 without loss while the stencils load and store the pairs
+// directly.  Where |hi| < 2^-80 (to_df64 keeps hi alone there) lo becomes 0, and a
+// subnormal hi becomes a zero of its sign (both conversions flush it).
+struct __align__(8) dstate {
+  float hi, lo;
+};
+
+__host__ __device__ __forceinline__ df64 canonical(df64 v) {
+  const unsigned uh = f2u(v.hi), ul = f2u(v.lo);
+  const int eh = (int)((uh >> 23) & 0xFFu), el = (int)((ul >> 23) & 0xFFu);
+  const int k = eh - el - 23;  // bits of lo's significand below the grid
+  unsigned lo = 0u;
+  if (eh >= 47 && k < 24) lo = k > 0 ? ul & (0xFFFFFFFFu << k) : ul;
+  return df64(eh == 0 ? u2f(uh & 0x80000000u) : v.hi, u2f(lo));
 }
 
 }  // namespace dfn

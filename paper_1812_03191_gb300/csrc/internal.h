@@ -158,6 +158,20 @@ struct ArithOf<double> {
 template <class T>
 using Arith = typename ArithOf<T>::type;
 
+// Storage type of the state fields: float for the FP32 state; for the FP64 state a
+// double-float pair whose value is a double (df64.h, dstate), 8 bytes like a double,
+// which the stencils load and store without conversion.
+template <class T>
+struct StateOf {
+  using type = T;
+};
+template <>
+struct StateOf<double> {
+  using type = dstate;
+};
+template <class T>
+using St = typename StateOf<T>::type;
+
 // a double constant in an arithmetic type (host side)
 template <class C>
 inline C to_arith(double x) {

@@ -81,12 +81,29 @@ __device__ __forceinline__ df64 hdiv(df64 a, df64 b) { return a / b; }
 // The stencils' arithmetic type C = Arith<T> (internal.h): float for the FP32 state,
 // double-float for the FP64 state.  Loads convert the stored value to C, stores round
 // C back to the state type.
+// The FP64 state is stored as pairs whose values are doubles (dstate, df64.h): loads
+// take the pair as it is, stores cut lo onto the pair's grid.
 __device__ __forceinline__ float ld(const float* __restrict__ p, int i) { return p[i]; }
-__device__ __forceinline__ df64 ld(const double* __restrict__ p, int i) { return to_df64(p[i]); }
 __device__ __forceinline__ df64 ld(const df64* __restrict__ p, int i) { return p[i]; }
+__device__ __forceinline__ df64 ld(const dstate* __restrict__ p, int i) {
+  const dstate v = p[i];
+  return df64(v.hi, v.lo);
+}
 __device__ __forceinline__ void st(df64* p, int i, df64 v) { p[i] = v; }
 __device__ __forceinline__ void st(float* p, int i, float v) { p[i] = v; }
-__device__ __forceinline__ void st(double* p, int i, df64 v) { p[i] = to_double(v); }
+__device__ __forceinline__ void st(dstate* p, int i, df64 v) {
+  const df64 c = canonical(v);
+  p[i] = dstate{c.hi, c.lo};
+}
+// A state value in the state's own type, for the kernels that compute in it (the
+// boundary fill, CommMean, the time step, I/O): the float itself, or the exact double
+// of a stored pair; put() stores such a value back (a double rounded to the pair).
+__device__ __forceinline__ float val(const float* __restrict__ p, int i) { return p[i]; }
+__device__ __forceinline__ double val(const dstate* __restrict__ p, int i) {
+  return to_double(ld(p, i));
+}
+__device__ __forceinline__ void put(float* p, int i, float x) { p[i] = x; }
+__device__ __forceinline__ void put(dstate* p, int i, double x) { st(p, i, to_df64(x)); }
 // exact scalings by 1/2 and 2
 __device__ __forceinline__ float halve(float v) { return 0.5f * v; }
 __device__ __forceinline__ df64 halve(df64 v) { return scale(v, 0.5f); }
@@ -189,8 +206,8 @@ __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, cons
   using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
-  const T* __restrict__ rho = (const T*)L.q[F_RHO];
-  const T* __restrict__ e = (const T*)L.q[F_E];
+  const St<T>* __restrict__ rho = (const St<T>*)L.q[F_RHO];
+  const St<T>* __restrict__ e = (const St<T>*)L.q[F_E];
   const Arith<T>* __restrict__ phi = (const Arith<T>*)L.phi;
   const C h = halve(dtp[0]);
   const int c = cidx(L, i, j, k);
@@ -198,7 +215,7 @@ __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, cons
   const C rc = ld(rho, c), ec = ld(e, c), fc = ld(phi, c);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    T* v = (T*)L.q[F_VX + d];
+    St<T>* v = (St<T>*)L.q[F_VX + d];
     if (c3[d] >= 1) {
       int m = c - L.st[d];
       C drf = halve(ld(rho, m) + rc);
@@ -230,20 +247,20 @@ __device__ __forceinline__ void el_visc_q(const LevelView& L, const Box& b, cons
   if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const C rc = bg.rho0 + ld((const T*)L.q[F_RHO], c);
+  const C rc = bg.rho0 + ld((const St<T>*)L.q[F_RHO], c);
   C heat = C(0.f);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     C q = C(0.f);
     if (c3[d] < L.s[d] - 1) {
-      const T* v = (const T*)L.q[F_VX + d];
+      const St<T>* v = (const St<T>*)L.q[F_VX + d];
       const C dv = ld(v, c + L.st[d]) - ld(v, c);
       if (lt0(dv)) q = av * rc * dv * dv;
       heat += q * dv * g.inv_dx[d];
     }
     st((Arith<T>*)S.P[d], c, q);
   }
-  T* e = (T*)L.q[F_E];
+  St<T>* e = (St<T>*)L.q[F_E];
   st(e, c, ld(e, c) - dtp[0] * heat);
 }
 
@@ -257,7 +274,7 @@ __device__ __forceinline__ void el_visc_v(const LevelView& L, const Box& b, cons
   using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
-  const T* __restrict__ rho = (const T*)L.q[F_RHO];
+  const St<T>* __restrict__ rho = (const St<T>*)L.q[F_RHO];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const C dt = dtp[0];
@@ -266,7 +283,7 @@ __device__ __forceinline__ void el_visc_v(const LevelView& L, const Box& b, cons
     if (c3[d] < 1) continue;
     const int m = c - L.st[d];
     const Arith<T>* q = (const Arith<T>*)S.P[d];
-    T* v = (T*)L.q[F_VX + d];
+    St<T>* v = (St<T>*)L.q[F_VX + d];
     const C drf = halve(ld(rho, m) + ld(rho, c));
     const C vn = ld(v, c) - dt * hdiv(ld(q, c) - ld(q, m), bg.rho0 + drf) * g.inv_dx[d];
     st(v, c, vn);
@@ -304,10 +321,10 @@ __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b
             j >= (L.mir & 2 ? 0 : L.G) && j < L.G + L.n[1] && k >= (L.mir & 4 ? 0 : L.G) &&
             k < L.G + L.n[2];
   }
-  T* e = (T*)L.q[F_E];
-  const T* vx = (const T*)L.q[F_VX];
-  const T* vy = (const T*)L.q[F_VX + 1];
-  const T* vz = (const T*)L.q[F_VX + 2];
+  St<T>* e = (St<T>*)L.q[F_E];
+  const St<T>* vx = (const St<T>*)L.q[F_VX];
+  const St<T>* vy = (const St<T>*)L.q[F_VX + 1];
+  const St<T>* vz = (const St<T>*)L.q[F_VX + 2];
   C ec[NC], x0[NC], x1[NC], y0[NC], y1[NC], z0[NC], z1[NC], lw[NC], dr[NC];
 #pragma unroll
   for (int n = 0; n < NC; ++n) {
@@ -321,7 +338,7 @@ __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b
       z1[n] = ld(vz, c[n] + L.st[2]);
     }
     if (lm[n]) lw[n] = ld((const Arith<T>*)L.lumw, c[n]);
-    if (do_eps) dr[n] = ld((const T*)L.q[F_RHO], c[n]);
+    if (do_eps) dr[n] = ld((const St<T>*)L.q[F_RHO], c[n]);
   }
   const C dt = dtp[0];
 #pragma unroll
@@ -387,7 +404,7 @@ __device__ __forceinline__ void fr_sums(const LevelView& L, const DevScalars* ds
 // energy moved in +d across a face during dt: -chi rho_f d(e/rho)/dx * area * dt
 template <class T>
 __device__ __forceinline__ Arith<T> diff_flux(const LevelView& L, const Geo<Arith<T>>& g,
-                                              const T* __restrict__ rho,
+                                              const St<T>* __restrict__ rho,
                                               const Arith<T>* __restrict__ eps, int f, int d,
                                               Arith<T> chi, Arith<T> dt, Arith<T> rho0, int dfr) {
   using C = Arith<T>;
@@ -417,15 +434,15 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
     c3[n][2] = k;
   }
   const C dt = dtp[0];
-  const T* __restrict__ rho = (const T*)L.q[F_RHO];
+  const St<T>* __restrict__ rho = (const St<T>*)L.q[F_RHO];
   const Arith<T>* __restrict__ eps = (const Arith<T>*)S.eps;
   C q[NC][3][2];  // flux through the lower and the upper d-face
 #pragma unroll
   for (int n = 0; n < NC; ++n)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      q[n][d][0] = diff_flux(L, g, rho, eps, c[n], d, chi, dt, rho0, dfr);
-      q[n][d][1] = diff_flux(L, g, rho, eps, c[n] + L.st[d], d, chi, dt, rho0, dfr);
+      q[n][d][0] = diff_flux<T>(L, g, rho, eps, c[n], d, chi, dt, rho0, dfr);
+      q[n][d][1] = diff_flux<T>(L, g, rho, eps, c[n] + L.st[d], d, chi, dt, rho0, dfr);
     }
   if (L.has_child) {
 #pragma unroll
@@ -443,7 +460,7 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
           q[n][d][1] = from_double<C>(L.cacc[((2 * d + side) * 3 + 2) * L.cacc_slots + slot]);
       }
   }
-  T* e = (T*)L.q[F_E];
+  St<T>* e = (St<T>*)L.q[F_E];
   C ev[NC];
 #pragma unroll
   for (int n = 0; n < NC; ++n) ev[n] = ld(e, c[n]);
@@ -483,7 +500,7 @@ __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scrat
       f3[t2] = L.G + 2 * b + v;
       const int f = (f3[2] * L.s[1] + f3[1]) * L.s[0] + f3[0];
       fr_put(L, d, fd, f3[t1], f3[t2], 2, sub,
-             as_double(diff_flux(L, g, (const T*)L.q[F_RHO], (const Arith<T>*)S.eps, f, d, chi, dt,
+             as_double(diff_flux<T>(L, g, (const St<T>*)L.q[F_RHO], (const Arith<T>*)S.eps, f, d, chi, dt,
                                  rho0, dfr)));
     }
 }
@@ -495,11 +512,11 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
   using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
-  const T* __restrict__ rho = (const T*)L.q[F_RHO];
+  const St<T>* __restrict__ rho = (const St<T>*)L.q[F_RHO];
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const C rc = ld(rho, c);
-  st((Arith<T>*)S.eps, c, hdiv(ld((const T*)L.q[F_E], c) - bg.eps0 * rc, bg.rho0 + rc));
+  st((Arith<T>*)S.eps, c, hdiv(ld((const St<T>*)L.q[F_E], c) - bg.eps0 * rc, bg.rho0 + rc));
   if (eps_only) return;
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
@@ -531,11 +548,11 @@ __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const
     const C dt = dtp[0];
     const int sd = L.st[d];
     const C Adt = g.area[d] * dt;
-    const C du = ld((const T*)L.q[F_VX + d], c);
+    const C du = ld((const St<T>*)L.q[F_VX + d], c);
     const C u = bg.V[d] + du;
     const C cour = u * (dt * g.inv_dx[d]);
     const C F0 = bg.rho0 * bg.V[d] * Adt;
-    C drs = upwind((const T*)L.q[F_RHO], c, sd, u, cour);
+    C drs = upwind((const St<T>*)L.q[F_RHO], c, sd, u, cour);
     Fv = (bg.rho0 * du + drs * u) * Adt;        // F - rho0 V_d A dt
     C des = upwind((const Arith<T>*)S.eps, c, sd, u, cour);
     Ev = bg.eps0 * Fv + des * (F0 + Fv);        // E - eps0 rho0 V_d A dt
@@ -562,7 +579,7 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
   const int c3[3] = {i, j, k};
   const C dt = dtp[0];
   const int sd = L.st[d];
-  const T* __restrict__ vd = (const T*)L.q[F_VX + d];
+  const St<T>* __restrict__ vd = (const St<T>*)L.q[F_VX + d];
   const Arith<T>* __restrict__ F = (const Arith<T>*)S.F;
   const C dtdx = dt * g.inv_dx[d];
   const C F0 = bg.rho0 * bg.V[d] * (g.area[d] * dt);
@@ -573,7 +590,7 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
       if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
         C uc = bg.V[d] + halve(ld(vd, c) + ld(vd, c + sd));
         C Fc = halve(ld(F, c) + ld(F, c + sd));
-        C ws = d == 0 ? upwind((const T*)S.w[m], c + sd, sd, uc, uc * dtdx)
+        C ws = d == 0 ? upwind((const St<T>*)S.w[m], c + sd, sd, uc, uc * dtdx)
                       : upwind((const Arith<T>*)S.w[m], c + sd, sd, uc, uc * dtdx);
         P = bg.V[m] * Fc + ws * (F0 + Fc);
       }
@@ -581,7 +598,7 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
       const int sm = L.st[m];
       C ue = bg.V[d] + halve(ld(vd, c - sm) + ld(vd, c));
       C Fe = halve(ld(F, c - sm) + ld(F, c));
-      C ws = d == 0 ? upwind((const T*)S.w[m], c, sd, ue, ue * dtdx)
+      C ws = d == 0 ? upwind((const St<T>*)S.w[m], c, sd, ue, ue * dtdx)
                     : upwind((const Arith<T>*)S.w[m], c, sd, ue, ue * dtdx);
       P = bg.V[m] * Fe + ws * (F0 + Fe);
     }
@@ -616,8 +633,8 @@ __device__ __forceinline__ void el_tupdate(const LevelView& L, const Box& b, con
         Ehi = from_double<C>(L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot]);
       }
     }
-    T* rho = (T*)L.q[F_RHO];
-    T* e = (T*)L.q[F_E];
+    St<T>* rho = (St<T>*)L.q[F_RHO];
+    St<T>* e = (St<T>*)L.q[F_E];
     st(rho, c, ld(rho, c) - (Fhi - Flo) * iv);
     st(e, c, ld(e, c) - (Ehi - Elo) * iv);
   }
@@ -714,13 +731,13 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
                      row < b.hi[RA];
   const bool xrbox = x >= b.lo[0] && x < b.hi[0] && row >= b.lo[RA] && row < b.hi[RA];
   const int cxr = x + row * stR;
-  const T* rhoA = (const T*)L.q[F_RHO];
-  const T* eA = (const T*)L.q[F_E];
-  const T* rhoS = kFromB ? (const T*)S.qb[0] : rhoA;
-  const T* eS = kFromB ? (const T*)S.qb[1] : eA;
-  const T* __restrict__ vd = (const T*)L.q[F_VX + d];
-  T* rhoD = kFromB ? (T*)L.q[F_RHO] : (T*)S.qb[0];
-  T* eD = kFromB ? (T*)L.q[F_E] : (T*)S.qb[1];
+  const St<T>* rhoA = (const St<T>*)L.q[F_RHO];
+  const St<T>* eA = (const St<T>*)L.q[F_E];
+  const St<T>* rhoS = kFromB ? (const St<T>*)S.qb[0] : rhoA;
+  const St<T>* eS = kFromB ? (const St<T>*)S.qb[1] : eA;
+  const St<T>* __restrict__ vd = (const St<T>*)L.q[F_VX + d];
+  St<T>* rhoD = kFromB ? (St<T>*)L.q[F_RHO] : (St<T>*)S.qb[0];
+  St<T>* eD = kFromB ? (St<T>*)L.q[F_E] : (St<T>*)S.qb[1];
   // the momenta are scratch (arithmetic type), rho and e the state type in both copies
   const C* piA[3] = {(const C*)S.pi[0], (const C*)S.pi[1], (const C*)S.pi[2]};
   const C* piS[3] = {kFromB ? (const C*)S.qb[2] : piA[0], kFromB ? (const C*)S.qb[3] : piA[1],
@@ -1028,31 +1045,31 @@ __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b,
   using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
-  T* rhoA = (T*)L.q[F_RHO];
-  T* eA = (T*)L.q[F_E];
+  St<T>* rhoA = (St<T>*)L.q[F_RHO];
+  St<T>* eA = (St<T>*)L.q[F_E];
   // after fused sweeps the box's state is in Scratch::qb; outside the box it is in
   // the level's arrays, which this op then updates for the box
-  const T* rho = fused ? (const T*)S.qb[0] : rhoA;
-  const T* e = fused ? (const T*)S.qb[1] : eA;
+  const St<T>* rho = fused ? (const St<T>*)S.qb[0] : rhoA;
+  const St<T>* e = fused ? (const St<T>*)S.qb[1] : eA;
   const Arith<T>* __restrict__ phi = (const Arith<T>*)L.phi;
   const C h = halve(dtp[0]);
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const T rc_s = rho[c], ec_s = e[c];
+  const St<T> rc_s = rho[c], ec_s = e[c];
   const C rc = ld(rho, c), ec = ld(e, c), fc = ld(phi, c);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (c3[d] < 1) continue;
     int m = c - L.st[d];
     const bool own = !fused || c3[d] - 1 >= b.lo[d];
-    const C rm = ld(own ? rho : (const T*)rhoA, m);
-    const C em = ld(own ? e : (const T*)eA, m);
+    const C rm = ld(own ? rho : (const St<T>*)rhoA, m);
+    const C em = ld(own ? e : (const St<T>*)eA, m);
     C drf = halve(rm + rc);
     C rinv = hdiv(C(1.f), bg.rho0 + drf);
     const C* pi = (const C*)(fused ? S.qb[2 + d] : S.pi[d]);
     C v = (ld(pi, c) - bg.V[d] * drf) * rinv;
     C acc = (gm1 * (ec - em) * rinv + (fc - ld(phi, m))) * g.inv_dx[d];
-    st((T*)L.q[F_VX + d], c, v - h * acc);
+    st((St<T>*)L.q[F_VX + d], c, v - h * acc);
   }
   if (fused) {
     rhoA[c] = rc_s;
@@ -1127,20 +1144,23 @@ __device__ __forceinline__ void el_bc_axis(const LevelView& L, int d, int type_l
   c3[t1] = a;
   c3[t2] = b;
   c3[d] = dst;
-  T* q = (T*)L.q[f];
+  St<T>* q = (St<T>*)L.q[f];
   int cd = (c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0];
   if (use_fixed) {
-    q[cd] = fixed;
+    put(q, cd, fixed);
   } else {
     c3[d] = src;
     int cs = (c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0];
-    q[cd] = sign * q[cs] + shift;
+    if (sign == T(1) && shift == T(0))
+      q[cd] = q[cs];  // a copy keeps the stored value as it is
+    else
+      put(q, cd, sign * val(q, cs) + shift);
   }
   // the lower boundary face G of v_d: 0 at a wall, V (zero deviation) on an injection
   // face; the upper boundary face G + n is the g = 1 element of the upper side
   if ((type == 3 || type == 2) && side == 0 && normal && g == 1) {
     c3[d] = G;
-    q[(c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0]] = type == 3 ? -Vd : T(0);
+    put(q, (c3[2] * L.s[1] + c3[1]) * L.s[0] + c3[0], type == 3 ? -Vd : T(0));
   }
 }
 
@@ -1205,7 +1225,7 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
   const int P = wx + 2;  // pitch of a row of columns
   // the two centred fine positions lie at -1/4 and +1/4 of a coarse cell: q0 -+ half
   // of the half slope hslope returns
-  const T* q = (const T*)C.q[f];
+  const St<T>* q = (const St<T>*)C.q[f];
   // z pass: the tile's columns and a halo of one (hosts in [-G/2 - 1, n/2 + G/2])
   for (int e = lt; e < P * (wy + 2); e += kBlock) {
     const int cy = e / P, cx = e - cy * P;
@@ -1241,7 +1261,7 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
   if (lt >= wx * wy) return;
   const int ty = lt / wx, tx = lt - ty * wx;
   const int h0 = X0 + tx, h1 = Y0 + ty;
-  T* out = (T*)F.q[f];
+  St<T>* out = (St<T>*)F.q[f];
   const int G = F.G;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -1294,7 +1314,7 @@ __device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView&
   if (in_band(F, band, a3[0], a3[1], a3[2])) {
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
-      const T* q = (const T*)F.q[f];
+      const St<T>* q = (const St<T>*)F.q[f];
       T sz[2];
 #pragma unroll
       for (int dz = 0; dz < 2; ++dz) {
@@ -1302,11 +1322,11 @@ __device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView&
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
           int c0 = ((Gf + 2 * cc + dz) * F.s[1] + Gf + 2 * b + dy) * F.s[0] + Gf + 2 * a;
-          sy[dy] = q[c0] + q[c0 + 1];
+          sy[dy] = val(q, c0) + val(q, c0 + 1);
         }
         sz[dz] = sy[0] + sy[1];
       }
-      ((T*)C.q[f])[dst] = T(0.125) * (sz[0] + sz[1]);
+      put((St<T>*)C.q[f], dst, T(0.125) * (sz[0] + sz[1]));
     }
   }
 #pragma unroll
@@ -1316,7 +1336,7 @@ __device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView&
     m3[sa] -= 1;
     if (!in_band(F, band, a3[0], a3[1], a3[2]) && !in_band(F, band, m3[0], m3[1], m3[2])) continue;
     int t1 = sa == 0 ? 1 : 0, t2 = sa == 2 ? 1 : 2;
-    const T* q = (const T*)F.q[F_VX + sa];
+    const St<T>* q = (const St<T>*)F.q[F_VX + sa];
     T sv[2];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
@@ -1327,11 +1347,11 @@ __device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView&
         fi[sa] = Gf + 2 * r[sa];
         fi[t1] = Gf + 2 * r[t1] + u;
         fi[t2] = Gf + 2 * r[t2] + v;
-        pair[u] = q[(fi[2] * F.s[1] + fi[1]) * F.s[0] + fi[0]];
+        pair[u] = val(q, (fi[2] * F.s[1] + fi[1]) * F.s[0] + fi[0]);
       }
       sv[v] = pair[0] + pair[1];
     }
-    ((T*)C.q[F_VX + sa])[dst] = T(0.25) * (sv[0] + sv[1]);
+    put((St<T>*)C.q[F_VX + sa], dst, T(0.25) * (sv[0] + sv[1]));
   }
 }
 
@@ -1367,16 +1387,16 @@ __device__ __forceinline__ void el_dt_level(const LevelView& L, int level, doubl
     int c = (k * L.s[1] + j) * L.s[0] + i;
     // per-cell arithmetic in the state's type (an FP32 state gives FP32 sound
     // speeds); the maxima, the minimum over levels and dt itself are FP64
-    T rho = (T)rho0 + ((const T*)L.q[F_RHO])[c];
-    T e = (T)e0 + ((const T*)L.q[F_E])[c];
+    T rho = (T)rho0 + val((const St<T>*)L.q[F_RHO], c);
+    T e = (T)e0 + val((const St<T>*)L.q[F_E], c);
     if (!(rho > T(0)) || !(e > T(0))) bad_s = 1;
     if (hydro) {
       T cs = sqrt((T)gg * e / rho);
       const T Vb[3] = {(T)V0, (T)V1, (T)V2};
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const T* v = (const T*)L.q[F_VX + d];
-        T v0 = fabs(Vb[d] + v[c]), v1 = fabs(Vb[d] + v[c + L.st[d]]);
+        const St<T>* v = (const St<T>*)L.q[F_VX + d];
+        T v0 = fabs(Vb[d] + val(v, c)), v1 = fabs(Vb[d] + val(v, c + L.st[d]));
         mx[d] = cs + (v0 > v1 ? v0 : v1);
       }
     }
@@ -1521,7 +1541,7 @@ __device__ __forceinline__ void el_force_level(const LevelView& L, const double*
                    aj >= L.coff[1] && aj < L.coff[1] + (L.cn[1] >> 1) && ak >= L.coff[2] &&
                    ak < L.coff[2] + (L.cn[2] >> 1);
     if (covered) continue;
-    double dr = (double)((const T*)L.q[F_RHO])[((L.G + ak) * L.s[1] + L.G + aj) * L.s[0] + L.G + ai];
+    double dr = (double)val((const St<T>*)L.q[F_RHO], ((L.G + ak) * L.s[1] + L.G + aj) * L.s[0] + L.G + ai);
     f[0] += dr * fx[t];
     f[1] += dr * fy[t];
     f[2] += dr * fz[t];
@@ -1619,7 +1639,7 @@ __global__ void __launch_bounds__(kBlock) k_init_uniform(LevelView L, T rho0, T 
   (void)V1;
   (void)V2;
 #pragma unroll
-  for (int f = 0; f < 5; ++f) ((T*)L.q[f])[c] = T(0);
+  for (int f = 0; f < 5; ++f) put((St<T>*)L.q[f], c, T(0));
 }
 
 // Plummer potential (Eq. 16, attractive sign) at every cell centre; luminosity
@@ -1706,32 +1726,32 @@ template <class T>
 __global__ void __launch_bounds__(kBlock) k_pack(LevelView L, int field, double* out, int full,
                                                  double bgv) {
   long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
-  const T* q = (const T*)L.q[field];
+  const St<T>* q = (const St<T>*)L.q[field];
   if (full) {
-    if (t < L.nc) out[t] = bgv + (double)q[t];
+    if (t < L.nc) out[t] = bgv + (double)val(q, t);
     return;
   }
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
   if (t >= na) return;
   int i = (int)(t % L.n[0]), j = (int)((t / L.n[0]) % L.n[1]),
       k = (int)(t / ((long long)L.n[0] * L.n[1]));
-  out[t] = bgv + (double)q[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G];
+  out[t] = bgv + (double)val(q, ((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G);
 }
 
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_unpack(LevelView L, int field, const double* in,
                                                    int full, double bgv) {
   long long t = blockIdx.x * (long long)kBlock + threadIdx.x;
-  T* q = (T*)L.q[field];
+  St<T>* q = (St<T>*)L.q[field];
   if (full) {
-    if (t < L.nc) q[t] = (T)(in[t] - bgv);
+    if (t < L.nc) put(q, t, (T)(in[t] - bgv));
     return;
   }
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
   if (t >= na) return;
   int i = (int)(t % L.n[0]), j = (int)((t / L.n[0]) % L.n[1]),
       k = (int)(t / ((long long)L.n[0] * L.n[1]));
-  q[((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G] = (T)(in[t] - bgv);
+  put(q, ((k + L.G) * L.s[1] + j + L.G) * L.s[0] + i + L.G, (T)(in[t] - bgv));
 }
 
 // hdiv versus IEEE division on the given operands: max |error| in ulps of the IEEE

@@ -83,6 +83,31 @@ int main() {
     }
     ++n;
   }
+  // the stored form of the FP64 state (canonical): its value is a double, the cut
+  // moves it by less than 2^-45 of itself, it is its own canonical form, and it
+  // survives the trip through double bit for bit (results of sums, products and
+  // quotients, whose low parts take every size, and values down to 1e-30, below the
+  // 2^-80 where lo becomes 0 and hi alone stands for the value, as in to_df64)
+  for (int k = 0; k < 2000000; ++k) {
+    const double x = operand() * (k % 7 == 0 ? 1e-10 : 1.0), y = operand();
+    const df64 a = to_df64(x), b = to_df64(y);
+    const df64 r = k % 3 == 0 ? a + b : (k % 3 == 1 ? a * b : a / b);
+    const df64 c = canonical(r);
+    const double v = to_double(c), vr = to_double(r);
+    const double cut = std::fabs(vr) < 0x1.0p-79 ? 0x1.0p-23 : 0x1.0p-45;  // hi alone below
+    if (v != (double)c.hi + (double)c.lo || std::fabs(v - vr) > cut * std::fabs(vr)) {
+      std::printf("FAIL canonical value %.17g %.17g\n", vr, v);
+      return 1;
+    }
+    const df64 cc = canonical(c), back = to_df64(v);
+    if (f2u(cc.hi) != f2u(c.hi) || f2u(cc.lo) != f2u(c.lo) || f2u(back.hi) != f2u(c.hi) ||
+        f2u(back.lo) != f2u(c.lo)) {
+      std::printf("FAIL canonical round trip %.17g: (%a, %a) -> (%a, %a)\n", v, c.hi, c.lo,
+                  back.hi, back.lo);
+      return 1;
+    }
+    ++n;
+  }
   // signed zeros, infinities and NaN survive both conversions
   if (to_double(to_df64(-0.0)) != 0.0 || !std::signbit(to_double(to_df64(-0.0))) ||
       !std::isinf(to_double(to_df64(1e300))) || !std::isnan(to_double(to_df64(NAN)))) {

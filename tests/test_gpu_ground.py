@@ -42,7 +42,10 @@ def _perturb(runs, seed, amp=1e-2):
             base = runs[0].get_field(l, f)
             pert = I.smooth_perturbation(base.shape, seed + 17 * l + f, amp)
             val = base * (1 + pert) if f < 2 else base + pert
-            for r in runs:
+            # the first run's stored values (its FP64 state keeps 47 significant bits)
+            runs[0].set_field(l, f, val)
+            val = runs[0].get_field(l, f)
+            for r in runs[1:]:
                 r.set_field(l, f, val)
     for l in range(runs[0].n_levels - 1):
         for r in runs:

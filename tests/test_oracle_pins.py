@@ -672,6 +672,42 @@ def test_momentum_conserved_periodic(av):
     assert np.abs(P1 - P0).max() < 1e-13 * n**3
 
 
+def test_nested_momentum_drift_is_bounded():
+    """Across a level frontier the staggered momenta are not flux-matched (only mass and
+    energy are, Sec. 3.2.3), so the coarse level's momentum, conserved by its own solver
+    in a periodic box, moves when CommMean restricts the covered faces.  This states by
+    how much, from the first coarse step on (when the covered cells first hold the
+    restriction), beside the composite mass, which stays exact."""
+    n, nl = 24, 2
+    o = make(nl, n, 6.0, GM=0.0, L=0.0, chi=0.3, mach=0.8, flow_dir=(0.6, 0.8, 0.0),
+             bc=(I.BC_PERIODIC,) * 6)
+    _perturb(o, nl, n, seed=5)
+    G = I.DEFAULT_G
+    vol0 = (12.0 / n) ** 3
+
+    def momentum():
+        o.fill_bc()
+        rho = o.get_full(0, RHO)
+        P, S = [], []
+        for m in range(3):
+            v = o.get_full(0, VX + m)
+            pm = 0.5 * (np.roll(rho, 1, axis=2 - m) + rho) * v
+            P.append(pm[G:G + n, G:G + n, G:G + n].sum() * vol0)
+            S.append(np.abs(pm[G:G + n, G:G + n, G:G + n]).sum() * vol0)
+        return np.array(P), np.array(S)
+
+    o.step(1)
+    P0, S0 = momentum()
+    m0 = _composite_sum(o, nl, n, RHO, vol0)
+    o.step(4)
+    P1, _ = momentum()
+    m1 = _composite_sum(o, nl, n, RHO, vol0)
+    drift = np.abs(P1 - P0) / S0
+    print("momentum drift / sum |rho v| per component after 4 coarse steps:", drift)
+    assert abs(m1 - m0) <= 1e-13 * abs(m0)
+    assert drift.max() < 2e-3
+
+
 @pytest.mark.parametrize("adv,comp", [(0, 1), (1, 2), (2, 0)])
 def test_transverse_momentum_advected_at_wind_speed(adv, comp):
     """A shear wave v_comp(x_adv) in a uniform wind along x_adv is carried
