@@ -37,9 +37,10 @@ from paper_1812_03191_gb300 import inputs as I  # noqa: E402
 
 METRIC = "cell-updates/s"
 UNIT = "cell-updates/s"
-# FP64 state: the stencils compute in double-float pairs on the FP32 pipe, the
+# FP64 state: stored as double-float pairs whose values are doubles of at most 47
+# significant bits; the stencils compute in double-float on the FP32 pipe, the
 # reductions, CommMean and the boundary fill in FP64
-DTYPE_FP64 = "f64-state/df64-stencils/f64-reductions"
+DTYPE_FP64 = "df64-state(47-bit doubles)/df64-stencils/f64-reductions"
 
 
 def workload(name):
