@@ -79,20 +79,19 @@ __host__ __device__ __forceinline__ float rcp_est(float b) {
 #endif
 }
 
-// a / b: q1 from the reciprocal estimate, the remainder a - b q1 in double-float,
-// then one correction q2 = remainder / b.hi (the long division of Dekker 1971): the
-// quotient's relative error is about the square of q1's (2^-22 each, so about
-// 2^-44, 6e-14) plus the double-float rounding.
+// a / b: q1 from the reciprocal estimate, the remainder a - b q1, then one correction
+// q2 = remainder * r (the long division of Dekker 1971).  The remainder is about
+// 2^-22 |a|, so it needs no double-float sum: one fused multiply-add gives
+// a.hi - b.hi q1 rounded once (2^-24 of the remainder, about 2^-46 |a|), a second
+// takes away b.lo q1 and adds a.lo.  The quotient's relative error is about the
+// square of q1's (2^-22 each, so about 2^-44, 6e-14) plus those roundings.
 // For the normal, non-zero divisors of the stencils (densities, 1 + a, sums of two
 // same-signed slopes).
 __host__ __device__ __forceinline__ df64 operator/(df64 a, df64 b) {
   const float r = rcp_est(b.hi);
   const float q1 = a.hi * r;
-  // remainder a - b q1, exact up to the double-float rounding
-  df64 p = two_prod(b.hi, q1);
-  p.lo = fmaf(b.lo, q1, p.lo);
-  df64 rem = a - fast_two_sum(p.hi, p.lo);
-  return fast_two_sum(q1, rem.hi * r);
+  const float rem = fmaf(-b.lo, q1, fmaf(-b.hi, q1, a.hi) + a.lo);
+  return fast_two_sum(q1, rem * r);
 }
 
 // a times a power of two (exact, both parts scaled; no overflow or underflow)

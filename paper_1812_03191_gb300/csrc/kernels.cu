@@ -139,14 +139,23 @@ __device__ __forceinline__ C hslope(C dl, C dr) {
 // The upwind side's value, slopes and coefficient are selected first, so one limiter
 // (one division) serves both flow directions: u > 0 gives qm + (1 - cour)/2 * slope,
 // u <= 0 gives q0 + (-1 - cour)/2 * slope = q0 - (1 + cour)/2 * slope, with
-// (+-1 - cour)/2 * slope = (+-1 - cour) * hslope.
+// (+-1 - cour)/2 * slope = (+-1 - cour) * hslope.  In double-float the operands of
+// the two one-sided differences are selected before subtracting (two subtractions of
+// 11 instructions, not three); in FP32 the three differences are formed and the
+// results selected, which measured faster in the fused sweeps (the same values).
 template <class C>
 __device__ __forceinline__ C upwind_v(C qmm, C qm, C q0, C qp, C u, C cour) {
   const bool up = gt0(u);
-  const C dm = q0 - qm;
   const C a = up ? qm : q0;
-  const C dl = up ? qm - qmm : dm;
-  const C dr = up ? dm : qp - q0;
+  C dl, dr;
+  if constexpr (sizeof(C) == 4) {
+    const C dm = q0 - qm;
+    dl = up ? qm - qmm : dm;
+    dr = up ? dm : qp - q0;
+  } else {
+    dl = a - (up ? qmm : qm);
+    dr = (up ? q0 : qp) - a;
+  }
   return a + ((up ? C(1.f) : C(-1.f)) - cour) * hslope(dl, dr);
 }
 
