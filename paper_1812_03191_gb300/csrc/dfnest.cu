@@ -598,6 +598,7 @@ struct Builder {
     it.chi = to_arith<C>(r.P.chi);
     it.av = to_arith<C>(r.P.av_c2);
     it.gg = r.P.gamma * (r.P.gamma - 1.0);
+    it.gga = to_arith<C>(it.gg);
     it.rho0d = r.P.rho0;
     it.e0d = r.P.e0;
     for (int d = 0; d < 3; ++d) it.V[d] = r.P.V[d];

@@ -341,6 +341,7 @@ struct __align__(16) Item {
   double* ring;         // force history
   long long* ring_pos;
   Arith<T> gm1, lum, chi, av;
+  Arith<T> gga;         // gamma (gamma - 1), the time step's per-cell factor
   double gg, rho0d, e0d, V[3], dt_fixed;
   int ring_cap, npart, level, band, flags, bc_lo, bc_hi;
   unsigned count;       // index-space size of the item

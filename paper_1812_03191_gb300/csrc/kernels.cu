@@ -104,7 +104,9 @@ __device__ __forceinline__ double val(const dstate* __restrict__ p, int i) {
 }
 __device__ __forceinline__ void put(float* p, int i, float x) { p[i] = x; }
 __device__ __forceinline__ void put(dstate* p, int i, double x) { st(p, i, to_df64(x)); }
-// exact scalings by 1/2 and 2
+// exact scalings by 1/2, 2 and other powers of two
+__device__ __forceinline__ float pow2_times(float v, float p) { return p * v; }
+__device__ __forceinline__ df64 pow2_times(df64 v, float p) { return scale(v, p); }
 __device__ __forceinline__ float halve(float v) { return 0.5f * v; }
 __device__ __forceinline__ df64 halve(df64 v) { return scale(v, 0.5f); }
 __device__ __forceinline__ float twice(float v) { return 2.f * v; }
@@ -1324,18 +1326,18 @@ __device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView&
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       const St<T>* q = (const St<T>*)F.q[f];
-      T sz[2];
+      Arith<T> sz[2];
 #pragma unroll
       for (int dz = 0; dz < 2; ++dz) {
-        T sy[2];
+        Arith<T> sy[2];
 #pragma unroll
         for (int dy = 0; dy < 2; ++dy) {
           int c0 = ((Gf + 2 * cc + dz) * F.s[1] + Gf + 2 * b + dy) * F.s[0] + Gf + 2 * a;
-          sy[dy] = val(q, c0) + val(q, c0 + 1);
+          sy[dy] = ld(q, c0) + ld(q, c0 + 1);
         }
         sz[dz] = sy[0] + sy[1];
       }
-      put((St<T>*)C.q[f], dst, T(0.125) * (sz[0] + sz[1]));
+      st((St<T>*)C.q[f], dst, pow2_times(sz[0] + sz[1], 0.125f));
     }
   }
 #pragma unroll
@@ -1346,85 +1348,128 @@ __device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView&
     if (!in_band(F, band, a3[0], a3[1], a3[2]) && !in_band(F, band, m3[0], m3[1], m3[2])) continue;
     int t1 = sa == 0 ? 1 : 0, t2 = sa == 2 ? 1 : 2;
     const St<T>* q = (const St<T>*)F.q[F_VX + sa];
-    T sv[2];
+    Arith<T> sv[2];
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-      T pair[2];
+      Arith<T> pair[2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         int fi[3];
         fi[sa] = Gf + 2 * r[sa];
         fi[t1] = Gf + 2 * r[t1] + u;
         fi[t2] = Gf + 2 * r[t2] + v;
-        pair[u] = val(q, (fi[2] * F.s[1] + fi[1]) * F.s[0] + fi[0]);
+        pair[u] = ld(q, (fi[2] * F.s[1] + fi[1]) * F.s[0] + fi[0]);
       }
       sv[v] = pair[0] + pair[1];
     }
-    put((St<T>*)C.q[F_VX + sa], dst, T(0.25) * (sv[0] + sv[1]));
+    st((St<T>*)C.q[F_VX + sa], dst, pow2_times(sv[0] + sv[1], 0.25f));
   }
 }
 
 // ------------------------------------------------------------- time step
-template <class T>
-__device__ __forceinline__ T warp_max_t(T v) {
+__device__ __forceinline__ float warp_max_t(float v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+// the larger of two double-float values (a total order on normalised pairs: hi, then
+// lo); a NaN operand loses, as in fmax
+__device__ __forceinline__ df64 dmax(df64 a, df64 b) {
+  return (a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo) || b.hi != b.hi) ? a : b;
+}
+__device__ __forceinline__ df64 warp_max_t(df64 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = dmax(v, df64(__shfl_xor_sync(0xffffffffu, v.hi, o),
+                     __shfl_xor_sync(0xffffffffu, v.lo, o)));
+  return v;
+}
+__device__ __forceinline__ df64 dabs(df64 v) { return v.hi < 0.f ? -v : v; }
+// Square root in double-float: the float root s refined by one Newton step on the
+// square (Heron's method; the double-length form of Karp & Markstein, ACM TOMS 23,
+// 1997): s + (x - s^2) / (2 s), with s^2 exact as a product plus its error, so the
+// residual is exact up to the low parts and the result good to about 2^-46.  For
+// x <= 0 (an unhealthy state, flagged by the caller) the float root of hi.
+__device__ __forceinline__ df64 dsqrt(df64 x) {
+  const float s = sqrtf(x.hi);
+  if (!(x.hi > 0.f)) return df64(s);
+  const df64 s2 = two_prod(s, s);
+  const float r = ((x.hi - s2.hi) - s2.lo + x.lo) * (0.5f * rcp_est(s));
+  return fast_two_sum(s, r);
 }
 
 // Per-level Courant limit: min over active cells and axes of cfl dx_d / (cs + |v_d|).
 // Division is correctly rounded and monotone, so that minimum equals
 // cfl dx_d / max(cs + |v_d|): the kernel reduces the per-axis maxima (one division
 // per level instead of three per cell); a maximum is exact in any precision, so it
-// is taken in the state's type and widened once per block.  Also flags NaN,
-// rho <= 0 or e <= 0.
+// is taken in the per-cell type and widened once per block.  Per-cell arithmetic:
+// FP32 for the FP32 state (FP32 sound speeds); double-float for the FP64 state (its
+// sound speed and |v| within about 2^-44, so the limit is within that of the FP64
+// one; the FP64 pipe would take ~40 operations per cell).  The maxima, the minimum
+// over levels and dt itself are FP64.  Also flags NaN, rho <= 0 or e <= 0.
 template <class T>
-__device__ __forceinline__ void el_dt_level(const LevelView& L, int level, double gg, int hydro,
-                                            DevScalars* ds, double rho0, double e0, double V0,
-                                            double V1, double V2, unsigned tid) {
-  __shared__ T sm[3][kBlock / 32];
+__device__ __forceinline__ void el_dt_level(const LevelView& L, int level, double gg,
+                                            Arith<T> gga, int hydro, DevScalars* ds,
+                                            double rho0, double e0, double V0, double V1,
+                                            double V2, const Bg<Arith<T>>& bg,
+                                            unsigned tid) {
+  using A = Arith<T>;
+  __shared__ A sm[3][kBlock / 32];
   __shared__ int bad_s;
   if (threadIdx.x == 0) bad_s = 0;
   __syncthreads();
   long long t = tid;
-  T mx[3] = {T(0), T(0), T(0)};
+  A mx[3] = {A(0.f), A(0.f), A(0.f)};
   long long na = (long long)L.n[0] * L.n[1] * L.n[2];
   if (t < na) {
     int i = L.G + (int)(t % L.n[0]);
     int j = L.G + (int)((t / L.n[0]) % L.n[1]);
     int k = L.G + (int)(t / ((long long)L.n[0] * L.n[1]));
     int c = (k * L.s[1] + j) * L.s[0] + i;
-    // per-cell arithmetic in the state's type (an FP32 state gives FP32 sound
-    // speeds); the maxima, the minimum over levels and dt itself are FP64
-    T rho = (T)rho0 + val((const St<T>*)L.q[F_RHO], c);
-    T e = (T)e0 + val((const St<T>*)L.q[F_E], c);
-    if (!(rho > T(0)) || !(e > T(0))) bad_s = 1;
-    if (hydro) {
-      T cs = sqrt((T)gg * e / rho);
-      const T Vb[3] = {(T)V0, (T)V1, (T)V2};
+    if constexpr (sizeof(T) == 4) {
+      float rho = (float)rho0 + val((const St<T>*)L.q[F_RHO], c);
+      float e = (float)e0 + val((const St<T>*)L.q[F_E], c);
+      if (!(rho > 0.f) || !(e > 0.f)) bad_s = 1;
+      if (hydro) {
+        float cs = sqrtf((float)gg * e / rho);
+        const float Vb[3] = {(float)V0, (float)V1, (float)V2};
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const St<T>* v = (const St<T>*)L.q[F_VX + d];
-        T v0 = fabs(Vb[d] + val(v, c)), v1 = fabs(Vb[d] + val(v, c + L.st[d]));
-        mx[d] = cs + (v0 > v1 ? v0 : v1);
+        for (int d = 0; d < 3; ++d) {
+          const St<T>* v = (const St<T>*)L.q[F_VX + d];
+          float v0 = fabsf(Vb[d] + val(v, c)), v1 = fabsf(Vb[d] + val(v, c + L.st[d]));
+          mx[d] = cs + (v0 > v1 ? v0 : v1);
+        }
+      }
+    } else {
+      const A rho = bg.rho0 + ld((const St<T>*)L.q[F_RHO], c);
+      const A e = bg.e0 + ld((const St<T>*)L.q[F_E], c);
+      if (!gt0(rho) || !gt0(e)) bad_s = 1;
+      if (hydro) {
+        const A cs = dsqrt(hdiv(gga * e, rho));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const St<T>* v = (const St<T>*)L.q[F_VX + d];
+          const A v0 = dabs(bg.V[d] + ld(v, c)), v1 = dabs(bg.V[d] + ld(v, c + L.st[d]));
+          mx[d] = cs + dmax(v0, v1);
+        }
       }
     }
   }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    T v = warp_max_t(mx[d]);
+    A v = warp_max_t(mx[d]);
     if ((threadIdx.x & 31) == 0) sm[d][threadIdx.x >> 5] = v;
   }
   __syncthreads();
   if (threadIdx.x < 32) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      T v = threadIdx.x < kBlock / 32 ? sm[d][threadIdx.x] : T(0);
+      A v = threadIdx.x < kBlock / 32 ? sm[d][threadIdx.x] : A(0.f);
       v = warp_max_t(v);
       // non-negative doubles order like their bit patterns (NaN is caught above)
-      if (threadIdx.x == 0 && v > T(0))
-        atomicMax(&ds->dtmin[3 * level + d],
-                  (unsigned long long)__double_as_longlong((double)v));
+      const double w = as_double(v);
+      if (threadIdx.x == 0 && w > 0.0)
+        atomicMax(&ds->dtmin[3 * level + d], (unsigned long long)__double_as_longlong(w));
     }
     if (threadIdx.x == 0 && bad_s) atomicOr(&ds->unhealthy, 1);
   }
@@ -1896,8 +1941,8 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
   else if (OP == OP_COMMMEAN)
     el_commmean<T>(it.L, it.F, it.band, tid);
   else if (OP == OP_DT_LEVEL)
-    el_dt_level<T>(it.L, it.level, it.gg, it.flags & FL_HYDRO, it.ds, it.rho0d, it.e0d, it.V[0],
-                   it.V[1], it.V[2], tid);
+    el_dt_level<T>(it.L, it.level, it.gg, it.gga, it.flags & FL_HYDRO, it.ds, it.rho0d, it.e0d,
+                   it.V[0], it.V[1], it.V[2], it.bg, tid);
   else if (OP == OP_DT_FINAL)
     el_dt_finalize(it.ds, it.level, *it.fin, it.dt_fixed);
   else if (OP == OP_FORCE_LEVEL)
