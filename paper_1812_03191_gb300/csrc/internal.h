@@ -246,10 +246,13 @@ __host__ __device__ inline bool is_box_op(int op) {
          op == OP_VISC_Q || op == OP_VISC_V;
 }
 
-// cells per thread of an op: the FP32 state's compression and diffusion ops take two
-// (with one they are latency-bound: too few bytes in flight per thread)
+// cells per thread of an op: the FP32 state's kicks, compression and diffusion take
+// two (with one they are latency-bound: too few bytes in flight per thread)
 __host__ __device__ constexpr int cells_per_thread(int op, int esz) {
-  return esz == 4 && (op == OP_COMPRESS || op == OP_DIFFUSE) ? 2 : 1;
+  return esz == 4 && (op == OP_COMPRESS || op == OP_DIFFUSE || op == OP_SOURCE ||
+                      op == OP_VREC)
+             ? 2
+             : 1;
 }
 
 // CommUp tiles (the kernel's comment in kernels.cu says how they are used): per

@@ -209,35 +209,63 @@ __device__ __forceinline__ bool near_frontier(const LevelView& L, int d, int gd)
 
 // ------------------------------------------------------------------ source S
 // S(h) of Eq. 15: v_d -= h [ (p_c - p_m)/(dx rho_face) + (Phi_c - Phi_m)/dx ]
-template <class T>
+// NC cells per thread (the two-cell form of the compression below): every load of
+// all cells first, then the arithmetic and the stores.
+template <class T, int NC>
 __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, const Scratch& S,
                                           const Arith<T>* __restrict__ dtp, int write_pi,
                                           Arith<T> gm1, const Bg<Arith<T>>& bg,
-                                          const Geo<Arith<T>>& g, unsigned tid) {
+                                          const Geo<Arith<T>>& g, const unsigned* el) {
   using C = Arith<T>;
-  int i, j, k;
-  if (!decode(b, tid, i, j, k)) return;
+  int c[NC], c3[NC][3];
+  bool ok[NC];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    int i, j, k;
+    ok[n] = decode(b, el[n], i, j, k);
+    if (NC == 1 && !ok[n]) return;
+    if (!ok[n]) i = j = k = 1;
+    c[n] = cidx(L, i, j, k);
+    c3[n][0] = i;
+    c3[n][1] = j;
+    c3[n][2] = k;
+  }
   const St<T>* __restrict__ rho = (const St<T>*)L.q[F_RHO];
   const St<T>* __restrict__ e = (const St<T>*)L.q[F_E];
   const Arith<T>* __restrict__ phi = (const Arith<T>*)L.phi;
   const C h = halve(dtp[0]);
-  const int c = cidx(L, i, j, k);
-  const int c3[3] = {i, j, k};
-  const C rc = ld(rho, c), ec = ld(e, c), fc = ld(phi, c);
+  C rc[NC], ec[NC], fc[NC], rm[NC][3], em[NC][3], fm[NC][3], vv[NC][3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    St<T>* v = (St<T>*)L.q[F_VX + d];
-    if (c3[d] >= 1) {
-      int m = c - L.st[d];
-      C drf = halve(ld(rho, m) + rc);
-      C rf = bg.rho0 + drf;
-      C acc = (hdiv(gm1 * (ec - ld(e, m)), rf) + (fc - ld(phi, m))) * g.inv_dx[d];
-      C vn = ld(v, c) - h * acc;
-      st(v, c, vn);
-      // momentum deviation: rf (V + dv) - rho0 V
-      if (write_pi) st((Arith<T>*)S.pi[d], c, bg.rho0 * vn + drf * (bg.V[d] + vn));
-    } else if (write_pi) {
-      ((Arith<T>*)S.pi[d])[c] = C(0.f);
+  for (int n = 0; n < NC; ++n) {
+    rc[n] = ld(rho, c[n]);
+    ec[n] = ld(e, c[n]);
+    fc[n] = ld(phi, c[n]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (c3[n][d] >= 1) {
+        const int m = c[n] - L.st[d];
+        rm[n][d] = ld(rho, m);
+        em[n][d] = ld(e, m);
+        fm[n][d] = ld(phi, m);
+        vv[n][d] = ld((const St<T>*)L.q[F_VX + d], c[n]);
+      }
+  }
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    if (!ok[n]) continue;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (c3[n][d] >= 1) {
+        C drf = halve(rm[n][d] + rc[n]);
+        C rf = bg.rho0 + drf;
+        C acc = (hdiv(gm1 * (ec[n] - em[n][d]), rf) + (fc[n] - fm[n][d])) * g.inv_dx[d];
+        C vn = vv[n][d] - h * acc;
+        st((St<T>*)L.q[F_VX + d], c[n], vn);
+        // momentum deviation: rf (V + dv) - rho0 V
+        if (write_pi) st((Arith<T>*)S.pi[d], c[n], bg.rho0 * vn + drf * (bg.V[d] + vn));
+      } else if (write_pi) {
+        ((Arith<T>*)S.pi[d])[c[n]] = C(0.f);
+      }
     }
   }
 }
@@ -1047,15 +1075,27 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
   }
 }
 
-// velocity from the transported momenta, then the second half kick S(dt/2)
-template <class T>
+// velocity from the transported momenta, then the second half kick S(dt/2); NC cells
+// per thread as in el_source
+template <class T, int NC>
 __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b, const Scratch& S,
                                                const Arith<T>* __restrict__ dtp, Arith<T> gm1,
                                                const Bg<Arith<T>>& bg, const Geo<Arith<T>>& g,
-                                               int fused, unsigned tid) {
+                                               int fused, const unsigned* el) {
   using C = Arith<T>;
-  int i, j, k;
-  if (!decode(b, tid, i, j, k)) return;
+  int c[NC], c3[NC][3];
+  bool ok[NC];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    int i, j, k;
+    ok[n] = decode(b, el[n], i, j, k);
+    if (NC == 1 && !ok[n]) return;
+    if (!ok[n]) i = j = k = 1;
+    c[n] = cidx(L, i, j, k);
+    c3[n][0] = i;
+    c3[n][1] = j;
+    c3[n][2] = k;
+  }
   St<T>* rhoA = (St<T>*)L.q[F_RHO];
   St<T>* eA = (St<T>*)L.q[F_E];
   // after fused sweeps the box's state is in Scratch::qb; outside the box it is in
@@ -1064,27 +1104,42 @@ __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b,
   const St<T>* e = fused ? (const St<T>*)S.qb[1] : eA;
   const Arith<T>* __restrict__ phi = (const Arith<T>*)L.phi;
   const C h = halve(dtp[0]);
-  const int c = cidx(L, i, j, k);
-  const int c3[3] = {i, j, k};
-  const St<T> rc_s = rho[c], ec_s = e[c];
-  const C rc = ld(rho, c), ec = ld(e, c), fc = ld(phi, c);
+  St<T> rc_s[NC], ec_s[NC];
+  C rc[NC], ec[NC], fc[NC], rm[NC][3], em[NC][3], fm[NC][3], pv[NC][3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    if (c3[d] < 1) continue;
-    int m = c - L.st[d];
-    const bool own = !fused || c3[d] - 1 >= b.lo[d];
-    const C rm = ld(own ? rho : (const St<T>*)rhoA, m);
-    const C em = ld(own ? e : (const St<T>*)eA, m);
-    C drf = halve(rm + rc);
-    C rinv = hdiv(C(1.f), bg.rho0 + drf);
-    const C* pi = (const C*)(fused ? S.qb[2 + d] : S.pi[d]);
-    C v = (ld(pi, c) - bg.V[d] * drf) * rinv;
-    C acc = (gm1 * (ec - em) * rinv + (fc - ld(phi, m))) * g.inv_dx[d];
-    st((St<T>*)L.q[F_VX + d], c, v - h * acc);
+  for (int n = 0; n < NC; ++n) {
+    rc_s[n] = rho[c[n]];
+    ec_s[n] = e[c[n]];
+    rc[n] = ld(rho, c[n]);
+    ec[n] = ld(e, c[n]);
+    fc[n] = ld(phi, c[n]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      if (c3[n][d] >= 1) {
+        const int m = c[n] - L.st[d];
+        const bool own = !fused || c3[n][d] - 1 >= b.lo[d];
+        rm[n][d] = ld(own ? rho : (const St<T>*)rhoA, m);
+        em[n][d] = ld(own ? e : (const St<T>*)eA, m);
+        fm[n][d] = ld(phi, m);
+        pv[n][d] = ld((const C*)(fused ? S.qb[2 + d] : S.pi[d]), c[n]);
+      }
   }
-  if (fused) {
-    rhoA[c] = rc_s;
-    eA[c] = ec_s;
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    if (!ok[n]) continue;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (c3[n][d] < 1) continue;
+      C drf = halve(rm[n][d] + rc[n]);
+      C rinv = hdiv(C(1.f), bg.rho0 + drf);
+      C v = (pv[n][d] - bg.V[d] * drf) * rinv;
+      C acc = (gm1 * (ec[n] - em[n][d]) * rinv + (fc[n] - fm[n][d])) * g.inv_dx[d];
+      st((St<T>*)L.q[F_VX + d], c[n], v - h * acc);
+    }
+    if (fused) {
+      rhoA[c[n]] = rc_s[n];
+      eA[c[n]] = ec_s[n];
+    }
   }
 }
 
@@ -1903,8 +1958,8 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
 #pragma unroll
   for (int n = 1; n < NC; ++n) el[n] = el[0] + n * kBlock;
   if (OP == OP_SOURCE)
-    el_source<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.flags & FL_WRITE_PI, it.gm1, it.bg, it.g,
-                 tid);
+    el_source<T, NC>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.flags & FL_WRITE_PI, it.gm1,
+                     it.bg, it.g, el);
   else if (OP == OP_COMPRESS) {
     if (it.L.has_child)  // before any consumer
 #pragma unroll 1
@@ -1932,8 +1987,8 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
   else if (OP == OP_VISC_V)
     el_visc_v<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.flags & FL_WRITE_PI, it.bg, it.g, tid);
   else if (OP == OP_VREC)
-    el_vrec_source<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.gm1, it.bg, it.g,
-                      it.flags & FL_FUSED, tid);
+    el_vrec_source<T, NC>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.gm1, it.bg, it.g,
+                          it.flags & FL_FUSED, el);
   else if (OP == OP_BC)
     el_bc_axis<T>(it.L, D, it.bc_lo, it.bc_hi, (T)it.V[0], (T)it.V[1], (T)it.V[2], tid);
   else if (OP == OP_COMMUP)
