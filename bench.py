@@ -145,9 +145,14 @@ ARRAYS_PER_ELEM = {
 
 # DRAM bytes (read + write) per box element of a launch, from the ncu captures in
 # profiles/ (k_sweep_fused_precision_5x128_fp32.md: fused sweeps, 144^3 box,
-# 80.2 / 99.5 / 85.0 MB); `traffic` scales them to the mean box of the timed launches.
+# 80.2 / 99.5 / 85.0 MB; k_tmom_df64_nested_3x64.md: double-float momentum fluxes, 80^3
+# box, 20.09 / 20.09 / 13.47 MB, a smaller case of the same kernel, whose traffic
+# grows with the box); `traffic` scales them to the mean box of the timed launches.
 # A kernel without a capture of its current code reports null.
-TRAFFIC_PER_ELEM = {("precision_5x128^3", 4, "sweep"): (80.2e6 + 99.5e6 + 85.0e6) / 3 / 144**3}
+_TMOM_DF64 = (20.0858e6 + 20.0865e6 + 13.4710e6) / 3 / 80**3
+TRAFFIC_PER_ELEM = {("precision_5x128^3", 4, "sweep"): (80.2e6 + 99.5e6 + 85.0e6) / 3 / 144**3,
+                    ("precision_5x128^3", 8, "tmom"): _TMOM_DF64,
+                    ("nested_3x64^3_fp64", 8, "tmom"): _TMOM_DF64}
 
 
 def level_step_boxes(cfg):

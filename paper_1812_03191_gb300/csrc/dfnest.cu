@@ -587,6 +587,13 @@ struct Builder {
     Item<T> it;
     memset(&it, 0, sizeof it);
     it.L = r.L[l].v;
+    // the active box: the enumeration of the time-step and force reductions (box ops
+    // set their own)
+    for (int d = 0; d < 3; ++d) {
+      it.b.lo[d] = it.L.G;
+      it.b.hi[d] = it.L.G + it.L.n[d];
+    }
+    it.b.set_divisors();
     it.S = r.S;
     using C = Arith<T>;
     it.bg = make_bg<C>(r.P);
@@ -901,7 +908,8 @@ int plan_build_ops(Plan& plan, Run* r, const std::vector<std::pair<int, int>>& o
   for (auto& ol : ops) {
     int op = ol.first, l = ol.second;
     Item<T> it = B.base(*r, l);
-    it.b = B.box(it.L, it.L.G);
+    // box ops over the whole array; the reductions keep base()'s active box
+    if (op != OP_DT_LEVEL && op != OP_FORCE_LEVEL) it.b = B.box(it.L, it.L.G);
     switch (op) {
       case OP_COMMUP:
         B.mirror_fill(it, v);  // as in the coarse step: the stencil reaches across a plane

@@ -95,6 +95,14 @@ __device__ __forceinline__ void st(dstate* p, int i, df64 v) {
   const df64 c = canonical(v);
   p[i] = dstate{c.hi, c.lo};
 }
+// two neighbouring elements e, e + 1 (e even) in one vector store
+__device__ __forceinline__ void st2(float* p, int e, float a, float b) {
+  *reinterpret_cast<float2*>(p + e) = make_float2(a, b);
+}
+__device__ __forceinline__ void st2(dstate* p, int e, df64 a, df64 b) {
+  const df64 ca = canonical(a), cb = canonical(b);
+  *reinterpret_cast<float4*>(p + e) = make_float4(ca.hi, ca.lo, cb.hi, cb.lo);
+}
 // A state value in the state's own type, for the kernels that compute in it (the
 // boundary fill, CommMean, the time step, I/O): the float itself, or the exact double
 // of a stored pair; put() stores such a value back (a double rounded to the pair).
@@ -513,7 +521,7 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
 }
 
 // CommFlux record of the diffusive energy fluxes through a child's frontier faces:
-// one thread per (side, coarse slot) evaluates its 4 fine faces (a launch of its own:
+// one thread per fine frontier face (a launch of its own:
 // inside the diffusion kernel the record code would cost that kernel occupancy)
 template <class T>
 __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scratch& S,
@@ -521,27 +529,25 @@ __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scrat
                                                  Arith<T> rho0, int dfr,
                                                  const Geo<Arith<T>>& g, int sub, unsigned tid) {
   using C = Arith<T>;
-  if (tid >= 6u * (unsigned)L.acc_slots) return;
-  const int side = (int)tid / L.acc_slots, slot = (int)tid - side * L.acc_slots;
+  // one thread per fine face: (side, coarse slot, fine face u, v of the slot)
+  if (tid >= 24u * (unsigned)L.acc_slots) return;
+  const int u = (int)(tid & 1u), v = (int)((tid >> 1) & 1u);
+  const int rest = (int)(tid >> 2);
+  const int side = rest / L.acc_slots, slot = rest - side * L.acc_slots;
   const int d = side >> 1, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
   const int h1 = L.n[t1] >> 1;
   if (slot >= h1 * (L.n[t2] >> 1)) return;
   const int a = slot % h1, b = slot / h1;
   const C dt = dtp[0];
   const int fd = (side & 1) ? L.G + L.n[d] : L.G;
-#pragma unroll
-  for (int v = 0; v < 2; ++v)
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      int f3[3];
-      f3[d] = fd;
-      f3[t1] = L.G + 2 * a + u;
-      f3[t2] = L.G + 2 * b + v;
-      const int f = (f3[2] * L.s[1] + f3[1]) * L.s[0] + f3[0];
-      fr_put(L, d, fd, f3[t1], f3[t2], 2, sub,
-             as_double(diff_flux<T>(L, g, (const St<T>*)L.q[F_RHO], (const Arith<T>*)S.eps, f, d, chi, dt,
-                                 rho0, dfr)));
-    }
+  int f3[3];
+  f3[d] = fd;
+  f3[t1] = L.G + 2 * a + u;
+  f3[t2] = L.G + 2 * b + v;
+  const int f = (f3[2] * L.s[1] + f3[1]) * L.s[0] + f3[0];
+  fr_put(L, d, fd, f3[t1], f3[t2], 2, sub,
+         as_double(diff_flux<T>(L, g, (const St<T>*)L.q[F_RHO], (const Arith<T>*)S.eps, f, d, chi,
+                                dt, rho0, dfr)));
 }
 
 // --------------------------------------------------------------- transport
@@ -1343,12 +1349,22 @@ __device__ __forceinline__ void el_commup(const LevelView& C, const LevelView& F
       v[0] = q0 - halve(sl);
       v[1] = q0 + halve(sl);
     }
+    // the two fine elements along x are neighbours in memory: one vector store when
+    // both are ghosts and the pair starts on an even element (aligned)
+    const int fi0 = G + 2 * h0, fj = G + 2 * h1 + iy, fk = G + 2 * h2 + iz;
+    const bool yz = fj >= G + (sa == 1) && fj < G + F.n[1] && fk >= G + (sa == 2) &&
+                    fk < G + F.n[2];
+    const bool act0 = yz && fi0 >= G + (sa == 0) && fi0 < G + F.n[0];
+    const bool act1 = yz && fi0 + 1 >= G + (sa == 0) && fi0 + 1 < G + F.n[0];
+    const int e0 = (fk * F.s[1] + fj) * F.s[0] + fi0;
+    if (!act0 && !act1 && (e0 & 1) == 0) {
+      st2(out, e0, v[0], v[1]);
+      continue;
+    }
 #pragma unroll
     for (int ix = 0; ix < 2; ++ix) {
-      const int fi = G + 2 * h0 + ix, fj = G + 2 * h1 + iy, fk = G + 2 * h2 + iz;
-      const bool act = fi >= G + (sa == 0) && fi < G + F.n[0] && fj >= G + (sa == 1) &&
-                       fj < G + F.n[1] && fk >= G + (sa == 2) && fk < G + F.n[2];
-      if (!act) st(out, (fk * F.s[1] + fj) * F.s[0] + fi, v[ix]);
+      const bool act = ix == 0 ? act0 : act1;
+      if (!act) st(out, e0 + ix, v[ix]);
     }
   }
 }
@@ -1369,10 +1385,11 @@ __device__ __forceinline__ bool in_band(const LevelView& F, int band, int a0, in
 
 template <class T>
 __device__ __forceinline__ void el_commmean(const LevelView& C, const LevelView& F, int band, unsigned tid) {
-  long long t = tid;
-  int h0 = F.n[0] >> 1, h1 = F.n[1] >> 1, h2 = F.n[2] >> 1;
-  if (t >= (long long)h0 * h1 * h2) return;
-  int a = (int)(t % h0), b = (int)((t / h0) % h1), cc = (int)(t / ((long long)h0 * h1));
+  const unsigned t = tid;  // coarse cells of the covered box: fewer than 2^31
+  const unsigned h0 = F.n[0] >> 1, h1 = F.n[1] >> 1, h2 = F.n[2] >> 1;
+  if (t >= h0 * h1 * h2) return;
+  const unsigned q = t / h0;
+  int a = (int)(t - q * h0), b = (int)(q % h1), cc = (int)(q / h1);
   int r[3] = {a, b, cc};
   int a3[3] = {a + F.off[0], b + F.off[1], cc + F.off[2]};
   const int Gf = F.G, Gc = C.G;
@@ -1463,7 +1480,7 @@ __device__ __forceinline__ df64 dsqrt(df64 x) {
 // one; the FP64 pipe would take ~40 operations per cell).  The maxima, the minimum
 // over levels and dt itself are FP64.  Also flags NaN, rho <= 0 or e <= 0.
 template <class T>
-__device__ __forceinline__ void el_dt_level(const LevelView& L, int level, double gg,
+__device__ __forceinline__ void el_dt_level(const LevelView& L, const Box& b, int level, double gg,
                                             Arith<T> gga, int hydro, DevScalars* ds,
                                             double rho0, double e0, double V0, double V1,
                                             double V2, const Bg<Arith<T>>& bg,
@@ -1473,13 +1490,9 @@ __device__ __forceinline__ void el_dt_level(const LevelView& L, int level, doubl
   __shared__ int bad_s;
   if (threadIdx.x == 0) bad_s = 0;
   __syncthreads();
-  long long t = tid;
   A mx[3] = {A(0.f), A(0.f), A(0.f)};
-  long long na = (long long)L.n[0] * L.n[1] * L.n[2];
-  if (t < na) {
-    int i = L.G + (int)(t % L.n[0]);
-    int j = L.G + (int)((t / L.n[0]) % L.n[1]);
-    int k = L.G + (int)(t / ((long long)L.n[0] * L.n[1]));
+  int i, j, k;  // b is the active box: multiply-shift division, no 64-bit divide
+  if (decode(b, tid, i, j, k)) {
     int c = (k * L.s[1] + j) * L.s[0] + i;
     if constexpr (sizeof(T) == 4) {
       float rho = (float)rho0 + val((const St<T>*)L.q[F_RHO], c);
@@ -1631,7 +1644,8 @@ __device__ __forceinline__ void el_time_advance(DevScalars* ds) {
 constexpr int kForceCells = 8;
 
 template <class T>
-__device__ __forceinline__ void el_force_level(const LevelView& L, const double* __restrict__ fw,
+__device__ __forceinline__ void el_force_level(const LevelView& L, const Box& b,
+                                               const double* __restrict__ fw,
                                                double* partials, unsigned tid) {
   __shared__ double sw[3][kBlock / 32];
   const long long na = (long long)L.n[0] * L.n[1] * L.n[2];
@@ -1641,11 +1655,10 @@ __device__ __forceinline__ void el_force_level(const LevelView& L, const double*
   double f[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int u = 0; u < kForceCells; ++u) {
-    long long t = (long long)(tid / kBlock) * kBlock * kForceCells + u * kBlock + threadIdx.x;
-    if (t >= na) break;
-    int ai = (int)(t % L.n[0]);
-    int aj = (int)((t / L.n[0]) % L.n[1]);
-    int ak = (int)(t / ((long long)L.n[0] * L.n[1]));
+    const unsigned t = (tid / kBlock) * kBlock * kForceCells + u * kBlock + threadIdx.x;
+    int i, j, k;  // b is the active box: multiply-shift division, no 64-bit divide
+    if (!decode(b, t, i, j, k)) break;
+    const int ai = i - L.G, aj = j - L.G, ak = k - L.G;
     bool covered = L.has_child && ai >= L.coff[0] && ai < L.coff[0] + (L.cn[0] >> 1) &&
                    aj >= L.coff[1] && aj < L.coff[1] + (L.cn[1] >> 1) && ak >= L.coff[2] &&
                    ak < L.coff[2] + (L.cn[2] >> 1);
@@ -1996,12 +2009,12 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
   else if (OP == OP_COMMMEAN)
     el_commmean<T>(it.L, it.F, it.band, tid);
   else if (OP == OP_DT_LEVEL)
-    el_dt_level<T>(it.L, it.level, it.gg, it.gga, it.flags & FL_HYDRO, it.ds, it.rho0d, it.e0d,
+    el_dt_level<T>(it.L, it.b, it.level, it.gg, it.gga, it.flags & FL_HYDRO, it.ds, it.rho0d, it.e0d,
                    it.V[0], it.V[1], it.V[2], it.bg, tid);
   else if (OP == OP_DT_FINAL)
     el_dt_finalize(it.ds, it.level, *it.fin, it.dt_fixed);
   else if (OP == OP_FORCE_LEVEL)
-    el_force_level<T>(it.L, it.L.fw, it.partials, tid);
+    el_force_level<T>(it.L, it.b, it.L.fw, it.partials, tid);
   else if (OP == OP_FORCE_FINAL)
     el_force_finalize(it.partials, it.npart, it.ds, it.ring, it.ring_cap, it.ring_pos);
   else if (OP == OP_TIME)
@@ -2250,7 +2263,7 @@ unsigned op_count(int op, int d, const LevelView& L, const LevelView& F, const B
     case OP_SWEEP:
       n = (long long)sweep_units(b, d) * kBlock;  // one chunk per (column, chunk) unit
       break;
-    case OP_FRONTIER_DIFF: n = 6LL * L.acc_slots; break;
+    case OP_FRONTIER_DIFF: n = 24LL * L.acc_slots; break;
     case OP_BC: {
       int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
       n = (long long)L.s[t1] * L.s[t2] * 2 * L.G * 5;
