@@ -284,8 +284,12 @@ def run_reference(args, cfg):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg["name"], "n_levels": cfg["n_levels"], "n": cfg["n"],
-                   "box": [cfg["lo"][0], cfg["hi"][0]], "ghost": cfg["G"]},
+        # the FP64 workload of the GPU arm's line, named as that line names it
+        "config": {"workload": cfg["name"].replace("_fp64", "") + "_fp64",
+                   "n_levels": cfg["n_levels"], "n": cfg["n"],
+                   "box": [cfg["lo"][0], cfg["hi"][0]], "ghost": cfg["G"],
+                   "mach": cfg["params"]["mach"], "chi": cfg["params"]["chi"],
+                   "luminosity": cfg["params"]["L"], "cell_updates_per_step": cu},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
                          "kind": "oracle (OpenMP build)" if omp else "oracle",
                          "sample": f"{args.steps} whole coarse steps of {cfg['name']} "

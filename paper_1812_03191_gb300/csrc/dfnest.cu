@@ -684,6 +684,14 @@ struct Builder {
     Item<T> it = base(r, l);
     it.b = box(it.L, m_out + kReach, r.P.av_c2 > 0.0, l == 0 ? 1 : 0);
     const Phys& P = r.P;
+    // The two sub-cycles of a finest level follow each other with nothing in between
+    // that changes it (no boundary fill, CommUp or CommMean; no mirror fill where it
+    // has no mirror plane; both always run without the Eq. 55-56 search): the first
+    // one's velocity recovery also applies the second one's first kick.
+    const bool paired = P.hydro_on && l > 0 && l + 1 == r.nl && r.xi[l - 1] == 2 &&
+                        r.prm.xi_mode != 1 && it.L.mir == 0;
+    const bool kick_done = paired && sub_of[l] == 1;
+    const int vrec_d = paired && sub_of[l] == 0 ? 1 : 0;
     if (l == 0)
       for (int d = 0; d < 3; ++d) {
         Item<T> bc = it;
@@ -693,7 +701,7 @@ struct Builder {
       }
     else
       mirror_fill(it, out);  // CommUp filled the rest of the ghosts
-    if (P.hydro_on) add(out, OP_SOURCE, 0, it);
+    if (P.hydro_on && !kick_done) add(out, OP_SOURCE, 0, it);
     if (P.hydro_on && P.av_c2 > 0.0) {
       add(out, OP_VISC_Q, 0, it);
       add(out, OP_VISC_V, 0, it);
@@ -710,7 +718,7 @@ struct Builder {
       }
       Item<T> vr = it;
       vr.flags |= FL_FUSED;
-      add(out, OP_VREC, 0, vr);
+      add(out, OP_VREC, vrec_d, vr);
     } else if (P.hydro_on) {
       // At the x sweep the staggered momenta were just formed from v and rho (the
       // kick, or the viscosity stage after it, wrote them; nothing since has changed
@@ -728,7 +736,7 @@ struct Builder {
         add(out, OP_TMOM, d, tm);
         add(out, OP_TUPDATE, d, it);
       }
-      add(out, OP_VREC, 0, it);
+      add(out, OP_VREC, vrec_d, it);
     }
   }
 

@@ -95,6 +95,9 @@ __device__ __forceinline__ void st(dstate* p, int i, df64 v) {
   const df64 c = canonical(v);
   p[i] = dstate{c.hi, c.lo};
 }
+// a value as a store of the state keeps it (the FP64 state's stores cut lo)
+__device__ __forceinline__ float as_stored(float v) { return v; }
+__device__ __forceinline__ df64 as_stored(df64 v) { return canonical(v); }
 // two neighbouring elements e, e + 1 (e even) in one vector store
 __device__ __forceinline__ void st2(float* p, int e, float a, float b) {
   *reinterpret_cast<float2*>(p + e) = make_float2(a, b);
@@ -1082,12 +1085,16 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
 }
 
 // velocity from the transported momenta, then the second half kick S(dt/2); NC cells
-// per thread as in el_source
-template <class T, int NC>
+// per thread as in el_source.  KICK2: the first sub-cycle of a finest level, whose
+// second sub-cycle follows with nothing in between that changes the level: the
+// second sub-cycle's first kick S(dt/2) is applied here too, as el_source computes it
+// from the stored velocity (so with the same bits), and the momenta its transport
+// starts from are written; that sub-cycle runs no kick of its own.
+template <class T, int NC, int KICK2>
 __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b, const Scratch& S,
                                                const Arith<T>* __restrict__ dtp, Arith<T> gm1,
                                                const Bg<Arith<T>>& bg, const Geo<Arith<T>>& g,
-                                               int fused, const unsigned* el) {
+                                               int fused, int write_pi, const unsigned* el) {
   using C = Arith<T>;
   int c[NC], c3[NC][3];
   bool ok[NC];
@@ -1135,12 +1142,22 @@ __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b,
     if (!ok[n]) continue;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      if (c3[n][d] < 1) continue;
+      if (c3[n][d] < 1) {
+        if (KICK2 && write_pi) ((Arith<T>*)S.pi[d])[c[n]] = C(0.f);
+        continue;
+      }
       C drf = halve(rm[n][d] + rc[n]);
       C rinv = hdiv(C(1.f), bg.rho0 + drf);
       C v = (pv[n][d] - bg.V[d] * drf) * rinv;
       C acc = (gm1 * (ec[n] - em[n][d]) * rinv + (fc[n] - fm[n][d])) * g.inv_dx[d];
-      st((St<T>*)L.q[F_VX + d], c[n], v - h * acc);
+      C vn = v - h * acc;
+      if (KICK2) {
+        const C rf = bg.rho0 + drf;
+        const C acc2 = (hdiv(gm1 * (ec[n] - em[n][d]), rf) + (fc[n] - fm[n][d])) * g.inv_dx[d];
+        vn = as_stored(vn) - h * acc2;
+        if (write_pi) st((Arith<T>*)S.pi[d], c[n], bg.rho0 * vn + drf * (bg.V[d] + vn));
+      }
+      st((St<T>*)L.q[F_VX + d], c[n], vn);
     }
     if (fused) {
       rhoA[c[n]] = rc_s[n];
@@ -1999,9 +2016,9 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
     el_visc_q<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.av, it.bg, it.g, tid);
   else if (OP == OP_VISC_V)
     el_visc_v<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.flags & FL_WRITE_PI, it.bg, it.g, tid);
-  else if (OP == OP_VREC)
-    el_vrec_source<T, NC>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.gm1, it.bg, it.g,
-                          it.flags & FL_FUSED, el);
+  else if (OP == OP_VREC)  // D = 1: with the next sub-cycle's first kick
+    el_vrec_source<T, NC, D>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.gm1, it.bg, it.g,
+                             it.flags & FL_FUSED, it.flags & FL_WRITE_PI, el);
   else if (OP == OP_BC)
     el_bc_axis<T>(it.L, D, it.bc_lo, it.bc_hi, (T)it.V[0], (T)it.V[1], (T)it.V[2], tid);
   else if (OP == OP_COMMUP)
@@ -2186,7 +2203,10 @@ int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, in
     DFN_OPD(OP_TFLUX)
     DFN_OPD(OP_TMOM)
     DFN_OPD(OP_TUPDATE)
-    DFN_OP(OP_VREC)
+    case OP_VREC:  // d = 1: with the next sub-cycle's first kick
+      if (d == 0) launch_one<T, OP_VREC, 0>(items, starts, nitems, nchunks, grid, st, host_item);
+      if (d == 1) launch_one<T, OP_VREC, 1>(items, starts, nitems, nchunks, grid, st, host_item);
+      break;
     DFN_OPD(OP_BC)
     DFN_OP(OP_COMMUP)
     DFN_OP(OP_COMMMEAN)
