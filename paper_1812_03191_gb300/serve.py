@@ -106,10 +106,13 @@ def summarize(results, t_begin, t_end):
 class Server:
     def __init__(self, budget_bytes, precision=binding.DF_FP32_STATE, tol=1e-3, step_cap=4000,
                  device=0, stream=None, tiles=None, check_every=8, keep_history=False,
-                 max_slots=None):
+                 max_slots=None, transport=binding.TRANSPORT_AUTO):
         """max_slots: at most this many runs at once (1: one request at a time, the
-        sequential baseline with the same stepping and stopping machinery)"""
+        sequential baseline with the same stepping and stopping machinery);
+        transport: the pool's transport kernels (binding.TRANSPORT_*)"""
         self.pool = binding.Pool(budget_bytes, precision=precision, device=device, stream=stream)
+        if transport != binding.TRANSPORT_AUTO:
+            self.pool.set_transport(transport)
         self.max_slots = max_slots
         self.budget = budget_bytes
         self.precision = precision
@@ -262,11 +265,12 @@ def solve_one(spec, precision, tol, step_cap, device=0, stream=None):
 
 
 def serve_sequential(requests, budget_bytes, precision=binding.DF_FP64, tol=1e-3,
-                     step_cap=4000, keep_history=False, tiles=None):
+                     step_cap=4000, keep_history=False, tiles=None,
+                     transport=binding.TRANSPORT_AUTO):
     """Sequential baseline on the serving machinery: one request at a time, FIFO, each
     alone on the GPU with the same batched stepping and stopping rule."""
     srv = Server(budget_bytes, precision=precision, tol=tol, step_cap=step_cap,
-                 keep_history=keep_history, max_slots=1, tiles=tiles)
+                 keep_history=keep_history, max_slots=1, tiles=tiles, transport=transport)
     try:
         return srv.run(requests)
     finally:
