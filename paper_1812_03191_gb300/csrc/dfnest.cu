@@ -707,12 +707,16 @@ struct Builder {
       add(out, OP_VISC_V, 0, it);
     }
     if (P.hydro_on || P.L != 0.0 || P.chi > 0.0) add(out, OP_COMPRESS, 0, it);
+    const bool fused_tr =
+        sweeps_fused(transport, sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE, it.L, pool);
+    // before the separate transport kernels the diffusion also forms the x sweep's
+    // e/rho (in Scratch::w[0]), in place of that sweep's preparation kernel
+    const bool eps_x = P.chi > 0.0 && P.hydro_on && !fused_tr;
     if (P.chi > 0.0) {
       if (it.L.is_child) add(out, OP_FRONTIER_DIFF, 0, it);
-      add(out, OP_DIFFUSE, 0, it);
+      add(out, OP_DIFFUSE, eps_x ? 1 : 0, it);
     }
-    if (P.hydro_on &&
-        sweeps_fused(transport, sizeof(T) == 8 ? DF_FP64 : DF_FP32_STATE, it.L, pool)) {
+    if (P.hydro_on && fused_tr) {
       for (int d = 0; d < 3; ++d) {
         add(out, OP_SWEEP, d, it);
       }
@@ -726,13 +730,14 @@ struct Builder {
       // momentum fluxes read v, and its preparation forms e/rho only.  The y and z
       // sweeps divide the updated momenta.
       for (int d = 0; d < 3; ++d) {
-        Item<T> tp = it, tm = it;
+        Item<T> tp = it, tm = it, tf = it;
         if (d == 0) {
           tp.flags |= FL_EPS_ONLY;
           for (int m = 0; m < 3; ++m) tm.S.w[m] = it.L.q[F_VX + m];
+          if (eps_x) tf.S.eps = it.S.w[0];
         }
-        add(out, OP_TPREP, 0, tp);
-        add(out, OP_TFLUX, d, it);
+        if (d > 0 || !eps_x) add(out, OP_TPREP, 0, tp);
+        add(out, OP_TFLUX, d, tf);
         add(out, OP_TMOM, d, tm);
         add(out, OP_TUPDATE, d, it);
       }

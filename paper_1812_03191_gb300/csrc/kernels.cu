@@ -463,20 +463,27 @@ __device__ __forceinline__ Arith<T> diff_flux(const LevelView& L, const Geo<Arit
   return -chi * rf * (ld(eps, f) - ld(eps, m)) * g.dcoef[d] * dt;
 }
 
-template <class T, int NC>
+// EPSX: the separate transport kernels follow, and the x sweep's preparation (e/rho
+// of the diffused state) is done here: written to Scratch::w[0] (a plane the x sweep
+// does not use otherwise; neighbours still read Scratch::eps in this launch), for
+// every box cell, from e as stored, so with the bits el_tprep would give.
+template <class T, int NC, int EPSX>
 __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, const Scratch& S,
                                            const Arith<T>* __restrict__ dtp, Arith<T> chi,
                                            Arith<T> rho0, int dfr, const Geo<Arith<T>>& g,
-                                           const unsigned* el) {
+                                           const Bg<Arith<T>>& bg, const unsigned* el) {
   using C = Arith<T>;
-  int c[NC], c3[NC][3];
-  bool ok[NC];
+  int c[NC], c3[NC][3], ce[NC];
+  bool ok[NC], edge[NC];
 #pragma unroll
   for (int n = 0; n < NC; ++n) {
     int i, j, k;
-    ok[n] = decode(b, el[n], i, j, k) && i >= 1 && j >= 1 && k >= 1 && i < L.s[0] - 1 &&
-            j < L.s[1] - 1 && k < L.s[2] - 1;
-    if (NC == 1 && !ok[n]) return;
+    const bool in = decode(b, el[n], i, j, k);
+    ok[n] = in && i >= 1 && j >= 1 && k >= 1 && i < L.s[0] - 1 && j < L.s[1] - 1 &&
+            k < L.s[2] - 1;
+    edge[n] = EPSX && in && !ok[n];
+    if (NC == 1 && !ok[n] && !edge[n]) return;
+    ce[n] = in ? cidx(L, i, j, k) : 0;
     if (!ok[n]) i = j = k = 1;
     c[n] = cidx(L, i, j, k);
     c3[n][0] = i;
@@ -519,7 +526,17 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
     C div = C(0.f);
 #pragma unroll
     for (int d = 0; d < 3; ++d) div += q[n][d][1] - q[n][d][0];
-    if (ok[n]) st(e, c[n], ev[n] - div * g.inv_vol);
+    if (ok[n]) {
+      const C en = ev[n] - div * g.inv_vol;
+      st(e, c[n], en);
+      if (EPSX) {
+        const C rc = ld(rho, c[n]);
+        st((Arith<T>*)S.w[0], c[n], hdiv(as_stored(en) - bg.eps0 * rc, bg.rho0 + rc));
+      }
+    } else if (edge[n]) {
+      const C rc = ld(rho, ce[n]);
+      st((Arith<T>*)S.w[0], ce[n], hdiv(ld(e, ce[n]) - bg.eps0 * rc, bg.rho0 + rc));
+    }
   }
 }
 
@@ -2001,9 +2018,9 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
   else if (OP == OP_FRONTIER_DIFF)
     el_frontier_diff<T>(it.L, it.S, (const Arith<T>*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
                         it.sub, tid);
-  else if (OP == OP_DIFFUSE)
-    el_diffuse<T, NC>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR,
-                      it.g, el);
+  else if (OP == OP_DIFFUSE)  // D = 1: with the x sweep's preparation
+    el_diffuse<T, NC, D>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.chi, it.bg.rho0,
+                         it.flags & FL_DFR, it.g, it.bg, el);
   else if (OP == OP_TPREP)
     el_tprep<T>(it.L, it.b, it.S, it.bg, it.flags & FL_EPS_ONLY, tid);
   else if (OP == OP_TFLUX)
@@ -2198,7 +2215,10 @@ int launch_batch(int op, int d, const Item<T>* items, const unsigned* starts, in
     DFN_OP(OP_SOURCE)
     DFN_OP(OP_COMPRESS)
     DFN_OP(OP_FRONTIER_DIFF)
-    DFN_OP(OP_DIFFUSE)
+    case OP_DIFFUSE:  // d = 1: with the x sweep's preparation
+      if (d == 0) launch_one<T, OP_DIFFUSE, 0>(items, starts, nitems, nchunks, grid, st, host_item);
+      if (d == 1) launch_one<T, OP_DIFFUSE, 1>(items, starts, nitems, nchunks, grid, st, host_item);
+      break;
     DFN_OP(OP_TPREP)
     DFN_OPD(OP_TFLUX)
     DFN_OPD(OP_TMOM)
