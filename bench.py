@@ -132,8 +132,10 @@ class ClockSampler:
 ARRAYS_PER_ELEM = {
     "source": 12,        # rho, e, phi, v3 -> v3, pi3
     "compress_lum": 8,   # e, v3, rho, lumw -> e, e/rho
-    "diffuse": 4,        # rho, e/rho, e -> e
-    "tprep": 7,          # rho, e, pi3 -> e/rho, w3 (9); the x sweep's: rho, e -> e/rho (3)
+    "diffuse": 4,        # rho, e/rho, e -> e (+1 before separate transport kernels: the
+                         # x sweep's e/rho, whose preparation kernel then is not launched)
+    "tprep": 9,          # rho, e, pi3 -> e/rho, w3: the y and z sweeps' (the workloads
+                         # all diffuse, so the x sweep's comes from the diffusion)
     "tflux": 5,          # rho, e/rho, v_d -> F, E
     "tmom": 8,           # w3, F, v_d -> P3
     "tupdate": 15,       # F, E, P3, rho, e, pi3 -> rho, e, pi3
@@ -171,6 +173,7 @@ def bytes_per_launch(cfg, kind, esz, fused=False):
     n, G = cfg["n"], cfg["G"]
     if kind in ARRAYS_PER_ELEM:
         arrays = ARRAYS_PER_ELEM[kind] + (2 if fused and kind == "vrec_source" else 0)
+        arrays += 1 if kind == "diffuse" and not fused else 0
         return arrays * esz * sum(boxes) / len(boxes)
     if kind == "commup":  # write every fine ghost element, read each coarse host once
         return 5 * esz * (((n + 2 * G) ** 3 - n**3) + (n // 2 + G + 2) ** 3)
