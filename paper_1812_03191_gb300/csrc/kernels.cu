@@ -95,6 +95,23 @@ __device__ __forceinline__ void st(dstate* p, int i, df64 v) {
   const df64 c = canonical(v);
   p[i] = dstate{c.hi, c.lo};
 }
+__device__ __forceinline__ bool is0(float v) { return v == 0.f; }
+__device__ __forceinline__ bool is0(df64 v) { return v.hi == 0.f; }
+// Sums and products with a per-item constant k that is often zero (the background
+// wind has one nonzero component): in double-float the operation is skipped when k is
+// 0, which gives the same value (a normalised pair plus zero is that pair); in FP32
+// the plain expression.  x + k, and x - k y:
+__device__ __forceinline__ float add_k(float x, float k) { return k + x; }
+__device__ __forceinline__ df64 add_k(df64 x, df64 k) { return k.hi == 0.f ? x : k + x; }
+__device__ __forceinline__ float sub_ky(float x, float k, float y) { return x - k * y; }
+__device__ __forceinline__ df64 sub_ky(df64 x, df64 k, df64 y) {
+  return k.hi == 0.f ? x : x - k * y;
+}
+// k y + z
+__device__ __forceinline__ float ky_add(float k, float y, float z) { return k * y + z; }
+__device__ __forceinline__ df64 ky_add(df64 k, df64 y, df64 z) {
+  return k.hi == 0.f ? z : k * y + z;
+}
 // a value as a store of the state keeps it (the FP64 state's stores cut lo)
 __device__ __forceinline__ float as_stored(float v) { return v; }
 __device__ __forceinline__ df64 as_stored(df64 v) { return canonical(v); }
@@ -273,7 +290,7 @@ __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, cons
         C vn = vv[n][d] - h * acc;
         st((St<T>*)L.q[F_VX + d], c[n], vn);
         // momentum deviation: rf (V + dv) - rho0 V
-        if (write_pi) st((Arith<T>*)S.pi[d], c[n], bg.rho0 * vn + drf * (bg.V[d] + vn));
+        if (write_pi) st((Arith<T>*)S.pi[d], c[n], bg.rho0 * vn + drf * add_k(vn, bg.V[d]));
       } else if (write_pi) {
         ((Arith<T>*)S.pi[d])[c[n]] = C(0.f);
       }
@@ -451,16 +468,21 @@ __device__ __forceinline__ void fr_sums(const LevelView& L, const DevScalars* ds
 
 
 // --------------------------------------------------------------- diffusion
-// energy moved in +d across a face during dt: -chi rho_f d(e/rho)/dx * area * dt
+// energy moved in +d across a face during dt: -chi rho_f d(e/rho)/dx * area * dt,
+// as rho_f (e/rho difference) K_d with K_d = (-chi dt) area_d / dx_d (dkoef), one
+// coefficient per axis instead of three products per face
 template <class T>
-__device__ __forceinline__ Arith<T> diff_flux(const LevelView& L, const Geo<Arith<T>>& g,
-                                              const St<T>* __restrict__ rho,
+__device__ __forceinline__ Arith<T> diff_flux(const LevelView& L, const St<T>* __restrict__ rho,
                                               const Arith<T>* __restrict__ eps, int f, int d,
-                                              Arith<T> chi, Arith<T> dt, Arith<T> rho0, int dfr) {
+                                              Arith<T> K, Arith<T> rho0, int dfr) {
   using C = Arith<T>;
   int m = f - L.st[d];
   C rf = dfr ? rho0 : rho0 + halve(ld(rho, m) + ld(rho, f));
-  return -chi * rf * (ld(eps, f) - ld(eps, m)) * g.dcoef[d] * dt;
+  return rf * (ld(eps, f) - ld(eps, m)) * K;
+}
+template <class C>
+__device__ __forceinline__ C dkoef(const Geo<C>& g, C chi, C dt, int d) {
+  return (-chi * dt) * g.dcoef[d];
 }
 
 // EPSX: the separate transport kernels follow, and the x sweep's preparation (e/rho
@@ -498,8 +520,9 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
   for (int n = 0; n < NC; ++n)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      q[n][d][0] = diff_flux<T>(L, g, rho, eps, c[n], d, chi, dt, rho0, dfr);
-      q[n][d][1] = diff_flux<T>(L, g, rho, eps, c[n] + L.st[d], d, chi, dt, rho0, dfr);
+      const C K = dkoef(g, chi, dt, d);
+      q[n][d][0] = diff_flux<T>(L, rho, eps, c[n], d, K, rho0, dfr);
+      q[n][d][1] = diff_flux<T>(L, rho, eps, c[n] + L.st[d], d, K, rho0, dfr);
     }
   if (L.has_child) {
 #pragma unroll
@@ -566,8 +589,8 @@ __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scrat
   f3[t2] = L.G + 2 * b + v;
   const int f = (f3[2] * L.s[1] + f3[1]) * L.s[0] + f3[0];
   fr_put(L, d, fd, f3[t1], f3[t2], 2, sub,
-         as_double(diff_flux<T>(L, g, (const St<T>*)L.q[F_RHO], (const Arith<T>*)S.eps, f, d, chi,
-                                dt, rho0, dfr)));
+         as_double(diff_flux<T>(L, (const St<T>*)L.q[F_RHO], (const Arith<T>*)S.eps, f, d,
+                                dkoef(g, chi, dt, d), rho0, dfr)));
 }
 
 // --------------------------------------------------------------- transport
@@ -589,7 +612,7 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
     if (c3[m] >= 1) {
       // Pi/rho_face - V = (dPi - V drf)/(rho0 + drf)
       C drf = halve(ld(rho, c - L.st[m]) + rc);
-      wv = hdiv(ld((const Arith<T>*)S.pi[m], c) - bg.V[m] * drf, bg.rho0 + drf);
+      wv = hdiv(sub_ky(ld((const Arith<T>*)S.pi[m], c), bg.V[m], drf), bg.rho0 + drf);
     }
     st((Arith<T>*)S.w[m], c, wv);
   }
@@ -614,13 +637,13 @@ __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const
     const int sd = L.st[d];
     const C Adt = g.area[d] * dt;
     const C du = ld((const St<T>*)L.q[F_VX + d], c);
-    const C u = bg.V[d] + du;
+    const C u = add_k(du, bg.V[d]);
     const C cour = u * (dt * g.inv_dx[d]);
-    const C F0 = bg.rho0 * bg.V[d] * Adt;
+    const C F0 = is0(bg.V[d]) ? C(0.f) : bg.rho0 * bg.V[d] * Adt;
     C drs = upwind((const St<T>*)L.q[F_RHO], c, sd, u, cour);
     Fv = (bg.rho0 * du + drs * u) * Adt;        // F - rho0 V_d A dt
     C des = upwind((const Arith<T>*)S.eps, c, sd, u, cour);
-    Ev = bg.eps0 * Fv + des * (F0 + Fv);        // E - eps0 rho0 V_d A dt
+    Ev = bg.eps0 * Fv + des * add_k(Fv, F0);        // E - eps0 rho0 V_d A dt
   }
   st((Arith<T>*)S.F, c, Fv);
   st((Arith<T>*)S.E, c, Ev);
@@ -647,25 +670,25 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
   const St<T>* __restrict__ vd = (const St<T>*)L.q[F_VX + d];
   const Arith<T>* __restrict__ F = (const Arith<T>*)S.F;
   const C dtdx = dt * g.inv_dx[d];
-  const C F0 = bg.rho0 * bg.V[d] * (g.area[d] * dt);
+  const C F0 = is0(bg.V[d]) ? C(0.f) : bg.rho0 * bg.V[d] * (g.area[d] * dt);
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     C P = C(0.f);
     if (m == d) {
       if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
-        C uc = bg.V[d] + halve(ld(vd, c) + ld(vd, c + sd));
+        C uc = add_k(halve(ld(vd, c) + ld(vd, c + sd)), bg.V[d]);
         C Fc = halve(ld(F, c) + ld(F, c + sd));
         C ws = d == 0 ? upwind((const St<T>*)S.w[m], c + sd, sd, uc, uc * dtdx)
                       : upwind((const Arith<T>*)S.w[m], c + sd, sd, uc, uc * dtdx);
-        P = bg.V[m] * Fc + ws * (F0 + Fc);
+        P = ky_add(bg.V[m], Fc, ws * add_k(Fc, F0));
       }
     } else if (c3[d] >= 2 && c3[d] < L.s[d] - 1 && c3[m] >= 1) {
       const int sm = L.st[m];
-      C ue = bg.V[d] + halve(ld(vd, c - sm) + ld(vd, c));
+      C ue = add_k(halve(ld(vd, c - sm) + ld(vd, c)), bg.V[d]);
       C Fe = halve(ld(F, c - sm) + ld(F, c));
       C ws = d == 0 ? upwind((const St<T>*)S.w[m], c, sd, ue, ue * dtdx)
                     : upwind((const Arith<T>*)S.w[m], c, sd, ue, ue * dtdx);
-      P = bg.V[m] * Fe + ws * (F0 + Fe);
+      P = ky_add(bg.V[m], Fe, ws * add_k(Fe, F0));
     }
     st((Arith<T>*)S.P[m], c, P);
   }
@@ -1165,14 +1188,14 @@ __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b,
       }
       C drf = halve(rm[n][d] + rc[n]);
       C rinv = hdiv(C(1.f), bg.rho0 + drf);
-      C v = (pv[n][d] - bg.V[d] * drf) * rinv;
+      C v = sub_ky(pv[n][d], bg.V[d], drf) * rinv;
       C acc = (gm1 * (ec[n] - em[n][d]) * rinv + (fc[n] - fm[n][d])) * g.inv_dx[d];
       C vn = v - h * acc;
       if (KICK2) {
         const C rf = bg.rho0 + drf;
         const C acc2 = (hdiv(gm1 * (ec[n] - em[n][d]), rf) + (fc[n] - fm[n][d])) * g.inv_dx[d];
         vn = as_stored(vn) - h * acc2;
-        if (write_pi) st((Arith<T>*)S.pi[d], c[n], bg.rho0 * vn + drf * (bg.V[d] + vn));
+        if (write_pi) st((Arith<T>*)S.pi[d], c[n], bg.rho0 * vn + drf * add_k(vn, bg.V[d]));
       }
       st((St<T>*)L.q[F_VX + d], c[n], vn);
     }
