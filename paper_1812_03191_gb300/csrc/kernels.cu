@@ -694,47 +694,72 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
   }
 }
 
-template <class T, int d>
+// Every load first, then the arithmetic and the stores (a load never waits for a store
+// it cannot be reordered with); NC cells per thread as in the compression (one here).
+template <class T, int d, int NC>
 __device__ __forceinline__ void el_tupdate(const LevelView& L, const Box& b, const Scratch& S,
-                                           const Geo<Arith<T>>& g, unsigned tid) {
+                                           const Geo<Arith<T>>& g, const unsigned* el) {
   using C = Arith<T>;
-  int i, j, k;
-  if (!decode(b, tid, i, j, k)) return;
-  const int c = cidx(L, i, j, k);
-  const int c3[3] = {i, j, k};
+  int c[NC], c3[NC][3];
+  bool ok[NC];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    int i, j, k;
+    ok[n] = decode(b, el[n], i, j, k);
+    if (NC == 1 && !ok[n]) return;
+    if (!ok[n]) i = j = k = 3;  // an in-bounds stand-in (arrays hold 2 G >= 6 ghosts)
+    c[n] = cidx(L, i, j, k);
+    c3[n][0] = i;
+    c3[n][1] = j;
+    c3[n][2] = k;
+  }
   const int sd = L.st[d];
   const C iv = g.inv_vol;
-  if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
-    C Flo = ld((const Arith<T>*)S.F, c), Fhi = ld((const Arith<T>*)S.F, c + sd);
-    C Elo = ld((const Arith<T>*)S.E, c), Ehi = ld((const Arith<T>*)S.E, c + sd);
-    if (L.has_child && near_frontier(L, d, c3[d])) {
-      int slot, f3[3] = {c3[0], c3[1], c3[2]};
-      int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
-      if (side >= 0) {
-        Flo = from_double<C>(L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot]);
-        Elo = from_double<C>(L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot]);
-      }
-      f3[d] += 1;
-      side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
-      if (side >= 0) {
-        Fhi = from_double<C>(L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot]);
-        Ehi = from_double<C>(L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot]);
-      }
+  St<T>* rho = (St<T>*)L.q[F_RHO];
+  St<T>* e = (St<T>*)L.q[F_E];
+  C Flo[NC], Fhi[NC], Elo[NC], Ehi[NC], rv[NC], ev[NC], pv[NC][3], Pa[NC][3], Pb[NC][3];
+#pragma unroll
+  for (int n = 0; n < NC; ++n) {
+    Flo[n] = ld((const Arith<T>*)S.F, c[n]);
+    Fhi[n] = ld((const Arith<T>*)S.F, c[n] + sd);
+    Elo[n] = ld((const Arith<T>*)S.E, c[n]);
+    Ehi[n] = ld((const Arith<T>*)S.E, c[n] + sd);
+    rv[n] = ld(rho, c[n]);
+    ev[n] = ld(e, c[n]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const Arith<T>* P = (const Arith<T>*)S.P[m];
+      pv[n][m] = ld((const Arith<T>*)S.pi[m], c[n]);
+      Pa[n][m] = ld(P, m == d ? c[n] - sd : c[n]);
+      Pb[n][m] = ld(P, m == d ? c[n] : c[n] + sd);
     }
-    St<T>* rho = (St<T>*)L.q[F_RHO];
-    St<T>* e = (St<T>*)L.q[F_E];
-    st(rho, c, ld(rho, c) - (Fhi - Flo) * iv);
-    st(e, c, ld(e, c) - (Ehi - Elo) * iv);
   }
 #pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    Arith<T>* pi = (Arith<T>*)S.pi[m];
-    const Arith<T>* P = (const Arith<T>*)S.P[m];
-    if (m == d) {
-      if (c3[d] >= 3 && c3[d] < L.s[d] - 2)
-        st(pi, c, ld(pi, c) - (ld(P, c) - ld(P, c - sd)) * iv);
-    } else if (c3[d] >= 2 && c3[d] < L.s[d] - 2 && c3[m] >= 1) {
-      st(pi, c, ld(pi, c) - (ld(P, c + sd) - ld(P, c)) * iv);
+  for (int n = 0; n < NC; ++n) {
+    if (!ok[n]) continue;
+    if (c3[n][d] >= 2 && c3[n][d] < L.s[d] - 2) {
+      if (L.has_child && near_frontier(L, d, c3[n][d])) {
+        int slot, f3[3] = {c3[n][0], c3[n][1], c3[n][2]};
+        int side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+        if (side >= 0) {
+          Flo[n] = from_double<C>(L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot]);
+          Elo[n] = from_double<C>(L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot]);
+        }
+        f3[d] += 1;
+        side = coarse_frontier(L, d, f3[0], f3[1], f3[2], slot);
+        if (side >= 0) {
+          Fhi[n] = from_double<C>(L.cacc[((2 * d + side) * 3 + 0) * L.cacc_slots + slot]);
+          Ehi[n] = from_double<C>(L.cacc[((2 * d + side) * 3 + 1) * L.cacc_slots + slot]);
+        }
+      }
+      st(rho, c[n], rv[n] - (Fhi[n] - Flo[n]) * iv);
+      st(e, c[n], ev[n] - (Ehi[n] - Elo[n]) * iv);
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const bool chg = m == d ? (c3[n][d] >= 3 && c3[n][d] < L.s[d] - 2)
+                              : (c3[n][d] >= 2 && c3[n][d] < L.s[d] - 2 && c3[n][m] >= 1);
+      if (chg) st((Arith<T>*)S.pi[m], c[n], pv[n][m] - (Pb[n][m] - Pa[n][m]) * iv);
     }
   }
 }
@@ -2051,7 +2076,7 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
   else if (OP == OP_TMOM)
     el_tmom<T, D>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.bg, it.g, tid);
   else if (OP == OP_TUPDATE)
-    el_tupdate<T, D>(it.L, it.b, it.S, it.g, tid);
+    el_tupdate<T, D, NC>(it.L, it.b, it.S, it.g, el);
   else if (OP == OP_VISC_Q)
     el_visc_q<T>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.av, it.bg, it.g, tid);
   else if (OP == OP_VISC_V)
