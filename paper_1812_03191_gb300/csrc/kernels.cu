@@ -604,18 +604,32 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
   const C rc = ld(rho, c);
-  st((Arith<T>*)S.eps, c, hdiv(ld((const St<T>*)L.q[F_E], c) - bg.eps0 * rc, bg.rho0 + rc));
-  if (eps_only) return;
+  const C ec = ld((const St<T>*)L.q[F_E], c);
+  if (eps_only) {
+    st((Arith<T>*)S.eps, c, hdiv(ec - bg.eps0 * rc, bg.rho0 + rc));
+    return;
+  }
+  // every load first, then the arithmetic and the stores
+  C rm[3], pm[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+    if (c3[m] >= 1) {
+      rm[m] = ld(rho, c - L.st[m]);
+      pm[m] = ld((const Arith<T>*)S.pi[m], c);
+    }
+  C wv[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
-    C wv = C(0.f);
+    wv[m] = C(0.f);
     if (c3[m] >= 1) {
       // Pi/rho_face - V = (dPi - V drf)/(rho0 + drf)
-      C drf = halve(ld(rho, c - L.st[m]) + rc);
-      wv = hdiv(sub_ky(ld((const Arith<T>*)S.pi[m], c), bg.V[m], drf), bg.rho0 + drf);
+      C drf = halve(rm[m] + rc);
+      wv[m] = hdiv(sub_ky(pm[m], bg.V[m], drf), bg.rho0 + drf);
     }
-    st((Arith<T>*)S.w[m], c, wv);
   }
+  st((Arith<T>*)S.eps, c, hdiv(ec - bg.eps0 * rc, bg.rho0 + rc));
+#pragma unroll
+  for (int m = 0; m < 3; ++m) st((Arith<T>*)S.w[m], c, wv[m]);
 }
 
 // mass and energy flux at d-faces 2 <= i_d < s_d - 1
@@ -671,6 +685,7 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
   const Arith<T>* __restrict__ F = (const Arith<T>*)S.F;
   const C dtdx = dt * g.inv_dx[d];
   const C F0 = is0(bg.V[d]) ? C(0.f) : bg.rho0 * bg.V[d] * (g.area[d] * dt);
+  C Pv[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
     C P = C(0.f);
@@ -690,8 +705,11 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
                     : upwind((const Arith<T>*)S.w[m], c, sd, ue, ue * dtdx);
       P = ky_add(bg.V[m], Fe, ws * add_k(Fe, F0));
     }
-    st((Arith<T>*)S.P[m], c, P);
+    Pv[m] = P;
   }
+  // the stores after every load of the three components
+#pragma unroll
+  for (int m = 0; m < 3; ++m) st((Arith<T>*)S.P[m], c, Pv[m]);
 }
 
 // Every load first, then the arithmetic and the stores (a load never waits for a store
