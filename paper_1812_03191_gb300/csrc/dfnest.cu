@@ -526,6 +526,7 @@ void fill_fin(const Run& r, DtFinal& fin) {
     fin.cost[l] = 0.0;
     fin.diff_lim[l] = INFINITY;
     for (int d = 0; d < 3; ++d) fin.cfl_dx[l][d] = 0.0;
+    for (int q = 0; q < 12; ++q) fin.kfac[l][q] = 0.0;
   }
   for (int l = 0; l < r.nl; ++l) {
     if (l > 0) pr *= r.xi[l - 1];
@@ -537,6 +538,12 @@ void fill_fin(const Run& r, DtFinal& fin) {
       fin.diff_lim[l] = r.P.cfl_diff / (2.0 * r.P.chi * sinv);
     }
     for (int d = 0; d < 3; ++d) fin.cfl_dx[l][d] = r.P.hydro_on ? r.P.cfl * v.dx[d] : 0.0;
+    for (int d = 0; d < 3; ++d) {
+      fin.kfac[l][K_ADT + d] = v.area[d];
+      fin.kfac[l][K_DTDX + d] = v.inv_dx[d];
+      fin.kfac[l][K_DIFF + d] = -r.P.chi * v.dcoef[d];
+      fin.kfac[l][K_F0 + d] = r.P.rho0 * r.P.V[d] * v.area[d];
+    }
     fin.cost[l] = (double)v.n[0] * v.n[1] * v.n[2];
   }
   fin.search = r.prm.xi_mode == 1 && r.nl > 1;
@@ -599,6 +606,7 @@ struct Builder {
     it.bg = make_bg<C>(r.P);
     it.g = make_geo<C>(it.L);
     it.dt = sizeof(T) == 8 ? (const void*)&r.ds->dtd[l] : (const void*)&r.ds->dtf[l];
+    it.kc = sizeof(T) == 8 ? (const void*)&r.ds->kd[l][0] : (const void*)&r.ds->kf[l][0];
     it.ds = r.ds;
     it.gm1 = to_arith<C>(r.P.gamma - 1.0);
     it.lum = to_arith<C>(r.P.L);

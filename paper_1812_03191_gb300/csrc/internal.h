@@ -128,6 +128,9 @@ struct Phys {
 // doubles per entry of a run's force history: F_x, F_y, F_z, t at the end of the step
 constexpr int kRingStride = 4;
 
+// the constants of a level step, DevScalars::kd / kf [level][K_* + axis]
+enum { K_ADT = 0, K_DTDX = 3, K_DIFF = 6, K_F0 = 9 };
+
 struct DevScalars {
   double dt;                  // current coarse step
   double t;                   // simulated time
@@ -138,6 +141,11 @@ struct DevScalars {
   double dtl[16];                // level step of each level: dt / prod_{m<l} xi_m
   float dtf[16];                 // the same in FP32
   df64 dtd[16];                  // and in double-float
+  // per level, the constants of its level step in the arithmetic types, each the
+  // product of its factor (DtFinal::kfac) and the level step, per axis d: A_d dt,
+  // dt / dx_d, -chi dt A_d / dx_d (diffusion), rho0 V_d A_d dt (background mass flux)
+  df64 kd[16][12];
+  float kf[16][12];
   int unhealthy;
   unsigned xi1;  // bit m set when the Eq. 55-56 search chose xi_m = 1 this coarse step
 };
@@ -223,6 +231,9 @@ struct DtFinal {
   double diff_lim[16];   // explicit-diffusion limit of each level
   double cfl_dx[16][3];  // cfl * dx_d (0 when hydro is off)
   double cost[16];       // Eq. 56 cost of a level step of each level (cells)
+  // per level and axis, the factors of the level step's constants (DevScalars::kd):
+  // area_d, 1/dx_d, -chi area_d/dx_d, rho0 V_d area_d
+  double kfac[16][12];
   int search;            // 1: choose xi_m in {1, 2} each coarse step (Eq. 55-56)
   int pad;
 };
@@ -338,6 +349,7 @@ struct __align__(16) Item {
   Bg<Arith<T>> bg;
   Geo<Arith<T>> g;
   const void* dt;       // this level's step, Arith<T>
+  const void* kc;       // this level step's constants (DevScalars::kd / kf), Arith<T>
   DevScalars* ds;       // the run's scalars
   const DtFinal* fin;   // OP_DT_FINAL constants
   double* partials;     // force partials (this level's first, or the run's for the final sum)

@@ -469,8 +469,8 @@ __device__ __forceinline__ void fr_sums(const LevelView& L, const DevScalars* ds
 
 // --------------------------------------------------------------- diffusion
 // energy moved in +d across a face during dt: -chi rho_f d(e/rho)/dx * area * dt,
-// as rho_f (e/rho difference) K_d with K_d = (-chi dt) area_d / dx_d (dkoef), one
-// coefficient per axis instead of three products per face
+// as rho_f (e/rho difference) K_d with K_d = -chi dt area_d / dx_d, one coefficient
+// per level step and axis (a level-step constant) instead of three products per face
 template <class T>
 __device__ __forceinline__ Arith<T> diff_flux(const LevelView& L, const St<T>* __restrict__ rho,
                                               const Arith<T>* __restrict__ eps, int f, int d,
@@ -480,10 +480,6 @@ __device__ __forceinline__ Arith<T> diff_flux(const LevelView& L, const St<T>* _
   C rf = dfr ? rho0 : rho0 + halve(ld(rho, m) + ld(rho, f));
   return rf * (ld(eps, f) - ld(eps, m)) * K;
 }
-template <class C>
-__device__ __forceinline__ C dkoef(const Geo<C>& g, C chi, C dt, int d) {
-  return (-chi * dt) * g.dcoef[d];
-}
 
 // EPSX: the separate transport kernels follow, and the x sweep's preparation (e/rho
 // of the diffused state) is done here: written to Scratch::w[0] (a plane the x sweep
@@ -491,7 +487,7 @@ __device__ __forceinline__ C dkoef(const Geo<C>& g, C chi, C dt, int d) {
 // every box cell, from e as stored, so with the bits el_tprep would give.
 template <class T, int NC, int EPSX>
 __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, const Scratch& S,
-                                           const Arith<T>* __restrict__ dtp, Arith<T> chi,
+                                           const Arith<T>* __restrict__ kc,
                                            Arith<T> rho0, int dfr, const Geo<Arith<T>>& g,
                                            const Bg<Arith<T>>& bg, const unsigned* el) {
   using C = Arith<T>;
@@ -512,7 +508,6 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
     c3[n][1] = j;
     c3[n][2] = k;
   }
-  const C dt = dtp[0];
   const St<T>* __restrict__ rho = (const St<T>*)L.q[F_RHO];
   const Arith<T>* __restrict__ eps = (const Arith<T>*)S.eps;
   C q[NC][3][2];  // flux through the lower and the upper d-face
@@ -520,7 +515,7 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
   for (int n = 0; n < NC; ++n)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const C K = dkoef(g, chi, dt, d);
+      const C K = kc[K_DIFF + d];
       q[n][d][0] = diff_flux<T>(L, rho, eps, c[n], d, K, rho0, dfr);
       q[n][d][1] = diff_flux<T>(L, rho, eps, c[n] + L.st[d], d, K, rho0, dfr);
     }
@@ -568,9 +563,8 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
 // inside the diffusion kernel the record code would cost that kernel occupancy)
 template <class T>
 __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scratch& S,
-                                                 const Arith<T>* __restrict__ dtp, Arith<T> chi,
-                                                 Arith<T> rho0, int dfr,
-                                                 const Geo<Arith<T>>& g, int sub, unsigned tid) {
+                                                 const Arith<T>* __restrict__ kc,
+                                                 Arith<T> rho0, int dfr, int sub, unsigned tid) {
   using C = Arith<T>;
   // one thread per fine face: (side, coarse slot, fine face u, v of the slot)
   if (tid >= 24u * (unsigned)L.acc_slots) return;
@@ -581,7 +575,6 @@ __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scrat
   const int h1 = L.n[t1] >> 1;
   if (slot >= h1 * (L.n[t2] >> 1)) return;
   const int a = slot % h1, b = slot / h1;
-  const C dt = dtp[0];
   const int fd = (side & 1) ? L.G + L.n[d] : L.G;
   int f3[3];
   f3[d] = fd;
@@ -590,7 +583,7 @@ __device__ __forceinline__ void el_frontier_diff(const LevelView& L, const Scrat
   const int f = (f3[2] * L.s[1] + f3[1]) * L.s[0] + f3[0];
   fr_put(L, d, fd, f3[t1], f3[t2], 2, sub,
          as_double(diff_flux<T>(L, (const St<T>*)L.q[F_RHO], (const Arith<T>*)S.eps, f, d,
-                                dkoef(g, chi, dt, d), rho0, dfr)));
+                                kc[K_DIFF + d], rho0, dfr)));
 }
 
 // --------------------------------------------------------------- transport
@@ -637,9 +630,8 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
 // fixed kernel-parameter operand instead of a dynamically indexed load
 template <class T, int d>
 __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const Scratch& S,
-                                         const Arith<T>* __restrict__ dtp,
-                                         const Bg<Arith<T>>& bg, const Geo<Arith<T>>& g,
-                                         int sub, unsigned tid) {
+                                         const Arith<T>* __restrict__ kc,
+                                         const Bg<Arith<T>>& bg, int sub, unsigned tid) {
   using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
@@ -647,13 +639,12 @@ __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const
   const int c3[3] = {i, j, k};
   C Fv = C(0.f), Ev = C(0.f);
   if (c3[d] >= 2 && c3[d] < L.s[d] - 1) {
-    const C dt = dtp[0];
     const int sd = L.st[d];
-    const C Adt = g.area[d] * dt;
+    const C Adt = kc[K_ADT + d];
     const C du = ld((const St<T>*)L.q[F_VX + d], c);
     const C u = add_k(du, bg.V[d]);
-    const C cour = u * (dt * g.inv_dx[d]);
-    const C F0 = is0(bg.V[d]) ? C(0.f) : bg.rho0 * bg.V[d] * Adt;
+    const C cour = u * kc[K_DTDX + d];
+    const C F0 = is0(bg.V[d]) ? C(0.f) : kc[K_F0 + d];
     C drs = upwind((const St<T>*)L.q[F_RHO], c, sd, u, cour);
     Fv = (bg.rho0 * du + drs * u) * Adt;        // F - rho0 V_d A dt
     C des = upwind((const Arith<T>*)S.eps, c, sd, u, cour);
@@ -672,19 +663,18 @@ __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const
 // staggered momentum fluxes of sweep d (deviation: P - V_m rho0 V_d A dt)
 template <class T, int d>
 __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const Scratch& S,
-                                        const Arith<T>* __restrict__ dtp, const Bg<Arith<T>>& bg,
-                                        const Geo<Arith<T>>& g, unsigned tid) {
+                                        const Arith<T>* __restrict__ kc, const Bg<Arith<T>>& bg,
+                                        unsigned tid) {
   using C = Arith<T>;
   int i, j, k;
   if (!decode(b, tid, i, j, k)) return;
   const int c = cidx(L, i, j, k);
   const int c3[3] = {i, j, k};
-  const C dt = dtp[0];
   const int sd = L.st[d];
   const St<T>* __restrict__ vd = (const St<T>*)L.q[F_VX + d];
   const Arith<T>* __restrict__ F = (const Arith<T>*)S.F;
-  const C dtdx = dt * g.inv_dx[d];
-  const C F0 = is0(bg.V[d]) ? C(0.f) : bg.rho0 * bg.V[d] * (g.area[d] * dt);
+  const C dtdx = kc[K_DTDX + d];
+  const C F0 = is0(bg.V[d]) ? C(0.f) : kc[K_F0 + d];
   C Pv[3];
 #pragma unroll
   for (int m = 0; m < 3; ++m) {
@@ -1728,6 +1718,12 @@ __device__ __forceinline__ void el_dt_finalize(DevScalars* ds, int n_levels, con
     ds->dtl[l] = dl;
     ds->dtf[l] = (float)dl;
     ds->dtd[l] = to_df64(dl);
+    // the level step's constants, once here instead of in every thread
+    for (int q = 0; q < 12; ++q) {
+      const double k = fin.kfac[l][q] * dl;
+      ds->kd[l][q] = to_df64(k);
+      ds->kf[l][q] = (float)k;
+    }
   }
 }
 
@@ -2082,17 +2078,17 @@ __device__ __forceinline__ void run_op(const Item<T>& it, unsigned tid) {
                            el);
   }
   else if (OP == OP_FRONTIER_DIFF)
-    el_frontier_diff<T>(it.L, it.S, (const Arith<T>*)it.dt, it.chi, it.bg.rho0, it.flags & FL_DFR, it.g,
-                        it.sub, tid);
+    el_frontier_diff<T>(it.L, it.S, (const Arith<T>*)it.kc, it.bg.rho0, it.flags & FL_DFR, it.sub,
+                        tid);
   else if (OP == OP_DIFFUSE)  // D = 1: with the x sweep's preparation
-    el_diffuse<T, NC, D>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.chi, it.bg.rho0,
-                         it.flags & FL_DFR, it.g, it.bg, el);
+    el_diffuse<T, NC, D>(it.L, it.b, it.S, (const Arith<T>*)it.kc, it.bg.rho0, it.flags & FL_DFR,
+                         it.g, it.bg, el);
   else if (OP == OP_TPREP)
     el_tprep<T>(it.L, it.b, it.S, it.bg, it.flags & FL_EPS_ONLY, tid);
   else if (OP == OP_TFLUX)
-    el_tflux<T, D>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.bg, it.g, it.sub, tid);
+    el_tflux<T, D>(it.L, it.b, it.S, (const Arith<T>*)it.kc, it.bg, it.sub, tid);
   else if (OP == OP_TMOM)
-    el_tmom<T, D>(it.L, it.b, it.S, (const Arith<T>*)it.dt, it.bg, it.g, tid);
+    el_tmom<T, D>(it.L, it.b, it.S, (const Arith<T>*)it.kc, it.bg, tid);
   else if (OP == OP_TUPDATE)
     el_tupdate<T, D, NC>(it.L, it.b, it.S, it.g, el);
   else if (OP == OP_VISC_Q)
