@@ -95,6 +95,25 @@ __host__ __device__ __forceinline__ df64 operator/(df64 a, df64 b) {
 }
 
 // a times a power of two (exact, both parts scaled; no overflow or underflow)
+// A product and a quotient without the final renormalisation: the pair (p, e) of the
+// operators above before their fast_two_sum, which is exact, so the value and its error
+// are the same; e may reach about 2^-22 |p| instead of half an ulp of p.  Such a pair is
+// an operand of +, -, * and / (their error bounds hold with |lo| <= 2^-21 |hi|) and of
+// the sign tests (p carries the sign), never of canonical(), to_double() or an ordered
+// comparison.  Three instructions fewer each, where the result feeds more arithmetic.
+__host__ __device__ __forceinline__ df64 mul_u(df64 a, df64 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  return df64(p, fmaf(a.lo, b.hi, e));
+}
+__host__ __device__ __forceinline__ df64 div_u(df64 a, df64 b) {
+  const float r = rcp_est(b.hi);
+  const float q1 = a.hi * r;
+  const float rem = fmaf(-b.lo, q1, fmaf(-b.hi, q1, a.hi) + a.lo);
+  return df64(q1, rem * r);
+}
+
 __host__ __device__ __forceinline__ df64 scale(df64 a, float p2) {
   return df64(a.hi * p2, a.lo * p2);
 }

@@ -77,6 +77,10 @@ __device__ __forceinline__ double hdiv(double a, double b) {
 }
 __device__ __forceinline__ float hdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ df64 hdiv(df64 a, df64 b) { return a / b; }
+// product and quotient whose result only feeds more arithmetic: in double-float left
+// without the final renormalisation (mul_u, div_u in df64.h), in FP32 the plain ones
+__device__ __forceinline__ float mul_u(float a, float b) { return a * b; }
+__device__ __forceinline__ float div_u(float a, float b) { return __fdividef(a, b); }
 
 // The stencils' arithmetic type C = Arith<T> (internal.h): float for the FP32 state,
 // double-float for the FP64 state.  Loads convert the stored value to C, stores round
@@ -105,12 +109,18 @@ __device__ __forceinline__ float add_k(float x, float k) { return k + x; }
 __device__ __forceinline__ df64 add_k(df64 x, df64 k) { return k.hi == 0.f ? x : k + x; }
 __device__ __forceinline__ float sub_ky(float x, float k, float y) { return x - k * y; }
 __device__ __forceinline__ df64 sub_ky(df64 x, df64 k, df64 y) {
-  return k.hi == 0.f ? x : x - k * y;
+  return k.hi == 0.f ? x : x - mul_u(k, y);
 }
 // k y + z
 __device__ __forceinline__ float ky_add(float k, float y, float z) { return k * y + z; }
 __device__ __forceinline__ df64 ky_add(df64 k, df64 y, df64 z) {
-  return k.hi == 0.f ? z : k * y + z;
+  return k.hi == 0.f ? z : mul_u(k, y) + z;
+}
+// e/rho - e0/rho0 of a cell from its deviations, (de - eps0 drho)/(rho0 + drho): one
+// expression for every kernel that forms it, so that all give the same bits
+template <class C, class B>
+__device__ __forceinline__ C eps_dev(C de, C dr, const B& bg) {
+  return hdiv(de - mul_u(bg.eps0, dr), bg.rho0 + dr);
 }
 // a value as a store of the state keeps it (the FP64 state's stores cut lo)
 __device__ __forceinline__ float as_stored(float v) { return v; }
@@ -159,11 +169,12 @@ __device__ __forceinline__ bool lt0(float v) { return v < 0.f; }
 // interpolation): dl dr / (dl + dr) where dl dr > 0, else 0.  Callers fold the
 // factor 2 into their coefficients; scaling by 2 is exact, so the results equal
 // those of the full slope bit for bit.  When the product underflows to zero the
-// slope is zero, so the divisor dl + dr is never zero or subnormal.
+// slope is zero, so the divisor dl + dr is never zero or subnormal.  The product and
+// the quotient stay unnormalised (mul_u, div_u): the slope only feeds more arithmetic.
 template <class C>
 __device__ __forceinline__ C hslope(C dl, C dr) {
-  C pr = dl * dr;
-  return le0(pr) ? C(0.f) : hdiv(pr, dl + dr);
+  C pr = mul_u(dl, dr);
+  return le0(pr) ? C(0.f) : div_u(pr, dl + dr);
 }
 
 // The upwind side's value, slopes and coefficient are selected first, so one limiter
@@ -186,7 +197,7 @@ __device__ __forceinline__ C upwind_v(C qmm, C qm, C q0, C qp, C u, C cour) {
     dl = a - (up ? qmm : qm);
     dr = (up ? q0 : qp) - a;
   }
-  return a + ((up ? C(1.f) : C(-1.f)) - cour) * hslope(dl, dr);
+  return a + mul_u((up ? C(1.f) : C(-1.f)) - cour, hslope(dl, dr));
 }
 
 template <class P, class C>
@@ -286,11 +297,13 @@ __device__ __forceinline__ void el_source(const LevelView& L, const Box& b, cons
       if (c3[n][d] >= 1) {
         C drf = halve(rm[n][d] + rc[n]);
         C rf = bg.rho0 + drf;
-        C acc = (hdiv(gm1 * (ec[n] - em[n][d]), rf) + (fc[n] - fm[n][d])) * g.inv_dx[d];
-        C vn = vv[n][d] - h * acc;
+        C acc = mul_u(div_u(mul_u(gm1, ec[n] - em[n][d]), rf) + (fc[n] - fm[n][d]),
+                      g.inv_dx[d]);
+        C vn = vv[n][d] - mul_u(h, acc);
         st((St<T>*)L.q[F_VX + d], c[n], vn);
         // momentum deviation: rf (V + dv) - rho0 V
-        if (write_pi) st((Arith<T>*)S.pi[d], c[n], bg.rho0 * vn + drf * add_k(vn, bg.V[d]));
+        if (write_pi)
+          st((Arith<T>*)S.pi[d], c[n], mul_u(bg.rho0, vn) + mul_u(drf, add_k(vn, bg.V[d])));
       } else if (write_pi) {
         ((Arith<T>*)S.pi[d])[c[n]] = C(0.f);
       }
@@ -413,16 +426,16 @@ __device__ __forceinline__ void el_compress_lum(const LevelView& L, const Box& b
     if (!ok[n]) continue;
     C ecn = ec[n];
     if (ss3[n]) {
-      C div = (x1[n] - x0[n]) * g.inv_dx[0] + (y1[n] - y0[n]) * g.inv_dx[1] +
-              (z1[n] - z0[n]) * g.inv_dx[2];
-      C a = halve(dt * gm1 * div);
+      C div = mul_u(x1[n] - x0[n], g.inv_dx[0]) + mul_u(y1[n] - y0[n], g.inv_dx[1]) +
+              mul_u(z1[n] - z0[n], g.inv_dx[2]);
+      C a = halve(mul_u(mul_u(dt, gm1), div));
       // (e0 + de)(1 - a)/(1 + a) - e0
-      ecn = hdiv(ecn * (C(1.f) - a) - twice(a * bg.e0), C(1.f) + a);
+      ecn = hdiv(mul_u(ecn, C(1.f) - a) - twice(mul_u(a, bg.e0)), C(1.f) + a);
     }
-    if (lm[n]) ecn = ecn + lum * dt * lw[n];
+    if (lm[n]) ecn = ecn + mul_u(mul_u(lum, dt), lw[n]);
     st(e, c[n], ecn);
     // e/rho - e0/rho0 = (de - eps0 drho)/(rho0 + drho)
-    if (do_eps) st((Arith<T>*)S.eps, c[n], hdiv(ecn - bg.eps0 * dr[n], bg.rho0 + dr[n]));
+    if (do_eps) st((Arith<T>*)S.eps, c[n], eps_dev(ecn, dr[n], bg));
   }
 }
 
@@ -478,7 +491,7 @@ __device__ __forceinline__ Arith<T> diff_flux(const LevelView& L, const St<T>* _
   using C = Arith<T>;
   int m = f - L.st[d];
   C rf = dfr ? rho0 : rho0 + halve(ld(rho, m) + ld(rho, f));
-  return rf * (ld(eps, f) - ld(eps, m)) * K;
+  return mul_u(rf, ld(eps, f) - ld(eps, m)) * K;
 }
 
 // EPSX: the separate transport kernels follow, and the x sweep's preparation (e/rho
@@ -549,11 +562,11 @@ __device__ __forceinline__ void el_diffuse(const LevelView& L, const Box& b, con
       st(e, c[n], en);
       if (EPSX) {
         const C rc = ld(rho, c[n]);
-        st((Arith<T>*)S.w[0], c[n], hdiv(as_stored(en) - bg.eps0 * rc, bg.rho0 + rc));
+        st((Arith<T>*)S.w[0], c[n], eps_dev(as_stored(en), rc, bg));
       }
     } else if (edge[n]) {
       const C rc = ld(rho, ce[n]);
-      st((Arith<T>*)S.w[0], ce[n], hdiv(ld(e, ce[n]) - bg.eps0 * rc, bg.rho0 + rc));
+      st((Arith<T>*)S.w[0], ce[n], eps_dev(ld(e, ce[n]), rc, bg));
     }
   }
 }
@@ -599,7 +612,7 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
   const C rc = ld(rho, c);
   const C ec = ld((const St<T>*)L.q[F_E], c);
   if (eps_only) {
-    st((Arith<T>*)S.eps, c, hdiv(ec - bg.eps0 * rc, bg.rho0 + rc));
+    st((Arith<T>*)S.eps, c, eps_dev(ec, rc, bg));
     return;
   }
   // every load first, then the arithmetic and the stores
@@ -620,7 +633,7 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
       wv[m] = hdiv(sub_ky(pm[m], bg.V[m], drf), bg.rho0 + drf);
     }
   }
-  st((Arith<T>*)S.eps, c, hdiv(ec - bg.eps0 * rc, bg.rho0 + rc));
+  st((Arith<T>*)S.eps, c, eps_dev(ec, rc, bg));
 #pragma unroll
   for (int m = 0; m < 3; ++m) st((Arith<T>*)S.w[m], c, wv[m]);
 }
@@ -643,12 +656,12 @@ __device__ __forceinline__ void el_tflux(const LevelView& L, const Box& b, const
     const C Adt = kc[K_ADT + d];
     const C du = ld((const St<T>*)L.q[F_VX + d], c);
     const C u = add_k(du, bg.V[d]);
-    const C cour = u * kc[K_DTDX + d];
+    const C cour = mul_u(u, kc[K_DTDX + d]);
     const C F0 = is0(bg.V[d]) ? C(0.f) : kc[K_F0 + d];
     C drs = upwind((const St<T>*)L.q[F_RHO], c, sd, u, cour);
-    Fv = (bg.rho0 * du + drs * u) * Adt;        // F - rho0 V_d A dt
+    Fv = (mul_u(bg.rho0, du) + mul_u(drs, u)) * Adt;  // F - rho0 V_d A dt
     C des = upwind((const Arith<T>*)S.eps, c, sd, u, cour);
-    Ev = bg.eps0 * Fv + des * add_k(Fv, F0);        // E - eps0 rho0 V_d A dt
+    Ev = mul_u(bg.eps0, Fv) + mul_u(des, add_k(Fv, F0));  // E - eps0 rho0 V_d A dt
   }
   st((Arith<T>*)S.F, c, Fv);
   st((Arith<T>*)S.E, c, Ev);
@@ -683,17 +696,17 @@ __device__ __forceinline__ void el_tmom(const LevelView& L, const Box& b, const 
       if (c3[d] >= 2 && c3[d] < L.s[d] - 2) {
         C uc = add_k(halve(ld(vd, c) + ld(vd, c + sd)), bg.V[d]);
         C Fc = halve(ld(F, c) + ld(F, c + sd));
-        C ws = d == 0 ? upwind((const St<T>*)S.w[m], c + sd, sd, uc, uc * dtdx)
-                      : upwind((const Arith<T>*)S.w[m], c + sd, sd, uc, uc * dtdx);
-        P = ky_add(bg.V[m], Fc, ws * add_k(Fc, F0));
+        C ws = d == 0 ? upwind((const St<T>*)S.w[m], c + sd, sd, uc, mul_u(uc, dtdx))
+                      : upwind((const Arith<T>*)S.w[m], c + sd, sd, uc, mul_u(uc, dtdx));
+        P = ky_add(bg.V[m], Fc, mul_u(ws, add_k(Fc, F0)));
       }
     } else if (c3[d] >= 2 && c3[d] < L.s[d] - 1 && c3[m] >= 1) {
       const int sm = L.st[m];
       C ue = add_k(halve(ld(vd, c - sm) + ld(vd, c)), bg.V[d]);
       C Fe = halve(ld(F, c - sm) + ld(F, c));
-      C ws = d == 0 ? upwind((const St<T>*)S.w[m], c, sd, ue, ue * dtdx)
-                    : upwind((const Arith<T>*)S.w[m], c, sd, ue, ue * dtdx);
-      P = ky_add(bg.V[m], Fe, ws * add_k(Fe, F0));
+      C ws = d == 0 ? upwind((const St<T>*)S.w[m], c, sd, ue, mul_u(ue, dtdx))
+                    : upwind((const Arith<T>*)S.w[m], c, sd, ue, mul_u(ue, dtdx));
+      P = ky_add(bg.V[m], Fe, mul_u(ws, add_k(Fe, F0)));
     }
     Pv[m] = P;
   }
@@ -925,7 +938,7 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
       const int r = m0 - 3 + i;
       rw[0] = rw[1]; rw[1] = rw[2]; rw[2] = rw[3]; rw[3] = nr;
       sw[0] = sw[1]; sw[1] = sw[2]; sw[2] = sw[3];
-      sw[3] = hdiv(ne - bg.eps0 * nr, bg.rho0 + nr);
+      sw[3] = eps_dev(ne, nr, bg);
       er[0] = er[1]; er[1] = er[2]; er[2] = ne;
       vw[0] = vw[1]; vw[1] = vw[2]; vw[2] = nv;
 #pragma unroll
@@ -1057,7 +1070,7 @@ __device__ __forceinline__ void el_sweep(const Item<T>& it, unsigned unit,
       const int r = m0 - 1 + i;
       const C rc = nr, ec = ne, vc = nv, pi0 = np[0], pi1 = np[1], pi2 = np[2];
       if (i + 1 < nit) load(r + 1, nr, ne, nv, np);
-      const C ep = hdiv(ec - bg.eps0 * rc, bg.rho0 + rc);
+      const C ep = eps_dev(ec, rc, bg);
       const C r_m2 = shfl_up(rc, 2), r_m1 = shfl_up(rc, 1), r_p1 = shfl_dn(rc, 1);
       const C e_m2 = shfl_up(ep, 2), e_m1 = shfl_up(ep, 1), e_p1 = shfl_dn(ep, 1);
       const bool pok = pos && (unsigned)r < (unsigned)sMU;
@@ -1220,15 +1233,18 @@ __device__ __forceinline__ void el_vrec_source(const LevelView& L, const Box& b,
         continue;
       }
       C drf = halve(rm[n][d] + rc[n]);
-      C rinv = hdiv(C(1.f), bg.rho0 + drf);
-      C v = sub_ky(pv[n][d], bg.V[d], drf) * rinv;
-      C acc = (gm1 * (ec[n] - em[n][d]) * rinv + (fc[n] - fm[n][d])) * g.inv_dx[d];
-      C vn = v - h * acc;
-      if (KICK2) {
+      C rinv = div_u(C(1.f), bg.rho0 + drf);
+      C v = mul_u(sub_ky(pv[n][d], bg.V[d], drf), rinv);
+      C acc = mul_u(mul_u(mul_u(gm1, ec[n] - em[n][d]), rinv) + (fc[n] - fm[n][d]),
+                    g.inv_dx[d]);
+      C vn = v - mul_u(h, acc);
+      if (KICK2) {  // the same expression as the kick's
         const C rf = bg.rho0 + drf;
-        const C acc2 = (hdiv(gm1 * (ec[n] - em[n][d]), rf) + (fc[n] - fm[n][d])) * g.inv_dx[d];
-        vn = as_stored(vn) - h * acc2;
-        if (write_pi) st((Arith<T>*)S.pi[d], c[n], bg.rho0 * vn + drf * add_k(vn, bg.V[d]));
+        const C acc2 = mul_u(div_u(mul_u(gm1, ec[n] - em[n][d]), rf) + (fc[n] - fm[n][d]),
+                             g.inv_dx[d]);
+        vn = as_stored(vn) - mul_u(h, acc2);
+        if (write_pi)
+          st((Arith<T>*)S.pi[d], c[n], mul_u(bg.rho0, vn) + mul_u(drf, add_k(vn, bg.V[d])));
       }
       st((St<T>*)L.q[F_VX + d], c[n], vn);
     }

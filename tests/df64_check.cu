@@ -7,6 +7,9 @@
 //   a * b        <= 2^-46 |a b| + 2^-120
 //   a / b        <= 2^-42 |a / b| + 2^-120  (the device's reciprocal estimate is
 //                                    checked on the GPU; here it is IEEE division)
+//   mul_u, div_u (unnormalised): the same bounds as *, /; |lo| <= 2^-21 |hi|; the sign
+//   of hi is the sign of the value; as operands of +, * and / they keep the bounds of
+//   the two operations added
 // The absolute floor 2^-120: below about 2^-102 the low float of a result leaves the
 // normal range of float, so its relative precision falls (on the device, where
 // subnormals flush to zero, the loss is below 2^-126 absolutely); the stencils' fields
@@ -63,6 +66,34 @@ int main() {
       std::printf("FAIL sign %.17g\n", A);
       return 1;
     }
+    // unnormalised product and quotient, alone and as operands (value of a pair:
+    // hi + lo in double, exact to 2^-53)
+    const double C3 = to_double(to_df64(operand()));
+    const df64 c = to_df64(C3);
+    const df64 mu = mul_u(a, b), qu = div_u(a, b);
+    const double MU = (double)mu.hi + (double)mu.lo, QU = (double)qu.hi + (double)qu.lo;
+    const double AB = A * B, QB = A / B;
+    if (std::fabs(MU - AB) > 0x1.0p-46 * std::fabs(AB) + 0x1.0p-120 ||
+        std::fabs(QU - QB) > 0x1.0p-42 * std::fabs(QB) + 0x1.0p-120 ||
+        std::fabs(mu.lo) > 0x1.0p-21 * std::fabs(mu.hi) ||
+        std::fabs(qu.lo) > 0x1.0p-21 * std::fabs(qu.hi) || gt0(mu) != (AB > 0) ||
+        lt0(mu) != (AB < 0) || gt0(qu) != (QB > 0)) {
+      std::printf("FAIL mul_u/div_u %.17g %.17g: %.17g %.17g\n", A, B, MU, QU);
+      return 1;
+    }
+    // (as operands: where the unnormalised pair's low float is itself normal, |value|
+    // >= 2^-100; below, its absolute error, within the floor, is what a quotient scales)
+    const double s2 = to_double(mu + c), m2 = to_double(mu * c), q2 = to_double(mu / c);
+    const double m3 = to_double(mul_u(qu, c) + c);
+    if (std::fabs(AB) >= 0x1.0p-100 && std::fabs(QB) >= 0x1.0p-100 &&
+        (std::fabs(s2 - (AB + C3)) > 0x1.0p-45 * (std::fabs(AB) + std::fabs(C3)) + 0x1.0p-120 ||
+        std::fabs(m2 - AB * C3) > 0x1.0p-45 * std::fabs(AB * C3) + 0x1.0p-120 ||
+        std::fabs(q2 - AB / C3) > 0x1.0p-41 * std::fabs(AB / C3) + 0x1.0p-120 ||
+        std::fabs(m3 - (QB * C3 + C3)) >
+            0x1.0p-41 * (std::fabs(QB * C3) + std::fabs(C3)) + 0x1.0p-120)) {
+      std::printf("FAIL unnormalised operands %.17g %.17g %.17g\n", A, B, C3);
+      return 1;
+    }
   }
   // the conversions against the compiler's: to_double of a normalised pair is the
   // correctly rounded sum to within one unit in the last place, and a float converts
@@ -100,8 +131,10 @@ int main() {
       return 1;
     }
     const df64 cc = canonical(c), back = to_df64(v);
+    // (bit for bit but for the sign of a zero lo: to_df64 gives -0 beside a negative hi
+    // where the cut leaves +0; the pairs' values are the same double)
     if (f2u(cc.hi) != f2u(c.hi) || f2u(cc.lo) != f2u(c.lo) || f2u(back.hi) != f2u(c.hi) ||
-        f2u(back.lo) != f2u(c.lo)) {
+        (f2u(back.lo) != f2u(c.lo) && !(back.lo == 0.f && c.lo == 0.f))) {
       std::printf("FAIL canonical round trip %.17g: (%a, %a) -> (%a, %a)\n", v, c.hi, c.lo,
                   back.hi, back.lo);
       return 1;
