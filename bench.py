@@ -151,7 +151,7 @@ ARRAYS_PER_ELEM = {
 # box, 20.09 / 20.09 / 13.47 MB, a smaller case of the same kernel, whose traffic
 # grows with the box); `traffic` scales them to the mean box of the timed launches.
 # A kernel without a capture of its current code reports null.
-_TMOM_DF64 = (20.0865e6 + 20.0855e6 + 13.4705e6) / 3 / 80**3
+_TMOM_DF64 = (20.0865e6 + 20.0840e6 + 13.4705e6) / 3 / 80**3
 TRAFFIC_PER_ELEM = {("precision_5x128^3", 4, "sweep"): (80.2e6 + 99.5e6 + 85.0e6) / 3 / 144**3,
                     ("precision_5x128^3", 8, "tmom"): _TMOM_DF64,
                     ("nested_3x64^3_fp64", 8, "tmom"): _TMOM_DF64}
