@@ -117,10 +117,11 @@ __device__ __forceinline__ df64 ky_add(df64 k, df64 y, df64 z) {
   return k.hi == 0.f ? z : mul_u(k, y) + z;
 }
 // e/rho - e0/rho0 of a cell from its deviations, (de - eps0 drho)/(rho0 + drho): one
-// expression for every kernel that forms it, so that all give the same bits
+// expression for every kernel that forms it, so that all give the same bits.  Its
+// consumers only take differences of it, so the quotient stays unnormalised.
 template <class C, class B>
 __device__ __forceinline__ C eps_dev(C de, C dr, const B& bg) {
-  return hdiv(de - mul_u(bg.eps0, dr), bg.rho0 + dr);
+  return div_u(de - mul_u(bg.eps0, dr), bg.rho0 + dr);
 }
 // a value as a store of the state keeps it (the FP64 state's stores cut lo)
 __device__ __forceinline__ float as_stored(float v) { return v; }
@@ -630,7 +631,7 @@ __device__ __forceinline__ void el_tprep(const LevelView& L, const Box& b, const
     if (c3[m] >= 1) {
       // Pi/rho_face - V = (dPi - V drf)/(rho0 + drf)
       C drf = halve(rm[m] + rc);
-      wv[m] = hdiv(sub_ky(pm[m], bg.V[m], drf), bg.rho0 + drf);
+      wv[m] = div_u(sub_ky(pm[m], bg.V[m], drf), bg.rho0 + drf);
     }
   }
   st((Arith<T>*)S.eps, c, eps_dev(ec, rc, bg));
