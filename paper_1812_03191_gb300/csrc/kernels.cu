@@ -1586,6 +1586,7 @@ __device__ __forceinline__ df64 dsqrt(df64 x) {
 // sound speed and |v| within about 2^-44, so the limit is within that of the FP64
 // one; the FP64 pipe would take ~40 operations per cell).  The maxima, the minimum
 // over levels and dt itself are FP64.  Also flags NaN, rho <= 0 or e <= 0.
+constexpr int kDtCells = 4;
 template <class T>
 __device__ __forceinline__ void el_dt_level(const LevelView& L, const Box& b, int level, double gg,
                                             Arith<T> gga, int hydro, DevScalars* ds,
@@ -1598,38 +1599,80 @@ __device__ __forceinline__ void el_dt_level(const LevelView& L, const Box& b, in
   if (threadIdx.x == 0) bad_s = 0;
   __syncthreads();
   A mx[3] = {A(0.f), A(0.f), A(0.f)};
-  int i, j, k;  // b is the active box: multiply-shift division, no 64-bit divide
-  if (decode(b, tid, i, j, k)) {
-    int c = (k * L.s[1] + j) * L.s[0] + i;
-    if constexpr (sizeof(T) == 4) {
-      float rho = (float)rho0 + val((const St<T>*)L.q[F_RHO], c);
-      float e = (float)e0 + val((const St<T>*)L.q[F_E], c);
-      if (!(rho > 0.f) || !(e > 0.f)) bad_s = 1;
-      if (hydro) {
-        float cs = sqrtf((float)gg * e / rho);
-        const float Vb[3] = {(float)V0, (float)V1, (float)V2};
+  // kDtCells cells per thread (strided by the block size), every load first: a block
+  // then issues one atomic per axis for kBlock kDtCells cells
+  int cc[kDtCells];
+  bool in[kDtCells];
+#pragma unroll
+  for (int u = 0; u < kDtCells; ++u) {
+    const unsigned t = (tid / kBlock) * kBlock * kDtCells + u * kBlock + threadIdx.x;
+    int i, j, k;  // b is the active box: multiply-shift division, no 64-bit divide
+    in[u] = decode(b, t, i, j, k);
+    cc[u] = in[u] ? (k * L.s[1] + j) * L.s[0] + i : (L.G * L.s[1] + L.G) * L.s[0] + L.G;
+  }
+  const St<T>* v3[3] = {(const St<T>*)L.q[F_VX], (const St<T>*)L.q[F_VX + 1],
+                        (const St<T>*)L.q[F_VX + 2]};
+  bool bad = false;
+  if constexpr (sizeof(T) == 4) {
+    float rho[kDtCells], e[kDtCells], va[kDtCells][3], vb[kDtCells][3];
+#pragma unroll
+    for (int u = 0; u < kDtCells; ++u) {
+      const int c = cc[u];
+      rho[u] = val((const St<T>*)L.q[F_RHO], c);
+      e[u] = val((const St<T>*)L.q[F_E], c);
+      if (hydro)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          const St<T>* v = (const St<T>*)L.q[F_VX + d];
-          float v0 = fabsf(Vb[d] + val(v, c)), v1 = fabsf(Vb[d] + val(v, c + L.st[d]));
-          mx[d] = cs + (v0 > v1 ? v0 : v1);
+          va[u][d] = val(v3[d], c);
+          vb[u][d] = val(v3[d], c + L.st[d]);
+        }
+    }
+    const float Vb[3] = {(float)V0, (float)V1, (float)V2};
+#pragma unroll
+    for (int u = 0; u < kDtCells; ++u) {
+      if (!in[u]) continue;
+      const float r = (float)rho0 + rho[u], ee = (float)e0 + e[u];
+      if (!(r > 0.f) || !(ee > 0.f)) bad = true;
+      if (hydro) {
+        const float cs = sqrtf((float)gg * ee / r);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float v0 = fabsf(Vb[d] + va[u][d]), v1 = fabsf(Vb[d] + vb[u][d]);
+          const float m = cs + (v0 > v1 ? v0 : v1);
+          mx[d] = m > mx[d] ? m : mx[d];
         }
       }
-    } else {
-      const A rho = bg.rho0 + ld((const St<T>*)L.q[F_RHO], c);
-      const A e = bg.e0 + ld((const St<T>*)L.q[F_E], c);
-      if (!gt0(rho) || !gt0(e)) bad_s = 1;
-      if (hydro) {
-        const A cs = dsqrt(hdiv(gga * e, rho));
+    }
+  } else {
+    A rho[kDtCells], e[kDtCells], va[kDtCells][3], vb[kDtCells][3];
+#pragma unroll
+    for (int u = 0; u < kDtCells; ++u) {
+      const int c = cc[u];
+      rho[u] = ld((const St<T>*)L.q[F_RHO], c);
+      e[u] = ld((const St<T>*)L.q[F_E], c);
+      if (hydro)
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          const St<T>* v = (const St<T>*)L.q[F_VX + d];
-          const A v0 = dabs(bg.V[d] + ld(v, c)), v1 = dabs(bg.V[d] + ld(v, c + L.st[d]));
-          mx[d] = cs + dmax(v0, v1);
+          va[u][d] = ld(v3[d], c);
+          vb[u][d] = ld(v3[d], c + L.st[d]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < kDtCells; ++u) {
+      if (!in[u]) continue;
+      const A r = bg.rho0 + rho[u], ee = bg.e0 + e[u];
+      if (!gt0(r) || !gt0(ee)) bad = true;
+      if (hydro) {
+        const A cs = dsqrt(hdiv(gga * ee, r));
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const A v0 = dabs(bg.V[d] + va[u][d]), v1 = dabs(bg.V[d] + vb[u][d]);
+          mx[d] = dmax(mx[d], cs + dmax(v0, v1));
         }
       }
     }
   }
+  if (bad) bad_s = 1;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     A v = warp_max_t(mx[d]);
@@ -2359,6 +2402,7 @@ int sweep_slots(int esz, int d) {
 
 // elements per chunk of each op (one chunk = one block pass)
 int op_chunk_elems(int op, int esz) {
+  if (op == OP_DT_LEVEL) return kBlock * kDtCells;
   return op == OP_FORCE_LEVEL ? kBlock * kForceCells : kBlock * cells_per_thread(op, esz);
 }
 
