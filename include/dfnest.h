@@ -256,9 +256,13 @@ int df_check_division(const double* a, const double* b, int n, double* max_ulp);
 
 /* Self-check of the double-float arithmetic (a float pair hi + lo, the FP64 state's
  * stencil arithmetic) on the current device: n operand pairs from host arrays;
- * worst[4] receives the largest error of conversion from double, sum, product and
- * quotient against FP64, each in units of its bound: 2^-45 |a|, 2^-46 (|a| + |b|),
- * 2^-46 |a b| + 2^-120, 2^-42 |a / b| + 2^-120 (<= 1 passes).  Synchronous. */
+ * worst[8] (caller-owned, 8 doubles) receives the largest error of conversion from
+ * double, sum, product and quotient against FP64, each in units of its bound: 2^-45
+ * |a|, 2^-46 (|a| + |b|), 2^-46 |a b| + 2^-120, 2^-42 |a / b| + 2^-120; then of the
+ * unnormalised product and quotient the stencils use where a result only feeds more
+ * arithmetic (the same two bounds), the size of their low parts against 2^-21 of
+ * their high parts, and a sum taking the unnormalised product, against 2^-45 (|a b| +
+ * |a|) + 2^-120 (<= 1 passes).  Synchronous. */
 int df_check_df64(const double* a, const double* b, int n, double* worst);
 
 /* Measured FP64 throughput of the device: a kernel of independent chains of

@@ -223,11 +223,13 @@ def measure_fp64_peak(device=0, repeats=5):
 
 def check_df64(a, b):
     """worst errors of the device's double-float conversion, sum, product and
-    quotient against FP64, each in units of its bound (<= 1 passes)"""
+    quotient against FP64, of the unnormalised product and quotient, the size of
+    their low parts and a sum taking one of them, each in units of its bound
+    (<= 1 passes)"""
     lib = load()
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
-    w = np.zeros(4)
+    w = np.zeros(8)
     _check(lib.df_check_df64(_dp(a), _dp(b), a.size, _dp(w)))
     return w
 

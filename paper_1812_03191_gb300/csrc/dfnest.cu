@@ -1785,13 +1785,13 @@ int df_check_df64(const double* a_host, const double* b_host, int n, double* wor
   double *da = nullptr, *db = nullptr, *dw = nullptr;
   CK(cudaMalloc(&da, n * sizeof(double)));
   CK(cudaMalloc(&db, n * sizeof(double)));
-  CK(cudaMalloc(&dw, 4 * sizeof(double)));
+  CK(cudaMalloc(&dw, 8 * sizeof(double)));
   CK(cudaMemcpy(da, a_host, n * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(db, b_host, n * sizeof(double), cudaMemcpyHostToDevice));
-  CK(cudaMemset(dw, 0, 4 * sizeof(double)));
+  CK(cudaMemset(dw, 0, 8 * sizeof(double)));
   launch_df64_check(da, db, n, dw, nullptr);
   CK(cudaGetLastError());
-  CK(cudaMemcpy(worst, dw, 4 * sizeof(double), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(worst, dw, 8 * sizeof(double), cudaMemcpyDeviceToHost));
   cudaFree(da);
   cudaFree(db);
   cudaFree(dw);

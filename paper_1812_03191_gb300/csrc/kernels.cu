@@ -2071,9 +2071,10 @@ __global__ void __launch_bounds__(kBlock) k_dfma_probe(int iters, double* sink) 
 // double-float arithmetic on the device versus FP64 on n operand pairs: the largest
 // error of conversion, sum, product and quotient, each in units of its bound
 // (2^-45 |a|; 2^-46 (|a| + |b|); 2^-46 |a b| + 2^-120; 2^-42 |a / b| + 2^-120)
+constexpr int kDf64Checks = 8;  // entries of df_check_df64's worst[]
 __global__ void k_df64_check(const double* a, const double* b, int n, double* worst) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double w[4] = {0.0, 0.0, 0.0, 0.0};
+  double w[kDf64Checks] = {};
   if (t < n) {
     const df64 x = to_df64(a[t]), y = to_df64(b[t]);
     const double A = to_double(x), B = to_double(y);
@@ -2081,8 +2082,19 @@ __global__ void k_df64_check(const double* a, const double* b, int n, double* wo
     w[1] = fabs(to_double(x + y) - (A + B)) / (0x1.0p-46 * (fabs(A) + fabs(B)) + 1e-300);
     w[2] = fabs(to_double(x * y) - A * B) / (0x1.0p-46 * fabs(A * B) + 0x1.0p-120);
     w[3] = fabs(to_double(x / y) - A / B) / (0x1.0p-42 * fabs(A / B) + 0x1.0p-120);
+    // the unnormalised product and quotient: their values (hi + lo in FP64) within
+    // the same bounds, lo within 2^-21 of hi, and as an operand of the next sum
+    const df64 mu = mul_u(x, y), qu = div_u(x, y);
+    const double AB = A * B, Q = A / B;
+    w[4] = fabs((double)mu.hi + (double)mu.lo - AB) / (0x1.0p-46 * fabs(AB) + 0x1.0p-120);
+    w[5] = fabs((double)qu.hi + (double)qu.lo - Q) / (0x1.0p-42 * fabs(Q) + 0x1.0p-120);
+    if (mu.hi != 0.f) w[6] = fabs((double)mu.lo) / (0x1.0p-21 * fabs((double)mu.hi));
+    if (qu.hi != 0.f) w[6] = fmax(w[6], fabs((double)qu.lo) / (0x1.0p-21 * fabs((double)qu.hi)));
+    if (fabs(AB) >= 0x1.0p-100)
+      w[7] = fabs(to_double(mu + x) - (AB + A)) /
+             (0x1.0p-45 * (fabs(AB) + fabs(A)) + 0x1.0p-120);
   }
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < kDf64Checks; ++q) {
     double u = w[q];
     for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
     if ((threadIdx.x & 31) == 0 && u > 0.0)

@@ -1,6 +1,8 @@
 """The double-float arithmetic of the FP64 stencils on the device (the hardware
 reciprocal estimate included) against FP64: conversion, sum, product and quotient,
-each within its bound, on operands spread over 40 decades."""
+each within its bound, on operands spread over 40 decades; the unnormalised product
+and quotient within the same bounds, their low parts within 2^-21 of their high
+parts, and a sum taking the unnormalised product within its bound."""
 import numpy as np
 import pytest
 
@@ -28,7 +30,8 @@ def test_double_float_operations_on_the_device():
                 * (1 + rng.random(n)))
 
     w = binding.check_df64(operands(), operands())
-    print("worst error / bound (conversion, sum, product, quotient):", w)
+    print("worst error / bound (conversion, sum, product, quotient, unnormalised "
+          "product, unnormalised quotient, their low parts, sum with one):", w)
     assert np.all(w <= 1.0), w
 
 
