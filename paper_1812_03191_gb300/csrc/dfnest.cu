@@ -610,7 +610,6 @@ struct Builder {
     it.ds = r.ds;
     it.gm1 = to_arith<C>(r.P.gamma - 1.0);
     it.lum = to_arith<C>(r.P.L);
-    it.chi = to_arith<C>(r.P.chi);
     it.av = to_arith<C>(r.P.av_c2);
     it.gg = r.P.gamma * (r.P.gamma - 1.0);
     it.gga = to_arith<C>(it.gg);

@@ -194,7 +194,7 @@ inline df64 to_arith<df64>(double x) {
 // FP32 kernels: GB300's FP64 pipe is 1/64 of its FP32 rate)
 template <class C>
 struct Geo {
-  C inv_dx[3], area[3], dcoef[3], inv_vol;
+  C inv_dx[3], area[3], inv_vol;
 };
 
 template <class C>
@@ -203,7 +203,6 @@ inline Geo<C> make_geo(const LevelView& L) {
   for (int d = 0; d < 3; ++d) {
     g.inv_dx[d] = to_arith<C>(L.inv_dx[d]);
     g.area[d] = to_arith<C>(L.area[d]);
-    g.dcoef[d] = to_arith<C>(L.dcoef[d]);
   }
   g.inv_vol = to_arith<C>(L.inv_vol);
   return g;
@@ -355,7 +354,7 @@ struct __align__(16) Item {
   double* partials;     // force partials (this level's first, or the run's for the final sum)
   double* ring;         // force history
   long long* ring_pos;
-  Arith<T> gm1, lum, chi, av;
+  Arith<T> gm1, lum, av;
   Arith<T> gga;         // gamma (gamma - 1), the time step's per-cell factor
   double gg, rho0d, e0d, V[3], dt_fixed;
   int ring_cap, npart, level, band, flags, bc_lo, bc_hi;
