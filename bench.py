@@ -715,8 +715,8 @@ def time_sim(sim, cfg, args, stream, flush, local, fused):
                 shapes=shapes, fused=fused)
 
 
-# SURVEY-defined algorithmic bytes per cell-update of a whole level step: the five
-# fields read and written once (rho, e, v_x, v_y, v_z)
+# algorithmic bytes per cell-update of a whole level step: the five fields read and
+# written once (rho, e, v_x, v_y, v_z)
 B_ALG = {8: 80, 4: 40}
 # kernels launched once per level step (or per sweep of one), each over one level's
 # active cells: the units one launch processes are that level's cells
