@@ -14,8 +14,8 @@ with inputs resident in HBM; `e2e` through the C ABI with the state uploaded fro
 pinned host memory and the force read back every step.  Multi-GPU runs are
 independent replicas (weak scaling, no collective on the data path).
 
---impl reference times the FP64 CPU oracle (the reference arm of this build) on
-whole coarse steps of the same workload.
+--impl reference times the FP64 CPU oracle (the reference arm) on whole coarse steps
+of the same workload.
 """
 from __future__ import annotations
 
