@@ -441,6 +441,23 @@ def test_full_size_nested_config(transport):
     assert np.abs(F[1:]).max() <= 1e-12 * abs(F[0]), F  # the transverse symmetry
 
 
+def test_full_size_precision_config():
+    """The precision configuration the bench's headline line times, at full size (5
+    levels of 128^3, coarse box [-16,16]^3, Mach 1.2, chi=1, Gaussian luminosity L_c),
+    FP64 state, the default transport form and tile order, 3 coarse steps (93 level
+    steps) against the oracle's OpenMP build, every field of every level compared."""
+    cfg = I.precision()
+    p = cfg["params"]
+    lo, hi = cfg["lo"], cfg["hi"]
+    sim = binding.Sim(cfg["n_levels"], cfg["n"], lo, hi, cfg["G"], p)
+    orc = Oracle(cfg["n_levels"], cfg["n"], lo, hi, cfg["G"], p, omp=True)
+    sim.step(3)
+    orc.step(3)
+    assert_parity(sim, orc, p, label="precision 5x128^3, 3 coarse steps")
+    F, _ = sim.force()
+    assert np.abs(F[1:]).max() <= 1e-12 * abs(F[0]), F  # the transverse symmetry
+
+
 def test_unhealthy_state_reported():
     p = I.base_params(GM=0.0, chi=0.5)
     sim = binding.Sim(1, 16, (-2.0,) * 3, (2.0,) * 3, I.DEFAULT_G, p)
