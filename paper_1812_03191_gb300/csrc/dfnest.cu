@@ -471,10 +471,6 @@ struct Plan {
   DtFinal* d_fins = nullptr;
   size_t cap_items = 0, cap_starts = 0, cap_fins = 0;
   cudaGraphExec_t gexec = nullptr;
-  // the executable graph of the plan before its last invalidation: the next capture
-  // tries to update it in place (same launch sequence, new parameters) before it
-  // instantiates a new one
-  cudaGraphExec_t stale = nullptr;
   long long kernels = 0;
   bool valid = false;
   Allocator al;  // the owner's
@@ -482,7 +478,6 @@ struct Plan {
 
 void plan_free(Plan& p) {
   if (p.gexec) cudaGraphExecDestroy(p.gexec);
-  if (p.stale) cudaGraphExecDestroy(p.stale);
   dev_free(p.al, p.d_items);
   dev_free(p.al, p.d_starts);
   dev_free(p.al, p.d_fins);
@@ -493,8 +488,7 @@ void plan_free(Plan& p) {
 
 void plan_invalidate(Plan& p) {
   if (p.gexec) {
-    if (p.stale) cudaGraphExecDestroy(p.stale);
-    p.stale = p.gexec;
+    cudaGraphExecDestroy(p.gexec);
     p.gexec = nullptr;
   }
   p.valid = false;
@@ -1071,22 +1065,7 @@ int plan_step(Plan& plan, Exec& x, int nsteps) {
     long long n = plan_run<T>(plan, x, false);
     cudaError_t e = cudaStreamEndCapture(x.st, &g);
     if (e != cudaSuccess) return fail(DF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    if (plan.stale) {
-      // a pool that admitted or released a run usually keeps its launch sequence (the
-      // same operators in the same order; items, chunk counts and grids change):
-      // update the previous executable graph instead of instantiating a new one.
-      // The stream is drained first, so no launch of the old graph is in flight.
-      CK(cudaStreamSynchronize(x.st));
-      cudaGraphExecUpdateResultInfo info;
-      if (cudaGraphExecUpdate(plan.stale, g, &info) == cudaSuccess) {
-        plan.gexec = plan.stale;
-      } else {
-        (void)cudaGetLastError();  // the update's failure is not sticky: clear it
-        cudaGraphExecDestroy(plan.stale);
-      }
-      plan.stale = nullptr;
-    }
-    if (!plan.gexec) e = cudaGraphInstantiate(&plan.gexec, g, 0);
+    e = cudaGraphInstantiate(&plan.gexec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(DF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
     plan.kernels = n;
