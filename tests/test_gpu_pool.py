@@ -118,62 +118,6 @@ def test_pool_runs_match_their_own_oracles():
         pool.close()
 
 
-def test_full_size_batched_config_sampled():
-    """The batched workload the bench times, at full size: its 64 uneven runs (2-4
-    levels of 32^3-96^3) in one pool, 2 coarse steps, in FP64 state and in FP32 state
-    with the pool's autotuned tiles (the bench's launch configuration).  Three runs
-    are sampled (the most and the fewest cell-updates, the first with the luminosity
-    on besides) and each is compared with its own oracle: FP64 fields to 1e-10 and the
-    force within the bound the density difference implies; FP32 state to the
-    precision form's targets (fields 1e-4, force 1e-3 relative)."""
-    from oracle import Oracle
-    from test_gpu_parity import force_bound
-    runs = I.batched()
-    work = [r["n"] ** 3 * (2 ** r["n_levels"] - 1) for r in runs]
-    pick = [int(np.argmax(work)), int(np.argmin(work))]
-    pick.append(next(k for k, r in enumerate(runs) if r["params"]["L"] > 0 and k not in pick))
-    orcs = {}
-    for k in pick:
-        r = runs[k]
-        orcs[k] = Oracle(r["n_levels"], r["n"], r["lo"], r["hi"], r["G"], r["params"],
-                         omp=True)
-        orcs[k].step(2)
-    for precision in (binding.DF_FP64, binding.DF_FP32_STATE):
-        pool = binding.Pool(64 << 30, precision=precision)
-        slots = [pool.admit(r["n_levels"], r["n"], r["lo"], r["hi"], r["G"], r["params"])
-                 for r in runs]
-        if precision == binding.DF_FP32_STATE:
-            pool.autotune()
-        pool.step(2)
-        for k in pick:
-            r, orc, slot = runs[k], orcs[k], slots[k]
-            p = r["params"]
-            vs = max(p["mach"] * p["cs"], 1e-3)
-            worst = rho_err = 0.0
-            for l in range(r["n_levels"]):
-                for f in range(5):
-                    e = np.abs(pool.get_field(slot, l, f) - orc.get_field(l, f)).max()
-                    e /= 1.0 if f < 2 else vs
-                    worst = max(worst, e)
-                    rho_err = max(rho_err, e) if f == 0 else rho_err
-            F, t = pool.force(slot)
-            Fo = orc.force()
-            dF = np.abs(F - Fo).max()
-            print(f"precision {precision} run {k} ({r['n_levels']} x {r['n']}^3): fields "
-                  f"{worst:.2e}, force {dF:.2e} abs, {dF / np.abs(Fo).max():.2e} rel")
-            if precision == binding.DF_FP64:
-                view = _View(r["n_levels"], r["n"], r["hi"][0])
-                assert worst <= 1e-10, (k, worst)
-                assert dF <= force_bound(view, orc, p, rho_err), (k, F, Fo)
-                assert abs(t - orc.t) <= 1e-13 * orc.t
-            else:
-                assert worst <= 1e-4, (k, worst)
-                assert dF <= 1e-3 * np.abs(Fo).max(), (k, F, Fo)
-        pool.close()
-    for orc in orcs.values():
-        orc.close()
-
-
 def test_pool_budget_admission_and_release():
     shape = (2, 24)
     need = binding.run_bytes(shape[0], shape[1], I.DEFAULT_G)
