@@ -86,3 +86,30 @@ def test_kernel_hbm_table():
     assert t["source"]["frac"] == pytest.approx(gbs / 6800.0, abs=1e-3)
     assert t["sweep"]["gbs"] == pytest.approx(11 * 4 * mean_box / (68.5 / 930 / 1e3) / 1e9,
                                               abs=0.1)
+
+
+def test_roofline_block_arithmetic():
+    """the dominant level-step kernel's roofline: 80 B (FP64) per cell-update of one
+    level step of one n^3 level over its mean launch time; traffic = the captured DRAM
+    bytes per box element times the mean box; the whole step on the same bytes"""
+    cfg = I.precision()
+    n = cfg["n"]
+    cu = bench.cell_updates_per_step(cfg)
+    kinds = {"tmom": (108.0, 1860), "tupdate": (98.0, 1860), "dt": (4.0, 100)}
+    m = {"kinds": kinds, "ms": 210.0, "steps": 10}
+    r = bench.roofline_block(cfg, m, cu, 8, 6786.2, "measured")
+    assert r["kernel"] == "tmom"  # the largest share among the level-step kernels
+    avg_s = 108.0 / 1860 / 1e3
+    assert r["achieved"] == pytest.approx(80 * n**3 / avg_s / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6786.2)
+    boxes = bench.level_step_boxes(cfg)
+    per_elem = bench.TRAFFIC_PER_ELEM[(cfg["name"], 8, "tmom")]
+    assert r["traffic"] == pytest.approx(per_elem * sum(boxes) / len(boxes))
+    # the capture's 34.9 B per box element of the 80^3 launches
+    assert per_elem == pytest.approx(34.9, abs=0.05)
+    assert r["step"]["frac"] == pytest.approx(cu * 80 / (21.0 / 1e3) / 1e9 / 6786.2)
+    assert r["share_of_kernel_time"] == pytest.approx(108.0 / 210.0)
+    # an FP32 run has no traffic figure for tmom and takes 40 B
+    r32 = bench.roofline_block(cfg, m, cu, 4, 6786.2, "measured")
+    assert r32["traffic"] is None
+    assert r32["achieved"] == pytest.approx(r["achieved"] / 2)
